@@ -1,0 +1,474 @@
+// ts_api.cu -- the batch object and the C ABI entry points of libts.so
+// (declared in include/ts.h).  Host code only orchestrates: every step of the
+// path runs in the kernels of ts_neighbor.cu, ts_pair.cu, ts_md.cu,
+// ts_fire.cu and ts_adjoint.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ts_api.h"
+
+using namespace ts;
+
+namespace ts {
+
+const char* kNoError = "";
+
+bool cuda_ok(ts_batch* b, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return true;
+  if (b) {
+    b->last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    b->sticky = TS_ERR_CUDA;
+  }
+  return false;
+}
+
+ts_status fail(ts_batch* b, ts_status st, const std::string& msg) {
+  if (b) b->last_error = msg;
+  return st;
+}
+
+static int grid_for(int64_t n, int threads) {
+  int64_t g = (n + threads - 1) / threads;
+  if (g < 1) g = 1;
+  if (g > 148 * 16) g = 148 * 16;
+  return (int)g;
+}
+
+template <typename T>
+static bool alloc(ts_batch* b, T*& p, size_t count) {
+  p = nullptr;
+  if (count == 0) count = 1;
+  size_t bytes = sizeof(T) * count;
+  if (!cuda_ok(b, cudaMalloc((void**)&p, bytes), "cudaMalloc")) return false;
+  b->allocations.push_back((void*)p);
+  b->bytes_allocated += bytes;
+  return true;
+}
+
+size_t scratch_bytes(int64_t Ncap, int64_t Bcap, int64_t Ccap, int32_t max_nbrs, bool f64) {
+  size_t per_slot = f64 ? (3 * 8 /*xd*/ + 3 * 8 /*vd*/ + 3 * 8 /*Fd*/ + 8 /*minv*/ + 3 * 8 /*xrd*/ +
+                           3 * 8 * 3 /*tmp d0,d1*/ + 4 * 8 /*tmp d2*/ + 2 * 3 * 8 /*gd*/)
+                        : (2 * 16 /*x*/ + 2 * 16 /*v*/ + 16 /*F*/ + 2 * 16 /*xr*/ + 2 * 16 + 2 * 16 /*tmp f*/ +
+                           2 * 16 /*g*/);
+  per_slot += 4 * 4 /*perm sys bin nn*/ + 3 * 4 /*tmp i*/ + (size_t)max_nbrs * 4 + 8 * 8 / 32 /*partials*/;
+  size_t per_sys = 8 * 4 + 9 * 8 * 3 + 6 * 4 + 4 * 4 + 8 + (size_t)kNCodes * (32 + 24);
+  return per_slot * (size_t)Ncap + per_sys * (size_t)Bcap + (size_t)Ccap * 8;
+}
+
+}  // namespace ts
+
+// ---------------------------------------------------------------------------
+extern "C" ts_status ts_batch_create(const ts_batch_config* cfg, const ts_potential* pots, int n_pots, ts_batch** out) {
+  if (!out) return TS_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!cfg || !pots || n_pots < 1 || n_pots > kMaxPots) return TS_ERR_INVALID_ARG;
+  if (cfg->atom_capacity < 1 || cfg->system_capacity < 1 || cfg->max_neighbors < 0 ||
+      (cfg->precision != TS_MIXED && cfg->precision != TS_FP64))
+    return TS_ERR_INVALID_ARG;
+  for (int q = 0; q < n_pots; q++) {
+    const ts_potential& P = pots[q];
+    if (P.kind < 0 || P.kind > 2 || !(P.skin >= 0) || !(P.cutoff > 0 || P.kind == TS_SOFT_SPHERE)) return TS_ERR_INVALID_ARG;
+    if (P.kind == TS_SOFT_SPHERE && !(P.p[0] > 0 && P.p[2] >= 1.0)) return TS_ERR_INVALID_ARG;
+    if (P.kind == TS_LJ && !(P.p[0] > 0)) return TS_ERR_INVALID_ARG;
+  }
+  ts_batch* b = new ts_batch();
+  b->cfg = *cfg;
+  if (cfg->autotune_cache) { b->cache_path = cfg->autotune_cache; b->cfg.autotune_cache = b->cache_path.c_str(); }
+  b->f64 = cfg->precision == TS_FP64;
+  b->n_pots = n_pots;
+  for (int q = 0; q < n_pots; q++) b->pots[q] = pots[q];
+  b->max_nbrs = cfg->max_neighbors > 0 ? cfg->max_neighbors : 128;
+  b->Bcap = cfg->system_capacity;
+  b->Ncap = ((cfg->atom_capacity + 31LL * cfg->system_capacity) + 31) / 32 * 32;
+  b->Wcap = b->Ncap / 32;
+  b->Ccap = cfg->atom_capacity + 27LL * cfg->system_capacity;
+  if (b->Ncap >= (1LL << 31) || b->Ccap >= (1LL << 31)) { delete b; return TS_ERR_UNSUPPORTED; }
+  size_t need = scratch_bytes(b->Ncap, b->Bcap, b->Ccap, b->max_nbrs, b->f64);
+  if (cfg->memory_budget_bytes && need > cfg->memory_budget_bytes) { delete b; return TS_ERR_BUDGET; }
+  if (!cuda_ok(b, cudaSetDevice(cfg->device), "cudaSetDevice")) { delete b; return TS_ERR_CUDA; }
+  // device potential table
+  DevPot dp[kMaxPots];
+  memset(dp, 0, sizeof dp);
+  for (int q = 0; q < n_pots; q++) {
+    const ts_potential& P = pots[q];
+    DevPot& D = dp[q];
+    D.kind = P.kind; D.shift = P.shift;
+    for (int c = 0; c < 3; c++) { D.pd[c] = P.p[c]; D.pf[c] = (float)P.p[c]; }
+    double rc = P.kind == TS_SOFT_SPHERE ? P.p[0] : P.cutoff;
+    D.rc2d = rc * rc; D.rc2f = (float)(rc * rc);
+    double phic = 0;
+    if (P.shift && P.kind == TS_LJ) { double s = P.p[0] / rc, s6 = s * s * s * s * s * s; phic = 4 * P.p[1] * (s6 * s6 - s6); }
+    if (P.shift && P.kind == TS_MORSE) { double e = exp(-P.p[1] * (rc - P.p[2])); phic = P.p[0] * (e * e - 2 * e); }
+    D.phicd = phic; D.phicf = (float)phic;
+    D.skin = P.skin;
+    D.rlist = rc + P.skin; D.rlist2d = D.rlist * D.rlist; D.rlist2f = (float)D.rlist2d;
+    b->rc[q] = rc;
+  }
+  bool ok = true;
+  SysArrays& S = b->S;
+  SlotArrays& A = b->A;
+  int64_t N = b->Ncap, B = b->Bcap;
+  ok = ok && alloc(b, b->d_pots, kMaxPots) && alloc(b, b->d_err, 4) && alloc(b, b->d_counters, 4) &&
+       alloc(b, b->d_step, 2);
+  ok = ok && alloc(b, S.seg_start, B) && alloc(b, S.n_atoms, B) && alloc(b, S.caller_off, B + 1) && alloc(b, S.pot, B) &&
+       alloc(b, S.uid, B) && alloc(b, S.bin_off, B) && alloc(b, S.bin_cap, B) && alloc(b, S.warp_start, B) &&
+       alloc(b, S.warp_end, B) && alloc(b, S.h, 9 * B) && alloc(b, S.hinv, 9 * B) && alloc(b, S.href, 9 * B) &&
+       alloc(b, S.nb, 3 * B) && alloc(b, S.reach, 3 * B) && alloc(b, S.relist, B) && alloc(b, S.dirty, B) &&
+       alloc(b, S.kT, B) && alloc(b, S.shift, 2 * B * kNCodes) && alloc(b, S.shiftd, 3 * B * kNCodes);
+  ok = ok && alloc(b, A.perm, N) && alloc(b, A.sys, N) && alloc(b, A.bin, N) && alloc(b, A.nn, N) &&
+       alloc(b, A.nbr, (size_t)b->max_nbrs * N) && alloc(b, A.tmp_i0, N) && alloc(b, A.tmp_i1, N) &&
+       alloc(b, A.tmp_i2, N);
+  if (b->f64) {
+    ok = ok && alloc(b, A.xd, 3 * N) && alloc(b, A.vd, 3 * N) && alloc(b, A.Fd, 3 * N) && alloc(b, A.minvd, N) &&
+         alloc(b, A.xrd, 3 * N) && alloc(b, A.tmp_d0, 3 * N) && alloc(b, A.tmp_d1, 3 * N) &&
+         alloc(b, A.tmp_d2, 4 * N) && alloc(b, A.gd0, 3 * N) && alloc(b, A.gd1, 3 * N);
+  } else {
+    ok = ok && alloc(b, A.xh, N) && alloc(b, A.xl, N) && alloc(b, A.vh, N) && alloc(b, A.vl, N) && alloc(b, A.F, N) &&
+         alloc(b, A.xrh, N) && alloc(b, A.xrl, N) && alloc(b, A.tmp_f0, 2 * N) && alloc(b, A.tmp_f1, N) &&
+         alloc(b, A.tmp_f2, N) && alloc(b, A.tmp_f3, N) && alloc(b, A.g0, N) && alloc(b, A.g1, N);
+  }
+  ok = ok && alloc(b, b->d_partial, (size_t)kPartialStride * b->Wcap) && alloc(b, b->d_warp_sys, b->Wcap) &&
+       alloc(b, b->d_count, b->Ccap) && alloc(b, b->d_cstart, b->Ccap) &&
+       alloc(b, b->d_bsum, (b->Ccap + 1023) / 1024 + 1) && alloc(b, b->d_starts, B + 1) &&
+       alloc(b, b->d_Eint, B) && alloc(b, b->d_Wint, 9 * B) && alloc(b, b->d_scal, 16 * B) &&
+       alloc(b, b->d_gparam_part, 4 * b->Wcap) && alloc(b, b->d_gacc, 3 * kMaxPots);
+  if (ok) ok = cuda_ok(b, cudaMemcpy(b->d_pots, dp, sizeof dp, cudaMemcpyHostToDevice), "copy pots");
+  if (ok) ok = cuda_ok(b, cudaMemset(b->d_err, 0, 16), "memset") && cuda_ok(b, cudaMemset(b->d_counters, 0, 32), "memset");
+  if (ok) ok = cuda_ok(b, cudaMemset(A.perm, 0xff, sizeof(int32_t) * N), "memset") &&
+               cuda_ok(b, cudaMemset(A.sys, 0xff, sizeof(int32_t) * N), "memset") &&
+               cuda_ok(b, cudaMemset(A.nn, 0, sizeof(int32_t) * N), "memset") &&
+               cuda_ok(b, cudaMemset(b->d_partial, 0, sizeof(double) * kPartialStride * b->Wcap), "memset");
+  if (ok) ok = cuda_ok(b, cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming), "event");
+  if (!ok) { ts_batch_destroy(b); return TS_ERR_CUDA; }
+  b->dp_host.assign(dp, dp + kMaxPots);
+  autotune_load(b);
+  *out = b;
+  return TS_OK;
+}
+
+extern "C" ts_status ts_batch_destroy(ts_batch* b) {
+  if (!b) return TS_ERR_INVALID_ARG;
+  cudaSetDevice(b->cfg.device);
+  cudaDeviceSynchronize();
+  for (void* p : b->allocations) cudaFree(p);
+  if (b->ev) cudaEventDestroy(b->ev);
+  for (auto& g : b->graphs) if (g.exec) cudaGraphExecDestroy(g.exec);
+  delete b;
+  return TS_OK;
+}
+
+extern "C" const char* ts_last_error(const ts_batch* b) {
+  if (!b) return "null batch";
+  return b->last_error.c_str();
+}
+
+extern "C" ts_status ts_batch_counters(const ts_batch* b, int64_t* launches, int64_t* relists) {
+  if (!b) return TS_ERR_INVALID_ARG;
+  if (launches) *launches = b->launches;
+  if (relists) {
+    int64_t c[4] = {0, 0, 0, 0};
+    cudaMemcpy(c, b->d_counters, sizeof c, cudaMemcpyDeviceToHost);
+    *relists = c[0];
+  }
+  return TS_OK;
+}
+
+extern "C" ts_status ts_batch_memory_model(const ts_batch* b, double* bytes_per_atom, double* bytes_per_system) {
+  if (!b) return TS_ERR_INVALID_ARG;
+  size_t a = scratch_bytes(1, 0, 0, b->max_nbrs, b->f64) + 8;   // + one bin per atom
+  size_t s = scratch_bytes(0, 1, 27, b->max_nbrs, b->f64) + scratch_bytes(31, 0, 0, b->max_nbrs, b->f64);
+  if (bytes_per_atom) *bytes_per_atom = (double)a;
+  if (bytes_per_system) *bytes_per_system = (double)s;
+  return TS_OK;
+}
+
+extern "C" ts_status ts_batch_poll(ts_batch* b, void* stream, int timeout_ms) {
+  if (!b) return TS_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!cuda_ok(b, cudaEventRecord(b->ev, st), "event record")) return TS_ERR_CUDA;
+  auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    cudaError_t q = cudaEventQuery(b->ev);
+    if (q == cudaSuccess) break;
+    if (q != cudaErrorNotReady) { cuda_ok(b, q, "event query"); return TS_ERR_CUDA; }
+    double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (timeout_ms >= 0 && ms > timeout_ms) return TS_ERR_NOT_READY;
+  }
+  int32_t e = 0;
+  if (!cuda_ok(b, cudaMemcpy(&e, b->d_err, sizeof e, cudaMemcpyDeviceToHost), "read error word")) return TS_ERR_CUDA;
+  if (e) cudaMemset(b->d_err, 0, sizeof e);
+  ts_status st2 = b->sticky;
+  b->sticky = TS_OK;
+  if (st2 != TS_OK) return st2;
+  if (e & kErrBadSystemIdx) return fail(b, TS_ERR_INVALID_ARG, "system_idx is not non-decreasing or a system is empty");
+  if (e & kErrNeighborOverflow) return fail(b, TS_ERR_NEIGHBOR_OVERFLOW, "an atom has more neighbours than max_neighbors");
+  if (e & kErrUnsupported) return fail(b, TS_ERR_UNSUPPORTED, "non-periodic axis or cell outside the supported range");
+  if (e & kErrNonFinite) return fail(b, TS_ERR_NONFINITE, "non-finite or out-of-range position or cell");
+  if (e & kErrTimeout) return fail(b, TS_ERR_TIMEOUT, "a bounded device wait ran out");
+  return TS_OK;
+}
+
+// ---------------------------------------------------------------------------
+namespace ts {
+
+// Derive the batch layout from system_idx: per-system caller offsets, padded
+// segments, warp ranges and bin reservations.  One device->host copy.
+ts_status derive_topology(ts_batch* b, const ts_state* s, cudaStream_t st) {
+  int32_t B = s->n_systems;
+  int64_t N = s->n_atoms;
+  if (B < 1 || N < 1 || B > b->Bcap || N > b->cfg.atom_capacity)
+    return fail(b, TS_ERR_BUDGET, "state exceeds the batch capacity");
+  if (!cuda_ok(b, cudaMemsetAsync(b->d_starts, 0xff, sizeof(int64_t) * (B + 1), st), "memset")) return TS_ERR_CUDA;
+  k_sys_bounds<<<grid_for(N, 256), 256, 0, st>>>(N, s->system_idx, B, b->d_starts, b->d_err);
+  b->launches++;
+  std::vector<int64_t> starts(B);
+  std::vector<int32_t> pot(B);
+  int32_t err = 0;
+  if (!cuda_ok(b, cudaMemcpyAsync(starts.data(), b->d_starts, sizeof(int64_t) * B, cudaMemcpyDeviceToHost, st), "d2h") ||
+      !cuda_ok(b, cudaMemcpyAsync(pot.data(), s->pot_idx, sizeof(int32_t) * B, cudaMemcpyDeviceToHost, st), "d2h") ||
+      !cuda_ok(b, cudaMemcpyAsync(&err, b->d_err, sizeof err, cudaMemcpyDeviceToHost, st), "d2h") ||
+      !cuda_ok(b, cudaStreamSynchronize(st), "sync"))
+    return TS_ERR_CUDA;
+  if (err & kErrBadSystemIdx) {
+    cudaMemset(b->d_err, 0, 4);
+    return fail(b, TS_ERR_INVALID_ARG, "system_idx must be non-decreasing, in range, with every system non-empty");
+  }
+  std::vector<int64_t> caller_off(B + 1), seg(B);
+  std::vector<int32_t> n(B), bin_off(B), bin_cap(B), ws(B), we(B);
+  for (int k = 0; k < B; k++) {
+    if (starts[k] < 0) return fail(b, TS_ERR_INVALID_ARG, "empty system");
+    caller_off[k] = starts[k];
+  }
+  caller_off[B] = N;
+  int64_t slot = 0, bins = 0;
+  std::vector<int32_t> warp_sys;
+  for (int k = 0; k < B; k++) {
+    n[k] = (int32_t)(caller_off[k + 1] - caller_off[k]);
+    if (n[k] < 1) return fail(b, TS_ERR_INVALID_ARG, "empty system");
+    if (n[k] > (int64_t)kJMask) return fail(b, TS_ERR_UNSUPPORTED, "system larger than 2^22 atoms");
+    if (pot[k] < 0 || pot[k] >= b->n_pots) return fail(b, TS_ERR_INVALID_ARG, "pot_idx out of range");
+    seg[k] = slot;
+    int64_t npad = (n[k] + 31) / 32 * 32;
+    ws[k] = (int32_t)(slot / 32);
+    slot += npad;
+    we[k] = (int32_t)(slot / 32);
+    for (int w = ws[k]; w < we[k]; w++) warp_sys.push_back(k);
+    bin_off[k] = (int32_t)bins;
+    bin_cap[k] = std::max<int32_t>(27, n[k]);
+    bins += bin_cap[k];
+  }
+  if (slot > b->Ncap || bins > b->Ccap) return fail(b, TS_ERR_BUDGET, "padded layout exceeds capacity");
+  b->B = B; b->N = N; b->Npad = slot; b->nwarps = (int32_t)(slot / 32); b->nbins = bins;
+  b->h_caller_off = caller_off; b->h_n = n; b->h_pot = pot; b->h_seg = seg;
+  SysArrays& S = b->S;
+  bool ok = cuda_ok(b, cudaMemcpyAsync(S.seg_start, seg.data(), 8 * B, cudaMemcpyHostToDevice, st), "h2d") &&
+            cuda_ok(b, cudaMemcpyAsync(S.n_atoms, n.data(), 4 * B, cudaMemcpyHostToDevice, st), "h2d") &&
+            cuda_ok(b, cudaMemcpyAsync(S.caller_off, caller_off.data(), 8 * (B + 1), cudaMemcpyHostToDevice, st), "h2d") &&
+            cuda_ok(b, cudaMemcpyAsync(S.pot, pot.data(), 4 * B, cudaMemcpyHostToDevice, st), "h2d") &&
+            cuda_ok(b, cudaMemcpyAsync(S.bin_off, bin_off.data(), 4 * B, cudaMemcpyHostToDevice, st), "h2d") &&
+            cuda_ok(b, cudaMemcpyAsync(S.bin_cap, bin_cap.data(), 4 * B, cudaMemcpyHostToDevice, st), "h2d") &&
+            cuda_ok(b, cudaMemcpyAsync(S.warp_start, ws.data(), 4 * B, cudaMemcpyHostToDevice, st), "h2d") &&
+            cuda_ok(b, cudaMemcpyAsync(S.warp_end, we.data(), 4 * B, cudaMemcpyHostToDevice, st), "h2d") &&
+            cuda_ok(b, cudaMemcpyAsync(b->d_warp_sys, warp_sys.data(), 4 * warp_sys.size(), cudaMemcpyHostToDevice, st), "h2d");
+  if (s->uid) {
+    ok = ok && cuda_ok(b, cudaMemcpyAsync(S.uid, s->uid, 4 * B, cudaMemcpyDeviceToDevice, st), "d2d");
+  } else {
+    std::vector<uint32_t> u(B);
+    for (int k = 0; k < B; k++) u[k] = (uint32_t)k;
+    ok = ok && cuda_ok(b, cudaMemcpyAsync(S.uid, u.data(), 4 * B, cudaMemcpyHostToDevice, st), "h2d") &&
+         cuda_ok(b, cudaStreamSynchronize(st), "sync");
+  }
+  ok = ok && cuda_ok(b, cudaMemsetAsync(b->A.perm, 0xff, 4 * b->Ncap, st), "memset") &&
+       cuda_ok(b, cudaMemsetAsync(b->A.sys, 0xff, 4 * b->Ncap, st), "memset");
+  if (!ok) return TS_ERR_CUDA;
+  k_init_slots<<<B, 128, 0, st>>>(B, S, b->A);
+  b->launches++;
+  std::vector<int32_t> ones(B, 1);
+  ok = cuda_ok(b, cudaMemcpyAsync(S.relist, ones.data(), 4 * B, cudaMemcpyHostToDevice, st), "h2d") &&
+       cuda_ok(b, cudaMemcpyAsync(S.dirty, ones.data(), 4 * B, cudaMemcpyHostToDevice, st), "h2d") &&
+       cuda_ok(b, cudaMemsetAsync(b->d_count, 0, 4 * b->Ccap, st), "memset") &&
+       cuda_ok(b, cudaStreamSynchronize(st), "sync");
+  if (!ok) return TS_ERR_CUDA;
+  b->topo_valid = true;
+  b->first_import = true;
+  b->graphs_valid = false;
+  return TS_OK;
+}
+
+ts_status check_state(ts_batch* b, const ts_state* s, bool need_vel) {
+  if (!b || !s) return TS_ERR_INVALID_ARG;
+  if (!s->pos || !s->mass || !s->cell || !s->system_idx || !s->pot_idx || (need_vel && !s->vel))
+    return fail(b, TS_ERR_INVALID_ARG, "null state pointer");
+  if (s->n_systems < 1 || s->n_atoms < 1) return fail(b, TS_ERR_INVALID_ARG, "empty state");
+  return TS_OK;
+}
+
+// Per-call prologue: topology (if needed), cell geometry, image shifts,
+// position import with dirty / skin flags.
+ts_status prologue(ts_batch* b, ts_state* s, cudaStream_t st, bool import_vel) {
+  cudaSetDevice(b->cfg.device);
+  if (!b->topo_valid || s->n_systems != b->B || s->n_atoms != b->N) {
+    ts_status r = derive_topology(b, s, st);
+    if (r != TS_OK) return r;
+  }
+  int B = b->B;
+  k_geometry<<<(B + 127) / 128, 128, 0, st>>>(B, b->S, s->cell, s->pbc, b->d_pots, b->d_err);
+  k_shift_table<<<(int)(((int64_t)B * kNCodes + 255) / 256), 256, 0, st>>>(B, b->S);
+  int g = grid_for(b->Npad, 256);
+  if (b->f64) k_import_pos<true><<<g, 256, 0, st>>>(b->Npad, b->S, b->A, s->pos, b->d_pots, !b->first_import, b->d_err);
+  else k_import_pos<false><<<g, 256, 0, st>>>(b->Npad, b->S, b->A, s->pos, b->d_pots, !b->first_import, b->d_err);
+  b->launches += 3;
+  if (import_vel) {
+    if (b->f64) k_import_vel<true><<<g, 256, 0, st>>>(b->Npad, b->A, s->vel, s->mass);
+    else k_import_vel<false><<<g, 256, 0, st>>>(b->Npad, b->A, s->vel, s->mass);
+    b->launches++;
+  }
+  b->first_import = false;
+  return cuda_ok(b, cudaGetLastError(), "prologue launch") ? TS_OK : TS_ERR_CUDA;
+}
+
+// Re-list every flagged system: bin, counting sort (canonical order inside a
+// bin), state move, explicit list.  Kernels skip unflagged systems, so the
+// sequence is safe to issue every step (and to capture in a graph).
+void relist(ts_batch* b, cudaStream_t st, bool move_fire) {
+  int B = b->B;
+  int64_t Np = b->Npad, nb = b->nbins;
+  int g = grid_for(Np, 256);
+  k_zero_bins<<<B, 256, 0, st>>>(B, b->S, b->d_count);
+  if (b->f64) k_bin_atoms<true><<<g, 256, 0, st>>>(Np, b->S, b->A, b->d_count);
+  else k_bin_atoms<false><<<g, 256, 0, st>>>(Np, b->S, b->A, b->d_count);
+  int nblk = (int)((nb + 1023) / 1024);
+  k_scan_block<<<nblk, 1024, 0, st>>>(nb, b->d_count, b->d_cstart, b->d_bsum);
+  k_scan_sums<<<1, 1024, 0, st>>>(nblk, b->d_bsum);
+  k_scan_add<<<nblk, 1024, 0, st>>>(nb, b->d_cstart, b->d_bsum);
+  k_scatter_ids<<<g, 256, 0, st>>>(Np, b->S, b->A, b->d_cstart);
+  if (b->f64) {
+    k_final_slot<true><<<g, 256, 0, st>>>(Np, b->S, b->A, b->d_cstart, b->d_count, move_fire);
+    k_copy_back<true><<<g, 256, 0, st>>>(Np, b->S, b->A, move_fire);
+    k_build_list<true><<<grid_for(Np, 128), 128, 0, st>>>(Np, b->S, b->A, b->d_cstart, b->d_count, b->d_pots,
+                                                          b->max_nbrs, b->Ncap, b->d_err);
+  } else {
+    k_final_slot<false><<<g, 256, 0, st>>>(Np, b->S, b->A, b->d_cstart, b->d_count, move_fire);
+    k_copy_back<false><<<g, 256, 0, st>>>(Np, b->S, b->A, move_fire);
+    k_build_list<false><<<grid_for(Np, 128), 128, 0, st>>>(Np, b->S, b->A, b->d_cstart, b->d_count, b->d_pots,
+                                                           b->max_nbrs, b->Ncap, b->d_err);
+  }
+  k_after_relist<<<(B + 127) / 128, 128, 0, st>>>(B, b->S, b->d_counters);
+  b->launches += 11;
+}
+
+void pair(ts_batch* b, cudaStream_t st, bool ew, bool only_dirty) {
+  int threads = b->pair_threads;
+  int blocks = (int)(((int64_t)b->nwarps * 32 + threads - 1) / threads);
+  if (b->f64) {
+    if (ew) k_pair<true, true><<<blocks, threads, 0, st>>>(b->nwarps, b->d_warp_sys, b->S, b->A, b->d_pots, b->Ncap, only_dirty, b->d_partial);
+    else k_pair<true, false><<<blocks, threads, 0, st>>>(b->nwarps, b->d_warp_sys, b->S, b->A, b->d_pots, b->Ncap, only_dirty, b->d_partial);
+  } else {
+    if (ew) k_pair<false, true><<<blocks, threads, 0, st>>>(b->nwarps, b->d_warp_sys, b->S, b->A, b->d_pots, b->Ncap, only_dirty, b->d_partial);
+    else k_pair<false, false><<<blocks, threads, 0, st>>>(b->nwarps, b->d_warp_sys, b->S, b->A, b->d_pots, b->Ncap, only_dirty, b->d_partial);
+  }
+  b->launches++;
+}
+
+void reduce_sys(ts_batch* b, cudaStream_t st, double* E, double* stress, double* KE) {
+  int B = b->B;
+  k_reduce_sys<<<(B * 32 + 127) / 128, 128, 0, st>>>(B, b->S, b->d_partial, E, stress, KE, b->d_Eint, b->d_Wint);
+  b->launches++;
+}
+
+void clear_dirty(ts_batch* b, cudaStream_t st) {
+  k_clear_dirty<<<(b->B + 127) / 128, 128, 0, st>>>(b->B, b->S);
+  b->launches++;
+}
+
+void export_state(ts_batch* b, cudaStream_t st, double* pos, double* vel) {
+  int g = grid_for(b->Npad, 256);
+  if (b->f64) k_export_state<true><<<g, 256, 0, st>>>(b->Npad, b->A, pos, vel);
+  else k_export_state<false><<<g, 256, 0, st>>>(b->Npad, b->A, pos, vel);
+  b->launches++;
+}
+
+void export_forces(ts_batch* b, cudaStream_t st, double* F) {
+  int g = grid_for(b->Npad, 256);
+  if (b->f64) k_export_forces<true><<<g, 256, 0, st>>>(b->Npad, b->A, F);
+  else k_export_forces<false><<<g, 256, 0, st>>>(b->Npad, b->A, F);
+  b->launches++;
+}
+
+// forces current for every system at the current positions
+void ensure_forces(ts_batch* b, cudaStream_t st) {
+  relist(b, st, false);
+  pair(b, st, true, true);
+  clear_dirty(b, st);
+}
+
+}  // namespace ts
+
+extern "C" ts_status ts_neighbor_build(ts_batch* b, ts_state* s, int force_rebuild, void* stream) {
+  ts_status r = check_state(b, s, false);
+  if (r != TS_OK) return r;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (force_rebuild) b->topo_valid = false;
+  r = prologue(b, s, st, false);
+  if (r != TS_OK) return r;
+  relist(b, st, false);
+  export_state(b, st, s->pos, nullptr);
+  return cuda_ok(b, cudaGetLastError(), "ts_neighbor_build") ? TS_OK : TS_ERR_CUDA;
+}
+
+extern "C" ts_status ts_pair_forces(ts_batch* b, ts_state* s, double* F, double* E, double* stress, void* stream) {
+  ts_status r = check_state(b, s, false);
+  if (r != TS_OK) return r;
+  cudaStream_t st = (cudaStream_t)stream;
+  r = prologue(b, s, st, false);
+  if (r != TS_OK) return r;
+  relist(b, st, false);
+  pair(b, st, true, false);
+  reduce_sys(b, st, E, stress, nullptr);
+  if (F) export_forces(b, st, F);
+  export_state(b, st, s->pos, nullptr);
+  clear_dirty(b, st);
+  return cuda_ok(b, cudaGetLastError(), "ts_pair_forces") ? TS_OK : TS_ERR_CUDA;
+}
+
+extern "C" ts_status ts_md_step(ts_batch* b, ts_state* s, const ts_md_params* p, int n_steps, double* E, double* KE,
+                                void* stream) {
+  ts_status r = check_state(b, s, true);
+  if (r != TS_OK) return r;
+  if (!p || n_steps < 0 || !(p->dt > 0) || (p->kind != TS_NVE && p->kind != TS_LANGEVIN) ||
+      (p->kind == TS_LANGEVIN && (!p->kT || !(p->gamma >= 0))))
+    return fail(b, TS_ERR_INVALID_ARG, "bad MD parameters");
+  cudaStream_t st = (cudaStream_t)stream;
+  r = prologue(b, s, st, true);
+  if (r != TS_OK) return r;
+  if (p->kind == TS_LANGEVIN &&
+      !cuda_ok(b, cudaMemcpyAsync(b->S.kT, p->kT, 8 * b->B, cudaMemcpyDeviceToDevice, st), "kT"))
+    return TS_ERR_CUDA;
+  ensure_forces(b, st);
+  double c1 = exp(-p->gamma * p->dt);
+  r = md_loop(b, st, p, n_steps, c1, E != nullptr || KE != nullptr);
+  if (r != TS_OK) return r;
+  reduce_sys(b, st, E, nullptr, KE);
+  export_state(b, st, s->pos, s->vel);
+  return cuda_ok(b, cudaGetLastError(), "ts_md_step") ? TS_OK : TS_ERR_CUDA;
+}
+
+extern "C" ts_status ts_neighbor_export(ts_batch* b, int32_t* j_out, int32_t* img_out, int32_t* count_out, void* stream) {
+  if (!b || !j_out || !img_out || !count_out) return TS_ERR_INVALID_ARG;
+  if (!b->topo_valid) return fail(b, TS_ERR_INVALID_ARG, "no neighbour lists yet");
+  cudaStream_t st = (cudaStream_t)stream;
+  int64_t blocks = (b->Npad + 127) / 128;
+  k_export_list<<<(int)(blocks < 1 ? 1 : blocks), 128, 0, st>>>(b->Npad, b->S, b->A, b->max_nbrs, b->Ncap, j_out,
+                                                                 img_out, count_out);
+  b->launches++;
+  return cuda_ok(b, cudaGetLastError(), "ts_neighbor_export") ? TS_OK : TS_ERR_CUDA;
+}
+
+extern "C" int32_t ts_batch_max_neighbors(const ts_batch* b) { return b ? b->max_nbrs : 0; }

@@ -1,0 +1,86 @@
+// ts_api.h -- the batch object shared by the host-side translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "ts_kernels.cuh"
+
+struct ts_graph_entry {
+  int kind = -1;            // 0 = MD loop
+  int n_steps = 0;
+  int md_kind = 0;
+  bool need_e = false;
+  double dt = 0, c1 = 0;
+  uint32_t seed = 0;
+  cudaStream_t stream = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+struct ts_batch {
+  ts_batch_config cfg{};
+  std::string cache_path;
+  bool f64 = false;
+  int n_pots = 0;
+  ts_potential pots[ts::kMaxPots];
+  double rc[ts::kMaxPots];
+  std::vector<ts::DevPot> dp_host;
+  int32_t max_nbrs = 128;
+  int64_t Ncap = 0, Wcap = 0, Ccap = 0;
+  int32_t Bcap = 0;
+  // topology
+  bool topo_valid = false, first_import = true;
+  int32_t B = 0, nwarps = 0;
+  int64_t N = 0, Npad = 0, nbins = 0;
+  std::vector<int64_t> h_caller_off, h_seg;
+  std::vector<int32_t> h_n, h_pot;
+  // device
+  ts::SysArrays S{};
+  ts::SlotArrays A{};
+  ts::DevPot* d_pots = nullptr;
+  int32_t* d_err = nullptr;
+  int64_t* d_counters = nullptr;
+  uint64_t* d_step = nullptr;
+  double* d_partial = nullptr;
+  int32_t* d_warp_sys = nullptr;
+  int32_t* d_count = nullptr;
+  int32_t* d_cstart = nullptr;
+  int32_t* d_bsum = nullptr;
+  int64_t* d_starts = nullptr;
+  double* d_Eint = nullptr;
+  double* d_Wint = nullptr;
+  double* d_scal = nullptr;         // per-system FIRE / scratch scalars [16 B]
+  double* d_gparam_part = nullptr;  // per-warp parameter-gradient partials [4 Wcap]
+  double* d_gacc = nullptr;
+  std::vector<void*> allocations;
+  size_t bytes_allocated = 0;
+  cudaEvent_t ev = nullptr;
+  // launch shapes (autotuned)
+  int pair_threads = 128;
+  bool use_graphs = true;
+  std::vector<ts_graph_entry> graphs;
+  bool graphs_valid = false;
+  // bookkeeping
+  int64_t launches = 0;
+  ts_status sticky = TS_OK;
+  std::string last_error;
+};
+
+namespace ts {
+bool cuda_ok(ts_batch* b, cudaError_t e, const char* what);
+ts_status fail(ts_batch* b, ts_status st, const std::string& msg);
+size_t scratch_bytes(int64_t Ncap, int64_t Bcap, int64_t Ccap, int32_t max_nbrs, bool f64);
+ts_status derive_topology(ts_batch* b, const ts_state* s, cudaStream_t st);
+ts_status check_state(ts_batch* b, const ts_state* s, bool need_vel);
+ts_status prologue(ts_batch* b, ts_state* s, cudaStream_t st, bool import_vel);
+void relist(ts_batch* b, cudaStream_t st, bool move_fire);
+void pair(ts_batch* b, cudaStream_t st, bool ew, bool only_dirty);
+void reduce_sys(ts_batch* b, cudaStream_t st, double* E, double* stress, double* KE);
+void clear_dirty(ts_batch* b, cudaStream_t st);
+void export_state(ts_batch* b, cudaStream_t st, double* pos, double* vel);
+void export_forces(ts_batch* b, cudaStream_t st, double* F);
+void ensure_forces(ts_batch* b, cudaStream_t st);
+ts_status md_loop(ts_batch* b, cudaStream_t st, const ts_md_params* p, int n_steps, double c1, bool need_e);
+void autotune_load(ts_batch* b);
+}  // namespace ts

@@ -1,0 +1,276 @@
+// ts_internal.cuh -- device-side data layout and helpers of libts.so.
+//
+// Layout (B300-first): every system occupies a contiguous segment of
+// "slots" padded to a multiple of 32, so a warp never straddles two systems:
+// the potential, cell and image table of a warp are uniform, and per-system
+// energy/virial reduce with warp shuffles into one FP64 partial per warp (no
+// scatter atomics).  Inside a segment, atoms are sorted by cell-list bin
+// (re-sorted at every re-listing), so neighbour gathers stay local in L1/L2.
+//
+// Mixed precision stores a position as hi + lo: hi on a 2^-12 A grid (exact
+// in FP32 for |x| < 2048 A), lo = x - hi (|lo| <= 2^-13).  A pair vector
+// d = x_j + n h - x_i is then formed as (hi_j + S_hi - hi_i) -- exact, all
+// terms on the grid -- plus (lo_j + S_lo - lo_i), so d carries one rounding
+// only, independent of the box size.  The lattice image shift S = n h is
+// stored the same way per (system, image code).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/ts.h"
+
+namespace ts {
+
+constexpr int kWarp = 32;
+constexpr float kGrid = 4096.0f;          // 2^12
+constexpr float kInvGrid = 1.0f / 4096.0f;
+constexpr double kMaxCoord = 2000.0;      // |x| bound of the hi/lo representation
+constexpr int kJBits = 22;                // neighbour entry: j (22 bits) | image code (10 bits)
+constexpr uint32_t kJMask = (1u << kJBits) - 1u;
+constexpr int kMaxReach = 4;              // images n_a in [-4, 4]
+constexpr int kImgSide = 2 * kMaxReach + 1;
+constexpr int kNCodes = kImgSide * kImgSide * kImgSide;   // 729
+constexpr int kCenter = kMaxReach + kImgSide * kMaxReach + kImgSide * kImgSide * kMaxReach;
+constexpr int kMaxPots = 16;
+constexpr int kPartialStride = 8;         // doubles per warp partial
+
+// error word bits (sticky, OR-ed)
+constexpr int kErrNeighborOverflow = 1;
+constexpr int kErrBadSystemIdx = 2;
+constexpr int kErrUnsupported = 4;
+constexpr int kErrNonFinite = 8;
+constexpr int kErrTimeout = 16;
+
+__host__ __device__ inline int img_code(int nx, int ny, int nz) {
+  return (nx + kMaxReach) + kImgSide * (ny + kMaxReach) + kImgSide * kImgSide * (nz + kMaxReach);
+}
+
+struct DevPot {
+  int kind, shift;
+  float pf[3];
+  float rc2f, phicf, rlist2f;
+  double pd[3];
+  double rc2d, phicd, rlist, rlist2d, skin;
+};
+
+// Per-system data the device reads (SoA, capacity Bcap).
+struct SysArrays {
+  int64_t* seg_start;     // padded slot start
+  int32_t* n_atoms;       // atoms of the system
+  int64_t* caller_off;    // first caller index of the system
+  int32_t* pot;           // potential index
+  uint32_t* uid;          // RNG key
+  int32_t* bin_off;       // first bin of the system
+  int32_t* bin_cap;       // bins reserved for the system
+  int32_t* warp_start;    // first warp
+  int32_t* warp_end;      // one past last warp
+  double* h;              // [9] cell rows
+  double* hinv;           // [9]
+  double* href;           // [9] cell at the last listing (FIRE)
+  int32_t* nb;            // [3] bins per axis (at last listing)
+  int32_t* reach;         // [3]
+  float4* shift;          // [kNCodes][2] (hi xyz, lo xyz) mixed
+  double* shiftd;         // [kNCodes][3] fp64
+  int32_t* relist;        // per-system re-list flag
+  int32_t* dirty;         // forces stale for this system
+  double* kT;             // per-system kT (MD)
+};
+
+struct SlotArrays {
+  float4* xh; float4* xl;     // mixed positions hi/lo (w unused)
+  float4* vh; float4* vl;     // mixed velocities hi/lo; vh.w = 1/m
+  float4* F;                  // mixed forces (w = per-atom energy)
+  double* xd;                 // fp64 positions [3]
+  double* vd;                 // fp64 velocities [3]
+  double* Fd;                 // fp64 forces [3]
+  double* minvd;              // fp64 inverse mass
+  float4* xrh; float4* xrl;   // positions at last listing (mixed)
+  double* xrd;                // positions at last listing (fp64) [3]
+  int32_t* perm;              // slot -> caller index (-1 padding)
+  int32_t* sys;               // slot -> system (-1 padding)
+  int32_t* bin;               // slot -> global bin (valid after a listing)
+  int32_t* nn;                // neighbour count
+  uint32_t* nbr;              // [max_nbrs][Ncap] (transposed ELL)
+  // reorder scratch
+  int32_t* tmp_i0; int32_t* tmp_i1; int32_t* tmp_i2;
+  float4* tmp_f0; float4* tmp_f1; float4* tmp_f2; float4* tmp_f3;
+  double* tmp_d0; double* tmp_d1; double* tmp_d2;
+  // FIRE / adjoint per-slot vectors (mixed: float4; fp64: double[3])
+  float4* g0; float4* g1;
+  double* gd0; double* gd1;
+};
+
+// ---------------------------------------------------------------------------
+// double-float helpers (FP32 pairs) for positions and velocities
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void split_pos(double x, float& hi, float& lo) {
+  double h = rint(x * 4096.0) * (1.0 / 4096.0);
+  hi = (float)h;
+  lo = (float)(x - h);
+}
+__device__ __forceinline__ void pos_add(float& hi, float& lo, float d) {
+  lo += d;
+  if (fabsf(lo) > 0.5f * kInvGrid) {
+    float q = rintf(lo * kGrid) * kInvGrid;
+    hi += q;
+    lo -= q;
+  }
+}
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void df_add(float& hi, float& lo, float a) {
+  float s, e;
+  two_sum(hi, a, s, e);
+  e += lo;
+  hi = s + e;
+  lo = e - (hi - s);
+}
+
+// ---------------------------------------------------------------------------
+// Pair potentials.  fr = phi'(r)/r; phi unshifted.  d2 = phi''(r).
+// ---------------------------------------------------------------------------
+template <typename T> struct PotMath;
+
+template <> struct PotMath<float> {
+  static __device__ __forceinline__ void eval(const DevPot& P, float r2, float& phi, float& fr) {
+    if (P.kind == TS_LJ) {
+      float ri2 = __frcp_rn(r2);
+      float s2 = P.pf[0] * P.pf[0] * ri2;
+      float s6 = s2 * s2 * s2, s12 = s6 * s6;
+      phi = 4.0f * P.pf[1] * (s12 - s6);
+      fr = -24.0f * P.pf[1] * ri2 * (2.0f * s12 - s6);
+    } else if (P.kind == TS_MORSE) {
+      float r = sqrtf(r2);
+      float e = expf(P.pf[1] * (P.pf[2] - r));
+      phi = P.pf[0] * (e * e - 2.0f * e);
+      fr = 2.0f * P.pf[1] * P.pf[0] * e * (1.0f - e) * __frcp_rn(r);
+    } else {
+      float r = sqrtf(r2);
+      float t = 1.0f - r * __frcp_rn(P.pf[0]);
+      float al = P.pf[2];
+      float ta1 = (al == 2.0f) ? t : __powf(t, al - 1.0f);
+      phi = P.pf[1] / al * ta1 * t;
+      fr = -P.pf[1] / P.pf[0] * ta1 * __frcp_rn(r);
+    }
+  }
+  // phi'/r and phi'' (for the adjoint), plus parameter derivatives of phi and phi'
+  static __device__ __forceinline__ void eval2(const DevPot& P, float r2, float& r, float& d1, float& d2,
+                                               float dphi[3], float dd1[3]) {
+    r = sqrtf(r2);
+    dphi[0] = dphi[1] = dphi[2] = 0.f; dd1[0] = dd1[1] = dd1[2] = 0.f;
+    if (P.kind == TS_LJ) {
+      float sg = P.pf[0], ep = P.pf[1];
+      float ri = __frcp_rn(r);
+      float s = sg * ri, s2 = s * s, s6 = s2 * s2 * s2, s12 = s6 * s6;
+      d1 = -24.0f * ep * ri * (2.0f * s12 - s6);
+      d2 = 24.0f * ep * ri * ri * (26.0f * s12 - 7.0f * s6);
+      dphi[0] = 24.0f * ep / sg * (2.0f * s12 - s6);
+      dphi[1] = 4.0f * (s12 - s6);
+      dd1[0] = -144.0f * ep * ri / sg * (4.0f * s12 - s6);
+      dd1[1] = -24.0f * ri * (2.0f * s12 - s6);
+    } else if (P.kind == TS_MORSE) {
+      float D = P.pf[0], a = P.pf[1], r0 = P.pf[2];
+      float x = r - r0, e = expf(-a * x);
+      d1 = 2.0f * a * D * (e - e * e);
+      d2 = 2.0f * a * a * D * (2.0f * e * e - e);
+      dphi[0] = e * e - 2.0f * e;
+      dphi[1] = 2.0f * D * x * (e - e * e);
+      dphi[2] = 2.0f * a * D * (e * e - e);
+      dd1[0] = 2.0f * a * (e - e * e);
+      dd1[1] = 2.0f * D * (e - e * e) + 2.0f * a * D * x * (2.0f * e * e - e);
+      dd1[2] = -d2;
+    } else {
+      float sg = P.pf[0], ep = P.pf[1], al = P.pf[2];
+      float t = 1.0f - r / sg;
+      float lt = logf(t);
+      float ta = __powf(t, al), ta1 = __powf(t, al - 1.0f), ta2 = __powf(t, al - 2.0f);
+      d1 = -ep / sg * ta1;
+      d2 = ep / (sg * sg) * (al - 1.0f) * ta2;
+      dphi[0] = ep * ta1 * r / (sg * sg);
+      dphi[1] = ta / al;
+      dphi[2] = -ep / (al * al) * ta + ep / al * ta * lt;
+      dd1[0] = ep / (sg * sg) * ta1 - ep / sg * (al - 1.0f) * ta2 * r / (sg * sg);
+      dd1[1] = -ta1 / sg;
+      dd1[2] = -ep / sg * ta1 * lt;
+    }
+  }
+};
+
+template <> struct PotMath<double> {
+  static __device__ __forceinline__ void eval(const DevPot& P, double r2, double& phi, double& fr) {
+    if (P.kind == TS_LJ) {
+      double ri2 = 1.0 / r2;
+      double s2 = P.pd[0] * P.pd[0] * ri2;
+      double s6 = s2 * s2 * s2, s12 = s6 * s6;
+      phi = 4.0 * P.pd[1] * (s12 - s6);
+      fr = -24.0 * P.pd[1] * ri2 * (2.0 * s12 - s6);
+    } else if (P.kind == TS_MORSE) {
+      double r = sqrt(r2);
+      double e = exp(-P.pd[1] * (r - P.pd[2]));
+      phi = P.pd[0] * (e * e - 2.0 * e);
+      fr = 2.0 * P.pd[1] * P.pd[0] * (e - e * e) / r;
+    } else {
+      double r = sqrt(r2);
+      double t = 1.0 - r / P.pd[0];
+      double al = P.pd[2];
+      double ta1 = (al == 2.0) ? t : pow(t, al - 1.0);
+      phi = P.pd[1] / al * ta1 * t;
+      fr = -P.pd[1] / P.pd[0] * ta1 / r;
+    }
+  }
+  static __device__ __forceinline__ void eval2(const DevPot& P, double r2, double& r, double& d1, double& d2,
+                                               double dphi[3], double dd1[3]) {
+    r = sqrt(r2);
+    dphi[0] = dphi[1] = dphi[2] = 0; dd1[0] = dd1[1] = dd1[2] = 0;
+    if (P.kind == TS_LJ) {
+      double sg = P.pd[0], ep = P.pd[1];
+      double s = sg / r, s2 = s * s, s6 = s2 * s2 * s2, s12 = s6 * s6;
+      d1 = -24.0 * ep / r * (2.0 * s12 - s6);
+      d2 = 24.0 * ep / (r * r) * (26.0 * s12 - 7.0 * s6);
+      dphi[0] = 24.0 * ep / sg * (2.0 * s12 - s6);
+      dphi[1] = 4.0 * (s12 - s6);
+      dd1[0] = -144.0 * ep / (r * sg) * (4.0 * s12 - s6);
+      dd1[1] = -24.0 / r * (2.0 * s12 - s6);
+    } else if (P.kind == TS_MORSE) {
+      double D = P.pd[0], a = P.pd[1], r0 = P.pd[2];
+      double x = r - r0, e = exp(-a * x);
+      d1 = 2.0 * a * D * (e - e * e);
+      d2 = 2.0 * a * a * D * (2.0 * e * e - e);
+      dphi[0] = e * e - 2.0 * e;
+      dphi[1] = 2.0 * D * x * (e - e * e);
+      dphi[2] = 2.0 * a * D * (e * e - e);
+      dd1[0] = 2.0 * a * (e - e * e);
+      dd1[1] = 2.0 * D * (e - e * e) + 2.0 * a * D * x * (2.0 * e * e - e);
+      dd1[2] = -d2;
+    } else {
+      double sg = P.pd[0], ep = P.pd[1], al = P.pd[2];
+      double t = 1.0 - r / sg, lt = log(t);
+      double ta = pow(t, al), ta1 = pow(t, al - 1.0), ta2 = pow(t, al - 2.0);
+      d1 = -ep / sg * ta1;
+      d2 = ep / (sg * sg) * (al - 1.0) * ta2;
+      dphi[0] = ep * ta1 * r / (sg * sg);
+      dphi[1] = ta / al;
+      dphi[2] = -ep / (al * al) * ta + ep / al * ta * lt;
+      dd1[0] = ep / (sg * sg) * ta1 - ep / sg * (al - 1.0) * ta2 * r / (sg * sg);
+      dd1[1] = -ta1 / sg;
+      dd1[2] = -ep / sg * ta1 * lt;
+    }
+  }
+};
+
+// warp-level reductions
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+}  // namespace ts

@@ -1,0 +1,166 @@
+// ts_md.cu -- velocity Verlet and BAOAB Langevin steps behind ts_md_step
+// (the paper's batched Langevin MD, Sec. 4).
+//
+// One step:  v += (dt/2m) F;  [VV]  x += dt v
+//                            [BAOAB] x += dt/2 v;  v = c1 v + sqrt((1-c1^2) kT/m) xi;  x += dt/2 v
+//            F = F(x);  v += (dt/2m) F.
+// Consecutive half kicks of adjacent steps are merged into one full kick, so
+// a step is one elementwise kernel plus the pair kernel.  The noise xi is
+// Philox4x32-10 (Salmon et al., SC'11) keyed by (seed, system uid) with
+// counter (step, atom index within its system), then Box-Muller, so it does
+// not depend on where the system sits in the batch.
+#include "ts_kernels.cuh"
+
+namespace ts {
+
+__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; r++) {
+    uint32_t lo0 = 0xD2511F53u * c[0], hi0 = __umulhi(0xD2511F53u, c[0]);
+    uint32_t lo1 = 0xCD9E8D57u * c[2], hi1 = __umulhi(0xCD9E8D57u, c[2]);
+    uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+    k0 += 0x9E3779B9u; k1 += 0xBB67AE85u;
+  }
+}
+
+// three standard normals for (step, local atom, seed, uid)
+template <bool F64>
+__device__ __forceinline__ void normals3(uint64_t step, uint32_t la, uint32_t seed, uint32_t uid, double z[3]) {
+  uint32_t c[4] = {(uint32_t)step, la, (uint32_t)(step >> 32), 0u};
+  philox4x32_10(c, seed, uid);
+  if constexpr (F64) {
+    const double two_pi = 6.283185307179586476925286766559;
+    double u0 = ((double)c[0] + 0.5) * 2.3283064365386962890625e-10;
+    double u1 = ((double)c[1] + 0.5) * 2.3283064365386962890625e-10;
+    double u2 = ((double)c[2] + 0.5) * 2.3283064365386962890625e-10;
+    double u3 = ((double)c[3] + 0.5) * 2.3283064365386962890625e-10;
+    double R0 = sqrt(-2.0 * log(u0)), R1 = sqrt(-2.0 * log(u2));
+    double sn, cs;
+    sincos(two_pi * u1, &sn, &cs);
+    z[0] = R0 * cs; z[1] = R0 * sn;
+    z[2] = R1 * cos(two_pi * u3);
+  } else {
+    float u0 = ((float)(c[0] >> 8) + 0.5f) * 5.9604644775390625e-08f;
+    float u1 = ((float)(c[1] >> 8) + 0.5f) * 5.9604644775390625e-08f;
+    float u2 = ((float)(c[2] >> 8) + 0.5f) * 5.9604644775390625e-08f;
+    float u3 = ((float)(c[3] >> 8) + 0.5f) * 5.9604644775390625e-08f;
+    float R0 = sqrtf(-2.0f * logf(u0)), R1 = sqrtf(-2.0f * logf(u2));
+    float sn, cs;
+    sincospif(2.0f * u1, &sn, &cs);
+    z[0] = R0 * cs; z[1] = R0 * sn;
+    z[2] = R1 * cospif(2.0f * u3);
+  }
+}
+
+// KIND 0: VV (kick, full drift); KIND 1: BAOAB (kick, half drift, O, half drift).
+// kick = dt/2 on the first step of a call, dt when merged with the previous
+// step's closing half kick.  Also flags systems whose atoms left the skin.
+template <bool F64, int KIND>
+__global__ void k_md_kick_drift(int64_t Npad, SysArrays S, SlotArrays A, const DevPot* __restrict__ pots, double kick,
+                                double dt, double c1, uint32_t seed, const uint64_t* __restrict__ step_base,
+                                uint64_t koff) {
+  const uint64_t step = *step_base + koff;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < Npad; k += (int64_t)gridDim.x * blockDim.x) {
+    int p = A.perm[k];
+    if (p < 0) continue;
+    int s = A.sys[k];
+    double z[3] = {0, 0, 0};
+    double osc = 0;
+    if (KIND == 1) {
+      normals3<F64>(step, (uint32_t)(p - S.caller_off[s]), seed, S.uid[s], z);
+    }
+    double dx, dy, dz;
+    if constexpr (F64) {
+      double mi = A.minvd[k];
+      double* v = A.vd + 3 * k;
+      double* x = A.xd + 3 * k;
+      const double* f = A.Fd + 3 * k;
+      for (int c = 0; c < 3; c++) v[c] += kick * mi * f[c];
+      if (KIND == 0) {
+        for (int c = 0; c < 3; c++) x[c] += dt * v[c];
+      } else {
+        osc = sqrt((1.0 - c1 * c1) * S.kT[s] * mi);
+        for (int c = 0; c < 3; c++) x[c] += 0.5 * dt * v[c];
+        for (int c = 0; c < 3; c++) v[c] = c1 * v[c] + osc * z[c];
+        for (int c = 0; c < 3; c++) x[c] += 0.5 * dt * v[c];
+      }
+      const double* xr = A.xrd + 3 * k;
+      dx = x[0] - xr[0]; dy = x[1] - xr[1]; dz = x[2] - xr[2];
+    } else {
+      float4 vh = A.vh[k], vl = A.vl[k], xh = A.xh[k], xl = A.xl[k], f = A.F[k];
+      float a = (float)kick * vh.w;
+      df_add(vh.x, vl.x, a * f.x); df_add(vh.y, vl.y, a * f.y); df_add(vh.z, vl.z, a * f.z);
+      if (KIND == 0) {
+        float t = (float)dt;
+        pos_add(xh.x, xl.x, t * vh.x + t * vl.x);
+        pos_add(xh.y, xl.y, t * vh.y + t * vl.y);
+        pos_add(xh.z, xl.z, t * vh.z + t * vl.z);
+      } else {
+        float t = (float)(0.5 * dt);
+        pos_add(xh.x, xl.x, t * vh.x + t * vl.x);
+        pos_add(xh.y, xl.y, t * vh.y + t * vl.y);
+        pos_add(xh.z, xl.z, t * vh.z + t * vl.z);
+        float cc = (float)c1;
+        float so = sqrtf((float)((1.0 - c1 * c1) * S.kT[s]) * vh.w);
+        // v <- c1 v + so z, in double-float: scale the pair, then add the noise
+        float nx = cc * vh.x, ny = cc * vh.y, nz = cc * vh.z;
+        float ex = fmaf(cc, vh.x, -nx) + cc * vl.x, ey = fmaf(cc, vh.y, -ny) + cc * vl.y,
+              ez = fmaf(cc, vh.z, -nz) + cc * vl.z;
+        vh.x = nx + ex; vl.x = ex - (vh.x - nx);
+        vh.y = ny + ey; vl.y = ey - (vh.y - ny);
+        vh.z = nz + ez; vl.z = ez - (vh.z - nz);
+        df_add(vh.x, vl.x, so * (float)z[0]); df_add(vh.y, vl.y, so * (float)z[1]); df_add(vh.z, vl.z, so * (float)z[2]);
+        pos_add(xh.x, xl.x, t * vh.x + t * vl.x);
+        pos_add(xh.y, xl.y, t * vh.y + t * vl.y);
+        pos_add(xh.z, xl.z, t * vh.z + t * vl.z);
+      }
+      A.vh[k] = vh; A.vl[k] = vl; A.xh[k] = xh; A.xl[k] = xl;
+      float4 rh = A.xrh[k], rl = A.xrl[k];
+      dx = (double)((xh.x - rh.x) + (xl.x - rl.x));
+      dy = (double)((xh.y - rh.y) + (xl.y - rl.y));
+      dz = (double)((xh.z - rh.z) + (xl.z - rl.z));
+    }
+    double sk = 0.5 * pots[S.pot[s]].skin;
+    if (dx * dx + dy * dy + dz * dz > sk * sk) S.relist[s] = 1;
+  }
+}
+
+// closing half kick of the last step; kinetic energy per warp (partial slot 7)
+template <bool F64>
+__global__ void k_md_final(int32_t n_warps, SysArrays S, SlotArrays A, double kick, double* partial) {
+  int w = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  int lane = threadIdx.x & 31;
+  if (w >= n_warps) return;
+  int64_t k = (int64_t)w * kWarp + lane;
+  double ke = 0;
+  if (A.perm[k] >= 0) {
+    if constexpr (F64) {
+      double mi = A.minvd[k];
+      double* v = A.vd + 3 * k;
+      const double* f = A.Fd + 3 * k;
+      for (int c = 0; c < 3; c++) v[c] += kick * mi * f[c];
+      ke = 0.5 / mi * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    } else {
+      float4 vh = A.vh[k], vl = A.vl[k], f = A.F[k];
+      float a = (float)kick * vh.w;
+      df_add(vh.x, vl.x, a * f.x); df_add(vh.y, vl.y, a * f.y); df_add(vh.z, vl.z, a * f.z);
+      A.vh[k] = vh; A.vl[k] = vl;
+      double v0 = (double)vh.x + vl.x, v1 = (double)vh.y + vl.y, v2 = (double)vh.z + vl.z;
+      ke = 0.5 / (double)vh.w * (v0 * v0 + v1 * v1 + v2 * v2);
+    }
+  }
+  ke = warp_sum(ke);
+  if (lane == 0) partial[(int64_t)w * kPartialStride + 7] = ke;
+}
+
+template __global__ void k_md_kick_drift<true, 0>(int64_t, SysArrays, SlotArrays, const DevPot*, double, double, double, uint32_t, const uint64_t*, uint64_t);
+template __global__ void k_md_kick_drift<true, 1>(int64_t, SysArrays, SlotArrays, const DevPot*, double, double, double, uint32_t, const uint64_t*, uint64_t);
+template __global__ void k_md_kick_drift<false, 0>(int64_t, SysArrays, SlotArrays, const DevPot*, double, double, double, uint32_t, const uint64_t*, uint64_t);
+template __global__ void k_md_kick_drift<false, 1>(int64_t, SysArrays, SlotArrays, const DevPot*, double, double, double, uint32_t, const uint64_t*, uint64_t);
+
+__global__ void k_set_u64(uint64_t* p, uint64_t v) { *p = v; }
+template __global__ void k_md_final<true>(int32_t, SysArrays, SlotArrays, double, double*);
+template __global__ void k_md_final<false>(int32_t, SysArrays, SlotArrays, double, double*);
+
+}  // namespace ts

@@ -1,0 +1,529 @@
+// ts_neighbor.cu -- topology, import/export and the per-system cell-list
+// neighbour build (triclinic, multi-image) behind ts_neighbor_build.
+//
+// Method: for every system, bins per lattice direction
+// n_a = max(1, floor(w_a / r_list)) with w_a = V / |h_b x h_c| the
+// perpendicular width, fractional coordinates wrapped to [0,1), and a
+// stencil reach m_a = ceil(r_list n_a / w_a) bins, stencil bins outside the
+// grid mapping back with a lattice image shift.  Several images of one bin
+// (small cells, the general multi-image case) are distinct stencil entries.
+// The explicit list at r_list = rc + skin (transposed ELL, one 32-bit entry
+// per neighbour: local index | image code) is rebuilt per system when one of
+// its atoms moved more than skin/2.
+#include "ts_kernels.cuh"
+
+namespace ts {
+
+// --- topology --------------------------------------------------------------
+// starts[s] = first caller index of system s; validates system_idx.
+__global__ void k_sys_bounds(int64_t N, const int32_t* __restrict__ sidx, int32_t B, int64_t* starts,
+                             int32_t* err) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    int s = sidx[i];
+    if (s < 0 || s >= B) { atomicOr(err, kErrBadSystemIdx); continue; }
+    int p = (i == 0) ? -1 : sidx[i - 1];
+    if (p > s || (p != s && p != s - 1)) atomicOr(err, kErrBadSystemIdx);
+    if (p != s) starts[s] = i;
+    if (i == N - 1 && s != B - 1) atomicOr(err, kErrBadSystemIdx);
+  }
+}
+
+// slot tables: perm/sys for every padded slot of every system (identity order)
+__global__ void k_init_slots(int32_t B, SysArrays S, SlotArrays A) {
+  int s = blockIdx.x;
+  if (s >= B) return;
+  int64_t st = S.seg_start[s];
+  int n = S.n_atoms[s];
+  int npad = (n + kWarp - 1) / kWarp * kWarp;
+  for (int k = threadIdx.x; k < npad; k += blockDim.x) {
+    A.perm[st + k] = k < n ? (int32_t)(S.caller_off[s] + k) : -1;
+    A.sys[st + k] = k < n ? s : -1;
+    A.nn[st + k] = 0;
+  }
+}
+
+// --- import / export ---------------------------------------------------------
+// Positions from the caller; marks systems whose positions changed (forces
+// stale) and systems whose atoms left the skin (re-list).  check_skin = 0 on
+// the first import after a topology change (everything is re-listed anyway).
+template <bool F64>
+__global__ void k_import_pos(int64_t Npad, SysArrays S, SlotArrays A, const double* __restrict__ pos,
+                             const DevPot* __restrict__ pots, int check_skin, int32_t* err) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < Npad; k += (int64_t)gridDim.x * blockDim.x) {
+    int p = A.perm[k];
+    if (p < 0) continue;
+    int s = A.sys[k];
+    double x0 = pos[3 * (int64_t)p], x1 = pos[3 * (int64_t)p + 1], x2 = pos[3 * (int64_t)p + 2];
+    if (!(isfinite(x0) && isfinite(x1) && isfinite(x2)) || fabs(x0) > kMaxCoord || fabs(x1) > kMaxCoord ||
+        fabs(x2) > kMaxCoord) {
+      atomicOr(err, kErrNonFinite);
+      continue;
+    }
+    bool changed;
+    double dx, dy, dz;
+    if constexpr (F64) {
+      double* xd = A.xd + 3 * k;
+      changed = (xd[0] != x0) || (xd[1] != x1) || (xd[2] != x2);
+      if (changed) { xd[0] = x0; xd[1] = x1; xd[2] = x2; }
+      const double* xr = A.xrd + 3 * k;
+      dx = x0 - xr[0]; dy = x1 - xr[1]; dz = x2 - xr[2];
+    } else {
+      float4 h, l;
+      split_pos(x0, h.x, l.x); split_pos(x1, h.y, l.y); split_pos(x2, h.z, l.z);
+      h.w = 0.f; l.w = 0.f;
+      float4 oh = A.xh[k], ol = A.xl[k];
+      changed = (oh.x != h.x) || (oh.y != h.y) || (oh.z != h.z) || (ol.x != l.x) || (ol.y != l.y) || (ol.z != l.z);
+      if (changed) { A.xh[k] = h; A.xl[k] = l; }
+      float4 rh = A.xrh[k], rl = A.xrl[k];
+      dx = (double)((h.x - rh.x) + (l.x - rl.x));
+      dy = (double)((h.y - rh.y) + (l.y - rl.y));
+      dz = (double)((h.z - rh.z) + (l.z - rl.z));
+    }
+    if (changed) S.dirty[s] = 1;
+    if (check_skin) {
+      double sk = 0.5 * pots[S.pot[s]].skin;
+      if (dx * dx + dy * dy + dz * dz > sk * sk) S.relist[s] = 1;
+    }
+  }
+}
+
+template <bool F64>
+__global__ void k_import_vel(int64_t Npad, SlotArrays A, const double* __restrict__ vel, const double* __restrict__ mass) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < Npad; k += (int64_t)gridDim.x * blockDim.x) {
+    int p = A.perm[k];
+    if (p < 0) continue;
+    double m = mass[p];
+    double v0 = vel ? vel[3 * (int64_t)p] : 0.0, v1 = vel ? vel[3 * (int64_t)p + 1] : 0.0,
+           v2 = vel ? vel[3 * (int64_t)p + 2] : 0.0;
+    if constexpr (F64) {
+      double* vd = A.vd + 3 * k;
+      vd[0] = v0; vd[1] = v1; vd[2] = v2;
+      A.minvd[k] = 1.0 / m;
+    } else {
+      float4 h, l;
+      h.x = (float)v0; l.x = (float)(v0 - (double)h.x);
+      h.y = (float)v1; l.y = (float)(v1 - (double)h.y);
+      h.z = (float)v2; l.z = (float)(v2 - (double)h.z);
+      h.w = (float)(1.0 / m); l.w = 0.f;
+      A.vh[k] = h; A.vl[k] = l;
+    }
+  }
+}
+
+template <bool F64>
+__global__ void k_export_state(int64_t Npad, SlotArrays A, double* pos, double* vel) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < Npad; k += (int64_t)gridDim.x * blockDim.x) {
+    int p = A.perm[k];
+    if (p < 0) continue;
+    if constexpr (F64) {
+      if (pos) for (int c = 0; c < 3; c++) pos[3 * (int64_t)p + c] = A.xd[3 * k + c];
+      if (vel) for (int c = 0; c < 3; c++) vel[3 * (int64_t)p + c] = A.vd[3 * k + c];
+    } else {
+      if (pos) {
+        float4 h = A.xh[k], l = A.xl[k];
+        pos[3 * (int64_t)p] = (double)h.x + (double)l.x;
+        pos[3 * (int64_t)p + 1] = (double)h.y + (double)l.y;
+        pos[3 * (int64_t)p + 2] = (double)h.z + (double)l.z;
+      }
+      if (vel) {
+        float4 h = A.vh[k], l = A.vl[k];
+        vel[3 * (int64_t)p] = (double)h.x + (double)l.x;
+        vel[3 * (int64_t)p + 1] = (double)h.y + (double)l.y;
+        vel[3 * (int64_t)p + 2] = (double)h.z + (double)l.z;
+      }
+    }
+  }
+}
+
+template <bool F64>
+__global__ void k_export_forces(int64_t Npad, SlotArrays A, double* F) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < Npad; k += (int64_t)gridDim.x * blockDim.x) {
+    int p = A.perm[k];
+    if (p < 0) continue;
+    if constexpr (F64) {
+      for (int c = 0; c < 3; c++) F[3 * (int64_t)p + c] = A.Fd[3 * k + c];
+    } else {
+      float4 f = A.F[k];
+      F[3 * (int64_t)p] = f.x; F[3 * (int64_t)p + 1] = f.y; F[3 * (int64_t)p + 2] = f.z;
+    }
+  }
+}
+
+// --- per-system geometry -----------------------------------------------------
+__device__ inline double det3(const double* h) {
+  return h[0] * (h[4] * h[8] - h[5] * h[7]) - h[1] * (h[3] * h[8] - h[5] * h[6]) + h[2] * (h[3] * h[7] - h[4] * h[6]);
+}
+
+// Cell import, inverse, bins and reach (bins clamped to the system's bin
+// reservation).  pbc must be periodic on all axes.
+__global__ void k_geometry(int32_t B, SysArrays S, const double* __restrict__ cell, const uint8_t* __restrict__ pbc,
+                           const DevPot* __restrict__ pots, int32_t* err) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= B) return;
+  double h[9];
+  for (int q = 0; q < 9; q++) h[q] = cell[9 * (int64_t)s + q];
+  for (int q = 0; q < 9; q++) S.h[9 * s + q] = h[q];
+  if (pbc && !(pbc[3 * s] && pbc[3 * s + 1] && pbc[3 * s + 2])) atomicOr(err, kErrUnsupported);
+  double d = det3(h);
+  if (!(fabs(d) > 0) || !isfinite(d)) { atomicOr(err, kErrNonFinite); return; }
+  double g[9];
+  g[0] = (h[4] * h[8] - h[5] * h[7]) / d; g[1] = (h[2] * h[7] - h[1] * h[8]) / d;
+  g[2] = (h[1] * h[5] - h[2] * h[4]) / d; g[3] = (h[5] * h[6] - h[3] * h[8]) / d;
+  g[4] = (h[0] * h[8] - h[2] * h[6]) / d; g[5] = (h[2] * h[3] - h[0] * h[5]) / d;
+  g[6] = (h[3] * h[7] - h[4] * h[6]) / d; g[7] = (h[1] * h[6] - h[0] * h[7]) / d;
+  g[8] = (h[0] * h[4] - h[1] * h[3]) / d;
+  for (int q = 0; q < 9; q++) S.hinv[9 * s + q] = g[q];
+  double V = fabs(d), w[3];
+  double ext = 0;
+  for (int a = 0; a < 3; a++) {
+    const double* b = h + 3 * ((a + 1) % 3);
+    const double* c = h + 3 * ((a + 2) % 3);
+    double cx = b[1] * c[2] - b[2] * c[1], cy = b[2] * c[0] - b[0] * c[2], cz = b[0] * c[1] - b[1] * c[0];
+    w[a] = V / sqrt(cx * cx + cy * cy + cz * cz);
+    ext += fabs(h[3 * a]) + fabs(h[3 * a + 1]) + fabs(h[3 * a + 2]);
+  }
+  double rl = pots[S.pot[s]].rlist;
+  int nb[3], m[3];
+  for (int a = 0; a < 3; a++) {
+    double f = floor(w[a] / rl);
+    nb[a] = f < 1.0 ? 1 : (f > 1024.0 ? 1024 : (int)f);
+  }
+  int cap = S.bin_cap[s];
+  while ((int64_t)nb[0] * nb[1] * nb[2] > cap) {
+    int a = (nb[0] >= nb[1] && nb[0] >= nb[2]) ? 0 : (nb[1] >= nb[2] ? 1 : 2);
+    nb[a] = nb[a] > 1 ? nb[a] - 1 : 1;
+    if (nb[0] == 1 && nb[1] == 1 && nb[2] == 1) break;
+  }
+  for (int a = 0; a < 3; a++) {
+    m[a] = (int)ceil(rl * nb[a] / w[a]);
+    if (m[a] < 1) m[a] = 1;
+    if (m[a] > kMaxReach) { m[a] = kMaxReach; atomicOr(err, kErrUnsupported); }
+    S.nb[3 * s + a] = nb[a];
+    S.reach[3 * s + a] = m[a];
+  }
+  // positions wrapped into the cell plus the skin must stay inside the hi/lo range
+  if (ext + 2.0 * rl > 0.5 * kMaxCoord) atomicOr(err, kErrUnsupported);
+}
+
+// Image shift table S = n h for every image code, stored hi/lo (mixed) and FP64.
+__global__ void k_shift_table(int32_t B, SysArrays S) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)B * kNCodes) return;
+  int s = (int)(t / kNCodes), code = (int)(t % kNCodes);
+  int nx = code % kImgSide - kMaxReach, ny = (code / kImgSide) % kImgSide - kMaxReach,
+      nz = code / (kImgSide * kImgSide) - kMaxReach;
+  const double* h = S.h + 9 * s;
+  double v[3];
+  for (int c = 0; c < 3; c++) v[c] = nx * h[c] + ny * h[3 + c] + nz * h[6 + c];
+  float4 hi, lo;
+  split_pos(v[0], hi.x, lo.x); split_pos(v[1], hi.y, lo.y); split_pos(v[2], hi.z, lo.z);
+  hi.w = 0.f; lo.w = 0.f;
+  S.shift[2 * t] = hi; S.shift[2 * t + 1] = lo;
+  for (int c = 0; c < 3; c++) S.shiftd[3 * t + c] = v[c];
+}
+
+// --- counting sort by (system, bin) ------------------------------------------
+__global__ void k_zero_bins(int32_t B, SysArrays S, int32_t* count) {
+  int s = blockIdx.x;
+  if (s >= B || !S.relist[s]) return;
+  int off = S.bin_off[s], cap = S.bin_cap[s];
+  for (int k = threadIdx.x; k < cap; k += blockDim.x) count[off + k] = 0;
+}
+
+// wrap positions into the cell, bin them, claim a (provisional) rank in the bin
+template <bool F64>
+__global__ void k_bin_atoms(int64_t Npad, SysArrays S, SlotArrays A, int32_t* count) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < Npad; k += (int64_t)gridDim.x * blockDim.x) {
+    int p = A.perm[k];
+    if (p < 0) continue;
+    int s = A.sys[k];
+    if (!S.relist[s]) continue;
+    double x[3];
+    if constexpr (F64) {
+      for (int c = 0; c < 3; c++) x[c] = A.xd[3 * k + c];
+    } else {
+      float4 h = A.xh[k], l = A.xl[k];
+      x[0] = (double)h.x + l.x; x[1] = (double)h.y + l.y; x[2] = (double)h.z + l.z;
+    }
+    const double* g = S.hinv + 9 * s;
+    const double* h = S.h + 9 * s;
+    double f[3];
+    int kb[3];
+    for (int a = 0; a < 3; a++) {
+      double v = x[0] * g[a] + x[1] * g[3 + a] + x[2] * g[6 + a];
+      v -= floor(v);
+      if (v >= 1.0) v = 0.0;
+      f[a] = v;
+      int nb = S.nb[3 * s + a];
+      int q = (int)(v * nb);
+      kb[a] = q >= nb ? nb - 1 : (q < 0 ? 0 : q);
+    }
+    double xw[3];
+    for (int c = 0; c < 3; c++) xw[c] = f[0] * h[c] + f[1] * h[3 + c] + f[2] * h[6 + c];
+    if constexpr (F64) {
+      for (int c = 0; c < 3; c++) A.tmp_d0[3 * k + c] = xw[c];
+    } else {
+      float4 hi, lo;
+      split_pos(xw[0], hi.x, lo.x); split_pos(xw[1], hi.y, lo.y); split_pos(xw[2], hi.z, lo.z);
+      hi.w = 0.f; lo.w = 0.f;
+      A.tmp_f0[k] = hi; A.tmp_f1[k] = lo;
+    }
+    int gb = S.bin_off[s] + (kb[2] * S.nb[3 * s + 1] + kb[1]) * S.nb[3 * s] + kb[0];
+    A.tmp_i0[k] = gb;
+    A.tmp_i1[k] = atomicAdd(&count[gb], 1);
+  }
+}
+
+// exclusive scan of bin counts: block sums, scan of sums, add
+__global__ void k_scan_block(int64_t n, const int32_t* __restrict__ in, int32_t* out, int32_t* bsum) {
+  __shared__ int32_t sh[1024];
+  int64_t i = blockIdx.x * 1024ll + threadIdx.x;
+  int v = i < n ? in[i] : 0;
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    int t = threadIdx.x >= o ? sh[threadIdx.x - o] : 0;
+    __syncthreads();
+    sh[threadIdx.x] += t;
+    __syncthreads();
+  }
+  if (i < n) out[i] = sh[threadIdx.x] - v;
+  if (threadIdx.x == 1023) bsum[blockIdx.x] = sh[1023];
+}
+__global__ void k_scan_sums(int32_t nb, int32_t* bsum) {   // one block, sequential chunks
+  __shared__ int32_t carry;
+  __shared__ int32_t sh[1024];
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < nb; base += 1024) {
+    int i = base + threadIdx.x;
+    int v = i < nb ? bsum[i] : 0;
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+      int t = threadIdx.x >= o ? sh[threadIdx.x - o] : 0;
+      __syncthreads();
+      sh[threadIdx.x] += t;
+      __syncthreads();
+    }
+    if (i < nb) bsum[i] = carry + sh[threadIdx.x] - v;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry += sh[1023];
+    __syncthreads();
+  }
+}
+__global__ void k_scan_add(int64_t n, int32_t* out, const int32_t* __restrict__ bsum) {
+  int64_t i = blockIdx.x * 1024ll + threadIdx.x;
+  if (i < n) out[i] += bsum[blockIdx.x];
+}
+
+// first slot of a bin: seg_start + (scan[bin] - scan[first bin]) and the
+// scan at a system's first bin equals its caller offset (counts are n_s)
+__device__ __forceinline__ int64_t bin_slot(const SysArrays& S, const int32_t* cstart, int s, int gb) {
+  return S.seg_start[s] + (int64_t)cstart[gb] - S.caller_off[s];
+}
+
+__global__ void k_scatter_ids(int64_t Npad, SysArrays S, SlotArrays A, const int32_t* __restrict__ cstart) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < Npad; k += (int64_t)gridDim.x * blockDim.x) {
+    int p = A.perm[k];
+    if (p < 0) continue;
+    int s = A.sys[k];
+    if (!S.relist[s]) continue;
+    int gb = A.tmp_i0[k];
+    A.tmp_i2[bin_slot(S, cstart, s, gb) + A.tmp_i1[k]] = p;
+  }
+}
+
+// canonical order inside a bin (ascending caller index) -> final slot; move
+// the per-slot state into the destination buffers
+template <bool F64>
+__global__ void k_final_slot(int64_t Npad, SysArrays S, SlotArrays A, const int32_t* __restrict__ cstart,
+                             const int32_t* __restrict__ count, int move_fire) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < Npad; k += (int64_t)gridDim.x * blockDim.x) {
+    int p = A.perm[k];
+    if (p < 0) continue;
+    int s = A.sys[k];
+    if (!S.relist[s]) continue;
+    int gb = A.tmp_i0[k];
+    int64_t base = bin_slot(S, cstart, s, gb);
+    int cnt = count[gb], r = 0;
+    for (int q = 0; q < cnt; q++) r += A.tmp_i2[base + q] < p;
+    int64_t d = base + r;
+    A.bin[d] = gb;
+    A.tmp_i1[d] = p;   // new perm (copied back below)
+    if constexpr (F64) {
+      for (int c = 0; c < 3; c++) A.xd[3 * d + c] = A.tmp_d0[3 * k + c];
+      for (int c = 0; c < 3; c++) A.tmp_d1[3 * d + c] = A.vd[3 * k + c];
+      A.tmp_d2[d] = A.minvd[k];
+      if (move_fire) for (int c = 0; c < 3; c++) A.tmp_d2[Npad + 3 * d + c] = A.gd0[3 * k + c];
+    } else {
+      A.xh[d] = A.tmp_f0[k];
+      A.xl[d] = A.tmp_f1[k];
+      A.tmp_f2[d] = A.vh[k];
+      A.tmp_f3[d] = A.vl[k];
+      if (move_fire) A.tmp_f0[Npad + d] = A.g0[k];
+    }
+  }
+}
+
+template <bool F64>
+__global__ void k_copy_back(int64_t Npad, SysArrays S, SlotArrays A, int move_fire) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < Npad; k += (int64_t)gridDim.x * blockDim.x) {
+    int s = A.sys[k];
+    if (s < 0 || !S.relist[s]) continue;
+    A.perm[k] = A.tmp_i1[k];
+    if constexpr (F64) {
+      for (int c = 0; c < 3; c++) A.vd[3 * k + c] = A.tmp_d1[3 * k + c];
+      A.minvd[k] = A.tmp_d2[k];
+      if (move_fire) for (int c = 0; c < 3; c++) A.gd0[3 * k + c] = A.tmp_d2[Npad + 3 * k + c];
+    } else {
+      A.vh[k] = A.tmp_f2[k];
+      A.vl[k] = A.tmp_f3[k];
+      if (move_fire) A.g0[k] = A.tmp_f0[Npad + k];
+    }
+  }
+}
+
+// explicit Verlet list at r_list: each atom scans its stencil bins
+template <bool F64>
+__global__ void k_build_list(int64_t Npad, SysArrays S, SlotArrays A, const int32_t* __restrict__ cstart,
+                             const int32_t* __restrict__ count, const DevPot* __restrict__ pots, int32_t max_nbrs,
+                             int64_t stride, int32_t* err) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < Npad; k += (int64_t)gridDim.x * blockDim.x) {
+    int s = A.sys[k];
+    if (s < 0 || !S.relist[s]) continue;
+    if (A.perm[k] < 0) continue;
+    const DevPot& P = pots[S.pot[s]];
+    int nb0 = S.nb[3 * s], nb1 = S.nb[3 * s + 1], nb2 = S.nb[3 * s + 2];
+    int m0 = S.reach[3 * s], m1 = S.reach[3 * s + 1], m2 = S.reach[3 * s + 2];
+    int lb = A.bin[k] - S.bin_off[s];
+    int kx = lb % nb0, ky = (lb / nb0) % nb1, kz = lb / (nb0 * nb1);
+    int64_t seg = S.seg_start[s];
+    int cnt = 0;
+    if constexpr (F64) {
+      double xi0 = A.xd[3 * k], xi1 = A.xd[3 * k + 1], xi2 = A.xd[3 * k + 2];
+      for (int dz = -m2; dz <= m2; dz++) {
+        int zz = kz + dz, iz = (zz >= 0) ? zz / nb2 : -((-zz + nb2 - 1) / nb2), cz = zz - iz * nb2;
+        for (int dy = -m1; dy <= m1; dy++) {
+          int yy = ky + dy, iy = (yy >= 0) ? yy / nb1 : -((-yy + nb1 - 1) / nb1), cy = yy - iy * nb1;
+          for (int dx = -m0; dx <= m0; dx++) {
+            int xx = kx + dx, ix = (xx >= 0) ? xx / nb0 : -((-xx + nb0 - 1) / nb0), cx = xx - ix * nb0;
+            int code = img_code(ix, iy, iz);
+            const double* sh = S.shiftd + 3 * ((int64_t)s * kNCodes + code);
+            double s0 = sh[0] - xi0, s1 = sh[1] - xi1, s2 = sh[2] - xi2;
+            int gb = S.bin_off[s] + (cz * nb1 + cy) * nb0 + cx;
+            int64_t b0 = bin_slot(S, cstart, s, gb);
+            int c = count[gb];
+            for (int q = 0; q < c; q++) {
+              int64_t j = b0 + q;
+              if (j == k && code == kCenter) continue;
+              double d0 = A.xd[3 * j] + s0, d1 = A.xd[3 * j + 1] + s1, d2 = A.xd[3 * j + 2] + s2;
+              double r2 = d0 * d0 + d1 * d1 + d2 * d2;
+              if (r2 < P.rlist2d) {
+                if (cnt < max_nbrs) A.nbr[cnt * stride + k] = (uint32_t)(j - seg) | ((uint32_t)code << kJBits);
+                cnt++;
+              }
+            }
+          }
+        }
+      }
+      for (int c = 0; c < 3; c++) A.xrd[3 * k + c] = A.xd[3 * k + c];
+    } else {
+      float4 hi = A.xh[k], lo = A.xl[k];
+      for (int dz = -m2; dz <= m2; dz++) {
+        int zz = kz + dz, iz = (zz >= 0) ? zz / nb2 : -((-zz + nb2 - 1) / nb2), cz = zz - iz * nb2;
+        for (int dy = -m1; dy <= m1; dy++) {
+          int yy = ky + dy, iy = (yy >= 0) ? yy / nb1 : -((-yy + nb1 - 1) / nb1), cy = yy - iy * nb1;
+          for (int dx = -m0; dx <= m0; dx++) {
+            int xx = kx + dx, ix = (xx >= 0) ? xx / nb0 : -((-xx + nb0 - 1) / nb0), cx = xx - ix * nb0;
+            int code = img_code(ix, iy, iz);
+            int64_t ti = (int64_t)s * kNCodes + code;
+            float4 sh = S.shift[2 * ti], sl = S.shift[2 * ti + 1];
+            // exact: all on the 2^-12 grid
+            float a0 = sh.x - hi.x, a1 = sh.y - hi.y, a2 = sh.z - hi.z;
+            float b0 = sl.x - lo.x, b1 = sl.y - lo.y, b2 = sl.z - lo.z;
+            int gb = S.bin_off[s] + (cz * nb1 + cy) * nb0 + cx;
+            int64_t jb = bin_slot(S, cstart, s, gb);
+            int c = count[gb];
+            for (int q = 0; q < c; q++) {
+              int64_t j = jb + q;
+              if (j == k && code == kCenter) continue;
+              float4 xj = A.xh[j], lj = A.xl[j];
+              float d0 = (xj.x + a0) + (lj.x + b0);
+              float d1 = (xj.y + a1) + (lj.y + b1);
+              float d2 = (xj.z + a2) + (lj.z + b2);
+              float r2 = d0 * d0 + d1 * d1 + d2 * d2;
+              if (r2 < P.rlist2f) {
+                if (cnt < max_nbrs) A.nbr[cnt * stride + k] = (uint32_t)(j - seg) | ((uint32_t)code << kJBits);
+                cnt++;
+              }
+            }
+          }
+        }
+      }
+      A.xrh[k] = hi; A.xrl[k] = lo;
+    }
+    if (cnt > max_nbrs) { atomicOr(err, kErrNeighborOverflow); cnt = max_nbrs; }
+    A.nn[k] = cnt;
+  }
+}
+
+// per-system flag bookkeeping after a listing: the re-listed systems' forces are stale
+__global__ void k_after_relist(int32_t B, SysArrays S, int64_t* relist_counter) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= B) return;
+  if (S.relist[s]) {
+    S.dirty[s] = 1;
+    S.relist[s] = 0;
+    for (int q = 0; q < 9; q++) S.href[9 * s + q] = S.h[9 * s + q];
+    atomicAdd((unsigned long long*)relist_counter, 1ull);
+  }
+}
+
+// list export in caller order (j as caller index, image n per axis)
+__global__ void k_export_list(int64_t Npad, SysArrays S, SlotArrays A, int32_t max_nbrs, int64_t stride,
+                              int32_t* j_out, int32_t* img_out, int32_t* count_out) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < Npad; k += (int64_t)gridDim.x * blockDim.x) {
+    int p = A.perm[k];
+    if (p < 0) continue;
+    int s = A.sys[k];
+    int64_t seg = S.seg_start[s];
+    int nn = A.nn[k];
+    count_out[p] = nn;
+    for (int q = 0; q < max_nbrs; q++) {
+      int64_t o = (int64_t)p * max_nbrs + q;
+      if (q < nn) {
+        uint32_t e = A.nbr[q * stride + k];
+        int code = (int)(e >> kJBits);
+        j_out[o] = A.perm[seg + (e & kJMask)];
+        img_out[3 * o] = code % kImgSide - kMaxReach;
+        img_out[3 * o + 1] = (code / kImgSide) % kImgSide - kMaxReach;
+        img_out[3 * o + 2] = code / (kImgSide * kImgSide) - kMaxReach;
+      } else {
+        j_out[o] = -1;
+        img_out[3 * o] = img_out[3 * o + 1] = img_out[3 * o + 2] = 0;
+      }
+    }
+  }
+}
+
+template __global__ void k_import_pos<true>(int64_t, SysArrays, SlotArrays, const double*, const DevPot*, int, int32_t*);
+template __global__ void k_import_pos<false>(int64_t, SysArrays, SlotArrays, const double*, const DevPot*, int, int32_t*);
+template __global__ void k_import_vel<true>(int64_t, SlotArrays, const double*, const double*);
+template __global__ void k_import_vel<false>(int64_t, SlotArrays, const double*, const double*);
+template __global__ void k_export_state<true>(int64_t, SlotArrays, double*, double*);
+template __global__ void k_export_state<false>(int64_t, SlotArrays, double*, double*);
+template __global__ void k_export_forces<true>(int64_t, SlotArrays, double*);
+template __global__ void k_export_forces<false>(int64_t, SlotArrays, double*);
+template __global__ void k_bin_atoms<true>(int64_t, SysArrays, SlotArrays, int32_t*);
+template __global__ void k_bin_atoms<false>(int64_t, SysArrays, SlotArrays, int32_t*);
+template __global__ void k_final_slot<true>(int64_t, SysArrays, SlotArrays, const int32_t*, const int32_t*, int);
+template __global__ void k_final_slot<false>(int64_t, SysArrays, SlotArrays, const int32_t*, const int32_t*, int);
+template __global__ void k_copy_back<true>(int64_t, SysArrays, SlotArrays, int);
+template __global__ void k_copy_back<false>(int64_t, SysArrays, SlotArrays, int);
+template __global__ void k_build_list<true>(int64_t, SysArrays, SlotArrays, const int32_t*, const int32_t*,
+                                            const DevPot*, int32_t, int64_t, int32_t*);
+template __global__ void k_build_list<false>(int64_t, SysArrays, SlotArrays, const int32_t*, const int32_t*,
+                                             const DevPot*, int32_t, int64_t, int32_t*);
+
+}  // namespace ts

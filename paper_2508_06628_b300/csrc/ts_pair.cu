@@ -1,0 +1,141 @@
+// ts_pair.cu -- fused pair energy / force / virial kernel and the per-system
+// FP64 reduction behind ts_pair_forces.
+//
+// Definitions (forces, energy and stress as the model output, Sec. 2 of the
+// TorchSim paper): with d = x_j + n h - x_i over the full neighbour list,
+//   F_i = sum_j phi'(r) d / r,  E_i = 1/2 sum_j [phi(r) - phi(rc)],
+//   W = 1/2 sum_ij phi'(r) d (x) d / r,  stress = W / V.
+// One thread per atom gathers its neighbours (no scatter atomics: the full
+// list gives every atom its own force); a warp holds 32 atoms of one system,
+// so energy and virial go through warp shuffles into one FP64 partial per
+// warp, and a second kernel sums each system's warps in a fixed order.
+#include "ts_kernels.cuh"
+
+namespace ts {
+
+template <bool F64, bool EW>
+__global__ void __launch_bounds__(128) k_pair(int32_t n_warps, const int32_t* __restrict__ warp_sys, SysArrays S,
+                                              SlotArrays A, const DevPot* __restrict__ pots, int64_t stride,
+                                              int only_dirty, double* __restrict__ partial) {
+  int w = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  int lane = threadIdx.x & 31;
+  if (w >= n_warps) return;
+  int s = warp_sys[w];
+  if (only_dirty && !S.dirty[s]) return;
+  int64_t k = (int64_t)w * kWarp + lane;
+  const DevPot P = pots[S.pot[s]];
+  bool valid = A.perm[k] >= 0;
+  int nn = valid ? A.nn[k] : 0;
+  int64_t seg = S.seg_start[s];
+  if constexpr (F64) {
+    const double* tab = S.shiftd + 3 * (int64_t)s * kNCodes;
+    double xi0 = A.xd[3 * k], xi1 = A.xd[3 * k + 1], xi2 = A.xd[3 * k + 2];
+    double f0 = 0, f1 = 0, f2 = 0, e = 0, w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0, w5 = 0;
+    for (int q = 0; q < nn; q++) {
+      uint32_t ent = __ldg(A.nbr + q * stride + k);
+      int64_t j = seg + (ent & kJMask);
+      int code = (int)(ent >> kJBits);
+      double d0 = A.xd[3 * j] - xi0, d1 = A.xd[3 * j + 1] - xi1, d2 = A.xd[3 * j + 2] - xi2;
+      if (code != kCenter) { d0 += tab[3 * code]; d1 += tab[3 * code + 1]; d2 += tab[3 * code + 2]; }
+      double r2 = d0 * d0 + d1 * d1 + d2 * d2;
+      if (r2 < P.rc2d) {
+        double phi, fr;
+        PotMath<double>::eval(P, r2, phi, fr);
+        f0 += fr * d0; f1 += fr * d1; f2 += fr * d2;
+        if (EW) {
+          e += 0.5 * (phi - P.phicd);
+          double hf = 0.5 * fr;
+          w0 += hf * d0 * d0; w1 += hf * d1 * d1; w2 += hf * d2 * d2;
+          w3 += hf * d0 * d1; w4 += hf * d0 * d2; w5 += hf * d1 * d2;
+        }
+      }
+    }
+    if (valid) { A.Fd[3 * k] = f0; A.Fd[3 * k + 1] = f1; A.Fd[3 * k + 2] = f2; }
+    if (EW) {
+      double v[7] = {e, w0, w1, w2, w3, w4, w5};
+#pragma unroll
+      for (int c = 0; c < 7; c++) {
+        double t = warp_sum(v[c]);
+        if (lane == 0) partial[(int64_t)w * kPartialStride + c] = t;
+      }
+    }
+  } else {
+    const float4* tab = S.shift + 2 * (int64_t)s * kNCodes;
+    float4 xi = A.xh[k], li = A.xl[k];
+    float f0 = 0.f, f1 = 0.f, f2 = 0.f, e = 0.f, w0 = 0.f, w1 = 0.f, w2 = 0.f, w3 = 0.f, w4 = 0.f, w5 = 0.f;
+    for (int q = 0; q < nn; q++) {
+      uint32_t ent = __ldg(A.nbr + q * stride + k);
+      int64_t j = seg + (ent & kJMask);
+      int code = (int)(ent >> kJBits);
+      float4 xj = __ldg(A.xh + j), lj = __ldg(A.xl + j);
+      // hi parts on the 2^-12 grid: exact; lo parts tiny
+      float a0 = xj.x - xi.x, a1 = xj.y - xi.y, a2 = xj.z - xi.z;
+      float b0 = lj.x - li.x, b1 = lj.y - li.y, b2 = lj.z - li.z;
+      if (code != kCenter) {
+        float4 sh = __ldg(tab + 2 * code), sl = __ldg(tab + 2 * code + 1);
+        a0 += sh.x; a1 += sh.y; a2 += sh.z;
+        b0 += sl.x; b1 += sl.y; b2 += sl.z;
+      }
+      float d0 = a0 + b0, d1 = a1 + b1, d2 = a2 + b2;
+      float r2 = fmaf(d0, d0, fmaf(d1, d1, d2 * d2));
+      if (r2 < P.rc2f) {
+        float phi, fr;
+        PotMath<float>::eval(P, r2, phi, fr);
+        f0 = fmaf(fr, d0, f0); f1 = fmaf(fr, d1, f1); f2 = fmaf(fr, d2, f2);
+        if (EW) {
+          e += 0.5f * (phi - P.phicf);
+          float hf = 0.5f * fr;
+          float h0 = hf * d0, h1 = hf * d1;
+          w0 = fmaf(h0, d0, w0); w1 = fmaf(h1, d1, w1); w2 = fmaf(hf * d2, d2, w2);
+          w3 = fmaf(h0, d1, w3); w4 = fmaf(h0, d2, w4); w5 = fmaf(h1, d2, w5);
+        }
+      }
+    }
+    if (valid) A.F[k] = make_float4(f0, f1, f2, e);
+    if (EW) {
+      double v[7] = {(double)e, (double)w0, (double)w1, (double)w2, (double)w3, (double)w4, (double)w5};
+#pragma unroll
+      for (int c = 0; c < 7; c++) {
+        double t = warp_sum(v[c]);
+        if (lane == 0) partial[(int64_t)w * kPartialStride + c] = t;
+      }
+    }
+  }
+}
+
+// One warp per system: FP64 sum of the system's warp partials in warp order
+// (deterministic, independent of the batch around the system).
+// partial slots: 0 energy, 1..6 virial (xx yy zz xy xz yz), 7 kinetic energy.
+__global__ void k_reduce_sys(int32_t B, SysArrays S, const double* __restrict__ partial, double* E, double* stress,
+                             double* KE, double* Eint, double* Wint) {
+  int s = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  int lane = threadIdx.x & 31;
+  if (s >= B) return;
+  int w0 = S.warp_start[s], w1 = S.warp_end[s];
+  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int w = w0 + lane; w < w1; w += 32)
+    for (int c = 0; c < 8; c++) acc[c] += partial[(int64_t)w * kPartialStride + c];
+  for (int c = 0; c < 8; c++) acc[c] = warp_sum(acc[c]);
+  if (lane != 0) return;
+  const double* h = S.h + 9 * s;
+  double V = fabs(h[0] * (h[4] * h[8] - h[5] * h[7]) - h[1] * (h[3] * h[8] - h[5] * h[6]) +
+                  h[2] * (h[3] * h[7] - h[4] * h[6]));
+  double W[9] = {acc[1], acc[4], acc[5], acc[4], acc[2], acc[6], acc[5], acc[6], acc[3]};
+  if (E) E[s] = acc[0];
+  if (Eint) Eint[s] = acc[0];
+  if (stress) for (int q = 0; q < 9; q++) stress[9 * (int64_t)s + q] = W[q] / V;
+  if (Wint) for (int q = 0; q < 9; q++) Wint[9 * (int64_t)s + q] = W[q];
+  if (KE) KE[s] = acc[7];
+}
+
+__global__ void k_clear_dirty(int32_t B, SysArrays S) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < B) S.dirty[s] = 0;
+}
+
+template __global__ void k_pair<true, true>(int32_t, const int32_t*, SysArrays, SlotArrays, const DevPot*, int64_t, int, double*);
+template __global__ void k_pair<true, false>(int32_t, const int32_t*, SysArrays, SlotArrays, const DevPot*, int64_t, int, double*);
+template __global__ void k_pair<false, true>(int32_t, const int32_t*, SysArrays, SlotArrays, const DevPot*, int64_t, int, double*);
+template __global__ void k_pair<false, false>(int32_t, const int32_t*, SysArrays, SlotArrays, const DevPot*, int64_t, int, double*);
+
+}  // namespace ts

@@ -1,0 +1,88 @@
+// ts_run.cu -- the persistent MD step loop behind ts_md_step.  The K-step
+// loop (kick/drift/noise + skin check, conditional per-system re-listing,
+// pair forces) is issued once into a CUDA graph per (K, parameters, stream)
+// and replayed on later calls, so the host crosses to the device once per
+// call instead of once per kernel.  Kernels read sizes and the Langevin
+// step counter from device memory, so one graph serves every call with the
+// same batch layout.
+#include "ts_api.h"
+
+namespace ts {
+
+static void md_body(ts_batch* b, cudaStream_t st, const ts_md_params* p, int n_steps, double c1, bool need_e) {
+  int g = 0;
+  {
+    int64_t blocks = (b->Npad + 255) / 256;
+    g = (int)(blocks < 148 * 16 ? (blocks < 1 ? 1 : blocks) : 148 * 16);
+  }
+  for (int k = 0; k < n_steps; k++) {
+    double kick = k == 0 ? 0.5 * p->dt : p->dt;
+    if (b->f64) {
+      if (p->kind == TS_NVE)
+        k_md_kick_drift<true, 0><<<g, 256, 0, st>>>(b->Npad, b->S, b->A, b->d_pots, kick, p->dt, c1, p->seed, b->d_step, k);
+      else
+        k_md_kick_drift<true, 1><<<g, 256, 0, st>>>(b->Npad, b->S, b->A, b->d_pots, kick, p->dt, c1, p->seed, b->d_step, k);
+    } else {
+      if (p->kind == TS_NVE)
+        k_md_kick_drift<false, 0><<<g, 256, 0, st>>>(b->Npad, b->S, b->A, b->d_pots, kick, p->dt, c1, p->seed, b->d_step, k);
+      else
+        k_md_kick_drift<false, 1><<<g, 256, 0, st>>>(b->Npad, b->S, b->A, b->d_pots, kick, p->dt, c1, p->seed, b->d_step, k);
+    }
+    b->launches++;
+    relist(b, st, false);
+    pair(b, st, need_e && k == n_steps - 1, false);
+  }
+  int blocks = (int)(((int64_t)b->nwarps * 32 + 127) / 128);
+  if (b->f64) k_md_final<true><<<blocks, 128, 0, st>>>(b->nwarps, b->S, b->A, n_steps > 0 ? 0.5 * p->dt : 0.0, b->d_partial);
+  else k_md_final<false><<<blocks, 128, 0, st>>>(b->nwarps, b->S, b->A, n_steps > 0 ? 0.5 * p->dt : 0.0, b->d_partial);
+  b->launches++;
+  clear_dirty(b, st);
+}
+
+ts_status md_loop(ts_batch* b, cudaStream_t st, const ts_md_params* p, int n_steps, double c1, bool need_e) {
+  k_set_u64<<<1, 1, 0, st>>>(b->d_step, p->step0);
+  b->launches++;
+  if (!b->graphs_valid) {
+    for (auto& g : b->graphs) if (g.exec) cudaGraphExecDestroy(g.exec);
+    b->graphs.clear();
+    b->graphs_valid = true;
+  }
+  bool capturable = b->use_graphs && st != nullptr && n_steps > 0;
+  if (capturable) {
+    for (auto& g : b->graphs) {
+      if (g.kind == 0 && g.n_steps == n_steps && g.md_kind == p->kind && g.need_e == need_e && g.dt == p->dt &&
+          g.c1 == c1 && g.seed == p->seed && g.stream == st) {
+        if (!cuda_ok(b, cudaGraphLaunch(g.exec, st), "cudaGraphLaunch")) return TS_ERR_CUDA;
+        b->launches += 1;
+        return TS_OK;
+      }
+    }
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      int64_t l0 = b->launches;
+      md_body(b, st, p, n_steps, c1, need_e);
+      b->launches = l0;
+      cudaError_t e = cudaStreamEndCapture(st, &graph);
+      cudaGraphExec_t exec = nullptr;
+      if (e == cudaSuccess && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess) {
+        cudaGraphDestroy(graph);
+        ts_graph_entry ge;
+        ge.kind = 0; ge.n_steps = n_steps; ge.md_kind = p->kind; ge.need_e = need_e; ge.dt = p->dt; ge.c1 = c1;
+        ge.seed = p->seed; ge.stream = st; ge.exec = exec;
+        if (b->graphs.size() > 16) { cudaGraphExecDestroy(b->graphs.front().exec); b->graphs.erase(b->graphs.begin()); }
+        b->graphs.push_back(ge);
+        if (!cuda_ok(b, cudaGraphLaunch(exec, st), "cudaGraphLaunch")) return TS_ERR_CUDA;
+        b->launches += 1;
+        return TS_OK;
+      }
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+    } else {
+      cudaGetLastError();
+    }
+  }
+  md_body(b, st, p, n_steps, c1, need_e);
+  return cuda_ok(b, cudaGetLastError(), "md loop") ? TS_OK : TS_ERR_CUDA;
+}
+
+}  // namespace ts
