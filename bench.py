@@ -1,0 +1,327 @@
+"""Benchmark: batched Langevin MD throughput (atom-steps/s) on the ragged
+512-system mix (LJ argon / Morse copper / soft spheres, 32-2048 atoms each),
+through the C ABI of libts.so.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+A step is one MD step of the whole batch: BAOAB kick/drift/noise, skin check
+with per-system conditional re-listing, fused pair forces.  Steps run as
+calls of ``--inner`` steps (one CUDA-graph replay each); L2 is flushed
+(256 MiB write) before every call, outside the timed events.  Rank 0 prints
+one JSON line.  ``--impl reference`` times the FP64 CPU oracle on a bounded
+sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "batched MD atom-steps/s on 1 B300 vs per-system loop; pair-kernel % HBM peak"
+UNIT = "atom-steps/s"
+FP32_LANES_PER_SM, N_SM = 128, 148
+FLOP_PER_PAIR = 30          # per ordered pair within the cutoff (force, energy, virial terms)
+BYTES_PER_ATOM = 32         # read own position, write own force, per atom-step
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6400.0), d.get("sm_max_mhz", 2032.0), "measured"
+    return 6400.0, 2032.0, "fallback"
+
+
+def workload(seed=1, n_systems=512):
+    from paper_2508_06628_b300 import workloads as W
+    return W.ragged_mix(seed=seed, n_systems=n_systems)
+
+
+class Clocks:
+    """Sample nvidia-smi during the timed region."""
+
+    def __init__(self, path):
+        self.path = path
+        self.p = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+            self.f.close()
+
+    def summary(self, device_index=0):
+        try:
+            rows = [l.split(",") for l in open(self.path) if l.strip()]
+        except Exception:
+            return None
+        rows = [[c.strip() for c in r] for r in rows if len(r) >= 9 and r[0].strip() == str(device_index)]
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for n, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(rows[0][2]), "samples": len(rows),
+                "reasons": sorted(reasons)}
+
+
+def run_ours(args, rank, world):
+    import torch
+    from paper_2508_06628_b300 import ts
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    hb = workload(seed=1 + 1000 * rank)
+    pots = [dict(p, skin=s) for p, s in zip(hb.pots, ts.default_skins(hb.pots))]
+    b = ts.Batch(pots, hb.n_atoms, hb.n_systems, precision=ts.TS_MIXED, device=dev.index)
+    s = ts.DeviceState.from_host(hb, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    dt, gamma = hb.meta["dt"], hb.meta["gamma"]
+    inner = max(1, min(args.inner, args.steps))
+    E = torch.zeros(hb.n_systems, dtype=torch.float64, device=dev)
+    KE = torch.zeros_like(E)
+    step = 0
+    with torch.cuda.stream(stream):
+        b.neighbor_build(s, force=True, stream=stream)
+        for _ in range(args.warmup):
+            b.md_step(s, inner, dt, kind=ts.TS_LANGEVIN, gamma=gamma, seed=5, step0=step, stream=stream)
+            step += inner
+        b.poll(stream)
+    ncalls = (args.steps + inner - 1) // inner
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(ncalls)]
+    l0, r0 = b.counters()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = Clocks(os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "",
+                              f"clocks_rank{rank}.csv"))
+    with clk, torch.cuda.stream(stream):
+        for c in range(ncalls):
+            flush.fill_(c & 0xff)
+            evs[c][0].record(stream)
+            b.md_step(s, inner, dt, kind=ts.TS_LANGEVIN, gamma=gamma, seed=5, step0=step, stream=stream)
+            evs[c][1].record(stream)
+            step += inner
+        stream.synchronize()
+    torch.cuda.synchronize()
+    ms = sum(e0.elapsed_time(e1) for e0, e1 in evs)
+    l1, r1 = b.counters()
+    b.poll(stream)
+    steps_done = ncalls * inner
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        na = torch.tensor([hb.n_atoms], dtype=torch.float64, device=dev)
+        dist.all_reduce(na)
+        total_atoms = float(na.item())
+    else:
+        total_atoms = float(hb.n_atoms)
+    value = total_atoms * steps_done / (ms / 1e3)
+    out = {"ms": ms, "steps": steps_done, "value": value, "launches": l1 - l0, "relists": r1 - r0,
+           "n_atoms": hb.n_atoms, "n_systems": hb.n_systems, "inner": inner, "clocks": clk.summary(dev.index or 0)}
+    if rank != 0:
+        return out, None
+    # --- dominant kernel: the pair kernel, timed alone with CUDA events on the stream
+    with torch.cuda.stream(stream):
+        kms, pairs, atoms = b.profile_pair(s, reps=10, flush=flush, stream=stream)
+    hbm, smmhz, src = peaks()
+    clocks = out["clocks"] or {}
+    flops = pairs * FLOP_PER_PAIR
+    alu_peak = N_SM * FP32_LANES_PER_SM * 2 * smmhz * 1e6 / 1e12      # TFLOP/s, FMA = 2
+    achieved = flops / (kms / 1e3) / 1e12
+    hbm_achieved = atoms * BYTES_PER_ATOM / (kms / 1e3) / 1e9
+    out["roofline"] = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                       "frac": achieved / alu_peak, "traffic": None, "kernel": "k_pair<mixed>",
+                       "kernel_ms": kms, "pairs_per_launch": pairs, "flop_per_pair": FLOP_PER_PAIR,
+                       "peak_source": f"148 SM x 128 FP32 lanes x 2 x {smmhz:.0f} MHz (max SM clock)",
+                       "hbm": {"achieved": hbm_achieved, "peak": hbm, "unit": "GB/s", "frac": hbm_achieved / hbm,
+                               "bytes_per_atom": BYTES_PER_ATOM, "peak_source": src}}
+    # --- per-system launch loop (same kernels, one system per batch, one step per call)
+    if not args.no_loop:
+        out["per_system_loop"] = per_system_loop(hb, pots, dev, args)
+    # --- end to end through the public API with host buffers
+    out["e2e"] = e2e(b, s, hb, dev, stream, args, dt, gamma, inner)
+    b.close()
+    return out, hb
+
+
+def per_system_loop(hb, pots, dev, args, n_sample=32, steps=3):
+    import torch
+    from paper_2508_06628_b300 import ts
+    rng = np.random.default_rng(0)
+    pick = np.sort(rng.choice(hb.n_systems, n_sample, replace=False))
+    stream = torch.cuda.Stream(device=dev)
+    runs = []
+    for k in pick:
+        sub = hb.subset([k])
+        bb = ts.Batch(pots, sub.n_atoms, 1, precision=ts.TS_MIXED, device=dev.index)
+        ss = ts.DeviceState.from_host(sub, device=dev)
+        with torch.cuda.stream(stream):
+            bb.neighbor_build(ss, force=True, stream=stream)
+            bb.md_step(ss, 1, hb.meta["dt"], kind=ts.TS_LANGEVIN, gamma=hb.meta["gamma"], seed=5, stream=stream)
+        runs.append((bb, ss, sub.n_atoms))
+    stream.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for t in range(steps):
+            for bb, ss, n in runs:
+                bb.md_step(ss, 1, hb.meta["dt"], kind=ts.TS_LANGEVIN, gamma=hb.meta["gamma"], seed=5, step0=t + 1,
+                           stream=stream)
+        e1.record(stream)
+    stream.synchronize()
+    ms = e0.elapsed_time(e1)
+    atoms = sum(n for _, _, n in runs)
+    for bb, _, _ in runs:
+        bb.close()
+    return {"value": atoms * steps / (ms / 1e3), "unit": UNIT, "systems_sampled": int(n_sample), "steps": steps,
+            "how": "each system its own batch, one ts_md_step(1) call per system per step, sequential"}
+
+
+def e2e(b, s, hb, dev, stream, args, dt, gamma, inner):
+    """Same metric through the public API with pinned host buffers: every call
+    copies the state in (H2D) and reads the per-system energies back (D2H)."""
+    import torch
+    from paper_2508_06628_b300 import ts
+    pos_h = torch.from_numpy(np.ascontiguousarray(hb.pos)).pin_memory()
+    vel_h = torch.from_numpy(np.ascontiguousarray(hb.vel)).pin_memory()
+    E = torch.zeros(hb.n_systems, dtype=torch.float64, device=dev)
+    KE = torch.zeros_like(E)
+    E_h = torch.zeros(hb.n_systems, dtype=torch.float64).pin_memory()
+    KE_h = torch.zeros_like(E_h).pin_memory()
+    ncalls = max(1, (args.steps + inner - 1) // inner)
+    with torch.cuda.stream(stream):
+        s.pos.copy_(pos_h, non_blocking=True)
+        s.vel.copy_(vel_h, non_blocking=True)
+        b.md_step(s, inner, dt, kind=ts.TS_LANGEVIN, gamma=gamma, seed=9, stream=stream)   # warm (re-list)
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for c in range(ncalls):
+            s.pos.copy_(pos_h, non_blocking=True)
+            s.vel.copy_(vel_h, non_blocking=True)
+            b.md_step(s, inner, dt, kind=ts.TS_LANGEVIN, gamma=gamma, seed=9, step0=c * inner, E=E, KE=KE,
+                      stream=stream)
+            E_h.copy_(E, non_blocking=True)
+            KE_h.copy_(KE, non_blocking=True)
+        e1.record(stream)
+        stream.synchronize()
+    ms = e0.elapsed_time(e1)
+    return {"value": hb.n_atoms * ncalls * inner / (ms / 1e3), "unit": UNIT,
+            "h2d_bytes_per_step": int(2 * hb.n_atoms * 24 / inner), "d2h_bytes_per_step": int(2 * hb.n_systems * 8 / inner),
+            "how": f"per call of {inner} steps: H2D pos+vel from pinned host, D2H energies"}
+
+
+def cpu_baseline(hb, budget_s=15.0):
+    """FP64 oracle (cell-list mode) on a bounded sample of the same workload."""
+    from oracle import oracle
+    rng = np.random.default_rng(0)
+    order = rng.permutation(hb.n_systems)
+    picked, atoms, t_used = [], 0, 0.0
+    # grow the sample until about budget_s of CPU work
+    chunk = 16
+    t0 = time.time()
+    total_atoms, total_time, steps = 0, 0.0, 1
+    for start in range(0, hb.n_systems, chunk):
+        sub = hb.subset(np.sort(order[start:start + chunk]))
+        t1 = time.time()
+        oracle.md(sub.offsets, sub.pos, sub.vel, sub.mass, sub.cell, sub.pbc, sub.pot_idx, sub.pots, hb.meta["dt"],
+                  steps, kind=1, kT=sub.kT, gamma=hb.meta["gamma"], seed=5, uid=sub.uid, use_cells=True)
+        total_time += time.time() - t1
+        total_atoms += sub.n_atoms
+        if time.time() - t0 > budget_s:
+            break
+    return {"value": total_atoms * steps / total_time, "unit": UNIT, "cores": oracle.num_threads(),
+            "kind": "oracle", "sample": f"{total_atoms} atoms in {start // chunk + 1} groups of {chunk} systems "
+                                        f"(random, seed 0) x {steps} BAOAB step, FP64 cell-list mode"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--inner", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-loop", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    hbcfg = {"workload": "ragged-mix-512: FCC/BCC n x m x k supercells of 32-2048 atoms, 1/3 each LJ argon, "
+                         "Morse Cu, soft sphere; 0.05 A rattle, +-5% strained triclinic cells; BAOAB 300 K, dt 1 fs",
+             "n_systems": 512}
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        hb = workload(seed=1)
+        t0 = time.time()
+        cb = cpu_baseline(hb, budget_s=max(5.0, min(60.0, 4.0 * (args.steps + args.warmup))))
+        line = {"metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": hb.n_atoms / cb["value"] * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+                "config": dict(hbcfg, n_atoms=hb.n_atoms), "cpu_baseline": cb,
+                "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        dist.init_process_group("nccl")
+    out, hb = run_ours(args, rank, world)
+    if rank == 0:
+        cb = None if args.no_cpu else cpu_baseline(hb)
+        ms_step = out["ms"] / out["steps"]
+        line = {"metric": METRIC, "value": out["value"], "unit": UNIT, "n_gpus": world, "steps": out["steps"],
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": dict(hbcfg, n_atoms=out["n_atoms"], md_steps_per_call=out["inner"],
+                               l2="flushed (256 MiB write) before every call, outside the timed events",
+                               precision="FP32 pair arithmetic, FP64 per-system energy/virial, double-float x and v",
+                               parallelism=f"systems sharded: dp{world}" if world > 1 else "single GPU"),
+                "roofline": out["roofline"], "cpu_baseline": cb, "e2e": out["e2e"],
+                "gpu_launches": out["launches"], "relists_in_timed_region": out["relists"],
+                "clocks": out["clocks"]}
+        if "per_system_loop" in out:
+            line["per_system_loop"] = out["per_system_loop"]
+            line["batched_over_loop"] = out["value"] / world / out["per_system_loop"]["value"]
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

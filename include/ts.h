@@ -318,6 +318,16 @@ ts_status ts_batch_poll(ts_batch* b, void* stream, int timeout_ms);
  * fastest; cached under cfg->autotune_cache by (potential mix, size class). */
 ts_status ts_autotune(ts_batch* b, ts_state* s, void* stream);
 
+/* Measurement hook: launch the pair-force kernel alone (forces only, the form
+ * an MD step uses) reps times on the current lists, each launch preceded by
+ * a write of flush_bytes to flush_buf (device scratch, may be NULL) to evict
+ * L2, timing each launch with CUDA events on the stream.  Synchronises.
+ * ms_out (host): mean launch duration in ms; pairs_out (host, may be NULL):
+ * ordered pairs within the cutoff (the algorithmic work of one launch);
+ * atoms_out (host, may be NULL): atoms per launch. */
+ts_status ts_profile_pair(ts_batch* b, ts_state* s, int reps, void* flush_buf, size_t flush_bytes, double* ms_out,
+                          int64_t* pairs_out, int64_t* atoms_out, void* stream);
+
 /* Human-readable text of the last host-side error of this batch (never NULL). */
 const char* ts_last_error(const ts_batch* b);
 

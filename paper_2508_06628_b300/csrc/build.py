@@ -6,10 +6,10 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 PKG = os.path.dirname(HERE)
 SO = os.path.join(PKG, "libts.so")
-SOURCES = ["ts_neighbor.cu", "ts_pair.cu", "ts_md.cu", "ts_run.cu", "ts_api.cu", "ts_pending.cu", "ts_sched.cpp"]
+SOURCES = ["ts_all.cu", "ts_sched.cpp"]
+UNITY_PARTS = ["ts_neighbor.cu", "ts_pair.cu", "ts_md.cu", "ts_run.cu", "ts_api.cu", "ts_pending.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
-         "-static-global-template-stub=false"]
+FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 
 
 def sources():
@@ -20,7 +20,7 @@ def stale():
     if not os.path.exists(SO):
         return True
     t = os.path.getmtime(SO)
-    deps = sources() + [os.path.join(HERE, f) for f in os.listdir(HERE) if f.endswith((".cuh", ".h"))]
+    deps = sources() + [os.path.join(HERE, f) for f in os.listdir(HERE) if f.endswith((".cuh", ".h", ".cu"))]
     deps.append(os.path.join(os.path.dirname(PKG), "include", "ts.h"))
     return any(os.path.getmtime(d) > t for d in deps)
 

@@ -472,3 +472,44 @@ extern "C" ts_status ts_neighbor_export(ts_batch* b, int32_t* j_out, int32_t* im
 }
 
 extern "C" int32_t ts_batch_max_neighbors(const ts_batch* b) { return b ? b->max_nbrs : 0; }
+
+extern "C" ts_status ts_profile_pair(ts_batch* b, ts_state* s, int reps, void* flush_buf, size_t flush_bytes,
+                                     double* ms_out, int64_t* pairs_out, int64_t* atoms_out, void* stream) {
+  ts_status r = check_state(b, s, false);
+  if (r != TS_OK) return r;
+  if (reps < 1 || !ms_out) return fail(b, TS_ERR_INVALID_ARG, "reps < 1 or null output");
+  cudaStream_t st = (cudaStream_t)stream;
+  r = prologue(b, s, st, false);
+  if (r != TS_OK) return r;
+  ensure_forces(b, st);
+  cudaEvent_t e0, e1;
+  if (!cuda_ok(b, cudaEventCreate(&e0), "event") || !cuda_ok(b, cudaEventCreate(&e1), "event")) return TS_ERR_CUDA;
+  double total = 0;
+  for (int k = 0; k < reps; k++) {
+    if (flush_buf && flush_bytes) cudaMemsetAsync(flush_buf, k & 0xff, flush_bytes, st);
+    cudaEventRecord(e0, st);
+    pair(b, st, false, false);
+    cudaEventRecord(e1, st);
+    if (!cuda_ok(b, cudaEventSynchronize(e1), "event sync")) return TS_ERR_CUDA;
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    total += ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *ms_out = total / reps;
+  if (pairs_out) {
+    unsigned long long* d = (unsigned long long*)b->d_counters + 2;
+    unsigned long long h = 0;
+    cudaMemsetAsync(d, 0, 8, st);
+    k_count_pairs<<<(int)(((int64_t)b->nwarps * 32 + 127) / 128), 128, 0, st>>>(b->nwarps, b->d_warp_sys, b->S, b->A,
+                                                                                 b->d_pots, b->Ncap, b->f64, d);
+    b->launches++;
+    if (!cuda_ok(b, cudaMemcpyAsync(&h, d, 8, cudaMemcpyDeviceToHost, st), "d2h") ||
+        !cuda_ok(b, cudaStreamSynchronize(st), "sync"))
+      return TS_ERR_CUDA;
+    *pairs_out = (int64_t)h;
+  }
+  if (atoms_out) *atoms_out = b->N;
+  return cuda_ok(b, cudaGetLastError(), "ts_profile_pair") ? TS_OK : TS_ERR_CUDA;
+}

@@ -16,6 +16,7 @@ struct ts_graph_entry {
   uint32_t seed = 0;
   cudaStream_t stream = nullptr;
   cudaGraphExec_t exec = nullptr;
+  int64_t kernels = 0;      // kernel nodes in the graph
 };
 
 struct ts_batch {

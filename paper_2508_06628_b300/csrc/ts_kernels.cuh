@@ -45,6 +45,8 @@ __global__ void k_pair(int32_t n_warps, const int32_t* warp_sys, SysArrays S, Sl
 __global__ void k_reduce_sys(int32_t B, SysArrays S, const double* partial, double* E, double* stress, double* KE,
                              double* Eint, double* Wint);
 __global__ void k_clear_dirty(int32_t B, SysArrays S);
+__global__ void k_count_pairs(int32_t n_warps, const int32_t* warp_sys, SysArrays S, SlotArrays A, const DevPot* pots,
+                              int64_t stride, int f64, unsigned long long* out);
 
 // MD (ts_md.cu)
 template <bool F64, int KIND>

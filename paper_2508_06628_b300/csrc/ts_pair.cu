@@ -133,6 +133,41 @@ __global__ void k_clear_dirty(int32_t B, SysArrays S) {
   if (s < B) S.dirty[s] = 0;
 }
 
+// ordered pairs within the cutoff (work of one pair launch)
+__global__ void k_count_pairs(int32_t n_warps, const int32_t* __restrict__ warp_sys, SysArrays S, SlotArrays A,
+                              const DevPot* __restrict__ pots, int64_t stride, int f64,
+                              unsigned long long* out) {
+  int w = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  int lane = threadIdx.x & 31;
+  if (w >= n_warps) return;
+  int s = warp_sys[w];
+  int64_t k = (int64_t)w * kWarp + lane;
+  const DevPot P = pots[S.pot[s]];
+  int nn = A.perm[k] >= 0 ? A.nn[k] : 0;
+  int64_t seg = S.seg_start[s];
+  unsigned long long c = 0;
+  for (int q = 0; q < nn; q++) {
+    uint32_t ent = A.nbr[q * stride + k];
+    int64_t j = seg + (ent & kJMask);
+    int code = (int)(ent >> kJBits);
+    double d0, d1, d2;
+    if (f64) {
+      const double* sh = S.shiftd + 3 * ((int64_t)s * kNCodes + code);
+      d0 = A.xd[3 * j] - A.xd[3 * k] + sh[0]; d1 = A.xd[3 * j + 1] - A.xd[3 * k + 1] + sh[1];
+      d2 = A.xd[3 * j + 2] - A.xd[3 * k + 2] + sh[2];
+    } else {
+      int64_t t = (int64_t)s * kNCodes + code;
+      float4 a = A.xh[j], b = A.xl[j], ia = A.xh[k], ib = A.xl[k], sh = S.shift[2 * t], sl = S.shift[2 * t + 1];
+      d0 = (double)((a.x - ia.x + sh.x) + (b.x - ib.x + sl.x));
+      d1 = (double)((a.y - ia.y + sh.y) + (b.y - ib.y + sl.y));
+      d2 = (double)((a.z - ia.z + sh.z) + (b.z - ib.z + sl.z));
+    }
+    c += (d0 * d0 + d1 * d1 + d2 * d2) < P.rc2d;
+  }
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if (lane == 0 && c) atomicAdd(out, c);
+}
+
 template __global__ void k_pair<true, true>(int32_t, const int32_t*, SysArrays, SlotArrays, const DevPot*, int64_t, int, double*);
 template __global__ void k_pair<true, false>(int32_t, const int32_t*, SysArrays, SlotArrays, const DevPot*, int64_t, int, double*);
 template __global__ void k_pair<false, true>(int32_t, const int32_t*, SysArrays, SlotArrays, const DevPot*, int64_t, int, double*);

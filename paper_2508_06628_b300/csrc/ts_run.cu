@@ -53,7 +53,7 @@ ts_status md_loop(ts_batch* b, cudaStream_t st, const ts_md_params* p, int n_ste
       if (g.kind == 0 && g.n_steps == n_steps && g.md_kind == p->kind && g.need_e == need_e && g.dt == p->dt &&
           g.c1 == c1 && g.seed == p->seed && g.stream == st) {
         if (!cuda_ok(b, cudaGraphLaunch(g.exec, st), "cudaGraphLaunch")) return TS_ERR_CUDA;
-        b->launches += 1;
+        b->launches += g.kernels;
         return TS_OK;
       }
     }
@@ -61,6 +61,7 @@ ts_status md_loop(ts_batch* b, cudaStream_t st, const ts_md_params* p, int n_ste
     if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
       int64_t l0 = b->launches;
       md_body(b, st, p, n_steps, c1, need_e);
+      int64_t nk = b->launches - l0;
       b->launches = l0;
       cudaError_t e = cudaStreamEndCapture(st, &graph);
       cudaGraphExec_t exec = nullptr;
@@ -68,11 +69,11 @@ ts_status md_loop(ts_batch* b, cudaStream_t st, const ts_md_params* p, int n_ste
         cudaGraphDestroy(graph);
         ts_graph_entry ge;
         ge.kind = 0; ge.n_steps = n_steps; ge.md_kind = p->kind; ge.need_e = need_e; ge.dt = p->dt; ge.c1 = c1;
-        ge.seed = p->seed; ge.stream = st; ge.exec = exec;
+        ge.seed = p->seed; ge.stream = st; ge.exec = exec; ge.kernels = nk;
         if (b->graphs.size() > 16) { cudaGraphExecDestroy(b->graphs.front().exec); b->graphs.erase(b->graphs.begin()); }
         b->graphs.push_back(ge);
         if (!cuda_ok(b, cudaGraphLaunch(exec, st), "cudaGraphLaunch")) return TS_ERR_CUDA;
-        b->launches += 1;
+        b->launches += nk;
         return TS_OK;
       }
       if (graph) cudaGraphDestroy(graph);

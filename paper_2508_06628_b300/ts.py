@@ -95,6 +95,8 @@ def lib():
         L.ts_autotune.argtypes = [P, C.POINTER(State), P]
         L.ts_batch_counters.argtypes = [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
         L.ts_batch_memory_model.argtypes = [P, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+        L.ts_profile_pair.argtypes = [P, C.POINTER(State), I, P, C.c_size_t, C.POINTER(C.c_double),
+                                      C.POINTER(C.c_int64), C.POINTER(C.c_int64), P]
         _lib = L
     return _lib
 
@@ -257,6 +259,13 @@ class Batch:
 
     def autotune(self, s, stream=None):
         self._check(lib().ts_autotune(self.h, C.byref(s.c()), _stream(stream)), "ts_autotune")
+
+    def profile_pair(self, s, reps=5, flush=None, stream=None):
+        ms, pairs, atoms = C.c_double(), C.c_int64(), C.c_int64()
+        nb = 0 if flush is None else flush.numel() * flush.element_size()
+        self._check(lib().ts_profile_pair(self.h, C.byref(s.c()), int(reps), _ptr(flush), nb, C.byref(ms),
+                                          C.byref(pairs), C.byref(atoms), _stream(stream)), "ts_profile_pair")
+        return ms.value, pairs.value, atoms.value
 
     def counters(self):
         a, b = C.c_int64(), C.c_int64()
