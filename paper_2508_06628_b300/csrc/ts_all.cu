@@ -6,4 +6,5 @@
 #include "ts_md.cu"
 #include "ts_run.cu"
 #include "ts_api.cu"
+#include "ts_fire.cu"
 #include "ts_pending.cu"

@@ -137,7 +137,7 @@ extern "C" ts_status ts_batch_create(const ts_batch_config* cfg, const ts_potent
   ok = ok && alloc(b, b->d_partial, (size_t)kPartialStride * b->Wcap) && alloc(b, b->d_warp_sys, b->Wcap) &&
        alloc(b, b->d_count, b->Ccap) && alloc(b, b->d_cstart, b->Ccap) &&
        alloc(b, b->d_bsum, (b->Ccap + 1023) / 1024 + 1) && alloc(b, b->d_starts, B + 1) &&
-       alloc(b, b->d_Eint, B) && alloc(b, b->d_Wint, 9 * B) && alloc(b, b->d_scal, 16 * B) &&
+       alloc(b, b->d_Eint, B) && alloc(b, b->d_Wint, 9 * B) && alloc(b, b->d_scal, 32 * B) &&
        alloc(b, b->d_gparam_part, 4 * b->Wcap) && alloc(b, b->d_gacc, 3 * kMaxPots);
   if (ok) ok = cuda_ok(b, cudaMemcpy(b->d_pots, dp, sizeof dp, cudaMemcpyHostToDevice), "copy pots");
   if (ok) ok = cuda_ok(b, cudaMemset(b->d_err, 0, 16), "memset") && cuda_ok(b, cudaMemset(b->d_counters, 0, 32), "memset");

@@ -154,13 +154,7 @@ __global__ void k_md_final(int32_t n_warps, SysArrays S, SlotArrays A, double ki
   if (lane == 0) partial[(int64_t)w * kPartialStride + 7] = ke;
 }
 
-template __global__ void k_md_kick_drift<true, 0>(int64_t, SysArrays, SlotArrays, const DevPot*, double, double, double, uint32_t, const uint64_t*, uint64_t);
-template __global__ void k_md_kick_drift<true, 1>(int64_t, SysArrays, SlotArrays, const DevPot*, double, double, double, uint32_t, const uint64_t*, uint64_t);
-template __global__ void k_md_kick_drift<false, 0>(int64_t, SysArrays, SlotArrays, const DevPot*, double, double, double, uint32_t, const uint64_t*, uint64_t);
-template __global__ void k_md_kick_drift<false, 1>(int64_t, SysArrays, SlotArrays, const DevPot*, double, double, double, uint32_t, const uint64_t*, uint64_t);
 
 __global__ void k_set_u64(uint64_t* p, uint64_t v) { *p = v; }
-template __global__ void k_md_final<true>(int32_t, SysArrays, SlotArrays, double, double*);
-template __global__ void k_md_final<false>(int32_t, SysArrays, SlotArrays, double, double*);
 
 }  // namespace ts

@@ -507,23 +507,5 @@ __global__ void k_export_list(int64_t Npad, SysArrays S, SlotArrays A, int32_t m
   }
 }
 
-template __global__ void k_import_pos<true>(int64_t, SysArrays, SlotArrays, const double*, const DevPot*, int, int32_t*);
-template __global__ void k_import_pos<false>(int64_t, SysArrays, SlotArrays, const double*, const DevPot*, int, int32_t*);
-template __global__ void k_import_vel<true>(int64_t, SlotArrays, const double*, const double*);
-template __global__ void k_import_vel<false>(int64_t, SlotArrays, const double*, const double*);
-template __global__ void k_export_state<true>(int64_t, SlotArrays, double*, double*);
-template __global__ void k_export_state<false>(int64_t, SlotArrays, double*, double*);
-template __global__ void k_export_forces<true>(int64_t, SlotArrays, double*);
-template __global__ void k_export_forces<false>(int64_t, SlotArrays, double*);
-template __global__ void k_bin_atoms<true>(int64_t, SysArrays, SlotArrays, int32_t*);
-template __global__ void k_bin_atoms<false>(int64_t, SysArrays, SlotArrays, int32_t*);
-template __global__ void k_final_slot<true>(int64_t, SysArrays, SlotArrays, const int32_t*, const int32_t*, int);
-template __global__ void k_final_slot<false>(int64_t, SysArrays, SlotArrays, const int32_t*, const int32_t*, int);
-template __global__ void k_copy_back<true>(int64_t, SysArrays, SlotArrays, int);
-template __global__ void k_copy_back<false>(int64_t, SysArrays, SlotArrays, int);
-template __global__ void k_build_list<true>(int64_t, SysArrays, SlotArrays, const int32_t*, const int32_t*,
-                                            const DevPot*, int32_t, int64_t, int32_t*);
-template __global__ void k_build_list<false>(int64_t, SysArrays, SlotArrays, const int32_t*, const int32_t*,
-                                             const DevPot*, int32_t, int64_t, int32_t*);
 
 }  // namespace ts

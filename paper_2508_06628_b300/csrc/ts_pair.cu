@@ -168,9 +168,5 @@ __global__ void k_count_pairs(int32_t n_warps, const int32_t* __restrict__ warp_
   if (lane == 0 && c) atomicAdd(out, c);
 }
 
-template __global__ void k_pair<true, true>(int32_t, const int32_t*, SysArrays, SlotArrays, const DevPot*, int64_t, int, double*);
-template __global__ void k_pair<true, false>(int32_t, const int32_t*, SysArrays, SlotArrays, const DevPot*, int64_t, int, double*);
-template __global__ void k_pair<false, true>(int32_t, const int32_t*, SysArrays, SlotArrays, const DevPot*, int64_t, int, double*);
-template __global__ void k_pair<false, false>(int32_t, const int32_t*, SysArrays, SlotArrays, const DevPot*, int64_t, int, double*);
 
 }  // namespace ts

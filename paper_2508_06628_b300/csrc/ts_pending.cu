@@ -1,13 +1,6 @@
 // ts_pending.cu -- entry points still to be written return TS_ERR_UNSUPPORTED.
 #include "ts_api.h"
 using namespace ts;
-extern "C" ts_status ts_fire_init(ts_batch* b, ts_state*, const ts_fire_params*, ts_fire_state*, double*, void*) {
-  return fail(b, TS_ERR_UNSUPPORTED, "not built");
-}
-extern "C" ts_status ts_fire_step(ts_batch* b, ts_state*, ts_fire_state*, double*, const ts_fire_params*, int, uint8_t*,
-                                  double*, double*, double*, void*) {
-  return fail(b, TS_ERR_UNSUPPORTED, "not built");
-}
 extern "C" ts_status ts_pair_forces_backward(ts_batch* b, ts_state*, const double*, const double*, const double*,
                                              double*, double*, int, void*) {
   return fail(b, TS_ERR_UNSUPPORTED, "not built");
