@@ -131,6 +131,12 @@ typedef struct ts_batch ts_batch;
  * (*out = NULL). */
 ts_status ts_batch_create(const ts_batch_config* cfg, const ts_potential* pots, int n_pots, ts_batch** out);
 
+/* Replace the potentials' parameters p[3] in place (kinds, cutoffs, shifts
+ * and skins must stay as created: TS_ERR_INVALID_ARG otherwise).  Used to
+ * evaluate a loss at new parameters, e.g. in a fitting loop (Sec. 2).
+ * Host array of n_pots entries; synchronous. */
+ts_status ts_batch_set_potentials(ts_batch* b, const ts_potential* pots, int n_pots);
+
 /* Free all scratch of the batch (synchronises the device first). */
 ts_status ts_batch_destroy(ts_batch* b);
 

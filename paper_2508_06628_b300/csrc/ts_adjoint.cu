@@ -1,0 +1,446 @@
+// ts_adjoint.cu -- differentiable path (the paper's Sec. 2: gradients of a
+// trajectory observable, a radial distribution function, with respect to
+// potential parameters): the pair-force adjoint, the smeared RDF and its
+// position gradient, and the reverse step of velocity Verlet.
+//
+// Pair adjoint, with d = x_j + n h - x_i over the full list and upstream
+// gF = dL/dF, gE = dL/dE, gS = dL/dstress:
+//   gx_i = sum_j K(d_ij) (gF_j - gF_i) - gE F_i - (1/V) sum_j dT(d_ij) : gS
+//   K(d) = phi'' u u^T + (phi'/r)(I - u u^T),  u = d/r
+//   T(d)_ab = (phi'/r) d_a d_b
+//   gtheta_p = sum_ij (dphi'/dp) u.gF_i + gE/2 sum (dphi/dp - dphi(rc)/dp)
+//              + 1/(2V) sum (dphi'/dp)/r (d.gS.d)
+// Each atom gathers gF of its neighbours (full list), so no scatter atomics;
+// parameter gradients go warp -> system -> potential in a fixed order.
+#include "ts_kernels.cuh"
+
+namespace ts {
+
+template <bool F64>
+__global__ void __launch_bounds__(128) k_pair_bwd(int32_t n_warps, const int32_t* __restrict__ warp_sys, SysArrays S,
+                                                  SlotArrays A, const DevPot* __restrict__ pots, int64_t stride,
+                                                  const double* __restrict__ gE, const double* __restrict__ gS,
+                                                  double* gpart) {
+  int w = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  int lane = threadIdx.x & 31;
+  if (w >= n_warps) return;
+  int s = warp_sys[w];
+  int64_t k = (int64_t)w * kWarp + lane;
+  const DevPot P = pots[S.pot[s]];
+  bool valid = A.perm[k] >= 0;
+  int nn = valid ? A.nn[k] : 0;
+  int64_t seg = S.seg_start[s];
+  const double* h = S.h + 9 * s;
+  double Vinv = 1.0 / fabs(h[0] * (h[4] * h[8] - h[5] * h[7]) - h[1] * (h[3] * h[8] - h[5] * h[6]) +
+                           h[2] * (h[3] * h[7] - h[4] * h[6]));
+  double gEs = gE ? gE[s] : 0.0;
+  double Sg[9];
+  bool stress = gS != nullptr;
+  for (int q = 0; q < 9; q++) Sg[q] = stress ? gS[9 * (int64_t)s + q] : 0.0;
+  // shift derivative dphi(rc)/dp (energy term only)
+  double dphic[3] = {0, 0, 0};
+  if (P.shift && P.kind != TS_SOFT_SPHERE && gEs != 0.0) {
+    double r, d1, d2, dd1[3];
+    PotMath<double>::eval2(P, P.rc2d, r, d1, d2, dphic, dd1);
+  }
+  double gx[3] = {0, 0, 0}, gth[3] = {0, 0, 0};
+  if constexpr (F64) {
+    const double* tab = S.shiftd + 3 * (int64_t)s * kNCodes;
+    const double* xi = A.xd + 3 * k;
+    const double* gi = A.gd1 + 3 * k;
+    for (int q = 0; q < nn; q++) {
+      uint32_t ent = A.nbr[q * stride + k];
+      int64_t j = seg + (ent & kJMask);
+      int code = (int)(ent >> kJBits);
+      double d[3];
+      for (int c = 0; c < 3; c++) d[c] = A.xd[3 * j + c] - xi[c] + tab[3 * code + c];
+      double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+      if (!(r2 < P.rc2d)) continue;
+      double r, d1, d2, dphi[3], dd1[3];
+      PotMath<double>::eval2(P, r2, r, d1, d2, dphi, dd1);
+      double u[3] = {d[0] / r, d[1] / r, d[2] / r};
+      double g[3];
+      for (int c = 0; c < 3; c++) g[c] = A.gd1[3 * j + c] - gi[c];
+      double ug = u[0] * g[0] + u[1] * g[1] + u[2] * g[2];
+      double ugi = u[0] * gi[0] + u[1] * gi[1] + u[2] * gi[2];
+      for (int c = 0; c < 3; c++) gx[c] += d2 * ug * u[c] + d1 / r * (g[c] - ug * u[c]);
+      for (int p = 0; p < 3; p++) gth[p] += dd1[p] * ugi + 0.5 * gEs * (dphi[p] - dphic[p]);
+      if (stress) {
+        double Aq = (d2 - d1 / r) / (r * r), dSd = 0;
+        for (int a = 0; a < 3; a++) for (int b = 0; b < 3; b++) dSd += d[a] * Sg[3 * a + b] * d[b];
+        for (int c = 0; c < 3; c++) {
+          double Sd = Sg[3 * c] * d[0] + Sg[3 * c + 1] * d[1] + Sg[3 * c + 2] * d[2];
+          double dS = d[0] * Sg[c] + d[1] * Sg[3 + c] + d[2] * Sg[6 + c];
+          gx[c] -= Vinv * (Aq * d[c] * dSd + d1 / r * (Sd + dS));
+        }
+        for (int p = 0; p < 3; p++) gth[p] += 0.5 * Vinv * dd1[p] / r * dSd;
+      }
+    }
+    if (valid) {
+      for (int c = 0; c < 3; c++) A.gd0[3 * k + c] = gx[c] - gEs * A.Fd[3 * k + c];
+    }
+  } else {
+    const float4* tab = S.shift + 2 * (int64_t)s * kNCodes;
+    float4 xi = A.xh[k], li = A.xl[k], gi = A.g1[k];
+    float gxf[3] = {0.f, 0.f, 0.f}, gtf[3] = {0.f, 0.f, 0.f};
+    float gEf = (float)gEs, Vf = (float)Vinv;
+    float Sf[9];
+    for (int q = 0; q < 9; q++) Sf[q] = (float)Sg[q];
+    float dpc[3] = {(float)dphic[0], (float)dphic[1], (float)dphic[2]};
+    for (int q = 0; q < nn; q++) {
+      uint32_t ent = __ldg(A.nbr + q * stride + k);
+      int64_t j = seg + (ent & kJMask);
+      int code = (int)(ent >> kJBits);
+      float4 xj = __ldg(A.xh + j), lj = __ldg(A.xl + j);
+      float4 sh = __ldg(tab + 2 * code), sl = __ldg(tab + 2 * code + 1);
+      float d[3] = {((xj.x - xi.x) + sh.x) + ((lj.x - li.x) + sl.x), ((xj.y - xi.y) + sh.y) + ((lj.y - li.y) + sl.y),
+                    ((xj.z - xi.z) + sh.z) + ((lj.z - li.z) + sl.z)};
+      float r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+      if (!(r2 < P.rc2f)) continue;
+      float r, d1, d2, dphi[3], dd1[3];
+      PotMath<float>::eval2(P, r2, r, d1, d2, dphi, dd1);
+      float ri = 1.0f / r;
+      float u[3] = {d[0] * ri, d[1] * ri, d[2] * ri};
+      float4 gj = __ldg(A.g1 + j);
+      float g[3] = {gj.x - gi.x, gj.y - gi.y, gj.z - gi.z};
+      float ug = u[0] * g[0] + u[1] * g[1] + u[2] * g[2];
+      float ugi = u[0] * gi.x + u[1] * gi.y + u[2] * gi.z;
+      for (int c = 0; c < 3; c++) gxf[c] += d2 * ug * u[c] + d1 * ri * (g[c] - ug * u[c]);
+      for (int p = 0; p < 3; p++) gtf[p] += dd1[p] * ugi + 0.5f * gEf * (dphi[p] - dpc[p]);
+      if (stress) {
+        float Aq = (d2 - d1 * ri) * ri * ri, dSd = 0.f;
+        for (int a = 0; a < 3; a++) for (int b = 0; b < 3; b++) dSd += d[a] * Sf[3 * a + b] * d[b];
+        for (int c = 0; c < 3; c++) {
+          float Sd = Sf[3 * c] * d[0] + Sf[3 * c + 1] * d[1] + Sf[3 * c + 2] * d[2];
+          float dS = d[0] * Sf[c] + d[1] * Sf[3 + c] + d[2] * Sf[6 + c];
+          gxf[c] -= Vf * (Aq * d[c] * dSd + d1 * ri * (Sd + dS));
+        }
+        for (int p = 0; p < 3; p++) gtf[p] += 0.5f * Vf * dd1[p] * ri * dSd;
+      }
+    }
+    if (valid) {
+      float4 F = A.F[k];
+      A.g0[k] = make_float4(gxf[0] - gEf * F.x, gxf[1] - gEf * F.y, gxf[2] - gEf * F.z, 0.f);
+    }
+    for (int p = 0; p < 3; p++) gth[p] = gtf[p];
+  }
+  for (int p = 0; p < 3; p++) {
+    double t = warp_sum(gth[p]);
+    if (lane == 0) gpart[4 * (int64_t)w + p] = t;
+  }
+}
+
+// upstream gF (caller order, FP64) -> slots (g1 / gd1), scaled per atom by
+// scale_dt_over_2m * (1/m) when scale > 0 (the velocity-Verlet kick factor)
+template <bool F64>
+__global__ void k_import_grad(int64_t Npad, SlotArrays A, const double* __restrict__ g, double kick) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < Npad; k += (int64_t)gridDim.x * blockDim.x) {
+    int p = A.perm[k];
+    if (p < 0) continue;
+    double c = 1.0;
+    if (kick > 0) c = kick * (F64 ? A.minvd[k] : (double)A.vh[k].w);
+    double v0 = c * g[3 * (int64_t)p], v1 = c * g[3 * (int64_t)p + 1], v2 = c * g[3 * (int64_t)p + 2];
+    if constexpr (F64) { A.gd1[3 * k] = v0; A.gd1[3 * k + 1] = v1; A.gd1[3 * k + 2] = v2; }
+    else A.g1[k] = make_float4((float)v0, (float)v1, (float)v2, 0.f);
+  }
+}
+
+// gPos[p] (+)= gx (slots g0 / gd0)
+template <bool F64>
+__global__ void k_export_grad(int64_t Npad, SlotArrays A, double* gPos, int accumulate) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < Npad; k += (int64_t)gridDim.x * blockDim.x) {
+    int p = A.perm[k];
+    if (p < 0) continue;
+    double v[3];
+    if constexpr (F64) { for (int c = 0; c < 3; c++) v[c] = A.gd0[3 * k + c]; }
+    else { float4 g = A.g0[k]; v[0] = g.x; v[1] = g.y; v[2] = g.z; }
+    for (int c = 0; c < 3; c++) gPos[3 * (int64_t)p + c] = (accumulate ? gPos[3 * (int64_t)p + c] : 0.0) + v[c];
+  }
+}
+
+// parameter gradients: warp partials -> per system (one warp each) -> per potential
+__global__ void k_gparam_sys(int32_t B, SysArrays S, const double* __restrict__ gpart, double* gsys) {
+  int s = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  int lane = threadIdx.x & 31;
+  if (s >= B) return;
+  double a[3] = {0, 0, 0};
+  for (int w = S.warp_start[s] + lane; w < S.warp_end[s]; w += 32)
+    for (int p = 0; p < 3; p++) a[p] += gpart[4 * (int64_t)w + p];
+  for (int p = 0; p < 3; p++) a[p] = warp_sum(a[p]);
+  if (lane == 0) for (int p = 0; p < 3; p++) gsys[3 * (int64_t)s + p] = a[p];
+}
+__global__ void k_gparam_pot(int32_t B, int32_t n_pots, SysArrays S, const double* __restrict__ gsys, double* gParams,
+                             int accumulate) {
+  int q = threadIdx.x;
+  if (q >= n_pots) return;
+  double a[3] = {0, 0, 0};
+  for (int s = 0; s < B; s++)
+    if (S.pot[s] == q) for (int p = 0; p < 3; p++) a[p] += gsys[3 * (int64_t)s + p];
+  for (int p = 0; p < 3; p++) gParams[3 * q + p] = (accumulate ? gParams[3 * q + p] : 0.0) + a[p];
+}
+
+// ---- smeared RDF ---------------------------------------------------------------
+// g_k = V/(N(N-1)) sum_{ordered pairs, r < rmax + 4D} exp(-(r-r_k)^2/2D^2) / (sqrt(2 pi) D 4 pi r_k^2)
+// Pairs add their Gaussian (|r - r_k| <= 8 D) into a per-warp shared
+// histogram; warps add into the system's FP64 row.
+__global__ void k_rdf(int32_t n_warps, const int32_t* __restrict__ warp_sys, SysArrays S, SlotArrays A,
+                      int64_t stride, int f64, double rmax, int K, double* g) {
+  extern __shared__ float hist[];
+  int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int w = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  float* hs = hist + wib * K;
+  for (int q = lane; q < K; q += 32) hs[q] = 0.f;
+  __syncwarp();
+  if (w >= n_warps) return;
+  int s = warp_sys[w];
+  int64_t k = (int64_t)w * kWarp + lane;
+  int nn = A.perm[k] >= 0 ? A.nn[k] : 0;
+  int64_t seg = S.seg_start[s];
+  float D = (float)(rmax / K), cut2 = (float)((rmax + 4 * rmax / K) * (rmax + 4 * rmax / K));
+  for (int q = 0; q < nn; q++) {
+    uint32_t ent = A.nbr[q * stride + k];
+    int64_t j = seg + (ent & kJMask);
+    int code = (int)(ent >> kJBits);
+    float r2;
+    if (f64) {
+      const double* sh = S.shiftd + 3 * ((int64_t)s * kNCodes + code);
+      double d0 = A.xd[3 * j] - A.xd[3 * k] + sh[0], d1 = A.xd[3 * j + 1] - A.xd[3 * k + 1] + sh[1],
+             d2 = A.xd[3 * j + 2] - A.xd[3 * k + 2] + sh[2];
+      r2 = (float)(d0 * d0 + d1 * d1 + d2 * d2);
+    } else {
+      int64_t t = (int64_t)s * kNCodes + code;
+      float4 a = A.xh[j], b = A.xl[j], ia = A.xh[k], ib = A.xl[k], sh = S.shift[2 * t], sl = S.shift[2 * t + 1];
+      float d0 = ((a.x - ia.x) + sh.x) + ((b.x - ib.x) + sl.x), d1 = ((a.y - ia.y) + sh.y) + ((b.y - ib.y) + sl.y),
+            d2 = ((a.z - ia.z) + sh.z) + ((b.z - ib.z) + sl.z);
+      r2 = d0 * d0 + d1 * d1 + d2 * d2;
+    }
+    if (!(r2 < cut2)) continue;
+    float r = sqrtf(r2);
+    int c = (int)(r / D);
+    for (int b = c - 8; b <= c + 8; b++) {
+      if (b < 0 || b >= K) continue;
+      float rk = (b + 0.5f) * D, t = (r - rk) / D;
+      atomicAdd(&hs[b], __expf(-0.5f * t * t) / (rk * rk));
+    }
+  }
+  __syncwarp();
+  for (int q = lane; q < K; q += 32)
+    if (hs[q] != 0.f) atomicAdd(&g[(int64_t)s * K + q], (double)hs[q]);
+}
+
+__global__ void k_rdf_norm(int32_t B, SysArrays S, double rmax, int K, double* g) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)B * K) return;
+  int s = (int)(t / K);
+  const double* h = S.h + 9 * s;
+  double V = fabs(h[0] * (h[4] * h[8] - h[5] * h[7]) - h[1] * (h[3] * h[8] - h[5] * h[6]) + h[2] * (h[3] * h[7] - h[4] * h[6]));
+  double n = S.n_atoms[s], D = rmax / K;
+  g[t] *= V / (n * (n - 1)) / (sqrt(2.0 * M_PI) * D * 4.0 * M_PI);
+}
+
+// gx_i = -2 sum_j dG(r_ij) u_ij,  dG(r) = sum_k gg_k pref exp(-t^2/2) (-t/D) / r_k^2
+template <bool F64>
+__global__ void k_rdf_bwd(int32_t n_warps, const int32_t* __restrict__ warp_sys, SysArrays S, SlotArrays A,
+                          int64_t stride, double rmax, int K, const double* __restrict__ gg) {
+  int w = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  int lane = threadIdx.x & 31;
+  if (w >= n_warps) return;
+  int s = warp_sys[w];
+  int64_t k = (int64_t)w * kWarp + lane;
+  bool valid = A.perm[k] >= 0;
+  int nn = valid ? A.nn[k] : 0;
+  int64_t seg = S.seg_start[s];
+  const double* h = S.h + 9 * s;
+  double V = fabs(h[0] * (h[4] * h[8] - h[5] * h[7]) - h[1] * (h[3] * h[8] - h[5] * h[6]) + h[2] * (h[3] * h[7] - h[4] * h[6]));
+  double n = S.n_atoms[s], D = rmax / K;
+  double pref = V / (n * (n - 1)) / (sqrt(2.0 * M_PI) * D * 4.0 * M_PI);
+  const double* ggs = gg + (int64_t)s * K;
+  double cut2 = (rmax + 4 * D) * (rmax + 4 * D);
+  double gx[3] = {0, 0, 0};
+  for (int q = 0; q < nn; q++) {
+    uint32_t ent = A.nbr[q * stride + k];
+    int64_t j = seg + (ent & kJMask);
+    int code = (int)(ent >> kJBits);
+    double d[3];
+    if constexpr (F64) {
+      const double* sh = S.shiftd + 3 * ((int64_t)s * kNCodes + code);
+      for (int c = 0; c < 3; c++) d[c] = A.xd[3 * j + c] - A.xd[3 * k + c] + sh[c];
+    } else {
+      int64_t t = (int64_t)s * kNCodes + code;
+      float4 a = A.xh[j], b = A.xl[j], ia = A.xh[k], ib = A.xl[k], sh = S.shift[2 * t], sl = S.shift[2 * t + 1];
+      d[0] = ((a.x - ia.x) + sh.x) + ((b.x - ib.x) + sl.x);
+      d[1] = ((a.y - ia.y) + sh.y) + ((b.y - ib.y) + sl.y);
+      d[2] = ((a.z - ia.z) + sh.z) + ((b.z - ib.z) + sl.z);
+    }
+    double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    if (!(r2 < cut2)) continue;
+    double r = sqrt(r2);
+    int c = (int)(r / D);
+    double dG = 0;
+    for (int b = c - 8; b <= c + 8; b++) {
+      if (b < 0 || b >= K) continue;
+      double rk = (b + 0.5) * D, t = (r - rk) / D;
+      dG += ggs[b] * pref * exp(-0.5 * t * t) / (rk * rk) * (-t / D);
+    }
+    for (int cc = 0; cc < 3; cc++) gx[cc] -= 2.0 * dG * d[cc] / r;
+  }
+  if (valid) {
+    if constexpr (F64) { for (int c = 0; c < 3; c++) A.gd0[3 * k + c] = gx[c]; }
+    else A.g0[k] = make_float4((float)gx[0], (float)gx[1], (float)gx[2], 0.f);
+  }
+}
+
+// velocity-Verlet reverse step, caller-order vectors:
+// stage 1: ub = ax + tmp; vh = av + dt ub (ub kept in ax, vh in av)
+// stage 2: ax = ub + tmp
+template <bool F64>
+__global__ void k_vv_adj(int64_t Npad, SlotArrays A, double* ax, double* av, double dt, int stage) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < Npad; k += (int64_t)gridDim.x * blockDim.x) {
+    int p = A.perm[k];
+    if (p < 0) continue;
+    double t[3];
+    if constexpr (F64) { for (int c = 0; c < 3; c++) t[c] = A.gd0[3 * k + c]; }
+    else { float4 g = A.g0[k]; t[0] = g.x; t[1] = g.y; t[2] = g.z; }
+    for (int c = 0; c < 3; c++) {
+      int64_t o = 3 * (int64_t)p + c;
+      double ub = ax[o] + t[c];
+      ax[o] = ub;
+      if (stage == 1) av[o] = av[o] + dt * ub;
+    }
+  }
+}
+
+}  // namespace ts
+
+using namespace ts;
+
+namespace ts {
+
+static int egrid(ts_batch* b) {
+  int64_t g = (b->Npad + 255) / 256;
+  return (int)(g < 1 ? 1 : (g > 148 * 16 ? 148 * 16 : g));
+}
+
+// gx of the current gF (in g1 / gd1) into slots g0 / gd0; parameter gradients into gParams
+static void backward_core(ts_batch* b, cudaStream_t st, const double* gE, const double* gS, double* gParams,
+                          int accumulate_params) {
+  int blocks = (int)(((int64_t)b->nwarps * 32 + 127) / 128);
+  if (b->f64) k_pair_bwd<true><<<blocks, 128, 0, st>>>(b->nwarps, b->d_warp_sys, b->S, b->A, b->d_pots, b->Ncap, gE, gS, b->d_gparam_part);
+  else k_pair_bwd<false><<<blocks, 128, 0, st>>>(b->nwarps, b->d_warp_sys, b->S, b->A, b->d_pots, b->Ncap, gE, gS, b->d_gparam_part);
+  b->launches++;
+  if (gParams) {
+    k_gparam_sys<<<(b->B * 32 + 127) / 128, 128, 0, st>>>(b->B, b->S, b->d_gparam_part, b->d_scal);
+    k_gparam_pot<<<1, 32, 0, st>>>(b->B, b->n_pots, b->S, b->d_scal, gParams, accumulate_params);
+    b->launches += 2;
+  }
+}
+
+static ts_status rdf_check(ts_batch* b, double rmax, int K) {
+  if (!(rmax > 0) || K < 1 || K > 4096) return fail(b, TS_ERR_INVALID_ARG, "bad rmax or K");
+  for (int q = 0; q < b->n_pots; q++)
+    if (b->rc[q] + b->pots[q].skin < rmax + 4.0 * rmax / K)
+      return fail(b, TS_ERR_INVALID_ARG, "neighbour lists shorter than rmax + 4 D: raise the skin");
+  return TS_OK;
+}
+
+}  // namespace ts
+
+extern "C" ts_status ts_pair_forces_backward(ts_batch* b, ts_state* s, const double* gF, const double* gE,
+                                             const double* gStress, double* gPos, double* gParams, int accumulate,
+                                             void* stream) {
+  ts_status r = check_state(b, s, false);
+  if (r != TS_OK) return r;
+  if (!gF || (!gPos && !gParams)) return fail(b, TS_ERR_INVALID_ARG, "null gradient pointer");
+  cudaStream_t st = (cudaStream_t)stream;
+  r = prologue(b, s, st, false);
+  if (r != TS_OK) return r;
+  ensure_forces(b, st);
+  int g = egrid(b);
+  if (b->f64) k_import_grad<true><<<g, 256, 0, st>>>(b->Npad, b->A, gF, 0.0);
+  else k_import_grad<false><<<g, 256, 0, st>>>(b->Npad, b->A, gF, 0.0);
+  b->launches++;
+  backward_core(b, st, gE, gStress, gParams, accumulate);
+  if (gPos) {
+    if (b->f64) k_export_grad<true><<<g, 256, 0, st>>>(b->Npad, b->A, gPos, accumulate);
+    else k_export_grad<false><<<g, 256, 0, st>>>(b->Npad, b->A, gPos, accumulate);
+    b->launches++;
+  }
+  export_state(b, st, s->pos, nullptr);
+  return cuda_ok(b, cudaGetLastError(), "ts_pair_forces_backward") ? TS_OK : TS_ERR_CUDA;
+}
+
+extern "C" ts_status ts_rdf(ts_batch* b, ts_state* s, double rmax, int K, double* g, void* stream) {
+  ts_status r = check_state(b, s, false);
+  if (r != TS_OK) return r;
+  if (!g) return fail(b, TS_ERR_INVALID_ARG, "null output");
+  if ((r = rdf_check(b, rmax, K)) != TS_OK) return r;
+  cudaStream_t st = (cudaStream_t)stream;
+  r = prologue(b, s, st, false);
+  if (r != TS_OK) return r;
+  relist(b, st, false);
+  if (!cuda_ok(b, cudaMemsetAsync(g, 0, sizeof(double) * K * (size_t)b->B, st), "memset")) return TS_ERR_CUDA;
+  int threads = 128;
+  size_t shm = sizeof(float) * K * (threads / 32);
+  if (shm > 48 * 1024) return fail(b, TS_ERR_INVALID_ARG, "K too large");
+  k_rdf<<<(int)(((int64_t)b->nwarps * 32 + threads - 1) / threads), threads, shm, st>>>(b->nwarps, b->d_warp_sys, b->S,
+                                                                                      b->A, b->Ncap, b->f64, rmax, K, g);
+  k_rdf_norm<<<(int)(((int64_t)b->B * K + 255) / 256), 256, 0, st>>>(b->B, b->S, rmax, K, g);
+  b->launches += 2;
+  export_state(b, st, s->pos, nullptr);
+  return cuda_ok(b, cudaGetLastError(), "ts_rdf") ? TS_OK : TS_ERR_CUDA;
+}
+
+extern "C" ts_status ts_rdf_backward(ts_batch* b, ts_state* s, double rmax, int K, const double* gg, double* gPos,
+                                     void* stream) {
+  ts_status r = check_state(b, s, false);
+  if (r != TS_OK) return r;
+  if (!gg || !gPos) return fail(b, TS_ERR_INVALID_ARG, "null pointer");
+  if ((r = rdf_check(b, rmax, K)) != TS_OK) return r;
+  cudaStream_t st = (cudaStream_t)stream;
+  r = prologue(b, s, st, false);
+  if (r != TS_OK) return r;
+  relist(b, st, false);
+  int blocks = (int)(((int64_t)b->nwarps * 32 + 127) / 128);
+  if (b->f64) k_rdf_bwd<true><<<blocks, 128, 0, st>>>(b->nwarps, b->d_warp_sys, b->S, b->A, b->Ncap, rmax, K, gg);
+  else k_rdf_bwd<false><<<blocks, 128, 0, st>>>(b->nwarps, b->d_warp_sys, b->S, b->A, b->Ncap, rmax, K, gg);
+  int g = egrid(b);
+  if (b->f64) k_export_grad<true><<<g, 256, 0, st>>>(b->Npad, b->A, gPos, 1);
+  else k_export_grad<false><<<g, 256, 0, st>>>(b->Npad, b->A, gPos, 1);
+  b->launches += 2;
+  export_state(b, st, s->pos, nullptr);
+  return cuda_ok(b, cudaGetLastError(), "ts_rdf_backward") ? TS_OK : TS_ERR_CUDA;
+}
+
+extern "C" ts_status ts_vv_adjoint_step(ts_batch* b, ts_state* s, const double* x_next, double dt, double* ax,
+                                        double* av, double* gParams, void* stream) {
+  ts_status r = check_state(b, s, false);
+  if (r != TS_OK) return r;
+  if (!x_next || !ax || !av || !gParams || !(dt > 0)) return fail(b, TS_ERR_INVALID_ARG, "bad adjoint arguments");
+  cudaStream_t st = (cudaStream_t)stream;
+  int g = egrid(b);
+  // (1) at u = x_{t+1}: ubar = ax + c J(u)^T av
+  ts_state su = *s;
+  su.pos = const_cast<double*>(x_next);
+  r = prologue(b, &su, st, true);
+  if (r != TS_OK) return r;
+  relist(b, st, false);
+  if (b->f64) k_import_grad<true><<<g, 256, 0, st>>>(b->Npad, b->A, av, 0.5 * dt);
+  else k_import_grad<false><<<g, 256, 0, st>>>(b->Npad, b->A, av, 0.5 * dt);
+  b->launches++;
+  backward_core(b, st, nullptr, nullptr, gParams, 1);
+  if (b->f64) k_vv_adj<true><<<g, 256, 0, st>>>(b->Npad, b->A, ax, av, dt, 1);
+  else k_vv_adj<false><<<g, 256, 0, st>>>(b->Npad, b->A, ax, av, dt, 1);
+  b->launches++;
+  // (2) at x_t: ax = ubar + c J(x_t)^T vh, av = vh
+  r = prologue(b, s, st, false);
+  if (r != TS_OK) return r;
+  relist(b, st, false);
+  if (b->f64) k_import_grad<true><<<g, 256, 0, st>>>(b->Npad, b->A, av, 0.5 * dt);
+  else k_import_grad<false><<<g, 256, 0, st>>>(b->Npad, b->A, av, 0.5 * dt);
+  b->launches++;
+  backward_core(b, st, nullptr, nullptr, gParams, 1);
+  if (b->f64) k_vv_adj<true><<<g, 256, 0, st>>>(b->Npad, b->A, ax, av, dt, 2);
+  else k_vv_adj<false><<<g, 256, 0, st>>>(b->Npad, b->A, ax, av, dt, 2);
+  b->launches++;
+  return cuda_ok(b, cudaGetLastError(), "ts_vv_adjoint_step") ? TS_OK : TS_ERR_CUDA;
+}

@@ -7,4 +7,5 @@
 #include "ts_run.cu"
 #include "ts_api.cu"
 #include "ts_fire.cu"
+#include "ts_adjoint.cu"
 #include "ts_pending.cu"

@@ -153,6 +153,35 @@ extern "C" ts_status ts_batch_create(const ts_batch_config* cfg, const ts_potent
   return TS_OK;
 }
 
+extern "C" ts_status ts_batch_set_potentials(ts_batch* b, const ts_potential* pots, int n_pots) {
+  if (!b || !pots || n_pots != b->n_pots) return TS_ERR_INVALID_ARG;
+  for (int q = 0; q < n_pots; q++) {
+    const ts_potential& P = pots[q];
+    const ts_potential& O = b->pots[q];
+    if (P.kind != O.kind || P.shift != O.shift || P.cutoff != O.cutoff || P.skin != O.skin ||
+        (P.kind == TS_SOFT_SPHERE && P.p[0] != O.p[0]))
+      return fail(b, TS_ERR_INVALID_ARG, "only the parameters p may change (and not the soft-sphere sigma)");
+  }
+  for (int q = 0; q < n_pots; q++) {
+    const ts_potential& P = pots[q];
+    DevPot& D = b->dp_host[q];
+    for (int c = 0; c < 3; c++) { D.pd[c] = P.p[c]; D.pf[c] = (float)P.p[c]; }
+    double rc = b->rc[q], phic = 0;
+    if (P.shift && P.kind == TS_LJ) { double s = P.p[0] / rc, s6 = s * s * s * s * s * s; phic = 4 * P.p[1] * (s6 * s6 - s6); }
+    if (P.shift && P.kind == TS_MORSE) { double e = exp(-P.p[1] * (rc - P.p[2])); phic = P.p[0] * (e * e - 2 * e); }
+    D.phicd = phic; D.phicf = (float)phic;
+    b->pots[q] = P;
+  }
+  cudaSetDevice(b->cfg.device);
+  if (!cuda_ok(b, cudaMemcpy(b->d_pots, b->dp_host.data(), sizeof(DevPot) * kMaxPots, cudaMemcpyHostToDevice), "pots"))
+    return TS_ERR_CUDA;
+  if (b->topo_valid) {   // forces at the current positions are stale for every system
+    std::vector<int32_t> ones(b->B, 1);
+    if (!cuda_ok(b, cudaMemcpy(b->S.dirty, ones.data(), 4 * b->B, cudaMemcpyHostToDevice), "dirty")) return TS_ERR_CUDA;
+  }
+  return TS_OK;
+}
+
 extern "C" ts_status ts_batch_destroy(ts_batch* b) {
   if (!b) return TS_ERR_INVALID_ARG;
   cudaSetDevice(b->cfg.device);

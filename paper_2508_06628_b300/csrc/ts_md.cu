@@ -41,10 +41,13 @@ __device__ __forceinline__ void normals3(uint64_t step, uint32_t la, uint32_t se
     z[0] = R0 * cs; z[1] = R0 * sn;
     z[2] = R1 * cos(two_pi * u3);
   } else {
-    float u0 = ((float)(c[0] >> 8) + 0.5f) * 5.9604644775390625e-08f;
-    float u1 = ((float)(c[1] >> 8) + 0.5f) * 5.9604644775390625e-08f;
-    float u2 = ((float)(c[2] >> 8) + 0.5f) * 5.9604644775390625e-08f;
-    float u3 = ((float)(c[3] >> 8) + 0.5f) * 5.9604644775390625e-08f;
+    // u = (c + 1/2) 2^-32 as in FP64; small words convert exactly, so the
+    // logarithm's tail matches the FP64 draw to FP32 rounding
+    const float s32 = 2.3283064365386962890625e-10f, h32 = 1.16415321826934814453125e-10f;
+    float u0 = fminf(fmaf((float)c[0], s32, h32), 0.99999994f);
+    float u1 = fmaf((float)c[1], s32, h32);
+    float u2 = fminf(fmaf((float)c[2], s32, h32), 0.99999994f);
+    float u3 = fmaf((float)c[3], s32, h32);
     float R0 = sqrtf(-2.0f * logf(u0)), R1 = sqrtf(-2.0f * logf(u2));
     float sn, cs;
     sincospif(2.0f * u1, &sn, &cs);

@@ -63,11 +63,8 @@ __global__ void __launch_bounds__(128) k_pair(int32_t n_warps, const int32_t* __
     const float4* tab = S.shift + 2 * (int64_t)s * kNCodes;
     float4 xi = A.xh[k], li = A.xl[k];
     float f0 = 0.f, f1 = 0.f, f2 = 0.f, e = 0.f, w0 = 0.f, w1 = 0.f, w2 = 0.f, w3 = 0.f, w4 = 0.f, w5 = 0.f;
-    for (int q = 0; q < nn; q++) {
-      uint32_t ent = __ldg(A.nbr + q * stride + k);
-      int64_t j = seg + (ent & kJMask);
+    auto one = [&](uint32_t ent, float4 xj, float4 lj) {
       int code = (int)(ent >> kJBits);
-      float4 xj = __ldg(A.xh + j), lj = __ldg(A.xl + j);
       // hi parts on the 2^-12 grid: exact; lo parts tiny
       float a0 = xj.x - xi.x, a1 = xj.y - xi.y, a2 = xj.z - xi.z;
       float b0 = lj.x - li.x, b1 = lj.y - li.y, b2 = lj.z - li.z;
@@ -90,6 +87,26 @@ __global__ void __launch_bounds__(128) k_pair(int32_t n_warps, const int32_t* __
           w3 = fmaf(h0, d1, w3); w4 = fmaf(h0, d2, w4); w5 = fmaf(h1, d2, w5);
         }
       }
+    };
+    // four independent gathers in flight per lane (the loop is latency bound
+    // on the neighbour-position loads otherwise); same summation order as a
+    // plain loop, so results do not depend on the unrolling
+    int q = 0;
+    for (; q + 4 <= nn; q += 4) {
+      uint32_t e0 = __ldg(A.nbr + (q + 0) * stride + k), e1 = __ldg(A.nbr + (q + 1) * stride + k);
+      uint32_t e2 = __ldg(A.nbr + (q + 2) * stride + k), e3 = __ldg(A.nbr + (q + 3) * stride + k);
+      const float4* ph = A.xh + seg;
+      const float4* pl = A.xl + seg;
+      float4 x0 = __ldg(ph + (e0 & kJMask)), l0 = __ldg(pl + (e0 & kJMask));
+      float4 x1 = __ldg(ph + (e1 & kJMask)), l1 = __ldg(pl + (e1 & kJMask));
+      float4 x2 = __ldg(ph + (e2 & kJMask)), l2 = __ldg(pl + (e2 & kJMask));
+      float4 x3 = __ldg(ph + (e3 & kJMask)), l3 = __ldg(pl + (e3 & kJMask));
+      one(e0, x0, l0); one(e1, x1, l1); one(e2, x2, l2); one(e3, x3, l3);
+    }
+    for (; q < nn; q++) {
+      uint32_t ent = __ldg(A.nbr + q * stride + k);
+      int64_t j = seg + (ent & kJMask);
+      one(ent, __ldg(A.xh + j), __ldg(A.xl + j));
     }
     if (valid) A.F[k] = make_float4(f0, f1, f2, e);
     if (EW) {

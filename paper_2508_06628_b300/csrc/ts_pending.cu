@@ -1,17 +1,6 @@
 // ts_pending.cu -- entry points still to be written return TS_ERR_UNSUPPORTED.
 #include "ts_api.h"
 using namespace ts;
-extern "C" ts_status ts_pair_forces_backward(ts_batch* b, ts_state*, const double*, const double*, const double*,
-                                             double*, double*, int, void*) {
-  return fail(b, TS_ERR_UNSUPPORTED, "not built");
-}
-extern "C" ts_status ts_rdf(ts_batch* b, ts_state*, double, int, double*, void*) { return fail(b, TS_ERR_UNSUPPORTED, "not built"); }
-extern "C" ts_status ts_rdf_backward(ts_batch* b, ts_state*, double, int, const double*, double*, void*) {
-  return fail(b, TS_ERR_UNSUPPORTED, "not built");
-}
-extern "C" ts_status ts_vv_adjoint_step(ts_batch* b, ts_state*, const double*, double, double*, double*, double*, void*) {
-  return fail(b, TS_ERR_UNSUPPORTED, "not built");
-}
 extern "C" ts_status ts_batch_compact_admit(ts_batch* b, const ts_state*, const uint8_t*, const ts_host_systems*,
                                             ts_state*, const ts_fire_state*, const double*, ts_fire_state*, double*,
                                             const ts_fire_params*, void*) {

@@ -1,0 +1,135 @@
+"""Differentiable simulation on top of libts.so (TorchSim, arXiv 2508.06628,
+Sec. 2: backpropagating an observable of a whole trajectory, a radial
+distribution function, to the potential parameters).
+
+Orchestration only: forces, their adjoint, the smeared RDF and its gradient,
+the MD steps and the reverse velocity-Verlet steps all run in the library's
+CUDA kernels.  The loss itself (an MSE on a 200-bin histogram) is the user's
+and is computed here with torch on the host-side tensors.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import ts
+
+
+def _torch():
+    return ts._torch()
+
+
+class PairForces:
+    """``F, E, stress = PairForces.apply(pos, params, batch, state)``.
+
+    pos [N,3] f64 and params [n_pots,3] f64 are differentiable; backward
+    calls ts_pair_forces_backward (gradients through F, E and stress)."""
+
+    @staticmethod
+    def _fn():
+        torch = _torch()
+
+        class _PF(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, pos, params, batch, state):
+                set_params(batch, params)
+                state.pos = pos.detach().contiguous()
+                N, B = state.n_atoms, state.n_systems
+                F = torch.zeros((N, 3), dtype=torch.float64, device=pos.device)
+                E = torch.zeros(B, dtype=torch.float64, device=pos.device)
+                S = torch.zeros((B, 3, 3), dtype=torch.float64, device=pos.device)
+                batch.pair_forces(state, F, E, S)
+                ctx.batch, ctx.state = batch, state
+                ctx.save_for_backward(state.pos, params)
+                return F, E, S
+
+            @staticmethod
+            def backward(ctx, gF, gE, gS):
+                pos, params = ctx.saved_tensors
+                b, s = ctx.batch, ctx.state
+                s.pos = pos
+                set_params(b, params)
+                gF = torch.zeros_like(pos) if gF is None else gF.contiguous()
+                gPos = torch.zeros_like(pos)
+                gPar = torch.zeros_like(params)
+                b.pair_forces_backward(s, gF, None if gE is None else gE.contiguous(),
+                                       None if gS is None else gS.contiguous(), gPos, gPar)
+                return gPos, gPar, None, None
+
+        return _PF
+
+    @classmethod
+    def apply(cls, pos, params, batch, state):
+        return cls._fn().apply(pos, params, batch, state)
+
+
+def set_params(batch, params):
+    """Push parameters [n_pots,3] (tensor or array) into the batch's potentials."""
+    p = params.detach().cpu().numpy() if hasattr(params, "detach") else np.asarray(params)
+    pots = [dict(d, p=tuple(float(v) for v in p[k])) for k, d in enumerate(batch.pots)]
+    arr = ts.potentials(pots)
+    st = ts.lib().ts_batch_set_potentials(batch.h, arr, len(pots))
+    batch._check(st, "ts_batch_set_potentials")
+    batch.pots = pots
+
+
+def trajectory_rdf(batch, state, dt, T, every, rmax, K, checkpoint=None, store=False):
+    """NVE velocity Verlet for T steps from ``state`` (not modified); smeared
+    RDF averaged over systems and the frames t = every, 2 every, ..., T.
+    Returns (g [K] tensor, checkpoints list of (t, x, v))."""
+    torch = _torch()
+    checkpoint = checkpoint or every
+    x = state.pos.clone()
+    v = state.vel.clone()
+    s = ts.DeviceState(x, v, state.mass, state.cell, state.pbc, state.system_idx, state.pot_idx, state.uid)
+    g = torch.zeros(K, dtype=torch.float64, device=x.device)
+    gs = torch.zeros((state.n_systems, K), dtype=torch.float64, device=x.device)
+    ckpts = [(0, x.clone(), v.clone())] if store else []
+    nfr = T // every
+    t = 0
+    while t < T:
+        nxt = min(T, (t // every + 1) * every, (t // checkpoint + 1) * checkpoint)
+        batch.md_step(s, nxt - t, dt, kind=ts.TS_NVE)
+        t = nxt
+        if t % every == 0:
+            batch.rdf(s, rmax, K, gs)
+            g += gs.sum(0) / (state.n_systems * nfr)
+        if store and t % checkpoint == 0 and t < T:
+            ckpts.append((t, s.pos.clone(), s.vel.clone()))
+    return g, ckpts
+
+
+def rdf_loss_and_grad(batch, state, dt, T, every, rmax, K, target, checkpoint=100):
+    """Loss = (1/K) sum_k (g_k - target_k)^2 of the trajectory-averaged smeared
+    RDF, and d loss / d params [n_pots,3] by the discrete adjoint of velocity
+    Verlet with checkpoints every ``checkpoint`` steps (segments recomputed
+    forward, then reversed step by step)."""
+    torch = _torch()
+    g, ckpts = trajectory_rdf(batch, state, dt, T, every, rmax, K, checkpoint, store=True)
+    target = torch.as_tensor(target, dtype=torch.float64, device=g.device)
+    loss = float(((g - target) ** 2).mean())
+    nfr = T // every
+    gg = (2.0 * (g - target) / K / (state.n_systems * nfr)).expand(state.n_systems, K).contiguous()
+    N = state.n_atoms
+    ax = torch.zeros((N, 3), dtype=torch.float64, device=g.device)
+    av = torch.zeros_like(ax)
+    gth = torch.zeros((len(batch.pots), 3), dtype=torch.float64, device=g.device)
+    bounds = [c[0] for c in ckpts] + [T]
+    for seg in range(len(ckpts) - 1, -1, -1):
+        t0, x0, v0 = ckpts[seg]
+        t1 = bounds[seg + 1]
+        xs = [x0.clone()]
+        s = ts.DeviceState(x0.clone(), v0.clone(), state.mass, state.cell, state.pbc, state.system_idx,
+                           state.pot_idx, state.uid)
+        for t in range(t0, t1):
+            batch.md_step(s, 1, dt, kind=ts.TS_NVE)
+            xs.append(s.pos.clone())
+        for t in range(t1 - 1, t0 - 1, -1):
+            xn = xs[t + 1 - t0]
+            if (t + 1) % every == 0:
+                sn = ts.DeviceState(xn, None, state.mass, state.cell, state.pbc, state.system_idx, state.pot_idx,
+                                    state.uid)
+                batch.rdf_backward(sn, rmax, K, gg, ax)
+            st = ts.DeviceState(xs[t - t0], None, state.mass, state.cell, state.pbc, state.system_idx,
+                                state.pot_idx, state.uid)
+            batch.vv_adjoint_step(st, xn, dt, ax, av, gth)
+    return loss, g, gth

@@ -1,0 +1,112 @@
+"""GPU parity of the differentiable path: pair-force adjoint, smeared RDF and
+its gradient, and the trajectory gradient through velocity Verlet."""
+import numpy as np
+import pytest
+
+from paper_2508_06628_b300 import workloads as W
+from tests.gpu_util import make_batch, small_mix, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_pair_backward_matches_oracle(orc, precision):
+    torch = torch_cuda()
+    from paper_2508_06628_b300 import ts
+    hb = small_mix(71, n_systems=6, lo=32, hi=300)
+    b = make_batch(hb, precision)
+    s = ts.DeviceState.from_host(hb)
+    b.neighbor_build(s, force=True)
+    rng = np.random.default_rng(0)
+    gF = rng.normal(size=(hb.n_atoms, 3))
+    gE = rng.normal(size=hb.n_systems)
+    gS = rng.normal(size=(hb.n_systems, 3, 3))
+    t = lambda a: torch.as_tensor(a, dtype=torch.float64, device="cuda").contiguous()
+    gx = torch.zeros((hb.n_atoms, 3), dtype=torch.float64, device="cuda")
+    gp = torch.zeros((len(hb.pots), 3), dtype=torch.float64, device="cuda")
+    b.pair_forces_backward(s, t(gF), t(gE), t(gS), gx, gp)
+    b.poll()
+    pos = s.pos.cpu().numpy()
+    gxr, gpr = orc.forces_backward(hb.offsets, pos, hb.cell, hb.pbc, hb.pot_idx, hb.pots, gF, gE, gS)
+    gx, gp = gx.cpu().numpy(), gp.cpu().numpy()
+    rel = 1e-9 if precision == 1 else 1e-4
+    scale = np.abs(gxr).max()
+    assert np.abs(gx - gxr).max() <= rel * scale
+    assert np.all(np.abs(gp - gpr) <= rel * np.abs(gpr) + rel * 1e-2 * np.abs(gpr).max())
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_rdf_and_its_gradient(orc, precision):
+    torch = torch_cuda()
+    from paper_2508_06628_b300 import ts
+    hb = W.lj_liquid(seed=2, n_systems=3, reps=(3, 3, 3), rattle=0.12)
+    pots = [dict(hb.pots[0], skin=0.3)]
+    b = ts.Batch(pots, hb.n_atoms, hb.n_systems, precision=precision)
+    s = ts.DeviceState.from_host(hb)
+    K, rmax = 200, 2.5
+    g = torch.zeros((hb.n_systems, K), dtype=torch.float64, device="cuda")
+    b.neighbor_build(s, force=True)
+    b.rdf(s, rmax, K, g)
+    gg = np.random.default_rng(1).normal(size=(hb.n_systems, K))
+    gx = torch.zeros((hb.n_atoms, 3), dtype=torch.float64, device="cuda")
+    b.rdf_backward(s, rmax, K, torch.as_tensor(gg, device="cuda"), gx)
+    b.poll()
+    pos = s.pos.cpu().numpy()
+    gr, gxr = orc.rdf(hb.offsets, pos, hb.cell, hb.pbc, rmax, K=K, gg=gg)
+    rel = 1e-5 if precision == 0 else 1e-9
+    assert np.abs(g.cpu().numpy() - gr).max() <= rel * np.abs(gr).max() + 1e-12
+    assert np.abs(gx.cpu().numpy() - gxr).max() <= (1e-4 if precision == 0 else 1e-8) * np.abs(gxr).max()
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_trajectory_gradient_matches_oracle(orc, precision):
+    """d loss / d (sigma, eps) through 60 NVE steps with frames and
+    checkpoints every 20 steps: GPU adjoint (checkpointed, recomputed) vs the
+    oracle's stored-trajectory adjoint."""
+    torch = torch_cuda()
+    from paper_2508_06628_b300 import grad, ts
+    hb = W.lj_liquid(seed=3, n_systems=2, reps=(2, 2, 3), rattle=0.08, kT=0.5)
+    pot = dict(W.LJ_REDUCED)
+    K, rmax, T, every, dt = 50, 2.5, 60, 20, 0.005
+    _, target, _ = orc.traj_rdf_loss(hb.offsets, hb.pos, hb.vel, hb.mass, hb.cell, hb.pbc, dict(pot, p=(1.05, 1.0, 0.0)),
+                                     dt, T, every, rmax, K, np.zeros(K), grad=False)
+    lr, gr, gthr = orc.traj_rdf_loss(hb.offsets, hb.pos, hb.vel, hb.mass, hb.cell, hb.pbc, pot, dt, T, every, rmax, K,
+                                     target)
+    b = ts.Batch([dict(pot, skin=0.4)], hb.n_atoms, hb.n_systems, precision=precision)
+    s = ts.DeviceState.from_host(hb)
+    b.neighbor_build(s, force=True)
+    loss, g, gth = grad.rdf_loss_and_grad(b, s, dt, T, every, rmax, K, target, checkpoint=20)
+    b.poll()
+    gth = gth.cpu().numpy()[0]
+    rel = 1e-7 if precision == 1 else 1e-4
+    assert loss == pytest.approx(lr, rel=rel * 10)
+    assert np.abs(g.cpu().numpy() - gr).max() <= rel * 10 * np.abs(gr).max()
+    for q in (0, 1):
+        assert gth[q] == pytest.approx(gthr[q], rel=rel)
+
+
+def test_pair_forces_autograd_function(orc):
+    """torch.autograd through PairForces: d(sum w.F)/dx and /dparams equal the
+    ABI adjoint, and a finite difference of the energy in eps."""
+    torch = torch_cuda()
+    from paper_2508_06628_b300 import grad, ts
+    hb = small_mix(81, n_systems=3, lo=32, hi=128)
+    b = make_batch(hb, 1)
+    s = ts.DeviceState.from_host(hb)
+    b.neighbor_build(s, force=True)
+    pos = s.pos.clone().requires_grad_(True)
+    params = torch.tensor([list(p["p"]) for p in hb.pots], dtype=torch.float64, device="cuda", requires_grad=True)
+    F, E, S = grad.PairForces.apply(pos, params, b, s)
+    E.sum().backward()
+    # dE/dx = -F
+    assert torch.allclose(pos.grad, -F.detach(), atol=1e-10)
+    # dE/deps of the LJ potential by central differences
+    h = 1e-6
+    Es = []
+    for sgn in (1, -1):
+        p2 = params.detach().clone()
+        p2[0, 1] += sgn * h * p2[0, 1]
+        _, E2, _ = grad.PairForces.apply(s.pos.clone(), p2, b, s)
+        Es.append(E2.sum().item())
+    fd = (Es[0] - Es[1]) / (2 * h * params[0, 1].item())
+    assert params.grad[0, 1].item() == pytest.approx(fd, rel=1e-6)
