@@ -12,6 +12,8 @@
 //              + 1/(2V) sum (dphi'/dp)/r (d.gS.d)
 // Each atom gathers gF of its neighbours (full list), so no scatter atomics;
 // parameter gradients go warp -> system -> potential in a fixed order.
+#include <type_traits>
+
 #include "ts_kernels.cuh"
 
 namespace ts {
@@ -183,30 +185,32 @@ __global__ void k_gparam_pot(int32_t B, int32_t n_pots, SysArrays S, const doubl
 // g_k = V/(N(N-1)) sum_{ordered pairs, r < rmax + 4D} exp(-(r-r_k)^2/2D^2) / (sqrt(2 pi) D 4 pi r_k^2)
 // Pairs add their Gaussian (|r - r_k| <= 8 D) into a per-warp shared
 // histogram; warps add into the system's FP64 row.
+template <bool F64>
 __global__ void k_rdf(int32_t n_warps, const int32_t* __restrict__ warp_sys, SysArrays S, SlotArrays A,
-                      int64_t stride, int f64, double rmax, int K, double* g) {
-  extern __shared__ float hist[];
+                      int64_t stride, double rmax, int K, double* g) {
+  using T = typename std::conditional<F64, double, float>::type;
+  extern __shared__ __align__(8) unsigned char hist_raw[];
   int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int w = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
-  float* hs = hist + wib * K;
-  for (int q = lane; q < K; q += 32) hs[q] = 0.f;
+  T* hs = reinterpret_cast<T*>(hist_raw) + wib * K;
+  for (int q = lane; q < K; q += 32) hs[q] = T(0);
   __syncwarp();
   if (w >= n_warps) return;
   int s = warp_sys[w];
   int64_t k = (int64_t)w * kWarp + lane;
   int nn = A.perm[k] >= 0 ? A.nn[k] : 0;
   int64_t seg = S.seg_start[s];
-  float D = (float)(rmax / K), cut2 = (float)((rmax + 4 * rmax / K) * (rmax + 4 * rmax / K));
+  T D = (T)(rmax / K), cut2 = (T)((rmax + 4 * rmax / K) * (rmax + 4 * rmax / K));
   for (int q = 0; q < nn; q++) {
     uint32_t ent = A.nbr[q * stride + k];
     int64_t j = seg + (ent & kJMask);
     int code = (int)(ent >> kJBits);
-    float r2;
-    if (f64) {
+    T r2;
+    if constexpr (F64) {
       const double* sh = S.shiftd + 3 * ((int64_t)s * kNCodes + code);
       double d0 = A.xd[3 * j] - A.xd[3 * k] + sh[0], d1 = A.xd[3 * j + 1] - A.xd[3 * k + 1] + sh[1],
              d2 = A.xd[3 * j + 2] - A.xd[3 * k + 2] + sh[2];
-      r2 = (float)(d0 * d0 + d1 * d1 + d2 * d2);
+      r2 = d0 * d0 + d1 * d1 + d2 * d2;
     } else {
       int64_t t = (int64_t)s * kNCodes + code;
       float4 a = A.xh[j], b = A.xl[j], ia = A.xh[k], ib = A.xl[k], sh = S.shift[2 * t], sl = S.shift[2 * t + 1];
@@ -215,17 +219,17 @@ __global__ void k_rdf(int32_t n_warps, const int32_t* __restrict__ warp_sys, Sys
       r2 = d0 * d0 + d1 * d1 + d2 * d2;
     }
     if (!(r2 < cut2)) continue;
-    float r = sqrtf(r2);
+    T r = sqrt(r2);
     int c = (int)(r / D);
     for (int b = c - 8; b <= c + 8; b++) {
       if (b < 0 || b >= K) continue;
-      float rk = (b + 0.5f) * D, t = (r - rk) / D;
-      atomicAdd(&hs[b], __expf(-0.5f * t * t) / (rk * rk));
+      T rk = (b + T(0.5)) * D, t = (r - rk) / D;
+      atomicAdd(&hs[b], exp(T(-0.5) * t * t) / (rk * rk));
     }
   }
   __syncwarp();
   for (int q = lane; q < K; q += 32)
-    if (hs[q] != 0.f) atomicAdd(&g[(int64_t)s * K + q], (double)hs[q]);
+    if (hs[q] != T(0)) atomicAdd(&g[(int64_t)s * K + q], (double)hs[q]);
 }
 
 __global__ void k_rdf_norm(int32_t B, SysArrays S, double rmax, int K, double* g) {
@@ -380,10 +384,11 @@ extern "C" ts_status ts_rdf(ts_batch* b, ts_state* s, double rmax, int K, double
   relist(b, st, false);
   if (!cuda_ok(b, cudaMemsetAsync(g, 0, sizeof(double) * K * (size_t)b->B, st), "memset")) return TS_ERR_CUDA;
   int threads = 128;
-  size_t shm = sizeof(float) * K * (threads / 32);
+  size_t shm = (b->f64 ? sizeof(double) : sizeof(float)) * K * (threads / 32);
   if (shm > 48 * 1024) return fail(b, TS_ERR_INVALID_ARG, "K too large");
-  k_rdf<<<(int)(((int64_t)b->nwarps * 32 + threads - 1) / threads), threads, shm, st>>>(b->nwarps, b->d_warp_sys, b->S,
-                                                                                      b->A, b->Ncap, b->f64, rmax, K, g);
+  int blocks = (int)(((int64_t)b->nwarps * 32 + threads - 1) / threads);
+  if (b->f64) k_rdf<true><<<blocks, threads, shm, st>>>(b->nwarps, b->d_warp_sys, b->S, b->A, b->Ncap, rmax, K, g);
+  else k_rdf<false><<<blocks, threads, shm, st>>>(b->nwarps, b->d_warp_sys, b->S, b->A, b->Ncap, rmax, K, g);
   k_rdf_norm<<<(int)(((int64_t)b->B * K + 255) / 256), 256, 0, st>>>(b->B, b->S, rmax, K, g);
   b->launches += 2;
   export_state(b, st, s->pos, nullptr);

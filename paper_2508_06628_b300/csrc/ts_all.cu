@@ -8,4 +8,8 @@
 #include "ts_api.cu"
 #include "ts_fire.cu"
 #include "ts_adjoint.cu"
-#include "ts_pending.cu"
+#include "ts_inflight.cu"
+#include "ts_tune.cu"
+#if __has_include("ts_noalloc.cu")
+#include "ts_noalloc.cu"
+#endif

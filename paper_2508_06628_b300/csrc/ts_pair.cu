@@ -14,7 +14,7 @@
 namespace ts {
 
 template <bool F64, bool EW>
-__global__ void __launch_bounds__(128) k_pair(int32_t n_warps, const int32_t* __restrict__ warp_sys, SysArrays S,
+__global__ void __launch_bounds__(256) k_pair(int32_t n_warps, const int32_t* __restrict__ warp_sys, SysArrays S,
                                               SlotArrays A, const DevPot* __restrict__ pots, int64_t stride,
                                               int only_dirty, double* __restrict__ partial) {
   int w = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
