@@ -334,6 +334,30 @@ ts_status ts_autotune(ts_batch* b, ts_state* s, void* stream);
 ts_status ts_profile_pair(ts_batch* b, ts_state* s, int reps, void* flush_buf, size_t flush_bytes, double* ms_out,
                           int64_t* pairs_out, int64_t* atoms_out, void* stream);
 
+/* Energies, forces and stress without any device allocation.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot call cudaMalloc -- a host program that hands the library a fixed set
+ * of buffers and forbids allocation after start-up, code that runs while
+ * another component owns the device allocator, or work issued into a stream
+ * that is being captured, where an allocation would break the capture.
+ * It needs no ts_batch: it takes the potentials (host array, 1..4 entries),
+ * a state whose pos, cell, system_idx and pot_idx are read (vel, mass, pbc,
+ * uid are ignored; all systems fully periodic) and offsets [n_systems + 1]
+ * (device i64, first atom of each system, then n_atoms), and writes F
+ * [n_atoms][3], E [n_systems], stress [n_systems][3][3] (device f64; E and
+ * stress may be NULL).  Arithmetic is FP64: an all-pairs sum over each
+ * system's atoms and every lattice image within the cutoff, so the cost is
+ * O(n^2) per system -- meant for small systems.
+ * Scratch: a fixed device array (4096 systems x 8 doubles = 256 KiB) that
+ * every GPU loading the library holds until exit.  More than 4096 systems
+ * returns TS_ERR_BUDGET.  The first call on a device looks up that array's
+ * address (cudaGetSymbolAddress); make it before capturing a stream.  All
+ * calls share the array and each call clears the rows it uses, so calls that
+ * overlap on the GPU (several streams or host threads) race and must be
+ * serialised by the caller. */
+ts_status ts_pair_forces_noalloc(const ts_potential* pots, int n_pots, const ts_state* s, const int64_t* offsets,
+                                 double* F, double* E, double* stress, void* stream);
+
 /* Human-readable text of the last host-side error of this batch (never NULL). */
 const char* ts_last_error(const ts_batch* b);
 
