@@ -275,7 +275,7 @@ def cpu_baseline(hb, budget_s=15.0):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=5000)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--inner", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])

@@ -7,7 +7,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 PKG = os.path.dirname(HERE)
 SO = os.path.join(PKG, "libts.so")
 SOURCES = ["ts_all.cu", "ts_sched.cpp"]
-UNITY_PARTS = ["ts_neighbor.cu", "ts_pair.cu", "ts_md.cu", "ts_run.cu", "ts_api.cu", "ts_fire.cu",
+UNITY_PARTS = ["ts_neighbor.cu", "ts_relist_small.cu", "ts_pair.cu", "ts_md.cu", "ts_run.cu", "ts_api.cu", "ts_fire.cu",
                "ts_adjoint.cu", "ts_inflight.cu", "ts_tune.cu", "ts_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]

@@ -2,6 +2,7 @@
 // kernel (template instantiations included) is launched from the unit that
 // defines it.
 #include "ts_neighbor.cu"
+#include "ts_relist_small.cu"
 #include "ts_pair.cu"
 #include "ts_md.cu"
 #include "ts_run.cu"

@@ -109,6 +109,12 @@ extern "C" ts_status ts_batch_create(const ts_batch_config* cfg, const ts_potent
     D.phicd = phic; D.phicf = (float)phic;
     D.skin = P.skin;
     D.rlist = rc + P.skin; D.rlist2d = D.rlist * D.rlist; D.rlist2f = (float)D.rlist2d;
+    {   // re-list hysteresis factor (tuning knob; 1 disables)
+      const char* e = getenv("TS_SOON");
+      double f = e ? atof(e) : 1.0;
+      if (!(f > 0 && f <= 1)) f = 1.0;
+      D.soon2 = f * f;
+    }
     b->rc[q] = rc;
   }
   bool ok = true;
@@ -121,6 +127,7 @@ extern "C" ts_status ts_batch_create(const ts_batch_config* cfg, const ts_potent
        alloc(b, S.uid, B) && alloc(b, S.bin_off, B) && alloc(b, S.bin_cap, B) && alloc(b, S.warp_start, B) &&
        alloc(b, S.warp_end, B) && alloc(b, S.h, 9 * B) && alloc(b, S.hinv, 9 * B) && alloc(b, S.href, 9 * B) &&
        alloc(b, S.nb, 3 * B) && alloc(b, S.reach, 3 * B) && alloc(b, S.relist, B) && alloc(b, S.dirty, B) &&
+       alloc(b, S.soon, B) && alloc(b, S.any, 1) &&
        alloc(b, S.kT, B) && alloc(b, S.shift, 2 * B * kNCodes) && alloc(b, S.shiftd, 3 * B * kNCodes);
   ok = ok && alloc(b, A.perm, N) && alloc(b, A.sys, N) && alloc(b, A.bin, N) && alloc(b, A.nn, N) &&
        alloc(b, A.nbr, (size_t)b->max_nbrs * N) && alloc(b, A.tmp_i0, N) && alloc(b, A.tmp_i1, N) &&
@@ -138,7 +145,8 @@ extern "C" ts_status ts_batch_create(const ts_batch_config* cfg, const ts_potent
        alloc(b, b->d_count, b->Ccap) && alloc(b, b->d_cstart, b->Ccap) &&
        alloc(b, b->d_bsum, (b->Ccap + 1023) / 1024 + 1) && alloc(b, b->d_starts, B + 1) &&
        alloc(b, b->d_Eint, B) && alloc(b, b->d_Wint, 9 * B) && alloc(b, b->d_scal, 32 * B) &&
-       alloc(b, b->d_gparam_part, 4 * b->Wcap) && alloc(b, b->d_gacc, 3 * kMaxPots);
+       alloc(b, b->d_gparam_part, 4 * b->Wcap) && alloc(b, b->d_gacc, 3 * kMaxPots) &&
+       alloc(b, b->d_chunk_sys, b->Wcap) && alloc(b, b->d_chunk_a0, b->Wcap);
   if (ok) ok = cuda_ok(b, cudaMemcpy(b->d_pots, dp, sizeof dp, cudaMemcpyHostToDevice), "copy pots");
   if (ok) ok = cuda_ok(b, cudaMemset(b->d_err, 0, 16), "memset") && cuda_ok(b, cudaMemset(b->d_counters, 0, 32), "memset");
   if (ok) ok = cuda_ok(b, cudaMemset(A.perm, 0xff, sizeof(int32_t) * N), "memset") &&
@@ -146,6 +154,14 @@ extern "C" ts_status ts_batch_create(const ts_batch_config* cfg, const ts_potent
                cuda_ok(b, cudaMemset(A.nn, 0, sizeof(int32_t) * N), "memset") &&
                cuda_ok(b, cudaMemset(b->d_partial, 0, sizeof(double) * kPartialStride * b->Wcap), "memset");
   if (ok) ok = cuda_ok(b, cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming), "event");
+  if (ok) ok = cuda_ok(b, cudaFuncSetAttribute(k_relist_small<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)sizeof(SmallSmem)), "smem attribute") &&
+               cuda_ok(b, cudaFuncSetAttribute(k_relist_small<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)sizeof(SmallSmem)), "smem attribute") &&
+               cuda_ok(b, cudaFuncSetAttribute(k_pair_small<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)(2 * sizeof(float4) * kSmallMax)), "smem attribute") &&
+               cuda_ok(b, cudaFuncSetAttribute(k_pair_small<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)(2 * sizeof(float4) * kSmallMax)), "smem attribute");
   if (!ok) { ts_batch_destroy(b); return TS_ERR_CUDA; }
   b->dp_host.assign(dp, dp + kMaxPots);
   autotune_load(b);
@@ -295,6 +311,18 @@ ts_status derive_topology(ts_batch* b, const ts_state* s, cudaStream_t st) {
   }
   if (slot > b->Ncap || bins > b->Ccap) return fail(b, TS_ERR_BUDGET, "padded layout exceeds capacity");
   b->B = B; b->N = N; b->Npad = slot; b->nwarps = (int32_t)(slot / 32); b->nbins = bins;
+  b->n_large = 0;
+  for (int k = 0; k < B; k++) b->n_large += n[k] > kSmallMax;
+  // 256-atom chunks of the small systems for the shared-memory pair kernel
+  std::vector<int32_t> csys, ca0;
+  b->nmax_small = 0;
+  for (int k = 0; k < B; k++) {
+    if (n[k] > kSmallMax) continue;
+    b->nmax_small = std::max(b->nmax_small, n[k]);
+    for (int a = 0; a < n[k]; a += kPairSmallThreads) { csys.push_back(k); ca0.push_back(a); }
+  }
+  b->n_chunks = (int32_t)csys.size();
+  if (b->n_chunks > b->Wcap) return fail(b, TS_ERR_BUDGET, "chunk table exceeds capacity");
   b->h_caller_off = caller_off; b->h_n = n; b->h_pot = pot; b->h_seg = seg;
   SysArrays& S = b->S;
   bool ok = cuda_ok(b, cudaMemcpyAsync(S.seg_start, seg.data(), 8 * B, cudaMemcpyHostToDevice, st), "h2d") &&
@@ -306,6 +334,9 @@ ts_status derive_topology(ts_batch* b, const ts_state* s, cudaStream_t st) {
             cuda_ok(b, cudaMemcpyAsync(S.warp_start, ws.data(), 4 * B, cudaMemcpyHostToDevice, st), "h2d") &&
             cuda_ok(b, cudaMemcpyAsync(S.warp_end, we.data(), 4 * B, cudaMemcpyHostToDevice, st), "h2d") &&
             cuda_ok(b, cudaMemcpyAsync(b->d_warp_sys, warp_sys.data(), 4 * warp_sys.size(), cudaMemcpyHostToDevice, st), "h2d");
+  if (ok && b->n_chunks > 0)
+    ok = cuda_ok(b, cudaMemcpyAsync(b->d_chunk_sys, csys.data(), 4 * csys.size(), cudaMemcpyHostToDevice, st), "h2d") &&
+         cuda_ok(b, cudaMemcpyAsync(b->d_chunk_a0, ca0.data(), 4 * ca0.size(), cudaMemcpyHostToDevice, st), "h2d");
   if (s->uid) {
     ok = ok && cuda_ok(b, cudaMemcpyAsync(S.uid, s->uid, 4 * B, cudaMemcpyDeviceToDevice, st), "d2d");
   } else {
@@ -322,6 +353,7 @@ ts_status derive_topology(ts_batch* b, const ts_state* s, cudaStream_t st) {
   std::vector<int32_t> ones(B, 1);
   ok = cuda_ok(b, cudaMemcpyAsync(S.relist, ones.data(), 4 * B, cudaMemcpyHostToDevice, st), "h2d") &&
        cuda_ok(b, cudaMemcpyAsync(S.dirty, ones.data(), 4 * B, cudaMemcpyHostToDevice, st), "h2d") &&
+       cuda_ok(b, cudaMemsetAsync(S.soon, 0, 4 * B, st), "memset") && cuda_ok(b, cudaMemsetAsync(S.any, 0, 4, st), "memset") &&
        cuda_ok(b, cudaMemsetAsync(b->d_count, 0, 4 * b->Ccap, st), "memset") &&
        cuda_ok(b, cudaStreamSynchronize(st), "sync");
   if (!ok) return TS_ERR_CUDA;
@@ -368,6 +400,29 @@ ts_status prologue(ts_batch* b, ts_state* s, cudaStream_t st, bool import_vel) {
 // sequence is safe to issue every step (and to capture in a graph).
 void relist(ts_batch* b, cudaStream_t st, bool move_fire) {
   int B = b->B;
+  // systems of up to kSmallMax atoms: bin and sort, one CTA per system
+  if (b->f64)
+    k_relist_small<true><<<B, kSmallThreads, sizeof(SmallSmem), st>>>(B, b->S, b->A, b->Ncap, move_fire, b->d_cstart,
+                                                                       b->d_count, b->d_pots, b->max_nbrs, b->d_err);
+  else
+    k_relist_small<false><<<B, kSmallThreads, sizeof(SmallSmem), st>>>(B, b->S, b->A, b->Ncap, move_fire, b->d_cstart,
+                                                                        b->d_count, b->d_pots, b->max_nbrs, b->d_err);
+  b->launches++;
+  if (b->n_large > 0) relist_large_sort(b, st, move_fire);
+  // Verlet lists of every flagged system, then the flag bookkeeping
+  int wb = (int)(((int64_t)b->nwarps * 32 + 127) / 128);
+  if (b->f64) k_build_list_warp<true><<<wb, 128, 0, st>>>(b->nwarps, b->d_warp_sys, b->S, b->A, b->d_cstart, b->d_count,
+                                                          b->d_pots, b->max_nbrs, b->Ncap, b->d_err);
+  else k_build_list_warp<false><<<wb, 128, 0, st>>>(b->nwarps, b->d_warp_sys, b->S, b->A, b->d_cstart, b->d_count,
+                                                    b->d_pots, b->max_nbrs, b->Ncap, b->d_err);
+  k_after_relist<<<(B + 127) / 128, 128, 0, st>>>(B, b->S, b->d_counters);
+  k_clear_any<<<1, 1, 0, st>>>(b->S);
+  b->launches += 3;
+}
+
+// systems above kSmallMax atoms: global counting sort over all bins
+void relist_large_sort(ts_batch* b, cudaStream_t st, bool move_fire) {
+  int B = b->B;
   int64_t Np = b->Npad, nb = b->nbins;
   int g = grid_for(Np, 256);
   k_zero_bins<<<B, 256, 0, st>>>(B, b->S, b->d_count);
@@ -381,29 +436,36 @@ void relist(ts_batch* b, cudaStream_t st, bool move_fire) {
   if (b->f64) {
     k_final_slot<true><<<g, 256, 0, st>>>(Np, b->S, b->A, b->d_cstart, b->d_count, move_fire);
     k_copy_back<true><<<g, 256, 0, st>>>(Np, b->S, b->A, move_fire);
-    k_build_list<true><<<grid_for(Np, 128), 128, 0, st>>>(Np, b->S, b->A, b->d_cstart, b->d_count, b->d_pots,
-                                                          b->max_nbrs, b->Ncap, b->d_err);
   } else {
     k_final_slot<false><<<g, 256, 0, st>>>(Np, b->S, b->A, b->d_cstart, b->d_count, move_fire);
     k_copy_back<false><<<g, 256, 0, st>>>(Np, b->S, b->A, move_fire);
-    k_build_list<false><<<grid_for(Np, 128), 128, 0, st>>>(Np, b->S, b->A, b->d_cstart, b->d_count, b->d_pots,
-                                                           b->max_nbrs, b->Ncap, b->d_err);
   }
-  k_after_relist<<<(B + 127) / 128, 128, 0, st>>>(B, b->S, b->d_counters);
-  b->launches += 11;
+  b->launches += 9;
 }
 
 void pair(ts_batch* b, cudaStream_t st, bool ew, bool only_dirty) {
   int threads = b->pair_threads;
   int blocks = (int)(((int64_t)b->nwarps * 32 + threads - 1) / threads);
   if (b->f64) {
-    if (ew) k_pair<true, true><<<blocks, threads, 0, st>>>(b->nwarps, b->d_warp_sys, b->S, b->A, b->d_pots, b->Ncap, only_dirty, b->d_partial);
-    else k_pair<true, false><<<blocks, threads, 0, st>>>(b->nwarps, b->d_warp_sys, b->S, b->A, b->d_pots, b->Ncap, only_dirty, b->d_partial);
-  } else {
-    if (ew) k_pair<false, true><<<blocks, threads, 0, st>>>(b->nwarps, b->d_warp_sys, b->S, b->A, b->d_pots, b->Ncap, only_dirty, b->d_partial);
-    else k_pair<false, false><<<blocks, threads, 0, st>>>(b->nwarps, b->d_warp_sys, b->S, b->A, b->d_pots, b->Ncap, only_dirty, b->d_partial);
+    if (ew) k_pair<true, true><<<blocks, threads, 0, st>>>(b->nwarps, b->d_warp_sys, b->S, b->A, b->d_pots, b->Ncap, only_dirty, b->d_partial, 0);
+    else k_pair<true, false><<<blocks, threads, 0, st>>>(b->nwarps, b->d_warp_sys, b->S, b->A, b->d_pots, b->Ncap, only_dirty, b->d_partial, 0);
+    b->launches++;
+    return;
   }
-  b->launches++;
+  // mixed precision: systems up to kSmallMax atoms from shared memory, larger ones gathered through L1
+  bool small = b->use_small_pair && b->n_chunks > 0;
+  if (small) {
+    size_t shm = 2 * sizeof(float4) * (size_t)b->nmax_small;
+    if (ew) k_pair_small<true><<<b->n_chunks, kPairSmallThreads, shm, st>>>(b->n_chunks, b->d_chunk_sys, b->d_chunk_a0, b->S, b->A, b->d_pots, b->Ncap, only_dirty, b->d_partial);
+    else k_pair_small<false><<<b->n_chunks, kPairSmallThreads, shm, st>>>(b->n_chunks, b->d_chunk_sys, b->d_chunk_a0, b->S, b->A, b->d_pots, b->Ncap, only_dirty, b->d_partial);
+    b->launches++;
+  }
+  if (!small || b->n_large > 0) {
+    int sk = small ? 1 : 0;
+    if (ew) k_pair<false, true><<<blocks, threads, 0, st>>>(b->nwarps, b->d_warp_sys, b->S, b->A, b->d_pots, b->Ncap, only_dirty, b->d_partial, sk);
+    else k_pair<false, false><<<blocks, threads, 0, st>>>(b->nwarps, b->d_warp_sys, b->S, b->A, b->d_pots, b->Ncap, only_dirty, b->d_partial, sk);
+    b->launches++;
+  }
 }
 
 void reduce_sys(ts_batch* b, cudaStream_t st, double* E, double* stress, double* KE) {

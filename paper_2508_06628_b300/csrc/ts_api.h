@@ -32,7 +32,10 @@ struct ts_batch {
   int32_t Bcap = 0;
   // topology
   bool topo_valid = false, first_import = true;
-  int32_t B = 0, nwarps = 0;
+  int32_t B = 0, nwarps = 0, n_large = 0, n_chunks = 0, nmax_small = 0;
+  bool use_small_pair = true;
+  int32_t* d_chunk_sys = nullptr;
+  int32_t* d_chunk_a0 = nullptr;
   int64_t N = 0, Npad = 0, nbins = 0;
   std::vector<int64_t> h_caller_off, h_seg;
   std::vector<int32_t> h_n, h_pot;
@@ -76,6 +79,7 @@ ts_status derive_topology(ts_batch* b, const ts_state* s, cudaStream_t st);
 ts_status check_state(ts_batch* b, const ts_state* s, bool need_vel);
 ts_status prologue(ts_batch* b, ts_state* s, cudaStream_t st, bool import_vel);
 void relist(ts_batch* b, cudaStream_t st, bool move_fire);
+void relist_large_sort(ts_batch* b, cudaStream_t st, bool move_fire);
 void pair(ts_batch* b, cudaStream_t st, bool ew, bool only_dirty);
 void reduce_sys(ts_batch* b, cudaStream_t st, double* E, double* stress, double* KE);
 void clear_dirty(ts_batch* b, cudaStream_t st);

@@ -194,14 +194,15 @@ __global__ void k_fire_sys(int32_t B, SysArrays S, ts_fire_state* fs, double* fv
   }
   double se = 0.5 * (pots[S.pot[s]].skin - dh);
   cf[31] = se;
-  if (se <= 0) S.relist[s] = 1;
+  if (se <= 0) { S.relist[s] = 1; S.any[0] = 1; }
   for (int q = 0; q < 9; q++) st.Fd[q] = Fn[q];
   st.nsteps++;
   fs[s] = st;
 }
 
 template <bool F64>
-__global__ void k_fire_update(int64_t Npad, SysArrays S, SlotArrays A, const double* __restrict__ coef) {
+__global__ void k_fire_update(int64_t Npad, SysArrays S, SlotArrays A, const double* __restrict__ coef,
+                              const DevPot* __restrict__ pots) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < Npad; k += (int64_t)gridDim.x * blockDim.x) {
     int p = A.perm[k];
     if (p < 0) continue;
@@ -250,7 +251,8 @@ __global__ void k_fire_update(int64_t Npad, SysArrays S, SlotArrays A, const dou
       dx2 = (double)(e0 * e0 + e1 * e1 + e2 * e2);
     }
     double se = cf[31];
-    if (se <= 0 || dx2 > se * se) S.relist[s] = 1;
+    if (se <= 0 || dx2 > se * se) { S.relist[s] = 1; S.any[0] = 1; }
+    else if (dx2 > pots[S.pot[s]].soon2 * se * se) S.soon[s] = 1;
   }
 }
 
@@ -300,8 +302,8 @@ extern "C" ts_status ts_fire_step(ts_batch* b, ts_state* s, ts_fire_state* fs, d
                                         s->cell, b->d_scal, converged, E, fmax, smax, k == n_steps);
     b->launches += 2;
     if (k == n_steps) break;
-    if (b->f64) k_fire_update<true><<<g, 256, 0, st>>>(b->Npad, b->S, b->A, b->d_scal);
-    else k_fire_update<false><<<g, 256, 0, st>>>(b->Npad, b->S, b->A, b->d_scal);
+    if (b->f64) k_fire_update<true><<<g, 256, 0, st>>>(b->Npad, b->S, b->A, b->d_scal, b->d_pots);
+    else k_fire_update<false><<<g, 256, 0, st>>>(b->Npad, b->S, b->A, b->d_scal, b->d_pots);
     k_geometry<<<(b->B + 127) / 128, 128, 0, st>>>(b->B, b->S, s->cell, s->pbc, b->d_pots, b->d_err);
     k_shift_table<<<(int)(((int64_t)b->B * kNCodes + 255) / 256), 256, 0, st>>>(b->B, b->S);
     b->launches += 3;

@@ -32,6 +32,16 @@ constexpr int kImgSide = 2 * kMaxReach + 1;
 constexpr int kNCodes = kImgSide * kImgSide * kImgSide;   // 729
 constexpr int kCenter = kMaxReach + kImgSide * kMaxReach + kImgSide * kImgSide * kMaxReach;
 constexpr int kMaxPots = 16;
+constexpr int kSmallMax = 2048;           // systems up to this size are sorted by one CTA
+
+// Few bins and few atoms: many images per atom, so the list build splits the
+// candidates of one atom across a warp instead of giving each lane an atom.
+__host__ __device__ inline bool is_tiny(int n_atoms, int nbins) { return nbins <= 8 && n_atoms <= 64; }
+
+// Re-list hysteresis: a system whose atoms moved more than skin/2 must be
+// re-listed; one past soon * skin/2 (soon per potential, 1 = off) is
+// re-listed in the same pass whenever any system must, so re-listings gather
+// into fewer, wider launches.
 constexpr int kPartialStride = 8;         // doubles per warp partial
 
 // error word bits (sticky, OR-ed)
@@ -51,6 +61,7 @@ struct DevPot {
   float rc2f, phicf, rlist2f;
   double pd[3];
   double rc2d, phicd, rlist, rlist2d, skin;
+  double soon2;   // squared hysteresis factor
 };
 
 // Per-system data the device reads (SoA, capacity Bcap).
@@ -72,9 +83,15 @@ struct SysArrays {
   float4* shift;          // [kNCodes][2] (hi xyz, lo xyz) mixed
   double* shiftd;         // [kNCodes][3] fp64
   int32_t* relist;        // per-system re-list flag
+  int32_t* soon;          // atoms past kSoon * skin/2: re-list along with any forced pass
+  int32_t* any;           // [1] some system must re-list in this pass
   int32_t* dirty;         // forces stale for this system
   double* kT;             // per-system kT (MD)
 };
+
+__device__ __forceinline__ bool need_relist(const SysArrays& S, int s) {
+  return S.relist[s] || (S.soon[s] && S.any[0]);
+}
 
 struct SlotArrays {
   float4* xh; float4* xl;     // mixed positions hi/lo (w unused)
@@ -137,23 +154,25 @@ template <typename T> struct PotMath;
 template <> struct PotMath<float> {
   static __device__ __forceinline__ void eval(const DevPot& P, float r2, float& phi, float& fr) {
     if (P.kind == TS_LJ) {
-      float ri2 = __frcp_rn(r2);
+      float ri2 = __fdividef(1.0f, r2);   // ~2 ulp; the LJ terms are well conditioned
       float s2 = P.pf[0] * P.pf[0] * ri2;
       float s6 = s2 * s2 * s2, s12 = s6 * s6;
       phi = 4.0f * P.pf[1] * (s12 - s6);
       fr = -24.0f * P.pf[1] * ri2 * (2.0f * s12 - s6);
     } else if (P.kind == TS_MORSE) {
+      // r correctly rounded: it sets the exponent's argument, where the
+      // stiff Morse force amplifies any error; 1/r only scales the result
       float r = sqrtf(r2);
-      float e = expf(P.pf[1] * (P.pf[2] - r));
+      float e = __expf(P.pf[1] * (P.pf[2] - r));
       phi = P.pf[0] * (e * e - 2.0f * e);
-      fr = 2.0f * P.pf[1] * P.pf[0] * e * (1.0f - e) * __frcp_rn(r);
+      fr = 2.0f * P.pf[1] * P.pf[0] * e * (1.0f - e) * rsqrtf(r2);
     } else {
-      float r = sqrtf(r2);
-      float t = 1.0f - r * __frcp_rn(P.pf[0]);
+      float ri = rsqrtf(r2);
+      float t = 1.0f - r2 * ri / P.pf[0];
       float al = P.pf[2];
       float ta1 = (al == 2.0f) ? t : __powf(t, al - 1.0f);
       phi = P.pf[1] / al * ta1 * t;
-      fr = -P.pf[1] / P.pf[0] * ta1 * __frcp_rn(r);
+      fr = -P.pf[1] / P.pf[0] * ta1 * ri;
     }
   }
   // phi'/r and phi'' (for the adjoint), plus parameter derivatives of phi and phi'

@@ -124,8 +124,9 @@ __global__ void k_md_kick_drift(int64_t Npad, SysArrays S, SlotArrays A, const D
       dy = (double)((xh.y - rh.y) + (xl.y - rl.y));
       dz = (double)((xh.z - rh.z) + (xl.z - rl.z));
     }
-    double sk = 0.5 * pots[S.pot[s]].skin;
-    if (dx * dx + dy * dy + dz * dz > sk * sk) S.relist[s] = 1;
+    double sk = 0.5 * pots[S.pot[s]].skin, d2 = dx * dx + dy * dy + dz * dz;
+    if (d2 > sk * sk) { S.relist[s] = 1; S.any[0] = 1; }
+    else if (d2 > pots[S.pot[s]].soon2 * sk * sk) S.soon[s] = 1;
   }
 }
 

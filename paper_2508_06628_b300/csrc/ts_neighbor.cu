@@ -81,8 +81,9 @@ __global__ void k_import_pos(int64_t Npad, SysArrays S, SlotArrays A, const doub
     }
     if (changed) S.dirty[s] = 1;
     if (check_skin) {
-      double sk = 0.5 * pots[S.pot[s]].skin;
-      if (dx * dx + dy * dy + dz * dz > sk * sk) S.relist[s] = 1;
+      double sk = 0.5 * pots[S.pot[s]].skin, d2 = dx * dx + dy * dy + dz * dz;
+      if (d2 > sk * sk) { S.relist[s] = 1; S.any[0] = 1; }
+      else if (d2 > pots[S.pot[s]].soon2 * sk * sk) S.soon[s] = 1;
     }
   }
 }
@@ -225,7 +226,7 @@ __global__ void k_shift_table(int32_t B, SysArrays S) {
 // --- counting sort by (system, bin) ------------------------------------------
 __global__ void k_zero_bins(int32_t B, SysArrays S, int32_t* count) {
   int s = blockIdx.x;
-  if (s >= B || !S.relist[s]) return;
+  if (s >= B || !need_relist(S, s) || S.n_atoms[s] <= kSmallMax) return;
   int off = S.bin_off[s], cap = S.bin_cap[s];
   for (int k = threadIdx.x; k < cap; k += blockDim.x) count[off + k] = 0;
 }
@@ -237,7 +238,7 @@ __global__ void k_bin_atoms(int64_t Npad, SysArrays S, SlotArrays A, int32_t* co
     int p = A.perm[k];
     if (p < 0) continue;
     int s = A.sys[k];
-    if (!S.relist[s]) continue;
+    if (!need_relist(S, s) || S.n_atoms[s] <= kSmallMax) continue;
     double x[3];
     if constexpr (F64) {
       for (int c = 0; c < 3; c++) x[c] = A.xd[3 * k + c];
@@ -328,7 +329,7 @@ __global__ void k_scatter_ids(int64_t Npad, SysArrays S, SlotArrays A, const int
     int p = A.perm[k];
     if (p < 0) continue;
     int s = A.sys[k];
-    if (!S.relist[s]) continue;
+    if (!need_relist(S, s) || S.n_atoms[s] <= kSmallMax) continue;
     int gb = A.tmp_i0[k];
     A.tmp_i2[bin_slot(S, cstart, s, gb) + A.tmp_i1[k]] = p;
   }
@@ -343,7 +344,7 @@ __global__ void k_final_slot(int64_t Npad, SysArrays S, SlotArrays A, const int3
     int p = A.perm[k];
     if (p < 0) continue;
     int s = A.sys[k];
-    if (!S.relist[s]) continue;
+    if (!need_relist(S, s) || S.n_atoms[s] <= kSmallMax) continue;
     int gb = A.tmp_i0[k];
     int64_t base = bin_slot(S, cstart, s, gb);
     int cnt = count[gb], r = 0;
@@ -370,7 +371,7 @@ template <bool F64>
 __global__ void k_copy_back(int64_t Npad, SysArrays S, SlotArrays A, int move_fire) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < Npad; k += (int64_t)gridDim.x * blockDim.x) {
     int s = A.sys[k];
-    if (s < 0 || !S.relist[s]) continue;
+    if (s < 0 || !need_relist(S, s) || S.n_atoms[s] <= kSmallMax) continue;
     A.perm[k] = A.tmp_i1[k];
     if constexpr (F64) {
       for (int c = 0; c < 3; c++) A.vd[3 * k + c] = A.tmp_d1[3 * k + c];
@@ -391,7 +392,7 @@ __global__ void k_build_list(int64_t Npad, SysArrays S, SlotArrays A, const int3
                              int64_t stride, int32_t* err) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < Npad; k += (int64_t)gridDim.x * blockDim.x) {
     int s = A.sys[k];
-    if (s < 0 || !S.relist[s]) continue;
+    if (s < 0 || !need_relist(S, s) || S.n_atoms[s] <= kSmallMax) continue;
     if (A.perm[k] < 0) continue;
     const DevPot& P = pots[S.pot[s]];
     int nb0 = S.nb[3 * s], nb1 = S.nb[3 * s + 1], nb2 = S.nb[3 * s + 2];
@@ -472,13 +473,17 @@ __global__ void k_build_list(int64_t Npad, SysArrays S, SlotArrays A, const int3
 __global__ void k_after_relist(int32_t B, SysArrays S, int64_t* relist_counter) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= B) return;
-  if (S.relist[s]) {
+  if (need_relist(S, s)) {
     S.dirty[s] = 1;
     S.relist[s] = 0;
+    S.soon[s] = 0;
     for (int q = 0; q < 9; q++) S.href[9 * s + q] = S.h[9 * s + q];
     atomicAdd((unsigned long long*)relist_counter, 1ull);
   }
 }
+
+// end of a re-listing pass: no system is forced any more
+__global__ void k_clear_any(SysArrays S) { S.any[0] = 0; }
 
 // list export in caller order (j as caller index, image n per axis)
 __global__ void k_export_list(int64_t Npad, SysArrays S, SlotArrays A, int32_t max_nbrs, int64_t stride,

@@ -16,12 +16,13 @@ namespace ts {
 template <bool F64, bool EW>
 __global__ void __launch_bounds__(256) k_pair(int32_t n_warps, const int32_t* __restrict__ warp_sys, SysArrays S,
                                               SlotArrays A, const DevPot* __restrict__ pots, int64_t stride,
-                                              int only_dirty, double* __restrict__ partial) {
+                                              int only_dirty, double* __restrict__ partial, int skip_small) {
   int w = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
   int lane = threadIdx.x & 31;
   if (w >= n_warps) return;
   int s = warp_sys[w];
   if (only_dirty && !S.dirty[s]) return;
+  if (skip_small && S.n_atoms[s] <= kSmallMax) return;   // handled by k_pair_small
   int64_t k = (int64_t)w * kWarp + lane;
   const DevPot P = pots[S.pot[s]];
   bool valid = A.perm[k] >= 0;
@@ -88,15 +89,25 @@ __global__ void __launch_bounds__(256) k_pair(int32_t n_warps, const int32_t* __
         }
       }
     };
-    // four independent gathers in flight per lane (the loop is latency bound
-    // on the neighbour-position loads otherwise); same summation order as a
-    // plain loop, so results do not depend on the unrolling
+    // Four independent gathers in flight per lane, and the next four list
+    // entries fetched before this block's gathers: the loop is otherwise
+    // latency bound on the streamed index loads (evict-first, so they do not
+    // push neighbour positions out of L1).  Same summation order as a plain
+    // loop, so results do not depend on the unrolling.
+    const float4* ph = A.xh + seg;
+    const float4* pl = A.xl + seg;
+    const uint32_t* lp = A.nbr + k;
     int q = 0;
+    uint32_t n0 = 0, n1 = 0, n2 = 0, n3 = 0;
+    if (nn >= 4) {
+      n0 = __ldcs(lp); n1 = __ldcs(lp + stride); n2 = __ldcs(lp + 2 * stride); n3 = __ldcs(lp + 3 * stride);
+    }
     for (; q + 4 <= nn; q += 4) {
-      uint32_t e0 = __ldg(A.nbr + (q + 0) * stride + k), e1 = __ldg(A.nbr + (q + 1) * stride + k);
-      uint32_t e2 = __ldg(A.nbr + (q + 2) * stride + k), e3 = __ldg(A.nbr + (q + 3) * stride + k);
-      const float4* ph = A.xh + seg;
-      const float4* pl = A.xl + seg;
+      uint32_t e0 = n0, e1 = n1, e2 = n2, e3 = n3;
+      if (q + 8 <= nn) {
+        const uint32_t* np = lp + (int64_t)(q + 4) * stride;
+        n0 = __ldcs(np); n1 = __ldcs(np + stride); n2 = __ldcs(np + 2 * stride); n3 = __ldcs(np + 3 * stride);
+      }
       float4 x0 = __ldg(ph + (e0 & kJMask)), l0 = __ldg(pl + (e0 & kJMask));
       float4 x1 = __ldg(ph + (e1 & kJMask)), l1 = __ldg(pl + (e1 & kJMask));
       float4 x2 = __ldg(ph + (e2 & kJMask)), l2 = __ldg(pl + (e2 & kJMask));
@@ -116,6 +127,90 @@ __global__ void __launch_bounds__(256) k_pair(int32_t n_warps, const int32_t* __
         double t = warp_sum(v[c]);
         if (lane == 0) partial[(int64_t)w * kPartialStride + c] = t;
       }
+    }
+  }
+}
+
+// Mixed-precision pair kernel for systems of up to kSmallMax atoms: one CTA
+// per 256-atom chunk of a system stages the whole system's positions (hi/lo)
+// in shared memory with coalesced loads, so every neighbour gather is a
+// shared-memory read; list entries stream from global memory (coalesced,
+// evict-first, prefetched one block ahead).  Same arithmetic and summation
+// order as k_pair, so the two kernels give identical results.
+constexpr int kPairSmallThreads = 256;
+
+template <bool EW>
+__global__ void __launch_bounds__(kPairSmallThreads) k_pair_small(
+    int32_t n_chunks, const int32_t* __restrict__ chunk_sys, const int32_t* __restrict__ chunk_a0, SysArrays S,
+    SlotArrays A, const DevPot* __restrict__ pots, int64_t stride, int only_dirty, double* __restrict__ partial) {
+  extern __shared__ __align__(16) float4 spos[];   // [nmax] hi, then [nmax] lo
+  int c = blockIdx.x;
+  if (c >= n_chunks) return;
+  int s = chunk_sys[c];
+  if (only_dirty && !S.dirty[s]) return;
+  const int n = S.n_atoms[s], a0 = chunk_a0[c];
+  const int64_t seg = S.seg_start[s];
+  float4* sh = spos;
+  float4* sl = spos + n;
+  for (int i = threadIdx.x; i < n; i += kPairSmallThreads) { sh[i] = __ldg(A.xh + seg + i); sl[i] = __ldg(A.xl + seg + i); }
+  __syncthreads();
+  const int i = a0 + threadIdx.x, lane = threadIdx.x & 31;
+  const bool valid = i < n;
+  const int64_t k = seg + i;
+  const DevPot P = pots[S.pot[s]];
+  const float4* tab = S.shift + 2 * (int64_t)s * kNCodes;
+  const int nn = valid ? A.nn[k] : 0;
+  float4 xi = valid ? sh[i] : make_float4(0, 0, 0, 0), li = valid ? sl[i] : make_float4(0, 0, 0, 0);
+  float f0 = 0.f, f1 = 0.f, f2 = 0.f, e = 0.f, w0 = 0.f, w1 = 0.f, w2 = 0.f, w3 = 0.f, w4 = 0.f, w5 = 0.f;
+  auto one = [&](uint32_t ent) {
+    int code = (int)(ent >> kJBits);
+    int j = (int)(ent & kJMask);
+    float4 xj = sh[j], lj = sl[j];
+    float a0_ = xj.x - xi.x, a1_ = xj.y - xi.y, a2_ = xj.z - xi.z;
+    float b0 = lj.x - li.x, b1 = lj.y - li.y, b2 = lj.z - li.z;
+    if (code != kCenter) {
+      float4 th = __ldg(tab + 2 * code), tl = __ldg(tab + 2 * code + 1);
+      a0_ += th.x; a1_ += th.y; a2_ += th.z;
+      b0 += tl.x; b1 += tl.y; b2 += tl.z;
+    }
+    float d0 = a0_ + b0, d1 = a1_ + b1, d2 = a2_ + b2;
+    float r2 = fmaf(d0, d0, fmaf(d1, d1, d2 * d2));
+    if (r2 < P.rc2f) {
+      float phi, fr;
+      PotMath<float>::eval(P, r2, phi, fr);
+      f0 = fmaf(fr, d0, f0); f1 = fmaf(fr, d1, f1); f2 = fmaf(fr, d2, f2);
+      if (EW) {
+        e += 0.5f * (phi - P.phicf);
+        float hf = 0.5f * fr;
+        float h0 = hf * d0, h1 = hf * d1;
+        w0 = fmaf(h0, d0, w0); w1 = fmaf(h1, d1, w1); w2 = fmaf(hf * d2, d2, w2);
+        w3 = fmaf(h0, d1, w3); w4 = fmaf(h0, d2, w4); w5 = fmaf(h1, d2, w5);
+      }
+    }
+  };
+  const uint32_t* lp = A.nbr + k;
+  int q = 0;
+  uint32_t n0 = 0, n1 = 0, n2 = 0, n3 = 0;
+  if (nn >= 4) { n0 = __ldcs(lp); n1 = __ldcs(lp + stride); n2 = __ldcs(lp + 2 * stride); n3 = __ldcs(lp + 3 * stride); }
+  for (; q + 4 <= nn; q += 4) {
+    uint32_t e0 = n0, e1 = n1, e2 = n2, e3 = n3;
+    if (q + 8 <= nn) {
+      const uint32_t* np = lp + (int64_t)(q + 4) * stride;
+      n0 = __ldcs(np); n1 = __ldcs(np + stride); n2 = __ldcs(np + 2 * stride); n3 = __ldcs(np + 3 * stride);
+    }
+    one(e0); one(e1); one(e2); one(e3);
+  }
+  for (; q < nn; q++) one(__ldcs(lp + (int64_t)q * stride));
+  if (valid) A.F[k] = make_float4(f0, f1, f2, e);
+  if (EW) {
+    // one FP64 partial per global warp of the system (warps past the padded end do not exist)
+    int wl = (a0 + (threadIdx.x & ~31));
+    int npad = (n + kWarp - 1) / kWarp * kWarp;
+    double v[7] = {(double)e, (double)w0, (double)w1, (double)w2, (double)w3, (double)w4, (double)w5};
+#pragma unroll
+    for (int cc = 0; cc < 7; cc++) {
+      double t = warp_sum(v[cc]);
+      if (lane == 0 && wl < npad) partial[((seg + wl) / kWarp) * kPartialStride + cc] = t;
     }
   }
 }

@@ -1,0 +1,379 @@
+// ts_relist_small.cu -- re-listing in two launches for every flagged system:
+// (A) k_relist_small: one CTA per flagged small system (n <= kSmallMax) bins
+//     and sorts the system in shared memory:
+//   1. wrap positions into the cell (FP64), bin them, count per bin;
+//   2. exclusive scan of the bin counts; provisional scatter; canonical rank
+//      inside each bin (ascending caller index, the same order as the
+//      multi-kernel path of ts_neighbor.cu used for larger systems);
+//   3. move the per-slot state into the new order (the CTA owns the whole
+//      segment, so a barrier separates all reads from all writes) and
+//      publish the bin starts in the layout the multi-kernel path uses.
+// (B) k_build_list_warp: the Verlet list of every flagged system, one warp
+//     per 32 sorted atoms: the warp walks the union of its lanes' stencils,
+//     stages each bin's atoms through shared memory in coalesced chunks of
+//     32, and every lane tests its own atom against each staged candidate
+//     (broadcast reads).  Each lane visits its stencil bins in the same order
+//     as a per-atom loop would, so the list order is canonical.
+#include "ts_kernels.cuh"
+
+namespace ts {
+
+constexpr int kSmallThreads = 512;
+
+struct SmallSmem {
+  int32_t bin_old[kSmallMax];
+  int32_t pid[kSmallMax];   // caller index, old order
+  int32_t start[kSmallMax + 1];
+  int32_t fill[kSmallMax];
+  int32_t tmp[kSmallMax];   // provisional order, then bin of the new slot
+  int32_t warp_tot[kSmallThreads / 32];
+};
+
+// block-wide exclusive scan of n <= kSmallMax counts held in `a` (in place);
+// returns the total
+__device__ int block_exclusive_scan(int32_t* a, int n, int32_t* warp_tot) {
+  constexpr int per = kSmallMax / kSmallThreads;   // 8 entries per thread
+  int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  int base = t * per;
+  int loc[per], sum = 0;
+#pragma unroll
+  for (int q = 0; q < per; q++) { loc[q] = (base + q < n) ? a[base + q] : 0; sum += loc[q]; }
+  int incl = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) { int v = __shfl_up_sync(0xffffffffu, incl, o); if (lane >= o) incl += v; }
+  if (lane == 31) warp_tot[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    int v = lane < kSmallThreads / 32 ? warp_tot[lane] : 0, inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) { int u = __shfl_up_sync(0xffffffffu, inc, o); if (lane >= o) inc += u; }
+    if (lane < kSmallThreads / 32) warp_tot[lane] = inc - v;
+  }
+  __syncthreads();
+  int run = warp_tot[wid] + incl - sum;
+#pragma unroll
+  for (int q = 0; q < per; q++) { if (base + q < n) a[base + q] = run; run += loc[q]; }
+  __syncthreads();
+  int total = 0;
+  if (n > 0) total = a[n - 1] + ((n - 1) / per == t ? loc[(n - 1) % per] : 0);
+  // broadcast the total from the owner of the last entry
+  __shared__ int s_total;
+  if (n > 0 && (n - 1) / per == t) s_total = total;
+  __syncthreads();
+  return n > 0 ? s_total : 0;
+}
+
+template <bool F64>
+__global__ void __launch_bounds__(kSmallThreads, 1)
+k_relist_small(int32_t B, SysArrays S, SlotArrays A, int64_t stride, int move_fire, int32_t* cstart, int32_t* count,
+               const DevPot* __restrict__ pots, int32_t max_nbrs, int32_t* err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SmallSmem& sm = *reinterpret_cast<SmallSmem*>(smem_raw);
+  int s = blockIdx.x;
+  if (s >= B || !need_relist(S, s)) return;
+  int n = S.n_atoms[s];
+  if (n > kSmallMax) return;
+  int t = threadIdx.x;
+  int64_t seg = S.seg_start[s];
+  const double* g = S.hinv + 9 * s;
+  const double* h = S.h + 9 * s;
+  const int nb0 = S.nb[3 * s], nb1 = S.nb[3 * s + 1], nb2 = S.nb[3 * s + 2];
+  int nbins = nb0 * nb1 * nb2;
+  int boff = S.bin_off[s];
+  for (int c = t; c < nbins; c += kSmallThreads) sm.start[c] = 0;
+  __syncthreads();
+  // 1. wrap, bin, count
+  for (int i = t; i < n; i += kSmallThreads) {
+    int64_t k = seg + i;
+    double x[3];
+    if constexpr (F64) {
+      for (int c = 0; c < 3; c++) x[c] = A.xd[3 * k + c];
+    } else {
+      float4 hi = A.xh[k], lo = A.xl[k];
+      x[0] = (double)hi.x + lo.x; x[1] = (double)hi.y + lo.y; x[2] = (double)hi.z + lo.z;
+    }
+    double f[3];
+    int kb[3], nbv[3] = {nb0, nb1, nb2};
+    for (int a = 0; a < 3; a++) {
+      double v = x[0] * g[a] + x[1] * g[3 + a] + x[2] * g[6 + a];
+      v -= floor(v);
+      if (v >= 1.0) v = 0.0;
+      f[a] = v;
+      int q = (int)(v * nbv[a]);
+      kb[a] = q >= nbv[a] ? nbv[a] - 1 : (q < 0 ? 0 : q);
+    }
+    double xw[3];
+    for (int c = 0; c < 3; c++) xw[c] = f[0] * h[c] + f[1] * h[3 + c] + f[2] * h[6 + c];
+    if constexpr (F64) {
+      for (int c = 0; c < 3; c++) A.tmp_d0[3 * k + c] = xw[c];
+    } else {
+      float4 hi, lo;
+      split_pos(xw[0], hi.x, lo.x); split_pos(xw[1], hi.y, lo.y); split_pos(xw[2], hi.z, lo.z);
+      hi.w = 0.f; lo.w = 0.f;
+      A.tmp_f0[k] = hi; A.tmp_f1[k] = lo;
+    }
+    int b = (kb[2] * nb1 + kb[1]) * nb0 + kb[0];
+    sm.bin_old[i] = b;
+    sm.pid[i] = A.perm[k];
+    atomicAdd(&sm.start[b], 1);
+  }
+  __syncthreads();
+  // 2. scan, provisional scatter, canonical rank
+  block_exclusive_scan(sm.start, nbins, sm.warp_tot);
+  if (t == 0) sm.start[nbins] = n;
+  for (int c = t; c < nbins; c += kSmallThreads) sm.fill[c] = 0;
+  __syncthreads();
+  for (int i = t; i < n; i += kSmallThreads) {
+    int b = sm.bin_old[i];
+    sm.tmp[sm.start[b] + atomicAdd(&sm.fill[b], 1)] = i;
+  }
+  __syncthreads();
+  int newslot[kSmallMax / kSmallThreads];
+  int nmine = 0;
+  for (int i = t; i < n; i += kSmallThreads) {
+    int b = sm.bin_old[i], p = sm.pid[i], r = 0;
+    for (int q = sm.start[b]; q < sm.start[b + 1]; q++) r += sm.pid[sm.tmp[q]] < p;
+    newslot[nmine++] = sm.start[b] + r;
+  }
+  __syncthreads();
+  // 3. move state: reads of the old order, then writes of the new order
+  nmine = 0;
+  for (int i = t; i < n; i += kSmallThreads) {
+    int d = newslot[nmine++];
+    int64_t ko = seg + i, kd = seg + d;
+    sm.tmp[d] = sm.bin_old[i];
+    A.tmp_i1[kd] = sm.pid[i];
+    if constexpr (F64) {
+      for (int c = 0; c < 3; c++) A.tmp_d1[3 * kd + c] = A.vd[3 * ko + c];
+      A.tmp_d2[kd] = A.minvd[ko];
+      if (move_fire) for (int c = 0; c < 3; c++) A.tmp_d2[stride + 3 * kd + c] = A.gd0[3 * ko + c];
+    } else {
+      A.tmp_f2[kd] = A.vh[ko];
+      A.tmp_f3[kd] = A.vl[ko];
+      if (move_fire) A.tmp_f0[stride + kd] = A.g0[ko];
+      A.xh[kd] = A.tmp_f0[ko];
+      A.xl[kd] = A.tmp_f1[ko];
+    }
+  }
+  __syncthreads();
+  for (int d = t; d < n; d += kSmallThreads) {
+    int64_t kd = seg + d;
+    A.perm[kd] = A.tmp_i1[kd];
+    A.bin[kd] = boff + sm.tmp[d];
+    if constexpr (F64) {
+      for (int c = 0; c < 3; c++) A.vd[3 * kd + c] = A.tmp_d1[3 * kd + c];
+      A.minvd[kd] = A.tmp_d2[kd];
+      if (move_fire) for (int c = 0; c < 3; c++) A.gd0[3 * kd + c] = A.tmp_d2[stride + 3 * kd + c];
+    } else {
+      A.vh[kd] = A.tmp_f2[kd];
+      A.vl[kd] = A.tmp_f3[kd];
+      if (move_fire) A.g0[kd] = A.tmp_f0[stride + kd];
+    }
+  }
+  if constexpr (F64) {
+    // FP64 positions: new order from the wrapped copy (old-order tmp_d0); the
+    // loop above read no xd, so write them after the barrier
+    __syncthreads();
+    nmine = 0;
+    for (int i = t; i < n; i += kSmallThreads) {
+      int d = newslot[nmine++];
+      for (int c = 0; c < 3; c++) A.xd[3 * (seg + d) + c] = A.tmp_d0[3 * (seg + i) + c];
+    }
+  }
+  // bin starts and counts in the multi-kernel layout: the scan at a
+  // system's first bin equals its caller offset
+  int64_t coff = S.caller_off[s];
+  for (int c = t; c < nbins; c += kSmallThreads) {
+    cstart[boff + c] = (int32_t)(coff + sm.start[c]);
+    count[boff + c] = sm.start[c + 1] - sm.start[c];
+  }
+  if (!is_tiny(n, nbins)) return;
+  // 4. tiny systems (few bins, many images per atom): Verlet list here, one
+  //    warp per atom, lanes splitting the candidates; a ballot and prefix
+  //    count append hits in candidate order, so the list order is the same
+  //    as a sequential loop's
+  __syncthreads();
+  const DevPot& P = pots[S.pot[s]];
+  const int m0 = S.reach[3 * s], m1 = S.reach[3 * s + 1], m2 = S.reach[3 * s + 2];
+  const int lane = t & 31, wid = t >> 5;
+  for (int d = wid; d < n; d += kSmallThreads / 32) {
+    int64_t k = seg + d;
+    int lb = sm.tmp[d];
+    int kx = lb % nb0, ky = (lb / nb0) % nb1, kz = lb / (nb0 * nb1);
+    float4 hi, lo;
+    double xi[3];
+    if constexpr (F64) { for (int c = 0; c < 3; c++) xi[c] = A.xd[3 * k + c]; }
+    else { hi = A.xh[k]; lo = A.xl[k]; }
+    int cnt = 0;
+    for (int dz = -m2; dz <= m2; dz++) {
+      int zz = kz + dz, iz = zz >= 0 ? zz / nb2 : -((-zz + nb2 - 1) / nb2), cz = zz - iz * nb2;
+      for (int dy = -m1; dy <= m1; dy++) {
+        int yy = ky + dy, iy = yy >= 0 ? yy / nb1 : -((-yy + nb1 - 1) / nb1), cy = yy - iy * nb1;
+        for (int dx = -m0; dx <= m0; dx++) {
+          int xx = kx + dx, ix = xx >= 0 ? xx / nb0 : -((-xx + nb0 - 1) / nb0), cx = xx - ix * nb0;
+          int code = img_code(ix, iy, iz);
+          int cb = (cz * nb1 + cy) * nb0 + cx;
+          int q0 = sm.start[cb], q1 = sm.start[cb + 1];
+          int64_t ti = (int64_t)s * kNCodes + code;
+          for (int qb = q0; qb < q1; qb += 32) {
+            int q = qb + lane;
+            bool hit = false;
+            if (q < q1 && !(q == d && code == kCenter)) {
+              if constexpr (F64) {
+                const double* sd = S.shiftd + 3 * ti;
+                double d0 = A.xd[3 * (seg + q)] + sd[0] - xi[0], d1 = A.xd[3 * (seg + q) + 1] + sd[1] - xi[1],
+                       d2 = A.xd[3 * (seg + q) + 2] + sd[2] - xi[2];
+                hit = d0 * d0 + d1 * d1 + d2 * d2 < P.rlist2d;
+              } else {
+                float4 sh = S.shift[2 * ti], sl = S.shift[2 * ti + 1];
+                float4 xj = A.xh[seg + q], lj = A.xl[seg + q];
+                float d0 = (xj.x + (sh.x - hi.x)) + (lj.x + (sl.x - lo.x));
+                float d1 = (xj.y + (sh.y - hi.y)) + (lj.y + (sl.y - lo.y));
+                float d2 = (xj.z + (sh.z - hi.z)) + (lj.z + (sl.z - lo.z));
+                hit = d0 * d0 + d1 * d1 + d2 * d2 < P.rlist2f;
+              }
+            }
+            unsigned bal = __ballot_sync(0xffffffffu, hit);
+            if (hit) {
+              int pos = cnt + __popc(bal & ((1u << lane) - 1u));
+              if (pos < max_nbrs) A.nbr[pos * stride + k] = (uint32_t)q | ((uint32_t)code << kJBits);
+            }
+            cnt += __popc(bal);
+          }
+        }
+      }
+    }
+    if (lane == 0) {
+      if (cnt > max_nbrs) { atomicOr(err, kErrNeighborOverflow); cnt = max_nbrs; }
+      A.nn[k] = cnt;
+      if constexpr (F64) { for (int c = 0; c < 3; c++) A.xrd[3 * k + c] = xi[c]; }
+      else { A.xrh[k] = hi; A.xrl[k] = lo; }
+    }
+  }
+}
+
+__device__ __forceinline__ int floor_div(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+// (B) Verlet list of every flagged system; one warp per 32 sorted atoms.
+template <bool F64>
+__global__ void __launch_bounds__(128) k_build_list_warp(int32_t n_warps, const int32_t* __restrict__ warp_sys,
+                                                         SysArrays S, SlotArrays A, const int32_t* __restrict__ cstart,
+                                                         const int32_t* __restrict__ count,
+                                                         const DevPot* __restrict__ pots, int32_t max_nbrs,
+                                                         int64_t stride, int32_t* err) {
+  __shared__ float4 sh_h[4][32], sh_l[4][32];
+  __shared__ double sh_d[4][32][3];
+  int w = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  if (w >= n_warps) return;
+  int s = warp_sys[w];
+  if (!need_relist(S, s)) return;   // warp-uniform
+  int64_t k = (int64_t)w * kWarp + lane;
+  bool valid = A.perm[k] >= 0;   // lane 0 of a warp is always a real atom
+  const DevPot& P = pots[S.pot[s]];
+  const int nb0 = S.nb[3 * s], nb1 = S.nb[3 * s + 1], nb2 = S.nb[3 * s + 2];
+  if (is_tiny(S.n_atoms[s], nb0 * nb1 * nb2)) return;   // listed by k_relist_small
+  const int m0 = S.reach[3 * s], m1 = S.reach[3 * s + 1], m2 = S.reach[3 * s + 2];
+  int64_t seg = S.seg_start[s];
+  int boff = S.bin_off[s];
+  int lbr = A.bin[k] - boff;                                   // padding lanes: any value
+  int lb = __shfl_sync(0xffffffffu, lbr, valid ? lane : 0);    // ... replaced by lane 0's bin
+  int kx = lb % nb0, ky = (lb / nb0) % nb1, kz = lb / (nb0 * nb1);
+  // union of the lanes' stencils, in unwrapped bin coordinates
+  int x0 = __reduce_min_sync(0xffffffffu, kx) - m0, x1 = __reduce_max_sync(0xffffffffu, kx) + m0;
+  int y0 = __reduce_min_sync(0xffffffffu, ky) - m1, y1 = __reduce_max_sync(0xffffffffu, ky) + m1;
+  int z0 = __reduce_min_sync(0xffffffffu, kz) - m2, z1 = __reduce_max_sync(0xffffffffu, kz) + m2;
+  float4 hi = make_float4(0, 0, 0, 0), lo = hi;
+  double xi[3] = {0, 0, 0};
+  if (valid) {
+    if constexpr (F64) { for (int c = 0; c < 3; c++) xi[c] = A.xd[3 * k + c]; }
+    else { hi = A.xh[k]; lo = A.xl[k]; }
+  }
+  int cnt = 0;
+  const int nx = x1 - x0 + 1, ny = y1 - y0 + 1, ncell = nx * ny * (z1 - z0 + 1);
+  const int64_t coff = S.caller_off[s];
+  // cells in (z, y, x) order, 32 at a time: each lane resolves one cell's
+  // bin start, count, image code and shift, then the warp walks them in order
+  for (int cb = 0; cb < ncell; cb += 32) {
+    int my_start = 0, my_count = 0, my_code = 0;
+    float4 my_sh = make_float4(0, 0, 0, 0), my_sl = my_sh;
+    {
+      int ci = cb + lane;
+      if (ci < ncell) {
+        int cx = x0 + ci % nx, cy = y0 + (ci / nx) % ny, cz = z0 + ci / (nx * ny);
+        int ix = floor_div(cx, nb0), iy = floor_div(cy, nb1), iz = floor_div(cz, nb2);
+        int gb = boff + ((cz - iz * nb2) * nb1 + (cy - iy * nb1)) * nb0 + (cx - ix * nb0);
+        my_code = img_code(ix, iy, iz);
+        my_start = (int)((int64_t)cstart[gb] - coff);
+        my_count = count[gb];
+        if constexpr (!F64) {
+          int64_t ti = (int64_t)s * kNCodes + my_code;
+          my_sh = S.shift[2 * ti];
+          my_sl = S.shift[2 * ti + 1];
+        }
+      }
+    }
+    const int ncb = min(32, ncell - cb);
+    for (int tc = 0; tc < ncb; tc++) {
+      int ci = cb + tc;
+      int cx = x0 + ci % nx, cy = y0 + (ci / nx) % ny, cz = z0 + ci / (nx * ny);
+      bool in = valid && abs(cz - kz) <= m2 && abs(cy - ky) <= m1 && abs(cx - kx) <= m0;
+      int code = __shfl_sync(0xffffffffu, my_code, tc);
+      int64_t b0 = seg + __shfl_sync(0xffffffffu, my_start, tc);
+      int c = __shfl_sync(0xffffffffu, my_count, tc);
+      float a0 = 0, a1 = 0, a2 = 0, e0 = 0, e1 = 0, e2 = 0;
+      double s0 = 0, s1 = 0, s2 = 0;
+      if constexpr (F64) {
+        const double* sd = S.shiftd + 3 * ((int64_t)s * kNCodes + code);
+        s0 = sd[0] - xi[0]; s1 = sd[1] - xi[1]; s2 = sd[2] - xi[2];
+      } else {
+        a0 = __shfl_sync(0xffffffffu, my_sh.x, tc) - hi.x;   // exact (2^-12 grid)
+        a1 = __shfl_sync(0xffffffffu, my_sh.y, tc) - hi.y;
+        a2 = __shfl_sync(0xffffffffu, my_sh.z, tc) - hi.z;
+        e0 = __shfl_sync(0xffffffffu, my_sl.x, tc) - lo.x;
+        e1 = __shfl_sync(0xffffffffu, my_sl.y, tc) - lo.y;
+        e2 = __shfl_sync(0xffffffffu, my_sl.z, tc) - lo.z;
+      }
+      if (!__any_sync(0xffffffffu, in) || c == 0) continue;
+      {
+        for (int base = 0; base < c; base += 32) {
+          int q = base + lane;
+          if (q < c) {
+            if constexpr (F64) { for (int cc = 0; cc < 3; cc++) sh_d[wib][lane][cc] = A.xd[3 * (b0 + q) + cc]; }
+            else { sh_h[wib][lane] = A.xh[b0 + q]; sh_l[wib][lane] = A.xl[b0 + q]; }
+          }
+          __syncwarp();
+          int nc = min(32, c - base);
+          if (in) {
+            for (int tq = 0; tq < nc; tq++) {
+              int64_t j = b0 + base + tq;
+              if (j == k && code == kCenter) continue;
+              bool hit;
+              if constexpr (F64) {
+                double d0 = sh_d[wib][tq][0] + s0, d1 = sh_d[wib][tq][1] + s1, d2 = sh_d[wib][tq][2] + s2;
+                hit = d0 * d0 + d1 * d1 + d2 * d2 < P.rlist2d;
+              } else {
+                float4 xj = sh_h[wib][tq], lj = sh_l[wib][tq];
+                float d0 = (xj.x + a0) + (lj.x + e0), d1 = (xj.y + a1) + (lj.y + e1), d2 = (xj.z + a2) + (lj.z + e2);
+                hit = d0 * d0 + d1 * d1 + d2 * d2 < P.rlist2f;
+              }
+              if (hit) {
+                if (cnt < max_nbrs) A.nbr[cnt * stride + k] = (uint32_t)(j - seg) | ((uint32_t)code << kJBits);
+                cnt++;
+              }
+            }
+          }
+          __syncwarp();
+        }
+      }
+    }
+  }
+  if (valid) {
+    if (cnt > max_nbrs) { atomicOr(err, kErrNeighborOverflow); cnt = max_nbrs; }
+    A.nn[k] = cnt;
+    if constexpr (F64) { for (int c = 0; c < 3; c++) A.xrd[3 * k + c] = xi[c]; }
+    else { A.xrh[k] = hi; A.xrl[k] = lo; }
+  }
+}
+
+}  // namespace ts

@@ -1,0 +1,146 @@
+"""In-flight batched relaxation (TorchSim, arXiv 2508.06628, Sec. 3 and
+Fig. 3): sample systems from a stream until the memory budget is full, run a
+few FIRE steps on the whole batch, retire converged systems and admit new
+ones, until every system has converged.
+
+Orchestration only: admission decisions come from the library's scheduler
+(ts_sched_*), data movement from ts_batch_compact_admit, the relaxation from
+ts_fire_step; the host reads back one flag per system per round.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import ts
+
+FIRE_DEFAULTS = dict(dt0=0.1, dt_max=1.0, finc=1.1, fdec=0.5, alpha0=0.1, falpha=0.99, maxstep=0.2, fmax=1e-3,
+                     smax=1e-4, p_ext=0.0, nmin=5, variable_cell=1)
+
+
+class HostSystems(C.Structure):
+    _fields_ = [("n_systems", C.c_int32), ("n_atoms", C.c_int64), ("pos", C.c_void_p), ("mass", C.c_void_p),
+                ("cell", C.c_void_p), ("n_per_system", C.c_void_p), ("pot_idx", C.c_void_p), ("uid", C.c_void_p)]
+
+
+def fire_params(**kw):
+    p = dict(FIRE_DEFAULTS)
+    p.update(kw)
+    return ts.FireParams(*[p[k] for k in ["dt0", "dt_max", "finc", "fdec", "alpha0", "falpha", "maxstep", "fmax",
+                                          "smax", "p_ext"]], p["nmin"], p["variable_cell"])
+
+
+class _Buffers:
+    """One device state of the batch capacity (ping-pong partner of another)."""
+
+    def __init__(self, torch, dev, atoms, systems):
+        f = lambda *shape, dt=torch.float64: torch.zeros(shape, dtype=dt, device=dev)
+        self.pos, self.vel, self.mass = f(atoms, 3), f(atoms, 3), f(atoms)
+        self.cell, self.pbc = f(systems, 3, 3), f(systems, 3, dt=torch.uint8)
+        self.sidx, self.pot, self.uid = f(atoms, dt=torch.int32), f(systems, dt=torch.int32), f(systems, dt=torch.int32)
+        self.fs = f(systems * ts.FIRE_STATE_BYTES, dt=torch.uint8)
+        self.fvel = f(atoms + 3 * systems, 3)
+        self.n_systems, self.n_atoms = 0, 0
+
+    def state(self):
+        return ts.State(self.n_systems, self.n_atoms, *[C.c_void_p(t.data_ptr()) for t in
+                        (self.pos, self.vel, self.mass, self.cell, self.pbc, self.sidx, self.pot, self.uid)])
+
+    def device_state(self):
+        n, B = self.n_atoms, self.n_systems
+        return ts.DeviceState(self.pos[:n], self.vel[:n], self.mass[:n], self.cell[:B], self.pbc[:B], self.sidx[:n],
+                              self.pot[:B], self.uid[:B])
+
+
+def relax_inflight(hb, pots, max_scaler, max_active=1024, n_inner=25, precision=ts.TS_MIXED, max_rounds=10000,
+                   device=0, on_round=None, **fire_kw):
+    """Relax every system of the host batch ``hb`` (workloads.Batch) with
+    variable-cell FIRE under an atom budget of ``max_scaler`` (memory scales
+    with n_atoms).  Returns a dict per system id with E, fmax, smax, cell and
+    positions at convergence, and the round log."""
+    torch = ts._torch()
+    dev = torch.device("cuda", device)
+    L = ts.lib()
+    L.ts_sched_create.argtypes = [C.c_double, C.c_int32, C.c_void_p]
+    L.ts_sched_push.argtypes = [C.c_void_p, C.c_int64, C.c_double]
+    L.ts_sched_fill.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]
+    L.ts_sched_retire.argtypes = [C.c_void_p, C.c_void_p, C.c_int]
+    L.ts_sched_stats.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    L.ts_sched_destroy.argtypes = [C.c_void_p]
+    L.ts_batch_compact_admit.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                         C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    prm = fire_params(**fire_kw)
+    atoms_cap = int(max_scaler)
+    b = ts.Batch(pots, atoms_cap, max_active, precision=precision, device=device)
+    q = C.c_void_p()
+    assert L.ts_sched_create(float(max_scaler), int(max_active), C.byref(q)) == 0
+    off = hb.offsets
+    n_of = np.diff(off)
+    for i in range(hb.n_systems):
+        st = L.ts_sched_push(q, i, float(n_of[i]))
+        if st != 0:
+            raise ts.TSError(st, f"system {i} ({n_of[i]} atoms) exceeds the budget")
+    bufs = [_Buffers(torch, dev, atoms_cap, max_active), _Buffers(torch, dev, atoms_cap, max_active)]
+    cur = 0
+    ids_active = []
+    results, log = {}, []
+    ids = (C.c_int64 * max_active)()
+    nout = C.c_int()
+    stream = torch.cuda.current_stream(dev)
+    sp = C.c_void_p(stream.cuda_stream)
+    conv = torch.zeros(max_active, dtype=torch.uint8, device=dev)
+    E = torch.zeros(max_active, dtype=torch.float64, device=dev)
+    fm, sm = torch.zeros_like(E), torch.zeros_like(E)
+    keep = np.ones(max_active, np.uint8)
+    for rnd in range(max_rounds):
+        assert L.ts_sched_fill(q, ids, max_active, C.byref(nout)) == 0
+        new = [ids[k] for k in range(nout.value)]
+        src, dst = bufs[cur], bufs[1 - cur]
+        add = None
+        if new:
+            pos = np.ascontiguousarray(np.concatenate([hb.pos[off[i]:off[i + 1]] for i in new]))
+            mass = np.ascontiguousarray(np.concatenate([hb.mass[off[i]:off[i + 1]] for i in new]))
+            cell = np.ascontiguousarray(hb.cell[new])
+            nps = np.ascontiguousarray(n_of[new].astype(np.int32))
+            potidx = np.ascontiguousarray(hb.pot_idx[new].astype(np.int32))
+            uid = np.ascontiguousarray(np.array(new, np.uint32))
+            keepalive = (pos, mass, cell, nps, potidx, uid)
+            add = HostSystems(len(new), int(pos.shape[0]), *[C.c_void_p(a.ctypes.data) for a in keepalive])
+        kmask = np.ascontiguousarray(keep[:src.n_systems])
+        if not new and not any(kmask):
+            break
+        sst = src.state()
+        dstc = dst.state()
+        st = L.ts_batch_compact_admit(b.h, C.byref(sst) if src.n_systems else None,
+                                      C.c_void_p(kmask.ctypes.data) if src.n_systems else None,
+                                      C.byref(add) if add else None, C.byref(dstc),
+                                      C.c_void_p(src.fs.data_ptr()), C.c_void_p(src.fvel.data_ptr()),
+                                      C.c_void_p(dst.fs.data_ptr()), C.c_void_p(dst.fvel.data_ptr()), C.byref(prm), sp)
+        b._check(st, "ts_batch_compact_admit")
+        dst.n_systems, dst.n_atoms = dstc.n_systems, dstc.n_atoms
+        ids_active = [i for i, k in zip(ids_active, kmask) if k] + new
+        cur = 1 - cur
+        buf = bufs[cur]
+        s = buf.device_state()
+        b.fire_step(s, buf.fs, buf.fvel, prm, n_inner, conv, E, fm, sm)
+        c = conv[:buf.n_systems].cpu().numpy().astype(bool)
+        log.append(dict(round=rnd, active=len(ids_active), atoms=buf.n_atoms, admitted=len(new), converged=int(c.sum())))
+        if on_round:
+            on_round(log[-1])
+        done = np.nonzero(c)[0]
+        if len(done):
+            Eh, fmh, smh = E.cpu().numpy(), fm.cpu().numpy(), sm.cpu().numpy()
+            offs = np.concatenate([[0], np.cumsum([n_of[i] for i in ids_active])])
+            posh = buf.pos[:buf.n_atoms].cpu().numpy()
+            cellh = buf.cell[:buf.n_systems].cpu().numpy()
+            for k in done:
+                i = ids_active[k]
+                results[i] = dict(E=Eh[k], fmax=fmh[k], smax=smh[k], cell=cellh[k], pos=posh[offs[k]:offs[k + 1]],
+                                  round=rnd)
+            arr = (C.c_int64 * len(done))(*[ids_active[k] for k in done])
+            assert L.ts_sched_retire(q, arr, len(done)) == 0
+        keep[:buf.n_systems] = (~c).astype(np.uint8)
+    L.ts_sched_destroy(q)
+    b.close()
+    return results, log

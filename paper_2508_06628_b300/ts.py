@@ -274,12 +274,13 @@ class Batch:
 
 
 def default_skins(pots):
-    """Skin per potential: 1.0 A for LJ argon scale, ~0.5 A for Morse Cu, 0.2 sigma for soft spheres,
+    """Skin per potential: 1.0 A for LJ argon scale, 0.5 A for Morse Cu, 0.6 sigma for soft spheres
+    (light, stiff particles whose thermal excursions would otherwise trigger a re-listing every step),
     0.3 sigma for reduced LJ."""
     out = []
     for d in pots:
         if d["kind"] == 2:
-            out.append(0.2 * d["p"][0])
+            out.append(0.6 * d["p"][0])
         elif d["kind"] == 0:
             out.append(0.3 * d["p"][0] if d["p"][0] < 2 else 1.0)
         else:

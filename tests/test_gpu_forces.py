@@ -121,3 +121,38 @@ def test_bad_system_idx_is_rejected():
     with pytest.raises(ts.TSError) as e:
         b.neighbor_build(s, force=True)
     assert e.value.status == ts.TS_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_large_system_path(orc, precision):
+    """A 2304-atom system (multi-kernel re-listing path) next to small ones
+    (fused per-system path): pair sets and forces match the oracle."""
+    rng = np.random.default_rng(8)
+    p, c = W.lattice("fcc", (8, 8, 9), 5.26)
+    c2 = c @ (np.eye(3) + np.array([[0, 0.03, 0], [0.01, 0, 0], [0, 0.02, 0]]))
+    p = p @ np.linalg.solve(c, c2) + rng.normal(0, 0.05, p.shape)
+    big = dict(pos=p, vel=np.zeros_like(p), mass=np.full(len(p), 39.948), cell=c2, pot=0)
+    small = small_mix(17, n_systems=3, lo=32, hi=200)
+    systems = [big] + [dict(pos=small.pos[small.offsets[k]:small.offsets[k + 1]], vel=np.zeros((small.offsets[k + 1] - small.offsets[k], 3)),
+                            mass=small.mass[small.offsets[k]:small.offsets[k + 1]], cell=small.cell[k], pot=int(small.pot_idx[k]))
+                       for k in range(3)]
+    hb = W.concat(systems, small.pots)
+    b, s, F, E, S, pos = run_forces(hb, precision)
+    Er, Fr, Sr = orc.forces(hb.offsets, pos, hb.cell, hb.pbc, hb.pot_idx, hb.pots, use_cells=True)
+    ok, worst, frac = force_tolerance_ok(F, Fr, hb.offsets, precision == 1)
+    assert ok, (worst, frac)
+    assert np.all(np.abs(E - Er) <= (1e-6 if precision == 0 else 1e-9) * np.abs(Er) + 1e-9)
+    # MD steps through both re-listing paths keep the state consistent
+    torch = torch_cuda()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        b.md_step(s, 30, 2.0 / W.T0_FS, kind=0, stream=stream)
+        b.pair_forces(s, None, None, None, stream=stream)
+        b.poll(stream)
+    F2 = torch.zeros((hb.n_atoms, 3), dtype=torch.float64, device="cuda")
+    b.pair_forces(s, F2)
+    b.poll()
+    pos2 = s.pos.cpu().numpy()
+    _, Fr2, _ = orc.forces(hb.offsets, pos2, hb.cell, hb.pbc, hb.pot_idx, hb.pots, use_cells=True)
+    ok, worst, frac = force_tolerance_ok(F2.cpu().numpy(), Fr2, hb.offsets, precision == 1)
+    assert ok, (worst, frac)
