@@ -80,8 +80,8 @@ typedef enum { TS_MIXED = 0, TS_FP64 = 1 } ts_precision;
  * atom_capacity / system_capacity: the largest total atom count and system
  *   count any state passed to this batch may have (in-flight admission
  *   included).  All scratch is allocated at create for these capacities.
- * max_neighbors: per-atom neighbour-list capacity; 0 picks a value from the
- *   potentials' densities (an atom beyond it sets TS_ERR_NEIGHBOR_OVERFLOW).
+ * max_neighbors: per-atom neighbour-list capacity; 0 picks 160
+ *   (an atom beyond it sets TS_ERR_NEIGHBOR_OVERFLOW).
  * memory_budget_bytes: 0 = no limit; otherwise create fails with
  *   TS_ERR_BUDGET if the scratch would exceed it, and in-flight admission
  *   admits systems only while their memory scaler fits (Sec. 3).

@@ -84,7 +84,7 @@ extern "C" ts_status ts_batch_create(const ts_batch_config* cfg, const ts_potent
   b->f64 = cfg->precision == TS_FP64;
   b->n_pots = n_pots;
   for (int q = 0; q < n_pots; q++) b->pots[q] = pots[q];
-  b->max_nbrs = cfg->max_neighbors > 0 ? cfg->max_neighbors : 128;
+  b->max_nbrs = cfg->max_neighbors > 0 ? cfg->max_neighbors : 160;
   b->Bcap = cfg->system_capacity;
   b->Ncap = ((cfg->atom_capacity + 31LL * cfg->system_capacity) + 31) / 32 * 32;
   b->Wcap = b->Ncap / 32;
@@ -109,9 +109,9 @@ extern "C" ts_status ts_batch_create(const ts_batch_config* cfg, const ts_potent
     D.phicd = phic; D.phicf = (float)phic;
     D.skin = P.skin;
     D.rlist = rc + P.skin; D.rlist2d = D.rlist * D.rlist; D.rlist2f = (float)D.rlist2d;
-    {   // re-list hysteresis factor (tuning knob; 1 disables)
+    {   // re-list hysteresis factor (0.5 measured best on ragged batches; TS_SOON overrides, 1 disables)
       const char* e = getenv("TS_SOON");
-      double f = e ? atof(e) : 1.0;
+      double f = e ? atof(e) : 0.5;
       if (!(f > 0 && f <= 1)) f = 1.0;
       D.soon2 = f * f;
     }
@@ -323,6 +323,23 @@ ts_status derive_topology(ts_batch* b, const ts_state* s, cudaStream_t st) {
   }
   b->n_chunks = (int32_t)csys.size();
   if (b->n_chunks > b->Wcap) return fail(b, TS_ERR_BUDGET, "chunk table exceeds capacity");
+  {   // largest chunks first, so that the tail of the pair launch is short
+      // (work proxy: atoms in the chunk; soft spheres carry about half the
+      // neighbours of the Lennard-Jones and Morse workloads)
+    std::vector<int32_t> order(b->n_chunks);
+    std::vector<double> work(b->n_chunks);
+    for (int c = 0; c < b->n_chunks; c++) {
+      int k = csys[c];
+      int atoms = std::min(kPairSmallThreads, n[k] - ca0[c]);
+      work[c] = atoms * (b->pots[pot[k]].kind == TS_SOFT_SPHERE ? 0.5 : 1.0);
+      order[c] = c;
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return work[a] > work[c]; });
+    std::vector<int32_t> s2(b->n_chunks), a2(b->n_chunks);
+    for (int c = 0; c < b->n_chunks; c++) { s2[c] = csys[order[c]]; a2[c] = ca0[order[c]]; }
+    csys.swap(s2);
+    ca0.swap(a2);
+  }
   b->h_caller_off = caller_off; b->h_n = n; b->h_pot = pot; b->h_seg = seg;
   SysArrays& S = b->S;
   bool ok = cuda_ok(b, cudaMemcpyAsync(S.seg_start, seg.data(), 8 * B, cudaMemcpyHostToDevice, st), "h2d") &&

@@ -274,15 +274,15 @@ class Batch:
 
 
 def default_skins(pots):
-    """Skin per potential: 1.0 A for LJ argon scale, 0.5 A for Morse Cu, 0.6 sigma for soft spheres
-    (light, stiff particles whose thermal excursions would otherwise trigger a re-listing every step),
-    0.3 sigma for reduced LJ."""
+    """Skin per potential, from a step-time sweep on the 512-system ragged batch at 300 K: 1.0 A for LJ
+    argon, 0.75 A for Morse Cu, 0.9 sigma for soft spheres (light, stiff particles whose thermal
+    excursions would otherwise force a re-listing every few steps), 0.3 sigma for reduced-unit LJ."""
     out = []
     for d in pots:
         if d["kind"] == 2:
-            out.append(0.6 * d["p"][0])
+            out.append(0.9 * d["p"][0])
         elif d["kind"] == 0:
             out.append(0.3 * d["p"][0] if d["p"][0] < 2 else 1.0)
         else:
-            out.append(0.5)
+            out.append(0.75)
     return out
