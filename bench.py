@@ -30,6 +30,17 @@ UNIT = "atom-steps/s"
 FP32_LANES_PER_SM, N_SM = 128, 148
 FLOP_PER_PAIR = 30          # per ordered pair within the cutoff (force, energy, virial terms)
 BYTES_PER_ATOM = 32         # read own position, write own force, per atom-step
+# DRAM bytes (read + write) of one forces-only k_pair_small launch on ragged-mix-512, from one ncu
+# capture (profiles/k_pair_small_ragged_mix_512.md); reported only while the kernel's sources
+# (ts_pair.cu, then ts_internal.cuh) hash to the value recorded with the capture
+PAIR_TRAFFIC = {"bytes": 73_277_952 + 1_381_376, "source_sha1": "27dfb7db12ccfbb4e699bad0eefb92958f0924c9"}
+
+
+def pair_traffic():
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_2508_06628_b300", "csrc")
+    h = hashlib.sha1(b"".join(open(os.path.join(csrc, f), "rb").read() for f in ("ts_pair.cu", "ts_internal.cuh")))
+    return PAIR_TRAFFIC["bytes"] if h.hexdigest() == PAIR_TRAFFIC["source_sha1"] else None
 
 
 def peaks():
@@ -166,7 +177,8 @@ def run_ours(args, rank, world):
     achieved = flops / (kms / 1e3) / 1e12
     hbm_achieved = atoms * BYTES_PER_ATOM / (kms / 1e3) / 1e9
     out["roofline"] = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                       "frac": achieved / alu_peak, "traffic": None, "kernel": "k_pair<mixed>",
+                       "frac": achieved / alu_peak, "traffic": pair_traffic(),
+                       "kernel": "k_pair_small" + (" + k_pair" if int(np.bincount(hb.system_idx).max()) > 2048 else ""),
                        "kernel_ms": kms, "kernel_ms_cold_l2": kms_cold, "kernel_ms_warm_l2": kms_warm,
                        "pairs_per_launch": pairs, "flop_per_pair": FLOP_PER_PAIR,
                        "peak_source": f"148 SM x 128 FP32 lanes x 2 x {smmhz:.0f} MHz (max SM clock)",

@@ -57,8 +57,8 @@ size_t scratch_bytes(int64_t Ncap, int64_t Bcap, int64_t Ccap, int32_t max_nbrs,
                            3 * 8 * 3 /*tmp d0,d1*/ + 4 * 8 /*tmp d2*/ + 2 * 3 * 8 /*gd*/)
                         : (2 * 16 /*x*/ + 2 * 16 /*v*/ + 16 /*F*/ + 2 * 16 /*xr*/ + 2 * 16 + 2 * 16 /*tmp f*/ +
                            2 * 16 /*g*/);
-  per_slot += 4 * 4 /*perm sys bin nn*/ + 3 * 4 /*tmp i*/ + (size_t)max_nbrs * 4 + 8 * 8 / 32 /*partials*/;
-  size_t per_sys = 8 * 4 + 9 * 8 * 3 + 6 * 4 + 4 * 4 + 8 + (size_t)kNCodes * (32 + 24);
+  per_slot += 4 * 4 /*perm sys bin nn*/ + 3 * 4 /*tmp i*/ + (size_t)max_nbrs * 4 + 8 * 8 / 32 /*partials*/ + 4 / 32 /*warp_sys*/ + 16 / 32 /*pair work items*/;
+  size_t per_sys = 8 * 4 + 9 * 8 * 3 + 9 * 4 + 6 * 4 + 4 * 4 + 8 + 8 /*list-build work table*/ + (size_t)kNCodes * (32 + 24);
   return per_slot * (size_t)Ncap + per_sys * (size_t)Bcap + (size_t)Ccap * 8;
 }
 
@@ -93,6 +93,10 @@ extern "C" ts_status ts_batch_create(const ts_batch_config* cfg, const ts_potent
   size_t need = scratch_bytes(b->Ncap, b->Bcap, b->Ccap, b->max_nbrs, b->f64);
   if (cfg->memory_budget_bytes && need > cfg->memory_budget_bytes) { delete b; return TS_ERR_BUDGET; }
   if (!cuda_ok(b, cudaSetDevice(cfg->device), "cudaSetDevice")) { delete b; return TS_ERR_CUDA; }
+  if (!cuda_ok(b, cudaDeviceGetAttribute(&b->n_sm, cudaDevAttrMultiProcessorCount, cfg->device), "SM count")) {
+    delete b;
+    return TS_ERR_CUDA;
+  }
   // device potential table
   DevPot dp[kMaxPots];
   memset(dp, 0, sizeof dp);
@@ -103,6 +107,7 @@ extern "C" ts_status ts_batch_create(const ts_batch_config* cfg, const ts_potent
     for (int c = 0; c < 3; c++) { D.pd[c] = P.p[c]; D.pf[c] = (float)P.p[c]; }
     double rc = P.kind == TS_SOFT_SPHERE ? P.p[0] : P.cutoff;
     D.rc2d = rc * rc; D.rc2f = (float)(rc * rc);
+    D.sinvf = (float)(1.0 / P.p[0]);
     double phic = 0;
     if (P.shift && P.kind == TS_LJ) { double s = P.p[0] / rc, s6 = s * s * s * s * s * s; phic = 4 * P.p[1] * (s6 * s6 - s6); }
     if (P.shift && P.kind == TS_MORSE) { double e = exp(-P.p[1] * (rc - P.p[2])); phic = P.p[0] * (e * e - 2 * e); }
@@ -115,6 +120,8 @@ extern "C" ts_status ts_batch_create(const ts_batch_config* cfg, const ts_potent
       if (!(f > 0 && f <= 1)) f = 1.0;
       D.soon2 = f * f;
     }
+    D.half_skin2f = (float)(0.25 * P.skin * P.skin);
+    D.soon_half_skin2f = (float)(D.soon2 * 0.25 * P.skin * P.skin);
     b->rc[q] = rc;
   }
   bool ok = true;
@@ -125,7 +132,7 @@ extern "C" ts_status ts_batch_create(const ts_batch_config* cfg, const ts_potent
        alloc(b, b->d_step, 2);
   ok = ok && alloc(b, S.seg_start, B) && alloc(b, S.n_atoms, B) && alloc(b, S.caller_off, B + 1) && alloc(b, S.pot, B) &&
        alloc(b, S.uid, B) && alloc(b, S.bin_off, B) && alloc(b, S.bin_cap, B) && alloc(b, S.warp_start, B) &&
-       alloc(b, S.warp_end, B) && alloc(b, S.h, 9 * B) && alloc(b, S.hinv, 9 * B) && alloc(b, S.href, 9 * B) &&
+       alloc(b, S.warp_end, B) && alloc(b, S.h, 9 * B) && alloc(b, S.hinv, 9 * B) && alloc(b, S.hinvf, 9 * B) && alloc(b, S.href, 9 * B) &&
        alloc(b, S.nb, 3 * B) && alloc(b, S.reach, 3 * B) && alloc(b, S.relist, B) && alloc(b, S.dirty, B) &&
        alloc(b, S.soon, B) && alloc(b, S.any, 1) &&
        alloc(b, S.kT, B) && alloc(b, S.shift, 2 * B * kNCodes) && alloc(b, S.shiftd, 3 * B * kNCodes);
@@ -146,7 +153,8 @@ extern "C" ts_status ts_batch_create(const ts_batch_config* cfg, const ts_potent
        alloc(b, b->d_bsum, (b->Ccap + 1023) / 1024 + 1) && alloc(b, b->d_starts, B + 1) &&
        alloc(b, b->d_Eint, B) && alloc(b, b->d_Wint, 9 * B) && alloc(b, b->d_scal, 32 * B) &&
        alloc(b, b->d_gparam_part, 4 * b->Wcap) && alloc(b, b->d_gacc, 3 * kMaxPots) &&
-       alloc(b, b->d_chunk_sys, b->Wcap) && alloc(b, b->d_chunk_a0, b->Wcap);
+       alloc(b, b->d_items, b->Wcap) && alloc(b, b->d_tab_sys, B) && alloc(b, b->d_tab_base, B + 1) &&
+       alloc(b, b->d_tab_n, 2);
   if (ok) ok = cuda_ok(b, cudaMemcpy(b->d_pots, dp, sizeof dp, cudaMemcpyHostToDevice), "copy pots");
   if (ok) ok = cuda_ok(b, cudaMemset(b->d_err, 0, 16), "memset") && cuda_ok(b, cudaMemset(b->d_counters, 0, 32), "memset");
   if (ok) ok = cuda_ok(b, cudaMemset(A.perm, 0xff, sizeof(int32_t) * N), "memset") &&
@@ -154,14 +162,24 @@ extern "C" ts_status ts_batch_create(const ts_batch_config* cfg, const ts_potent
                cuda_ok(b, cudaMemset(A.nn, 0, sizeof(int32_t) * N), "memset") &&
                cuda_ok(b, cudaMemset(b->d_partial, 0, sizeof(double) * kPartialStride * b->Wcap), "memset");
   if (ok) ok = cuda_ok(b, cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming), "event");
+  if (ok) {
+    int least = 0, greatest = 0;
+    ok = cuda_ok(b, cudaDeviceGetStreamPriorityRange(&least, &greatest), "priority range") &&
+         cuda_ok(b, cudaStreamCreateWithPriority(&b->side, cudaStreamNonBlocking, greatest), "side stream") &&
+         cuda_ok(b, cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming), "event") &&
+         cuda_ok(b, cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming), "event");
+    b->prio_hi = greatest;
+    const char* e = getenv("TS_OVERLAP_RELIST");
+    if (e && atoi(e) == 0) b->overlap_relist = false;
+  }
   if (ok) ok = cuda_ok(b, cudaFuncSetAttribute(k_relist_small<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)sizeof(SmallSmem)), "smem attribute") &&
                cuda_ok(b, cudaFuncSetAttribute(k_relist_small<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)sizeof(SmallSmem)), "smem attribute") &&
                cuda_ok(b, cudaFuncSetAttribute(k_pair_small<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)(2 * sizeof(float4) * kSmallMax)), "smem attribute") &&
+                                               (int)(kSmallRecord * kSmallMax)), "smem attribute") &&
                cuda_ok(b, cudaFuncSetAttribute(k_pair_small<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)(2 * sizeof(float4) * kSmallMax)), "smem attribute");
+                                               (int)(kSmallRecord * kSmallMax)), "smem attribute");
   if (!ok) { ts_batch_destroy(b); return TS_ERR_CUDA; }
   b->dp_host.assign(dp, dp + kMaxPots);
   autotune_load(b);
@@ -204,6 +222,9 @@ extern "C" ts_status ts_batch_destroy(ts_batch* b) {
   cudaDeviceSynchronize();
   for (void* p : b->allocations) cudaFree(p);
   if (b->ev) cudaEventDestroy(b->ev);
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  if (b->ev_join) cudaEventDestroy(b->ev_join);
+  if (b->side) cudaStreamDestroy(b->side);
   for (auto& g : b->graphs) if (g.exec) cudaGraphExecDestroy(g.exec);
   delete b;
   return TS_OK;
@@ -313,32 +334,48 @@ ts_status derive_topology(ts_batch* b, const ts_state* s, cudaStream_t st) {
   b->B = B; b->N = N; b->Npad = slot; b->nwarps = (int32_t)(slot / 32); b->nbins = bins;
   b->n_large = 0;
   for (int k = 0; k < B; k++) b->n_large += n[k] > kSmallMax;
-  // 256-atom chunks of the small systems for the shared-memory pair kernel
-  std::vector<int32_t> csys, ca0;
-  b->nmax_small = 0;
-  for (int k = 0; k < B; k++) {
-    if (n[k] > kSmallMax) continue;
-    b->nmax_small = std::max(b->nmax_small, n[k]);
-    for (int a = 0; a < n[k]; a += kPairSmallThreads) { csys.push_back(k); ca0.push_back(a); }
-  }
-  b->n_chunks = (int32_t)csys.size();
-  if (b->n_chunks > b->Wcap) return fail(b, TS_ERR_BUDGET, "chunk table exceeds capacity");
-  {   // largest chunks first, so that the tail of the pair launch is short
-      // (work proxy: atoms in the chunk; soft spheres carry about half the
-      // neighbours of the Lennard-Jones and Morse workloads)
-    std::vector<int32_t> order(b->n_chunks);
-    std::vector<double> work(b->n_chunks);
-    for (int c = 0; c < b->n_chunks; c++) {
-      int k = csys[c];
-      int atoms = std::min(kPairSmallThreads, n[k] - ca0[c]);
-      work[c] = atoms * (b->pots[pot[k]].kind == TS_SOFT_SPHERE ? 0.5 : 1.0);
-      order[c] = c;
+  // work items of the shared-memory pair kernel (systems up to kSmallMax atoms):
+  // the warps of those systems, in order, cut into runs of at most 8; a run
+  // may straddle systems, and stages every system it touches, as long as
+  // that staged range stays within kSmallMax slots (otherwise it is cut at
+  // the system boundary)
+  const int wpi = kPairSmallThreads / kWarp, cap = kSmallMax / kWarp;
+  std::vector<int4> items;
+  std::vector<double> work;
+  b->nst_max = 0;
+  {
+    int first = -1, count = 0, s0 = -1;
+    double wk = 0;
+    auto flush = [&](int s_last) {
+      if (count == 0) return;
+      items.push_back(make_int4(ws[s0], we[s_last] - ws[s0], first, count));
+      work.push_back(wk);
+      b->nst_max = std::max(b->nst_max, (we[s_last] - ws[s0]) * kWarp);
+      count = 0; wk = 0;
+    };
+    int s_prev = -1;
+    for (int k = 0; k < B; k++) {
+      if (n[k] > kSmallMax) { flush(s_prev); continue; }
+      double c = b->pots[pot[k]].kind == TS_SOFT_SPHERE ? 0.5 : 1.0;   // soft spheres: about half the list length
+      for (int w = ws[k]; w < we[k]; w++) {
+        if (count > 0 && (count == wpi || we[k] - ws[s0] > cap)) flush(s_prev);
+        if (count == 0) { first = w; s0 = k; }
+        count++;
+        wk += c * std::min(kWarp, n[k] - (w - ws[k]) * kWarp);
+        s_prev = k;
+      }
     }
+    flush(s_prev);
+  }
+  b->n_items = (int32_t)items.size();
+  if (b->n_items > b->Wcap) return fail(b, TS_ERR_BUDGET, "pair work table exceeds capacity");
+  {   // most work first (atoms, soft spheres weighted by half for their shorter lists), so the launch ends on small items
+    std::vector<int32_t> order(b->n_items);
+    for (int c = 0; c < b->n_items; c++) order[c] = c;
     std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return work[a] > work[c]; });
-    std::vector<int32_t> s2(b->n_chunks), a2(b->n_chunks);
-    for (int c = 0; c < b->n_chunks; c++) { s2[c] = csys[order[c]]; a2[c] = ca0[order[c]]; }
-    csys.swap(s2);
-    ca0.swap(a2);
+    std::vector<int4> sorted(b->n_items);
+    for (int c = 0; c < b->n_items; c++) sorted[c] = items[order[c]];
+    items.swap(sorted);
   }
   b->h_caller_off = caller_off; b->h_n = n; b->h_pot = pot; b->h_seg = seg;
   SysArrays& S = b->S;
@@ -351,9 +388,8 @@ ts_status derive_topology(ts_batch* b, const ts_state* s, cudaStream_t st) {
             cuda_ok(b, cudaMemcpyAsync(S.warp_start, ws.data(), 4 * B, cudaMemcpyHostToDevice, st), "h2d") &&
             cuda_ok(b, cudaMemcpyAsync(S.warp_end, we.data(), 4 * B, cudaMemcpyHostToDevice, st), "h2d") &&
             cuda_ok(b, cudaMemcpyAsync(b->d_warp_sys, warp_sys.data(), 4 * warp_sys.size(), cudaMemcpyHostToDevice, st), "h2d");
-  if (ok && b->n_chunks > 0)
-    ok = cuda_ok(b, cudaMemcpyAsync(b->d_chunk_sys, csys.data(), 4 * csys.size(), cudaMemcpyHostToDevice, st), "h2d") &&
-         cuda_ok(b, cudaMemcpyAsync(b->d_chunk_a0, ca0.data(), 4 * ca0.size(), cudaMemcpyHostToDevice, st), "h2d");
+  if (ok && b->n_items > 0)
+    ok = cuda_ok(b, cudaMemcpyAsync(b->d_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice, st), "h2d");
   if (s->uid) {
     ok = ok && cuda_ok(b, cudaMemcpyAsync(S.uid, s->uid, 4 * B, cudaMemcpyDeviceToDevice, st), "d2d");
   } else {
@@ -415,26 +451,74 @@ ts_status prologue(ts_batch* b, ts_state* s, cudaStream_t st, bool import_vel) {
 // Re-list every flagged system: bin, counting sort (canonical order inside a
 // bin), state move, explicit list.  Kernels skip unflagged systems, so the
 // sequence is safe to issue every step (and to capture in a graph).
-void relist(ts_batch* b, cudaStream_t st, bool move_fire) {
+void relist_sort(ts_batch* b, cudaStream_t st, bool move_fire, int prio) {
   int B = b->B;
-  // systems of up to kSmallMax atoms: bin and sort, one CTA per system
+  // systems of up to kSmallMax atoms: bin and sort, one CTA per system, plus
+  // one CTA that writes the list-build work table
   if (b->f64)
-    k_relist_small<true><<<B, kSmallThreads, sizeof(SmallSmem), st>>>(B, b->S, b->A, b->Ncap, move_fire, b->d_cstart,
-                                                                       b->d_count, b->d_pots, b->max_nbrs, b->d_err);
+    launch_k(st, prio, B + 1, kSmallThreads, sizeof(SmallSmem), k_relist_small<true>, B, b->S, b->A, b->Ncap,
+             (int)move_fire, b->d_cstart, b->d_count, (const DevPot*)b->d_pots, b->max_nbrs, b->d_err, b->d_tab_sys,
+             b->d_tab_base, b->d_tab_n);
   else
-    k_relist_small<false><<<B, kSmallThreads, sizeof(SmallSmem), st>>>(B, b->S, b->A, b->Ncap, move_fire, b->d_cstart,
-                                                                        b->d_count, b->d_pots, b->max_nbrs, b->d_err);
+    launch_k(st, prio, B + 1, kSmallThreads, sizeof(SmallSmem), k_relist_small<false>, B, b->S, b->A, b->Ncap,
+             (int)move_fire, b->d_cstart, b->d_count, (const DevPot*)b->d_pots, b->max_nbrs, b->d_err, b->d_tab_sys,
+             b->d_tab_base, b->d_tab_n);
   b->launches++;
   if (b->n_large > 0) relist_large_sort(b, st, move_fire);
-  // Verlet lists of every flagged system, then the flag bookkeeping
-  int wb = (int)(((int64_t)b->nwarps * 32 + 127) / 128);
-  if (b->f64) k_build_list_warp<true><<<wb, 128, 0, st>>>(b->nwarps, b->d_warp_sys, b->S, b->A, b->d_cstart, b->d_count,
-                                                          b->d_pots, b->max_nbrs, b->Ncap, b->d_err);
-  else k_build_list_warp<false><<<wb, 128, 0, st>>>(b->nwarps, b->d_warp_sys, b->S, b->A, b->d_cstart, b->d_count,
-                                                    b->d_pots, b->max_nbrs, b->Ncap, b->d_err);
-  k_after_relist<<<(B + 127) / 128, 128, 0, st>>>(B, b->S, b->d_counters);
+}
+
+void relist_build(ts_batch* b, cudaStream_t st, int prio) {
+  // Verlet lists of the table's warps: a resident grid taking warps from a counter
+  int grid = b->n_sm * kBuildCtasPerSm;
+  if (b->f64)
+    launch_k(st, prio, grid, 128, 0, k_build_list_warp<true>, b->S, b->A, (const int32_t*)b->d_tab_sys,
+             (const int32_t*)b->d_tab_base, b->d_tab_n, (const int32_t*)b->d_cstart, (const int32_t*)b->d_count,
+             (const DevPot*)b->d_pots, b->max_nbrs, b->Ncap, b->d_err);
+  else
+    launch_k(st, prio, grid, 128, 0, k_build_list_warp<false>, b->S, b->A, (const int32_t*)b->d_tab_sys,
+             (const int32_t*)b->d_tab_base, b->d_tab_n, (const int32_t*)b->d_cstart, (const int32_t*)b->d_count,
+             (const DevPot*)b->d_pots, b->max_nbrs, b->Ncap, b->d_err);
+  b->launches++;
+}
+
+void relist_lists(ts_batch* b, cudaStream_t st, bool move_fire, int prio) {
+  relist_sort(b, st, move_fire, prio);
+  relist_build(b, st, prio);
+}
+
+// end of a re-listing pass: flag bookkeeping
+void relist_finish(ts_batch* b, cudaStream_t st) {
+  k_after_relist<<<(b->B + 127) / 128, 128, 0, st>>>(b->B, b->S, b->d_counters);
   k_clear_any<<<1, 1, 0, st>>>(b->S);
-  b->launches += 3;
+  b->launches += 2;
+}
+
+void relist(ts_batch* b, cudaStream_t st, bool move_fire) {
+  relist_lists(b, st, move_fire);
+  relist_finish(b, st);
+}
+
+// Re-listing pass and pair forces with the list build off the critical
+// path.  The flagged systems are re-sorted first (a short launch with few
+// CTAs, which needs most of an SM's registers per CTA); then the systems that
+// keep their lists get their forces on `st` while the flagged ones are
+// re-listed and get theirs on the side stream (highest priority, so that its
+// latency-bound kernels are dispatched ahead of the pair kernel's pending
+// CTAs).  The two halves touch disjoint systems.  Returns false (nothing
+// issued) when the overlap is off or `st` is the legacy default stream.
+bool relist_pair_overlapped(ts_batch* b, cudaStream_t st, bool move_fire, bool ew) {
+  if (!b->overlap_relist || !b->side || st == nullptr) return false;
+  relist_sort(b, st, move_fire, 0);
+  if (!cuda_ok(b, cudaEventRecord(b->ev_fork, st), "event record") ||
+      !cuda_ok(b, cudaStreamWaitEvent(b->side, b->ev_fork, 0), "stream wait"))
+    return false;
+  relist_build(b, b->side, b->prio_hi);
+  pair(b, b->side, ew, kPairRelisted, b->prio_hi);
+  cuda_ok(b, cudaEventRecord(b->ev_join, b->side), "event record");
+  pair(b, st, ew, kPairKept);
+  cuda_ok(b, cudaStreamWaitEvent(st, b->ev_join, 0), "stream wait");
+  relist_finish(b, st);
+  return true;
 }
 
 // systems above kSmallMax atoms: global counting sort over all bins
@@ -460,27 +544,30 @@ void relist_large_sort(ts_batch* b, cudaStream_t st, bool move_fire) {
   b->launches += 9;
 }
 
-void pair(ts_batch* b, cudaStream_t st, bool ew, bool only_dirty) {
+void pair(ts_batch* b, cudaStream_t st, bool ew, int filter, int prio) {
   int threads = b->pair_threads;
   int blocks = (int)(((int64_t)b->nwarps * 32 + threads - 1) / threads);
+  const DevPot* pots = b->d_pots;
+  const int32_t* ws = b->d_warp_sys;
   if (b->f64) {
-    if (ew) k_pair<true, true><<<blocks, threads, 0, st>>>(b->nwarps, b->d_warp_sys, b->S, b->A, b->d_pots, b->Ncap, only_dirty, b->d_partial, 0);
-    else k_pair<true, false><<<blocks, threads, 0, st>>>(b->nwarps, b->d_warp_sys, b->S, b->A, b->d_pots, b->Ncap, only_dirty, b->d_partial, 0);
+    if (ew) launch_k(st, prio, blocks, threads, 0, k_pair<true, true>, b->nwarps, ws, b->S, b->A, pots, b->Ncap, filter, b->d_partial, 0);
+    else launch_k(st, prio, blocks, threads, 0, k_pair<true, false>, b->nwarps, ws, b->S, b->A, pots, b->Ncap, filter, b->d_partial, 0);
     b->launches++;
     return;
   }
   // mixed precision: systems up to kSmallMax atoms from shared memory, larger ones gathered through L1
-  bool small = b->use_small_pair && b->n_chunks > 0;
+  bool small = b->use_small_pair && b->n_items > 0;
   if (small) {
-    size_t shm = 2 * sizeof(float4) * (size_t)b->nmax_small;
-    if (ew) k_pair_small<true><<<b->n_chunks, kPairSmallThreads, shm, st>>>(b->n_chunks, b->d_chunk_sys, b->d_chunk_a0, b->S, b->A, b->d_pots, b->Ncap, only_dirty, b->d_partial);
-    else k_pair_small<false><<<b->n_chunks, kPairSmallThreads, shm, st>>>(b->n_chunks, b->d_chunk_sys, b->d_chunk_a0, b->S, b->A, b->d_pots, b->Ncap, only_dirty, b->d_partial);
+    size_t shm = (size_t)kSmallRecord * b->nst_max;
+    const int4* it = b->d_items;
+    if (ew) launch_k(st, prio, b->n_items, kPairSmallThreads, shm, k_pair_small<true>, b->n_items, it, ws, b->S, b->A, pots, b->Ncap, filter, b->d_partial);
+    else launch_k(st, prio, b->n_items, kPairSmallThreads, shm, k_pair_small<false>, b->n_items, it, ws, b->S, b->A, pots, b->Ncap, filter, b->d_partial);
     b->launches++;
   }
   if (!small || b->n_large > 0) {
     int sk = small ? 1 : 0;
-    if (ew) k_pair<false, true><<<blocks, threads, 0, st>>>(b->nwarps, b->d_warp_sys, b->S, b->A, b->d_pots, b->Ncap, only_dirty, b->d_partial, sk);
-    else k_pair<false, false><<<blocks, threads, 0, st>>>(b->nwarps, b->d_warp_sys, b->S, b->A, b->d_pots, b->Ncap, only_dirty, b->d_partial, sk);
+    if (ew) launch_k(st, prio, blocks, threads, 0, k_pair<false, true>, b->nwarps, ws, b->S, b->A, pots, b->Ncap, filter, b->d_partial, sk);
+    else launch_k(st, prio, blocks, threads, 0, k_pair<false, false>, b->nwarps, ws, b->S, b->A, pots, b->Ncap, filter, b->d_partial, sk);
     b->launches++;
   }
 }

@@ -32,10 +32,13 @@ struct ts_batch {
   int32_t Bcap = 0;
   // topology
   bool topo_valid = false, first_import = true;
-  int32_t B = 0, nwarps = 0, n_large = 0, n_chunks = 0, nmax_small = 0;
+  int32_t B = 0, nwarps = 0, n_large = 0, n_items = 0, nst_max = 0;
   bool use_small_pair = true;
-  int32_t* d_chunk_sys = nullptr;
-  int32_t* d_chunk_a0 = nullptr;
+  int4* d_items = nullptr;        // work items of k_pair_small
+  int32_t* d_tab_sys = nullptr;   // list-build work table (k_relist_small writes it)
+  int32_t* d_tab_base = nullptr;
+  int32_t* d_tab_n = nullptr;
+  int n_sm = 148;
   int64_t N = 0, Npad = 0, nbins = 0;
   std::vector<int64_t> h_caller_off, h_seg;
   std::vector<int32_t> h_n, h_pot;
@@ -60,6 +63,12 @@ struct ts_batch {
   std::vector<void*> allocations;
   size_t bytes_allocated = 0;
   cudaEvent_t ev = nullptr;
+  // second stream (highest priority) and fork/join events: a re-listing pass
+  // runs beside the pair forces of the systems that keep their lists
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  bool overlap_relist = true;
+  int prio_hi = 0;                // numerically greatest-priority value of the device
   // launch shapes (autotuned)
   int pair_threads = 128;
   bool use_graphs = true;
@@ -78,9 +87,31 @@ size_t scratch_bytes(int64_t Ncap, int64_t Bcap, int64_t Ccap, int32_t max_nbrs,
 ts_status derive_topology(ts_batch* b, const ts_state* s, cudaStream_t st);
 ts_status check_state(ts_batch* b, const ts_state* s, bool need_vel);
 ts_status prologue(ts_batch* b, ts_state* s, cudaStream_t st, bool import_vel);
+// Kernel launch with a scheduling priority (0: the stream's own).  Stream
+// capture keeps the launch attribute as the kernel node's priority.
+template <typename... KArgs, typename... Args>
+inline void launch_k(cudaStream_t st, int prio, dim3 grid, dim3 block, size_t shm, void (*kern)(KArgs...),
+                     Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = shm;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributePriority;
+  at[0].val.priority = prio;
+  cfg.attrs = at;
+  cfg.numAttrs = prio != 0 ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, kern, args...);
+}
 void relist(ts_batch* b, cudaStream_t st, bool move_fire);
+void relist_lists(ts_batch* b, cudaStream_t st, bool move_fire, int prio = 0);
+void relist_sort(ts_batch* b, cudaStream_t st, bool move_fire, int prio);
+void relist_build(ts_batch* b, cudaStream_t st, int prio);
+void relist_finish(ts_batch* b, cudaStream_t st);
+bool relist_pair_overlapped(ts_batch* b, cudaStream_t st, bool move_fire, bool ew);
 void relist_large_sort(ts_batch* b, cudaStream_t st, bool move_fire);
-void pair(ts_batch* b, cudaStream_t st, bool ew, bool only_dirty);
+void pair(ts_batch* b, cudaStream_t st, bool ew, int filter, int prio = 0);
 void reduce_sys(ts_batch* b, cudaStream_t st, double* E, double* stress, double* KE);
 void clear_dirty(ts_batch* b, cudaStream_t st);
 void export_state(ts_batch* b, cudaStream_t st, double* pos, double* vel);

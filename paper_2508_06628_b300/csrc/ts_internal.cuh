@@ -34,10 +34,6 @@ constexpr int kCenter = kMaxReach + kImgSide * kMaxReach + kImgSide * kImgSide *
 constexpr int kMaxPots = 16;
 constexpr int kSmallMax = 2048;           // systems up to this size are sorted by one CTA
 
-// Few bins and few atoms: many images per atom, so the list build splits the
-// candidates of one atom across a warp instead of giving each lane an atom.
-__host__ __device__ inline bool is_tiny(int n_atoms, int nbins) { return nbins <= 8 && n_atoms <= 64; }
-
 // Re-list hysteresis: a system whose atoms moved more than skin/2 must be
 // re-listed; one past soon * skin/2 (soon per potential, 1 = off) is
 // re-listed in the same pass whenever any system must, so re-listings gather
@@ -59,6 +55,8 @@ struct DevPot {
   int kind, shift;
   float pf[3];
   float rc2f, phicf, rlist2f;
+  float sinvf;    // 1/sigma in FP32 (soft sphere)
+  float half_skin2f, soon_half_skin2f;   // (skin/2)^2 and soon^2 (skin/2)^2, FP32 (mixed skin check)
   double pd[3];
   double rc2d, phicd, rlist, rlist2d, skin;
   double soon2;   // squared hysteresis factor
@@ -77,6 +75,7 @@ struct SysArrays {
   int32_t* warp_end;      // one past last warp
   double* h;              // [9] cell rows
   double* hinv;           // [9]
+  float* hinvf;           // [9] FP32 copy (bin choice)
   double* href;           // [9] cell at the last listing (FIRE)
   int32_t* nb;            // [3] bins per axis (at last listing)
   int32_t* reach;         // [3]
@@ -91,6 +90,17 @@ struct SysArrays {
 
 __device__ __forceinline__ bool need_relist(const SysArrays& S, int s) {
   return S.relist[s] || (S.soon[s] && S.any[0]);
+}
+
+// Which systems a pair launch covers: all, those flagged dirty, or (while a
+// re-listing pass runs beside it) those keeping their lists or those being
+// re-listed.  The re-list flags stay fixed until the pass's bookkeeping
+// kernel runs after both halves.
+enum PairFilter : int { kPairAll = 0, kPairDirty = 1, kPairKept = 2, kPairRelisted = 3 };
+__device__ __forceinline__ bool pair_skip(const SysArrays& S, int s, int filter) {
+  if (filter == kPairAll) return false;
+  if (filter == kPairDirty) return !S.dirty[s];
+  return need_relist(S, s) == (filter == kPairKept);
 }
 
 struct SlotArrays {
@@ -168,11 +178,11 @@ template <> struct PotMath<float> {
       fr = 2.0f * P.pf[1] * P.pf[0] * e * (1.0f - e) * rsqrtf(r2);
     } else {
       float ri = rsqrtf(r2);
-      float t = 1.0f - r2 * ri / P.pf[0];
+      float t = fmaf(-r2 * ri, P.sinvf, 1.0f);   // 1 - r/sigma in one fused operation
       float al = P.pf[2];
       float ta1 = (al == 2.0f) ? t : __powf(t, al - 1.0f);
       phi = P.pf[1] / al * ta1 * t;
-      fr = -P.pf[1] / P.pf[0] * ta1 * ri;
+      fr = -P.pf[1] * P.sinvf * ta1 * ri;
     }
   }
   // phi'/r and phi'' (for the adjoint), plus parameter derivatives of phi and phi'

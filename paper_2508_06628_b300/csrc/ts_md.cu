@@ -9,6 +9,8 @@
 // Philox4x32-10 (Salmon et al., SC'11) keyed by (seed, system uid) with
 // counter (step, atom index within its system), then Box-Muller, so it does
 // not depend on where the system sits in the batch.
+#include <type_traits>
+
 #include "ts_kernels.cuh"
 
 namespace ts {
@@ -24,9 +26,10 @@ __device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32
   }
 }
 
-// three standard normals for (step, local atom, seed, uid)
-template <bool F64>
-__device__ __forceinline__ void normals3(uint64_t step, uint32_t la, uint32_t seed, uint32_t uid, double z[3]) {
+// three standard normals for (step, local atom, seed, uid); T = double in
+// FP64 mode, float in mixed mode (no FP64 arithmetic or conversions there)
+template <bool F64, typename T>
+__device__ __forceinline__ void normals3(uint64_t step, uint32_t la, uint32_t seed, uint32_t uid, T z[3]) {
   uint32_t c[4] = {(uint32_t)step, la, (uint32_t)(step >> 32), 0u};
   philox4x32_10(c, seed, uid);
   if constexpr (F64) {
@@ -64,16 +67,18 @@ __global__ void k_md_kick_drift(int64_t Npad, SysArrays S, SlotArrays A, const D
                                 double dt, double c1, uint32_t seed, const uint64_t* __restrict__ step_base,
                                 uint64_t koff) {
   const uint64_t step = *step_base + koff;
+  const float omc2f = (float)(1.0 - c1 * c1);
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < Npad; k += (int64_t)gridDim.x * blockDim.x) {
     int p = A.perm[k];
     if (p < 0) continue;
     int s = A.sys[k];
-    double z[3] = {0, 0, 0};
+    using Real = typename std::conditional<F64, double, float>::type;
+    Real z[3] = {0, 0, 0};
     double osc = 0;
     if (KIND == 1) {
       normals3<F64>(step, (uint32_t)(p - S.caller_off[s]), seed, S.uid[s], z);
     }
-    double dx, dy, dz;
+    double dx = 0, dy = 0, dz = 0;
     if constexpr (F64) {
       double mi = A.minvd[k];
       double* v = A.vd + 3 * k;
@@ -105,7 +110,7 @@ __global__ void k_md_kick_drift(int64_t Npad, SysArrays S, SlotArrays A, const D
         pos_add(xh.y, xl.y, t * vh.y + t * vl.y);
         pos_add(xh.z, xl.z, t * vh.z + t * vl.z);
         float cc = (float)c1;
-        float so = sqrtf((float)((1.0 - c1 * c1) * S.kT[s]) * vh.w);
+        float so = sqrtf(omc2f * (float)S.kT[s] * vh.w);
         // v <- c1 v + so z, in double-float: scale the pair, then add the noise
         float nx = cc * vh.x, ny = cc * vh.y, nz = cc * vh.z;
         float ex = fmaf(cc, vh.x, -nx) + cc * vl.x, ey = fmaf(cc, vh.y, -ny) + cc * vl.y,
@@ -113,16 +118,20 @@ __global__ void k_md_kick_drift(int64_t Npad, SysArrays S, SlotArrays A, const D
         vh.x = nx + ex; vl.x = ex - (vh.x - nx);
         vh.y = ny + ey; vl.y = ey - (vh.y - ny);
         vh.z = nz + ez; vl.z = ez - (vh.z - nz);
-        df_add(vh.x, vl.x, so * (float)z[0]); df_add(vh.y, vl.y, so * (float)z[1]); df_add(vh.z, vl.z, so * (float)z[2]);
+        df_add(vh.x, vl.x, so * z[0]); df_add(vh.y, vl.y, so * z[1]); df_add(vh.z, vl.z, so * z[2]);
         pos_add(xh.x, xl.x, t * vh.x + t * vl.x);
         pos_add(xh.y, xl.y, t * vh.y + t * vl.y);
         pos_add(xh.z, xl.z, t * vh.z + t * vl.z);
       }
       A.vh[k] = vh; A.vl[k] = vl; A.xh[k] = xh; A.xl[k] = xl;
+      // skin check in FP32 (a threshold decision; FP64 is slow on this part)
       float4 rh = A.xrh[k], rl = A.xrl[k];
-      dx = (double)((xh.x - rh.x) + (xl.x - rl.x));
-      dy = (double)((xh.y - rh.y) + (xl.y - rl.y));
-      dz = (double)((xh.z - rh.z) + (xl.z - rl.z));
+      float ex = (xh.x - rh.x) + (xl.x - rl.x), ey = (xh.y - rh.y) + (xl.y - rl.y), ez = (xh.z - rh.z) + (xl.z - rl.z);
+      float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+      const DevPot& P = pots[S.pot[s]];
+      if (d2 > P.half_skin2f) { S.relist[s] = 1; S.any[0] = 1; }
+      else if (d2 > P.soon_half_skin2f) S.soon[s] = 1;
+      continue;
     }
     double sk = 0.5 * pots[S.pot[s]].skin, d2 = dx * dx + dy * dy + dz * dz;
     if (d2 > sk * sk) { S.relist[s] = 1; S.any[0] = 1; }

@@ -173,7 +173,7 @@ __global__ void k_geometry(int32_t B, SysArrays S, const double* __restrict__ ce
   g[4] = (h[0] * h[8] - h[2] * h[6]) / d; g[5] = (h[2] * h[3] - h[0] * h[5]) / d;
   g[6] = (h[3] * h[7] - h[4] * h[6]) / d; g[7] = (h[1] * h[6] - h[0] * h[7]) / d;
   g[8] = (h[0] * h[4] - h[1] * h[3]) / d;
-  for (int q = 0; q < 9; q++) S.hinv[9 * s + q] = g[q];
+  for (int q = 0; q < 9; q++) { S.hinv[9 * s + q] = g[q]; S.hinvf[9 * s + q] = (float)g[q]; }
   double V = fabs(d), w[3];
   double ext = 0;
   for (int a = 0; a < 3; a++) {
@@ -223,6 +223,37 @@ __global__ void k_shift_table(int32_t B, SysArrays S) {
   for (int c = 0; c < 3; c++) S.shiftd[3 * t + c] = v[c];
 }
 
+// Wrap a double-float position into its cell by a whole lattice vector and
+// find its bin.  FP32 fractional coordinates choose the lattice vector and the
+// bin (an atom within ~1e-7 of a face may end up a few 1e-6 A outside its bin,
+// far inside any skin); the shift itself is the system's double-float image
+// shift, added exactly to hi and with one FP32 rounding to lo, so an atom that
+// stays inside its cell is left bit-identical.  No FP64 arithmetic (slow on
+// this part).  Returns false when the atom lies more than kMaxReach cells away
+// (the caller then takes the FP64 route).
+__device__ __forceinline__ bool wrap_bin_mixed(const SysArrays& S, int s, float4& hi, float4& lo, int kb[3]) {
+  const float* g = S.hinvf + 9 * s;
+  const float x0 = hi.x + lo.x, x1 = hi.y + lo.y, x2 = hi.z + lo.z;
+  int n[3];
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    float v = fmaf(x0, g[a], fmaf(x1, g[3 + a], x2 * g[6 + a]));
+    float fl = floorf(v);
+    if (!(fabsf(fl) <= (float)kMaxReach)) return false;
+    n[a] = (int)fl;
+    int nb = S.nb[3 * s + a];
+    int q = (int)((v - fl) * (float)nb);
+    kb[a] = q >= nb ? nb - 1 : (q < 0 ? 0 : q);
+  }
+  if (n[0] | n[1] | n[2]) {
+    int64_t ti = (int64_t)s * kNCodes + img_code(-n[0], -n[1], -n[2]);
+    float4 sh = S.shift[2 * ti], sl = S.shift[2 * ti + 1];
+    hi.x += sh.x; hi.y += sh.y; hi.z += sh.z;   // exact: both on the 2^-12 grid
+    pos_add(hi.x, lo.x, sl.x); pos_add(hi.y, lo.y, sl.y); pos_add(hi.z, lo.z, sl.z);
+  }
+  return true;
+}
+
 // --- counting sort by (system, bin) ------------------------------------------
 __global__ void k_zero_bins(int32_t B, SysArrays S, int32_t* count) {
   int s = blockIdx.x;
@@ -239,6 +270,17 @@ __global__ void k_bin_atoms(int64_t Npad, SysArrays S, SlotArrays A, int32_t* co
     if (p < 0) continue;
     int s = A.sys[k];
     if (!need_relist(S, s) || S.n_atoms[s] <= kSmallMax) continue;
+    int kb[3];
+    if constexpr (!F64) {
+      float4 hi = A.xh[k], lo = A.xl[k];
+      if (wrap_bin_mixed(S, s, hi, lo, kb)) {
+        A.tmp_f0[k] = hi; A.tmp_f1[k] = lo;
+        int gb = S.bin_off[s] + (kb[2] * S.nb[3 * s + 1] + kb[1]) * S.nb[3 * s] + kb[0];
+        A.tmp_i0[k] = gb;
+        A.tmp_i1[k] = atomicAdd(&count[gb], 1);
+        continue;
+      }
+    }
     double x[3];
     if constexpr (F64) {
       for (int c = 0; c < 3; c++) x[c] = A.xd[3 * k + c];
@@ -249,7 +291,6 @@ __global__ void k_bin_atoms(int64_t Npad, SysArrays S, SlotArrays A, int32_t* co
     const double* g = S.hinv + 9 * s;
     const double* h = S.h + 9 * s;
     double f[3];
-    int kb[3];
     for (int a = 0; a < 3; a++) {
       double v = x[0] * g[a] + x[1] * g[3 + a] + x[2] * g[6 + a];
       v -= floor(v);

@@ -16,12 +16,12 @@ namespace ts {
 template <bool F64, bool EW>
 __global__ void __launch_bounds__(256) k_pair(int32_t n_warps, const int32_t* __restrict__ warp_sys, SysArrays S,
                                               SlotArrays A, const DevPot* __restrict__ pots, int64_t stride,
-                                              int only_dirty, double* __restrict__ partial, int skip_small) {
+                                              int filter, double* __restrict__ partial, int skip_small) {
   int w = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
   int lane = threadIdx.x & 31;
   if (w >= n_warps) return;
   int s = warp_sys[w];
-  if (only_dirty && !S.dirty[s]) return;
+  if (pair_skip(S, s, filter)) return;
   if (skip_small && S.n_atoms[s] <= kSmallMax) return;   // handled by k_pair_small
   int64_t k = (int64_t)w * kWarp + lane;
   const DevPot P = pots[S.pot[s]];
@@ -131,43 +131,65 @@ __global__ void __launch_bounds__(256) k_pair(int32_t n_warps, const int32_t* __
   }
 }
 
-// Mixed-precision pair kernel for systems of up to kSmallMax atoms: one CTA
-// per 256-atom chunk of a system stages the whole system's positions (hi/lo)
-// in shared memory with coalesced loads, so every neighbour gather is a
-// shared-memory read; list entries stream from global memory (coalesced,
-// evict-first, prefetched one block ahead).  Same arithmetic and summation
-// order as k_pair, so the two kernels give identical results.
+// Mixed-precision pair kernel for systems of up to kSmallMax atoms.  One CTA
+// per work item (built on the host, int4 in warp units):
+//   x = first staged warp, y = staged warps, z = first computed warp,
+//   w = computed warps (at most 8).
+// An item is a run of consecutive warps that may straddle systems; its staged
+// range holds every system those warps belong to (at most kSmallMax slots),
+// so every neighbour gather is a shared-memory read.  Staged record per atom: 24 B
+// (hi.xyz and lo.x as a float4, lo.yz as a float2), so that a 2048-atom
+// system takes 48 KB and four CTAs fit on an SM.  List entries stream from
+// global memory (coalesced, evict-first, prefetched one block ahead).  The
+// arithmetic and summation order are those of k_pair, so both kernels give
+// identical results.
 constexpr int kPairSmallThreads = 256;
+constexpr int kSmallRecord = 24;   // staged bytes per atom
 
 template <bool EW>
-__global__ void __launch_bounds__(kPairSmallThreads) k_pair_small(
-    int32_t n_chunks, const int32_t* __restrict__ chunk_sys, const int32_t* __restrict__ chunk_a0, SysArrays S,
-    SlotArrays A, const DevPot* __restrict__ pots, int64_t stride, int only_dirty, double* __restrict__ partial) {
-  extern __shared__ __align__(16) float4 spos[];   // [nmax] hi, then [nmax] lo
-  int c = blockIdx.x;
-  if (c >= n_chunks) return;
-  int s = chunk_sys[c];
-  if (only_dirty && !S.dirty[s]) return;
-  const int n = S.n_atoms[s], a0 = chunk_a0[c];
-  const int64_t seg = S.seg_start[s];
-  float4* sh = spos;
-  float4* sl = spos + n;
-  for (int i = threadIdx.x; i < n; i += kPairSmallThreads) { sh[i] = __ldg(A.xh + seg + i); sl[i] = __ldg(A.xl + seg + i); }
+__global__ void __launch_bounds__(kPairSmallThreads, 4) k_pair_small(
+    int32_t n_items, const int4* __restrict__ items, const int32_t* __restrict__ warp_sys, SysArrays S,
+    SlotArrays A, const DevPot* __restrict__ pots, int64_t stride, int filter, double* __restrict__ partial) {
+  extern __shared__ __align__(16) float4 sa[];   // [staged] (hi.x hi.y hi.z lo.x), then [staged] float2 (lo.y lo.z)
+  if ((int)blockIdx.x >= n_items) return;
+  const int4 W = items[blockIdx.x];
+  const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // leave before staging when no warp of the item is selected
+  const bool mine = wl < W.w && !pair_skip(S, warp_sys[W.z + wl], filter);
+  if (!__syncthreads_or(mine)) return;
+  const int64_t st0 = (int64_t)W.x * kWarp;
+  const int nst = W.y * kWarp;
+  float2* sb = reinterpret_cast<float2*>(sa + nst);
+#pragma unroll 4
+  for (int t = threadIdx.x; t < nst; t += kPairSmallThreads) {
+    float4 h = __ldg(A.xh + st0 + t), l = __ldg(A.xl + st0 + t);
+    sa[t] = make_float4(h.x, h.y, h.z, l.x);
+    sb[t] = make_float2(l.y, l.z);
+  }
   __syncthreads();
-  const int i = a0 + threadIdx.x, lane = threadIdx.x & 31;
+  if (!mine) return;
+  const int wg = W.z + wl;
+  const int s = warp_sys[wg];
+  const int64_t seg = S.seg_start[s];
+  const int64_t k = (int64_t)wg * kWarp + lane;
+  const int i = (int)(k - seg);
+  const int n = S.n_atoms[s];
   const bool valid = i < n;
-  const int64_t k = seg + i;
+  const float4* ha = sa + (seg - st0);
+  const float2* hb = sb + (seg - st0);
   const DevPot P = pots[S.pot[s]];
   const float4* tab = S.shift + 2 * (int64_t)s * kNCodes;
   const int nn = valid ? A.nn[k] : 0;
-  float4 xi = valid ? sh[i] : make_float4(0, 0, 0, 0), li = valid ? sl[i] : make_float4(0, 0, 0, 0);
+  const float4 xi = valid ? ha[i] : make_float4(0, 0, 0, 0);
+  const float2 li = valid ? hb[i] : make_float2(0, 0);
   float f0 = 0.f, f1 = 0.f, f2 = 0.f, e = 0.f, w0 = 0.f, w1 = 0.f, w2 = 0.f, w3 = 0.f, w4 = 0.f, w5 = 0.f;
   auto one = [&](uint32_t ent) {
     int code = (int)(ent >> kJBits);
     int j = (int)(ent & kJMask);
-    float4 xj = sh[j], lj = sl[j];
+    float4 xj = ha[j];
+    float2 lj = hb[j];
     float a0_ = xj.x - xi.x, a1_ = xj.y - xi.y, a2_ = xj.z - xi.z;
-    float b0 = lj.x - li.x, b1 = lj.y - li.y, b2 = lj.z - li.z;
+    float b0 = xj.w - xi.w, b1 = lj.x - li.x, b2 = lj.y - li.y;
     if (code != kCenter) {
       float4 th = __ldg(tab + 2 * code), tl = __ldg(tab + 2 * code + 1);
       a0_ += th.x; a1_ += th.y; a2_ += th.z;
@@ -202,15 +224,12 @@ __global__ void __launch_bounds__(kPairSmallThreads) k_pair_small(
   }
   for (; q < nn; q++) one(__ldcs(lp + (int64_t)q * stride));
   if (valid) A.F[k] = make_float4(f0, f1, f2, e);
-  if (EW) {
-    // one FP64 partial per global warp of the system (warps past the padded end do not exist)
-    int wl = (a0 + (threadIdx.x & ~31));
-    int npad = (n + kWarp - 1) / kWarp * kWarp;
+  if (EW) {   // one FP64 partial per warp (every computed warp lies inside its system's padded segment)
     double v[7] = {(double)e, (double)w0, (double)w1, (double)w2, (double)w3, (double)w4, (double)w5};
 #pragma unroll
     for (int cc = 0; cc < 7; cc++) {
       double t = warp_sum(v[cc]);
-      if (lane == 0 && wl < npad) partial[((seg + wl) / kWarp) * kPartialStride + cc] = t;
+      if (lane == 0) partial[(int64_t)wg * kPartialStride + cc] = t;
     }
   }
 }

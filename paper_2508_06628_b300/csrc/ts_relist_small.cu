@@ -1,24 +1,30 @@
 // ts_relist_small.cu -- re-listing in two launches for every flagged system:
 // (A) k_relist_small: one CTA per flagged small system (n <= kSmallMax) bins
 //     and sorts the system in shared memory:
-//   1. wrap positions into the cell (FP64), bin them, count per bin;
+//   1. wrap positions into the cell (by a whole lattice vector, from the
+//      image-shift table), bin them, count per bin;
 //   2. exclusive scan of the bin counts; provisional scatter; canonical rank
 //      inside each bin (ascending caller index, the same order as the
 //      multi-kernel path of ts_neighbor.cu used for larger systems);
 //   3. move the per-slot state into the new order (the CTA owns the whole
 //      segment, so a barrier separates all reads from all writes) and
 //      publish the bin starts in the layout the multi-kernel path uses.
-// (B) k_build_list_warp: the Verlet list of every flagged system, one warp
-//     per 32 sorted atoms: the warp walks the union of its lanes' stencils,
-//     stages each bin's atoms through shared memory in coalesced chunks of
-//     32, and every lane tests its own atom against each staged candidate
-//     (broadcast reads).  Each lane visits its stencil bins in the same order
-//     as a per-atom loop would, so the list order is canonical.
+//     One extra CTA writes the work table of (B): the flagged systems in
+//     system order, with the exclusive prefix of their warps.
+// (B) k_build_list_warp: the Verlet list of every atom of those systems, one
+//     warp per 32 sorted atoms: the warp walks the union of its lanes'
+//     stencils, stages each bin's atoms through shared memory in coalesced
+//     chunks of 32, and every lane tests its own atom against each staged
+//     candidate (broadcast reads, so the loads and the image shift of a
+//     candidate are shared by 32 atoms).  Each lane visits its stencil bins
+//     in the same order as a per-atom loop would, so the list order is
+//     canonical.
 #include "ts_kernels.cuh"
 
 namespace ts {
 
 constexpr int kSmallThreads = 512;
+constexpr int kBuildCtasPerSm = 5;   // grid of k_build_list_warp: resident CTAs of 128 threads per SM (96 registers)
 
 struct SmallSmem {
   int32_t bin_old[kSmallMax];
@@ -63,14 +69,48 @@ __device__ int block_exclusive_scan(int32_t* a, int n, int32_t* warp_tot) {
   return n > 0 ? s_total : 0;
 }
 
+// Work table of k_build_list_warp (one CTA): entries e = 0..ne-1 are the
+// flagged systems in system order; tab_base[e] is the number of
+// their warps (32-slot groups) before entry e, tab_base[ne] the total;
+// tab_n = {ne, 0}, the second word being the build kernel's work counter.
+__device__ void relist_table(int32_t B, const SysArrays& S, SmallSmem& sm, int32_t* tab_sys, int32_t* tab_base,
+                             int32_t* tab_n) {
+  const int t = threadIdx.x;
+  int ecarry = 0, acarry = 0;
+  for (int c0 = 0; c0 < B; c0 += kSmallMax) {
+    const int m = min(kSmallMax, B - c0);
+    for (int i = t; i < m; i += kSmallThreads) {
+      int s = c0 + i;
+      bool f = need_relist(S, s);
+      sm.tmp[i] = f;
+      sm.start[i] = f;
+      sm.fill[i] = f ? S.warp_end[s] - S.warp_start[s] : 0;
+    }
+    __syncthreads();
+    int ne = block_exclusive_scan(sm.start, m, sm.warp_tot);
+    int na = block_exclusive_scan(sm.fill, m, sm.warp_tot);
+    for (int i = t; i < m; i += kSmallThreads)
+      if (sm.tmp[i]) {
+        tab_sys[ecarry + sm.start[i]] = c0 + i;
+        tab_base[ecarry + sm.start[i]] = acarry + sm.fill[i];
+      }
+    ecarry += ne;
+    acarry += na;
+    __syncthreads();
+  }
+  if (t == 0) { tab_base[ecarry] = acarry; tab_n[0] = ecarry; tab_n[1] = 0; }   // tab_n[1]: next atom to build
+}
+
 template <bool F64>
 __global__ void __launch_bounds__(kSmallThreads, 1)
 k_relist_small(int32_t B, SysArrays S, SlotArrays A, int64_t stride, int move_fire, int32_t* cstart, int32_t* count,
-               const DevPot* __restrict__ pots, int32_t max_nbrs, int32_t* err) {
+               const DevPot* __restrict__ pots, int32_t max_nbrs, int32_t* err, int32_t* tab_sys, int32_t* tab_base,
+               int32_t* tab_n) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SmallSmem& sm = *reinterpret_cast<SmallSmem*>(smem_raw);
   int s = blockIdx.x;
-  if (s >= B || !need_relist(S, s)) return;
+  if (s == B) { relist_table(B, S, sm, tab_sys, tab_base, tab_n); return; }   // the extra CTA
+  if (s > B || !need_relist(S, s)) return;
   int n = S.n_atoms[s];
   if (n > kSmallMax) return;
   int t = threadIdx.x;
@@ -85,32 +125,43 @@ k_relist_small(int32_t B, SysArrays S, SlotArrays A, int64_t stride, int move_fi
   // 1. wrap, bin, count
   for (int i = t; i < n; i += kSmallThreads) {
     int64_t k = seg + i;
-    double x[3];
-    if constexpr (F64) {
-      for (int c = 0; c < 3; c++) x[c] = A.xd[3 * k + c];
-    } else {
-      float4 hi = A.xh[k], lo = A.xl[k];
-      x[0] = (double)hi.x + lo.x; x[1] = (double)hi.y + lo.y; x[2] = (double)hi.z + lo.z;
-    }
-    double f[3];
     int kb[3], nbv[3] = {nb0, nb1, nb2};
-    for (int a = 0; a < 3; a++) {
-      double v = x[0] * g[a] + x[1] * g[3 + a] + x[2] * g[6 + a];
-      v -= floor(v);
-      if (v >= 1.0) v = 0.0;
-      f[a] = v;
-      int q = (int)(v * nbv[a]);
-      kb[a] = q >= nbv[a] ? nbv[a] - 1 : (q < 0 ? 0 : q);
+    bool done = false;
+    if constexpr (!F64) {
+      float4 hi = A.xh[k], lo = A.xl[k];
+      if (wrap_bin_mixed(S, s, hi, lo, kb)) {
+        A.tmp_f0[k] = hi; A.tmp_f1[k] = lo;
+        done = true;
+      }
     }
-    double xw[3];
-    for (int c = 0; c < 3; c++) xw[c] = f[0] * h[c] + f[1] * h[3 + c] + f[2] * h[6 + c];
-    if constexpr (F64) {
-      for (int c = 0; c < 3; c++) A.tmp_d0[3 * k + c] = xw[c];
-    } else {
-      float4 hi, lo;
-      split_pos(xw[0], hi.x, lo.x); split_pos(xw[1], hi.y, lo.y); split_pos(xw[2], hi.z, lo.z);
-      hi.w = 0.f; lo.w = 0.f;
-      A.tmp_f0[k] = hi; A.tmp_f1[k] = lo;
+    if (!done) {
+      // FP64 route: FP64 positions, or an atom more than kMaxReach cells away
+      double x[3];
+      if constexpr (F64) {
+        for (int c = 0; c < 3; c++) x[c] = A.xd[3 * k + c];
+      } else {
+        float4 hi = A.xh[k], lo = A.xl[k];
+        x[0] = (double)hi.x + lo.x; x[1] = (double)hi.y + lo.y; x[2] = (double)hi.z + lo.z;
+      }
+      double f[3];
+      for (int a = 0; a < 3; a++) {
+        double v = x[0] * g[a] + x[1] * g[3 + a] + x[2] * g[6 + a];
+        v -= floor(v);
+        if (v >= 1.0) v = 0.0;
+        f[a] = v;
+        int q = (int)(v * nbv[a]);
+        kb[a] = q >= nbv[a] ? nbv[a] - 1 : (q < 0 ? 0 : q);
+      }
+      double xw[3];
+      for (int c = 0; c < 3; c++) xw[c] = f[0] * h[c] + f[1] * h[3 + c] + f[2] * h[6 + c];
+      if constexpr (F64) {
+        for (int c = 0; c < 3; c++) A.tmp_d0[3 * k + c] = xw[c];
+      } else {
+        float4 hi, lo;
+        split_pos(xw[0], hi.x, lo.x); split_pos(xw[1], hi.y, lo.y); split_pos(xw[2], hi.z, lo.z);
+        hi.w = 0.f; lo.w = 0.f;
+        A.tmp_f0[k] = hi; A.tmp_f1[k] = lo;
+      }
     }
     int b = (kb[2] * nb1 + kb[1]) * nb0 + kb[0];
     sm.bin_old[i] = b;
@@ -187,92 +238,22 @@ k_relist_small(int32_t B, SysArrays S, SlotArrays A, int64_t stride, int move_fi
     cstart[boff + c] = (int32_t)(coff + sm.start[c]);
     count[boff + c] = sm.start[c + 1] - sm.start[c];
   }
-  if (!is_tiny(n, nbins)) return;
-  // 4. tiny systems (few bins, many images per atom): Verlet list here, one
-  //    warp per atom, lanes splitting the candidates; a ballot and prefix
-  //    count append hits in candidate order, so the list order is the same
-  //    as a sequential loop's
-  __syncthreads();
-  const DevPot& P = pots[S.pot[s]];
-  const int m0 = S.reach[3 * s], m1 = S.reach[3 * s + 1], m2 = S.reach[3 * s + 2];
-  const int lane = t & 31, wid = t >> 5;
-  for (int d = wid; d < n; d += kSmallThreads / 32) {
-    int64_t k = seg + d;
-    int lb = sm.tmp[d];
-    int kx = lb % nb0, ky = (lb / nb0) % nb1, kz = lb / (nb0 * nb1);
-    float4 hi, lo;
-    double xi[3];
-    if constexpr (F64) { for (int c = 0; c < 3; c++) xi[c] = A.xd[3 * k + c]; }
-    else { hi = A.xh[k]; lo = A.xl[k]; }
-    int cnt = 0;
-    for (int dz = -m2; dz <= m2; dz++) {
-      int zz = kz + dz, iz = zz >= 0 ? zz / nb2 : -((-zz + nb2 - 1) / nb2), cz = zz - iz * nb2;
-      for (int dy = -m1; dy <= m1; dy++) {
-        int yy = ky + dy, iy = yy >= 0 ? yy / nb1 : -((-yy + nb1 - 1) / nb1), cy = yy - iy * nb1;
-        for (int dx = -m0; dx <= m0; dx++) {
-          int xx = kx + dx, ix = xx >= 0 ? xx / nb0 : -((-xx + nb0 - 1) / nb0), cx = xx - ix * nb0;
-          int code = img_code(ix, iy, iz);
-          int cb = (cz * nb1 + cy) * nb0 + cx;
-          int q0 = sm.start[cb], q1 = sm.start[cb + 1];
-          int64_t ti = (int64_t)s * kNCodes + code;
-          for (int qb = q0; qb < q1; qb += 32) {
-            int q = qb + lane;
-            bool hit = false;
-            if (q < q1 && !(q == d && code == kCenter)) {
-              if constexpr (F64) {
-                const double* sd = S.shiftd + 3 * ti;
-                double d0 = A.xd[3 * (seg + q)] + sd[0] - xi[0], d1 = A.xd[3 * (seg + q) + 1] + sd[1] - xi[1],
-                       d2 = A.xd[3 * (seg + q) + 2] + sd[2] - xi[2];
-                hit = d0 * d0 + d1 * d1 + d2 * d2 < P.rlist2d;
-              } else {
-                float4 sh = S.shift[2 * ti], sl = S.shift[2 * ti + 1];
-                float4 xj = A.xh[seg + q], lj = A.xl[seg + q];
-                float d0 = (xj.x + (sh.x - hi.x)) + (lj.x + (sl.x - lo.x));
-                float d1 = (xj.y + (sh.y - hi.y)) + (lj.y + (sl.y - lo.y));
-                float d2 = (xj.z + (sh.z - hi.z)) + (lj.z + (sl.z - lo.z));
-                hit = d0 * d0 + d1 * d1 + d2 * d2 < P.rlist2f;
-              }
-            }
-            unsigned bal = __ballot_sync(0xffffffffu, hit);
-            if (hit) {
-              int pos = cnt + __popc(bal & ((1u << lane) - 1u));
-              if (pos < max_nbrs) A.nbr[pos * stride + k] = (uint32_t)q | ((uint32_t)code << kJBits);
-            }
-            cnt += __popc(bal);
-          }
-        }
-      }
-    }
-    if (lane == 0) {
-      if (cnt > max_nbrs) { atomicOr(err, kErrNeighborOverflow); cnt = max_nbrs; }
-      A.nn[k] = cnt;
-      if constexpr (F64) { for (int c = 0; c < 3; c++) A.xrd[3 * k + c] = xi[c]; }
-      else { A.xrh[k] = hi; A.xrl[k] = lo; }
-    }
-  }
 }
 
 __device__ __forceinline__ int floor_div(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
 
-// (B) Verlet list of every flagged system; one warp per 32 sorted atoms.
+// One warp: the lists of the 32 slots of warp `wi` of system `s` (a flagged
+// system).  sh_h / sh_l / sh_d: this warp's staging area.
 template <bool F64>
-__global__ void __launch_bounds__(128) k_build_list_warp(int32_t n_warps, const int32_t* __restrict__ warp_sys,
-                                                         SysArrays S, SlotArrays A, const int32_t* __restrict__ cstart,
-                                                         const int32_t* __restrict__ count,
-                                                         const DevPot* __restrict__ pots, int32_t max_nbrs,
-                                                         int64_t stride, int32_t* err) {
-  __shared__ float4 sh_h[4][32], sh_l[4][32];
-  __shared__ double sh_d[4][32][3];
-  int w = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
-  int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  if (w >= n_warps) return;
-  int s = warp_sys[w];
-  if (!need_relist(S, s)) return;   // warp-uniform
+__device__ void build_warp(int s, int wi, const SysArrays& S, const SlotArrays& A, const int32_t* __restrict__ cstart,
+                           const int32_t* __restrict__ count, const DevPot* __restrict__ pots, int32_t max_nbrs,
+                           int64_t stride, int32_t* err, float4* sh_h, float4* sh_l, double (*sh_d)[3]) {
+  const int lane = threadIdx.x & 31;
+  const int w = S.warp_start[s] + wi;
   int64_t k = (int64_t)w * kWarp + lane;
   bool valid = A.perm[k] >= 0;   // lane 0 of a warp is always a real atom
   const DevPot& P = pots[S.pot[s]];
   const int nb0 = S.nb[3 * s], nb1 = S.nb[3 * s + 1], nb2 = S.nb[3 * s + 2];
-  if (is_tiny(S.n_atoms[s], nb0 * nb1 * nb2)) return;   // listed by k_relist_small
   const int m0 = S.reach[3 * s], m1 = S.reach[3 * s + 1], m2 = S.reach[3 * s + 2];
   int64_t seg = S.seg_start[s];
   int boff = S.bin_off[s];
@@ -339,29 +320,40 @@ __global__ void __launch_bounds__(128) k_build_list_warp(int32_t n_warps, const 
         for (int base = 0; base < c; base += 32) {
           int q = base + lane;
           if (q < c) {
-            if constexpr (F64) { for (int cc = 0; cc < 3; cc++) sh_d[wib][lane][cc] = A.xd[3 * (b0 + q) + cc]; }
-            else { sh_h[wib][lane] = A.xh[b0 + q]; sh_l[wib][lane] = A.xl[b0 + q]; }
+            if constexpr (F64) { for (int cc = 0; cc < 3; cc++) sh_d[lane][cc] = A.xd[3 * (b0 + q) + cc]; }
+            else { sh_h[lane] = A.xh[b0 + q]; sh_l[lane] = A.xl[b0 + q]; }
           }
           __syncwarp();
           int nc = min(32, c - base);
           if (in) {
-            for (int tq = 0; tq < nc; tq++) {
-              int64_t j = b0 + base + tq;
-              if (j == k && code == kCenter) continue;
+            const uint32_t cbits = (uint32_t)code << kJBits;
+            const int j0 = (int)(b0 - seg) + base;                            // local index of candidate 0
+            const int self = code == kCenter ? (int)(k - b0) - base : -1;     // the atom itself, if staged here
+            auto test = [&](int tq) -> bool {
               bool hit;
               if constexpr (F64) {
-                double d0 = sh_d[wib][tq][0] + s0, d1 = sh_d[wib][tq][1] + s1, d2 = sh_d[wib][tq][2] + s2;
+                double d0 = sh_d[tq][0] + s0, d1 = sh_d[tq][1] + s1, d2 = sh_d[tq][2] + s2;
                 hit = d0 * d0 + d1 * d1 + d2 * d2 < P.rlist2d;
               } else {
-                float4 xj = sh_h[wib][tq], lj = sh_l[wib][tq];
+                float4 xj = sh_h[tq], lj = sh_l[tq];
                 float d0 = (xj.x + a0) + (lj.x + e0), d1 = (xj.y + a1) + (lj.y + e1), d2 = (xj.z + a2) + (lj.z + e2);
                 hit = d0 * d0 + d1 * d1 + d2 * d2 < P.rlist2f;
               }
+              return hit && tq != self;
+            };
+            auto append = [&](bool hit, int tq) {
               if (hit) {
-                if (cnt < max_nbrs) A.nbr[cnt * stride + k] = (uint32_t)(j - seg) | ((uint32_t)code << kJBits);
+                if (cnt < max_nbrs) A.nbr[cnt * stride + k] = (uint32_t)(j0 + tq) | cbits;
                 cnt++;
               }
+            };
+            // four independent distance tests per round, appended in candidate order
+            int tq = 0;
+            for (; tq + 4 <= nc; tq += 4) {
+              bool h0 = test(tq), h1 = test(tq + 1), h2 = test(tq + 2), h3 = test(tq + 3);
+              append(h0, tq); append(h1, tq + 1); append(h2, tq + 2); append(h3, tq + 3);
             }
+            for (; tq < nc; tq++) append(test(tq), tq);
           }
           __syncwarp();
         }
@@ -373,6 +365,35 @@ __global__ void __launch_bounds__(128) k_build_list_warp(int32_t n_warps, const 
     A.nn[k] = cnt;
     if constexpr (F64) { for (int c = 0; c < 3; c++) A.xrd[3 * k + c] = xi[c]; }
     else { A.xrh[k] = hi; A.xrl[k] = lo; }
+  }
+}
+
+// (B) Verlet lists of the work table's warps: one warp per 32 sorted atoms,
+// warps taken from a counter (a fixed, resident grid; consecutive grabs are
+// neighbouring atoms, and CTAs that start late beside another kernel just
+// take less work).
+template <bool F64>
+__global__ void __launch_bounds__(128, kBuildCtasPerSm) k_build_list_warp(
+    SysArrays S, SlotArrays A, const int32_t* __restrict__ tab_sys, const int32_t* __restrict__ tab_base,
+    int32_t* __restrict__ tab_n, const int32_t* __restrict__ cstart, const int32_t* __restrict__ count,
+    const DevPot* __restrict__ pots, int32_t max_nbrs, int64_t stride, int32_t* err) {
+  __shared__ float4 sh_h[4][32], sh_l[4][32];
+  __shared__ double sh_d[4][32][3];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int ne = tab_n[0];
+  const int total = tab_base[ne];
+  for (;;) {
+    int t = 0;
+    if (lane == 0) t = atomicAdd(tab_n + 1, 1);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t >= total) break;
+    int e0 = 0, e1 = ne - 1;   // last entry with tab_base[e] <= t (warp-uniform search)
+    while (e0 < e1) {
+      int mid = (e0 + e1 + 1) >> 1;
+      if (tab_base[mid] <= t) e0 = mid; else e1 = mid - 1;
+    }
+    build_warp<F64>(tab_sys[e0], t - tab_base[e0], S, A, cstart, count, pots, max_nbrs, stride, err, sh_h[wib], sh_l[wib],
+                    sh_d[wib]);
   }
 }
 

@@ -29,8 +29,11 @@ static void md_body(ts_batch* b, cudaStream_t st, const ts_md_params* p, int n_s
         k_md_kick_drift<false, 1><<<g, 256, 0, st>>>(b->Npad, b->S, b->A, b->d_pots, kick, p->dt, c1, p->seed, b->d_step, k);
     }
     b->launches++;
-    relist(b, st, false);
-    pair(b, st, need_e && k == n_steps - 1, false);
+    bool ew = need_e && k == n_steps - 1;
+    if (!relist_pair_overlapped(b, st, false, ew)) {
+      relist(b, st, false);
+      pair(b, st, ew, kPairAll);
+    }
   }
   int blocks = (int)(((int64_t)b->nwarps * 32 + 127) / 128);
   if (b->f64) k_md_final<true><<<blocks, 128, 0, st>>>(b->nwarps, b->S, b->A, n_steps > 0 ? 0.5 * p->dt : 0.0, b->d_partial);
@@ -65,7 +68,7 @@ ts_status md_loop(ts_batch* b, cudaStream_t st, const ts_md_params* p, int n_ste
       b->launches = l0;
       cudaError_t e = cudaStreamEndCapture(st, &graph);
       cudaGraphExec_t exec = nullptr;
-      if (e == cudaSuccess && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess) {
+      if (e == cudaSuccess && cudaGraphInstantiate(&exec, graph, cudaGraphInstantiateFlagUseNodePriority) == cudaSuccess) {
         cudaGraphDestroy(graph);
         ts_graph_entry ge;
         ge.kind = 0; ge.n_steps = n_steps; ge.md_kind = p->kind; ge.need_e = need_e; ge.dt = p->dt; ge.c1 = c1;
