@@ -120,6 +120,8 @@ extern "C" ts_status ts_batch_create(const ts_batch_config* cfg, const ts_potent
       if (!(f > 0 && f <= 1)) f = 1.0;
       D.soon2 = f * f;
     }
+    D.rlist_in2f = (float)((D.rlist - kListBand) * (D.rlist - kListBand));
+    D.rlist_out2f = (float)((D.rlist + kListBand) * (D.rlist + kListBand));
     D.half_skin2f = (float)(0.25 * P.skin * P.skin);
     D.soon_half_skin2f = (float)(D.soon2 * 0.25 * P.skin * P.skin);
     b->rc[q] = rc;
@@ -320,15 +322,24 @@ ts_status derive_topology(ts_batch* b, const ts_state* s, cudaStream_t st) {
     if (n[k] < 1) return fail(b, TS_ERR_INVALID_ARG, "empty system");
     if (n[k] > (int64_t)kJMask) return fail(b, TS_ERR_UNSUPPORTED, "system larger than 2^22 atoms");
     if (pot[k] < 0 || pot[k] >= b->n_pots) return fail(b, TS_ERR_INVALID_ARG, "pot_idx out of range");
+    bin_off[k] = (int32_t)bins;
+    bin_cap[k] = std::max<int32_t>(27, n[k]);
+    bins += bin_cap[k];
+  }
+  // Slot layout order: by potential, larger systems first.  The pair
+  // kernel's work items are runs of consecutive warps, so they then hold
+  // warps of one potential and similar cost.  A system's results do not
+  // depend on where its segment lies.
+  std::vector<int32_t> lay(B);
+  for (int k = 0; k < B; k++) lay[k] = k;
+  std::stable_sort(lay.begin(), lay.end(), [&](int a, int c) { return pot[a] != pot[c] ? pot[a] < pot[c] : n[a] > n[c]; });
+  for (int k : lay) {
     seg[k] = slot;
     int64_t npad = (n[k] + 31) / 32 * 32;
     ws[k] = (int32_t)(slot / 32);
     slot += npad;
     we[k] = (int32_t)(slot / 32);
     for (int w = ws[k]; w < we[k]; w++) warp_sys.push_back(k);
-    bin_off[k] = (int32_t)bins;
-    bin_cap[k] = std::max<int32_t>(27, n[k]);
-    bins += bin_cap[k];
   }
   if (slot > b->Ncap || bins > b->Ccap) return fail(b, TS_ERR_BUDGET, "padded layout exceeds capacity");
   b->B = B; b->N = N; b->Npad = slot; b->nwarps = (int32_t)(slot / 32); b->nbins = bins;
@@ -354,9 +365,10 @@ ts_status derive_topology(ts_batch* b, const ts_state* s, cudaStream_t st) {
       count = 0; wk = 0;
     };
     int s_prev = -1;
-    for (int k = 0; k < B; k++) {
+    for (int k : lay) {   // systems in slot order
       if (n[k] > kSmallMax) { flush(s_prev); continue; }
-      double c = b->pots[pot[k]].kind == TS_SOFT_SPHERE ? 0.5 : 1.0;   // soft spheres: about half the list length
+      // relative cost of a warp-entry: soft-sphere lists are about half as long
+      double c = b->pots[pot[k]].kind == TS_SOFT_SPHERE ? 0.5 : (b->pots[pot[k]].kind == TS_MORSE ? 1.1 : 1.0);
       for (int w = ws[k]; w < we[k]; w++) {
         if (count > 0 && (count == wpi || we[k] - ws[s0] > cap)) flush(s_prev);
         if (count == 0) { first = w; s0 = k; }

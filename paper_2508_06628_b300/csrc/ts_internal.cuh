@@ -23,6 +23,9 @@ namespace ts {
 
 constexpr int kWarp = 32;
 constexpr float kGrid = 4096.0f;          // 2^12
+// Half-width of the shell around the list radius where the hi-only distance
+// (off by at most 3 * 2^-13 * sqrt(3) = 6.3e-4 A) cannot decide a list test.
+constexpr double kListBand = 1e-3;
 constexpr float kInvGrid = 1.0f / 4096.0f;
 constexpr double kMaxCoord = 2000.0;      // |x| bound of the hi/lo representation
 constexpr int kJBits = 22;                // neighbour entry: j (22 bits) | image code (10 bits)
@@ -57,6 +60,7 @@ struct DevPot {
   float rc2f, phicf, rlist2f;
   float sinvf;    // 1/sigma in FP32 (soft sphere)
   float half_skin2f, soon_half_skin2f;   // (skin/2)^2 and soon^2 (skin/2)^2, FP32 (mixed skin check)
+  float rlist_in2f, rlist_out2f;         // (rlist -+ 1e-3 A)^2: certain hit / miss of the hi-only list test
   double pd[3];
   double rc2d, phicd, rlist, rlist2d, skin;
   double soon2;   // squared hysteresis factor
@@ -162,6 +166,29 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float a) {
 template <typename T> struct PotMath;
 
 template <> struct PotMath<float> {
+  // one potential kind, no branches (K known at compile time)
+  template <int K>
+  static __device__ __forceinline__ void eval_k(const DevPot& P, float r2, float& phi, float& fr) {
+    if constexpr (K == TS_LJ) {
+      float ri2 = __fdividef(1.0f, r2);   // ~2 ulp; the LJ terms are well conditioned
+      float s2 = P.pf[0] * P.pf[0] * ri2;
+      float s6 = s2 * s2 * s2, s12 = s6 * s6;
+      phi = 4.0f * P.pf[1] * (s12 - s6);
+      fr = -24.0f * P.pf[1] * ri2 * (2.0f * s12 - s6);
+    } else if constexpr (K == TS_MORSE) {
+      float r = sqrtf(r2);
+      float e = __expf(P.pf[1] * (P.pf[2] - r));
+      phi = P.pf[0] * (e * e - 2.0f * e);
+      fr = 2.0f * P.pf[1] * P.pf[0] * e * (1.0f - e) * rsqrtf(r2);
+    } else {
+      float ri = rsqrtf(r2);
+      float t = fmaf(-r2 * ri, P.sinvf, 1.0f);
+      float al = P.pf[2];
+      float ta1 = (al == 2.0f) ? t : __powf(t, al - 1.0f);
+      phi = P.pf[1] / al * ta1 * t;
+      fr = -P.pf[1] * P.sinvf * ta1 * ri;
+    }
+  }
   static __device__ __forceinline__ void eval(const DevPot& P, float r2, float& phi, float& fr) {
     if (P.kind == TS_LJ) {
       float ri2 = __fdividef(1.0f, r2);   // ~2 ulp; the LJ terms are well conditioned

@@ -9,6 +9,8 @@
 // list gives every atom its own force); a warp holds 32 atoms of one system,
 // so energy and virial go through warp shuffles into one FP64 partial per
 // warp, and a second kernel sums each system's warps in a fixed order.
+#include <type_traits>
+
 #include "ts_kernels.cuh"
 
 namespace ts {
@@ -183,46 +185,57 @@ __global__ void __launch_bounds__(kPairSmallThreads, 4) k_pair_small(
   const float4 xi = valid ? ha[i] : make_float4(0, 0, 0, 0);
   const float2 li = valid ? hb[i] : make_float2(0, 0);
   float f0 = 0.f, f1 = 0.f, f2 = 0.f, e = 0.f, w0 = 0.f, w1 = 0.f, w2 = 0.f, w3 = 0.f, w4 = 0.f, w5 = 0.f;
-  auto one = [&](uint32_t ent) {
-    int code = (int)(ent >> kJBits);
-    int j = (int)(ent & kJMask);
-    float4 xj = ha[j];
-    float2 lj = hb[j];
-    float a0_ = xj.x - xi.x, a1_ = xj.y - xi.y, a2_ = xj.z - xi.z;
-    float b0 = xj.w - xi.w, b1 = lj.x - li.x, b2 = lj.y - li.y;
-    if (code != kCenter) {
-      float4 th = __ldg(tab + 2 * code), tl = __ldg(tab + 2 * code + 1);
+  // The potential kind is uniform over a warp (one system): one loop per kind,
+  // with no branch inside an entry.  Every entry evaluates the potential and
+  // selects a zero force factor beyond rc (fmaf(0, d, f) == f, so the sums are
+  // those of the branching form), which lets the four entries of a round
+  // overlap.
+  auto run = [&](auto kind) {
+    constexpr int K = decltype(kind)::value;
+    auto one = [&](uint32_t ent) {
+      const int code = (int)(ent >> kJBits);
+      const int j = (int)(ent & kJMask);
+      const bool img = code != kCenter;
+      const float4 zero = make_float4(0, 0, 0, 0);
+      const float4 th = img ? __ldg(tab + 2 * code) : zero, tl = img ? __ldg(tab + 2 * code + 1) : zero;
+      const float4 xj = ha[j];
+      const float2 lj = hb[j];
+      float a0_ = xj.x - xi.x, a1_ = xj.y - xi.y, a2_ = xj.z - xi.z;
+      float b0 = xj.w - xi.w, b1 = lj.x - li.x, b2 = lj.y - li.y;
       a0_ += th.x; a1_ += th.y; a2_ += th.z;
       b0 += tl.x; b1 += tl.y; b2 += tl.z;
-    }
-    float d0 = a0_ + b0, d1 = a1_ + b1, d2 = a2_ + b2;
-    float r2 = fmaf(d0, d0, fmaf(d1, d1, d2 * d2));
-    if (r2 < P.rc2f) {
+      const float d0 = a0_ + b0, d1 = a1_ + b1, d2 = a2_ + b2;
+      const float r2 = fmaf(d0, d0, fmaf(d1, d1, d2 * d2));
+      const bool in = r2 < P.rc2f;
       float phi, fr;
-      PotMath<float>::eval(P, r2, phi, fr);
+      PotMath<float>::eval_k<K>(P, r2, phi, fr);
+      fr = in ? fr : 0.f;
       f0 = fmaf(fr, d0, f0); f1 = fmaf(fr, d1, f1); f2 = fmaf(fr, d2, f2);
       if (EW) {
-        e += 0.5f * (phi - P.phicf);
+        e += in ? 0.5f * (phi - P.phicf) : 0.f;
         float hf = 0.5f * fr;
         float h0 = hf * d0, h1 = hf * d1;
         w0 = fmaf(h0, d0, w0); w1 = fmaf(h1, d1, w1); w2 = fmaf(hf * d2, d2, w2);
         w3 = fmaf(h0, d1, w3); w4 = fmaf(h0, d2, w4); w5 = fmaf(h1, d2, w5);
       }
+    };
+    const uint32_t* lp = A.nbr + k;
+    int q = 0;
+    uint32_t n0 = 0, n1 = 0, n2 = 0, n3 = 0;
+    if (nn >= 4) { n0 = __ldcs(lp); n1 = __ldcs(lp + stride); n2 = __ldcs(lp + 2 * stride); n3 = __ldcs(lp + 3 * stride); }
+    for (; q + 4 <= nn; q += 4) {
+      uint32_t e0 = n0, e1 = n1, e2 = n2, e3 = n3;
+      if (q + 8 <= nn) {
+        const uint32_t* np = lp + (int64_t)(q + 4) * stride;
+        n0 = __ldcs(np); n1 = __ldcs(np + stride); n2 = __ldcs(np + 2 * stride); n3 = __ldcs(np + 3 * stride);
+      }
+      one(e0); one(e1); one(e2); one(e3);
     }
+    for (; q < nn; q++) one(__ldcs(lp + (int64_t)q * stride));
   };
-  const uint32_t* lp = A.nbr + k;
-  int q = 0;
-  uint32_t n0 = 0, n1 = 0, n2 = 0, n3 = 0;
-  if (nn >= 4) { n0 = __ldcs(lp); n1 = __ldcs(lp + stride); n2 = __ldcs(lp + 2 * stride); n3 = __ldcs(lp + 3 * stride); }
-  for (; q + 4 <= nn; q += 4) {
-    uint32_t e0 = n0, e1 = n1, e2 = n2, e3 = n3;
-    if (q + 8 <= nn) {
-      const uint32_t* np = lp + (int64_t)(q + 4) * stride;
-      n0 = __ldcs(np); n1 = __ldcs(np + stride); n2 = __ldcs(np + 2 * stride); n3 = __ldcs(np + 3 * stride);
-    }
-    one(e0); one(e1); one(e2); one(e3);
-  }
-  for (; q < nn; q++) one(__ldcs(lp + (int64_t)q * stride));
+  if (P.kind == TS_LJ) run(std::integral_constant<int, TS_LJ>{});
+  else if (P.kind == TS_MORSE) run(std::integral_constant<int, TS_MORSE>{});
+  else run(std::integral_constant<int, TS_SOFT_SPHERE>{});
   if (valid) A.F[k] = make_float4(f0, f1, f2, e);
   if (EW) {   // one FP64 partial per warp (every computed warp lies inside its system's padded segment)
     double v[7] = {(double)e, (double)w0, (double)w1, (double)w2, (double)w3, (double)w4, (double)w5};

@@ -243,11 +243,11 @@ k_relist_small(int32_t B, SysArrays S, SlotArrays A, int64_t stride, int move_fi
 __device__ __forceinline__ int floor_div(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
 
 // One warp: the lists of the 32 slots of warp `wi` of system `s` (a flagged
-// system).  sh_h / sh_l / sh_d: this warp's staging area.
+// system).  sh_h / sh_d: this warp's staging area.
 template <bool F64>
 __device__ void build_warp(int s, int wi, const SysArrays& S, const SlotArrays& A, const int32_t* __restrict__ cstart,
                            const int32_t* __restrict__ count, const DevPot* __restrict__ pots, int32_t max_nbrs,
-                           int64_t stride, int32_t* err, float4* sh_h, float4* sh_l, double (*sh_d)[3]) {
+                           int64_t stride, int32_t* err, float4* sh_h, double (*sh_d)[3]) {
   const int lane = threadIdx.x & 31;
   const int w = S.warp_start[s] + wi;
   int64_t k = (int64_t)w * kWarp + lane;
@@ -321,7 +321,7 @@ __device__ void build_warp(int s, int wi, const SysArrays& S, const SlotArrays& 
           int q = base + lane;
           if (q < c) {
             if constexpr (F64) { for (int cc = 0; cc < 3; cc++) sh_d[lane][cc] = A.xd[3 * (b0 + q) + cc]; }
-            else { sh_h[lane] = A.xh[b0 + q]; sh_l[lane] = A.xl[b0 + q]; }
+            else sh_h[lane] = A.xh[b0 + q];   // lo parts only for the rare undecided tests
           }
           __syncwarp();
           int nc = min(32, c - base);
@@ -329,31 +329,65 @@ __device__ void build_warp(int s, int wi, const SysArrays& S, const SlotArrays& 
             const uint32_t cbits = (uint32_t)code << kJBits;
             const int j0 = (int)(b0 - seg) + base;                            // local index of candidate 0
             const int self = code == kCenter ? (int)(k - b0) - base : -1;     // the atom itself, if staged here
-            auto test = [&](int tq) -> bool {
-              bool hit;
-              if constexpr (F64) {
-                double d0 = sh_d[tq][0] + s0, d1 = sh_d[tq][1] + s1, d2 = sh_d[tq][2] + s2;
-                hit = d0 * d0 + d1 * d1 + d2 * d2 < P.rlist2d;
-              } else {
-                float4 xj = sh_h[tq], lj = sh_l[tq];
-                float d0 = (xj.x + a0) + (lj.x + e0), d1 = (xj.y + a1) + (lj.y + e1), d2 = (xj.z + a2) + (lj.z + e2);
-                hit = d0 * d0 + d1 * d1 + d2 * d2 < P.rlist2f;
-              }
-              return hit && tq != self;
-            };
             auto append = [&](bool hit, int tq) {
               if (hit) {
                 if (cnt < max_nbrs) A.nbr[cnt * stride + k] = (uint32_t)(j0 + tq) | cbits;
                 cnt++;
               }
             };
-            // four independent distance tests per round, appended in candidate order
-            int tq = 0;
-            for (; tq + 4 <= nc; tq += 4) {
-              bool h0 = test(tq), h1 = test(tq + 1), h2 = test(tq + 2), h3 = test(tq + 3);
-              append(h0, tq); append(h1, tq + 1); append(h2, tq + 2); append(h3, tq + 3);
+            if constexpr (F64) {
+              auto test = [&](int tq) -> bool {
+                double d0 = sh_d[tq][0] + s0, d1 = sh_d[tq][1] + s1, d2 = sh_d[tq][2] + s2;
+                return d0 * d0 + d1 * d1 + d2 * d2 < P.rlist2d && tq != self;
+              };
+              for (int tq = 0; tq < nc; tq++) append(test(tq), tq);
+            } else {
+              // hi parts (exact sum on the 2^-12 grid) decide every test but
+              // those in a thin shell around the list radius, which take the
+              // double-float test; four tests per round, straight-line unless
+              // one of them is undecided
+              auto rh2 = [&](int tq) {
+                const float4 xj = sh_h[tq];
+                const float h0 = xj.x + a0, h1 = xj.y + a1, h2 = xj.z + a2;
+                return fmaf(h0, h0, fmaf(h1, h1, h2 * h2));
+              };
+              auto exact = [&](int tq) {
+                const float4 xj = sh_h[tq];
+                const float4 lj = A.xl[b0 + base + tq];
+                const float d0 = (xj.x + a0) + (lj.x + e0), d1 = (xj.y + a1) + (lj.y + e1),
+                            d2 = (xj.z + a2) + (lj.z + e2);
+                return d0 * d0 + d1 * d1 + d2 * d2 < P.rlist2f;
+              };
+              const float in2 = P.rlist_in2f, out2 = P.rlist_out2f;
+              int tq = 0;
+              for (; tq + 4 <= nc; tq += 4) {
+                const float r0 = rh2(tq), r1 = rh2(tq + 1), r2 = rh2(tq + 2), r3 = rh2(tq + 3);
+                bool h0 = r0 < in2, h1 = r1 < in2, h2 = r2 < in2, h3 = r3 < in2;
+                const bool u0 = !h0 && r0 <= out2, u1 = !h1 && r1 <= out2, u2 = !h2 && r2 <= out2,
+                           u3 = !h3 && r3 <= out2;
+                if (u0 | u1 | u2 | u3) {
+                  if (u0) h0 = exact(tq);
+                  if (u1) h1 = exact(tq + 1);
+                  if (u2) h2 = exact(tq + 2);
+                  if (u3) h3 = exact(tq + 3);
+                }
+                h0 = h0 && tq != self; h1 = h1 && tq + 1 != self;
+                h2 = h2 && tq + 2 != self; h3 = h3 && tq + 3 != self;
+                const int c0 = cnt, c1 = c0 + h0, c2 = c1 + h1, c3 = c2 + h2;
+                cnt = c3 + h3;
+                uint32_t* out = A.nbr + k;
+                if (h0 && c0 < max_nbrs) out[c0 * stride] = (uint32_t)(j0 + tq) | cbits;
+                if (h1 && c1 < max_nbrs) out[c1 * stride] = (uint32_t)(j0 + tq + 1) | cbits;
+                if (h2 && c2 < max_nbrs) out[c2 * stride] = (uint32_t)(j0 + tq + 2) | cbits;
+                if (h3 && c3 < max_nbrs) out[c3 * stride] = (uint32_t)(j0 + tq + 3) | cbits;
+              }
+              for (; tq < nc; tq++) {
+                const float r = rh2(tq);
+                bool h = r < in2;
+                if (!h && r <= out2) h = exact(tq);
+                append(h && tq != self, tq);
+              }
             }
-            for (; tq < nc; tq++) append(test(tq), tq);
           }
           __syncwarp();
         }
@@ -377,7 +411,7 @@ __global__ void __launch_bounds__(128, kBuildCtasPerSm) k_build_list_warp(
     SysArrays S, SlotArrays A, const int32_t* __restrict__ tab_sys, const int32_t* __restrict__ tab_base,
     int32_t* __restrict__ tab_n, const int32_t* __restrict__ cstart, const int32_t* __restrict__ count,
     const DevPot* __restrict__ pots, int32_t max_nbrs, int64_t stride, int32_t* err) {
-  __shared__ float4 sh_h[4][32], sh_l[4][32];
+  __shared__ float4 sh_h[4][32];
   __shared__ double sh_d[4][32][3];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int ne = tab_n[0];
@@ -392,7 +426,7 @@ __global__ void __launch_bounds__(128, kBuildCtasPerSm) k_build_list_warp(
       int mid = (e0 + e1 + 1) >> 1;
       if (tab_base[mid] <= t) e0 = mid; else e1 = mid - 1;
     }
-    build_warp<F64>(tab_sys[e0], t - tab_base[e0], S, A, cstart, count, pots, max_nbrs, stride, err, sh_h[wib], sh_l[wib],
+    build_warp<F64>(tab_sys[e0], t - tab_base[e0], S, A, cstart, count, pots, max_nbrs, stride, err, sh_h[wib],
                     sh_d[wib]);
   }
 }
