@@ -134,6 +134,22 @@ struct SlotArrays {
 // ---------------------------------------------------------------------------
 // double-float helpers (FP32 pairs) for positions and velocities
 // ---------------------------------------------------------------------------
+// Two FP32 lanes in one 64-bit register pair, for the packed f32x2
+// instructions of sm_100+ (each lane rounds exactly as the scalar operation).
+__device__ __forceinline__ unsigned long long f2_pack(float a, float b) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void f2_unpack(unsigned long long r, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ unsigned long long f2_add(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+
 __device__ __forceinline__ void split_pos(double x, float& hi, float& lo) {
   double h = rint(x * 4096.0) * (1.0 / 4096.0);
   hi = (float)h;

@@ -140,8 +140,9 @@ __global__ void __launch_bounds__(256) k_pair(int32_t n_warps, const int32_t* __
 // An item is a run of consecutive warps that may straddle systems; its staged
 // range holds every system those warps belong to (at most kSmallMax slots),
 // so every neighbour gather is a shared-memory read.  Staged record per atom: 24 B
-// (hi.xyz and lo.x as a float4, lo.yz as a float2), so that a 2048-atom
-// system takes 48 KB and four CTAs fit on an SM.  List entries stream from
+// (hi.x, hi.y, lo.x, lo.y as a float4 and hi.z, lo.z as a float2: x and y
+// pair up for packed f32x2 arithmetic), so that a 2048-atom system takes
+// 48 KB and four CTAs fit on an SM.  List entries stream from
 // global memory (coalesced, evict-first, prefetched one block ahead).  The
 // arithmetic and summation order are those of k_pair, so both kernels give
 // identical results.
@@ -149,10 +150,10 @@ constexpr int kPairSmallThreads = 256;
 constexpr int kSmallRecord = 24;   // staged bytes per atom
 
 template <bool EW>
-__global__ void __launch_bounds__(kPairSmallThreads, 4) k_pair_small(
+__global__ void __launch_bounds__(kPairSmallThreads) k_pair_small(
     int32_t n_items, const int4* __restrict__ items, const int32_t* __restrict__ warp_sys, SysArrays S,
     SlotArrays A, const DevPot* __restrict__ pots, int64_t stride, int filter, double* __restrict__ partial) {
-  extern __shared__ __align__(16) float4 sa[];   // [staged] (hi.x hi.y hi.z lo.x), then [staged] float2 (lo.y lo.z)
+  extern __shared__ __align__(16) float4 sa[];   // [staged] (hi.x hi.y lo.x lo.y), then [staged] float2 (hi.z lo.z)
   if ((int)blockIdx.x >= n_items) return;
   const int4 W = items[blockIdx.x];
   const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -165,8 +166,8 @@ __global__ void __launch_bounds__(kPairSmallThreads, 4) k_pair_small(
 #pragma unroll 4
   for (int t = threadIdx.x; t < nst; t += kPairSmallThreads) {
     float4 h = __ldg(A.xh + st0 + t), l = __ldg(A.xl + st0 + t);
-    sa[t] = make_float4(h.x, h.y, h.z, l.x);
-    sb[t] = make_float2(l.y, l.z);
+    sa[t] = make_float4(h.x, h.y, l.x, l.y);
+    sb[t] = make_float2(h.z, l.z);
   }
   __syncthreads();
   if (!mine) return;
@@ -182,8 +183,9 @@ __global__ void __launch_bounds__(kPairSmallThreads, 4) k_pair_small(
   const DevPot P = pots[S.pot[s]];
   const float4* tab = S.shift + 2 * (int64_t)s * kNCodes;
   const int nn = valid ? A.nn[k] : 0;
-  const float4 xi = valid ? ha[i] : make_float4(0, 0, 0, 0);
-  const float2 li = valid ? hb[i] : make_float2(0, 0);
+  const float4 xi = valid ? ha[i] : make_float4(0, 0, 0, 0);   // (hi.x, hi.y, lo.x, lo.y)
+  const float2 zi = valid ? hb[i] : make_float2(0, 0);          // (hi.z, lo.z)
+  const unsigned long long nxh = f2_pack(-xi.x, -xi.y), nxl = f2_pack(-xi.z, -xi.w);
   float f0 = 0.f, f1 = 0.f, f2 = 0.f, e = 0.f, w0 = 0.f, w1 = 0.f, w2 = 0.f, w3 = 0.f, w4 = 0.f, w5 = 0.f;
   // The potential kind is uniform over a warp (one system): one loop per kind,
   // with no branch inside an entry.  Every entry evaluates the potential and
@@ -199,12 +201,14 @@ __global__ void __launch_bounds__(kPairSmallThreads, 4) k_pair_small(
       const float4 zero = make_float4(0, 0, 0, 0);
       const float4 th = img ? __ldg(tab + 2 * code) : zero, tl = img ? __ldg(tab + 2 * code + 1) : zero;
       const float4 xj = ha[j];
-      const float2 lj = hb[j];
-      float a0_ = xj.x - xi.x, a1_ = xj.y - xi.y, a2_ = xj.z - xi.z;
-      float b0 = xj.w - xi.w, b1 = lj.x - li.x, b2 = lj.y - li.y;
-      a0_ += th.x; a1_ += th.y; a2_ += th.z;
-      b0 += tl.x; b1 += tl.y; b2 += tl.z;
-      const float d0 = a0_ + b0, d1 = a1_ + b1, d2 = a2_ + b2;
+      const float2 zj = hb[j];
+      // d = ((x_j - x_i) + S)_hi + ((x_j - x_i) + S)_lo; x and y as packed
+      // pairs (subtraction as the exact addition of -x_i)
+      const unsigned long long axy = f2_add(f2_add(f2_pack(xj.x, xj.y), nxh), f2_pack(th.x, th.y));
+      const unsigned long long bxy = f2_add(f2_add(f2_pack(xj.z, xj.w), nxl), f2_pack(tl.x, tl.y));
+      float d0, d1;
+      f2_unpack(f2_add(axy, bxy), d0, d1);
+      const float d2 = ((zj.x - zi.x) + th.z) + ((zj.y - zi.y) + tl.z);
       const float r2 = fmaf(d0, d0, fmaf(d1, d1, d2 * d2));
       const bool in = r2 < P.rc2f;
       float phi, fr;
