@@ -58,7 +58,7 @@ size_t scratch_bytes(int64_t Ncap, int64_t Bcap, int64_t Ccap, int32_t max_nbrs,
                         : (2 * 16 /*x*/ + 2 * 16 /*v*/ + 16 /*F*/ + 2 * 16 /*xr*/ + 2 * 16 + 2 * 16 /*tmp f*/ +
                            2 * 16 /*g*/);
   per_slot += 4 * 4 /*perm sys bin nn*/ + 3 * 4 /*tmp i*/ + (size_t)max_nbrs * 4 + 8 * 8 / 32 /*partials*/ + 4 / 32 /*warp_sys*/ + 16 / 32 /*pair work items*/;
-  size_t per_sys = 8 * 4 + 9 * 8 * 3 + 9 * 4 + 6 * 4 + 4 * 4 + 8 + 8 /*list-build work table*/ + (size_t)kNCodes * (32 + 24);
+  size_t per_sys = 8 * 4 + 9 * 8 * 3 + 9 * 4 + 6 * 4 + 4 * 4 + 8 + 12 /*list-build work table*/ + (size_t)kNCodes * (32 + 24);
   return per_slot * (size_t)Ncap + per_sys * (size_t)Bcap + (size_t)Ccap * 8;
 }
 
@@ -155,8 +155,8 @@ extern "C" ts_status ts_batch_create(const ts_batch_config* cfg, const ts_potent
        alloc(b, b->d_bsum, (b->Ccap + 1023) / 1024 + 1) && alloc(b, b->d_starts, B + 1) &&
        alloc(b, b->d_Eint, B) && alloc(b, b->d_Wint, 9 * B) && alloc(b, b->d_scal, 32 * B) &&
        alloc(b, b->d_gparam_part, 4 * b->Wcap) && alloc(b, b->d_gacc, 3 * kMaxPots) &&
-       alloc(b, b->d_items, b->Wcap) && alloc(b, b->d_tab_sys, B) && alloc(b, b->d_tab_base, B + 1) &&
-       alloc(b, b->d_tab_n, 2);
+       alloc(b, b->d_items, b->Wcap) && alloc(b, b->d_tab_sys, B) && alloc(b, b->d_tab_base, B + 1) && alloc(b, b->d_tab_base_a, B + 1) &&
+       alloc(b, b->d_tab_n, 3);
   if (ok) ok = cuda_ok(b, cudaMemcpy(b->d_pots, dp, sizeof dp, cudaMemcpyHostToDevice), "copy pots");
   if (ok) ok = cuda_ok(b, cudaMemset(b->d_err, 0, 16), "memset") && cuda_ok(b, cudaMemset(b->d_counters, 0, 32), "memset");
   if (ok) ok = cuda_ok(b, cudaMemset(A.perm, 0xff, sizeof(int32_t) * N), "memset") &&
@@ -470,11 +470,11 @@ void relist_sort(ts_batch* b, cudaStream_t st, bool move_fire, int prio) {
   if (b->f64)
     launch_k(st, prio, B + 1, kSmallThreads, sizeof(SmallSmem), k_relist_small<true>, B, b->S, b->A, b->Ncap,
              (int)move_fire, b->d_cstart, b->d_count, (const DevPot*)b->d_pots, b->max_nbrs, b->d_err, b->d_tab_sys,
-             b->d_tab_base, b->d_tab_n);
+             b->d_tab_base, b->d_tab_base_a, b->d_tab_n);
   else
     launch_k(st, prio, B + 1, kSmallThreads, sizeof(SmallSmem), k_relist_small<false>, B, b->S, b->A, b->Ncap,
              (int)move_fire, b->d_cstart, b->d_count, (const DevPot*)b->d_pots, b->max_nbrs, b->d_err, b->d_tab_sys,
-             b->d_tab_base, b->d_tab_n);
+             b->d_tab_base, b->d_tab_base_a, b->d_tab_n);
   b->launches++;
   if (b->n_large > 0) relist_large_sort(b, st, move_fire);
 }
@@ -484,11 +484,11 @@ void relist_build(ts_batch* b, cudaStream_t st, int prio) {
   int grid = b->n_sm * kBuildCtasPerSm;
   if (b->f64)
     launch_k(st, prio, grid, 128, 0, k_build_list_warp<true>, b->S, b->A, (const int32_t*)b->d_tab_sys,
-             (const int32_t*)b->d_tab_base, b->d_tab_n, (const int32_t*)b->d_cstart, (const int32_t*)b->d_count,
+             (const int32_t*)b->d_tab_base, (const int32_t*)b->d_tab_base_a, b->d_tab_n, (const int32_t*)b->d_cstart, (const int32_t*)b->d_count,
              (const DevPot*)b->d_pots, b->max_nbrs, b->Ncap, b->d_err);
   else
     launch_k(st, prio, grid, 128, 0, k_build_list_warp<false>, b->S, b->A, (const int32_t*)b->d_tab_sys,
-             (const int32_t*)b->d_tab_base, b->d_tab_n, (const int32_t*)b->d_cstart, (const int32_t*)b->d_count,
+             (const int32_t*)b->d_tab_base, (const int32_t*)b->d_tab_base_a, b->d_tab_n, (const int32_t*)b->d_cstart, (const int32_t*)b->d_count,
              (const DevPot*)b->d_pots, b->max_nbrs, b->Ncap, b->d_err);
   b->launches++;
 }

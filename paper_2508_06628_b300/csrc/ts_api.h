@@ -37,6 +37,7 @@ struct ts_batch {
   int4* d_items = nullptr;        // work items of k_pair_small
   int32_t* d_tab_sys = nullptr;   // list-build work table (k_relist_small writes it)
   int32_t* d_tab_base = nullptr;
+  int32_t* d_tab_base_a = nullptr;
   int32_t* d_tab_n = nullptr;
   int n_sm = 148;
   int64_t N = 0, Npad = 0, nbins = 0;

@@ -25,6 +25,9 @@ namespace ts {
 
 constexpr int kSmallThreads = 512;
 constexpr int kBuildCtasPerSm = 5;   // grid of k_build_list_warp: resident CTAs of 128 threads per SM (96 registers)
+// Passes that re-list at most this many atoms build one warp per atom (short
+// dependency chains); larger passes one warp per 32 atoms (fewer instructions).
+constexpr int kAtomModeMaxAtoms = 32768;
 
 struct SmallSmem {
   int32_t bin_old[kSmallMax];
@@ -70,13 +73,13 @@ __device__ int block_exclusive_scan(int32_t* a, int n, int32_t* warp_tot) {
 }
 
 // Work table of k_build_list_warp (one CTA): entries e = 0..ne-1 are the
-// flagged systems in system order; tab_base[e] is the number of
-// their warps (32-slot groups) before entry e, tab_base[ne] the total;
-// tab_n = {ne, 0}, the second word being the build kernel's work counter.
+// flagged systems in system order; tab_base[e] / tab_base_a[e] count their
+// warps (32-slot groups) / atoms before entry e, [ne] the totals;
+// tab_n = {ne, work counter of the build, build mode}.
 __device__ void relist_table(int32_t B, const SysArrays& S, SmallSmem& sm, int32_t* tab_sys, int32_t* tab_base,
-                             int32_t* tab_n) {
+                             int32_t* tab_base_a, int32_t* tab_n) {
   const int t = threadIdx.x;
-  int ecarry = 0, acarry = 0;
+  int ecarry = 0, wcarry = 0, acarry = 0;
   for (int c0 = 0; c0 < B; c0 += kSmallMax) {
     const int m = min(kSmallMax, B - c0);
     for (int i = t; i < m; i += kSmallThreads) {
@@ -85,31 +88,41 @@ __device__ void relist_table(int32_t B, const SysArrays& S, SmallSmem& sm, int32
       sm.tmp[i] = f;
       sm.start[i] = f;
       sm.fill[i] = f ? S.warp_end[s] - S.warp_start[s] : 0;
+      sm.pid[i] = f ? S.n_atoms[s] : 0;
     }
     __syncthreads();
     int ne = block_exclusive_scan(sm.start, m, sm.warp_tot);
-    int na = block_exclusive_scan(sm.fill, m, sm.warp_tot);
+    int nw = block_exclusive_scan(sm.fill, m, sm.warp_tot);
+    int na = block_exclusive_scan(sm.pid, m, sm.warp_tot);
     for (int i = t; i < m; i += kSmallThreads)
       if (sm.tmp[i]) {
         tab_sys[ecarry + sm.start[i]] = c0 + i;
-        tab_base[ecarry + sm.start[i]] = acarry + sm.fill[i];
+        tab_base[ecarry + sm.start[i]] = wcarry + sm.fill[i];
+        tab_base_a[ecarry + sm.start[i]] = acarry + sm.pid[i];
       }
     ecarry += ne;
+    wcarry += nw;
     acarry += na;
     __syncthreads();
   }
-  if (t == 0) { tab_base[ecarry] = acarry; tab_n[0] = ecarry; tab_n[1] = 0; }   // tab_n[1]: next atom to build
+  if (t == 0) {
+    tab_base[ecarry] = wcarry;
+    tab_base_a[ecarry] = acarry;
+    tab_n[0] = ecarry;
+    tab_n[1] = 0;                               // work counter of the build
+    tab_n[2] = acarry <= kAtomModeMaxAtoms;     // build mode: one warp per atom for small passes
+  }
 }
 
 template <bool F64>
 __global__ void __launch_bounds__(kSmallThreads, 1)
 k_relist_small(int32_t B, SysArrays S, SlotArrays A, int64_t stride, int move_fire, int32_t* cstart, int32_t* count,
                const DevPot* __restrict__ pots, int32_t max_nbrs, int32_t* err, int32_t* tab_sys, int32_t* tab_base,
-               int32_t* tab_n) {
+               int32_t* tab_base_a, int32_t* tab_n) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SmallSmem& sm = *reinterpret_cast<SmallSmem*>(smem_raw);
   int s = blockIdx.x;
-  if (s == B) { relist_table(B, S, sm, tab_sys, tab_base, tab_n); return; }   // the extra CTA
+  if (s == B) { relist_table(B, S, sm, tab_sys, tab_base, tab_base_a, tab_n); return; }   // the extra CTA
   if (s > B || !need_relist(S, s)) return;
   int n = S.n_atoms[s];
   if (n > kSmallMax) return;
@@ -402,6 +415,94 @@ __device__ void build_warp(int s, int wi, const SysArrays& S, const SlotArrays& 
   }
 }
 
+// One warp: the list of atom `a` of system `s` (sorted order), the lanes
+// taking 32 consecutive candidates at a time.  For each stencil row (dz, dy)
+// the bins kx-m..kx+m that share one image index are consecutive in the
+// sorted order, so their atoms form one contiguous slot range; a ballot and
+// prefix count append the hits in candidate order, which is the order of
+// build_warp's per-lane loop.  Short dependency chains: the mode for passes
+// that re-list few atoms, where build_warp's long per-warp loops would set
+// the pass's latency.
+template <bool F64>
+__device__ void build_atom(int s, int a, const SysArrays& S, const SlotArrays& A, const int32_t* __restrict__ cstart,
+                           const int32_t* __restrict__ count, const DevPot* __restrict__ pots, int32_t max_nbrs,
+                           int64_t stride, int32_t* err) {
+  const int lane = threadIdx.x & 31;
+  const int64_t seg = S.seg_start[s];
+  const int64_t k = seg + a;
+  const DevPot& P = pots[S.pot[s]];
+  const int nb0 = S.nb[3 * s], nb1 = S.nb[3 * s + 1], nb2 = S.nb[3 * s + 2];
+  const int m0 = S.reach[3 * s], m1 = S.reach[3 * s + 1], m2 = S.reach[3 * s + 2];
+  const int boff = S.bin_off[s];
+  const int64_t coff = S.caller_off[s];
+  const int lb = A.bin[k] - boff;
+  const int kx = lb % nb0, ky = (lb / nb0) % nb1, kz = lb / (nb0 * nb1);
+  float4 hi = make_float4(0, 0, 0, 0), lo = hi;
+  double xi[3] = {0, 0, 0};
+  if constexpr (F64) { for (int c = 0; c < 3; c++) xi[c] = A.xd[3 * k + c]; }
+  else { hi = A.xh[k]; lo = A.xl[k]; }
+  int cnt = 0;
+  for (int dz = -m2; dz <= m2; dz++) {
+    const int zz = kz + dz, iz = floor_div(zz, nb2), cz = zz - iz * nb2;
+    for (int dy = -m1; dy <= m1; dy++) {
+      const int yy = ky + dy, iy = floor_div(yy, nb1), cy = yy - iy * nb1;
+      const int rowb = boff + (cz * nb1 + cy) * nb0;
+      for (int xx = kx - m0; xx <= kx + m0;) {
+        const int ix = floor_div(xx, nb0);
+        const int xe = min(kx + m0, (ix + 1) * nb0 - 1);
+        const int gb0 = rowb + (xx - ix * nb0), gb1 = rowb + (xe - ix * nb0);
+        const int q0 = (int)(cstart[gb0] - coff), q1 = (int)(cstart[gb1] - coff) + count[gb1];
+        const int code = img_code(ix, iy, iz);
+        const int64_t ti = (int64_t)s * kNCodes + code;
+        float a0 = 0, a1 = 0, a2 = 0, e0 = 0, e1 = 0, e2 = 0;
+        double s0 = 0, s1 = 0, s2 = 0;
+        if constexpr (F64) {
+          const double* sd = S.shiftd + 3 * ti;
+          s0 = sd[0] - xi[0]; s1 = sd[1] - xi[1]; s2 = sd[2] - xi[2];
+        } else {
+          const float4 sh = S.shift[2 * ti], sl = S.shift[2 * ti + 1];
+          a0 = sh.x - hi.x; a1 = sh.y - hi.y; a2 = sh.z - hi.z;   // exact (2^-12 grid)
+          e0 = sl.x - lo.x; e1 = sl.y - lo.y; e2 = sl.z - lo.z;
+        }
+        for (int qb = q0; qb < q1; qb += 32) {
+          const int q = qb + lane;
+          bool hit = false;
+          if (q < q1 && !(q == a && code == kCenter)) {
+            if constexpr (F64) {
+              const double* xj = A.xd + 3 * (seg + q);
+              const double d0 = xj[0] + s0, d1 = xj[1] + s1, d2 = xj[2] + s2;
+              hit = d0 * d0 + d1 * d1 + d2 * d2 < P.rlist2d;
+            } else {
+              const float4 xj = A.xh[seg + q];
+              const float h0 = xj.x + a0, h1 = xj.y + a1, h2 = xj.z + a2;
+              const float rh2 = fmaf(h0, h0, fmaf(h1, h1, h2 * h2));
+              hit = rh2 < P.rlist_in2f;
+              if (!hit && rh2 <= P.rlist_out2f) {   // within 1e-3 A of the list radius
+                const float4 lj = A.xl[seg + q];
+                const float d0 = h0 + (lj.x + e0), d1 = h1 + (lj.y + e1), d2 = h2 + (lj.z + e2);
+                hit = d0 * d0 + d1 * d1 + d2 * d2 < P.rlist2f;
+              }
+            }
+          }
+          const unsigned bal = __ballot_sync(0xffffffffu, hit);
+          if (hit) {
+            const int pos = cnt + __popc(bal & ((1u << lane) - 1u));
+            if (pos < max_nbrs) A.nbr[pos * stride + k] = (uint32_t)q | ((uint32_t)code << kJBits);
+          }
+          cnt += __popc(bal);
+        }
+        xx = xe + 1;
+      }
+    }
+  }
+  if (lane == 0) {
+    if (cnt > max_nbrs) { atomicOr(err, kErrNeighborOverflow); cnt = max_nbrs; }
+    A.nn[k] = cnt;
+    if constexpr (F64) { for (int c = 0; c < 3; c++) A.xrd[3 * k + c] = xi[c]; }
+    else { A.xrh[k] = hi; A.xrl[k] = lo; }
+  }
+}
+
 // (B) Verlet lists of the work table's warps: one warp per 32 sorted atoms,
 // warps taken from a counter (a fixed, resident grid; consecutive grabs are
 // neighbouring atoms, and CTAs that start late beside another kernel just
@@ -409,25 +510,29 @@ __device__ void build_warp(int s, int wi, const SysArrays& S, const SlotArrays& 
 template <bool F64>
 __global__ void __launch_bounds__(128, kBuildCtasPerSm) k_build_list_warp(
     SysArrays S, SlotArrays A, const int32_t* __restrict__ tab_sys, const int32_t* __restrict__ tab_base,
-    int32_t* __restrict__ tab_n, const int32_t* __restrict__ cstart, const int32_t* __restrict__ count,
-    const DevPot* __restrict__ pots, int32_t max_nbrs, int64_t stride, int32_t* err) {
+    const int32_t* __restrict__ tab_base_a, int32_t* __restrict__ tab_n, const int32_t* __restrict__ cstart,
+    const int32_t* __restrict__ count, const DevPot* __restrict__ pots, int32_t max_nbrs, int64_t stride,
+    int32_t* err) {
   __shared__ float4 sh_h[4][32];
   __shared__ double sh_d[4][32][3];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int ne = tab_n[0];
-  const int total = tab_base[ne];
+  const bool per_atom = tab_n[2] != 0;   // chosen by the table CTA from the pass's size
+  const int32_t* base = per_atom ? tab_base_a : tab_base;
+  const int total = base[ne];
   for (;;) {
     int t = 0;
     if (lane == 0) t = atomicAdd(tab_n + 1, 1);
     t = __shfl_sync(0xffffffffu, t, 0);
     if (t >= total) break;
-    int e0 = 0, e1 = ne - 1;   // last entry with tab_base[e] <= t (warp-uniform search)
+    int e0 = 0, e1 = ne - 1;   // last entry with base[e] <= t (warp-uniform search)
     while (e0 < e1) {
       int mid = (e0 + e1 + 1) >> 1;
-      if (tab_base[mid] <= t) e0 = mid; else e1 = mid - 1;
+      if (base[mid] <= t) e0 = mid; else e1 = mid - 1;
     }
-    build_warp<F64>(tab_sys[e0], t - tab_base[e0], S, A, cstart, count, pots, max_nbrs, stride, err, sh_h[wib],
-                    sh_d[wib]);
+    if (per_atom) build_atom<F64>(tab_sys[e0], t - base[e0], S, A, cstart, count, pots, max_nbrs, stride, err);
+    else build_warp<F64>(tab_sys[e0], t - base[e0], S, A, cstart, count, pots, max_nbrs, stride, err, sh_h[wib],
+                         sh_d[wib]);
   }
 }
 
