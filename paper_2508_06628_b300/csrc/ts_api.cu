@@ -58,7 +58,7 @@ size_t scratch_bytes(int64_t Ncap, int64_t Bcap, int64_t Ccap, int32_t max_nbrs,
                         : (2 * 16 /*x*/ + 2 * 16 /*v*/ + 16 /*F*/ + 2 * 16 /*xr*/ + 2 * 16 + 2 * 16 /*tmp f*/ +
                            2 * 16 /*g*/);
   per_slot += 4 * 4 /*perm sys bin nn*/ + 3 * 4 /*tmp i*/ + (size_t)max_nbrs * 4 + 8 * 8 / 32 /*partials*/ + 4 / 32 /*warp_sys*/ + 16 / 32 /*pair work items*/;
-  size_t per_sys = 8 * 4 + 9 * 8 * 3 + 9 * 4 + 6 * 4 + 4 * 4 + 8 + 12 /*list-build work table*/ + (size_t)kNCodes * (32 + 24);
+  size_t per_sys = 8 * 4 + 9 * 8 * 3 + 9 * 4 + 6 * 4 + 4 * 4 + 8 + 12 /*list-build work table*/ + (size_t)kNCodes * (32 + 24 + 16);
   return per_slot * (size_t)Ncap + per_sys * (size_t)Bcap + (size_t)Ccap * 8;
 }
 
@@ -125,6 +125,7 @@ extern "C" ts_status ts_batch_create(const ts_batch_config* cfg, const ts_potent
     D.half_skin2f = (float)(0.25 * P.skin * P.skin);
     D.soon_half_skin2f = (float)(D.soon2 * 0.25 * P.skin * P.skin);
     b->rc[q] = rc;
+    if (D.rlist >= kFixMaxList) b->use_small_pair = false;   // beyond the fixed-point range of k_pair_small
   }
   bool ok = true;
   SysArrays& S = b->S;
@@ -137,7 +138,7 @@ extern "C" ts_status ts_batch_create(const ts_batch_config* cfg, const ts_potent
        alloc(b, S.warp_end, B) && alloc(b, S.h, 9 * B) && alloc(b, S.hinv, 9 * B) && alloc(b, S.hinvf, 9 * B) && alloc(b, S.href, 9 * B) &&
        alloc(b, S.nb, 3 * B) && alloc(b, S.reach, 3 * B) && alloc(b, S.relist, B) && alloc(b, S.dirty, B) &&
        alloc(b, S.soon, B) && alloc(b, S.any, 1) &&
-       alloc(b, S.kT, B) && alloc(b, S.shift, 2 * B * kNCodes) && alloc(b, S.shiftd, 3 * B * kNCodes);
+       alloc(b, S.kT, B) && alloc(b, S.shift, 2 * B * kNCodes) && alloc(b, S.shiftd, 3 * B * kNCodes) && alloc(b, S.shiftq, B * kNCodes);
   ok = ok && alloc(b, A.perm, N) && alloc(b, A.sys, N) && alloc(b, A.bin, N) && alloc(b, A.nn, N) &&
        alloc(b, A.nbr, (size_t)b->max_nbrs * N) && alloc(b, A.tmp_i0, N) && alloc(b, A.tmp_i1, N) &&
        alloc(b, A.tmp_i2, N);

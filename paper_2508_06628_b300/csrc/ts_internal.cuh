@@ -85,6 +85,7 @@ struct SysArrays {
   int32_t* reach;         // [3]
   float4* shift;          // [kNCodes][2] (hi xyz, lo xyz) mixed
   double* shiftd;         // [kNCodes][3] fp64
+  uint4* shiftq;          // [kNCodes] (x, y, z) in units of 2^-26 A, modulo 2^32 (shared-memory pair kernel)
   int32_t* relist;        // per-system re-list flag
   int32_t* soon;          // atoms past kSoon * skin/2: re-list along with any forced pass
   int32_t* any;           // [1] some system must re-list in this pass
@@ -134,6 +135,19 @@ struct SlotArrays {
 // ---------------------------------------------------------------------------
 // double-float helpers (FP32 pairs) for positions and velocities
 // ---------------------------------------------------------------------------
+// Fixed-point coordinates of the shared-memory pair kernel: units of 2^-26 A,
+// kept modulo 2^32.  A pair vector is the exact integer x_j - x_i + S (exact
+// as long as it is shorter than 2^31 units = 32 A) and then one conversion
+// to FP32: the same single rounding as the double-float form, plus the
+// quantisation of each coordinate (at most 2^-27 A = 7.5e-9 A).
+constexpr float kFix = 67108864.0f;               // 2^26
+constexpr float kFixInv = 1.4901161193847656e-8f; // 2^-26
+constexpr double kFixMaxList = 30.0;             // list radii at or above this use the general kernel
+__device__ __forceinline__ uint32_t fix_coord(float hi, float lo) {
+  // hi * 2^26 is an integer (hi lies on the 2^-12 grid); lo * 2^26 is rounded
+  return (uint32_t)(unsigned long long)__float2ll_rn(hi * kFix) + (uint32_t)__float2int_rn(lo * kFix);
+}
+
 // Two FP32 lanes in one 64-bit register pair, for the packed f32x2
 // instructions of sm_100+ (each lane rounds exactly as the scalar operation).
 __device__ __forceinline__ unsigned long long f2_pack(float a, float b) {

@@ -221,6 +221,9 @@ __global__ void k_shift_table(int32_t B, SysArrays S) {
   hi.w = 0.f; lo.w = 0.f;
   S.shift[2 * t] = hi; S.shift[2 * t + 1] = lo;
   for (int c = 0; c < 3; c++) S.shiftd[3 * t + c] = v[c];
+  S.shiftq[t] = make_uint4((uint32_t)(unsigned long long)llrint(v[0] * (double)kFix),
+                           (uint32_t)(unsigned long long)llrint(v[1] * (double)kFix),
+                           (uint32_t)(unsigned long long)llrint(v[2] * (double)kFix), 0u);
 }
 
 // Wrap a double-float position into its cell by a whole lattice vector and

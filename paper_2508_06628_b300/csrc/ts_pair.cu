@@ -139,21 +139,24 @@ __global__ void __launch_bounds__(256) k_pair(int32_t n_warps, const int32_t* __
 //   w = computed warps (at most 8).
 // An item is a run of consecutive warps that may straddle systems; its staged
 // range holds every system those warps belong to (at most kSmallMax slots),
-// so every neighbour gather is a shared-memory read.  Staged record per atom: 24 B
-// (hi.x, hi.y, lo.x, lo.y as a float4 and hi.z, lo.z as a float2: x and y
-// pair up for packed f32x2 arithmetic), so that a 2048-atom system takes
-// 48 KB and four CTAs fit on an SM.  List entries stream from
-// global memory (coalesced, evict-first, prefetched one block ahead).  The
-// arithmetic and summation order are those of k_pair, so both kernels give
-// identical results.
+// so every neighbour gather is a shared-memory read.  Staged record per atom:
+// 16 B, the fixed-point coordinates (units of 2^-26 A, modulo 2^32), so that
+// a gather is one 16-byte read and a 2048-atom system takes 32 KB; a pair
+// vector is the exact integer difference plus the fixed-point image shift,
+// converted once to FP32.  List entries stream from global memory
+// (coalesced, evict-first, prefetched one block ahead).  The potential
+// arithmetic and summation order are those of k_pair; the pair vectors carry
+// the same single FP32 rounding but a different quantisation of the
+// coordinates, so the two kernels agree within the mixed-precision tolerance,
+// not bit for bit.
 constexpr int kPairSmallThreads = 256;
-constexpr int kSmallRecord = 24;   // staged bytes per atom
+constexpr int kSmallRecord = 16;   // staged bytes per atom
 
 template <bool EW>
 __global__ void __launch_bounds__(kPairSmallThreads) k_pair_small(
     int32_t n_items, const int4* __restrict__ items, const int32_t* __restrict__ warp_sys, SysArrays S,
     SlotArrays A, const DevPot* __restrict__ pots, int64_t stride, int filter, double* __restrict__ partial) {
-  extern __shared__ __align__(16) float4 sa[];   // [staged] (hi.x hi.y lo.x lo.y), then [staged] float2 (hi.z lo.z)
+  extern __shared__ __align__(16) uint4 sq[];   // [staged] fixed-point (x, y, z, -)
   if ((int)blockIdx.x >= n_items) return;
   const int4 W = items[blockIdx.x];
   const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -162,12 +165,10 @@ __global__ void __launch_bounds__(kPairSmallThreads) k_pair_small(
   if (!__syncthreads_or(mine)) return;
   const int64_t st0 = (int64_t)W.x * kWarp;
   const int nst = W.y * kWarp;
-  float2* sb = reinterpret_cast<float2*>(sa + nst);
 #pragma unroll 4
   for (int t = threadIdx.x; t < nst; t += kPairSmallThreads) {
     float4 h = __ldg(A.xh + st0 + t), l = __ldg(A.xl + st0 + t);
-    sa[t] = make_float4(h.x, h.y, l.x, l.y);
-    sb[t] = make_float2(h.z, l.z);
+    sq[t] = make_uint4(fix_coord(h.x, l.x), fix_coord(h.y, l.y), fix_coord(h.z, l.z), 0u);
   }
   __syncthreads();
   if (!mine) return;
@@ -178,14 +179,11 @@ __global__ void __launch_bounds__(kPairSmallThreads) k_pair_small(
   const int i = (int)(k - seg);
   const int n = S.n_atoms[s];
   const bool valid = i < n;
-  const float4* ha = sa + (seg - st0);
-  const float2* hb = sb + (seg - st0);
+  const uint4* hq = sq + (seg - st0);
   const DevPot P = pots[S.pot[s]];
-  const float4* tab = S.shift + 2 * (int64_t)s * kNCodes;
+  const uint4* tab = S.shiftq + (int64_t)s * kNCodes;
   const int nn = valid ? A.nn[k] : 0;
-  const float4 xi = valid ? ha[i] : make_float4(0, 0, 0, 0);   // (hi.x, hi.y, lo.x, lo.y)
-  const float2 zi = valid ? hb[i] : make_float2(0, 0);          // (hi.z, lo.z)
-  const unsigned long long nxh = f2_pack(-xi.x, -xi.y), nxl = f2_pack(-xi.z, -xi.w);
+  const uint4 xi = valid ? hq[i] : make_uint4(0, 0, 0, 0);
   float f0 = 0.f, f1 = 0.f, f2 = 0.f, e = 0.f, w0 = 0.f, w1 = 0.f, w2 = 0.f, w3 = 0.f, w4 = 0.f, w5 = 0.f;
   // The potential kind is uniform over a warp (one system): one loop per kind,
   // with no branch inside an entry.  Every entry evaluates the potential and
@@ -198,17 +196,12 @@ __global__ void __launch_bounds__(kPairSmallThreads) k_pair_small(
       const int code = (int)(ent >> kJBits);
       const int j = (int)(ent & kJMask);
       const bool img = code != kCenter;
-      const float4 zero = make_float4(0, 0, 0, 0);
-      const float4 th = img ? __ldg(tab + 2 * code) : zero, tl = img ? __ldg(tab + 2 * code + 1) : zero;
-      const float4 xj = ha[j];
-      const float2 zj = hb[j];
-      // d = ((x_j - x_i) + S)_hi + ((x_j - x_i) + S)_lo; x and y as packed
-      // pairs (subtraction as the exact addition of -x_i)
-      const unsigned long long axy = f2_add(f2_add(f2_pack(xj.x, xj.y), nxh), f2_pack(th.x, th.y));
-      const unsigned long long bxy = f2_add(f2_add(f2_pack(xj.z, xj.w), nxl), f2_pack(tl.x, tl.y));
-      float d0, d1;
-      f2_unpack(f2_add(axy, bxy), d0, d1);
-      const float d2 = ((zj.x - zi.x) + th.z) + ((zj.y - zi.y) + tl.z);
+      const uint4 sh = img ? __ldg(tab + code) : make_uint4(0, 0, 0, 0);
+      const uint4 xj = hq[j];
+      // exact integer pair vector (modulo 2^32), one rounding to FP32
+      const float d0 = (float)(int)(xj.x - xi.x + sh.x) * kFixInv;
+      const float d1 = (float)(int)(xj.y - xi.y + sh.y) * kFixInv;
+      const float d2 = (float)(int)(xj.z - xi.z + sh.z) * kFixInv;
       const float r2 = fmaf(d0, d0, fmaf(d1, d1, d2 * d2));
       const bool in = r2 < P.rc2f;
       float phi, fr;
