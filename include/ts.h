@@ -16,8 +16,10 @@
  *  - Units: Angstrom, eV, amu.  Time unit t0 = sqrt(amu A^2/eV) = 10.1805 fs;
  *    callers convert dt.  Temperatures are passed as kT in eV.
  *  - Cells are row-major [3][3] with rows = lattice vectors (x = s h for a
- *    fractional row vector s).  Only fully periodic systems are supported
- *    (pbc must be {1,1,1}; anything else returns TS_ERR_UNSUPPORTED).
+ *    fractional row vector s).  pbc[a] = 0 makes axis a non-periodic: no
+ *    images and no wrapping along it (atoms may lie outside the cell, which
+ *    then only sets the binning).  Variable-cell FIRE needs pbc = {1,1,1}
+ *    (other systems report TS_ERR_UNSUPPORTED at poll).
  *  - Every array pointer in ts_state and every output pointer is DEVICE
  *    memory owned by the caller, unless the comment says "host".  The library
  *    never frees caller memory; it owns only its scratch, sized at

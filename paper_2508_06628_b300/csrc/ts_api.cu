@@ -136,7 +136,7 @@ extern "C" ts_status ts_batch_create(const ts_batch_config* cfg, const ts_potent
   ok = ok && alloc(b, S.seg_start, B) && alloc(b, S.n_atoms, B) && alloc(b, S.caller_off, B + 1) && alloc(b, S.pot, B) &&
        alloc(b, S.uid, B) && alloc(b, S.bin_off, B) && alloc(b, S.bin_cap, B) && alloc(b, S.warp_start, B) &&
        alloc(b, S.warp_end, B) && alloc(b, S.h, 9 * B) && alloc(b, S.hinv, 9 * B) && alloc(b, S.hinvf, 9 * B) && alloc(b, S.href, 9 * B) &&
-       alloc(b, S.nb, 3 * B) && alloc(b, S.reach, 3 * B) && alloc(b, S.relist, B) && alloc(b, S.dirty, B) &&
+       alloc(b, S.nb, 3 * B) && alloc(b, S.reach, 3 * B) && alloc(b, S.pmask, B) && alloc(b, S.relist, B) && alloc(b, S.dirty, B) &&
        alloc(b, S.soon, B) && alloc(b, S.any, 1) &&
        alloc(b, S.kT, B) && alloc(b, S.shift, 2 * B * kNCodes) && alloc(b, S.shiftd, 3 * B * kNCodes) && alloc(b, S.shiftq, B * kNCodes);
   ok = ok && alloc(b, A.perm, N) && alloc(b, A.sys, N) && alloc(b, A.bin, N) && alloc(b, A.nn, N) &&
@@ -278,7 +278,8 @@ extern "C" ts_status ts_batch_poll(ts_batch* b, void* stream, int timeout_ms) {
   if (st2 != TS_OK) return st2;
   if (e & kErrBadSystemIdx) return fail(b, TS_ERR_INVALID_ARG, "system_idx is not non-decreasing or a system is empty");
   if (e & kErrNeighborOverflow) return fail(b, TS_ERR_NEIGHBOR_OVERFLOW, "an atom has more neighbours than max_neighbors");
-  if (e & kErrUnsupported) return fail(b, TS_ERR_UNSUPPORTED, "non-periodic axis or cell outside the supported range");
+  if (e & kErrUnsupported)
+    return fail(b, TS_ERR_UNSUPPORTED, "cell outside the supported range, or variable-cell FIRE with a non-periodic axis");
   if (e & kErrNonFinite) return fail(b, TS_ERR_NONFINITE, "non-finite or out-of-range position or cell");
   if (e & kErrTimeout) return fail(b, TS_ERR_TIMEOUT, "a bounded device wait ran out");
   return TS_OK;

@@ -31,6 +31,13 @@ __device__ inline void inv_T3(const double* A, double* out) {   // out = A^-T
   for (int a = 0; a < 3; a++) for (int b = 0; b < 3; b++) out[3 * a + b] = g[3 * b + a];
 }
 
+// The variable-cell filter needs a stress along every axis: a system with a
+// non-periodic axis is refused (device error word, read at poll).
+__global__ void k_require_periodic(int32_t B, SysArrays S, int32_t* err) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < B && S.pmask[s] != 7) atomicOr(err, kErrUnsupported);
+}
+
 __global__ void k_fire_init(int32_t B, const double* __restrict__ cell, const ts_fire_params p, ts_fire_state* fs) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= B) return;
@@ -284,6 +291,10 @@ extern "C" ts_status ts_fire_step(ts_batch* b, ts_state* s, ts_fire_state* fs, d
   cudaStream_t st = (cudaStream_t)stream;
   r = prologue(b, s, st, false);
   if (r != TS_OK) return r;
+  if (p->variable_cell) {
+    k_require_periodic<<<(b->B + 127) / 128, 128, 0, st>>>(b->B, b->S, b->d_err);
+    b->launches++;
+  }
   int g = (int)std::min<int64_t>(std::max<int64_t>((b->Npad + 255) / 256, 1), 148 * 16);
   if (b->f64) k_fire_vel_io<true><<<g, 256, 0, st>>>(b->Npad, b->A, fvel, 1);
   else k_fire_vel_io<false><<<g, 256, 0, st>>>(b->Npad, b->A, fvel, 1);

@@ -83,6 +83,7 @@ struct SysArrays {
   double* href;           // [9] cell at the last listing (FIRE)
   int32_t* nb;            // [3] bins per axis (at last listing)
   int32_t* reach;         // [3]
+  int32_t* pmask;         // periodic axes, bit a set when axis a is periodic
   float4* shift;          // [kNCodes][2] (hi xyz, lo xyz) mixed
   double* shiftd;         // [kNCodes][3] fp64
   uint4* shiftq;          // [kNCodes] (x, y, z) in units of 2^-26 A, modulo 2^32 (shared-memory pair kernel)

@@ -156,7 +156,10 @@ __device__ inline double det3(const double* h) {
 }
 
 // Cell import, inverse, bins and reach (bins clamped to the system's bin
-// reservation).  pbc must be periodic on all axes.
+// reservation), periodic axes.  Along a non-periodic axis there are no
+// images and no wrapping: the cell spans the bins, atoms beyond it fall into
+// the edge bins (bins are at least r_list wide, so every pair within r_list
+// still lies in neighbouring bins), and the stencil stops at the edges.
 __global__ void k_geometry(int32_t B, SysArrays S, const double* __restrict__ cell, const uint8_t* __restrict__ pbc,
                            const DevPot* __restrict__ pots, int32_t* err) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -164,7 +167,8 @@ __global__ void k_geometry(int32_t B, SysArrays S, const double* __restrict__ ce
   double h[9];
   for (int q = 0; q < 9; q++) h[q] = cell[9 * (int64_t)s + q];
   for (int q = 0; q < 9; q++) S.h[9 * s + q] = h[q];
-  if (pbc && !(pbc[3 * s] && pbc[3 * s + 1] && pbc[3 * s + 2])) atomicOr(err, kErrUnsupported);
+  const int pm = pbc ? ((pbc[3 * s] ? 1 : 0) | (pbc[3 * s + 1] ? 2 : 0) | (pbc[3 * s + 2] ? 4 : 0)) : 7;
+  S.pmask[s] = pm;
   double d = det3(h);
   if (!(fabs(d) > 0) || !isfinite(d)) { atomicOr(err, kErrNonFinite); return; }
   double g[9];
@@ -198,7 +202,8 @@ __global__ void k_geometry(int32_t B, SysArrays S, const double* __restrict__ ce
   for (int a = 0; a < 3; a++) {
     m[a] = (int)ceil(rl * nb[a] / w[a]);
     if (m[a] < 1) m[a] = 1;
-    if (m[a] > kMaxReach) { m[a] = kMaxReach; atomicOr(err, kErrUnsupported); }
+    if (!(pm >> a & 1)) m[a] = m[a] < nb[a] ? m[a] : nb[a];   // open axis: no images, the stencil stops at the edges
+    else if (m[a] > kMaxReach) { m[a] = kMaxReach; atomicOr(err, kErrUnsupported); }
     S.nb[3 * s + a] = nb[a];
     S.reach[3 * s + a] = m[a];
   }
@@ -226,8 +231,8 @@ __global__ void k_shift_table(int32_t B, SysArrays S) {
                            (uint32_t)(unsigned long long)llrint(v[2] * (double)kFix), 0u);
 }
 
-// Wrap a double-float position into its cell by a whole lattice vector and
-// find its bin.  FP32 fractional coordinates choose the lattice vector and the
+// Wrap a double-float position into its cell by a whole lattice vector (along
+// periodic axes) and find its bin.  FP32 fractional coordinates choose the lattice vector and the
 // bin (an atom within ~1e-7 of a face may end up a few 1e-6 A outside its bin,
 // far inside any skin); the shift itself is the system's double-float image
 // shift, added exactly to hi and with one FP32 rounding to lo, so an atom that
@@ -237,15 +242,21 @@ __global__ void k_shift_table(int32_t B, SysArrays S) {
 __device__ __forceinline__ bool wrap_bin_mixed(const SysArrays& S, int s, float4& hi, float4& lo, int kb[3]) {
   const float* g = S.hinvf + 9 * s;
   const float x0 = hi.x + lo.x, x1 = hi.y + lo.y, x2 = hi.z + lo.z;
+  const int pm = S.pmask[s];
   int n[3];
 #pragma unroll
   for (int a = 0; a < 3; a++) {
     float v = fmaf(x0, g[a], fmaf(x1, g[3 + a], x2 * g[6 + a]));
-    float fl = floorf(v);
-    if (!(fabsf(fl) <= (float)kMaxReach)) return false;
-    n[a] = (int)fl;
     int nb = S.nb[3 * s + a];
-    int q = (int)((v - fl) * (float)nb);
+    float fl = 0.f;
+    if (pm >> a & 1) {   // periodic: whole lattice vectors back into the cell
+      fl = floorf(v);
+      if (!(fabsf(fl) <= (float)kMaxReach)) return false;
+    } else if (!(fabsf(v) <= 4096.f)) {
+      return false;
+    }
+    n[a] = (int)fl;
+    int q = (int)floorf((v - fl) * (float)nb);   // open axis: atoms beyond the cell go to the edge bins
     kb[a] = q >= nb ? nb - 1 : (q < 0 ? 0 : q);
   }
   if (n[0] | n[1] | n[2]) {
@@ -294,13 +305,16 @@ __global__ void k_bin_atoms(int64_t Npad, SysArrays S, SlotArrays A, int32_t* co
     const double* g = S.hinv + 9 * s;
     const double* h = S.h + 9 * s;
     double f[3];
+    const int pm = S.pmask[s];
     for (int a = 0; a < 3; a++) {
       double v = x[0] * g[a] + x[1] * g[3 + a] + x[2] * g[6 + a];
-      v -= floor(v);
-      if (v >= 1.0) v = 0.0;
+      if (pm >> a & 1) {
+        v -= floor(v);
+        if (v >= 1.0) v = 0.0;
+      }
       f[a] = v;
       int nb = S.nb[3 * s + a];
-      int q = (int)(v * nb);
+      int q = (int)floor(v * nb);
       kb[a] = q >= nb ? nb - 1 : (q < 0 ? 0 : q);
     }
     double xw[3];

@@ -157,12 +157,15 @@ k_relist_small(int32_t B, SysArrays S, SlotArrays A, int64_t stride, int move_fi
         x[0] = (double)hi.x + lo.x; x[1] = (double)hi.y + lo.y; x[2] = (double)hi.z + lo.z;
       }
       double f[3];
+      const int pm = S.pmask[s];
       for (int a = 0; a < 3; a++) {
         double v = x[0] * g[a] + x[1] * g[3 + a] + x[2] * g[6 + a];
-        v -= floor(v);
-        if (v >= 1.0) v = 0.0;
+        if (pm >> a & 1) {
+          v -= floor(v);
+          if (v >= 1.0) v = 0.0;
+        }
         f[a] = v;
-        int q = (int)(v * nbv[a]);
+        int q = (int)floor(v * nbv[a]);
         kb[a] = q >= nbv[a] ? nbv[a] - 1 : (q < 0 ? 0 : q);
       }
       double xw[3];
@@ -268,6 +271,7 @@ __device__ void build_warp(int s, int wi, const SysArrays& S, const SlotArrays& 
   const DevPot& P = pots[S.pot[s]];
   const int nb0 = S.nb[3 * s], nb1 = S.nb[3 * s + 1], nb2 = S.nb[3 * s + 2];
   const int m0 = S.reach[3 * s], m1 = S.reach[3 * s + 1], m2 = S.reach[3 * s + 2];
+  const int pm = S.pmask[s];
   int64_t seg = S.seg_start[s];
   int boff = S.bin_off[s];
   int lbr = A.bin[k] - boff;                                   // padding lanes: any value
@@ -298,8 +302,10 @@ __device__ void build_warp(int s, int wi, const SysArrays& S, const SlotArrays& 
         int ix = floor_div(cx, nb0), iy = floor_div(cy, nb1), iz = floor_div(cz, nb2);
         int gb = boff + ((cz - iz * nb2) * nb1 + (cy - iy * nb1)) * nb0 + (cx - ix * nb0);
         my_code = img_code(ix, iy, iz);
-        my_start = (int)((int64_t)cstart[gb] - coff);
-        my_count = count[gb];
+        // a cell beyond the edge of a non-periodic axis is empty
+        const bool open_edge = ((pm & 1) == 0 && ix != 0) || ((pm & 2) == 0 && iy != 0) || ((pm & 4) == 0 && iz != 0);
+        my_start = open_edge ? 0 : (int)((int64_t)cstart[gb] - coff);
+        my_count = open_edge ? 0 : count[gb];
         if constexpr (!F64) {
           int64_t ti = (int64_t)s * kNCodes + my_code;
           my_sh = S.shift[2 * ti];
@@ -442,14 +448,19 @@ __device__ void build_atom(int s, int a, const SysArrays& S, const SlotArrays& A
   if constexpr (F64) { for (int c = 0; c < 3; c++) xi[c] = A.xd[3 * k + c]; }
   else { hi = A.xh[k]; lo = A.xl[k]; }
   int cnt = 0;
+  const int pm = S.pmask[s];
+  // along a non-periodic axis the stencil stops at the edges (no images)
+  const int xlo = (pm & 1) ? kx - m0 : max(kx - m0, 0), xhi = (pm & 1) ? kx + m0 : min(kx + m0, nb0 - 1);
   for (int dz = -m2; dz <= m2; dz++) {
     const int zz = kz + dz, iz = floor_div(zz, nb2), cz = zz - iz * nb2;
+    if (!(pm & 4) && iz != 0) continue;
     for (int dy = -m1; dy <= m1; dy++) {
       const int yy = ky + dy, iy = floor_div(yy, nb1), cy = yy - iy * nb1;
+      if (!(pm & 2) && iy != 0) continue;
       const int rowb = boff + (cz * nb1 + cy) * nb0;
-      for (int xx = kx - m0; xx <= kx + m0;) {
+      for (int xx = xlo; xx <= xhi;) {
         const int ix = floor_div(xx, nb0);
-        const int xe = min(kx + m0, (ix + 1) * nb0 - 1);
+        const int xe = min(xhi, (ix + 1) * nb0 - 1);
         const int gb0 = rowb + (xx - ix * nb0), gb1 = rowb + (xe - ix * nb0);
         const int q0 = (int)(cstart[gb0] - coff), q1 = (int)(cstart[gb1] - coff) + count[gb1];
         const int code = img_code(ix, iy, iz);
