@@ -293,6 +293,15 @@ ts_status ts_sched_fill(ts_sched* q, int64_t* ids_out, int cap, int* n_out);
 ts_status ts_sched_retire(ts_sched* q, const int64_t* ids, int n);
 ts_status ts_sched_stats(const ts_sched* q, int32_t* n_active, int64_t* n_pending, double* active_scaler);
 
+/* BinningAutobatcher (Sec. 3, Fig. 3, fixed-length runs): pack n systems of
+ * memory footprint sizes[k] (host, in the units of the maximum memory, e.g.
+ * atoms) into as few bins of `capacity` as the first-fit-decreasing
+ * heuristic finds (systems by decreasing size, ties by index; each into the
+ * first bin with room).  Writes bin_out[k] (host, [n]) and the bin count.
+ * A size above capacity returns TS_ERR_BUDGET; a size <= 0 or a bad argument
+ * TS_ERR_INVALID_ARG.  Pure host code. */
+ts_status ts_bin_pack(const double* sizes, int n, double capacity, int32_t* bin_out, int32_t* n_bins_out);
+
 /* Compact a batched device state: keep the systems whose keep[k] != 0
  * (host mask [n_systems]) and append n_new staged systems from host arrays
  * (pinned or pageable), writing the new state into dst (device arrays sized

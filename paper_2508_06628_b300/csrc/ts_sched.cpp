@@ -1,11 +1,13 @@
-// ts_sched.cpp -- host-side batching logic of the in-flight runtime
-// (TorchSim, Sec. 3): the memory probe of Fig. 2 and the admission queue of
-// the InFlightAutobatcher (Fig. 3).  No device memory is touched here.
+// ts_sched.cpp -- host-side batching logic (TorchSim, Sec. 3): the memory
+// probe of Fig. 2, the admission queue of the InFlightAutobatcher and the bin
+// packing of the BinningAutobatcher (Fig. 3).  No device memory is touched here.
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <deque>
 #include <new>
 #include <unordered_map>
+#include <vector>
 
 #include "../../include/ts.h"
 
@@ -93,5 +95,31 @@ extern "C" ts_status ts_sched_stats(const ts_sched* q, int32_t* n_active, int64_
   if (n_active) *n_active = (int32_t)q->active.size();
   if (n_pending) *n_pending = (int64_t)q->pending.size();
   if (active_scaler) *active_scaler = q->active_scaler;
+  return TS_OK;
+}
+
+// BinningAutobatcher: 1-D bin packing by first fit decreasing (the paper asks
+// for as few bins as possible and names no algorithm; exact packing is
+// NP-hard, and FFD uses at most 11/9 OPT + 6/9 bins).
+extern "C" ts_status ts_bin_pack(const double* sizes, int n, double capacity, int32_t* bin_out,
+                                 int32_t* n_bins_out) {
+  if (n < 0 || (n > 0 && (!sizes || !bin_out)) || !(capacity > 0) || !std::isfinite(capacity) || !n_bins_out)
+    return TS_ERR_INVALID_ARG;
+  for (int k = 0; k < n; k++) {
+    if (!(sizes[k] > 0) || !std::isfinite(sizes[k])) return TS_ERR_INVALID_ARG;
+    if (sizes[k] > capacity) return TS_ERR_BUDGET;
+  }
+  std::vector<int> order(n);
+  for (int k = 0; k < n; k++) order[k] = k;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return sizes[a] > sizes[b]; });
+  std::vector<double> room;
+  for (int k : order) {
+    size_t c = 0;
+    while (c < room.size() && room[c] < sizes[k]) c++;
+    if (c == room.size()) room.push_back(capacity);
+    room[c] -= sizes[k];
+    bin_out[k] = (int32_t)c;
+  }
+  *n_bins_out = (int32_t)room.size();
   return TS_OK;
 }

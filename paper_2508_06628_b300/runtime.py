@@ -1,11 +1,15 @@
-"""In-flight batched relaxation (TorchSim, arXiv 2508.06628, Sec. 3 and
-Fig. 3): sample systems from a stream until the memory budget is full, run a
-few FIRE steps on the whole batch, retire converged systems and admit new
-ones, until every system has converged.
+"""The two autobatchers of TorchSim (arXiv 2508.06628, Sec. 3 and Fig. 3).
 
-Orchestration only: admission decisions come from the library's scheduler
-(ts_sched_*), data movement from ts_batch_compact_admit, the relaxation from
-ts_fire_step; the host reads back one flag per system per round.
+* In-flight batched relaxation (variable length): sample systems from a
+  stream until the memory budget is full, run a few FIRE steps on the whole
+  batch, retire converged systems and admit new ones, until every system has
+  converged.  Admission decisions come from the library's scheduler
+  (ts_sched_*), data movement from ts_batch_compact_admit, the relaxation
+  from ts_fire_step; the host reads back one flag per system per round.
+* Binned fixed-length MD: pack the systems into as few bins of the maximum
+  memory as ts_bin_pack finds and evolve the bins one after another.
+
+Orchestration only: every step of the simulations runs in the library.
 """
 from __future__ import annotations
 
@@ -144,3 +148,54 @@ def relax_inflight(hb, pots, max_scaler, max_active=1024, n_inner=25, precision=
     L.ts_sched_destroy(q)
     b.close()
     return results, log
+
+
+def memory_sizes(hb, memory_scales_with="n_atoms"):
+    """Memory footprint of every system in the units of the maximum memory
+    (Sec. 3): ``n_atoms``, or ``n_atoms_x_density`` (atoms times atoms per
+    A^3, for neighbour counts that grow with density)."""
+    n = np.diff(hb.offsets).astype(np.float64)
+    if memory_scales_with == "n_atoms":
+        return n
+    if memory_scales_with == "n_atoms_x_density":
+        vol = np.abs(np.linalg.det(hb.cell))
+        return n * n / vol
+    raise ValueError(f"unknown memory_scales_with {memory_scales_with!r}")
+
+
+def run_binned(hb, pots, max_scaler, n_steps, dt, kind=ts.TS_LANGEVIN, gamma=0.0, seed=0, inner=10,
+               memory_scales_with="n_atoms", precision=ts.TS_MIXED, device=0):
+    """Fixed-length MD of every system of ``hb`` (BinningAutobatcher, Sec. 3,
+    Fig. 3): pack the systems into bins of ``max_scaler`` (ts_bin_pack) and
+    evolve the bins one after another, each for ``n_steps`` steps, through one
+    reused batch.  Returns ({system id: dict(pos, vel, E, KE, bin)}, bins)."""
+    torch = ts._torch()
+    dev = torch.device("cuda", device)
+    bins, n_bins = ts.bin_pack(memory_sizes(hb, memory_scales_with), max_scaler)
+    members = [np.nonzero(bins == k)[0] for k in range(n_bins)]
+    n_of = np.diff(hb.offsets)
+    atom_cap = int(max(n_of[m].sum() for m in members))
+    sys_cap = int(max(len(m) for m in members))
+    b = ts.Batch(pots, atom_cap, sys_cap, precision=precision, device=device)
+    stream = torch.cuda.Stream(device=dev)
+    results = {}
+    for k, ids in enumerate(members):
+        sub = hb.subset(ids)
+        s = ts.DeviceState.from_host(sub, device=dev)
+        E = torch.zeros(sub.n_systems, dtype=torch.float64, device=dev)
+        KE = torch.zeros_like(E)
+        with torch.cuda.stream(stream):
+            b.neighbor_build(s, force=True, stream=stream)   # a new set of systems: new layout
+            done = 0
+            while done < n_steps:
+                m = min(inner, n_steps - done)
+                b.md_step(s, m, dt, kind=kind, gamma=gamma, seed=seed, step0=done, E=E, KE=KE, stream=stream)
+                done += m
+            b.poll(stream)
+        stream.synchronize()
+        pos, vel, Eh, KEh = s.pos.cpu().numpy(), s.vel.cpu().numpy(), E.cpu().numpy(), KE.cpu().numpy()
+        off = sub.offsets
+        for j, i in enumerate(ids):
+            results[int(i)] = dict(pos=pos[off[j]:off[j + 1]], vel=vel[off[j]:off[j + 1]], E=Eh[j], KE=KEh[j], bin=k)
+    b.close()
+    return results, bins

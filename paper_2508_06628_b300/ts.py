@@ -97,6 +97,7 @@ def lib():
         L.ts_batch_memory_model.argtypes = [P, C.POINTER(C.c_double), C.POINTER(C.c_double)]
         L.ts_profile_pair.argtypes = [P, C.POINTER(State), I, P, C.c_size_t, C.POINTER(C.c_double),
                                       C.POINTER(C.c_int64), C.POINTER(C.c_int64), P]
+        L.ts_bin_pack.argtypes = [P, I, C.c_double, P, C.POINTER(C.c_int32)]
         _lib = L
     return _lib
 
@@ -271,6 +272,20 @@ class Batch:
         a, b = C.c_int64(), C.c_int64()
         lib().ts_batch_counters(self.h, C.byref(a), C.byref(b))
         return a.value, b.value
+
+
+def bin_pack(sizes, capacity):
+    """ts_bin_pack: first-fit-decreasing bins of ``capacity`` for the memory
+    footprints ``sizes``; returns (bin index per system, number of bins).
+    Host code only (no GPU needed)."""
+    sz = np.ascontiguousarray(np.asarray(sizes, dtype=np.float64))
+    out = np.zeros(len(sz), np.int32)
+    nb = C.c_int32()
+    st = lib().ts_bin_pack(sz.ctypes.data if len(sz) else None, len(sz), float(capacity),
+                           out.ctypes.data if len(sz) else None, C.byref(nb))
+    if st != TS_OK:
+        raise TSError(st, "ts_bin_pack")
+    return out, nb.value
 
 
 def default_skins(pots):
