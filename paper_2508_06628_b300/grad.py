@@ -133,3 +133,46 @@ def rdf_loss_and_grad(batch, state, dt, T, every, rmax, K, target, checkpoint=10
                                 state.pot_idx, state.uid)
             batch.vv_adjoint_step(st, xn, dt, ax, av, gth)
     return loss, g, gth
+
+
+def hessian_vector_product(batch, state, v, stream=None):
+    """H v, H = d2E/dx2 of the batch's potential energy (block diagonal over
+    systems), for a direction v [n_atoms, 3] (device, FP64).  The pair-force
+    adjoint with gF = v returns d<v, F>/dx = (dF/dx)^T v = -H v (F = -dE/dx,
+    H symmetric), so one backward launch gives one product (second-order work
+    of the kind phonon and elastic-constant codes need, Sec. 5).  The
+    neighbour list must be current (call neighbor_build first)."""
+    torch = _torch()
+    g = torch.zeros_like(state.pos)
+    batch.pair_forces_backward(state, v.contiguous(), None, None, gPos=g, stream=stream)
+    return -g
+
+
+def hessian_blocks(batch, state, stream=None):
+    """The Hessian block of every system, [3 n_s, 3 n_s] numpy arrays (A, eV/A^2),
+    from 3 * max_s n_s products: product (a, c) displaces local atom a along
+    axis c in every system at once."""
+    torch = _torch()
+    off = state.offsets_host()
+    n = np.diff(off)
+    N = int(off[-1])
+    blocks = [np.zeros((3 * k, 3 * k)) for k in n]
+    for a in range(int(n.max())):
+        for c in range(3):
+            v = torch.zeros((N, 3), dtype=torch.float64, device=state.pos.device)
+            rows = torch.as_tensor(off[:-1][n > a] + a, device=v.device)
+            v[rows, c] = 1.0
+            hv = hessian_vector_product(batch, state, v, stream=stream).cpu().numpy()
+            for s in np.nonzero(n > a)[0]:
+                blocks[s][:, 3 * a + c] = hv[off[s]:off[s + 1]].reshape(-1)
+    return blocks
+
+
+def gamma_frequencies(block, mass):
+    """Phonon angular frequencies at Gamma of one system (rad per internal time
+    unit; sqrt of the eigenvalues of M^-1/2 H M^-1/2, negative for unstable
+    modes), from its Hessian block and masses [n_s]."""
+    w = 1.0 / np.sqrt(np.repeat(np.asarray(mass, np.float64), 3))
+    d = 0.5 * (block + block.T) * w[:, None] * w[None, :]
+    lam = np.linalg.eigvalsh(d)
+    return np.sign(lam) * np.sqrt(np.abs(lam))

@@ -140,6 +140,11 @@ class DeviceState:
     def n_atoms(self):
         return int(self.pos.shape[0])
 
+    def offsets_host(self):
+        """System offsets [n_systems + 1] (host numpy) from system_idx."""
+        counts = np.bincount(self.system_idx.cpu().numpy(), minlength=self.n_systems)
+        return np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+
     def c(self):
         self._c = State(self.n_systems, self.n_atoms, _ptr(self.pos), _ptr(self.vel), _ptr(self.mass),
                         _ptr(self.cell), _ptr(self.pbc), _ptr(self.system_idx), _ptr(self.pot_idx), _ptr(self.uid))
