@@ -135,6 +135,46 @@ def rdf_loss_and_grad(batch, state, dt, T, every, rmax, K, target, checkpoint=10
     return loss, g, gth
 
 
+def fit_rdf(batch, state, target, dt, T, every, rmax, K, iters=10, lr=0.02, fit=((0, 0), (0, 1)),
+            checkpoint=100, on_iter=None):
+    """Differentiable fitting of potential parameters to a target RDF (Sec. 2,
+    ref. [19]): Adam on the entries ``fit`` (pot index, parameter index) of the
+    batch's parameters, every iteration a fresh trajectory from ``state``
+    (not modified) and its checkpointed adjoint (rdf_loss_and_grad).  Steps
+    are scaled by each parameter's starting magnitude (``lr`` is relative);
+    the step is halved whenever the loss rises (the moments carry the search
+    past a minimum otherwise).  Returns (the parameters with the lowest loss
+    [n_pots, 3] numpy, history of (loss, parameters))."""
+    params = np.array([list(p["p"]) for p in batch.pots], dtype=np.float64)
+    mask = np.zeros_like(params)
+    for q, c in fit:
+        mask[q, c] = 1.0
+    scale = np.abs(params) * mask
+    m = np.zeros_like(params)
+    v = np.zeros_like(params)
+    b1, b2, eps = 0.9, 0.999, 1e-12
+    history = []
+    best = (np.inf, params.copy())
+    for it in range(iters):
+        set_params(batch, params)
+        loss, _, gth = rdf_loss_and_grad(batch, state, dt, T, every, rmax, K, target, checkpoint=checkpoint)
+        history.append((loss, params.copy()))
+        if on_iter:
+            on_iter(it, loss, params)
+        if len(history) > 1 and loss > history[-2][0]:
+            lr *= 0.5
+        if loss < best[0]:
+            best = (loss, params.copy())
+        g = gth.cpu().numpy() * scale              # gradient in relative units of each parameter
+        m = b1 * m + (1 - b1) * g
+        v = b2 * v + (1 - b2) * g * g
+        mh = m / (1 - b1 ** (it + 1))
+        vh = v / (1 - b2 ** (it + 1))
+        params = params - lr * scale * mh / (np.sqrt(vh) + eps)
+    set_params(batch, best[1])
+    return best[1], history
+
+
 def hessian_vector_product(batch, state, v, stream=None):
     """H v, H = d2E/dx2 of the batch's potential energy (block diagonal over
     systems), for a direction v [n_atoms, 3] (device, FP64).  The pair-force
