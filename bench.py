@@ -33,7 +33,7 @@ BYTES_PER_ATOM = 32         # read own position, write own force, per atom-step
 # DRAM bytes (read + write) of one forces-only k_pair_small launch on ragged-mix-512, from one ncu
 # capture (profiles/k_pair_small_ragged_mix_512.md); reported only while the kernel's sources
 # (ts_pair.cu, then ts_internal.cuh) hash to the value recorded with the capture
-PAIR_TRAFFIC = {"bytes": 73_297_920 + 1_231_616, "source_sha1": "8e9b3a3a634029afb20b504d22e2352e16c32726"}
+PAIR_TRAFFIC = {"bytes": 73_058_048 + 1_058_816, "source_sha1": "0f2e0618892f6230be70bf2c13d6c51b84f5f8ba"}
 
 
 def pair_traffic():
