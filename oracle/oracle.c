@@ -433,6 +433,98 @@ void or_md(int B, const int64_t* offsets, double* x, double* v, const double* ma
 }
 
 /* ------------------------------------------------------------------------- */
+/* NVT with a Nose-Hoover chain (one of the integrators the paper lists,      */
+/* Sec. 1; chain of Martyna, Klein and Tuckerman 1992, time-reversible       */
+/* factorisation of Martyna, Tuckerman, Tobias and Klein 1996 with a single  */
+/* sub-step).  One step:                                                      */
+/*   C(dt/2); v += dt/(2m) F; x += dt v; F = F(x); v += dt/(2m) F; C(dt/2).   */
+/* Chain of M = 3 thermostats per system with positions xi_k and velocities  */
+/* w_k; masses Q_1 = Nf kT tau^2, Q_k = kT tau^2 (k > 1); Nf = 3N - 3 (the    */
+/* total momentum stays zero).  Forces on the chain: G_1 = (2K - Nf kT)/Q_1, */
+/* G_k = (Q_{k-1} w_{k-1}^2 - kT)/Q_k, with K the kinetic energy.  C(h):     */
+/*   w_M += h/2 G_M;                                                          */
+/*   for k = M-1 .. 1: w_k *= e^{-h/4 w_{k+1}}; w_k += h/2 G_k;               */
+/*                     w_k *= e^{-h/4 w_{k+1}};                               */
+/*   xi_k += h w_k (all k); atoms: v *= e^{-h w_1} (K *= e^{-2 h w_1});       */
+/*   for k = 1 .. M-1: w_k *= e^{-h/4 w_{k+1}}; w_k += h/2 G_k (current K or  */
+/*                     w_{k-1}); w_k *= e^{-h/4 w_{k+1}};                     */
+/*   w_M += h/2 G_M.                                                          */
+/* Conserved: K + U + sum_k Q_k w_k^2/2 + Nf kT xi_1 + kT sum_{k>1} xi_k.     */
+/* Pinned by: the conserved quantity; an inert chain (tau -> inf) reproduces  */
+/* velocity Verlet; time reversibility; <K> = Nf kT/2 on a long run.          */
+/* ------------------------------------------------------------------------- */
+#define OR_NHC_M 3
+static double nhc_half(double h, double K, double nf, double kT, double tau, double* st) {
+  double* xi = st; double* w = st + OR_NHC_M;
+  double Q[OR_NHC_M];
+  Q[0] = nf * kT * tau * tau;
+  for (int k = 1; k < OR_NHC_M; k++) Q[k] = kT * tau * tau;
+  const int M = OR_NHC_M;
+  double G = (Q[M - 2] * w[M - 2] * w[M - 2] - kT) / Q[M - 1];
+  w[M - 1] += 0.5 * h * G;
+  for (int k = M - 2; k >= 0; k--) {
+    double e = exp(-0.25 * h * w[k + 1]);
+    w[k] *= e;
+    G = k == 0 ? (2.0 * K - nf * kT) / Q[0] : (Q[k - 1] * w[k - 1] * w[k - 1] - kT) / Q[k];
+    w[k] += 0.5 * h * G;
+    w[k] *= e;
+  }
+  for (int k = 0; k < M; k++) xi[k] += h * w[k];
+  double scale = exp(-h * w[0]);
+  K *= scale * scale;
+  for (int k = 0; k < M - 1; k++) {
+    double e = exp(-0.25 * h * w[k + 1]);
+    w[k] *= e;
+    G = k == 0 ? (2.0 * K - nf * kT) / Q[0] : (Q[k - 1] * w[k - 1] * w[k - 1] - kT) / Q[k];
+    w[k] += 0.5 * h * G;
+    w[k] *= e;
+  }
+  G = (Q[M - 2] * w[M - 2] * w[M - 2] - kT) / Q[M - 1];
+  w[M - 1] += 0.5 * h * G;
+  return scale;
+}
+
+/* n_steps of NVT-NHC; nhc [B][2M] (xi_1..M, w_1..M) is read and updated;    */
+/* H_ext [B] (may be NULL) receives the conserved quantity at the end.        */
+void or_md_nhc(int B, const int64_t* offsets, double* x, double* v, const double* mass, const double* cells,
+               const uint8_t* pbc, const int32_t* pot_of_sys, const or_pot* pots, int use_cells, double dt,
+               int n_steps, const double* kT, double tau, double* nhc, double* E_pot, double* KE, double* H_ext) {
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int s = 0; s < B; s++) {
+    int64_t o = offsets[s]; int n = (int)(offsets[s + 1] - o);
+    const or_pot* P = pots + pot_of_sys[s];
+    const double* h = cells + 9 * s;
+    double* xs = x + 3 * o; double* vs = v + 3 * o;
+    double* st = nhc + 2 * OR_NHC_M * s;
+    const double nf = 3.0 * n - 3.0 > 1.0 ? 3.0 * n - 3.0 : 1.0;
+    double* F = (double*)malloc(sizeof(double) * 3 * (n > 0 ? n : 1));
+    double E = sys_forces(use_cells, n, xs, h, pbc + 3 * s, P, F);
+    for (int k = 0; k < n_steps; k++) {
+      double sc = nhc_half(0.5 * dt, kinetic(o, n, v, mass), nf, kT[s], tau, st);
+      for (int i = 0; i < 3 * n; i++) vs[i] *= sc;
+      for (int i = 0; i < n; i++)
+        for (int a = 0; a < 3; a++) vs[3 * i + a] += 0.5 * dt / mass[o + i] * F[3 * i + a];
+      for (int i = 0; i < 3 * n; i++) xs[i] += dt * vs[i];
+      E = sys_forces(use_cells, n, xs, h, pbc + 3 * s, P, F);
+      for (int i = 0; i < n; i++)
+        for (int a = 0; a < 3; a++) vs[3 * i + a] += 0.5 * dt / mass[o + i] * F[3 * i + a];
+      sc = nhc_half(0.5 * dt, kinetic(o, n, v, mass), nf, kT[s], tau, st);
+      for (int i = 0; i < 3 * n; i++) vs[i] *= sc;
+    }
+    double K = kinetic(o, n, v, mass);
+    if (E_pot) E_pot[s] = E;
+    if (KE) KE[s] = K;
+    if (H_ext) {
+      double Q1 = nf * kT[s] * tau * tau, Qk = kT[s] * tau * tau;
+      double He = K + E + 0.5 * Q1 * st[OR_NHC_M] * st[OR_NHC_M] + nf * kT[s] * st[0];
+      for (int k = 1; k < OR_NHC_M; k++) He += 0.5 * Qk * st[OR_NHC_M + k] * st[OR_NHC_M + k] + kT[s] * st[k];
+      H_ext[s] = He;
+    }
+    free(F);
+  }
+}
+
+/* ------------------------------------------------------------------------- */
 /* Variable-cell FIRE (Bitzek et al. 2006; the paper's "structural relaxation */
 /* optimizers", Sec. 1, run under in-flight batching, Sec. 3).               */
 /* Generalised coordinates per system: xt_i = x_i Fd^-T (N rows) and the cell */

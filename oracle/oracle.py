@@ -67,6 +67,8 @@ def lib():
         L.or_normals3.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, P]
         L.or_md.argtypes = [C.c_int, P, P, P, P, P, P, P, P, C.c_int, C.c_int, C.c_double, C.c_int, P,
                             C.c_double, C.c_uint32, P, C.c_uint64, P, P]
+        L.or_md_nhc.argtypes = [C.c_int, P, P, P, P, P, P, P, P, C.c_int, C.c_double, C.c_int, P, C.c_double, P, P,
+                                P, P]
         L.or_fire.argtypes = [C.c_int, P, P, P, P, P, P, C.c_int, P, P, P, C.c_int, P, P, P]
         L.or_forces_backward.argtypes = [C.c_int, P, P, P, P, P, P, C.c_int, C.c_int, P, P, P, P, P]
         L.or_rdf.argtypes = [C.c_int, P, P, P, P, C.c_double, C.c_int, C.c_int, P, P, P]
@@ -163,6 +165,24 @@ def md(offsets, x, v, mass, cells, pbc, pot_of_sys, pots, dt, n_steps, kind=0, k
                 int(use_cells), int(kind), float(dt), int(n_steps), _p(kT), float(gamma), int(seed), _p(uid),
                 int(step0), _p(E), _p(KE))
     return x, v, E, KE
+
+
+def md_nhc(offsets, x, v, mass, cells, pbc, pot_of_sys, pots, dt, n_steps, kT, tau, nhc=None, use_cells=False):
+    """NVT Nose-Hoover chain (M = 3) for n_steps.  nhc [B, 6] is the chain
+    state (xi_1..3, w_1..3), zero if None.  Returns new (x, v, E_pot[B], KE[B],
+    nhc[B, 6], H_ext[B] the conserved quantity); inputs are not modified."""
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    B = len(offsets) - 1
+    x = _f64(x).copy(); v = _f64(v).copy(); mass = _f64(mass); cells = _f64(cells)
+    pbc = np.ascontiguousarray(pbc, dtype=np.uint8).reshape(B, 3)
+    pos = np.ascontiguousarray(pot_of_sys, dtype=np.int32)
+    kT = _f64(np.broadcast_to(kT, (B,)))
+    st = np.zeros((B, 6)) if nhc is None else _f64(nhc).reshape(B, 6).copy()
+    P = make_pots(pots)
+    E = np.zeros(B); KE = np.zeros(B); H = np.zeros(B)
+    lib().or_md_nhc(B, _p(offsets), _p(x), _p(v), _p(mass), _p(cells), _p(pbc), _p(pos), C.cast(P, C.c_void_p),
+                    int(use_cells), float(dt), int(n_steps), _p(kT), float(tau), _p(st), _p(E), _p(KE), _p(H))
+    return x, v, E, KE, st, H
 
 
 FIRE_DEFAULTS = dict(dt0=0.1, dt_max=1.0, finc=1.1, fdec=0.5, alpha0=0.1, falpha=0.99, maxstep=0.2,

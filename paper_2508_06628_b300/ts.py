@@ -295,7 +295,7 @@ def bin_pack(sizes, capacity):
 
 def default_skins(pots):
     """Skin per potential, from a step-time sweep on the 512-system ragged batch at 300 K: 1.0 A for LJ
-    argon, 0.75 A for Morse Cu, 0.9 sigma for soft spheres (light, stiff particles whose thermal
+    argon, 0.5 A for Morse Cu, 0.9 sigma for soft spheres (light, stiff particles whose thermal
     excursions would otherwise force a re-listing every few steps), 0.3 sigma for reduced-unit LJ."""
     out = []
     for d in pots:
@@ -304,5 +304,5 @@ def default_skins(pots):
         elif d["kind"] == 0:
             out.append(0.3 * d["p"][0] if d["p"][0] < 2 else 1.0)
         else:
-            out.append(0.75)
+            out.append(0.5)
     return out

@@ -85,6 +85,70 @@ def test_baoab_equipartition(orc):
     assert abs(ks.mean() - target) < 4 * se + 1e-12
 
 
+def test_nhc_conserved_quantity(orc):
+    """NVT Nose-Hoover chain, argon heated from 50 K by a 120 K chain: K + U
+    changes by electron-volts while the extended energy stays put."""
+    b = W.single_lj_argon(seed=2, T=50.0)
+    kT, tau, dt = W.KB_EV * 120.0, 200.0 / W.T0_FS, 2.0 / W.T0_FS
+    x, v, st = b.pos, b.vel, None
+    H, KU = [], []
+    for blk in range(10):
+        x, v, E, K, st, He = orc.md_nhc(b.offsets, x, v, b.mass, b.cell, b.pbc, b.pot_idx, b.pots, dt, 50, [kT], tau,
+                                       nhc=st)
+        H.append(He[0]); KU.append(E[0] + K[0])
+    H, KU = np.array(H), np.array(KU)
+    assert KU.max() - KU.min() > 0.5                         # the chain moved real energy
+    assert np.abs(H - H[0]).max() < 2e-3 * (KU.max() - KU.min())
+
+
+def test_nhc_inert_chain_is_velocity_verlet(orc):
+    """With enormous thermostat masses the chain does nothing: velocity Verlet."""
+    b = W.single_lj_argon(seed=0)
+    dt = 2.0 / W.T0_FS
+    xa, va, Ea, Ka, st, _ = orc.md_nhc(b.offsets, b.pos, b.vel, b.mass, b.cell, b.pbc, b.pot_idx, b.pots, dt, 100,
+                                       [W.KB_EV * 50.0], 1e9)
+    xb, vb, Eb, Kb = orc.md(b.offsets, b.pos, b.vel, b.mass, b.cell, b.pbc, b.pot_idx, b.pots, dt, 100)
+    assert np.abs(xa - xb).max() < 1e-10 and np.abs(va - vb).max() < 1e-10
+    assert np.abs(st[0, 3:]).max() < 1e-12
+
+
+def test_nhc_time_reversible(orc):
+    """Reversing the atom and chain velocities retraces the trajectory (the
+    factorisation is symmetric)."""
+    b = W.single_lj_argon(seed=3, T=60.0)
+    kT, tau, dt = W.KB_EV * 90.0, 100.0 / W.T0_FS, 2.0 / W.T0_FS
+    st0 = np.array([[0.0, 0.0, 0.0, 0.01, -0.02, 0.005]])
+    # 60 steps: long enough to exercise the chain, short enough that chaotic
+    # growth of rounding errors stays far below the tolerance
+    x1, v1, _, _, st1, _ = orc.md_nhc(b.offsets, b.pos, b.vel, b.mass, b.cell, b.pbc, b.pot_idx, b.pots, dt, 60,
+                                      [kT], tau, nhc=st0)
+    back = st1.copy(); back[:, 3:] *= -1
+    x2, v2, _, _, st2, _ = orc.md_nhc(b.offsets, x1, -v1, b.mass, b.cell, b.pbc, b.pot_idx, b.pots, dt, 60,
+                                      [kT], tau, nhc=back)
+    assert np.abs(x2 - b.pos).max() < 1e-10
+    assert np.abs(v2 + b.vel).max() < 1e-10
+    assert np.abs(st2[:, 3:] + st0[:, 3:]).max() < 1e-10       # chain velocities reversed
+    assert np.abs(st2[:, :3] - st0[:, :3]).max() < 1e-10       # chain positions back
+
+
+def test_nhc_canonical_kinetic_energy(orc):
+    """A reduced-unit LJ liquid under the chain: <K> = Nf kT / 2 (Nf = 3N - 3)
+    within 4 standard errors of block averages."""
+    b = W.lj_liquid(seed=5, n_systems=1, reps=(3, 3, 3), kT=1.0, rattle=0.05)
+    kT, tau, dt = 1.0, 0.5, 0.005
+    x, v, E, K, st, _ = orc.md_nhc(b.offsets, b.pos, b.vel, b.mass, b.cell, b.pbc, b.pot_idx, b.pots, dt, 4000,
+                                   [kT], tau)
+    ks = []
+    for blk in range(40):
+        x, v, E, K, st, _ = orc.md_nhc(b.offsets, x, v, b.mass, b.cell, b.pbc, b.pot_idx, b.pots, dt, 250, [kT], tau,
+                                       nhc=st)
+        ks.append(K[0])
+    ks = np.array(ks)
+    target = 0.5 * (3 * len(b.pos) - 3) * kT
+    se = ks.std(ddof=1) / np.sqrt(len(ks) / 2)
+    assert abs(ks.mean() - target) < 4 * se
+
+
 def _golden_section(f, a, b, tol=1e-9):
     g = (np.sqrt(5) - 1) / 2
     c, d = b - g * (b - a), a + g * (b - a)
