@@ -168,13 +168,21 @@ int32_t ts_batch_max_neighbors(const ts_batch* b);
  * E and stress are summed per system in FP64, deterministically. */
 ts_status ts_pair_forces(ts_batch* b, ts_state* s, double* F, double* E, double* stress, void* stream);
 
-typedef enum { TS_NVE = 0, TS_LANGEVIN = 1 } ts_md_kind;
+typedef enum { TS_NVE = 0, TS_LANGEVIN = 1, TS_NVT_NHC = 2 } ts_md_kind;
 
-/* MD parameters.  NVE: velocity Verlet.  LANGEVIN: BAOAB with friction
- * gamma (1/t0) and per-system kT (device array [n_systems], eV); the noise
- * is Philox4x32-10 keyed by (seed, uid) with counter (step, atom index within
- * its system), so it is independent of batch layout.  step0 is the counter
- * of the first step of this call. */
+/* MD parameters (Sec. 1 lists NVE, NVT and Langevin integrators).
+ * NVE: velocity Verlet.  LANGEVIN: BAOAB with friction gamma (1/t0) and
+ * per-system kT (device array [n_systems], eV); the noise is Philox4x32-10
+ * keyed by (seed, uid) with counter (step, atom index within its system), so
+ * it is independent of batch layout.  step0 is the counter of the first step
+ * of this call.  NVT_NHC: Nose-Hoover chain of three per system (Martyna,
+ * Klein and Tuckerman 1992; time-reversible factorisation C(dt/2) B A B
+ * C(dt/2) of Martyna, Tuckerman, Tobias and Klein 1996), thermostat time
+ * constant tau (t0), masses Q1 = Nf kT tau^2 and Qk = kT tau^2 with
+ * Nf = 3n - 3; nhc is the chain state, device [n_systems][6] f64 (xi_1..3,
+ * then the thermostat velocities w_1..3; zeros to start), read and written.
+ * The extended energy K + U + sum Q_k w_k^2/2 + Nf kT xi_1 + kT (xi_2 + xi_3)
+ * is conserved. */
 typedef struct {
   int32_t kind;
   double dt;
@@ -182,6 +190,8 @@ typedef struct {
   const double* kT;
   uint32_t seed;
   uint64_t step0;
+  double tau;      /* NVT_NHC only */
+  double* nhc;     /* NVT_NHC only */
 } ts_md_params;
 
 /* Run n_steps MD steps on the whole batch (Sec. 4 runs Langevin MD).  The

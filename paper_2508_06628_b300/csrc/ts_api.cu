@@ -154,7 +154,7 @@ extern "C" ts_status ts_batch_create(const ts_batch_config* cfg, const ts_potent
   ok = ok && alloc(b, b->d_partial, (size_t)kPartialStride * b->Wcap) && alloc(b, b->d_warp_sys, b->Wcap) &&
        alloc(b, b->d_count, b->Ccap) && alloc(b, b->d_cstart, b->Ccap) &&
        alloc(b, b->d_bsum, (b->Ccap + 1023) / 1024 + 1) && alloc(b, b->d_starts, B + 1) &&
-       alloc(b, b->d_Eint, B) && alloc(b, b->d_Wint, 9 * B) && alloc(b, b->d_scal, 32 * B) &&
+       alloc(b, b->d_Eint, B) && alloc(b, b->d_Wint, 9 * B) && alloc(b, b->d_scal, 32 * B) && alloc(b, b->d_nhc, 6 * B) &&
        alloc(b, b->d_gparam_part, 4 * b->Wcap) && alloc(b, b->d_gacc, 3 * kMaxPots) &&
        alloc(b, b->d_items, b->Wcap) && alloc(b, b->d_tab_sys, B) && alloc(b, b->d_tab_base, B + 1) && alloc(b, b->d_tab_base_a, B + 1) &&
        alloc(b, b->d_tab_n, 3);
@@ -651,19 +651,29 @@ extern "C" ts_status ts_md_step(ts_batch* b, ts_state* s, const ts_md_params* p,
                                 void* stream) {
   ts_status r = check_state(b, s, true);
   if (r != TS_OK) return r;
-  if (!p || n_steps < 0 || !(p->dt > 0) || (p->kind != TS_NVE && p->kind != TS_LANGEVIN) ||
-      (p->kind == TS_LANGEVIN && (!p->kT || !(p->gamma >= 0))))
+  if (!p || n_steps < 0 || !(p->dt > 0) ||
+      (p->kind != TS_NVE && p->kind != TS_LANGEVIN && p->kind != TS_NVT_NHC) ||
+      (p->kind == TS_LANGEVIN && (!p->kT || !(p->gamma >= 0))) ||
+      (p->kind == TS_NVT_NHC && (!p->kT || !p->nhc || !(p->tau > 0))))
     return fail(b, TS_ERR_INVALID_ARG, "bad MD parameters");
   cudaStream_t st = (cudaStream_t)stream;
   r = prologue(b, s, st, true);
   if (r != TS_OK) return r;
-  if (p->kind == TS_LANGEVIN &&
+  if (p->kind != TS_NVE &&
       !cuda_ok(b, cudaMemcpyAsync(b->S.kT, p->kT, 8 * b->B, cudaMemcpyDeviceToDevice, st), "kT"))
+    return TS_ERR_CUDA;
+  // the chain state lives in batch memory during the call (the step loop is
+  // captured once as a graph, with fixed pointers)
+  if (p->kind == TS_NVT_NHC &&
+      !cuda_ok(b, cudaMemcpyAsync(b->d_nhc, p->nhc, 48 * b->B, cudaMemcpyDeviceToDevice, st), "nhc"))
     return TS_ERR_CUDA;
   ensure_forces(b, st);
   double c1 = exp(-p->gamma * p->dt);
   r = md_loop(b, st, p, n_steps, c1, E != nullptr || KE != nullptr);
   if (r != TS_OK) return r;
+  if (p->kind == TS_NVT_NHC &&
+      !cuda_ok(b, cudaMemcpyAsync(p->nhc, b->d_nhc, 48 * b->B, cudaMemcpyDeviceToDevice, st), "nhc"))
+    return TS_ERR_CUDA;
   reduce_sys(b, st, E, nullptr, KE);
   export_state(b, st, s->pos, s->vel);
   return cuda_ok(b, cudaGetLastError(), "ts_md_step") ? TS_OK : TS_ERR_CUDA;

@@ -14,6 +14,7 @@ struct ts_graph_entry {
   bool need_e = false;
   double dt = 0, c1 = 0;
   uint32_t seed = 0;
+  double tau = 0;
   cudaStream_t stream = nullptr;
   cudaGraphExec_t exec = nullptr;
   int64_t kernels = 0;      // kernel nodes in the graph
@@ -59,6 +60,7 @@ struct ts_batch {
   double* d_Eint = nullptr;
   double* d_Wint = nullptr;
   double* d_scal = nullptr;         // per-system FIRE / scratch scalars [16 B]
+  double* d_nhc = nullptr;          // Nose-Hoover chain state during a call [6 per system]
   double* d_gparam_part = nullptr;  // per-warp parameter-gradient partials [4 Wcap]
   double* d_gacc = nullptr;
   std::vector<void*> allocations;

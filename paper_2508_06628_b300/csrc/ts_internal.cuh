@@ -178,6 +178,14 @@ __device__ __forceinline__ void pos_add(float& hi, float& lo, float d) {
     lo -= q;
   }
 }
+// (h, l) <- c (h, l) as a double-float: the product of the high part exactly
+// (fma residual), then renormalised
+__device__ __forceinline__ void df_scale(float& h, float& l, float c) {
+  const float p = c * h;
+  const float e = fmaf(c, h, -p) + c * l;
+  h = p + e;
+  l = e - (h - p);
+}
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   s = a + b;
   float bb = s - a;

@@ -65,7 +65,7 @@ __device__ __forceinline__ void normals3(uint64_t step, uint32_t la, uint32_t se
 template <bool F64, int KIND>
 __global__ void k_md_kick_drift(int64_t Npad, SysArrays S, SlotArrays A, const DevPot* __restrict__ pots, double kick,
                                 double dt, double c1, uint32_t seed, const uint64_t* __restrict__ step_base,
-                                uint64_t koff) {
+                                uint64_t koff, const double* __restrict__ vscale) {
   const uint64_t step = *step_base + koff;
   const float omc2f = (float)(1.0 - c1 * c1);
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < Npad; k += (int64_t)gridDim.x * blockDim.x) {
@@ -84,8 +84,9 @@ __global__ void k_md_kick_drift(int64_t Npad, SysArrays S, SlotArrays A, const D
       double* v = A.vd + 3 * k;
       double* x = A.xd + 3 * k;
       const double* f = A.Fd + 3 * k;
+      if (KIND == 2) { const double c = vscale[s]; for (int q = 0; q < 3; q++) v[q] *= c; }   // chain scaling
       for (int c = 0; c < 3; c++) v[c] += kick * mi * f[c];
-      if (KIND == 0) {
+      if (KIND != 1) {
         for (int c = 0; c < 3; c++) x[c] += dt * v[c];
       } else {
         osc = sqrt((1.0 - c1 * c1) * S.kT[s] * mi);
@@ -97,9 +98,13 @@ __global__ void k_md_kick_drift(int64_t Npad, SysArrays S, SlotArrays A, const D
       dx = x[0] - xr[0]; dy = x[1] - xr[1]; dz = x[2] - xr[2];
     } else {
       float4 vh = A.vh[k], vl = A.vl[k], xh = A.xh[k], xl = A.xl[k], f = A.F[k];
+      if (KIND == 2) {   // chain scaling of the double-float velocity
+        const float c = (float)vscale[s];
+        df_scale(vh.x, vl.x, c); df_scale(vh.y, vl.y, c); df_scale(vh.z, vl.z, c);
+      }
       float a = (float)kick * vh.w;
       df_add(vh.x, vl.x, a * f.x); df_add(vh.y, vl.y, a * f.y); df_add(vh.z, vl.z, a * f.z);
-      if (KIND == 0) {
+      if (KIND != 1) {
         float t = (float)dt;
         pos_add(xh.x, xl.x, t * vh.x + t * vl.x);
         pos_add(xh.y, xl.y, t * vh.y + t * vl.y);
@@ -141,7 +146,8 @@ __global__ void k_md_kick_drift(int64_t Npad, SysArrays S, SlotArrays A, const D
 
 // closing half kick of the last step; kinetic energy per warp (partial slot 7)
 template <bool F64>
-__global__ void k_md_final(int32_t n_warps, SysArrays S, SlotArrays A, double kick, double* partial) {
+__global__ void k_md_final(int32_t n_warps, SysArrays S, SlotArrays A, double kick, double* partial,
+                           const double* __restrict__ vscale) {
   int w = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
   int lane = threadIdx.x & 31;
   if (w >= n_warps) return;
@@ -153,11 +159,16 @@ __global__ void k_md_final(int32_t n_warps, SysArrays S, SlotArrays A, double ki
       double* v = A.vd + 3 * k;
       const double* f = A.Fd + 3 * k;
       for (int c = 0; c < 3; c++) v[c] += kick * mi * f[c];
+      if (vscale) { const double c = vscale[A.sys[k]]; for (int q = 0; q < 3; q++) v[q] *= c; }
       ke = 0.5 / mi * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
     } else {
       float4 vh = A.vh[k], vl = A.vl[k], f = A.F[k];
       float a = (float)kick * vh.w;
       df_add(vh.x, vl.x, a * f.x); df_add(vh.y, vl.y, a * f.y); df_add(vh.z, vl.z, a * f.z);
+      if (vscale) {
+        const float c = (float)vscale[A.sys[k]];
+        df_scale(vh.x, vl.x, c); df_scale(vh.y, vl.y, c); df_scale(vh.z, vl.z, c);
+      }
       A.vh[k] = vh; A.vl[k] = vl;
       double v0 = (double)vh.x + vl.x, v1 = (double)vh.y + vl.y, v2 = (double)vh.z + vl.z;
       ke = 0.5 / (double)vh.w * (v0 * v0 + v1 * v1 + v2 * v2);
@@ -169,5 +180,60 @@ __global__ void k_md_final(int32_t n_warps, SysArrays S, SlotArrays A, double ki
 
 
 __global__ void k_set_u64(uint64_t* p, uint64_t v) { *p = v; }
+
+// NVT Nose-Hoover chain (Martyna, Klein and Tuckerman 1992), chain of three
+// per system, with the time-reversible factorisation of Martyna, Tuckerman,
+// Tobias and Klein 1996: C(dt/2) B A (forces) B C(dt/2).  One chain half-step
+// C(h), K the kinetic energy, Nf = 3n - 3, Q1 = Nf kT tau^2, Qk = kT tau^2:
+// the last thermostat velocity takes a quarter kick from its force, the
+// others (from the top down) are damped by the next one over h/4, kicked by
+// h/2 and damped again; the thermostat positions advance by h w; the atoms'
+// velocities scale by exp(-h w1); the same sweep runs bottom up with the new
+// K.  Returns the velocity scale.
+__device__ double nhc_half_step(double h, double K, double nf, double kT, double tau, double* xi, double* w) {
+  constexpr int M = 3;
+  const double q1 = nf * kT * tau * tau, qk = kT * tau * tau;
+  auto force = [&](int k, double Kin) {   // G_k
+    return k == 0 ? (2.0 * Kin - nf * kT) / q1 : ((k == 1 ? q1 : qk) * w[k - 1] * w[k - 1] - kT) / qk;
+  };
+  w[M - 1] += 0.5 * h * force(M - 1, K);
+  for (int k = M - 2; k >= 0; k--) {
+    const double d = exp(-0.25 * h * w[k + 1]);
+    w[k] = (w[k] * d + 0.5 * h * force(k, K)) * d;
+  }
+  for (int k = 0; k < M; k++) xi[k] += h * w[k];
+  const double sc = exp(-h * w[0]);
+  K *= sc * sc;
+  for (int k = 0; k < M - 1; k++) {
+    const double d = exp(-0.25 * h * w[k + 1]);
+    w[k] = (w[k] * d + 0.5 * h * force(k, K)) * d;
+  }
+  w[M - 1] += 0.5 * h * force(M - 1, K);
+  return sc;
+}
+
+// One warp per system: the kinetic energy from the per-warp partials (slot 7,
+// fixed order), `halves` chain half-steps of dt/2 (two between consecutive
+// steps, one at the ends of a call), the product of their velocity scales.
+// nhc: [B][6] (xi_1..3, w_1..3).
+__global__ void k_nhc_update(int32_t B, SysArrays S, const double* __restrict__ partial, double dt, double tau,
+                             int halves, double* nhc, double* vscale) {
+  const int s = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (s >= B) return;
+  double K = 0;
+  for (int w = S.warp_start[s] + lane; w < S.warp_end[s]; w += 32) K += partial[(int64_t)w * kPartialStride + 7];
+  K = warp_sum(K);
+  if (lane != 0) return;
+  const double nf = fmax(3.0 * S.n_atoms[s] - 3.0, 1.0);
+  double* st = nhc + 6 * (int64_t)s;
+  double sc = 1.0;
+  for (int q = 0; q < halves; q++) {
+    const double c = nhc_half_step(0.5 * dt, K, nf, S.kT[s], tau, st, st + 3);
+    K *= c * c;
+    sc *= c;
+  }
+  vscale[s] = sc;
+}
 
 }  // namespace ts

@@ -15,18 +15,41 @@ static void md_body(ts_batch* b, cudaStream_t st, const ts_md_params* p, int n_s
     int64_t blocks = (b->Npad + 255) / 256;
     g = (int)(blocks < 148 * 16 ? (blocks < 1 ? 1 : blocks) : 148 * 16);
   }
+  const int wblocks = (int)(((int64_t)b->nwarps * 32 + 127) / 128);
+  const int sblocks = (int)(((int64_t)b->B * 32 + 127) / 128);
+  const bool nhc = p->kind == TS_NVT_NHC;
+  double* vscale = b->d_scal;   // per-system velocity scale of the chain
+  auto final_ke = [&](double kick, const double* scale) {   // kick (if any), scale (if any), KE partials
+    if (b->f64) k_md_final<true><<<wblocks, 128, 0, st>>>(b->nwarps, b->S, b->A, kick, b->d_partial, scale);
+    else k_md_final<false><<<wblocks, 128, 0, st>>>(b->nwarps, b->S, b->A, kick, b->d_partial, scale);
+    b->launches++;
+  };
+  auto chain = [&](int halves) {
+    k_nhc_update<<<sblocks, 128, 0, st>>>(b->B, b->S, b->d_partial, p->dt, p->tau, halves, b->d_nhc, vscale);
+    b->launches++;
+  };
+  if (nhc && n_steps > 0) {   // the opening chain half-step of the first step
+    final_ke(0.0, nullptr);
+    chain(1);
+  }
   for (int k = 0; k < n_steps; k++) {
-    double kick = k == 0 ? 0.5 * p->dt : p->dt;
+    // BAOAB and NVE merge the closing half kick of a step with the opening
+    // one of the next; the chain sits between them, so NHC kicks by dt/2
+    double kick = (k == 0 || nhc) ? 0.5 * p->dt : p->dt;
     if (b->f64) {
       if (p->kind == TS_NVE)
-        k_md_kick_drift<true, 0><<<g, 256, 0, st>>>(b->Npad, b->S, b->A, b->d_pots, kick, p->dt, c1, p->seed, b->d_step, k);
+        k_md_kick_drift<true, 0><<<g, 256, 0, st>>>(b->Npad, b->S, b->A, b->d_pots, kick, p->dt, c1, p->seed, b->d_step, k, nullptr);
+      else if (p->kind == TS_LANGEVIN)
+        k_md_kick_drift<true, 1><<<g, 256, 0, st>>>(b->Npad, b->S, b->A, b->d_pots, kick, p->dt, c1, p->seed, b->d_step, k, nullptr);
       else
-        k_md_kick_drift<true, 1><<<g, 256, 0, st>>>(b->Npad, b->S, b->A, b->d_pots, kick, p->dt, c1, p->seed, b->d_step, k);
+        k_md_kick_drift<true, 2><<<g, 256, 0, st>>>(b->Npad, b->S, b->A, b->d_pots, kick, p->dt, c1, p->seed, b->d_step, k, vscale);
     } else {
       if (p->kind == TS_NVE)
-        k_md_kick_drift<false, 0><<<g, 256, 0, st>>>(b->Npad, b->S, b->A, b->d_pots, kick, p->dt, c1, p->seed, b->d_step, k);
+        k_md_kick_drift<false, 0><<<g, 256, 0, st>>>(b->Npad, b->S, b->A, b->d_pots, kick, p->dt, c1, p->seed, b->d_step, k, nullptr);
+      else if (p->kind == TS_LANGEVIN)
+        k_md_kick_drift<false, 1><<<g, 256, 0, st>>>(b->Npad, b->S, b->A, b->d_pots, kick, p->dt, c1, p->seed, b->d_step, k, nullptr);
       else
-        k_md_kick_drift<false, 1><<<g, 256, 0, st>>>(b->Npad, b->S, b->A, b->d_pots, kick, p->dt, c1, p->seed, b->d_step, k);
+        k_md_kick_drift<false, 2><<<g, 256, 0, st>>>(b->Npad, b->S, b->A, b->d_pots, kick, p->dt, c1, p->seed, b->d_step, k, vscale);
     }
     b->launches++;
     bool ew = need_e && k == n_steps - 1;
@@ -34,11 +57,13 @@ static void md_body(ts_batch* b, cudaStream_t st, const ts_md_params* p, int n_s
       relist(b, st, false);
       pair(b, st, ew, kPairAll);
     }
+    if (nhc) {   // closing half kick and the kinetic energy, then the chain (two half-steps between steps)
+      final_ke(0.5 * p->dt, nullptr);
+      chain(k == n_steps - 1 ? 1 : 2);
+    }
   }
-  int blocks = (int)(((int64_t)b->nwarps * 32 + 127) / 128);
-  if (b->f64) k_md_final<true><<<blocks, 128, 0, st>>>(b->nwarps, b->S, b->A, n_steps > 0 ? 0.5 * p->dt : 0.0, b->d_partial);
-  else k_md_final<false><<<blocks, 128, 0, st>>>(b->nwarps, b->S, b->A, n_steps > 0 ? 0.5 * p->dt : 0.0, b->d_partial);
-  b->launches++;
+  if (nhc) final_ke(0.0, n_steps > 0 ? vscale : nullptr);   // the last chain scaling, kinetic energy
+  else final_ke(n_steps > 0 ? 0.5 * p->dt : 0.0, nullptr);
   clear_dirty(b, st);
 }
 
@@ -54,7 +79,7 @@ ts_status md_loop(ts_batch* b, cudaStream_t st, const ts_md_params* p, int n_ste
   if (capturable) {
     for (auto& g : b->graphs) {
       if (g.kind == 0 && g.n_steps == n_steps && g.md_kind == p->kind && g.need_e == need_e && g.dt == p->dt &&
-          g.c1 == c1 && g.seed == p->seed && g.stream == st) {
+          g.c1 == c1 && g.seed == p->seed && g.tau == p->tau && g.stream == st) {
         if (!cuda_ok(b, cudaGraphLaunch(g.exec, st), "cudaGraphLaunch")) return TS_ERR_CUDA;
         b->launches += g.kernels;
         return TS_OK;
@@ -72,7 +97,7 @@ ts_status md_loop(ts_batch* b, cudaStream_t st, const ts_md_params* p, int n_ste
         cudaGraphDestroy(graph);
         ts_graph_entry ge;
         ge.kind = 0; ge.n_steps = n_steps; ge.md_kind = p->kind; ge.need_e = need_e; ge.dt = p->dt; ge.c1 = c1;
-        ge.seed = p->seed; ge.stream = st; ge.exec = exec; ge.kernels = nk;
+        ge.seed = p->seed; ge.tau = p->tau; ge.stream = st; ge.exec = exec; ge.kernels = nk;
         if (b->graphs.size() > 16) { cudaGraphExecDestroy(b->graphs.front().exec); b->graphs.erase(b->graphs.begin()); }
         b->graphs.push_back(ge);
         if (!cuda_ok(b, cudaGraphLaunch(exec, st), "cudaGraphLaunch")) return TS_ERR_CUDA;
