@@ -345,8 +345,9 @@ ts_status ts_batch_poll(ts_batch* b, void* stream, int timeout_ms);
  * fastest; cached under cfg->autotune_cache by (potential mix, size class). */
 ts_status ts_autotune(ts_batch* b, ts_state* s, void* stream);
 
-/* Measurement hook: launch the pair-force kernel alone (forces only, the form
- * an MD step uses) reps times on the current lists, each launch preceded by
+/* Measurement hook: launch the pair-force kernel alone (forces only, from the
+ * inner lists, the form an MD step uses) reps times, after re-listing flagged
+ * systems and re-filtering every inner list, each launch preceded by
  * a write of flush_bytes to flush_buf (device scratch, may be NULL) to evict
  * L2, timing each launch with CUDA events on the stream.  Synchronises.
  * ms_out (host): mean launch duration in ms; pairs_out (host, may be NULL):
@@ -385,6 +386,17 @@ const char* ts_last_error(const ts_batch* b);
 /* Counters for reporting: kernel launches issued so far by this batch, and
  * neighbour-list rebuilds (system re-listings) so far. */
 ts_status ts_batch_counters(const ts_batch* b, int64_t* launches, int64_t* relists);
+
+/* Inner-list refreshes so far (one per system and refresh).  MD steps compute
+ * forces from an inner list, the entries of the Verlet list within
+ * rc + f * skin (f = 0.3, or TS_INNER at batch creation; 1 turns pruning
+ * off).  A system's inner list is re-filtered from its Verlet list by the
+ * pair launch of the MD step in which it was re-listed or one of its atoms
+ * had moved f * skin / 2 since the last filtering; that launch runs the full
+ * list.  Pairs beyond rc contribute exactly zero, so results are
+ * bit-identical with pruning on or off; this count is for reporting.
+ * Synchronises the device; TS_ERR_INVALID_ARG on a null argument. */
+ts_status ts_batch_prunes(const ts_batch* b, int64_t* prunes);
 
 #ifdef __cplusplus
 }

@@ -57,6 +57,7 @@ size_t scratch_bytes(int64_t Ncap, int64_t Bcap, int64_t Ccap, int32_t max_nbrs,
                            3 * 8 * 3 /*tmp d0,d1*/ + 4 * 8 /*tmp d2*/ + 2 * 3 * 8 /*gd*/)
                         : (2 * 16 /*x*/ + 2 * 16 /*v*/ + 16 /*F*/ + 2 * 16 /*xr*/ + 2 * 16 + 2 * 16 /*tmp f*/ +
                            2 * 16 /*g*/);
+  per_slot += (f64 ? 3 * 8 : 2 * 16) /*prune reference*/ + 4 /*nn_in*/ + (size_t)max_nbrs * 4 /*inner list*/;
   per_slot += 4 * 4 /*perm sys bin nn*/ + 3 * 4 /*tmp i*/ + (size_t)max_nbrs * 4 + 8 * 8 / 32 /*partials*/ + 4 / 32 /*warp_sys*/ + 16 / 32 /*pair work items*/;
   size_t per_sys = 8 * 4 + 9 * 8 * 3 + 9 * 4 + 6 * 4 + 4 * 4 + 8 + 12 /*list-build work table*/ + (size_t)kNCodes * (32 + 24 + 16);
   return per_slot * (size_t)Ncap + per_sys * (size_t)Bcap + (size_t)Ccap * 8;
@@ -120,6 +121,14 @@ extern "C" ts_status ts_batch_create(const ts_batch_config* cfg, const ts_potent
       if (!(f > 0 && f <= 1)) f = 1.0;
       D.soon2 = f * f;
     }
+    {   // inner skin of the pruned list: a fraction of the skin (TS_INNER; 1 = no pruning)
+      const char* e = getenv("TS_INNER");
+      double f = e ? atof(e) : kInnerSkinFraction;
+      if (!(f > 0 && f <= 1)) f = 1.0;
+      double sin = f * P.skin, ri = rc + sin + kListBand;
+      D.rin2d = ri * ri; D.rin2f = (float)D.rin2d;
+      D.half_in2d = 0.25 * sin * sin; D.half_in2f = (float)D.half_in2d;
+    }
     D.rlist_in2f = (float)((D.rlist - kListBand) * (D.rlist - kListBand));
     D.rlist_out2f = (float)((D.rlist + kListBand) * (D.rlist + kListBand));
     D.half_skin2f = (float)(0.25 * P.skin * P.skin);
@@ -136,18 +145,18 @@ extern "C" ts_status ts_batch_create(const ts_batch_config* cfg, const ts_potent
   ok = ok && alloc(b, S.seg_start, B) && alloc(b, S.n_atoms, B) && alloc(b, S.caller_off, B + 1) && alloc(b, S.pot, B) &&
        alloc(b, S.uid, B) && alloc(b, S.bin_off, B) && alloc(b, S.bin_cap, B) && alloc(b, S.warp_start, B) &&
        alloc(b, S.warp_end, B) && alloc(b, S.h, 9 * B) && alloc(b, S.hinv, 9 * B) && alloc(b, S.hinvf, 9 * B) && alloc(b, S.href, 9 * B) &&
-       alloc(b, S.nb, 3 * B) && alloc(b, S.reach, 3 * B) && alloc(b, S.pmask, B) && alloc(b, S.relist, B) && alloc(b, S.dirty, B) &&
+       alloc(b, S.nb, 3 * B) && alloc(b, S.reach, 3 * B) && alloc(b, S.pmask, B) && alloc(b, S.relist, B) && alloc(b, S.prune, B) && alloc(b, S.dirty, B) &&
        alloc(b, S.soon, B) && alloc(b, S.any, 1) &&
        alloc(b, S.kT, B) && alloc(b, S.shift, 2 * B * kNCodes) && alloc(b, S.shiftd, 3 * B * kNCodes) && alloc(b, S.shiftq, B * kNCodes);
   ok = ok && alloc(b, A.perm, N) && alloc(b, A.sys, N) && alloc(b, A.bin, N) && alloc(b, A.nn, N) &&
-       alloc(b, A.nbr, (size_t)b->max_nbrs * N) && alloc(b, A.tmp_i0, N) && alloc(b, A.tmp_i1, N) &&
+       alloc(b, A.nbr, (size_t)b->max_nbrs * N) && alloc(b, A.nbr_in, (size_t)b->max_nbrs * N) && alloc(b, A.nn_in, N) && alloc(b, A.tmp_i0, N) && alloc(b, A.tmp_i1, N) &&
        alloc(b, A.tmp_i2, N);
   if (b->f64) {
-    ok = ok && alloc(b, A.xd, 3 * N) && alloc(b, A.vd, 3 * N) && alloc(b, A.Fd, 3 * N) && alloc(b, A.minvd, N) &&
+    ok = ok && alloc(b, A.xpd, 3 * N) && alloc(b, A.xd, 3 * N) && alloc(b, A.vd, 3 * N) && alloc(b, A.Fd, 3 * N) && alloc(b, A.minvd, N) &&
          alloc(b, A.xrd, 3 * N) && alloc(b, A.tmp_d0, 3 * N) && alloc(b, A.tmp_d1, 3 * N) &&
          alloc(b, A.tmp_d2, 4 * N) && alloc(b, A.gd0, 3 * N) && alloc(b, A.gd1, 3 * N);
   } else {
-    ok = ok && alloc(b, A.xh, N) && alloc(b, A.xl, N) && alloc(b, A.vh, N) && alloc(b, A.vl, N) && alloc(b, A.F, N) &&
+    ok = ok && alloc(b, A.xph, N) && alloc(b, A.xpl, N) && alloc(b, A.xh, N) && alloc(b, A.xl, N) && alloc(b, A.vh, N) && alloc(b, A.vl, N) && alloc(b, A.F, N) &&
          alloc(b, A.xrh, N) && alloc(b, A.xrl, N) && alloc(b, A.tmp_f0, 2 * N) && alloc(b, A.tmp_f1, N) &&
          alloc(b, A.tmp_f2, N) && alloc(b, A.tmp_f3, N) && alloc(b, A.g0, N) && alloc(b, A.g1, N);
   }
@@ -163,6 +172,7 @@ extern "C" ts_status ts_batch_create(const ts_batch_config* cfg, const ts_potent
   if (ok) ok = cuda_ok(b, cudaMemset(A.perm, 0xff, sizeof(int32_t) * N), "memset") &&
                cuda_ok(b, cudaMemset(A.sys, 0xff, sizeof(int32_t) * N), "memset") &&
                cuda_ok(b, cudaMemset(A.nn, 0, sizeof(int32_t) * N), "memset") &&
+               cuda_ok(b, cudaMemset(A.nn_in, 0, sizeof(int32_t) * N), "memset") &&
                cuda_ok(b, cudaMemset(b->d_partial, 0, sizeof(double) * kPartialStride * b->Wcap), "memset");
   if (ok) ok = cuda_ok(b, cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming), "event");
   if (ok) {
@@ -246,6 +256,15 @@ extern "C" ts_status ts_batch_counters(const ts_batch* b, int64_t* launches, int
     cudaMemcpy(c, b->d_counters, sizeof c, cudaMemcpyDeviceToHost);
     *relists = c[0];
   }
+  return TS_OK;
+}
+
+extern "C" ts_status ts_batch_prunes(const ts_batch* b, int64_t* prunes) {
+  if (!b || !prunes) return TS_ERR_INVALID_ARG;
+  int64_t c[2] = {0, 0};
+  if (!cuda_ok(const_cast<ts_batch*>(b), cudaMemcpy(c, b->d_counters, sizeof c, cudaMemcpyDeviceToHost), "d2h"))
+    return TS_ERR_CUDA;
+  *prunes = c[1];
   return TS_OK;
 }
 
@@ -421,6 +440,7 @@ ts_status derive_topology(ts_batch* b, const ts_state* s, cudaStream_t st) {
   ok = cuda_ok(b, cudaMemcpyAsync(S.relist, ones.data(), 4 * B, cudaMemcpyHostToDevice, st), "h2d") &&
        cuda_ok(b, cudaMemcpyAsync(S.dirty, ones.data(), 4 * B, cudaMemcpyHostToDevice, st), "h2d") &&
        cuda_ok(b, cudaMemsetAsync(S.soon, 0, 4 * B, st), "memset") && cuda_ok(b, cudaMemsetAsync(S.any, 0, 4, st), "memset") &&
+       cuda_ok(b, cudaMemsetAsync(S.prune, 0, 4 * B, st), "memset") &&
        cuda_ok(b, cudaMemsetAsync(b->d_count, 0, 4 * b->Ccap, st), "memset") &&
        cuda_ok(b, cudaStreamSynchronize(st), "sync");
   if (!ok) return TS_ERR_CUDA;
@@ -440,14 +460,19 @@ ts_status check_state(ts_batch* b, const ts_state* s, bool need_vel) {
 
 // Per-call prologue: topology (if needed), cell geometry, image shifts,
 // position import with dirty / skin flags.
-ts_status prologue(ts_batch* b, ts_state* s, cudaStream_t st, bool import_vel) {
+ts_status prologue(ts_batch* b, ts_state* s, cudaStream_t st, bool import_vel, bool fire) {
   cudaSetDevice(b->cfg.device);
   if (!b->topo_valid || s->n_systems != b->B || s->n_atoms != b->N) {
     ts_status r = derive_topology(b, s, st);
     if (r != TS_OK) return r;
   }
   int B = b->B;
-  k_geometry<<<(B + 127) / 128, 128, 0, st>>>(B, b->S, s->cell, s->pbc, b->d_pots, b->d_err);
+  // A cell other than the one the lists were built for: every call but FIRE
+  // checks against the listing cell (its skin test has no room for a cell
+  // change); FIRE, whose own test budgets the cell change since the listing,
+  // checks only for a change made by the caller since the last call.
+  const int cell_check = b->first_import ? 0 : (fire ? 1 : 2);
+  k_geometry<<<(B + 127) / 128, 128, 0, st>>>(B, b->S, s->cell, s->pbc, b->d_pots, b->d_err, cell_check);
   k_shift_table<<<(int)(((int64_t)B * kNCodes + 255) / 256), 256, 0, st>>>(B, b->S);
   int g = grid_for(b->Npad, 256);
   if (b->f64) k_import_pos<true><<<g, 256, 0, st>>>(b->Npad, b->S, b->A, s->pos, b->d_pots, !b->first_import, b->d_err);
@@ -500,16 +525,17 @@ void relist_lists(ts_batch* b, cudaStream_t st, bool move_fire, int prio) {
   relist_build(b, st, prio);
 }
 
-// end of a re-listing pass: flag bookkeeping
-void relist_finish(ts_batch* b, cudaStream_t st) {
-  k_after_relist<<<(b->B + 127) / 128, 128, 0, st>>>(b->B, b->S, b->d_counters);
+// end of a re-listing pass: flag bookkeeping.  md_pass: the pass's pair
+// launches ran in inner-list mode and refreshed every flagged system.
+void relist_finish(ts_batch* b, cudaStream_t st, bool md_pass) {
+  k_after_relist<<<(b->B + 127) / 128, 128, 0, st>>>(b->B, b->S, b->d_counters, md_pass ? 1 : 0);
   k_clear_any<<<1, 1, 0, st>>>(b->S);
   b->launches += 2;
 }
 
 void relist(ts_batch* b, cudaStream_t st, bool move_fire) {
   relist_lists(b, st, move_fire);
-  relist_finish(b, st);
+  relist_finish(b, st, false);
 }
 
 // Re-listing pass and pair forces with the list build off the critical
@@ -527,11 +553,11 @@ bool relist_pair_overlapped(ts_batch* b, cudaStream_t st, bool move_fire, bool e
       !cuda_ok(b, cudaStreamWaitEvent(b->side, b->ev_fork, 0), "stream wait"))
     return false;
   relist_build(b, b->side, b->prio_hi);
-  pair(b, b->side, ew, kPairRelisted, b->prio_hi);
+  pair(b, b->side, ew, kPairRelisted, b->prio_hi, true);
   cuda_ok(b, cudaEventRecord(b->ev_join, b->side), "event record");
-  pair(b, st, ew, kPairKept);
+  pair(b, st, ew, kPairKept, 0, true);
   cuda_ok(b, cudaStreamWaitEvent(st, b->ev_join, 0), "stream wait");
-  relist_finish(b, st);
+  relist_finish(b, st, true);
   return true;
 }
 
@@ -558,14 +584,15 @@ void relist_large_sort(ts_batch* b, cudaStream_t st, bool move_fire) {
   b->launches += 9;
 }
 
-void pair(ts_batch* b, cudaStream_t st, bool ew, int filter, int prio) {
+void pair(ts_batch* b, cudaStream_t st, bool ew, int filter, int prio, bool inner) {
+  const int in = inner ? 1 : 0;
   int threads = b->pair_threads;
   int blocks = (int)(((int64_t)b->nwarps * 32 + threads - 1) / threads);
   const DevPot* pots = b->d_pots;
   const int32_t* ws = b->d_warp_sys;
   if (b->f64) {
-    if (ew) launch_k(st, prio, blocks, threads, 0, k_pair<true, true>, b->nwarps, ws, b->S, b->A, pots, b->Ncap, filter, b->d_partial, 0);
-    else launch_k(st, prio, blocks, threads, 0, k_pair<true, false>, b->nwarps, ws, b->S, b->A, pots, b->Ncap, filter, b->d_partial, 0);
+    if (ew) launch_k(st, prio, blocks, threads, 0, k_pair<true, true>, b->nwarps, ws, b->S, b->A, pots, b->Ncap, filter, b->d_partial, 0, in);
+    else launch_k(st, prio, blocks, threads, 0, k_pair<true, false>, b->nwarps, ws, b->S, b->A, pots, b->Ncap, filter, b->d_partial, 0, in);
     b->launches++;
     return;
   }
@@ -574,14 +601,14 @@ void pair(ts_batch* b, cudaStream_t st, bool ew, int filter, int prio) {
   if (small) {
     size_t shm = (size_t)kSmallRecord * b->nst_max;
     const int4* it = b->d_items;
-    if (ew) launch_k(st, prio, b->n_items, kPairSmallThreads, shm, k_pair_small<true>, b->n_items, it, ws, b->S, b->A, pots, b->Ncap, filter, b->d_partial);
-    else launch_k(st, prio, b->n_items, kPairSmallThreads, shm, k_pair_small<false>, b->n_items, it, ws, b->S, b->A, pots, b->Ncap, filter, b->d_partial);
+    if (ew) launch_k(st, prio, b->n_items, kPairSmallThreads, shm, k_pair_small<true>, b->n_items, it, ws, b->S, b->A, pots, b->Ncap, filter, b->d_partial, in);
+    else launch_k(st, prio, b->n_items, kPairSmallThreads, shm, k_pair_small<false>, b->n_items, it, ws, b->S, b->A, pots, b->Ncap, filter, b->d_partial, in);
     b->launches++;
   }
   if (!small || b->n_large > 0) {
     int sk = small ? 1 : 0;
-    if (ew) launch_k(st, prio, blocks, threads, 0, k_pair<false, true>, b->nwarps, ws, b->S, b->A, pots, b->Ncap, filter, b->d_partial, sk);
-    else launch_k(st, prio, blocks, threads, 0, k_pair<false, false>, b->nwarps, ws, b->S, b->A, pots, b->Ncap, filter, b->d_partial, sk);
+    if (ew) launch_k(st, prio, blocks, threads, 0, k_pair<false, true>, b->nwarps, ws, b->S, b->A, pots, b->Ncap, filter, b->d_partial, sk, in);
+    else launch_k(st, prio, blocks, threads, 0, k_pair<false, false>, b->nwarps, ws, b->S, b->A, pots, b->Ncap, filter, b->d_partial, sk, in);
     b->launches++;
   }
 }
@@ -701,13 +728,17 @@ extern "C" ts_status ts_profile_pair(ts_batch* b, ts_state* s, int reps, void* f
   r = prologue(b, s, st, false);
   if (r != TS_OK) return r;
   ensure_forces(b, st);
+  // inner lists at the current positions for every system (one refreshing launch)
+  if (!cuda_ok(b, cudaMemsetAsync(b->S.prune, 1, 4 * (size_t)b->B, st), "memset")) return TS_ERR_CUDA;
+  pair(b, st, false, kPairAll, 0, true);
+  if (!cuda_ok(b, cudaMemsetAsync(b->S.prune, 0, 4 * (size_t)b->B, st), "memset")) return TS_ERR_CUDA;
   cudaEvent_t e0, e1;
   if (!cuda_ok(b, cudaEventCreate(&e0), "event") || !cuda_ok(b, cudaEventCreate(&e1), "event")) return TS_ERR_CUDA;
   double total = 0;
   for (int k = 0; k < reps; k++) {
     if (flush_buf && flush_bytes) cudaMemsetAsync(flush_buf, k & 0xff, flush_bytes, st);
     cudaEventRecord(e0, st);
-    pair(b, st, false, false);
+    pair(b, st, false, kPairAll, 0, true);
     cudaEventRecord(e1, st);
     if (!cuda_ok(b, cudaEventSynchronize(e1), "event sync")) return TS_ERR_CUDA;
     float ms = 0;

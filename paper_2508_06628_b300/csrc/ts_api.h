@@ -89,7 +89,7 @@ ts_status fail(ts_batch* b, ts_status st, const std::string& msg);
 size_t scratch_bytes(int64_t Ncap, int64_t Bcap, int64_t Ccap, int32_t max_nbrs, bool f64);
 ts_status derive_topology(ts_batch* b, const ts_state* s, cudaStream_t st);
 ts_status check_state(ts_batch* b, const ts_state* s, bool need_vel);
-ts_status prologue(ts_batch* b, ts_state* s, cudaStream_t st, bool import_vel);
+ts_status prologue(ts_batch* b, ts_state* s, cudaStream_t st, bool import_vel, bool fire = false);
 // Kernel launch with a scheduling priority (0: the stream's own).  Stream
 // capture keeps the launch attribute as the kernel node's priority.
 template <typename... KArgs, typename... Args>
@@ -111,10 +111,10 @@ void relist(ts_batch* b, cudaStream_t st, bool move_fire);
 void relist_lists(ts_batch* b, cudaStream_t st, bool move_fire, int prio = 0);
 void relist_sort(ts_batch* b, cudaStream_t st, bool move_fire, int prio);
 void relist_build(ts_batch* b, cudaStream_t st, int prio);
-void relist_finish(ts_batch* b, cudaStream_t st);
+void relist_finish(ts_batch* b, cudaStream_t st, bool md_pass);
 bool relist_pair_overlapped(ts_batch* b, cudaStream_t st, bool move_fire, bool ew);
 void relist_large_sort(ts_batch* b, cudaStream_t st, bool move_fire);
-void pair(ts_batch* b, cudaStream_t st, bool ew, int filter, int prio = 0);
+void pair(ts_batch* b, cudaStream_t st, bool ew, int filter, int prio = 0, bool inner = false);
 void reduce_sys(ts_batch* b, cudaStream_t st, double* E, double* stress, double* KE);
 void clear_dirty(ts_batch* b, cudaStream_t st);
 void export_state(ts_batch* b, cudaStream_t st, double* pos, double* vel);

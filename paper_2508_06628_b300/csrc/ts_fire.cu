@@ -289,7 +289,7 @@ extern "C" ts_status ts_fire_step(ts_batch* b, ts_state* s, ts_fire_state* fs, d
   if (!p || !fs || !fvel || n_steps < 0 || !(p->dt0 > 0) || !(p->maxstep > 0))
     return fail(b, TS_ERR_INVALID_ARG, "bad FIRE arguments");
   cudaStream_t st = (cudaStream_t)stream;
-  r = prologue(b, s, st, false);
+  r = prologue(b, s, st, false, true);
   if (r != TS_OK) return r;
   if (p->variable_cell) {
     k_require_periodic<<<(b->B + 127) / 128, 128, 0, st>>>(b->B, b->S, b->d_err);
@@ -315,7 +315,7 @@ extern "C" ts_status ts_fire_step(ts_batch* b, ts_state* s, ts_fire_state* fs, d
     if (k == n_steps) break;
     if (b->f64) k_fire_update<true><<<g, 256, 0, st>>>(b->Npad, b->S, b->A, b->d_scal, b->d_pots);
     else k_fire_update<false><<<g, 256, 0, st>>>(b->Npad, b->S, b->A, b->d_scal, b->d_pots);
-    k_geometry<<<(b->B + 127) / 128, 128, 0, st>>>(b->B, b->S, s->cell, s->pbc, b->d_pots, b->d_err);
+    k_geometry<<<(b->B + 127) / 128, 128, 0, st>>>(b->B, b->S, s->cell, s->pbc, b->d_pots, b->d_err, 0);
     k_shift_table<<<(int)(((int64_t)b->B * kNCodes + 255) / 256), 256, 0, st>>>(b->B, b->S);
     b->launches += 3;
     relist(b, st, true);

@@ -26,6 +26,8 @@ constexpr float kGrid = 4096.0f;          // 2^12
 // Half-width of the shell around the list radius where the hi-only distance
 // (off by at most 3 * 2^-13 * sqrt(3) = 6.3e-4 A) cannot decide a list test.
 constexpr double kListBand = 1e-3;
+// Default inner skin of the pruned pair list, as a fraction of the skin.
+constexpr double kInnerSkinFraction = 0.3;
 constexpr float kInvGrid = 1.0f / 4096.0f;
 constexpr double kMaxCoord = 2000.0;      // |x| bound of the hi/lo representation
 constexpr int kJBits = 22;                // neighbour entry: j (22 bits) | image code (10 bits)
@@ -61,6 +63,11 @@ struct DevPot {
   float sinvf;    // 1/sigma in FP32 (soft sphere)
   float half_skin2f, soon_half_skin2f;   // (skin/2)^2 and soon^2 (skin/2)^2, FP32 (mixed skin check)
   float rlist_in2f, rlist_out2f;         // (rlist -+ 1e-3 A)^2: certain hit / miss of the hi-only list test
+  // dynamic pruning: the inner list keeps the entries within rc + inner skin
+  // (squared, with a 1e-3 A margin: the test may keep a few more); a system's
+  // list is refreshed once an atom moved more than half the inner skin
+  float rin2f; double rin2d;
+  float half_in2f; double half_in2d;
   double pd[3];
   double rc2d, phicd, rlist, rlist2d, skin;
   double soon2;   // squared hysteresis factor
@@ -88,6 +95,8 @@ struct SysArrays {
   double* shiftd;         // [kNCodes][3] fp64
   uint4* shiftq;          // [kNCodes] (x, y, z) in units of 2^-26 A, modulo 2^32 (shared-memory pair kernel)
   int32_t* relist;        // per-system re-list flag
+  int32_t* prune;         // per-system flag: the next MD pair launch refreshes the inner list (an atom
+                          // moved half the inner skin since the last refresh, or the list is stale)
   int32_t* soon;          // atoms past kSoon * skin/2: re-list along with any forced pass
   int32_t* any;           // [1] some system must re-list in this pass
   int32_t* dirty;         // forces stale for this system
@@ -124,6 +133,12 @@ struct SlotArrays {
   int32_t* bin;               // slot -> global bin (valid after a listing)
   int32_t* nn;                // neighbour count
   uint32_t* nbr;              // [max_nbrs][Ncap] (transposed ELL)
+  // inner list (dynamic pruning): the entries of nbr within rc + inner skin at
+  // the last refresh, in the same order; positions at that refresh
+  int32_t* nn_in;
+  uint32_t* nbr_in;           // [max_nbrs][Ncap]
+  float4* xph; float4* xpl;   // mixed
+  double* xpd;                // fp64 [3]
   // reorder scratch
   int32_t* tmp_i0; int32_t* tmp_i1; int32_t* tmp_i2;
   float4* tmp_f0; float4* tmp_f1; float4* tmp_f2; float4* tmp_f3;

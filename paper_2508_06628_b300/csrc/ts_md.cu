@@ -136,11 +136,21 @@ __global__ void k_md_kick_drift(int64_t Npad, SysArrays S, SlotArrays A, const D
       const DevPot& P = pots[S.pot[s]];
       if (d2 > P.half_skin2f) { S.relist[s] = 1; S.any[0] = 1; }
       else if (d2 > P.soon_half_skin2f) S.soon[s] = 1;
+      // inner list: refreshed in this step's pair launch once an atom moved half the inner skin
+      float4 ph = A.xph[k], pl = A.xpl[k];
+      float px = (xh.x - ph.x) + (xl.x - pl.x), py = (xh.y - ph.y) + (xl.y - pl.y), pz = (xh.z - ph.z) + (xl.z - pl.z);
+      if (fmaf(px, px, fmaf(py, py, pz * pz)) > P.half_in2f) S.prune[s] = 1;
       continue;
     }
     double sk = 0.5 * pots[S.pot[s]].skin, d2 = dx * dx + dy * dy + dz * dz;
     if (d2 > sk * sk) { S.relist[s] = 1; S.any[0] = 1; }
     else if (d2 > pots[S.pot[s]].soon2 * sk * sk) S.soon[s] = 1;
+    if constexpr (F64) {
+      const double* x = A.xd + 3 * k;
+      const double* xp = A.xpd + 3 * k;
+      const double p0 = x[0] - xp[0], p1 = x[1] - xp[1], p2 = x[2] - xp[2];
+      if (p0 * p0 + p1 * p1 + p2 * p2 > pots[S.pot[s]].half_in2d) S.prune[s] = 1;
+    }
   }
 }
 

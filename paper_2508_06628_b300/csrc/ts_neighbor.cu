@@ -39,13 +39,16 @@ __global__ void k_init_slots(int32_t B, SysArrays S, SlotArrays A) {
     A.perm[st + k] = k < n ? (int32_t)(S.caller_off[s] + k) : -1;
     A.sys[st + k] = k < n ? s : -1;
     A.nn[st + k] = 0;
+    A.nn_in[st + k] = 0;
   }
 }
 
 // --- import / export ---------------------------------------------------------
 // Positions from the caller; marks systems whose positions changed (forces
-// stale) and systems whose atoms left the skin (re-list).  check_skin = 0 on
-// the first import after a topology change (everything is re-listed anyway).
+// stale), systems whose atoms left the skin (re-list) and systems whose atoms
+// moved half the inner skin since their last prune (whoever moved them: the
+// caller, or FIRE, which keeps no inner list).  check_skin = 0 on the first
+// import after a topology change (everything is re-listed anyway).
 template <bool F64>
 __global__ void k_import_pos(int64_t Npad, SysArrays S, SlotArrays A, const double* __restrict__ pos,
                              const DevPot* __restrict__ pots, int check_skin, int32_t* err) {
@@ -84,6 +87,17 @@ __global__ void k_import_pos(int64_t Npad, SysArrays S, SlotArrays A, const doub
       double sk = 0.5 * pots[S.pot[s]].skin, d2 = dx * dx + dy * dy + dz * dz;
       if (d2 > sk * sk) { S.relist[s] = 1; S.any[0] = 1; }
       else if (d2 > pots[S.pot[s]].soon2 * sk * sk) S.soon[s] = 1;
+      double p0, p1, p2;
+      if constexpr (F64) {
+        const double* xp = A.xpd + 3 * k;
+        p0 = x0 - xp[0]; p1 = x1 - xp[1]; p2 = x2 - xp[2];
+      } else {
+        const float4 h = A.xh[k], l = A.xl[k], ph = A.xph[k], pl = A.xpl[k];
+        p0 = (double)((h.x - ph.x) + (l.x - pl.x));
+        p1 = (double)((h.y - ph.y) + (l.y - pl.y));
+        p2 = (double)((h.z - ph.z) + (l.z - pl.z));
+      }
+      if (p0 * p0 + p1 * p1 + p2 * p2 > pots[S.pot[s]].half_in2d) S.prune[s] = 1;
     }
   }
 }
@@ -161,11 +175,17 @@ __device__ inline double det3(const double* h) {
 // the edge bins (bins are at least r_list wide, so every pair within r_list
 // still lies in neighbouring bins), and the stencil stops at the edges.
 __global__ void k_geometry(int32_t B, SysArrays S, const double* __restrict__ cell, const uint8_t* __restrict__ pbc,
-                           const DevPot* __restrict__ pots, int32_t* err) {
+                           const DevPot* __restrict__ pots, int32_t* err, int cell_check) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= B) return;
   double h[9];
   for (int q = 0; q < 9; q++) h[q] = cell[9 * (int64_t)s + q];
+  if (cell_check) {   // lists built for another cell: re-list (see the prologue for the two checks)
+    const double* ref = cell_check == 1 ? S.h + 9 * s : S.href + 9 * s;
+    bool moved = false;
+    for (int q = 0; q < 9; q++) moved |= h[q] != ref[q];
+    if (moved) { S.relist[s] = 1; S.any[0] = 1; }
+  }
   for (int q = 0; q < 9; q++) S.h[9 * s + q] = h[q];
   const int pm = pbc ? ((pbc[3 * s] ? 1 : 0) | (pbc[3 * s + 1] ? 2 : 0) | (pbc[3 * s + 2] ? 4 : 0)) : 7;
   S.pmask[s] = pm;
@@ -443,100 +463,25 @@ __global__ void k_copy_back(int64_t Npad, SysArrays S, SlotArrays A, int move_fi
   }
 }
 
-// explicit Verlet list at r_list: each atom scans its stencil bins
-template <bool F64>
-__global__ void k_build_list(int64_t Npad, SysArrays S, SlotArrays A, const int32_t* __restrict__ cstart,
-                             const int32_t* __restrict__ count, const DevPot* __restrict__ pots, int32_t max_nbrs,
-                             int64_t stride, int32_t* err) {
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < Npad; k += (int64_t)gridDim.x * blockDim.x) {
-    int s = A.sys[k];
-    if (s < 0 || !need_relist(S, s) || S.n_atoms[s] <= kSmallMax) continue;
-    if (A.perm[k] < 0) continue;
-    const DevPot& P = pots[S.pot[s]];
-    int nb0 = S.nb[3 * s], nb1 = S.nb[3 * s + 1], nb2 = S.nb[3 * s + 2];
-    int m0 = S.reach[3 * s], m1 = S.reach[3 * s + 1], m2 = S.reach[3 * s + 2];
-    int lb = A.bin[k] - S.bin_off[s];
-    int kx = lb % nb0, ky = (lb / nb0) % nb1, kz = lb / (nb0 * nb1);
-    int64_t seg = S.seg_start[s];
-    int cnt = 0;
-    if constexpr (F64) {
-      double xi0 = A.xd[3 * k], xi1 = A.xd[3 * k + 1], xi2 = A.xd[3 * k + 2];
-      for (int dz = -m2; dz <= m2; dz++) {
-        int zz = kz + dz, iz = (zz >= 0) ? zz / nb2 : -((-zz + nb2 - 1) / nb2), cz = zz - iz * nb2;
-        for (int dy = -m1; dy <= m1; dy++) {
-          int yy = ky + dy, iy = (yy >= 0) ? yy / nb1 : -((-yy + nb1 - 1) / nb1), cy = yy - iy * nb1;
-          for (int dx = -m0; dx <= m0; dx++) {
-            int xx = kx + dx, ix = (xx >= 0) ? xx / nb0 : -((-xx + nb0 - 1) / nb0), cx = xx - ix * nb0;
-            int code = img_code(ix, iy, iz);
-            const double* sh = S.shiftd + 3 * ((int64_t)s * kNCodes + code);
-            double s0 = sh[0] - xi0, s1 = sh[1] - xi1, s2 = sh[2] - xi2;
-            int gb = S.bin_off[s] + (cz * nb1 + cy) * nb0 + cx;
-            int64_t b0 = bin_slot(S, cstart, s, gb);
-            int c = count[gb];
-            for (int q = 0; q < c; q++) {
-              int64_t j = b0 + q;
-              if (j == k && code == kCenter) continue;
-              double d0 = A.xd[3 * j] + s0, d1 = A.xd[3 * j + 1] + s1, d2 = A.xd[3 * j + 2] + s2;
-              double r2 = d0 * d0 + d1 * d1 + d2 * d2;
-              if (r2 < P.rlist2d) {
-                if (cnt < max_nbrs) A.nbr[cnt * stride + k] = (uint32_t)(j - seg) | ((uint32_t)code << kJBits);
-                cnt++;
-              }
-            }
-          }
-        }
-      }
-      for (int c = 0; c < 3; c++) A.xrd[3 * k + c] = A.xd[3 * k + c];
-    } else {
-      float4 hi = A.xh[k], lo = A.xl[k];
-      for (int dz = -m2; dz <= m2; dz++) {
-        int zz = kz + dz, iz = (zz >= 0) ? zz / nb2 : -((-zz + nb2 - 1) / nb2), cz = zz - iz * nb2;
-        for (int dy = -m1; dy <= m1; dy++) {
-          int yy = ky + dy, iy = (yy >= 0) ? yy / nb1 : -((-yy + nb1 - 1) / nb1), cy = yy - iy * nb1;
-          for (int dx = -m0; dx <= m0; dx++) {
-            int xx = kx + dx, ix = (xx >= 0) ? xx / nb0 : -((-xx + nb0 - 1) / nb0), cx = xx - ix * nb0;
-            int code = img_code(ix, iy, iz);
-            int64_t ti = (int64_t)s * kNCodes + code;
-            float4 sh = S.shift[2 * ti], sl = S.shift[2 * ti + 1];
-            // exact: all on the 2^-12 grid
-            float a0 = sh.x - hi.x, a1 = sh.y - hi.y, a2 = sh.z - hi.z;
-            float b0 = sl.x - lo.x, b1 = sl.y - lo.y, b2 = sl.z - lo.z;
-            int gb = S.bin_off[s] + (cz * nb1 + cy) * nb0 + cx;
-            int64_t jb = bin_slot(S, cstart, s, gb);
-            int c = count[gb];
-            for (int q = 0; q < c; q++) {
-              int64_t j = jb + q;
-              if (j == k && code == kCenter) continue;
-              float4 xj = A.xh[j], lj = A.xl[j];
-              float d0 = (xj.x + a0) + (lj.x + b0);
-              float d1 = (xj.y + a1) + (lj.y + b1);
-              float d2 = (xj.z + a2) + (lj.z + b2);
-              float r2 = d0 * d0 + d1 * d1 + d2 * d2;
-              if (r2 < P.rlist2f) {
-                if (cnt < max_nbrs) A.nbr[cnt * stride + k] = (uint32_t)(j - seg) | ((uint32_t)code << kJBits);
-                cnt++;
-              }
-            }
-          }
-        }
-      }
-      A.xrh[k] = hi; A.xrl[k] = lo;
-    }
-    if (cnt > max_nbrs) { atomicOr(err, kErrNeighborOverflow); cnt = max_nbrs; }
-    A.nn[k] = cnt;
-  }
-}
-
 // per-system flag bookkeeping after a listing: the re-listed systems' forces are stale
-__global__ void k_after_relist(int32_t B, SysArrays S, int64_t* relist_counter) {
+__global__ void k_after_relist(int32_t B, SysArrays S, int64_t* counters, int md_pass) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= B) return;
+  // inner lists: an MD pass's pair launches refreshed every flagged or
+  // re-listed system (counted in counters[1]); after any other pass a
+  // re-listed system's inner list is stale until the next MD pass
+  if (md_pass) {
+    if (S.prune[s] || need_relist(S, s)) atomicAdd((unsigned long long*)(counters + 1), 1ull);
+    S.prune[s] = 0;
+  } else if (need_relist(S, s)) {
+    S.prune[s] = 1;
+  }
   if (need_relist(S, s)) {
     S.dirty[s] = 1;
     S.relist[s] = 0;
     S.soon[s] = 0;
     for (int q = 0; q < 9; q++) S.href[9 * s + q] = S.h[9 * s + q];
-    atomicAdd((unsigned long long*)relist_counter, 1ull);
+    atomicAdd((unsigned long long*)counters, 1ull);
   }
 }
 

@@ -18,29 +18,36 @@ namespace ts {
 template <bool F64, bool EW>
 __global__ void __launch_bounds__(256) k_pair(int32_t n_warps, const int32_t* __restrict__ warp_sys, SysArrays S,
                                               SlotArrays A, const DevPot* __restrict__ pots, int64_t stride,
-                                              int filter, double* __restrict__ partial, int skip_small) {
+                                              int filter, double* __restrict__ partial, int skip_small, int inner) {
   int w = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
   int lane = threadIdx.x & 31;
   if (w >= n_warps) return;
   int s = warp_sys[w];
   if (pair_skip(S, s, filter)) return;
   if (skip_small && S.n_atoms[s] <= kSmallMax) return;   // handled by k_pair_small
+  // inner-list mode (MD steps): a system flagged for pruning, or re-listed in
+  // this pass, runs its full list and writes the inner list on the way
+  const bool refresh = inner && (S.prune[s] || need_relist(S, s));   // warp-uniform
+  const uint32_t* NB = inner && !refresh ? A.nbr_in : A.nbr;
   int64_t k = (int64_t)w * kWarp + lane;
   const DevPot P = pots[S.pot[s]];
   bool valid = A.perm[k] >= 0;
-  int nn = valid ? A.nn[k] : 0;
+  int nn = valid ? (inner && !refresh ? A.nn_in : A.nn)[k] : 0;
+  int cin = 0;
+  uint32_t* out_in = A.nbr_in + k;
   int64_t seg = S.seg_start[s];
   if constexpr (F64) {
     const double* tab = S.shiftd + 3 * (int64_t)s * kNCodes;
     double xi0 = A.xd[3 * k], xi1 = A.xd[3 * k + 1], xi2 = A.xd[3 * k + 2];
     double f0 = 0, f1 = 0, f2 = 0, e = 0, w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0, w5 = 0;
     for (int q = 0; q < nn; q++) {
-      uint32_t ent = __ldg(A.nbr + q * stride + k);
+      uint32_t ent = __ldg(NB + q * stride + k);
       int64_t j = seg + (ent & kJMask);
       int code = (int)(ent >> kJBits);
       double d0 = A.xd[3 * j] - xi0, d1 = A.xd[3 * j + 1] - xi1, d2 = A.xd[3 * j + 2] - xi2;
       if (code != kCenter) { d0 += tab[3 * code]; d1 += tab[3 * code + 1]; d2 += tab[3 * code + 2]; }
       double r2 = d0 * d0 + d1 * d1 + d2 * d2;
+      if (refresh && r2 < P.rin2d) out_in[(int64_t)(cin++) * stride] = ent;
       if (r2 < P.rc2d) {
         double phi, fr;
         PotMath<double>::eval(P, r2, phi, fr);
@@ -54,6 +61,10 @@ __global__ void __launch_bounds__(256) k_pair(int32_t n_warps, const int32_t* __
       }
     }
     if (valid) { A.Fd[3 * k] = f0; A.Fd[3 * k + 1] = f1; A.Fd[3 * k + 2] = f2; }
+    if (refresh && valid) {
+      A.nn_in[k] = cin;
+      A.xpd[3 * k] = xi0; A.xpd[3 * k + 1] = xi1; A.xpd[3 * k + 2] = xi2;
+    }
     if (EW) {
       double v[7] = {e, w0, w1, w2, w3, w4, w5};
 #pragma unroll
@@ -78,6 +89,7 @@ __global__ void __launch_bounds__(256) k_pair(int32_t n_warps, const int32_t* __
       }
       float d0 = a0 + b0, d1 = a1 + b1, d2 = a2 + b2;
       float r2 = fmaf(d0, d0, fmaf(d1, d1, d2 * d2));
+      if (refresh && r2 < P.rin2f) out_in[(int64_t)(cin++) * stride] = ent;
       if (r2 < P.rc2f) {
         float phi, fr;
         PotMath<float>::eval(P, r2, phi, fr);
@@ -98,7 +110,7 @@ __global__ void __launch_bounds__(256) k_pair(int32_t n_warps, const int32_t* __
     // loop, so results do not depend on the unrolling.
     const float4* ph = A.xh + seg;
     const float4* pl = A.xl + seg;
-    const uint32_t* lp = A.nbr + k;
+    const uint32_t* lp = NB + k;
     int q = 0;
     uint32_t n0 = 0, n1 = 0, n2 = 0, n3 = 0;
     if (nn >= 4) {
@@ -117,11 +129,12 @@ __global__ void __launch_bounds__(256) k_pair(int32_t n_warps, const int32_t* __
       one(e0, x0, l0); one(e1, x1, l1); one(e2, x2, l2); one(e3, x3, l3);
     }
     for (; q < nn; q++) {
-      uint32_t ent = __ldg(A.nbr + q * stride + k);
+      uint32_t ent = __ldg(NB + q * stride + k);
       int64_t j = seg + (ent & kJMask);
       one(ent, __ldg(A.xh + j), __ldg(A.xl + j));
     }
     if (valid) A.F[k] = make_float4(f0, f1, f2, e);
+    if (refresh && valid) { A.nn_in[k] = cin; A.xph[k] = xi; A.xpl[k] = li; }
     if (EW) {
       double v[7] = {(double)e, (double)w0, (double)w1, (double)w2, (double)w3, (double)w4, (double)w5};
 #pragma unroll
@@ -155,7 +168,8 @@ constexpr int kSmallRecord = 16;   // staged bytes per atom
 template <bool EW>
 __global__ void __launch_bounds__(kPairSmallThreads) k_pair_small(
     int32_t n_items, const int4* __restrict__ items, const int32_t* __restrict__ warp_sys, SysArrays S,
-    SlotArrays A, const DevPot* __restrict__ pots, int64_t stride, int filter, double* __restrict__ partial) {
+    SlotArrays A, const DevPot* __restrict__ pots, int64_t stride, int filter, double* __restrict__ partial,
+    int inner) {
   extern __shared__ __align__(16) uint4 sq[];   // [staged] fixed-point (x, y, z, -)
   if ((int)blockIdx.x >= n_items) return;
   const int4 W = items[blockIdx.x];
@@ -182,16 +196,22 @@ __global__ void __launch_bounds__(kPairSmallThreads) k_pair_small(
   const uint4* hq = sq + (seg - st0);
   const DevPot P = pots[S.pot[s]];
   const uint4* tab = S.shiftq + (int64_t)s * kNCodes;
-  const int nn = valid ? A.nn[k] : 0;
+  // inner-list mode (MD steps): a system flagged for pruning, or re-listed in
+  // this pass, runs its full list and writes the inner list on the way
+  const bool refresh = inner && (S.prune[s] || need_relist(S, s));   // warp-uniform
+  const bool use_in = inner && !refresh;
+  const int nn = valid ? (use_in ? A.nn_in : A.nn)[k] : 0;
   const uint4 xi = valid ? hq[i] : make_uint4(0, 0, 0, 0);
+  int cin = 0;
   float f0 = 0.f, f1 = 0.f, f2 = 0.f, e = 0.f, w0 = 0.f, w1 = 0.f, w2 = 0.f, w3 = 0.f, w4 = 0.f, w5 = 0.f;
   // The potential kind is uniform over a warp (one system): one loop per kind,
   // with no branch inside an entry.  Every entry evaluates the potential and
   // selects a zero force factor beyond rc (fmaf(0, d, f) == f, so the sums are
   // those of the branching form), which lets the four entries of a round
   // overlap.
-  auto run = [&](auto kind) {
+  auto run = [&](auto kind, auto refresh_c) {
     constexpr int K = decltype(kind)::value;
+    constexpr bool R = decltype(refresh_c)::value;
     auto one = [&](uint32_t ent) {
       const int code = (int)(ent >> kJBits);
       const int j = (int)(ent & kJMask);
@@ -204,6 +224,10 @@ __global__ void __launch_bounds__(kPairSmallThreads) k_pair_small(
       const float d2 = (float)(int)(xj.z - xi.z + sh.z) * kFixInv;
       const float r2 = fmaf(d0, d0, fmaf(d1, d1, d2 * d2));
       const bool in = r2 < P.rc2f;
+      if (R) {   // inner list: within rc + inner skin (+ 1e-3 A), in list order
+        if (r2 < P.rin2f) A.nbr_in[(int64_t)cin * stride + k] = ent;
+        cin += r2 < P.rin2f;
+      }
       float phi, fr;
       PotMath<float>::eval_k<K>(P, r2, phi, fr);
       fr = in ? fr : 0.f;
@@ -216,7 +240,7 @@ __global__ void __launch_bounds__(kPairSmallThreads) k_pair_small(
         w3 = fmaf(h0, d1, w3); w4 = fmaf(h0, d2, w4); w5 = fmaf(h1, d2, w5);
       }
     };
-    const uint32_t* lp = A.nbr + k;
+    const uint32_t* lp = (use_in ? A.nbr_in : A.nbr) + k;
     int q = 0;
     uint32_t n0 = 0, n1 = 0, n2 = 0, n3 = 0;
     if (nn >= 4) { n0 = __ldcs(lp); n1 = __ldcs(lp + stride); n2 = __ldcs(lp + 2 * stride); n3 = __ldcs(lp + 3 * stride); }
@@ -230,9 +254,18 @@ __global__ void __launch_bounds__(kPairSmallThreads) k_pair_small(
     }
     for (; q < nn; q++) one(__ldcs(lp + (int64_t)q * stride));
   };
-  if (P.kind == TS_LJ) run(std::integral_constant<int, TS_LJ>{});
-  else if (P.kind == TS_MORSE) run(std::integral_constant<int, TS_MORSE>{});
-  else run(std::integral_constant<int, TS_SOFT_SPHERE>{});
+  using Off = std::false_type;
+  using On = std::true_type;
+  if (!refresh) {
+    if (P.kind == TS_LJ) run(std::integral_constant<int, TS_LJ>{}, Off{});
+    else if (P.kind == TS_MORSE) run(std::integral_constant<int, TS_MORSE>{}, Off{});
+    else run(std::integral_constant<int, TS_SOFT_SPHERE>{}, Off{});
+  } else {
+    if (P.kind == TS_LJ) run(std::integral_constant<int, TS_LJ>{}, On{});
+    else if (P.kind == TS_MORSE) run(std::integral_constant<int, TS_MORSE>{}, On{});
+    else run(std::integral_constant<int, TS_SOFT_SPHERE>{}, On{});
+    if (valid) { A.nn_in[k] = cin; A.xph[k] = __ldg(A.xh + k); A.xpl[k] = __ldg(A.xl + k); }
+  }
   if (valid) A.F[k] = make_float4(f0, f1, f2, e);
   if (EW) {   // one FP64 partial per warp (every computed warp lies inside its system's padded segment)
     double v[7] = {(double)e, (double)w0, (double)w1, (double)w2, (double)w3, (double)w4, (double)w5};

@@ -53,9 +53,12 @@ static void md_body(ts_batch* b, cudaStream_t st, const ts_md_params* p, int n_s
     }
     b->launches++;
     bool ew = need_e && k == n_steps - 1;
+    // forces from the inner lists; systems flagged for pruning or re-listed
+    // in this pass refresh theirs in the same launch
     if (!relist_pair_overlapped(b, st, false, ew)) {
-      relist(b, st, false);
-      pair(b, st, ew, kPairAll);
+      relist_lists(b, st, false);
+      pair(b, st, ew, kPairAll, 0, true);
+      relist_finish(b, st, true);
     }
     if (nhc) {   // closing half kick and the kinetic energy, then the chain (two half-steps between steps)
       final_ke(0.5 * p->dt, nullptr);

@@ -94,6 +94,7 @@ def lib():
         L.ts_batch_poll.argtypes = [P, P, I]
         L.ts_autotune.argtypes = [P, C.POINTER(State), P]
         L.ts_batch_counters.argtypes = [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+        L.ts_batch_prunes.argtypes = [P, C.POINTER(C.c_int64)]
         L.ts_batch_memory_model.argtypes = [P, C.POINTER(C.c_double), C.POINTER(C.c_double)]
         L.ts_profile_pair.argtypes = [P, C.POINTER(State), I, P, C.c_size_t, C.POINTER(C.c_double),
                                       C.POINTER(C.c_int64), C.POINTER(C.c_int64), P]
@@ -280,6 +281,12 @@ class Batch:
         a, b = C.c_int64(), C.c_int64()
         lib().ts_batch_counters(self.h, C.byref(a), C.byref(b))
         return a.value, b.value
+
+    def prunes(self):
+        """Inner-list prunes so far (one per system and prune)."""
+        n = C.c_int64()
+        self._check(lib().ts_batch_prunes(self.h, C.byref(n)), "ts_batch_prunes")
+        return n.value
 
 
 def bin_pack(sizes, capacity):

@@ -1,0 +1,91 @@
+"""Dynamic pruning of the Verlet list in MD steps.
+
+Forces in MD steps come from an inner list: the Verlet-list entries within
+rc plus a fraction of the skin, re-filtered for a system once one of its
+atoms moved half that fraction.  Every pair inside rc between two filterings
+is in the inner list and pairs beyond rc contribute exactly zero, so the
+trajectory is bit-identical to one computed from the full Verlet list
+(TS_INNER=1: the inner list is the Verlet list).  Checked with Langevin
+steps in both precisions, with positions moved by the caller and by FIRE
+between MD calls (both must trigger a re-filtering), and with a cell changed
+by the caller (which must trigger a re-listing)."""
+import numpy as np
+import pytest
+
+from tests.gpu_util import make_batch, small_mix, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+def run(hb, precision, steps=150, jolt=False, fire=False):
+    torch = torch_cuda()
+    from paper_2508_06628_b300 import ts
+    b = make_batch(hb, precision)
+    s = ts.DeviceState.from_host(hb)
+    stream = torch.cuda.Stream()
+    rng = np.random.default_rng(5)
+    with torch.cuda.stream(stream):
+        b.neighbor_build(s, force=True, stream=stream)
+        for c in range(steps // 10):
+            if jolt and c == 5:      # the caller moves every atom by 0.1 A: more than half the inner skin
+                d = rng.normal(size=(hb.n_atoms, 3))
+                d *= 0.1 / np.linalg.norm(d, axis=1, keepdims=True)
+                s.pos.add_(torch.as_tensor(d, device="cuda"))
+            if fire and c == 8:      # a few fixed-cell FIRE steps move the atoms outside MD
+                P = ts.FireParams(0.1, 1.0, 1.1, 0.5, 0.1, 0.99, 0.2, 1e-3, 1e-4, 0.0, 5, 0)
+                fs = torch.zeros(hb.n_systems * ts.FIRE_STATE_BYTES, dtype=torch.uint8, device="cuda")
+                fv = torch.zeros((hb.n_atoms + 3 * hb.n_systems, 3), dtype=torch.float64, device="cuda")
+                b.fire_init(s, P, fs, fv, stream=stream)
+                b.fire_step(s, fs, fv, P, 5, stream=stream)
+            b.md_step(s, 10, hb.meta["dt"], kind=1, gamma=hb.meta["gamma"], seed=4, step0=10 * c, stream=stream)
+        b.poll(stream)
+    stream.synchronize()
+    out = s.pos.cpu().numpy(), s.vel.cpu().numpy(), b.counters()[1], b.prunes()
+    b.close()
+    return out
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_pruned_md_bit_identical(monkeypatch, precision):
+    hb = small_mix(111, n_systems=10, lo=32, hi=600)
+    xa, va, ra, pa = run(hb, precision)
+    monkeypatch.setenv("TS_INNER", "1")
+    xb, vb, rb, _ = run(hb, precision)
+    assert pa > 0                        # filterings happened
+    assert ra == rb
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_pruned_md_after_caller_and_fire_moves(monkeypatch, precision):
+    hb = small_mix(112, n_systems=8, lo=32, hi=400)
+    xa, va, _, _ = run(hb, precision, jolt=True, fire=True)
+    monkeypatch.setenv("TS_INNER", "1")
+    xb, vb, _, _ = run(hb, precision, jolt=True, fire=True)
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb)
+
+
+def test_cell_change_by_caller_relists(orc):
+    """A caller that strains the cell (positions unchanged) gets forces for the
+    new cell: the lists built for the old cell are re-listed."""
+    torch = torch_cuda()
+    from paper_2508_06628_b300 import ts
+    hb = small_mix(113, n_systems=4, lo=64, hi=300)
+    b = make_batch(hb, 1)
+    s = ts.DeviceState.from_host(hb)
+    b.neighbor_build(s, force=True)
+    f = torch.zeros_like(s.pos)
+    b.pair_forces(s, f, None, None)
+    b.poll()
+    _, r0 = b.counters()
+    strain = np.eye(3) + np.diag([0.04, -0.03, 0.02])
+    cell = hb.cell @ strain
+    s.cell.copy_(torch.as_tensor(cell, device="cuda"))
+    b.pair_forces(s, f, None, None)
+    b.poll()
+    _, r1 = b.counters()
+    assert r1 - r0 == hb.n_systems
+    F = f.cpu().numpy()
+    _, Fr, _ = orc.forces(hb.offsets, s.pos.cpu().numpy(), cell, hb.pbc, hb.pot_idx, hb.pots)
+    assert np.abs(F - Fr).max() <= 1e-9 * np.abs(Fr).max()
+    b.close()
