@@ -30,10 +30,10 @@ UNIT = "atom-steps/s"
 FP32_LANES_PER_SM, N_SM = 128, 148
 FLOP_PER_PAIR = 30          # per ordered pair within the cutoff (force, energy, virial terms)
 BYTES_PER_ATOM = 32         # read own position, write own force, per atom-step
-# DRAM bytes (read + write) of one forces-only k_pair_small launch on ragged-mix-512, from one ncu
+# DRAM bytes (read + write) of one forces-only k_pair_small launch (inner lists) on ragged-mix-512, from one ncu
 # capture (profiles/k_pair_small_ragged_mix_512.md); reported only while the kernel's sources
 # (ts_pair.cu, then ts_internal.cuh) hash to the value recorded with the capture
-PAIR_TRAFFIC = {"bytes": 73_058_048 + 1_058_816, "source_sha1": "0f2e0618892f6230be70bf2c13d6c51b84f5f8ba"}
+PAIR_TRAFFIC = {"bytes": 49_016_576 + 146_944, "source_sha1": "6d758aa10d21075b5dcb2485497745e1fce19ad9"}
 
 
 def pair_traffic():

@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(256) k_pair(int32_t n_warps, const int32_t* __
 // a gather is one 16-byte read and a 2048-atom system takes 32 KB; a pair
 // vector is the exact integer difference plus the fixed-point image shift,
 // converted once to FP32.  List entries stream from global memory
-// (coalesced, evict-first, prefetched one block ahead).  The potential
+// (coalesced, evict-first, prefetched two blocks of four ahead).  The potential
 // arithmetic and summation order are those of k_pair; the pair vectors carry
 // the same single FP32 rounding but a different quantisation of the
 // coordinates, so the two kernels agree within the mixed-precision tolerance,
@@ -242,13 +242,20 @@ __global__ void __launch_bounds__(kPairSmallThreads) k_pair_small(
     };
     const uint32_t* lp = (use_in ? A.nbr_in : A.nbr) + k;
     int q = 0;
-    uint32_t n0 = 0, n1 = 0, n2 = 0, n3 = 0;
+    // list entries stream two blocks of four ahead of use (n: the next
+    // block, m: the one after)
+    uint32_t n0 = 0, n1 = 0, n2 = 0, n3 = 0, m0 = 0, m1 = 0, m2 = 0, m3 = 0;
     if (nn >= 4) { n0 = __ldcs(lp); n1 = __ldcs(lp + stride); n2 = __ldcs(lp + 2 * stride); n3 = __ldcs(lp + 3 * stride); }
+    if (nn >= 8) {
+      const uint32_t* np = lp + 4 * stride;
+      m0 = __ldcs(np); m1 = __ldcs(np + stride); m2 = __ldcs(np + 2 * stride); m3 = __ldcs(np + 3 * stride);
+    }
     for (; q + 4 <= nn; q += 4) {
       uint32_t e0 = n0, e1 = n1, e2 = n2, e3 = n3;
-      if (q + 8 <= nn) {
-        const uint32_t* np = lp + (int64_t)(q + 4) * stride;
-        n0 = __ldcs(np); n1 = __ldcs(np + stride); n2 = __ldcs(np + 2 * stride); n3 = __ldcs(np + 3 * stride);
+      n0 = m0; n1 = m1; n2 = m2; n3 = m3;
+      if (q + 12 <= nn) {
+        const uint32_t* np = lp + (int64_t)(q + 8) * stride;
+        m0 = __ldcs(np); m1 = __ldcs(np + stride); m2 = __ldcs(np + 2 * stride); m3 = __ldcs(np + 3 * stride);
       }
       one(e0); one(e1); one(e2); one(e3);
     }
