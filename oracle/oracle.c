@@ -525,6 +525,111 @@ void or_md_nhc(int B, const int64_t* offsets, double* x, double* v, const double
 }
 
 /* ------------------------------------------------------------------------- */
+/* NPT: isotropic barostat of Martyna, Tobias and Klein (1994) with Langevin  */
+/* (Ornstein-Uhlenbeck) friction and noise on the atoms and on the piston;   */
+/* the paper lists NPT among its integrators (Sec. 1) without a scheme.       */
+/* Per system: piston velocity v_e (the cell scales isotropically,            */
+/* dh/dt = v_e h), piston mass W = (Nf + 3) kT tau^2, Nf = 3N, a = 1 + 3/Nf. */
+/* Without friction:                                                          */
+/*   dx/dt = v + v_e x,   dv/dt = F/m - a v_e v,   dh/dt = v_e h,            */
+/*   W dv_e/dt = a 2K + Xi - 3 V P_ext,                                       */
+/* with K the kinetic energy, V = |det h| and Xi = -sum_pairs phi'(r) r the  */
+/* pair virial (= -tr of the stress accumulator W_ab = 1/2 sum phi' d d / r). */
+/* It conserves H = K + U + W v_e^2 / 2 + P_ext V.                            */
+/* One step, each sub-flow solved exactly (symmetric, as in the MTK           */
+/* integrator of Tuckerman et al. 2006, with BAOAB's O in the middle):        */
+/*   Be(dt/2): v_e += dt/2 (a 2K + Xi - 3 V P_ext) / W                       */
+/*   B(dt/2):  v <- v e^{-c dt/2} + dt/2 e^{-c dt/4} shc(c dt/4) F/m, c = a v_e */
+/*   A(dt/2):  x <- x e^{v_e dt/2} + dt/2 e^{v_e dt/4} shc(v_e dt/4) v;       */
+/*             h <- h e^{v_e dt/2}                                            */
+/*   O(dt):    v <- c1 v + sqrt((1 - c1^2) kT/m) xi_i,                        */
+/*             v_e <- c1 v_e + sqrt((1 - c1^2) kT/W) xi_e,  c1 = e^{-gamma dt} */
+/*   A(dt/2); forces, U and Xi at the new x and h; B(dt/2); Be(dt/2).         */
+/* shc(y) = sinh(y)/y.  xi_i = or_normals3(step, i, seed, uid); xi_e = the    */
+/* first normal of or_normals3(step, 0xffffffff, seed, uid).                  */
+/* Pinned by: the conserved H without friction (and its O(dt^2) size),        */
+/* time reversibility, an inert piston (tau -> inf) reproducing BAOAB, and   */
+/* the lattice constant of a cold damped FCC crystal against the minimum of  */
+/* the independent lattice sum's enthalpy u(a) + P_ext a^3/4.                */
+/* ------------------------------------------------------------------------- */
+static double shc(double y) {
+  if (fabs(y) < 1e-3) { double y2 = y * y; return 1.0 + y2 / 6.0 * (1.0 + y2 / 20.0); }
+  return sinh(y) / y;
+}
+
+/* One system's forces into F, energy returned, pair virial Xi into *xi. */
+static double sys_forces_virial(int use_cells, int n, const double* x, const double* h, const uint8_t* pbc,
+                                const or_pot* P, double* F, double* xi) {
+  memset(F, 0, sizeof(double) * 3 * n);
+  force_ctx c = {P, pot_shift(P), 0.0, F, {0}, NULL};
+  for_pairs(use_cells, n, x, h, pbc, pot_cutoff(P), force_cb, &c);
+  *xi = -(c.W[0] + c.W[4] + c.W[8]);
+  return c.E;
+}
+
+/* n_steps of NPT per system; cells [B][9] and baro [B] (v_e) are read and   */
+/* updated.  Outputs after the last step: E_pot, KE, H_ext (the quantity     */
+/* conserved without friction) and P_inst = (2K + Xi)/(3V) (may be NULL).    */
+void or_md_npt(int B, const int64_t* offsets, double* x, double* v, const double* mass, double* cells,
+               const uint8_t* pbc, const int32_t* pot_of_sys, const or_pot* pots, int use_cells, double dt,
+               int n_steps, const double* kT, double gamma, double tau, double p_ext, uint32_t seed,
+               const uint32_t* uid, uint64_t step0, double* baro, double* E_pot, double* KE, double* H_ext,
+               double* P_inst) {
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int s = 0; s < B; s++) {
+    int64_t o = offsets[s]; int n = (int)(offsets[s + 1] - o);
+    const or_pot* P = pots + pot_of_sys[s];
+    double* h = cells + 9 * s;
+    double* xs = x + 3 * o; double* vs = v + 3 * o;
+    const double nf = 3.0 * n, al = 1.0 + 3.0 / nf;
+    const double Wp = (nf + 3.0) * kT[s] * tau * tau;
+    const double c1 = exp(-gamma * dt);
+    double ve = baro[s];
+    double* F = (double*)malloc(sizeof(double) * 3 * (n > 0 ? n : 1));
+    double xi;
+    double E = sys_forces_virial(use_cells, n, xs, h, pbc + 3 * s, P, F, &xi);
+    for (int k = 0; k < n_steps; k++) {
+      double V = fabs(det3(h));
+      ve += 0.5 * dt * (al * 2.0 * kinetic(o, n, v, mass) + xi - 3.0 * V * p_ext) / Wp;   /* Be */
+      double c = al * ve;                                                                  /* B */
+      double eb = exp(-0.5 * c * dt), fb = 0.5 * dt * exp(-0.25 * c * dt) * shc(0.25 * c * dt);
+      for (int i = 0; i < n; i++)
+        for (int a = 0; a < 3; a++) vs[3 * i + a] = vs[3 * i + a] * eb + fb * F[3 * i + a] / mass[o + i];
+      for (int half = 0; half < 2; half++) {                                               /* A O A */
+        if (half == 1) {
+          for (int i = 0; i < n; i++) {
+            double z[3];
+            or_normals3(step0 + (uint64_t)k, (uint32_t)i, seed, uid[s], z);
+            double sc = sqrt((1.0 - c1 * c1) * kT[s] / mass[o + i]);
+            for (int a = 0; a < 3; a++) vs[3 * i + a] = c1 * vs[3 * i + a] + sc * z[a];
+          }
+          double z[3];
+          or_normals3(step0 + (uint64_t)k, 0xffffffffu, seed, uid[s], z);
+          ve = c1 * ve + sqrt((1.0 - c1 * c1) * kT[s] / Wp) * z[0];
+        }
+        double ea = exp(0.5 * ve * dt), fa = 0.5 * dt * exp(0.25 * ve * dt) * shc(0.25 * ve * dt);
+        for (int i = 0; i < 3 * n; i++) xs[i] = xs[i] * ea + fa * vs[i];
+        for (int q = 0; q < 9; q++) h[q] *= ea;
+      }
+      E = sys_forces_virial(use_cells, n, xs, h, pbc + 3 * s, P, F, &xi);
+      c = al * ve;                                                                         /* B */
+      eb = exp(-0.5 * c * dt); fb = 0.5 * dt * exp(-0.25 * c * dt) * shc(0.25 * c * dt);
+      for (int i = 0; i < n; i++)
+        for (int a = 0; a < 3; a++) vs[3 * i + a] = vs[3 * i + a] * eb + fb * F[3 * i + a] / mass[o + i];
+      V = fabs(det3(h));
+      ve += 0.5 * dt * (al * 2.0 * kinetic(o, n, v, mass) + xi - 3.0 * V * p_ext) / Wp;   /* Be */
+    }
+    double K = kinetic(o, n, v, mass), V = fabs(det3(h));
+    baro[s] = ve;
+    if (E_pot) E_pot[s] = E;
+    if (KE) KE[s] = K;
+    if (H_ext) H_ext[s] = K + E + 0.5 * Wp * ve * ve + p_ext * V;
+    if (P_inst) P_inst[s] = (2.0 * K + xi) / (3.0 * V);
+    free(F);
+  }
+}
+
+/* ------------------------------------------------------------------------- */
 /* Variable-cell FIRE (Bitzek et al. 2006; the paper's "structural relaxation */
 /* optimizers", Sec. 1, run under in-flight batching, Sec. 3).               */
 /* Generalised coordinates per system: xt_i = x_i Fd^-T (N rows) and the cell */

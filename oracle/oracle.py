@@ -69,6 +69,8 @@ def lib():
                             C.c_double, C.c_uint32, P, C.c_uint64, P, P]
         L.or_md_nhc.argtypes = [C.c_int, P, P, P, P, P, P, P, P, C.c_int, C.c_double, C.c_int, P, C.c_double, P, P,
                                 P, P]
+        L.or_md_npt.argtypes = [C.c_int, P, P, P, P, P, P, P, P, C.c_int, C.c_double, C.c_int, P, C.c_double,
+                                C.c_double, C.c_double, C.c_uint32, P, C.c_uint64, P, P, P, P, P]
         L.or_fire.argtypes = [C.c_int, P, P, P, P, P, P, C.c_int, P, P, P, C.c_int, P, P, P]
         L.or_forces_backward.argtypes = [C.c_int, P, P, P, P, P, P, C.c_int, C.c_int, P, P, P, P, P]
         L.or_rdf.argtypes = [C.c_int, P, P, P, P, C.c_double, C.c_int, C.c_int, P, P, P]
@@ -183,6 +185,27 @@ def md_nhc(offsets, x, v, mass, cells, pbc, pot_of_sys, pots, dt, n_steps, kT, t
     lib().or_md_nhc(B, _p(offsets), _p(x), _p(v), _p(mass), _p(cells), _p(pbc), _p(pos), C.cast(P, C.c_void_p),
                     int(use_cells), float(dt), int(n_steps), _p(kT), float(tau), _p(st), _p(E), _p(KE), _p(H))
     return x, v, E, KE, st, H
+
+
+def md_npt(offsets, x, v, mass, cells, pbc, pot_of_sys, pots, dt, n_steps, kT, gamma, tau, p_ext, seed=0, uid=None,
+           step0=0, baro=None, use_cells=False):
+    """NPT (isotropic MTK barostat, Langevin atoms and piston) for n_steps.
+    baro [B] is the piston velocity v_e (zero if None).  Returns new (x, v,
+    cells, baro, E_pot[B], KE[B], H_ext[B], P_inst[B]); inputs are not modified."""
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    B = len(offsets) - 1
+    x = _f64(x).copy(); v = _f64(v).copy(); mass = _f64(mass); cells = _f64(cells).reshape(B, 3, 3).copy()
+    pbc = np.ascontiguousarray(pbc, dtype=np.uint8).reshape(B, 3)
+    pos = np.ascontiguousarray(pot_of_sys, dtype=np.int32)
+    kT = _f64(np.broadcast_to(kT, (B,)))
+    uid = np.ascontiguousarray(np.arange(B) if uid is None else uid, dtype=np.uint32)
+    ve = np.zeros(B) if baro is None else _f64(baro).reshape(B).copy()
+    P = make_pots(pots)
+    E = np.zeros(B); KE = np.zeros(B); H = np.zeros(B); Pi = np.zeros(B)
+    lib().or_md_npt(B, _p(offsets), _p(x), _p(v), _p(mass), _p(cells), _p(pbc), _p(pos), C.cast(P, C.c_void_p),
+                    int(use_cells), float(dt), int(n_steps), _p(kT), float(gamma), float(tau), float(p_ext),
+                    C.c_uint32(seed), _p(uid), C.c_uint64(step0), _p(ve), _p(E), _p(KE), _p(H), _p(Pi))
+    return x, v, cells, ve, E, KE, H, Pi
 
 
 FIRE_DEFAULTS = dict(dt0=0.1, dt_max=1.0, finc=1.1, fdec=0.5, alpha0=0.1, falpha=0.99, maxstep=0.2,

@@ -149,6 +149,73 @@ def test_nhc_canonical_kinetic_energy(orc):
     assert abs(ks.mean() - target) < 4 * se
 
 
+def test_npt_nph_conserved_quantity(orc):
+    """NPT without friction (the MTK equations alone): the piston trades real
+    energy with the atoms (K + U moves by several epsilon, the volume by over
+    ten per cent) while K + U + W v_e^2/2 + P_ext V stays put.  A wrong sign
+    of the virial or a wrong P V term breaks this by orders of magnitude."""
+    b = W.lj_liquid(seed=5, n_systems=1, reps=(2, 2, 2), kT=1.0, rattle=0.05)
+    V0 = abs(np.linalg.det(b.cell[0]))
+    for p_ext in (0.0, 1.0):
+        x, v, h, ve = b.pos, b.vel, b.cell, None
+        H, KU, V = [], [], []
+        for blk in range(40):
+            x, v, h, ve, E, K, He, _ = orc.md_npt(b.offsets, x, v, b.mass, h, b.pbc, b.pot_idx, b.pots, 0.005, 50,
+                                                 [1.0], 0.0, 0.5, p_ext, baro=ve)
+            H.append(He[0]); KU.append(E[0] + K[0]); V.append(abs(np.linalg.det(h[0])))
+        H, KU, V = np.array(H), np.array(KU), np.array(V)
+        assert KU.max() - KU.min() > 2.0 and V.max() - V.min() > 0.1 * V0
+        assert np.abs(H - H[0]).max() < 0.03 * (KU.max() - KU.min())
+
+
+def test_npt_time_reversible(orc):
+    """Without friction, reversing the atom and piston velocities retraces
+    positions, cell and velocities (the splitting is symmetric)."""
+    b = W.lj_liquid(seed=6, n_systems=1, reps=(2, 2, 2), kT=1.0, rattle=0.05)
+    x1, v1, h1, ve1, _, _, _, _ = orc.md_npt(b.offsets, b.pos, b.vel, b.mass, b.cell, b.pbc, b.pot_idx, b.pots,
+                                             0.005, 60, [1.0], 0.0, 0.5, 1.0, baro=[0.3])
+    assert abs(np.linalg.det(h1[0]) / np.linalg.det(b.cell[0]) - 1) > 0.005     # the cell moved
+    x2, v2, h2, ve2, _, _, _, _ = orc.md_npt(b.offsets, x1, -v1, b.mass, h1, b.pbc, b.pot_idx, b.pots,
+                                             0.005, 60, [1.0], 0.0, 0.5, 1.0, baro=-ve1)
+    assert np.abs(x2 - b.pos).max() < 1e-10 and np.abs(v2 + b.vel).max() < 1e-10
+    assert np.abs(h2 - b.cell).max() < 1e-12 and abs(ve2[0] + 0.3) < 1e-10
+
+
+def test_npt_inert_piston_is_baoab(orc):
+    """An enormous piston mass keeps the cell fixed: the atoms follow BAOAB
+    with the same noise."""
+    b = _small_batch(4)
+    dt, gamma = 1.0 / W.T0_FS, 0.01 * W.T0_FS
+    kT = np.full(b.n_systems, W.KB_EV * 300.0)
+    xa, va, ha, _, Ea, Ka, _, _ = orc.md_npt(b.offsets, b.pos, b.vel, b.mass, b.cell, b.pbc, b.pot_idx, b.pots,
+                                             dt, 80, kT, gamma, 1e15, 0.0, seed=9, uid=[5, 6, 7], step0=40)
+    xb, vb, Eb, Kb = orc.md(b.offsets, b.pos, b.vel, b.mass, b.cell, b.pbc, b.pot_idx, b.pots, dt, 80, kind=1,
+                            kT=kT, gamma=gamma, seed=9, uid=[5, 6, 7], step0=40)
+    assert np.abs(ha - b.cell).max() < 1e-12
+    assert np.abs(xa - xb).max() < 1e-9 and np.abs(va - vb).max() < 1e-9
+    assert np.allclose(Ea, Eb, rtol=1e-9, atol=1e-12)
+
+
+def test_npt_ideal_gas_volume(orc):
+    """Four non-interacting atoms (epsilon = 0) at kT = P_ext = 1: the NPT
+    volume distribution is V^N exp(-P V / kT), so <V> = (N + 1) kT / P_ext = 5.
+    The MTK coupling factor 1 + 3/Nf is what gives the V^N; with the factor 1
+    the mean falls to N kT / P = 4."""
+    pos, cell = W.lattice("fcc", (1, 1, 1), 1.6)
+    pot = dict(kind=0, p=[1.0, 0.0, 0.0], rc=2.5, shift=1)
+    vel = np.random.default_rng(1).normal(size=pos.shape)
+    x, v, h, ve = pos, vel, cell[None], None
+    V = []
+    for blk in range(2000):
+        x, v, h, ve, _, _, _, _ = orc.md_npt([0, 4], x, v, np.ones(4), h, [[1, 1, 1]], [0], [pot], 0.005, 100,
+                                             [1.0], 1.0, 0.5, 1.0, seed=3, step0=100 * blk, baro=ve)
+        V.append(abs(np.linalg.det(h[0])))
+    V = np.array(V[20:])
+    blocks = V.reshape(-1, 20).mean(1)                       # 99 blocks of 2000 steps, far beyond the correlation time
+    se = blocks.std(ddof=1) / np.sqrt(len(blocks))
+    assert abs(V.mean() - 5.0) < 4 * se and se < 0.15
+
+
 def _golden_section(f, a, b, tol=1e-9):
     g = (np.sqrt(5) - 1) / 2
     c, d = b - g * (b - a), a + g * (b - a)
@@ -200,6 +267,23 @@ def test_fire_reaches_fcc_lattice_constant(orc, pot, a0, astar_survey):
     assert E[0] / len(pos) == pytest.approx(_fcc_energy_per_atom_numpy(pot, astar), abs=1e-6)
     # the relaxed cell stays cubic
     assert np.allclose(h / a_fit, 2 * np.eye(3), atol=1e-4)
+
+
+@pytest.mark.parametrize("p_ext", [0.0, 2.0])
+def test_npt_cold_crystal_enthalpy_minimum(orc, p_ext):
+    """A perfect FCC crystal at kT = 1e-8 under friction settles at the lattice
+    constant that minimises the independent lattice sum's enthalpy per atom,
+    u(a) + P_ext a^3 / 4 (a light piston: tau scaled so W = (Nf + 3) kT tau^2 = 24)."""
+    astar = _golden_section(lambda a: _fcc_energy_per_atom_numpy(LJR, a) + p_ext * a ** 3 / 4, 1.3, 1.8)
+    if p_ext == 0.0:
+        assert astar == pytest.approx(1.549603, abs=2e-6)
+    pos, cell = W.lattice("fcc", (2, 2, 2), 1.50)
+    x, v, h, _, _, K, _, Pi = orc.md_npt([0, 32], pos, np.zeros_like(pos), np.ones(32), cell[None], [[1, 1, 1]], [0],
+                                          [LJR], 0.005, 6000, [1e-8], 1.0, 5000.0, p_ext, seed=1)
+    a = np.cbrt(abs(np.linalg.det(h[0])) / 8)
+    assert a == pytest.approx(astar, rel=5e-6)
+    assert Pi[0] == pytest.approx(p_ext, abs=2e-3)
+    assert np.allclose(h[0] / a, 2 * np.eye(3), atol=1e-9)   # isotropic scaling keeps the cube
 
 
 def test_fire_fixed_cell_reduces_forces(orc):
