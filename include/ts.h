@@ -168,7 +168,7 @@ int32_t ts_batch_max_neighbors(const ts_batch* b);
  * E and stress are summed per system in FP64, deterministically. */
 ts_status ts_pair_forces(ts_batch* b, ts_state* s, double* F, double* E, double* stress, void* stream);
 
-typedef enum { TS_NVE = 0, TS_LANGEVIN = 1, TS_NVT_NHC = 2 } ts_md_kind;
+typedef enum { TS_NVE = 0, TS_LANGEVIN = 1, TS_NVT_NHC = 2, TS_NPT_LANGEVIN = 3 } ts_md_kind;
 
 /* MD parameters (Sec. 1 lists NVE, NVT and Langevin integrators).
  * NVE: velocity Verlet.  LANGEVIN: BAOAB with friction gamma (1/t0) and
@@ -182,7 +182,25 @@ typedef enum { TS_NVE = 0, TS_LANGEVIN = 1, TS_NVT_NHC = 2 } ts_md_kind;
  * Nf = 3n - 3; nhc is the chain state, device [n_systems][6] f64 (xi_1..3,
  * then the thermostat velocities w_1..3; zeros to start), read and written.
  * The extended energy K + U + sum Q_k w_k^2/2 + Nf kT xi_1 + kT (xi_2 + xi_3)
- * is conserved. */
+ * is conserved.
+ * NPT_LANGEVIN (Sec. 1 lists NPT): isotropic barostat of Martyna, Tobias and
+ * Klein (1994) with Langevin friction gamma and noise on the atoms and on the
+ * piston.  Per system the cell scales as dh/dt = v_e h; piston mass
+ * W = (Nf + 3) kT tau^2 with Nf = 3n and barostat time tau (t0); external
+ * pressure p_ext (eV/A^3); the atoms couple through a = 1 + 3/Nf:
+ *   dx/dt = v + v_e x, dv/dt = F/m - a v_e v,
+ *   W dv_e/dt = a 2K + Xi - 3 V p_ext   (Xi = -sum over pairs phi'(r) r).
+ * One step: piston half kick, atom half kick, half drift, O step of atoms
+ * and piston (the piston's normal is the first of the atom-index counter
+ * 0xffffffff), half drift, forces, atom half kick, piston half kick; every
+ * sub-flow is solved exactly.  baro: device [n_systems] f64, the piston
+ * velocities v_e (zeros to start), read and written; s->cell is updated in
+ * place.  Every system must be periodic along all three axes
+ * (TS_ERR_UNSUPPORTED otherwise).  Without friction K + U + W v_e^2/2 +
+ * p_ext V is conserved.  MD steps of this kind compute forces from the full
+ * neighbour lists (no inner lists) and re-list a system when its atoms'
+ * displacement plus the image shifts' movement under the cell change could
+ * reach the skin. */
 typedef struct {
   int32_t kind;
   double dt;
@@ -190,8 +208,10 @@ typedef struct {
   const double* kT;
   uint32_t seed;
   uint64_t step0;
-  double tau;      /* NVT_NHC only */
+  double tau;      /* NVT_NHC: thermostat time; NPT_LANGEVIN: barostat time */
   double* nhc;     /* NVT_NHC only */
+  double p_ext;    /* NPT_LANGEVIN only */
+  double* baro;    /* NPT_LANGEVIN only */
 } ts_md_params;
 
 /* Run n_steps MD steps on the whole batch (Sec. 4 runs Langevin MD).  The

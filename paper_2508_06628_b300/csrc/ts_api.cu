@@ -59,7 +59,8 @@ size_t scratch_bytes(int64_t Ncap, int64_t Bcap, int64_t Ccap, int32_t max_nbrs,
                            2 * 16 /*g*/);
   per_slot += (f64 ? 3 * 8 : 2 * 16) /*prune reference*/ + 4 /*nn_in*/ + (size_t)max_nbrs * 4 /*inner list*/;
   per_slot += 4 * 4 /*perm sys bin nn*/ + 3 * 4 /*tmp i*/ + (size_t)max_nbrs * 4 + 8 * 8 / 32 /*partials*/ + 4 / 32 /*warp_sys*/ + 16 / 32 /*pair work items*/;
-  size_t per_sys = 8 * 4 + 9 * 8 * 3 + 9 * 4 + 6 * 4 + 4 * 4 + 8 + 12 /*list-build work table*/ + (size_t)kNCodes * (32 + 24 + 16);
+  size_t per_sys = 8 * 4 + 9 * 8 * 3 + 9 * 4 + 6 * 4 + 4 * 4 + 8 + 12 /*list-build work table*/ + 8 /*piston*/ +
+                   (size_t)kNCodes * (32 + 24 + 16);
   return per_slot * (size_t)Ncap + per_sys * (size_t)Bcap + (size_t)Ccap * 8;
 }
 
@@ -163,7 +164,7 @@ extern "C" ts_status ts_batch_create(const ts_batch_config* cfg, const ts_potent
   ok = ok && alloc(b, b->d_partial, (size_t)kPartialStride * b->Wcap) && alloc(b, b->d_warp_sys, b->Wcap) &&
        alloc(b, b->d_count, b->Ccap) && alloc(b, b->d_cstart, b->Ccap) &&
        alloc(b, b->d_bsum, (b->Ccap + 1023) / 1024 + 1) && alloc(b, b->d_starts, B + 1) &&
-       alloc(b, b->d_Eint, B) && alloc(b, b->d_Wint, 9 * B) && alloc(b, b->d_scal, 32 * B) && alloc(b, b->d_nhc, 6 * B) &&
+       alloc(b, b->d_Eint, B) && alloc(b, b->d_Wint, 9 * B) && alloc(b, b->d_scal, 32 * B) && alloc(b, b->d_nhc, 6 * B) && alloc(b, b->d_baro, B) &&
        alloc(b, b->d_gparam_part, 4 * b->Wcap) && alloc(b, b->d_gacc, 3 * kMaxPots) &&
        alloc(b, b->d_items, b->Wcap) && alloc(b, b->d_tab_sys, B) && alloc(b, b->d_tab_base, B + 1) && alloc(b, b->d_tab_base_a, B + 1) &&
        alloc(b, b->d_tab_n, 3);
@@ -546,18 +547,18 @@ void relist(ts_batch* b, cudaStream_t st, bool move_fire) {
 // latency-bound kernels are dispatched ahead of the pair kernel's pending
 // CTAs).  The two halves touch disjoint systems.  Returns false (nothing
 // issued) when the overlap is off or `st` is the legacy default stream.
-bool relist_pair_overlapped(ts_batch* b, cudaStream_t st, bool move_fire, bool ew) {
+bool relist_pair_overlapped(ts_batch* b, cudaStream_t st, bool move_fire, bool ew, bool inner) {
   if (!b->overlap_relist || !b->side || st == nullptr) return false;
   relist_sort(b, st, move_fire, 0);
   if (!cuda_ok(b, cudaEventRecord(b->ev_fork, st), "event record") ||
       !cuda_ok(b, cudaStreamWaitEvent(b->side, b->ev_fork, 0), "stream wait"))
     return false;
   relist_build(b, b->side, b->prio_hi);
-  pair(b, b->side, ew, kPairRelisted, b->prio_hi, true);
+  pair(b, b->side, ew, kPairRelisted, b->prio_hi, inner);
   cuda_ok(b, cudaEventRecord(b->ev_join, b->side), "event record");
-  pair(b, st, ew, kPairKept, 0, true);
+  pair(b, st, ew, kPairKept, 0, inner);
   cuda_ok(b, cudaStreamWaitEvent(st, b->ev_join, 0), "stream wait");
-  relist_finish(b, st, true);
+  relist_finish(b, st, inner);
   return true;
 }
 
@@ -679,10 +680,13 @@ extern "C" ts_status ts_md_step(ts_batch* b, ts_state* s, const ts_md_params* p,
   ts_status r = check_state(b, s, true);
   if (r != TS_OK) return r;
   if (!p || n_steps < 0 || !(p->dt > 0) ||
-      (p->kind != TS_NVE && p->kind != TS_LANGEVIN && p->kind != TS_NVT_NHC) ||
+      (p->kind != TS_NVE && p->kind != TS_LANGEVIN && p->kind != TS_NVT_NHC && p->kind != TS_NPT_LANGEVIN) ||
       (p->kind == TS_LANGEVIN && (!p->kT || !(p->gamma >= 0))) ||
-      (p->kind == TS_NVT_NHC && (!p->kT || !p->nhc || !(p->tau > 0))))
+      (p->kind == TS_NVT_NHC && (!p->kT || !p->nhc || !(p->tau > 0))) ||
+      (p->kind == TS_NPT_LANGEVIN &&
+       (!p->kT || !p->baro || !(p->tau > 0) || !(p->gamma >= 0) || !std::isfinite(p->p_ext))))
     return fail(b, TS_ERR_INVALID_ARG, "bad MD parameters");
+  const bool npt = p->kind == TS_NPT_LANGEVIN;
   cudaStream_t st = (cudaStream_t)stream;
   r = prologue(b, s, st, true);
   if (r != TS_OK) return r;
@@ -694,12 +698,22 @@ extern "C" ts_status ts_md_step(ts_batch* b, ts_state* s, const ts_md_params* p,
   if (p->kind == TS_NVT_NHC &&
       !cuda_ok(b, cudaMemcpyAsync(b->d_nhc, p->nhc, 48 * b->B, cudaMemcpyDeviceToDevice, st), "nhc"))
     return TS_ERR_CUDA;
+  if (npt) {   // the piston velocities live in batch memory during the call; every axis periodic
+    if (!cuda_ok(b, cudaMemcpyAsync(b->d_baro, p->baro, 8 * b->B, cudaMemcpyDeviceToDevice, st), "baro"))
+      return TS_ERR_CUDA;
+    k_require_periodic<<<(b->B + 127) / 128, 128, 0, st>>>(b->B, b->S, b->d_err);
+    b->launches++;
+  }
   ensure_forces(b, st);
+  if (npt) pair(b, st, true, kPairAll);   // the virial of every system for the first piston kick
   double c1 = exp(-p->gamma * p->dt);
   r = md_loop(b, st, p, n_steps, c1, E != nullptr || KE != nullptr);
   if (r != TS_OK) return r;
   if (p->kind == TS_NVT_NHC &&
       !cuda_ok(b, cudaMemcpyAsync(p->nhc, b->d_nhc, 48 * b->B, cudaMemcpyDeviceToDevice, st), "nhc"))
+    return TS_ERR_CUDA;
+  if (npt && (!cuda_ok(b, cudaMemcpyAsync(p->baro, b->d_baro, 8 * b->B, cudaMemcpyDeviceToDevice, st), "baro") ||
+              !cuda_ok(b, cudaMemcpyAsync(s->cell, b->S.h, 72 * b->B, cudaMemcpyDeviceToDevice, st), "cell")))
     return TS_ERR_CUDA;
   reduce_sys(b, st, E, nullptr, KE);
   export_state(b, st, s->pos, s->vel);

@@ -14,7 +14,7 @@ struct ts_graph_entry {
   bool need_e = false;
   double dt = 0, c1 = 0;
   uint32_t seed = 0;
-  double tau = 0;
+  double tau = 0, p_ext = 0;
   cudaStream_t stream = nullptr;
   cudaGraphExec_t exec = nullptr;
   int64_t kernels = 0;      // kernel nodes in the graph
@@ -61,6 +61,7 @@ struct ts_batch {
   double* d_Wint = nullptr;
   double* d_scal = nullptr;         // per-system FIRE / scratch scalars [16 B]
   double* d_nhc = nullptr;          // Nose-Hoover chain state during a call [6 per system]
+  double* d_baro = nullptr;         // NPT piston velocities during a call [1 per system]
   double* d_gparam_part = nullptr;  // per-warp parameter-gradient partials [4 Wcap]
   double* d_gacc = nullptr;
   std::vector<void*> allocations;
@@ -112,7 +113,7 @@ void relist_lists(ts_batch* b, cudaStream_t st, bool move_fire, int prio = 0);
 void relist_sort(ts_batch* b, cudaStream_t st, bool move_fire, int prio);
 void relist_build(ts_batch* b, cudaStream_t st, int prio);
 void relist_finish(ts_batch* b, cudaStream_t st, bool md_pass);
-bool relist_pair_overlapped(ts_batch* b, cudaStream_t st, bool move_fire, bool ew);
+bool relist_pair_overlapped(ts_batch* b, cudaStream_t st, bool move_fire, bool ew, bool inner);
 void relist_large_sort(ts_batch* b, cudaStream_t st, bool move_fire);
 void pair(ts_batch* b, cudaStream_t st, bool ew, int filter, int prio = 0, bool inner = false);
 void reduce_sys(ts_batch* b, cudaStream_t st, double* E, double* stress, double* KE);

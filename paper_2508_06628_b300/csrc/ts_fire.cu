@@ -31,13 +31,6 @@ __device__ inline void inv_T3(const double* A, double* out) {   // out = A^-T
   for (int a = 0; a < 3; a++) for (int b = 0; b < 3; b++) out[3 * a + b] = g[3 * b + a];
 }
 
-// The variable-cell filter needs a stress along every axis: a system with a
-// non-periodic axis is refused (device error word, read at poll).
-__global__ void k_require_periodic(int32_t B, SysArrays S, int32_t* err) {
-  int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s < B && S.pmask[s] != 7) atomicOr(err, kErrUnsupported);
-}
-
 __global__ void k_fire_init(int32_t B, const double* __restrict__ cell, const ts_fire_params p, ts_fire_state* fs) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= B) return;

@@ -28,6 +28,14 @@ constexpr float kGrid = 4096.0f;          // 2^12
 constexpr double kListBand = 1e-3;
 // Default inner skin of the pruned pair list, as a fraction of the skin.
 constexpr double kInnerSkinFraction = 0.3;
+// NPT: per-system factors written by k_npt_sys for the step's atom updates
+// (stride in doubles and slots): atom kicks v <- v eb + fb F/m at the step's
+// opening and closing, half drifts x <- x + x ea + fa v (ea = e^{v_e dt/2} - 1)
+// before and after the O step, the displacement allowance and lambda - 1, the
+// isotropic scale of the cell since the listing.
+constexpr int kNptStride = 32;
+enum NptFactor : int { kNptEbOpen = 0, kNptFbOpen, kNptEa1, kNptFa1, kNptEa2, kNptFa2, kNptEbClose, kNptFbClose,
+                       kNptAllow, kNptLam };
 constexpr float kInvGrid = 1.0f / 4096.0f;
 constexpr double kMaxCoord = 2000.0;      // |x| bound of the hi/lo representation
 constexpr int kJBits = 22;                // neighbour entry: j (22 bits) | image code (10 bits)

@@ -175,7 +175,7 @@ __device__ inline double det3(const double* h) {
 // the edge bins (bins are at least r_list wide, so every pair within r_list
 // still lies in neighbouring bins), and the stencil stops at the edges.
 __global__ void k_geometry(int32_t B, SysArrays S, const double* __restrict__ cell, const uint8_t* __restrict__ pbc,
-                           const DevPot* __restrict__ pots, int32_t* err, int cell_check) {
+                           const DevPot* __restrict__ pots, int32_t* err, int cell_check, int keep_pmask = 0) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= B) return;
   double h[9];
@@ -187,7 +187,7 @@ __global__ void k_geometry(int32_t B, SysArrays S, const double* __restrict__ ce
     if (moved) { S.relist[s] = 1; S.any[0] = 1; }
   }
   for (int q = 0; q < 9; q++) S.h[9 * s + q] = h[q];
-  const int pm = pbc ? ((pbc[3 * s] ? 1 : 0) | (pbc[3 * s + 1] ? 2 : 0) | (pbc[3 * s + 2] ? 4 : 0)) : 7;
+  const int pm = keep_pmask ? S.pmask[s] : pbc ? ((pbc[3 * s] ? 1 : 0) | (pbc[3 * s + 1] ? 2 : 0) | (pbc[3 * s + 2] ? 4 : 0)) : 7;
   S.pmask[s] = pm;
   double d = det3(h);
   if (!(fabs(d) > 0) || !isfinite(d)) { atomicOr(err, kErrNonFinite); return; }

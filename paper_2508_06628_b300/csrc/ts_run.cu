@@ -1,6 +1,7 @@
 // ts_run.cu -- the persistent MD step loop behind ts_md_step.  The K-step
 // loop (kick/drift/noise + skin check, conditional per-system re-listing,
-// pair forces) is issued once into a CUDA graph per (K, parameters, stream)
+// pair forces; the chain or the piston between steps under NVT-NHC and NPT)
+// is issued once into a CUDA graph per (K, parameters, stream)
 // and replayed on later calls, so the host crosses to the device once per
 // call instead of once per kernel.  Kernels read sizes and the Langevin
 // step counter from device memory, so one graph serves every call with the
@@ -18,19 +19,30 @@ static void md_body(ts_batch* b, cudaStream_t st, const ts_md_params* p, int n_s
   const int wblocks = (int)(((int64_t)b->nwarps * 32 + 127) / 128);
   const int sblocks = (int)(((int64_t)b->B * 32 + 127) / 128);
   const bool nhc = p->kind == TS_NVT_NHC;
-  double* vscale = b->d_scal;   // per-system velocity scale of the chain
-  auto final_ke = [&](double kick, const double* scale) {   // kick (if any), scale (if any), KE partials
-    if (b->f64) k_md_final<true><<<wblocks, 128, 0, st>>>(b->nwarps, b->S, b->A, kick, b->d_partial, scale);
-    else k_md_final<false><<<wblocks, 128, 0, st>>>(b->nwarps, b->S, b->A, kick, b->d_partial, scale);
+  const bool npt = p->kind == TS_NPT_LANGEVIN;
+  const bool inner = !npt;      // NPT: full lists (the inner lists' refresh test has no cell term)
+  double* vscale = b->d_scal;   // per-system velocity scale of the chain, or the NPT factors
+  auto final_ke = [&](double kick, const double* scale, const double* nptf) {   // kick, scale, KE partials
+    if (b->f64) k_md_final<true><<<wblocks, 128, 0, st>>>(b->nwarps, b->S, b->A, kick, b->d_partial, scale, nptf);
+    else k_md_final<false><<<wblocks, 128, 0, st>>>(b->nwarps, b->S, b->A, kick, b->d_partial, scale, nptf);
     b->launches++;
   };
   auto chain = [&](int halves) {
     k_nhc_update<<<sblocks, 128, 0, st>>>(b->B, b->S, b->d_partial, p->dt, p->tau, halves, b->d_nhc, vscale);
     b->launches++;
   };
+  auto piston = [&](int mode, int koff) {
+    k_npt_sys<<<sblocks, 128, 0, st>>>(b->B, b->S, b->d_pots, b->d_partial, p->dt, c1, p->tau, p->p_ext, p->seed,
+                                       b->d_step, (uint64_t)koff, mode, b->d_baro, b->d_scal, b->d_err);
+    b->launches++;
+  };
   if (nhc && n_steps > 0) {   // the opening chain half-step of the first step
-    final_ke(0.0, nullptr);
+    final_ke(0.0, nullptr, nullptr);
     chain(1);
+  }
+  if (npt && n_steps > 0) {   // the opening piston half kick and the first step's factors
+    final_ke(0.0, nullptr, nullptr);
+    piston(kNptOpen, 0);
   }
   for (int k = 0; k < n_steps; k++) {
     // BAOAB and NVE merge the closing half kick of a step with the opening
@@ -41,32 +53,45 @@ static void md_body(ts_batch* b, cudaStream_t st, const ts_md_params* p, int n_s
         k_md_kick_drift<true, 0><<<g, 256, 0, st>>>(b->Npad, b->S, b->A, b->d_pots, kick, p->dt, c1, p->seed, b->d_step, k, nullptr);
       else if (p->kind == TS_LANGEVIN)
         k_md_kick_drift<true, 1><<<g, 256, 0, st>>>(b->Npad, b->S, b->A, b->d_pots, kick, p->dt, c1, p->seed, b->d_step, k, nullptr);
-      else
+      else if (nhc)
         k_md_kick_drift<true, 2><<<g, 256, 0, st>>>(b->Npad, b->S, b->A, b->d_pots, kick, p->dt, c1, p->seed, b->d_step, k, vscale);
+      else
+        k_md_kick_drift<true, 3><<<g, 256, 0, st>>>(b->Npad, b->S, b->A, b->d_pots, kick, p->dt, c1, p->seed, b->d_step, k, vscale);
     } else {
       if (p->kind == TS_NVE)
         k_md_kick_drift<false, 0><<<g, 256, 0, st>>>(b->Npad, b->S, b->A, b->d_pots, kick, p->dt, c1, p->seed, b->d_step, k, nullptr);
       else if (p->kind == TS_LANGEVIN)
         k_md_kick_drift<false, 1><<<g, 256, 0, st>>>(b->Npad, b->S, b->A, b->d_pots, kick, p->dt, c1, p->seed, b->d_step, k, nullptr);
-      else
+      else if (nhc)
         k_md_kick_drift<false, 2><<<g, 256, 0, st>>>(b->Npad, b->S, b->A, b->d_pots, kick, p->dt, c1, p->seed, b->d_step, k, vscale);
+      else
+        k_md_kick_drift<false, 3><<<g, 256, 0, st>>>(b->Npad, b->S, b->A, b->d_pots, kick, p->dt, c1, p->seed, b->d_step, k, vscale);
     }
     b->launches++;
-    bool ew = need_e && k == n_steps - 1;
+    if (npt) {   // geometry and image shifts of the new cell (k_npt_sys scaled it)
+      k_geometry<<<(b->B + 127) / 128, 128, 0, st>>>(b->B, b->S, b->S.h, nullptr, b->d_pots, b->d_err, 0, 1);
+      k_shift_table<<<(int)(((int64_t)b->B * kNCodes + 255) / 256), 256, 0, st>>>(b->B, b->S);
+      b->launches += 2;
+    }
+    bool ew = npt || (need_e && k == n_steps - 1);   // NPT: the virial drives the piston
     // forces from the inner lists; systems flagged for pruning or re-listed
     // in this pass refresh theirs in the same launch
-    if (!relist_pair_overlapped(b, st, false, ew)) {
+    if (!relist_pair_overlapped(b, st, false, ew, inner)) {
       relist_lists(b, st, false);
-      pair(b, st, ew, kPairAll, 0, true);
-      relist_finish(b, st, true);
+      pair(b, st, ew, kPairAll, 0, inner);
+      relist_finish(b, st, inner);
     }
     if (nhc) {   // closing half kick and the kinetic energy, then the chain (two half-steps between steps)
-      final_ke(0.5 * p->dt, nullptr);
+      final_ke(0.5 * p->dt, nullptr, nullptr);
       chain(k == n_steps - 1 ? 1 : 2);
     }
+    if (npt) {   // closing atom kick and the kinetic energy, then the piston (closing + next opening)
+      final_ke(0.0, nullptr, vscale);
+      piston(kNptClose | (k < n_steps - 1 ? kNptOpen : 0), k + 1);
+    }
   }
-  if (nhc) final_ke(0.0, n_steps > 0 ? vscale : nullptr);   // the last chain scaling, kinetic energy
-  else final_ke(n_steps > 0 ? 0.5 * p->dt : 0.0, nullptr);
+  if (nhc) final_ke(0.0, n_steps > 0 ? vscale : nullptr, nullptr);   // the last chain scaling, kinetic energy
+  else if (!npt || n_steps == 0) final_ke(n_steps > 0 ? 0.5 * p->dt : 0.0, nullptr, nullptr);
   clear_dirty(b, st);
 }
 
@@ -82,7 +107,7 @@ ts_status md_loop(ts_batch* b, cudaStream_t st, const ts_md_params* p, int n_ste
   if (capturable) {
     for (auto& g : b->graphs) {
       if (g.kind == 0 && g.n_steps == n_steps && g.md_kind == p->kind && g.need_e == need_e && g.dt == p->dt &&
-          g.c1 == c1 && g.seed == p->seed && g.tau == p->tau && g.stream == st) {
+          g.c1 == c1 && g.seed == p->seed && g.tau == p->tau && g.p_ext == p->p_ext && g.stream == st) {
         if (!cuda_ok(b, cudaGraphLaunch(g.exec, st), "cudaGraphLaunch")) return TS_ERR_CUDA;
         b->launches += g.kernels;
         return TS_OK;
@@ -100,7 +125,7 @@ ts_status md_loop(ts_batch* b, cudaStream_t st, const ts_md_params* p, int n_ste
         cudaGraphDestroy(graph);
         ts_graph_entry ge;
         ge.kind = 0; ge.n_steps = n_steps; ge.md_kind = p->kind; ge.need_e = need_e; ge.dt = p->dt; ge.c1 = c1;
-        ge.seed = p->seed; ge.tau = p->tau; ge.stream = st; ge.exec = exec; ge.kernels = nk;
+        ge.seed = p->seed; ge.tau = p->tau; ge.p_ext = p->p_ext; ge.stream = st; ge.exec = exec; ge.kernels = nk;
         if (b->graphs.size() > 16) { cudaGraphExecDestroy(b->graphs.front().exec); b->graphs.erase(b->graphs.begin()); }
         b->graphs.push_back(ge);
         if (!cuda_ok(b, cudaGraphLaunch(exec, st), "cudaGraphLaunch")) return TS_ERR_CUDA;

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libts.so")
 TS_OK, TS_ERR_INVALID_ARG, TS_ERR_UNSUPPORTED, TS_ERR_BUDGET, TS_ERR_CUDA = 0, 1, 2, 3, 4
 TS_ERR_NEIGHBOR_OVERFLOW, TS_ERR_TIMEOUT, TS_ERR_NONFINITE, TS_ERR_NOT_READY = 5, 6, 7, 8
 TS_MIXED, TS_FP64 = 0, 1
-TS_NVE, TS_LANGEVIN, TS_NVT_NHC = 0, 1, 2
+TS_NVE, TS_LANGEVIN, TS_NVT_NHC, TS_NPT_LANGEVIN = 0, 1, 2, 3
 STATUS_NAMES = {0: "TS_OK", 1: "TS_ERR_INVALID_ARG", 2: "TS_ERR_UNSUPPORTED", 3: "TS_ERR_BUDGET", 4: "TS_ERR_CUDA",
                 5: "TS_ERR_NEIGHBOR_OVERFLOW", 6: "TS_ERR_TIMEOUT", 7: "TS_ERR_NONFINITE", 8: "TS_ERR_NOT_READY"}
 
@@ -48,7 +48,8 @@ class State(C.Structure):
 
 class MDParams(C.Structure):
     _fields_ = [("kind", C.c_int32), ("dt", C.c_double), ("gamma", C.c_double), ("kT", C.c_void_p),
-                ("seed", C.c_uint32), ("step0", C.c_uint64), ("tau", C.c_double), ("nhc", C.c_void_p)]
+                ("seed", C.c_uint32), ("step0", C.c_uint64), ("tau", C.c_double), ("nhc", C.c_void_p),
+                ("p_ext", C.c_double), ("baro", C.c_void_p)]
 
 
 class FireParams(C.Structure):
@@ -233,12 +234,14 @@ class Batch:
                     "ts_pair_forces")
 
     def md_step(self, s: DeviceState, n_steps, dt, kind=TS_NVE, gamma=0.0, kT=None, seed=0, step0=0, E=None, KE=None,
-                stream=None, tau=0.0, nhc=None):
-        """n_steps MD steps (kind TS_NVE, TS_LANGEVIN or TS_NVT_NHC; the chain
-        state ``nhc`` [n_systems, 6] f64 device tensor is updated in place)."""
+                stream=None, tau=0.0, nhc=None, p_ext=0.0, baro=None):
+        """n_steps MD steps (kind TS_NVE, TS_LANGEVIN, TS_NVT_NHC or
+        TS_NPT_LANGEVIN; the chain state ``nhc`` [n_systems, 6] and the piston
+        velocities ``baro`` [n_systems] are f64 device tensors updated in
+        place; under NPT ``s.cell`` is updated too)."""
         kT = kT if kT is not None else s.kT
         p = MDParams(int(kind), float(dt), float(gamma), _ptr(kT) if kT is not None else None, int(seed), int(step0),
-                     float(tau), _ptr(nhc))
+                     float(tau), _ptr(nhc), float(p_ext), _ptr(baro))
         self._check(lib().ts_md_step(self.h, C.byref(s.c()), C.byref(p), int(n_steps), _ptr(E), _ptr(KE),
                                      _stream(stream)), "ts_md_step")
 
