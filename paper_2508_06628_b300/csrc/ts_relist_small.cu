@@ -290,6 +290,25 @@ __device__ void build_warp(int s, int wi, const SysArrays& S, const SlotArrays& 
   int cnt = 0;
   const int nx = x1 - x0 + 1, ny = y1 - y0 + 1, ncell = nx * ny * (z1 - z0 + 1);
   const int64_t coff = S.caller_off[s];
+  // bounding box of the warp's atoms (hi parts; padding lanes take lane 0's
+  // atom): a staged candidate farther than r_list + 1e-3 A from it is no
+  // lane's neighbour and is dropped before the per-lane tests
+  float3 bb_lo = make_float3(0.f, 0.f, 0.f), bb_hi = bb_lo;
+  if constexpr (!F64) {
+    float bx = __shfl_sync(0xffffffffu, hi.x, valid ? lane : 0), by = __shfl_sync(0xffffffffu, hi.y, valid ? lane : 0),
+          bz = __shfl_sync(0xffffffffu, hi.z, valid ? lane : 0);
+    bb_lo = make_float3(bx, by, bz); bb_hi = bb_lo;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      bb_lo.x = fminf(bb_lo.x, __shfl_xor_sync(0xffffffffu, bb_lo.x, o));
+      bb_lo.y = fminf(bb_lo.y, __shfl_xor_sync(0xffffffffu, bb_lo.y, o));
+      bb_lo.z = fminf(bb_lo.z, __shfl_xor_sync(0xffffffffu, bb_lo.z, o));
+      bb_hi.x = fmaxf(bb_hi.x, __shfl_xor_sync(0xffffffffu, bb_hi.x, o));
+      bb_hi.y = fmaxf(bb_hi.y, __shfl_xor_sync(0xffffffffu, bb_hi.y, o));
+      bb_hi.z = fmaxf(bb_hi.z, __shfl_xor_sync(0xffffffffu, bb_hi.z, o));
+    }
+  }
+  const unsigned lanes_below = (1u << lane) - 1u;
   // cells in (z, y, x) order, 32 at a time: each lane resolves one cell's
   // bin start, count, image code and shift, then the warp walks them in order
   for (int cb = 0; cb < ncell; cb += 32) {
@@ -321,15 +340,18 @@ __device__ void build_warp(int s, int wi, const SysArrays& S, const SlotArrays& 
       int code = __shfl_sync(0xffffffffu, my_code, tc);
       int64_t b0 = seg + __shfl_sync(0xffffffffu, my_start, tc);
       int c = __shfl_sync(0xffffffffu, my_count, tc);
-      float a0 = 0, a1 = 0, a2 = 0, e0 = 0, e1 = 0, e2 = 0;
+      float a0 = 0, a1 = 0, a2 = 0, e0 = 0, e1 = 0, e2 = 0, cs0 = 0, cs1 = 0, cs2 = 0;
       double s0 = 0, s1 = 0, s2 = 0;
       if constexpr (F64) {
         const double* sd = S.shiftd + 3 * ((int64_t)s * kNCodes + code);
         s0 = sd[0] - xi[0]; s1 = sd[1] - xi[1]; s2 = sd[2] - xi[2];
       } else {
-        a0 = __shfl_sync(0xffffffffu, my_sh.x, tc) - hi.x;   // exact (2^-12 grid)
-        a1 = __shfl_sync(0xffffffffu, my_sh.y, tc) - hi.y;
-        a2 = __shfl_sync(0xffffffffu, my_sh.z, tc) - hi.z;
+        cs0 = __shfl_sync(0xffffffffu, my_sh.x, tc);   // the cell's image shift (hi)
+        cs1 = __shfl_sync(0xffffffffu, my_sh.y, tc);
+        cs2 = __shfl_sync(0xffffffffu, my_sh.z, tc);
+        a0 = cs0 - hi.x;   // exact (2^-12 grid)
+        a1 = cs1 - hi.y;
+        a2 = cs2 - hi.z;
         e0 = __shfl_sync(0xffffffffu, my_sl.x, tc) - lo.x;
         e1 = __shfl_sync(0xffffffffu, my_sl.y, tc) - lo.y;
         e2 = __shfl_sync(0xffffffffu, my_sl.z, tc) - lo.z;
@@ -338,12 +360,27 @@ __device__ void build_warp(int s, int wi, const SysArrays& S, const SlotArrays& 
       {
         for (int base = 0; base < c; base += 32) {
           int q = base + lane;
-          if (q < c) {
-            if constexpr (F64) { for (int cc = 0; cc < 3; cc++) sh_d[lane][cc] = A.xd[3 * (b0 + q) + cc]; }
-            else sh_h[lane] = A.xh[b0 + q];   // lo parts only for the rare undecided tests
+          int nc = min(32, c - base);
+          if constexpr (F64) {
+            if (q < c) { for (int cc = 0; cc < 3; cc++) sh_d[lane][cc] = A.xd[3 * (b0 + q) + cc]; }
+          } else {
+            // stage the candidates near the warp's box, in order, with their
+            // index in the chunk in w (lo parts only for the rare undecided tests)
+            float4 cj = make_float4(0.f, 0.f, 0.f, 0.f);
+            bool keep = false;
+            if (q < c) {
+              cj = A.xh[b0 + q];
+              const float px = cj.x + cs0, py = cj.y + cs1, pz = cj.z + cs2;   // exact (2^-12 grid)
+              const float ux = fmaxf(fmaxf(bb_lo.x - px, px - bb_hi.x), 0.f),
+                          uy = fmaxf(fmaxf(bb_lo.y - py, py - bb_hi.y), 0.f),
+                          uz = fmaxf(fmaxf(bb_lo.z - pz, pz - bb_hi.z), 0.f);
+              keep = fmaf(ux, ux, fmaf(uy, uy, uz * uz)) < P.rlist_out2f;
+            }
+            const unsigned km = __ballot_sync(0xffffffffu, keep);
+            nc = __popc(km);
+            if (keep) { cj.w = __int_as_float(lane); sh_h[__popc(km & lanes_below)] = cj; }
           }
           __syncwarp();
-          int nc = min(32, c - base);
           if (in) {
             const uint32_t cbits = (uint32_t)code << kJBits;
             const int j0 = (int)(b0 - seg) + base;                            // local index of candidate 0
@@ -365,46 +402,50 @@ __device__ void build_warp(int s, int wi, const SysArrays& S, const SlotArrays& 
               // those in a thin shell around the list radius, which take the
               // double-float test; four tests per round, straight-line unless
               // one of them is undecided
-              auto rh2 = [&](int tq) {
-                const float4 xj = sh_h[tq];
+              // staged entry t: hi position, index in the chunk in w
+              auto rh2 = [&](const float4 xj) {
                 const float h0 = xj.x + a0, h1 = xj.y + a1, h2 = xj.z + a2;
                 return fmaf(h0, h0, fmaf(h1, h1, h2 * h2));
               };
-              auto exact = [&](int tq) {
-                const float4 xj = sh_h[tq];
-                const float4 lj = A.xl[b0 + base + tq];
+              auto exact = [&](const float4 xj, int o) {
+                const float4 lj = A.xl[b0 + base + o];
                 const float d0 = (xj.x + a0) + (lj.x + e0), d1 = (xj.y + a1) + (lj.y + e1),
                             d2 = (xj.z + a2) + (lj.z + e2);
                 return d0 * d0 + d1 * d1 + d2 * d2 < P.rlist2f;
               };
               const float in2 = P.rlist_in2f, out2 = P.rlist_out2f;
-              int tq = 0;
-              for (; tq + 4 <= nc; tq += 4) {
-                const float r0 = rh2(tq), r1 = rh2(tq + 1), r2 = rh2(tq + 2), r3 = rh2(tq + 3);
+              int t = 0;
+              for (; t + 4 <= nc; t += 4) {
+                const float4 x0 = sh_h[t], x1 = sh_h[t + 1], x2 = sh_h[t + 2], x3 = sh_h[t + 3];
+                const int o0 = __float_as_int(x0.w), o1 = __float_as_int(x1.w), o2 = __float_as_int(x2.w),
+                          o3 = __float_as_int(x3.w);
+                const float r0 = rh2(x0), r1 = rh2(x1), r2 = rh2(x2), r3 = rh2(x3);
                 bool h0 = r0 < in2, h1 = r1 < in2, h2 = r2 < in2, h3 = r3 < in2;
                 const bool u0 = !h0 && r0 <= out2, u1 = !h1 && r1 <= out2, u2 = !h2 && r2 <= out2,
                            u3 = !h3 && r3 <= out2;
                 if (u0 | u1 | u2 | u3) {
-                  if (u0) h0 = exact(tq);
-                  if (u1) h1 = exact(tq + 1);
-                  if (u2) h2 = exact(tq + 2);
-                  if (u3) h3 = exact(tq + 3);
+                  if (u0) h0 = exact(x0, o0);
+                  if (u1) h1 = exact(x1, o1);
+                  if (u2) h2 = exact(x2, o2);
+                  if (u3) h3 = exact(x3, o3);
                 }
-                h0 = h0 && tq != self; h1 = h1 && tq + 1 != self;
-                h2 = h2 && tq + 2 != self; h3 = h3 && tq + 3 != self;
+                h0 = h0 && o0 != self; h1 = h1 && o1 != self;
+                h2 = h2 && o2 != self; h3 = h3 && o3 != self;
                 const int c0 = cnt, c1 = c0 + h0, c2 = c1 + h1, c3 = c2 + h2;
                 cnt = c3 + h3;
                 uint32_t* out = A.nbr + k;
-                if (h0 && c0 < max_nbrs) out[c0 * stride] = (uint32_t)(j0 + tq) | cbits;
-                if (h1 && c1 < max_nbrs) out[c1 * stride] = (uint32_t)(j0 + tq + 1) | cbits;
-                if (h2 && c2 < max_nbrs) out[c2 * stride] = (uint32_t)(j0 + tq + 2) | cbits;
-                if (h3 && c3 < max_nbrs) out[c3 * stride] = (uint32_t)(j0 + tq + 3) | cbits;
+                if (h0 && c0 < max_nbrs) out[c0 * stride] = (uint32_t)(j0 + o0) | cbits;
+                if (h1 && c1 < max_nbrs) out[c1 * stride] = (uint32_t)(j0 + o1) | cbits;
+                if (h2 && c2 < max_nbrs) out[c2 * stride] = (uint32_t)(j0 + o2) | cbits;
+                if (h3 && c3 < max_nbrs) out[c3 * stride] = (uint32_t)(j0 + o3) | cbits;
               }
-              for (; tq < nc; tq++) {
-                const float r = rh2(tq);
+              for (; t < nc; t++) {
+                const float4 xj = sh_h[t];
+                const int o = __float_as_int(xj.w);
+                const float r = rh2(xj);
                 bool h = r < in2;
-                if (!h && r <= out2) h = exact(tq);
-                append(h && tq != self, tq);
+                if (!h && r <= out2) h = exact(xj, o);
+                append(h && o != self, o);
               }
             }
           }
