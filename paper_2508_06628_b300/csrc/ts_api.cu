@@ -539,20 +539,22 @@ void relist(ts_batch* b, cudaStream_t st, bool move_fire) {
   relist_finish(b, st, false);
 }
 
-// Re-listing pass and pair forces with the list build off the critical
-// path.  The flagged systems are re-sorted first (a short launch with few
-// CTAs, which needs most of an SM's registers per CTA); then the systems that
-// keep their lists get their forces on `st` while the flagged ones are
-// re-listed and get theirs on the side stream (highest priority, so that its
-// latency-bound kernels are dispatched ahead of the pair kernel's pending
-// CTAs).  The two halves touch disjoint systems.  Returns false (nothing
-// issued) when the overlap is off or `st` is the legacy default stream.
+// Re-listing pass and pair forces with the re-listing off the critical path.
+// The systems that keep their lists get their forces on `st` while the
+// flagged ones are re-sorted, re-listed and get theirs on the side stream
+// (highest priority, so that its latency-bound kernels are dispatched ahead
+// of the pair kernel's pending CTAs).  The two halves touch disjoint systems:
+// the sort moves only flagged systems' slots, and a pair CTA that stages a
+// flagged neighbour system's positions while they move never reads them.  In
+// a step that re-lists nothing the side stream's launches find no work, and
+// they overlap the pair forces.  Returns false (nothing issued) when the
+// overlap is off or `st` is the legacy default stream.
 bool relist_pair_overlapped(ts_batch* b, cudaStream_t st, bool move_fire, bool ew, bool inner) {
   if (!b->overlap_relist || !b->side || st == nullptr) return false;
-  relist_sort(b, st, move_fire, 0);
   if (!cuda_ok(b, cudaEventRecord(b->ev_fork, st), "event record") ||
       !cuda_ok(b, cudaStreamWaitEvent(b->side, b->ev_fork, 0), "stream wait"))
     return false;
+  relist_sort(b, b->side, move_fire, b->prio_hi);
   relist_build(b, b->side, b->prio_hi);
   pair(b, b->side, ew, kPairRelisted, b->prio_hi, inner);
   cuda_ok(b, cudaEventRecord(b->ev_join, b->side), "event record");
