@@ -333,9 +333,13 @@ __device__ void build_warp(int s, int wi, const SysArrays& S, const SlotArrays& 
       }
     }
     const int ncb = min(32, ncell - cb);
+    // coordinates of cell cb, then stepped in (z, y, x) order
+    int cx = x0 + cb % nx, cy = y0 + (cb / nx) % ny, cz = z0 + cb / (nx * ny);
     for (int tc = 0; tc < ncb; tc++) {
-      int ci = cb + tc;
-      int cx = x0 + ci % nx, cy = y0 + (ci / nx) % ny, cz = z0 + ci / (nx * ny);
+      if (tc > 0 && ++cx > x1) {
+        cx = x0;
+        if (++cy > y1) { cy = y0; ++cz; }
+      }
       bool in = valid && abs(cz - kz) <= m2 && abs(cy - ky) <= m1 && abs(cx - kx) <= m0;
       int code = __shfl_sync(0xffffffffu, my_code, tc);
       int64_t b0 = seg + __shfl_sync(0xffffffffu, my_start, tc);
@@ -361,6 +365,7 @@ __device__ void build_warp(int s, int wi, const SysArrays& S, const SlotArrays& 
         for (int base = 0; base < c; base += 32) {
           int q = base + lane;
           int nc = min(32, c - base);
+          unsigned km = 0;   // staged candidates kept by the box test (bit = index in the chunk)
           if constexpr (F64) {
             if (q < c) { for (int cc = 0; cc < 3; cc++) sh_d[lane][cc] = A.xd[3 * (b0 + q) + cc]; }
           } else {
@@ -376,7 +381,7 @@ __device__ void build_warp(int s, int wi, const SysArrays& S, const SlotArrays& 
                           uz = fmaxf(fmaxf(bb_lo.z - pz, pz - bb_hi.z), 0.f);
               keep = fmaf(ux, ux, fmaf(uy, uy, uz * uz)) < P.rlist_out2f;
             }
-            const unsigned km = __ballot_sync(0xffffffffu, keep);
+            km = __ballot_sync(0xffffffffu, keep);
             nc = __popc(km);
             if (keep) { cj.w = __int_as_float(lane); sh_h[__popc(km & lanes_below)] = cj; }
           }
@@ -414,38 +419,29 @@ __device__ void build_warp(int s, int wi, const SysArrays& S, const SlotArrays& 
                 return d0 * d0 + d1 * d1 + d2 * d2 < P.rlist2f;
               };
               const float in2 = P.rlist_in2f, out2 = P.rlist_out2f;
-              int t = 0;
-              for (; t + 4 <= nc; t += 4) {
-                const float4 x0 = sh_h[t], x1 = sh_h[t + 1], x2 = sh_h[t + 2], x3 = sh_h[t + 3];
-                const int o0 = __float_as_int(x0.w), o1 = __float_as_int(x1.w), o2 = __float_as_int(x2.w),
-                          o3 = __float_as_int(x3.w);
-                const float r0 = rh2(x0), r1 = rh2(x1), r2 = rh2(x2), r3 = rh2(x3);
-                bool h0 = r0 < in2, h1 = r1 < in2, h2 = r2 < in2, h3 = r3 < in2;
-                const bool u0 = !h0 && r0 <= out2, u1 = !h1 && r1 <= out2, u2 = !h2 && r2 <= out2,
-                           u3 = !h3 && r3 <= out2;
-                if (u0 | u1 | u2 | u3) {
-                  if (u0) h0 = exact(x0, o0);
-                  if (u1) h1 = exact(x1, o1);
-                  if (u2) h2 = exact(x2, o2);
-                  if (u3) h3 = exact(x3, o3);
-                }
-                h0 = h0 && o0 != self; h1 = h1 && o1 != self;
-                h2 = h2 && o2 != self; h3 = h3 && o3 != self;
-                const int c0 = cnt, c1 = c0 + h0, c2 = c1 + h1, c3 = c2 + h2;
-                cnt = c3 + h3;
-                uint32_t* out = A.nbr + k;
-                if (h0 && c0 < max_nbrs) out[c0 * stride] = (uint32_t)(j0 + o0) | cbits;
-                if (h1 && c1 < max_nbrs) out[c1 * stride] = (uint32_t)(j0 + o1) | cbits;
-                if (h2 && c2 < max_nbrs) out[c2 * stride] = (uint32_t)(j0 + o2) | cbits;
-                if (h3 && c3 < max_nbrs) out[c3 * stride] = (uint32_t)(j0 + o3) | cbits;
+              // hits as a bit mask over the staged entries (the rare entries in
+              // the 1e-3 A shell take the exact test), then appended in order
+              unsigned hm = 0, um = 0;
+#pragma unroll 4
+              for (int t = 0; t < nc; t++) {
+                const float r = rh2(sh_h[t]);
+                hm |= (unsigned)(r < in2) << t;
+                um |= (unsigned)(r >= in2 && r <= out2) << t;
               }
-              for (; t < nc; t++) {
+              while (um) {
+                const int t = __ffs(um) - 1;
+                um &= um - 1;
                 const float4 xj = sh_h[t];
-                const int o = __float_as_int(xj.w);
-                const float r = rh2(xj);
-                bool h = r < in2;
-                if (!h && r <= out2) h = exact(xj, o);
-                append(h && o != self, o);
+                if (exact(xj, __float_as_int(xj.w))) hm |= 1u << t;
+              }
+              if (self >= 0 && self < 32) hm &= ~(1u << __popc(km & ((1u << self) - 1u)));   // the atom itself
+              uint32_t* out = A.nbr + k;
+              while (hm) {
+                const int t = __ffs(hm) - 1;
+                hm &= hm - 1;
+                const int o = __float_as_int(sh_h[t].w);
+                if (cnt < max_nbrs) out[(int64_t)cnt * stride] = (uint32_t)(j0 + o) | cbits;
+                cnt++;
               }
             }
           }
