@@ -530,8 +530,7 @@ void relist_lists(ts_batch* b, cudaStream_t st, bool move_fire, int prio) {
 // launches ran in inner-list mode and refreshed every flagged system.
 void relist_finish(ts_batch* b, cudaStream_t st, bool md_pass) {
   k_after_relist<<<(b->B + 127) / 128, 128, 0, st>>>(b->B, b->S, b->d_counters, md_pass ? 1 : 0);
-  k_clear_any<<<1, 1, 0, st>>>(b->S);
-  b->launches += 2;
+  b->launches++;
 }
 
 void relist(ts_batch* b, cudaStream_t st, bool move_fire) {

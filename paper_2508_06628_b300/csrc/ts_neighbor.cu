@@ -466,27 +466,33 @@ __global__ void k_copy_back(int64_t Npad, SysArrays S, SlotArrays A, int move_fi
 // per-system flag bookkeeping after a listing: the re-listed systems' forces are stale
 __global__ void k_after_relist(int32_t B, SysArrays S, int64_t* counters, int md_pass) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= B) return;
-  // inner lists: an MD pass's pair launches refreshed every flagged or
-  // re-listed system (counted in counters[1]); after any other pass a
-  // re-listed system's inner list is stale until the next MD pass
-  if (md_pass) {
-    if (S.prune[s] || need_relist(S, s)) atomicAdd((unsigned long long*)(counters + 1), 1ull);
-    S.prune[s] = 0;
-  } else if (need_relist(S, s)) {
-    S.prune[s] = 1;
+  if (s < B) {
+    // inner lists: an MD pass's pair launches refreshed every flagged or
+    // re-listed system (counted in counters[1]); after any other pass a
+    // re-listed system's inner list is stale until the next MD pass
+    const bool re = need_relist(S, s);
+    if (md_pass) {
+      if (S.prune[s] || re) atomicAdd((unsigned long long*)(counters + 1), 1ull);
+      S.prune[s] = 0;
+    } else if (re) {
+      S.prune[s] = 1;
+    }
+    if (re) {
+      S.dirty[s] = 1;
+      S.relist[s] = 0;
+      S.soon[s] = 0;
+      for (int q = 0; q < 9; q++) S.href[9 * s + q] = S.h[9 * s + q];
+      atomicAdd((unsigned long long*)counters, 1ull);
+    }
   }
-  if (need_relist(S, s)) {
-    S.dirty[s] = 1;
-    S.relist[s] = 0;
-    S.soon[s] = 0;
-    for (int q = 0; q < 9; q++) S.href[9 * s + q] = S.h[9 * s + q];
-    atomicAdd((unsigned long long*)counters, 1ull);
+  // end of the pass: the last block to finish clears the batch-wide flag,
+  // once every block has read it (counters[3]: a wrapping block counter)
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicInc((unsigned*)(counters + 3), gridDim.x - 1) == gridDim.x - 1) S.any[0] = 0;
   }
 }
-
-// end of a re-listing pass: no system is forced any more
-__global__ void k_clear_any(SysArrays S) { S.any[0] = 0; }
 
 // list export in caller order (j as caller index, image n per axis)
 __global__ void k_export_list(int64_t Npad, SysArrays S, SlotArrays A, int32_t max_nbrs, int64_t stride,

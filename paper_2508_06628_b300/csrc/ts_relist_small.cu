@@ -256,7 +256,12 @@ k_relist_small(int32_t B, SysArrays S, SlotArrays A, int64_t stride, int move_fi
   }
 }
 
-__device__ __forceinline__ int floor_div(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+// floor(a / b) for b > 0; stencil coordinates lie within a cell width or
+// two of the cell, so the common cases take no integer division
+__device__ __forceinline__ int floor_div(int a, int b) {
+  if (a >= 0) return a < b ? 0 : (a < 2 * b ? 1 : a / b);
+  return a >= -b ? -1 : -((-a + b - 1) / b);
+}
 
 // One warp: the lists of the 32 slots of warp `wi` of system `s` (a flagged
 // system).  sh_h / sh_d: this warp's staging area.
