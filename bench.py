@@ -33,7 +33,7 @@ BYTES_PER_ATOM = 32         # read own position, write own force, per atom-step
 # DRAM bytes (read + write) of one forces-only k_pair_small launch (inner lists) on ragged-mix-512, from one ncu
 # capture (profiles/k_pair_small_ragged_mix_512.md); reported only while the kernel's sources
 # (ts_pair.cu, then ts_internal.cuh) hash to the value recorded with the capture
-PAIR_TRAFFIC = {"bytes": 49_016_576 + 146_944, "source_sha1": "6d758aa10d21075b5dcb2485497745e1fce19ad9"}
+PAIR_TRAFFIC = {"bytes": 49_635_840 + 162_304, "source_sha1": "22fba4e9418d60c8ff584cc779a7f22f27286841"}
 
 
 def pair_traffic():
@@ -227,8 +227,10 @@ def per_system_loop(hb, pots, dev, args, n_sample=32, steps=3):
 
 
 def e2e(b, s, hb, dev, stream, args, dt, gamma, inner):
-    """Same metric through the public API with pinned host buffers: every call
-    copies the state in (H2D) and reads the per-system energies back (D2H)."""
+    """Same metric through the public API with the state held on the host in
+    pinned buffers: every call copies positions and velocities in (H2D), runs
+    its steps and copies the new positions, velocities and per-system energies
+    back (D2H), so the trajectory continues from call to call."""
     import torch
     from paper_2508_06628_b300 import ts
     pos_h = torch.from_numpy(np.ascontiguousarray(hb.pos)).pin_memory()
@@ -242,22 +244,27 @@ def e2e(b, s, hb, dev, stream, args, dt, gamma, inner):
         s.pos.copy_(pos_h, non_blocking=True)
         s.vel.copy_(vel_h, non_blocking=True)
         b.md_step(s, inner, dt, kind=ts.TS_LANGEVIN, gamma=gamma, seed=9, stream=stream)   # warm (re-list)
+        pos_h.copy_(s.pos, non_blocking=True)
+        vel_h.copy_(s.vel, non_blocking=True)
         stream.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for c in range(ncalls):
             s.pos.copy_(pos_h, non_blocking=True)
             s.vel.copy_(vel_h, non_blocking=True)
-            b.md_step(s, inner, dt, kind=ts.TS_LANGEVIN, gamma=gamma, seed=9, step0=c * inner, E=E, KE=KE,
+            b.md_step(s, inner, dt, kind=ts.TS_LANGEVIN, gamma=gamma, seed=9, step0=(c + 1) * inner, E=E, KE=KE,
                       stream=stream)
+            pos_h.copy_(s.pos, non_blocking=True)
+            vel_h.copy_(s.vel, non_blocking=True)
             E_h.copy_(E, non_blocking=True)
             KE_h.copy_(KE, non_blocking=True)
         e1.record(stream)
         stream.synchronize()
     ms = e0.elapsed_time(e1)
     return {"value": hb.n_atoms * ncalls * inner / (ms / 1e3), "unit": UNIT,
-            "h2d_bytes_per_step": int(2 * hb.n_atoms * 24 / inner), "d2h_bytes_per_step": int(2 * hb.n_systems * 8 / inner),
-            "how": f"per call of {inner} steps: H2D pos+vel from pinned host, D2H energies"}
+            "h2d_bytes_per_step": int(2 * hb.n_atoms * 24 / inner),
+            "d2h_bytes_per_step": int((2 * hb.n_atoms * 24 + 2 * hb.n_systems * 8) / inner),
+            "how": f"per call of {inner} steps: H2D pos+vel from pinned host, D2H pos+vel+energies"}
 
 
 def cpu_baseline(hb, budget_s=15.0):

@@ -307,15 +307,15 @@ def bin_pack(sizes, capacity):
 
 
 def default_skins(pots):
-    """Skin per potential, from a step-time sweep on the 512-system ragged batch at 300 K: 1.0 A for LJ
-    argon, 0.5 A for Morse Cu, 0.9 sigma for soft spheres (light, stiff particles whose thermal
+    """Skin per potential, from a step-time sweep on the 512-system ragged batch at 300 K: 1.1 A for LJ
+    argon, 0.55 A for Morse Cu, 1.0 sigma for soft spheres (light, stiff particles whose thermal
     excursions would otherwise force a re-listing every few steps), 0.3 sigma for reduced-unit LJ."""
     out = []
     for d in pots:
         if d["kind"] == 2:
-            out.append(0.9 * d["p"][0])
+            out.append(1.0 * d["p"][0])
         elif d["kind"] == 0:
-            out.append(0.3 * d["p"][0] if d["p"][0] < 2 else 1.0)
+            out.append(0.3 * d["p"][0] if d["p"][0] < 2 else 1.1)
         else:
-            out.append(0.5)
+            out.append(0.55)
     return out
