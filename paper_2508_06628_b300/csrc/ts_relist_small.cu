@@ -375,7 +375,7 @@ __device__ void build_warp(int s, int wi, const SysArrays& S, const SlotArrays& 
             if (q < c) { for (int cc = 0; cc < 3; cc++) sh_d[lane][cc] = A.xd[3 * (b0 + q) + cc]; }
           } else {
             // stage the candidates near the warp's box, in order, with their
-            // index in the chunk in w (lo parts only for the rare undecided tests)
+            // list entry in w (lo parts only for the rare undecided tests)
             float4 cj = make_float4(0.f, 0.f, 0.f, 0.f);
             bool keep = false;
             if (q < c) {
@@ -388,7 +388,10 @@ __device__ void build_warp(int s, int wi, const SysArrays& S, const SlotArrays& 
             }
             km = __ballot_sync(0xffffffffu, keep);
             nc = __popc(km);
-            if (keep) { cj.w = __int_as_float(lane); sh_h[__popc(km & lanes_below)] = cj; }
+            if (keep) {
+              cj.w = __uint_as_float((uint32_t)(b0 - seg + q) | ((uint32_t)code << kJBits));
+              sh_h[__popc(km & lanes_below)] = cj;
+            }
           }
           __syncwarp();
           if (in) {
@@ -417,8 +420,8 @@ __device__ void build_warp(int s, int wi, const SysArrays& S, const SlotArrays& 
                 const float h0 = xj.x + a0, h1 = xj.y + a1, h2 = xj.z + a2;
                 return fmaf(h0, h0, fmaf(h1, h1, h2 * h2));
               };
-              auto exact = [&](const float4 xj, int o) {
-                const float4 lj = A.xl[b0 + base + o];
+              auto exact = [&](const float4 xj) {
+                const float4 lj = A.xl[seg + (__float_as_uint(xj.w) & kJMask)];
                 const float d0 = (xj.x + a0) + (lj.x + e0), d1 = (xj.y + a1) + (lj.y + e1),
                             d2 = (xj.z + a2) + (lj.z + e2);
                 return d0 * d0 + d1 * d1 + d2 * d2 < P.rlist2f;
@@ -426,28 +429,27 @@ __device__ void build_warp(int s, int wi, const SysArrays& S, const SlotArrays& 
               const float in2 = P.rlist_in2f, out2 = P.rlist_out2f;
               // hits as a bit mask over the staged entries (the rare entries in
               // the 1e-3 A shell take the exact test), then appended in order
-              unsigned hm = 0, um = 0;
+              unsigned hm = 0, ho = 0;
 #pragma unroll 4
               for (int t = 0; t < nc; t++) {
                 const float r = rh2(sh_h[t]);
                 hm |= (unsigned)(r < in2) << t;
-                um |= (unsigned)(r >= in2 && r <= out2) << t;
+                ho |= (unsigned)(r <= out2) << t;
               }
-              while (um) {
+              for (unsigned um = ho & ~hm; um; um &= um - 1) {   // the shell
                 const int t = __ffs(um) - 1;
-                um &= um - 1;
-                const float4 xj = sh_h[t];
-                if (exact(xj, __float_as_int(xj.w))) hm |= 1u << t;
+                if (exact(sh_h[t])) hm |= 1u << t;
               }
               if (self >= 0 && self < 32) hm &= ~(1u << __popc(km & ((1u << self) - 1u)));   // the atom itself
-              uint32_t* out = A.nbr + k;
-              while (hm) {
-                const int t = __ffs(hm) - 1;
-                hm &= hm - 1;
-                const int o = __float_as_int(sh_h[t].w);
-                if (cnt < max_nbrs) out[(int64_t)cnt * stride] = (uint32_t)(j0 + o) | cbits;
-                cnt++;
+              const int nh = __popc(hm);
+              if (cnt + nh <= max_nbrs) {
+                uint32_t* out = A.nbr + k + (int64_t)cnt * stride;
+                for (; hm; hm &= hm - 1, out += stride) *out = __float_as_uint(sh_h[__ffs(hm) - 1].w);
+              } else {
+                for (int c2 = cnt; hm; hm &= hm - 1, c2++)
+                  if (c2 < max_nbrs) A.nbr[(int64_t)c2 * stride + k] = __float_as_uint(sh_h[__ffs(hm) - 1].w);
               }
+              cnt += nh;
             }
           }
           __syncwarp();
