@@ -115,7 +115,7 @@ __device__ void relist_table(int32_t B, const SysArrays& S, SmallSmem& sm, int32
 }
 
 template <bool F64>
-__global__ void __launch_bounds__(kSmallThreads, 1)
+__global__ void __launch_bounds__(kSmallThreads, 2)   // at most 64 registers: fits beside pair CTAs
 k_relist_small(int32_t B, SysArrays S, SlotArrays A, int64_t stride, int move_fire, int32_t* cstart, int32_t* count,
                const DevPot* __restrict__ pots, int32_t max_nbrs, int32_t* err, int32_t* tab_sys, int32_t* tab_base,
                int32_t* tab_base_a, int32_t* tab_n) {
