@@ -59,7 +59,7 @@ size_t scratch_bytes(int64_t Ncap, int64_t Bcap, int64_t Ccap, int32_t max_nbrs,
                            2 * 16 /*g*/);
   per_slot += (f64 ? 3 * 8 : 2 * 16) /*prune reference*/ + 4 /*nn_in*/ + (size_t)max_nbrs * 4 /*inner list*/;
   per_slot += 4 * 4 /*perm sys bin nn*/ + 3 * 4 /*tmp i*/ + (size_t)max_nbrs * 4 + 8 * 8 / 32 /*partials*/ + 4 / 32 /*warp_sys*/ + 16 / 32 /*pair work items*/;
-  size_t per_sys = 8 * 4 + 9 * 8 * 3 + 9 * 4 + 6 * 4 + 4 * 4 + 8 + 12 /*list-build work table*/ + 8 /*piston*/ +
+  size_t per_sys = 8 * 4 + 9 * 8 * 3 + 9 * 4 + 6 * 4 + 4 * 4 + 8 + 12 /*list-build work table*/ + 8 /*piston*/ + 4 /*geometry state*/ +
                    (size_t)kNCodes * (32 + 24 + 16);
   return per_slot * (size_t)Ncap + per_sys * (size_t)Bcap + (size_t)Ccap * 8;
 }
@@ -147,7 +147,7 @@ extern "C" ts_status ts_batch_create(const ts_batch_config* cfg, const ts_potent
        alloc(b, S.uid, B) && alloc(b, S.bin_off, B) && alloc(b, S.bin_cap, B) && alloc(b, S.warp_start, B) &&
        alloc(b, S.warp_end, B) && alloc(b, S.h, 9 * B) && alloc(b, S.hinv, 9 * B) && alloc(b, S.hinvf, 9 * B) && alloc(b, S.href, 9 * B) &&
        alloc(b, S.nb, 3 * B) && alloc(b, S.reach, 3 * B) && alloc(b, S.pmask, B) && alloc(b, S.relist, B) && alloc(b, S.prune, B) && alloc(b, S.dirty, B) &&
-       alloc(b, S.soon, B) && alloc(b, S.any, 1) &&
+       alloc(b, S.soon, B) && alloc(b, S.any, 1) && alloc(b, S.geom, B) &&
        alloc(b, S.kT, B) && alloc(b, S.shift, 2 * B * kNCodes) && alloc(b, S.shiftd, 3 * B * kNCodes) && alloc(b, S.shiftq, B * kNCodes);
   ok = ok && alloc(b, A.perm, N) && alloc(b, A.sys, N) && alloc(b, A.bin, N) && alloc(b, A.nn, N) &&
        alloc(b, A.nbr, (size_t)b->max_nbrs * N) && alloc(b, A.nbr_in, (size_t)b->max_nbrs * N) && alloc(b, A.nn_in, N) && alloc(b, A.tmp_i0, N) && alloc(b, A.tmp_i1, N) &&
@@ -442,6 +442,7 @@ ts_status derive_topology(ts_batch* b, const ts_state* s, cudaStream_t st) {
        cuda_ok(b, cudaMemcpyAsync(S.dirty, ones.data(), 4 * B, cudaMemcpyHostToDevice, st), "h2d") &&
        cuda_ok(b, cudaMemsetAsync(S.soon, 0, 4 * B, st), "memset") && cuda_ok(b, cudaMemsetAsync(S.any, 0, 4, st), "memset") &&
        cuda_ok(b, cudaMemsetAsync(S.prune, 0, 4 * B, st), "memset") &&
+       cuda_ok(b, cudaMemsetAsync(S.geom, 0, 4 * B, st), "memset") &&
        cuda_ok(b, cudaMemsetAsync(b->d_count, 0, 4 * b->Ccap, st), "memset") &&
        cuda_ok(b, cudaStreamSynchronize(st), "sync");
   if (!ok) return TS_ERR_CUDA;

@@ -107,6 +107,7 @@ struct SysArrays {
                           // moved half the inner skin since the last refresh, or the list is stale)
   int32_t* soon;          // atoms past kSoon * skin/2: re-list along with any forced pass
   int32_t* any;           // [1] some system must re-list in this pass
+  int32_t* geom;          // bit 0: geometry and image tables current for h and pmask; bit 1: just recomputed
   int32_t* dirty;         // forces stale for this system
   double* kT;             // per-system kT (MD)
 };

@@ -175,7 +175,8 @@ __device__ inline double det3(const double* h) {
 // the edge bins (bins are at least r_list wide, so every pair within r_list
 // still lies in neighbouring bins), and the stencil stops at the edges.
 __global__ void k_geometry(int32_t B, SysArrays S, const double* __restrict__ cell, const uint8_t* __restrict__ pbc,
-                           const DevPot* __restrict__ pots, int32_t* err, int cell_check, int keep_pmask = 0) {
+                           const DevPot* __restrict__ pots, int32_t* err, int cell_check, int keep_pmask = 0,
+                           int force = 0) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= B) return;
   double h[9];
@@ -186,8 +187,17 @@ __global__ void k_geometry(int32_t B, SysArrays S, const double* __restrict__ ce
     for (int q = 0; q < 9; q++) moved |= h[q] != ref[q];
     if (moved) { S.relist[s] = 1; S.any[0] = 1; }
   }
-  for (int q = 0; q < 9; q++) S.h[9 * s + q] = h[q];
   const int pm = keep_pmask ? S.pmask[s] : pbc ? ((pbc[3 * s] ? 1 : 0) | (pbc[3 * s + 1] ? 2 : 0) | (pbc[3 * s + 2] ? 4 : 0)) : 7;
+  // the same cell and periodicity as at the last (error-free) computation:
+  // geometry and image tables stand (S.geom bit 0: valid, bit 1: recomputed
+  // by this launch, so k_shift_table rebuilds the tables)
+  if (!force && (S.geom[s] & 1) && pm == S.pmask[s]) {
+    bool same = true;
+    for (int q = 0; q < 9; q++) same &= h[q] == S.h[9 * s + q];
+    if (same) { S.geom[s] = 1; return; }
+  }
+  S.geom[s] = 2;
+  for (int q = 0; q < 9; q++) S.h[9 * s + q] = h[q];
   S.pmask[s] = pm;
   double d = det3(h);
   if (!(fabs(d) > 0) || !isfinite(d)) { atomicOr(err, kErrNonFinite); return; }
@@ -209,6 +219,7 @@ __global__ void k_geometry(int32_t B, SysArrays S, const double* __restrict__ ce
   }
   double rl = pots[S.pot[s]].rlist;
   int nb[3], m[3];
+  bool bad = false;
   for (int a = 0; a < 3; a++) {
     double f = floor(w[a] / rl);
     nb[a] = f < 1.0 ? 1 : (f > 1024.0 ? 1024 : (int)f);
@@ -223,12 +234,13 @@ __global__ void k_geometry(int32_t B, SysArrays S, const double* __restrict__ ce
     m[a] = (int)ceil(rl * nb[a] / w[a]);
     if (m[a] < 1) m[a] = 1;
     if (!(pm >> a & 1)) m[a] = m[a] < nb[a] ? m[a] : nb[a];   // open axis: no images, the stencil stops at the edges
-    else if (m[a] > kMaxReach) { m[a] = kMaxReach; atomicOr(err, kErrUnsupported); }
+    else if (m[a] > kMaxReach) { m[a] = kMaxReach; atomicOr(err, kErrUnsupported); bad = true; }
     S.nb[3 * s + a] = nb[a];
     S.reach[3 * s + a] = m[a];
   }
   // positions wrapped into the cell plus the skin must stay inside the hi/lo range
-  if (ext + 2.0 * rl > 0.5 * kMaxCoord) atomicOr(err, kErrUnsupported);
+  if (ext + 2.0 * rl > 0.5 * kMaxCoord) { atomicOr(err, kErrUnsupported); bad = true; }
+  S.geom[s] = bad ? 2 : 3;   // an error is raised again by every call until the cell changes
 }
 
 // Image shift table S = n h for every image code, stored hi/lo (mixed) and FP64.
@@ -236,6 +248,7 @@ __global__ void k_shift_table(int32_t B, SysArrays S) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= (int64_t)B * kNCodes) return;
   int s = (int)(t / kNCodes), code = (int)(t % kNCodes);
+  if (!(S.geom[s] & 2)) return;   // cell unchanged: the tables stand
   int nx = code % kImgSide - kMaxReach, ny = (code / kImgSide) % kImgSide - kMaxReach,
       nz = code / (kImgSide * kImgSide) - kMaxReach;
   const double* h = S.h + 9 * s;
