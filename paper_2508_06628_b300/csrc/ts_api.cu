@@ -477,14 +477,10 @@ ts_status prologue(ts_batch* b, ts_state* s, cudaStream_t st, bool import_vel, b
   k_geometry<<<(B + 127) / 128, 128, 0, st>>>(B, b->S, s->cell, s->pbc, b->d_pots, b->d_err, cell_check);
   k_shift_table<<<(int)(((int64_t)B * kNCodes + 255) / 256), 256, 0, st>>>(B, b->S);
   int g = grid_for(b->Npad, 256);
-  if (b->f64) k_import_pos<true><<<g, 256, 0, st>>>(b->Npad, b->S, b->A, s->pos, b->d_pots, !b->first_import, b->d_err);
-  else k_import_pos<false><<<g, 256, 0, st>>>(b->Npad, b->S, b->A, s->pos, b->d_pots, !b->first_import, b->d_err);
+  const int wv = import_vel ? 1 : 0;   // velocities in the same pass
+  if (b->f64) k_import_pos<true><<<g, 256, 0, st>>>(b->Npad, b->S, b->A, s->pos, b->d_pots, !b->first_import, b->d_err, wv, s->vel, s->mass);
+  else k_import_pos<false><<<g, 256, 0, st>>>(b->Npad, b->S, b->A, s->pos, b->d_pots, !b->first_import, b->d_err, wv, s->vel, s->mass);
   b->launches += 3;
-  if (import_vel) {
-    if (b->f64) k_import_vel<true><<<g, 256, 0, st>>>(b->Npad, b->A, s->vel, s->mass);
-    else k_import_vel<false><<<g, 256, 0, st>>>(b->Npad, b->A, s->vel, s->mass);
-    b->launches++;
-  }
   b->first_import = false;
   return cuda_ok(b, cudaGetLastError(), "prologue launch") ? TS_OK : TS_ERR_CUDA;
 }

@@ -50,11 +50,34 @@ __global__ void k_init_slots(int32_t B, SysArrays S, SlotArrays A) {
 // caller, or FIRE, which keeps no inner list).  check_skin = 0 on the first
 // import after a topology change (everything is re-listed anyway).
 template <bool F64>
+__device__ __forceinline__ void import_vel_slot(SlotArrays& A, int64_t k, int p, const double* __restrict__ vel,
+                                                const double* __restrict__ mass) {
+  double m = mass[p];
+  double v0 = vel ? vel[3 * (int64_t)p] : 0.0, v1 = vel ? vel[3 * (int64_t)p + 1] : 0.0,
+         v2 = vel ? vel[3 * (int64_t)p + 2] : 0.0;
+  if constexpr (F64) {
+    double* vd = A.vd + 3 * k;
+    vd[0] = v0; vd[1] = v1; vd[2] = v2;
+    A.minvd[k] = 1.0 / m;
+  } else {
+    float4 h, l;
+    h.x = (float)v0; l.x = (float)(v0 - (double)h.x);
+    h.y = (float)v1; l.y = (float)(v1 - (double)h.y);
+    h.z = (float)v2; l.z = (float)(v2 - (double)h.z);
+    h.w = (float)(1.0 / m); l.w = 0.f;
+    A.vh[k] = h; A.vl[k] = l;
+  }
+}
+
+// with_vel: velocities and inverse masses too (MD calls), in the same pass
+template <bool F64>
 __global__ void k_import_pos(int64_t Npad, SysArrays S, SlotArrays A, const double* __restrict__ pos,
-                             const DevPot* __restrict__ pots, int check_skin, int32_t* err) {
+                             const DevPot* __restrict__ pots, int check_skin, int32_t* err, int with_vel = 0,
+                             const double* __restrict__ vel = nullptr, const double* __restrict__ mass = nullptr) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < Npad; k += (int64_t)gridDim.x * blockDim.x) {
     int p = A.perm[k];
     if (p < 0) continue;
+    if (with_vel) import_vel_slot<F64>(A, k, p, vel, mass);
     int s = A.sys[k];
     double x0 = pos[3 * (int64_t)p], x1 = pos[3 * (int64_t)p + 1], x2 = pos[3 * (int64_t)p + 2];
     if (!(isfinite(x0) && isfinite(x1) && isfinite(x2)) || fabs(x0) > kMaxCoord || fabs(x1) > kMaxCoord ||
@@ -71,12 +94,16 @@ __global__ void k_import_pos(int64_t Npad, SysArrays S, SlotArrays A, const doub
       const double* xr = A.xrd + 3 * k;
       dx = x0 - xr[0]; dy = x1 - xr[1]; dz = x2 - xr[2];
     } else {
-      float4 h, l;
-      split_pos(x0, h.x, l.x); split_pos(x1, h.y, l.y); split_pos(x2, h.z, l.z);
-      h.w = 0.f; l.w = 0.f;
-      float4 oh = A.xh[k], ol = A.xl[k];
-      changed = (oh.x != h.x) || (oh.y != h.y) || (oh.z != h.z) || (ol.x != l.x) || (ol.y != l.y) || (ol.z != l.z);
-      if (changed) { A.xh[k] = h; A.xl[k] = l; }
+      // unchanged when the caller's value is the one the slot holds (the
+      // double the export wrote), whatever its hi/lo split
+      float4 h = A.xh[k], l = A.xl[k];
+      changed = (x0 != (double)h.x + (double)l.x) || (x1 != (double)h.y + (double)l.y) ||
+                (x2 != (double)h.z + (double)l.z);
+      if (changed) {
+        split_pos(x0, h.x, l.x); split_pos(x1, h.y, l.y); split_pos(x2, h.z, l.z);
+        h.w = 0.f; l.w = 0.f;
+        A.xh[k] = h; A.xl[k] = l;
+      }
       float4 rh = A.xrh[k], rl = A.xrl[k];
       dx = (double)((h.x - rh.x) + (l.x - rl.x));
       dy = (double)((h.y - rh.y) + (l.y - rl.y));
@@ -102,28 +129,6 @@ __global__ void k_import_pos(int64_t Npad, SysArrays S, SlotArrays A, const doub
   }
 }
 
-template <bool F64>
-__global__ void k_import_vel(int64_t Npad, SlotArrays A, const double* __restrict__ vel, const double* __restrict__ mass) {
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < Npad; k += (int64_t)gridDim.x * blockDim.x) {
-    int p = A.perm[k];
-    if (p < 0) continue;
-    double m = mass[p];
-    double v0 = vel ? vel[3 * (int64_t)p] : 0.0, v1 = vel ? vel[3 * (int64_t)p + 1] : 0.0,
-           v2 = vel ? vel[3 * (int64_t)p + 2] : 0.0;
-    if constexpr (F64) {
-      double* vd = A.vd + 3 * k;
-      vd[0] = v0; vd[1] = v1; vd[2] = v2;
-      A.minvd[k] = 1.0 / m;
-    } else {
-      float4 h, l;
-      h.x = (float)v0; l.x = (float)(v0 - (double)h.x);
-      h.y = (float)v1; l.y = (float)(v1 - (double)h.y);
-      h.z = (float)v2; l.z = (float)(v2 - (double)h.z);
-      h.w = (float)(1.0 / m); l.w = 0.f;
-      A.vh[k] = h; A.vl[k] = l;
-    }
-  }
-}
 
 template <bool F64>
 __global__ void k_export_state(int64_t Npad, SlotArrays A, double* pos, double* vel) {
