@@ -702,8 +702,6 @@ extern "C" ts_status ts_md_step(ts_batch* b, ts_state* s, const ts_md_params* p,
     k_require_periodic<<<(b->B + 127) / 128, 128, 0, st>>>(b->B, b->S, b->d_err);
     b->launches++;
   }
-  ensure_forces(b, st);
-  if (npt) pair(b, st, true, kPairAll);   // the virial of every system for the first piston kick
   double c1 = exp(-p->gamma * p->dt);
   r = md_loop(b, st, p, n_steps, c1, E != nullptr || KE != nullptr);
   if (r != TS_OK) return r;

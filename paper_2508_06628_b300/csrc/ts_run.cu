@@ -1,9 +1,9 @@
-// ts_run.cu -- the persistent MD step loop behind ts_md_step.  The K-step
-// loop (kick/drift/noise + skin check, conditional per-system re-listing,
-// pair forces; the chain or the piston between steps under NVT-NHC and NPT)
-// is issued once into a CUDA graph per (K, parameters, stream)
-// and replayed on later calls, so the host crosses to the device once per
-// call instead of once per kernel.  Kernels read sizes and the Langevin
+// ts_run.cu -- the persistent MD step loop behind ts_md_step.  The forces at
+// the call's start and the K-step loop (kick/drift/noise + skin check,
+// conditional per-system re-listing, pair forces; the chain or the piston
+// between steps under NVT-NHC and NPT) are issued once into a CUDA graph per
+// (K, parameters, stream) and replayed on later calls, so the host crosses to
+// the device once per call instead of once per kernel.  Kernels read sizes and the Langevin
 // step counter from device memory, so one graph serves every call with the
 // same batch layout.
 #include "ts_api.h"
@@ -11,6 +11,10 @@
 namespace ts {
 
 static void md_body(ts_batch* b, cudaStream_t st, const ts_md_params* p, int n_steps, double c1, bool need_e) {
+  // forces current for every system (re-listing what the import flagged),
+  // inside the step graph so that an unchanged state costs a few empty launches
+  ensure_forces(b, st);
+  if (p->kind == TS_NPT_LANGEVIN) pair(b, st, true, kPairAll);   // the virial of every system for the first piston kick
   int g = 0;
   {
     int64_t blocks = (b->Npad + 255) / 256;
