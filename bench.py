@@ -33,7 +33,7 @@ BYTES_PER_ATOM = 32         # read own position, write own force, per atom-step
 # DRAM bytes (read + write) of one forces-only k_pair_small launch (inner lists) on ragged-mix-512, from one ncu
 # capture (profiles/k_pair_small_ragged_mix_512.md); reported only while the kernel's sources
 # (ts_pair.cu, then ts_internal.cuh) hash to the value recorded with the capture
-PAIR_TRAFFIC = {"bytes": 49_635_840 + 162_304, "source_sha1": "22fba4e9418d60c8ff584cc779a7f22f27286841"}
+PAIR_TRAFFIC = {"bytes": 49_635_328 + 164_864, "source_sha1": "82d2c4a7ca834a3b1f070cff17c93d4982c96088"}
 
 
 def pair_traffic():
