@@ -193,6 +193,9 @@ __global__ void k_geometry(int32_t B, SysArrays S, const double* __restrict__ ce
     if (moved) { S.relist[s] = 1; S.any[0] = 1; }
   }
   const int pm = keep_pmask ? S.pmask[s] : pbc ? ((pbc[3 * s] ? 1 : 0) | (pbc[3 * s + 1] ? 2 : 0) | (pbc[3 * s + 2] ? 4 : 0)) : 7;
+  // lists built with another periodicity hold images along an axis that is
+  // now open (or miss those of one now periodic): re-list
+  if (cell_check && pm != S.pmask[s]) { S.relist[s] = 1; S.any[0] = 1; }
   // the same cell and periodicity as at the last (error-free) computation:
   // geometry and image tables stand (S.geom bit 0: valid, bit 1: recomputed
   // by this launch, so k_shift_table rebuilds the tables)
