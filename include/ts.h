@@ -111,7 +111,14 @@ typedef struct {
  *   system_idx [n_atoms] i32 (non-decreasing, every system non-empty),
  *   pot_idx [n_systems] i32 (index into the batch's potentials),
  *   uid [n_systems] u32 stable system ids keying the Langevin noise (NULL =
- *   the system's index). */
+ *   the system's index).
+ * system_idx, pot_idx and uid set the batch topology (the engine's slot
+ * layout and noise keys), read when it is derived: on a batch's first call,
+ * when n_systems or n_atoms differ from the last call's, and on
+ * ts_neighbor_build with force_rebuild != 0.  A caller that changes one of
+ * them with the same counts calls ts_neighbor_build(force_rebuild = 1) first.  pos, vel, mass,
+ * cell and pbc may change freely between calls (changed cells and
+ * periodicity re-list their systems). */
 typedef struct {
   int32_t n_systems;
   int64_t n_atoms;
