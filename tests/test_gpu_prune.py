@@ -89,3 +89,28 @@ def test_cell_change_by_caller_relists(orc):
     _, Fr, _ = orc.forces(hb.offsets, s.pos.cpu().numpy(), cell, hb.pbc, hb.pot_idx, hb.pots)
     assert np.abs(F - Fr).max() <= 1e-9 * np.abs(Fr).max()
     b.close()
+
+
+def test_pruned_md_large_system_mixed(monkeypatch):
+    """A system above the shared-memory pair kernel's size (the gather kernel's
+    inner-list path, mixed precision) beside small ones: bit-identical to MD
+    from the full lists."""
+    from paper_2508_06628_b300 import workloads as W
+    rng = np.random.default_rng(7)
+    small = small_mix(114, n_systems=4, lo=32, hi=200)
+    pos, cell = W.lattice("fcc", (9, 9, 8), 5.26)                 # 2,592 argon atoms
+    pos = pos + rng.normal(0.0, 0.05, pos.shape)
+    mass = np.full(len(pos), 39.948)
+    big = dict(pos=pos, vel=W.maxwell_boltzmann(rng, mass, W.KB_EV * 300.0), mass=mass, cell=cell, pot=0,
+               kT=W.KB_EV * 300.0, uid=99)
+    systems = [big] + [dict(pos=small.pos[a:e], vel=small.vel[a:e], mass=small.mass[a:e], cell=small.cell[k],
+                            pot=int(small.pot_idx[k]), kT=W.KB_EV * 300.0, uid=k)
+                       for k, (a, e) in enumerate(zip(small.offsets[:-1], small.offsets[1:]))]
+    hb = W.concat(systems, small.pots)
+    hb.meta = dict(small.meta)
+    assert np.diff(hb.offsets).max() > 2048
+    xa, va, ra, pa = run(hb, 0, steps=100)
+    monkeypatch.setenv("TS_INNER", "1")
+    xb, vb, rb, _ = run(hb, 0, steps=100)
+    assert pa > 0 and ra == rb
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb)
