@@ -104,3 +104,33 @@ def test_npt_refuses_open_axes():
         b.poll()
     assert ei.value.status == ts.TS_ERR_UNSUPPORTED
     b.close()
+
+
+def test_npt_mixed_large_system(orc):
+    """A system above 2048 atoms (the gather pair kernel and the multi-kernel
+    re-listing) under the barostat beside small ones, mixed precision, against
+    the oracle over a short run."""
+    rng = np.random.default_rng(8)
+    small = small_mix(125, n_systems=3, lo=32, hi=200)
+    pos, cell = W.lattice("fcc", (9, 9, 8), 5.26)
+    pos = pos + rng.normal(0.0, 0.05, pos.shape)
+    mass = np.full(len(pos), 39.948)
+    big = dict(pos=pos, vel=W.maxwell_boltzmann(rng, mass, W.KB_EV * 300.0), mass=mass, cell=cell, pot=0,
+               kT=W.KB_EV * 300.0, uid=9)
+    systems = [big] + [dict(pos=small.pos[a:e], vel=small.vel[a:e], mass=small.mass[a:e], cell=small.cell[k],
+                            pot=int(small.pot_idx[k]), kT=W.KB_EV * 300.0, uid=k)
+                       for k, (a, e) in enumerate(zip(small.offsets[:-1], small.offsets[1:]))]
+    hb = W.concat(systems, small.pots)
+    hb.meta = dict(small.meta)
+    dt, gamma, tau = hb.meta["dt"], hb.meta["gamma"], 50.0 / W.T0_FS
+    kT = np.full(hb.n_systems, W.KB_EV * 300.0)
+    p_ext = 0.5 * GPA
+    x, v, out = gpu_npt(hb, 0, 1, 5, dt, gamma, tau, p_ext, kT)
+    xr, vr, hr, ver, Er, Kr, _, _ = orc.md_npt(hb.offsets, hb.pos, hb.vel, hb.mass, hb.cell, hb.pbc, hb.pot_idx,
+                                               hb.pots, dt, 5, kT, gamma, tau, p_ext, seed=7, uid=hb.uid,
+                                               use_cells=True)
+    E, K, ve, h = out[-1]
+    assert np.abs(h - hr).max() <= 1e-7 * np.abs(hr).max()
+    assert np.abs(frac_diff(x, xr, hr, hb.offsets)).max() < 1e-6
+    assert np.abs(v - vr).max() < 1e-5 * np.abs(vr).max()
+    assert np.all(np.abs(E - Er) <= 1e-6 * np.abs(Er) + 1e-6)
