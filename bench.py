@@ -18,6 +18,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -132,8 +133,8 @@ def run_ours(args, rank, world):
         import torch.distributed as dist
         dist.barrier()
     torch.cuda.synchronize()
-    clk = Clocks(os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "",
-                              f"clocks_rank{rank}.csv"))
+    # the raw clock samples go to TS_BENCH_OUT (default: the system's temporary directory)
+    clk = Clocks(os.path.join(os.environ.get("TS_BENCH_OUT", tempfile.gettempdir()), f"clocks_rank{rank}.csv"))
     with clk, torch.cuda.stream(stream):
         for c in range(ncalls):
             flush.fill_(c & 0xff)
