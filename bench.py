@@ -292,6 +292,105 @@ def cpu_baseline(hb, budget_s=15.0):
                                         f"(random, seed 0) x {steps} BAOAB step, FP64 cell-list mode"}
 
 
+FLOP_PER_PAIR_BWD = 100   # pair-force backward, per pair within rc (positions and parameters)
+
+
+def run_row_adjoint(args):
+    """the pair-force backward (gF, gE -> gradients in positions
+    and potential parameters) on the MD workload after its warm-up, timed with
+    CUDA events around whole backward calls (the call's gradient import,
+    pair-backward kernel, export and parameter reductions)."""
+    import torch
+    from paper_2508_06628_b300 import ts
+    dev = torch.device("cuda", 0)
+    hb = workload(seed=1)
+    pots = [dict(p, skin=s) for p, s in zip(hb.pots, ts.default_skins(hb.pots))]
+    b = ts.Batch(pots, hb.n_atoms, hb.n_systems, precision=ts.TS_MIXED, device=0)
+    s = ts.DeviceState.from_host(hb, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    g = torch.Generator(device=dev).manual_seed(3)
+    gF = torch.randn((hb.n_atoms, 3), dtype=torch.float64, device=dev, generator=g)
+    gE = torch.ones(hb.n_systems, dtype=torch.float64, device=dev)
+    gPos = torch.zeros_like(gF)
+    gPar = torch.zeros((len(hb.pots), 3), dtype=torch.float64, device=dev)
+    with torch.cuda.stream(stream):
+        b.neighbor_build(s, force=True, stream=stream)
+        b.md_step(s, 20, hb.meta["dt"], kind=ts.TS_LANGEVIN, gamma=hb.meta["gamma"], seed=5, stream=stream)
+        b.pair_forces(s, None, None, None, stream=stream)
+        for _ in range(args.warmup):
+            b.pair_forces_backward(s, gF, gE, None, gPos, gPar, stream=stream)
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            b.pair_forces_backward(s, gF, gE, None, gPos, gPar, stream=stream)
+        e1.record(stream)
+        stream.synchronize()
+        _, pairs, _ = b.profile_pair(s, reps=1, flush=None, stream=stream)
+    ms = e0.elapsed_time(e1) / args.steps
+    b.poll()
+    _, smmhz, _ = peaks()
+    alu_peak = N_SM * FP32_LANES_PER_SM * 2 * smmhz * 1e6 / 1e12
+    achieved = pairs * FLOP_PER_PAIR_BWD / (ms / 1e3) / 1e12
+    b.close()
+    return {"metric": "pair-force backward (positions + parameters) atom-evaluations/s", "value": hb.n_atoms / (ms / 1e3),
+            "unit": "atom-evals/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "row": "adjoint",
+            "config": {"workload": "ragged-mix-512 after 20 BAOAB steps; upstream gF ~ N(0,1), gE = 1",
+                       "n_systems": hb.n_systems, "n_atoms": hb.n_atoms},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                         "frac": achieved / alu_peak, "traffic": None, "kernel": "k_pair_bwd (whole backward call timed)",
+                         "pairs_per_launch": pairs, "flop_per_pair": FLOP_PER_PAIR_BWD}}
+
+
+def run_row_fire(args):
+    """variable-cell FIRE on 1024 systems of the relaxation
+    stream (Morse Cu FCC, 64-864 atoms, rattled and scaled), timed with CUDA
+    events around calls of 10 FIRE steps."""
+    import torch
+    from paper_2508_06628_b300 import ts, workloads as W
+    dev = torch.device("cuda", 0)
+    hb = W.fire_stream(seed=2, n_systems=8192).subset(list(range(1024)))
+    pots = [dict(p, skin=s) for p, s in zip(hb.pots, ts.default_skins(hb.pots))]
+    b = ts.Batch(pots, hb.n_atoms, hb.n_systems, precision=ts.TS_MIXED, device=0)
+    s = ts.DeviceState.from_host(hb, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    # fmax and smax far below reach, so that every system takes every timed step
+    P = ts.FireParams(0.1, 1.0, 1.1, 0.5, 0.1, 0.99, 0.2, 1e-12, 1e-12, 0.0, 5, 1)
+    conv = torch.zeros(hb.n_systems, dtype=torch.uint8, device=dev)
+    fs = torch.zeros(hb.n_systems * ts.FIRE_STATE_BYTES, dtype=torch.uint8, device=dev)
+    fv = torch.zeros((hb.n_atoms + 3 * hb.n_systems, 3), dtype=torch.float64, device=dev)
+    inner = 10
+    ncalls = max(1, (args.steps + inner - 1) // inner)
+    with torch.cuda.stream(stream):
+        b.neighbor_build(s, force=True, stream=stream)
+        b.fire_init(s, P, fs, fv, stream=stream)
+        for _ in range(args.warmup):
+            b.fire_step(s, fs, fv, P, inner, stream=stream)
+        stream.synchronize()
+        l0 = b.counters()[0]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(ncalls):
+            b.fire_step(s, fs, fv, P, inner, stream=stream)
+        e1.record(stream)
+        b.fire_step(s, fs, fv, P, 1, converged=conv, stream=stream)
+        stream.synchronize()
+    assert int(conv.sum()) == 0, "a system converged inside the timed region"
+    ms = e0.elapsed_time(e1) / (ncalls * inner)
+    launches = b.counters()[0] - l0
+    b.poll()
+    b.close()
+    return {"metric": "batched variable-cell FIRE atom-steps/s", "value": hb.n_atoms / (ms / 1e3),
+            "unit": "atom-steps/s", "n_gpus": 1, "steps": ncalls * inner, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "row": "fire", "gpu_launches": launches,
+            "config": {"workload": "fire-stream: first 1024 of 8192 Morse Cu FCC supercells of 64-864 atoms, "
+                                   "0.1 A rattle, isotropic scale U[0.97, 1.03]; variable cell",
+                       "n_systems": hb.n_systems, "n_atoms": hb.n_atoms, "fire_steps_per_call": inner}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -301,7 +400,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-loop", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--row", default="md", choices=["md", "adjoint", "fire"],
+                    help="md: the MD step (the default line); adjoint, fire: other rows of the path, one GPU")
     args = ap.parse_args()
+    if args.row != "md":
+        print(json.dumps(run_row_adjoint(args) if args.row == "adjoint" else run_row_fire(args)))
+        return
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     hbcfg = {"workload": "ragged-mix-512: FCC/BCC n x m x k supercells of 32-2048 atoms, 1/3 each LJ argon, "

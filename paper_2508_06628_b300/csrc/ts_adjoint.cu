@@ -18,8 +18,10 @@
 
 namespace ts {
 
-template <bool F64>
-__global__ void __launch_bounds__(128) k_pair_bwd(int32_t n_warps, const int32_t* __restrict__ warp_sys, SysArrays S,
+// STRESS: gS given (the stress terms are compiled out of the common case, which
+// keeps the mixed variant within 64 registers: 8 CTAs of 128 threads per SM)
+template <bool F64, bool STRESS>
+__global__ void __launch_bounds__(128, F64 ? 4 : 8) k_pair_bwd(int32_t n_warps, const int32_t* __restrict__ warp_sys, SysArrays S,
                                                   SlotArrays A, const DevPot* __restrict__ pots, int64_t stride,
                                                   const double* __restrict__ gE, const double* __restrict__ gS,
                                                   double* gpart) {
@@ -30,28 +32,39 @@ __global__ void __launch_bounds__(128) k_pair_bwd(int32_t n_warps, const int32_t
   int64_t k = (int64_t)w * kWarp + lane;
   const DevPot P = pots[S.pot[s]];
   bool valid = A.perm[k] >= 0;
-  int nn = valid ? A.nn[k] : 0;
+  // the inner (pruned) list holds every pair within rc while the system is
+  // neither flagged for a refresh nor re-listed since: every caller re-lists
+  // flagged systems first, and a non-MD re-listing flags the system, so the
+  // test is warp-uniform and needs no host state; the inner list keeps the
+  // outer list's order, so the sums are the same either way
+  const bool use_in = !S.prune[s] && !need_relist(S, s);
+  const uint32_t* NB = use_in ? A.nbr_in : A.nbr;
+  int nn = valid ? (use_in ? A.nn_in : A.nn)[k] : 0;
   int64_t seg = S.seg_start[s];
-  const double* h = S.h + 9 * s;
-  double Vinv = 1.0 / fabs(h[0] * (h[4] * h[8] - h[5] * h[7]) - h[1] * (h[3] * h[8] - h[5] * h[6]) +
-                           h[2] * (h[3] * h[7] - h[4] * h[6]));
-  double gEs = gE ? gE[s] : 0.0;
-  double Sg[9];
-  bool stress = gS != nullptr;
-  for (int q = 0; q < 9; q++) Sg[q] = stress ? gS[9 * (int64_t)s + q] : 0.0;
-  // shift derivative dphi(rc)/dp (energy term only)
-  double dphic[3] = {0, 0, 0};
-  if (P.shift && P.kind != TS_SOFT_SPHERE && gEs != 0.0) {
-    double r, d1, d2, dd1[3];
-    PotMath<double>::eval2(P, P.rc2d, r, d1, d2, dphic, dd1);
+  constexpr bool stress = STRESS;
+  double Vinv = 0.0, Sg[9];
+  if constexpr (stress) {
+    const double* h = S.h + 9 * s;
+    Vinv = 1.0 / fabs(h[0] * (h[4] * h[8] - h[5] * h[7]) - h[1] * (h[3] * h[8] - h[5] * h[6]) +
+                      h[2] * (h[3] * h[7] - h[4] * h[6]));
   }
-  double gx[3] = {0, 0, 0}, gth[3] = {0, 0, 0};
+  for (int q = 0; q < 9; q++) Sg[q] = stress ? gS[9 * (int64_t)s + q] : 0.0;
+  double gEs = gE ? gE[s] : 0.0;
+  // the energy term needs the shift derivative dphi(rc)/dp (in the loop's
+  // precision: the FP64 pipe is a small fraction of the FP32 one)
+  const bool shift_e = P.shift && P.kind != TS_SOFT_SPHERE && gEs != 0.0;
   if constexpr (F64) {
+    double dphic[3] = {0, 0, 0};
+    if (shift_e) {
+      double r, d1, d2, dd1[3];
+      PotMath<double>::eval2(P, P.rc2d, r, d1, d2, dphic, dd1);
+    }
+    double gx[3] = {0, 0, 0}, gth[3] = {0, 0, 0};
     const double* tab = S.shiftd + 3 * (int64_t)s * kNCodes;
     const double* xi = A.xd + 3 * k;
     const double* gi = A.gd1 + 3 * k;
     for (int q = 0; q < nn; q++) {
-      uint32_t ent = A.nbr[q * stride + k];
+      uint32_t ent = NB[q * stride + k];
       int64_t j = seg + (ent & kJMask);
       int code = (int)(ent >> kJBits);
       double d[3];
@@ -67,7 +80,7 @@ __global__ void __launch_bounds__(128) k_pair_bwd(int32_t n_warps, const int32_t
       double ugi = u[0] * gi[0] + u[1] * gi[1] + u[2] * gi[2];
       for (int c = 0; c < 3; c++) gx[c] += d2 * ug * u[c] + d1 / r * (g[c] - ug * u[c]);
       for (int p = 0; p < 3; p++) gth[p] += dd1[p] * ugi + 0.5 * gEs * (dphi[p] - dphic[p]);
-      if (stress) {
+      if constexpr (stress) {
         double Aq = (d2 - d1 / r) / (r * r), dSd = 0;
         for (int a = 0; a < 3; a++) for (int b = 0; b < 3; b++) dSd += d[a] * Sg[3 * a + b] * d[b];
         for (int c = 0; c < 3; c++) {
@@ -81,6 +94,10 @@ __global__ void __launch_bounds__(128) k_pair_bwd(int32_t n_warps, const int32_t
     if (valid) {
       for (int c = 0; c < 3; c++) A.gd0[3 * k + c] = gx[c] - gEs * A.Fd[3 * k + c];
     }
+    for (int p = 0; p < 3; p++) {
+      double t = warp_sum(gth[p]);
+      if (lane == 0) gpart[4 * (int64_t)w + p] = t;
+    }
   } else {
     const float4* tab = S.shift + 2 * (int64_t)s * kNCodes;
     float4 xi = A.xh[k], li = A.xl[k], gi = A.g1[k];
@@ -88,9 +105,15 @@ __global__ void __launch_bounds__(128) k_pair_bwd(int32_t n_warps, const int32_t
     float gEf = (float)gEs, Vf = (float)Vinv;
     float Sf[9];
     for (int q = 0; q < 9; q++) Sf[q] = (float)Sg[q];
-    float dpc[3] = {(float)dphic[0], (float)dphic[1], (float)dphic[2]};
+    float dpc[3] = {0.f, 0.f, 0.f};
+    if (shift_e) {
+      float r, d1, d2, dd1[3];
+      PotMath<float>::eval2(P, P.rc2f, r, d1, d2, dpc, dd1);
+    }
+    uint32_t next = nn > 0 ? __ldg(NB + k) : 0u;
     for (int q = 0; q < nn; q++) {
-      uint32_t ent = __ldg(A.nbr + q * stride + k);
+      uint32_t ent = next;
+      if (q + 1 < nn) next = __ldg(NB + (q + 1) * stride + k);
       int64_t j = seg + (ent & kJMask);
       int code = (int)(ent >> kJBits);
       float4 xj = __ldg(A.xh + j), lj = __ldg(A.xl + j);
@@ -109,7 +132,7 @@ __global__ void __launch_bounds__(128) k_pair_bwd(int32_t n_warps, const int32_t
       float ugi = u[0] * gi.x + u[1] * gi.y + u[2] * gi.z;
       for (int c = 0; c < 3; c++) gxf[c] += d2 * ug * u[c] + d1 * ri * (g[c] - ug * u[c]);
       for (int p = 0; p < 3; p++) gtf[p] += dd1[p] * ugi + 0.5f * gEf * (dphi[p] - dpc[p]);
-      if (stress) {
+      if constexpr (stress) {
         float Aq = (d2 - d1 * ri) * ri * ri, dSd = 0.f;
         for (int a = 0; a < 3; a++) for (int b = 0; b < 3; b++) dSd += d[a] * Sf[3 * a + b] * d[b];
         for (int c = 0; c < 3; c++) {
@@ -124,11 +147,12 @@ __global__ void __launch_bounds__(128) k_pair_bwd(int32_t n_warps, const int32_t
       float4 F = A.F[k];
       A.g0[k] = make_float4(gxf[0] - gEf * F.x, gxf[1] - gEf * F.y, gxf[2] - gEf * F.z, 0.f);
     }
-    for (int p = 0; p < 3; p++) gth[p] = gtf[p];
-  }
-  for (int p = 0; p < 3; p++) {
-    double t = warp_sum(gth[p]);
-    if (lane == 0) gpart[4 * (int64_t)w + p] = t;
+    for (int p = 0; p < 3; p++) {
+      float t = gtf[p];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane == 0) gpart[4 * (int64_t)w + p] = (double)t;
+    }
   }
 }
 
@@ -171,14 +195,18 @@ __global__ void k_gparam_sys(int32_t B, SysArrays S, const double* __restrict__ 
   for (int p = 0; p < 3; p++) a[p] = warp_sum(a[p]);
   if (lane == 0) for (int p = 0; p < 3; p++) gsys[3 * (int64_t)s + p] = a[p];
 }
+// one warp per potential (at most kMaxPots = 16 warps, one CTA): lanes stride
+// over the systems, then a fixed-order warp sum, so the result is deterministic
 __global__ void k_gparam_pot(int32_t B, int32_t n_pots, SysArrays S, const double* __restrict__ gsys, double* gParams,
                              int accumulate) {
-  int q = threadIdx.x;
+  int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (q >= n_pots) return;
   double a[3] = {0, 0, 0};
-  for (int s = 0; s < B; s++)
+  for (int s = lane; s < B; s += 32)
     if (S.pot[s] == q) for (int p = 0; p < 3; p++) a[p] += gsys[3 * (int64_t)s + p];
-  for (int p = 0; p < 3; p++) gParams[3 * q + p] = (accumulate ? gParams[3 * q + p] : 0.0) + a[p];
+  for (int p = 0; p < 3; p++) a[p] = warp_sum(a[p]);
+  if (lane == 0)
+    for (int p = 0; p < 3; p++) gParams[3 * q + p] = (accumulate ? gParams[3 * q + p] : 0.0) + a[p];
 }
 
 // ---- smeared RDF ---------------------------------------------------------------
@@ -329,12 +357,13 @@ static int egrid(ts_batch* b) {
 static void backward_core(ts_batch* b, cudaStream_t st, const double* gE, const double* gS, double* gParams,
                           int accumulate_params) {
   int blocks = (int)(((int64_t)b->nwarps * 32 + 127) / 128);
-  if (b->f64) k_pair_bwd<true><<<blocks, 128, 0, st>>>(b->nwarps, b->d_warp_sys, b->S, b->A, b->d_pots, b->Ncap, gE, gS, b->d_gparam_part);
-  else k_pair_bwd<false><<<blocks, 128, 0, st>>>(b->nwarps, b->d_warp_sys, b->S, b->A, b->d_pots, b->Ncap, gE, gS, b->d_gparam_part);
+  auto kern = b->f64 ? (gS ? k_pair_bwd<true, true> : k_pair_bwd<true, false>)
+                     : (gS ? k_pair_bwd<false, true> : k_pair_bwd<false, false>);
+  kern<<<blocks, 128, 0, st>>>(b->nwarps, b->d_warp_sys, b->S, b->A, b->d_pots, b->Ncap, gE, gS, b->d_gparam_part);
   b->launches++;
   if (gParams) {
     k_gparam_sys<<<(b->B * 32 + 127) / 128, 128, 0, st>>>(b->B, b->S, b->d_gparam_part, b->d_scal);
-    k_gparam_pot<<<1, 32, 0, st>>>(b->B, b->n_pots, b->S, b->d_scal, gParams, accumulate_params);
+    k_gparam_pot<<<1, 32 * b->n_pots, 0, st>>>(b->B, b->n_pots, b->S, b->d_scal, gParams, accumulate_params);
     b->launches += 2;
   }
 }

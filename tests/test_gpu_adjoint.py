@@ -35,6 +35,46 @@ def test_pair_backward_matches_oracle(orc, precision):
     assert np.all(np.abs(gp - gpr) <= rel * np.abs(gpr) + rel * 1e-2 * np.abs(gpr).max())
 
 
+def backward_after_md(hb, precision, with_stress):
+    torch = torch_cuda()
+    from paper_2508_06628_b300 import ts
+    b = make_batch(hb, precision)
+    s = ts.DeviceState.from_host(hb)
+    rng = np.random.default_rng(6)
+    gF, gE, gS = rng.normal(size=(hb.n_atoms, 3)), rng.normal(size=hb.n_systems), rng.normal(size=(hb.n_systems, 3, 3))
+    t = lambda a: torch.as_tensor(a, dtype=torch.float64, device="cuda").contiguous()
+    gx = torch.zeros((hb.n_atoms, 3), dtype=torch.float64, device="cuda")
+    gp = torch.zeros((len(hb.pots), 3), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        b.neighbor_build(s, force=True, stream=stream)
+        b.md_step(s, 40, hb.meta["dt"], kind=ts.TS_LANGEVIN, gamma=hb.meta["gamma"], seed=4, stream=stream)
+        b.pair_forces_backward(s, t(gF), t(gE), t(gS) if with_stress else None, gx, gp, stream=stream)
+        b.poll(stream)
+    stream.synchronize()
+    out = s.pos.cpu().numpy(), gx.cpu().numpy(), gp.cpu().numpy(), b.prunes(), (gF, gE, gS if with_stress else None)
+    b.close()
+    return out
+
+
+@pytest.mark.parametrize("precision,with_stress", [(0, False), (0, True), (1, False), (1, True)])
+def test_pair_backward_after_md_uses_inner_lists(orc, monkeypatch, precision, with_stress):
+    """After MD steps the backward reads the pruned (inner) lists; with
+    TS_INNER=1 the inner list is the whole Verlet list, so the two runs must
+    agree bit for bit, and both with the oracle at the final positions."""
+    hb = small_mix(72, n_systems=8, lo=32, hi=500)
+    xa, gxa, gpa, pa, (gF, gE, gS) = backward_after_md(hb, precision, with_stress)
+    monkeypatch.setenv("TS_INNER", "1")
+    xb, gxb, gpb, _, _ = backward_after_md(hb, precision, with_stress)
+    assert pa > 0
+    assert np.array_equal(xa, xb)
+    assert np.array_equal(gxa, gxb) and np.array_equal(gpa, gpb)
+    gxr, gpr = orc.forces_backward(hb.offsets, xa, hb.cell, hb.pbc, hb.pot_idx, hb.pots, gF, gE, gS)
+    rel = 1e-9 if precision == 1 else 1e-4
+    assert np.abs(gxa - gxr).max() <= rel * np.abs(gxr).max()
+    assert np.all(np.abs(gpa - gpr) <= rel * np.abs(gpr) + rel * 1e-2 * np.abs(gpr).max())
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_rdf_and_its_gradient(orc, precision):
     torch = torch_cuda()
