@@ -59,7 +59,7 @@ size_t scratch_bytes(int64_t Ncap, int64_t Bcap, int64_t Ccap, int32_t max_nbrs,
                            2 * 16 /*g*/);
   per_slot += (f64 ? 3 * 8 : 2 * 16) /*prune reference*/ + 4 /*nn_in*/ + (size_t)max_nbrs * 4 /*inner list*/;
   per_slot += 4 * 4 /*perm sys bin nn*/ + 3 * 4 /*tmp i*/ + (size_t)max_nbrs * 4 + 8 * 8 / 32 /*partials*/ + 4 / 32 /*warp_sys*/ + 16 / 32 /*pair work items*/;
-  size_t per_sys = 8 * 4 + 9 * 8 * 3 + 9 * 4 + 6 * 4 + 4 * 4 + 8 + 12 /*list-build work table*/ + 8 /*piston*/ + 4 /*geometry state*/ +
+  size_t per_sys = 8 * 4 + 9 * 8 * 3 + 9 * 4 + 6 * 4 + 4 * 4 + 8 + 12 /*list-build work table*/ + 8 /*piston*/ + 4 /*geometry state*/ + 8 /*table bounds*/ + 32 * 4 /*FIRE FP32 coefficients*/ +
                    (size_t)kNCodes * (32 + 24 + 16);
   return per_slot * (size_t)Ncap + per_sys * (size_t)Bcap + (size_t)Ccap * 8;
 }
@@ -147,7 +147,7 @@ extern "C" ts_status ts_batch_create(const ts_batch_config* cfg, const ts_potent
        alloc(b, S.uid, B) && alloc(b, S.bin_off, B) && alloc(b, S.bin_cap, B) && alloc(b, S.warp_start, B) &&
        alloc(b, S.warp_end, B) && alloc(b, S.h, 9 * B) && alloc(b, S.hinv, 9 * B) && alloc(b, S.hinvf, 9 * B) && alloc(b, S.href, 9 * B) &&
        alloc(b, S.nb, 3 * B) && alloc(b, S.reach, 3 * B) && alloc(b, S.pmask, B) && alloc(b, S.relist, B) && alloc(b, S.prune, B) && alloc(b, S.dirty, B) &&
-       alloc(b, S.soon, B) && alloc(b, S.any, 1) && alloc(b, S.geom, B) &&
+       alloc(b, S.soon, B) && alloc(b, S.any, 1) && alloc(b, S.geom, B) && alloc(b, S.tbound, B) && alloc(b, S.lbound, B) &&
        alloc(b, S.kT, B) && alloc(b, S.shift, 2 * B * kNCodes) && alloc(b, S.shiftd, 3 * B * kNCodes) && alloc(b, S.shiftq, B * kNCodes);
   ok = ok && alloc(b, A.perm, N) && alloc(b, A.sys, N) && alloc(b, A.bin, N) && alloc(b, A.nn, N) &&
        alloc(b, A.nbr, (size_t)b->max_nbrs * N) && alloc(b, A.nbr_in, (size_t)b->max_nbrs * N) && alloc(b, A.nn_in, N) && alloc(b, A.tmp_i0, N) && alloc(b, A.tmp_i1, N) &&
@@ -164,7 +164,7 @@ extern "C" ts_status ts_batch_create(const ts_batch_config* cfg, const ts_potent
   ok = ok && alloc(b, b->d_partial, (size_t)kPartialStride * b->Wcap) && alloc(b, b->d_warp_sys, b->Wcap) &&
        alloc(b, b->d_count, b->Ccap) && alloc(b, b->d_cstart, b->Ccap) &&
        alloc(b, b->d_bsum, (b->Ccap + 1023) / 1024 + 1) && alloc(b, b->d_starts, B + 1) &&
-       alloc(b, b->d_Eint, B) && alloc(b, b->d_Wint, 9 * B) && alloc(b, b->d_scal, 32 * B) && alloc(b, b->d_nhc, 6 * B) && alloc(b, b->d_baro, B) &&
+       alloc(b, b->d_Eint, B) && alloc(b, b->d_Wint, 9 * B) && alloc(b, b->d_scal, 32 * B) && alloc(b, b->d_fcoef, 32 * B) && alloc(b, b->d_nhc, 6 * B) && alloc(b, b->d_baro, B) &&
        alloc(b, b->d_gparam_part, 4 * b->Wcap) && alloc(b, b->d_gacc, 3 * kMaxPots) &&
        alloc(b, b->d_items, b->Wcap) && alloc(b, b->d_tab_sys, B) && alloc(b, b->d_tab_base, B + 1) && alloc(b, b->d_tab_base_a, B + 1) &&
        alloc(b, b->d_tab_n, 3);
@@ -474,8 +474,8 @@ ts_status prologue(ts_batch* b, ts_state* s, cudaStream_t st, bool import_vel, b
   // change); FIRE, whose own test budgets the cell change since the listing,
   // checks only for a change made by the caller since the last call.
   const int cell_check = b->first_import ? 0 : (fire ? 1 : 2);
-  k_geometry<<<(B + 127) / 128, 128, 0, st>>>(B, b->S, s->cell, s->pbc, b->d_pots, b->d_err, cell_check);
-  k_shift_table<<<(int)(((int64_t)B * kNCodes + 255) / 256), 256, 0, st>>>(B, b->S);
+  k_geometry<<<(B + 31) / 32, 32, 0, st>>>(B, b->S, s->cell, s->pbc, b->d_pots, b->d_err, cell_check);
+  k_shift_table<<<(int)(((int64_t)B * 32 + 127) / 128), 128, 0, st>>>(B, b->S);
   int g = grid_for(b->Npad, 256);
   const int wv = import_vel ? 1 : 0;   // velocities in the same pass
   if (b->f64) k_import_pos<true><<<g, 256, 0, st>>>(b->Npad, b->S, b->A, s->pos, b->d_pots, !b->first_import, b->d_err, wv, s->vel, s->mass);

@@ -59,7 +59,8 @@ struct ts_batch {
   int64_t* d_starts = nullptr;
   double* d_Eint = nullptr;
   double* d_Wint = nullptr;
-  double* d_scal = nullptr;         // per-system FIRE / scratch scalars [16 B]
+  double* d_scal = nullptr;         // per-system FIRE / scratch scalars [32 B]
+  float* d_fcoef = nullptr;         // FP32 copy of the per-system FIRE step coefficients [32 B]
   double* d_nhc = nullptr;          // Nose-Hoover chain state during a call [6 per system]
   double* d_baro = nullptr;         // NPT piston velocities during a call [1 per system]
   double* d_gparam_part = nullptr;  // per-warp parameter-gradient partials [4 Wcap]

@@ -12,22 +12,27 @@
 //   clamped to |dq| <= maxstep over the whole system vector; q <- q + dq.
 // The new velocity is v' = A v + g f with per-system scalars A, g, so |v'|^2
 // follows from the reduced f.v, v.v, f.f and the clamp needs no second pass:
-// kernel 1 reduces per warp, kernel 2 updates per system in FP64, kernel 3
+// kernel 1 reduces per warp, kernel 2 updates per system (FP64 cell state), kernel 3
 // moves the atoms.
+#include <type_traits>
+
 #include "ts_kernels.cuh"
 
 namespace ts {
 
 constexpr int kFireCoef = 32;   // doubles of per-system coefficients
+constexpr int kFireSysWarps = 16;   // warps of a k_fire_sys CTA (32 systems per CTA)
 
 __device__ inline void inv_T3(const double* A, double* out) {   // out = A^-T
   double d = A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) + A[2] * (A[3] * A[7] - A[4] * A[6]);
+  // one division: an FP64 divide is a long instruction sequence on this part
+  const double id = 1.0 / d;
   double g[9];
-  g[0] = (A[4] * A[8] - A[5] * A[7]) / d; g[1] = (A[2] * A[7] - A[1] * A[8]) / d;
-  g[2] = (A[1] * A[5] - A[2] * A[4]) / d; g[3] = (A[5] * A[6] - A[3] * A[8]) / d;
-  g[4] = (A[0] * A[8] - A[2] * A[6]) / d; g[5] = (A[2] * A[3] - A[0] * A[5]) / d;
-  g[6] = (A[3] * A[7] - A[4] * A[6]) / d; g[7] = (A[1] * A[6] - A[0] * A[7]) / d;
-  g[8] = (A[0] * A[4] - A[1] * A[3]) / d;
+  g[0] = (A[4] * A[8] - A[5] * A[7]) * id; g[1] = (A[2] * A[7] - A[1] * A[8]) * id;
+  g[2] = (A[1] * A[5] - A[2] * A[4]) * id; g[3] = (A[5] * A[6] - A[3] * A[8]) * id;
+  g[4] = (A[0] * A[8] - A[2] * A[6]) * id; g[5] = (A[2] * A[3] - A[0] * A[5]) * id;
+  g[6] = (A[3] * A[7] - A[4] * A[6]) * id; g[7] = (A[1] * A[6] - A[0] * A[7]) * id;
+  g[8] = (A[0] * A[4] - A[1] * A[3]) * id;
   for (int a = 0; a < 3; a++) for (int b = 0; b < 3; b++) out[3 * a + b] = g[3 * b + a];
 }
 
@@ -68,10 +73,13 @@ __global__ void k_fire_reduce(int32_t n_warps, const int32_t* __restrict__ warp_
   if (w >= n_warps) return;
   int s = warp_sys[w];
   int64_t k = (int64_t)w * kWarp + lane;
-  double P = 0, vv = 0, ff = 0, fm = 0;
+  // the mixed variant works in FP32 (its forces and velocities are FP32; the
+  // FP64 pipe is a small fraction of the FP32 one) and hands FP64 partials on
+  using R = typename std::conditional<F64, double, float>::type;
+  R P = 0, vv = 0, ff = 0, fm = 0;
   if (A.perm[k] >= 0) {
     const double* Fd = fs[s].Fd;
-    double F[3], v[3];
+    R F[3], v[3];
     if constexpr (F64) {
       for (int c = 0; c < 3; c++) { F[c] = A.Fd[3 * k + c]; v[c] = A.gd0[3 * k + c]; }
     } else {
@@ -79,94 +87,122 @@ __global__ void k_fire_reduce(int32_t n_warps, const int32_t* __restrict__ warp_
       F[0] = f.x; F[1] = f.y; F[2] = f.z; v[0] = g.x; v[1] = g.y; v[2] = g.z;
     }
     for (int b = 0; b < 3; b++) {
-      double ft = F[0] * Fd[b] + F[1] * Fd[3 + b] + F[2] * Fd[6 + b];
+      R ft = F[0] * (R)Fd[b] + F[1] * (R)Fd[3 + b] + F[2] * (R)Fd[6 + b];
       P += ft * v[b]; vv += v[b] * v[b]; ff += ft * ft;
     }
     fm = F[0] * F[0] + F[1] * F[1] + F[2] * F[2];
   }
-  P = warp_sum(P); vv = warp_sum(vv); ff = warp_sum(ff);
-  for (int o = 16; o > 0; o >>= 1) fm = fmax(fm, __shfl_xor_sync(0xffffffffu, fm, o));
+  for (int o = 16; o > 0; o >>= 1) {
+    P += __shfl_xor_sync(0xffffffffu, P, o);
+    vv += __shfl_xor_sync(0xffffffffu, vv, o);
+    ff += __shfl_xor_sync(0xffffffffu, ff, o);
+    fm = fmax(fm, __shfl_xor_sync(0xffffffffu, fm, o));
+  }
   if (lane == 0) {
     part[4 * (int64_t)w] = P; part[4 * (int64_t)w + 1] = vv; part[4 * (int64_t)w + 2] = ff; part[4 * (int64_t)w + 3] = fm;
   }
 }
 
-// per system (one warp): convergence test, FIRE scalars, cell update; writes
-// the coefficients the atom kernel applies.  final_mode: outputs only.
-__global__ void k_fire_sys(int32_t B, SysArrays S, ts_fire_state* fs, double* fvel, const double* __restrict__ Wint,
+// per system: convergence test, FIRE scalars, cell update; writes the
+// coefficients the atom kernel applies.  final_mode: outputs only.
+//
+// A CTA of kFireSysWarps warps takes 32 systems: each warp reduces the
+// partials of some of them (lanes over the system's warps), then one thread
+// per system takes the system's step.  That step is a serial dependency chain,
+// and a dependent FP64 operation costs tens of cycles on this part, so the
+// mixed variant keeps FP64 only where the state needs it (the deformation
+// gradient, the cell, the atom map and the skin budget) and takes the
+// stress, the cell force and the FIRE scalars in FP32.
+template <bool F64>
+__global__ void __launch_bounds__(32 * kFireSysWarps) k_fire_sys(int32_t B, SysArrays S, ts_fire_state* fs, double* fvel, const double* __restrict__ Wint,
                            const double* __restrict__ Eint, const double* __restrict__ part, const ts_fire_params p,
-                           const DevPot* __restrict__ pots, double* cell, double* coef, uint8_t* conv_out,
+                           const DevPot* __restrict__ pots, double* cell, double* coef, float* fcoef, uint8_t* conv_out,
                            double* E_out, double* fmax_out, double* smax_out, int final_mode) {
-  int s = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
-  int lane = threadIdx.x & 31;
-  if (s >= B) return;
-  double P = 0, vv = 0, ff = 0, fm2 = 0;
-  for (int w = S.warp_start[s] + lane; w < S.warp_end[s]; w += 32) {
-    P += part[4 * (int64_t)w]; vv += part[4 * (int64_t)w + 1]; ff += part[4 * (int64_t)w + 2];
-    fm2 = fmax(fm2, part[4 * (int64_t)w + 3]);
+  using R = typename std::conditional<F64, double, float>::type;
+  __shared__ double red[32][4];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int s0 = blockIdx.x * 32;
+  for (int i = warp; i < 32 && s0 + i < B; i += kFireSysWarps) {
+    const int sr = s0 + i;
+    double P = 0, vv = 0, ff = 0, fm2 = 0;
+    for (int w = S.warp_start[sr] + lane; w < S.warp_end[sr]; w += 32) {
+      P += part[4 * (int64_t)w]; vv += part[4 * (int64_t)w + 1]; ff += part[4 * (int64_t)w + 2];
+      fm2 = fmax(fm2, part[4 * (int64_t)w + 3]);
+    }
+    P = warp_sum(P); vv = warp_sum(vv); ff = warp_sum(ff);
+    for (int o = 16; o > 0; o >>= 1) fm2 = fmax(fm2, __shfl_xor_sync(0xffffffffu, fm2, o));
+    if (lane == 0) { red[i][0] = P; red[i][1] = vv; red[i][2] = ff; red[i][3] = fm2; }
   }
-  P = warp_sum(P); vv = warp_sum(vv); ff = warp_sum(ff);
-  for (int o = 16; o > 0; o >>= 1) fm2 = fmax(fm2, __shfl_xor_sync(0xffffffffu, fm2, o));
-  if (lane != 0) return;
+  __syncthreads();
+  const int s = s0 + lane;
+  if (warp != 0 || s >= B) return;
+  R P = (R)red[lane][0], vv = (R)red[lane][1], ff = (R)red[lane][2];
+  const double fm2 = red[lane][3];
   ts_fire_state st = fs[s];
   double* h = cell + 9 * (int64_t)s;
   double V = fabs(h[0] * (h[4] * h[8] - h[5] * h[7]) - h[1] * (h[3] * h[8] - h[5] * h[6]) + h[2] * (h[3] * h[7] - h[4] * h[6]));
-  double sig[9], sm = 0;
-  for (int q = 0; q < 9; q++) { sig[q] = Wint[9 * (int64_t)s + q] / V; sm = fmax(sm, fabs(sig[q])); }
-  double fm = sqrt(fm2);
+  const R iV = (R)1 / (R)V;
+  R sig[9], sm = 0;
+  for (int q = 0; q < 9; q++) sig[q] = (R)Wint[9 * (int64_t)s + q] * iV;
+  for (int q = 0; q < 9; q++) sm = fmax(sm, fabs(sig[q]));
+  const R fm = sqrt((R)fm2);
   if (E_out) E_out[s] = Eint[s];
   if (fmax_out) fmax_out[s] = fm;
   if (smax_out) smax_out[s] = sm;
   double* cf = coef + kFireCoef * (int64_t)s;
+  float* fc = fcoef + kFireCoef * (int64_t)s;
   if (final_mode) { if (conv_out) conv_out[s] = (uint8_t)st.converged; return; }
   cf[0] = 0.0;
-  if (!st.converged && fm <= p.fmax && (!p.variable_cell || sm <= p.smax)) st.converged = 1;
+  fc[0] = 0.f;
+  if (!st.converged && fm <= (R)p.fmax && (!p.variable_cell || sm <= (R)p.smax)) st.converged = 1;
   if (conv_out) conv_out[s] = (uint8_t)st.converged;
   if (st.converged) { fs[s] = st; return; }
   int n = S.n_atoms[s];
-  double c = (double)n;
+  const R ic = (R)1 / (R)n;
   int64_t row0 = S.caller_off[s] + 3 * (int64_t)s + n;
   double* vc = fvel + 3 * row0;
-  double FiT[9], G[9];
+  double FiT[9];
   inv_T3(st.Fd, FiT);
-  for (int q = 0; q < 9; q++) G[q] = 0;
+  R G[9], vcr[9];
+  for (int q = 0; q < 9; q++) { G[q] = 0; vcr[q] = (R)vc[q]; }
   if (p.variable_cell) {
-    double sp[9];
+    R sp[9];
     for (int q = 0; q < 9; q++) sp[q] = sig[q];
-    sp[0] += p.p_ext; sp[4] += p.p_ext; sp[8] += p.p_ext;
+    sp[0] += (R)p.p_ext; sp[4] += (R)p.p_ext; sp[8] += (R)p.p_ext;
     for (int a = 0; a < 3; a++)
       for (int b = 0; b < 3; b++) {
-        double acc = 0;
-        for (int q = 0; q < 3; q++) acc += sp[3 * a + q] * FiT[3 * q + b];
-        G[3 * a + b] = -V * acc / c;
+        R acc = 0;
+        for (int q = 0; q < 3; q++) acc += sp[3 * a + q] * (R)FiT[3 * q + b];
+        G[3 * a + b] = -(R)V * acc * ic;
       }
-    for (int q = 0; q < 9; q++) { P += G[q] * vc[q]; vv += vc[q] * vc[q]; ff += G[q] * G[q]; }
+    for (int q = 0; q < 9; q++) { P += G[q] * vcr[q]; vv += vcr[q] * vcr[q]; ff += G[q] * G[q]; }
   }
-  double Ac = 1.0, bc = 0.0;
+  R Ac = 1, bc = 0;
   if (st.started) {
     if (P > 0) {
-      Ac = 1.0 - st.alpha;
-      bc = ff > 0 ? st.alpha * sqrt(vv / ff) : 0.0;
+      Ac = (R)1 - (R)st.alpha;
+      bc = ff > 0 ? (R)st.alpha * sqrt(vv / ff) : (R)0;
       if (st.npos > p.nmin) { st.dt = fmin(st.dt * p.finc, p.dt_max); st.alpha *= p.falpha; }
       st.npos++;
     } else {
-      Ac = 0.0; bc = 0.0;
+      Ac = 0; bc = 0;
       st.dt *= p.fdec; st.alpha = p.alpha0; st.npos = 0;
     }
   }
   st.started = 1;
-  double g = bc + st.dt;
-  double vn2 = Ac * Ac * vv + g * g * ff + 2.0 * Ac * g * P;
-  double nrm = st.dt * sqrt(fmax(vn2, 0.0));
-  double scale = nrm > p.maxstep ? p.maxstep / nrm : 1.0;
-  double sdt = scale * st.dt;
+  const R dt = (R)st.dt;
+  R g = bc + dt;
+  R vn2 = Ac * Ac * vv + g * g * ff + (R)2 * Ac * g * P;
+  R nrm = dt * sqrt(fmax(vn2, (R)0));
+  R scale = nrm > (R)p.maxstep ? (R)p.maxstep / nrm : (R)1;
+  R sdt = scale * dt;
   double Fn[9];
   for (int q = 0; q < 9; q++) Fn[q] = st.Fd[q];
   if (p.variable_cell) {
     for (int q = 0; q < 9; q++) {
-      double vn = Ac * vc[q] + g * G[q];
-      vc[q] = vn;
-      Fn[q] = st.Fd[q] + sdt * vn / c;
+      R vn = Ac * vcr[q] + g * G[q];
+      vc[q] = (double)vn;
+      Fn[q] = st.Fd[q] + (double)(sdt * vn * ic);
     }
   }
   // h = h0 Fn^T
@@ -175,7 +211,7 @@ __global__ void k_fire_sys(int32_t B, SysArrays S, ts_fire_state* fs, double* fv
     for (int b = 0; b < 3; b++) hn[3 * a + b] = st.h0[3 * a] * Fn[3 * b] + st.h0[3 * a + 1] * Fn[3 * b + 1] + st.h0[3 * a + 2] * Fn[3 * b + 2];
   for (int q = 0; q < 9; q++) h[q] = hn[q];
   // atom map: x' = x (Fd^-T Fn^T) + dq Fn^T ;  M = Fd^-T Fn^T - I,  T = Fn^T
-  cf[0] = 1.0; cf[1] = Ac; cf[2] = g; cf[3] = sdt;
+  cf[0] = 1.0; cf[1] = (double)Ac; cf[2] = (double)g; cf[3] = (double)sdt;
   for (int a = 0; a < 3; a++)
     for (int b = 0; b < 3; b++) {
       double m = 0;
@@ -194,6 +230,7 @@ __global__ void k_fire_sys(int32_t B, SysArrays S, ts_fire_state* fs, double* fv
   }
   double se = 0.5 * (pots[S.pot[s]].skin - dh);
   cf[31] = se;
+  for (int q = 0; q < kFireCoef; q++) fc[q] = (float)cf[q];   // the mixed atom kernel's copy
   if (se <= 0) { S.relist[s] = 1; S.any[0] = 1; }
   for (int q = 0; q < 9; q++) st.Fd[q] = Fn[q];
   st.nsteps++;
@@ -202,19 +239,18 @@ __global__ void k_fire_sys(int32_t B, SysArrays S, ts_fire_state* fs, double* fv
 
 template <bool F64>
 __global__ void k_fire_update(int64_t Npad, SysArrays S, SlotArrays A, const double* __restrict__ coef,
-                              const DevPot* __restrict__ pots) {
+                              const float* __restrict__ fcoef, const DevPot* __restrict__ pots) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < Npad; k += (int64_t)gridDim.x * blockDim.x) {
     int p = A.perm[k];
     if (p < 0) continue;
     int s = A.sys[k];
-    const double* cf = coef + kFireCoef * (int64_t)s;
-    if (cf[0] == 0.0) continue;
-    double Ac = cf[1], g = cf[2], sdt = cf[3];
-    const double* M = cf + 4;
-    const double* T = cf + 13;
-    const double* Fd = cf + 22;
-    double dx2;
     if constexpr (F64) {
+      const double* cf = coef + kFireCoef * (int64_t)s;
+      if (cf[0] == 0.0) continue;
+      double Ac = cf[1], g = cf[2], sdt = cf[3];
+      const double* M = cf + 4;
+      const double* T = cf + 13;
+      const double* Fd = cf + 22;
       double* x = A.xd + 3 * k;
       double* v = A.gd0 + 3 * k;
       const double* F = A.Fd + 3 * k;
@@ -228,31 +264,39 @@ __global__ void k_fire_update(int64_t Npad, SysArrays S, SlotArrays A, const dou
         nx[c] = x[c] + (x[0] * M[c] + x[1] * M[3 + c] + x[2] * M[6 + c]) + (dq[0] * T[c] + dq[1] * T[3 + c] + dq[2] * T[6 + c]);
       for (int c = 0; c < 3; c++) x[c] = nx[c];
       const double* xr = A.xrd + 3 * k;
-      dx2 = 0;
+      double dx2 = 0;
       for (int c = 0; c < 3; c++) dx2 += (x[c] - xr[c]) * (x[c] - xr[c]);
+      double se = cf[31];
+      if (se <= 0 || dx2 > se * se) { S.relist[s] = 1; S.any[0] = 1; }
+      else if (dx2 > pots[S.pot[s]].soon2 * se * se) S.soon[s] = 1;
     } else {
+      // FP32 throughout, from the FP32 copy of the coefficients
+      const float* cf = fcoef + kFireCoef * (int64_t)s;
+      if (cf[0] == 0.f) continue;
+      const float Ac = cf[1], g = cf[2], sdt = cf[3];
+      const float* M = cf + 4;
+      const float* T = cf + 13;
+      const float* Fd = cf + 22;
       float4 xh = A.xh[k], xl = A.xl[k], f = A.F[k], v = A.g0[k];
       float F[3] = {f.x, f.y, f.z}, vv[3] = {v.x, v.y, v.z}, dq[3];
       for (int b = 0; b < 3; b++) {
-        float ft = F[0] * (float)Fd[b] + F[1] * (float)Fd[3 + b] + F[2] * (float)Fd[6 + b];
-        vv[b] = (float)Ac * vv[b] + (float)g * ft;
-        dq[b] = (float)sdt * vv[b];
+        float ft = F[0] * Fd[b] + F[1] * Fd[3 + b] + F[2] * Fd[6 + b];
+        vv[b] = Ac * vv[b] + g * ft;
+        dq[b] = sdt * vv[b];
       }
       float x0 = xh.x + xl.x, x1 = xh.y + xl.y, x2 = xh.z + xl.z;
       float d[3];
       for (int c = 0; c < 3; c++)
-        d[c] = (x0 * (float)M[c] + x1 * (float)M[3 + c] + x2 * (float)M[6 + c]) +
-               (dq[0] * (float)T[c] + dq[1] * (float)T[3 + c] + dq[2] * (float)T[6 + c]);
+        d[c] = (x0 * M[c] + x1 * M[3 + c] + x2 * M[6 + c]) + (dq[0] * T[c] + dq[1] * T[3 + c] + dq[2] * T[6 + c]);
       pos_add(xh.x, xl.x, d[0]); pos_add(xh.y, xl.y, d[1]); pos_add(xh.z, xl.z, d[2]);
       A.xh[k] = xh; A.xl[k] = xl;
       A.g0[k] = make_float4(vv[0], vv[1], vv[2], 0.f);
       float4 rh = A.xrh[k], rl = A.xrl[k];
       float e0 = (xh.x - rh.x) + (xl.x - rl.x), e1 = (xh.y - rh.y) + (xl.y - rl.y), e2 = (xh.z - rh.z) + (xl.z - rl.z);
-      dx2 = (double)(e0 * e0 + e1 * e1 + e2 * e2);
+      const float dx2 = e0 * e0 + e1 * e1 + e2 * e2, se = cf[31], se2 = se * se;
+      if (se <= 0.f || dx2 > se2) { S.relist[s] = 1; S.any[0] = 1; }
+      else if (dx2 > (float)pots[S.pot[s]].soon2 * se2) S.soon[s] = 1;
     }
-    double se = cf[31];
-    if (se <= 0 || dx2 > se * se) { S.relist[s] = 1; S.any[0] = 1; }
-    else if (dx2 > pots[S.pot[s]].soon2 * se * se) S.soon[s] = 1;
   }
 }
 
@@ -298,18 +342,18 @@ extern "C" ts_status ts_fire_step(ts_batch* b, ts_state* s, ts_fire_state* fs, d
   reduce_sys(b, st, nullptr, nullptr, nullptr);
   clear_dirty(b, st);
   int wblocks = (int)(((int64_t)b->nwarps * 32 + 127) / 128);
-  int sblocks = (b->B * 32 + 127) / 128;
+  int sblocks = (b->B + 31) / 32;
   for (int k = 0; k <= n_steps; k++) {
     if (b->f64) k_fire_reduce<true><<<wblocks, 128, 0, st>>>(b->nwarps, b->d_warp_sys, b->A, fs, b->d_gparam_part);
     else k_fire_reduce<false><<<wblocks, 128, 0, st>>>(b->nwarps, b->d_warp_sys, b->A, fs, b->d_gparam_part);
-    k_fire_sys<<<sblocks, 128, 0, st>>>(b->B, b->S, fs, fvel, b->d_Wint, b->d_Eint, b->d_gparam_part, *p, b->d_pots,
-                                        s->cell, b->d_scal, converged, E, fmax, smax, k == n_steps);
+    (b->f64 ? k_fire_sys<true> : k_fire_sys<false>)<<<sblocks, 32 * kFireSysWarps, 0, st>>>(b->B, b->S, fs, fvel, b->d_Wint, b->d_Eint, b->d_gparam_part, *p, b->d_pots,
+                                        s->cell, b->d_scal, b->d_fcoef, converged, E, fmax, smax, k == n_steps);
     b->launches += 2;
     if (k == n_steps) break;
-    if (b->f64) k_fire_update<true><<<g, 256, 0, st>>>(b->Npad, b->S, b->A, b->d_scal, b->d_pots);
-    else k_fire_update<false><<<g, 256, 0, st>>>(b->Npad, b->S, b->A, b->d_scal, b->d_pots);
-    k_geometry<<<(b->B + 127) / 128, 128, 0, st>>>(b->B, b->S, s->cell, s->pbc, b->d_pots, b->d_err, 0);
-    k_shift_table<<<(int)(((int64_t)b->B * kNCodes + 255) / 256), 256, 0, st>>>(b->B, b->S);
+    if (b->f64) k_fire_update<true><<<g, 256, 0, st>>>(b->Npad, b->S, b->A, b->d_scal, b->d_fcoef, b->d_pots);
+    else k_fire_update<false><<<g, 256, 0, st>>>(b->Npad, b->S, b->A, b->d_scal, b->d_fcoef, b->d_pots);
+    k_geometry<<<(b->B + 31) / 32, 32, 0, st>>>(b->B, b->S, s->cell, s->pbc, b->d_pots, b->d_err, 0);
+    k_shift_table<<<(int)(((int64_t)b->B * 32 + 127) / 128), 128, 0, st>>>(b->B, b->S);
     b->launches += 3;
     relist(b, st, true);
     pair(b, st, true, false);

@@ -108,9 +108,25 @@ struct SysArrays {
   int32_t* soon;          // atoms past kSoon * skin/2: re-list along with any forced pass
   int32_t* any;           // [1] some system must re-list in this pass
   int32_t* geom;          // bit 0: geometry and image tables current for h and pmask; bit 1: just recomputed
+  int32_t* tbound;        // image codes with every |n_a| <= tbound are current in the shift tables
+  int32_t* lbound;        // largest |n_a| the system's Verlet list can hold (set when it is listed)
   int32_t* dirty;         // forces stale for this system
   double* kT;             // per-system kT (MD)
 };
+
+// Largest |n_a| of an image code that a list built for the current geometry
+// can hold: a stencil of reach m over nb cells wraps at most ceil(m / nb)
+// times along a periodic axis (open axes hold no images), and at least 1, so
+// that an atom one cell outside is wrapped from the table.
+__device__ __forceinline__ int image_bound(const SysArrays& S, int s) {
+  int r = 1;
+  for (int a = 0; a < 3; a++)
+    if (S.pmask[s] >> a & 1) {
+      int nb = S.nb[3 * s + a], m = S.reach[3 * s + a];
+      r = max(r, (m + nb - 1) / nb);
+    }
+  return min(r, kMaxReach);
+}
 
 __device__ __forceinline__ bool need_relist(const SysArrays& S, int s) {
   return S.relist[s] || (S.soon[s] && S.any[0]);

@@ -32,6 +32,7 @@ __global__ void k_sys_bounds(int64_t N, const int32_t* __restrict__ sidx, int32_
 __global__ void k_init_slots(int32_t B, SysArrays S, SlotArrays A) {
   int s = blockIdx.x;
   if (s >= B) return;
+  if (threadIdx.x == 0) S.lbound[s] = kMaxReach;   // no list yet: the first tables are complete
   int64_t st = S.seg_start[s];
   int n = S.n_atoms[s];
   int npad = (n + kWarp - 1) / kWarp * kWarp;
@@ -209,12 +210,15 @@ __global__ void k_geometry(int32_t B, SysArrays S, const double* __restrict__ ce
   S.pmask[s] = pm;
   double d = det3(h);
   if (!(fabs(d) > 0) || !isfinite(d)) { atomicOr(err, kErrNonFinite); return; }
+  // inverse cell by one reciprocal (an FP64 divide is a long sequence on this
+  // part); it only places atoms in bins and wraps them, which tolerate ulps
+  const double id = 1.0 / d;
   double g[9];
-  g[0] = (h[4] * h[8] - h[5] * h[7]) / d; g[1] = (h[2] * h[7] - h[1] * h[8]) / d;
-  g[2] = (h[1] * h[5] - h[2] * h[4]) / d; g[3] = (h[5] * h[6] - h[3] * h[8]) / d;
-  g[4] = (h[0] * h[8] - h[2] * h[6]) / d; g[5] = (h[2] * h[3] - h[0] * h[5]) / d;
-  g[6] = (h[3] * h[7] - h[4] * h[6]) / d; g[7] = (h[1] * h[6] - h[0] * h[7]) / d;
-  g[8] = (h[0] * h[4] - h[1] * h[3]) / d;
+  g[0] = (h[4] * h[8] - h[5] * h[7]) * id; g[1] = (h[2] * h[7] - h[1] * h[8]) * id;
+  g[2] = (h[1] * h[5] - h[2] * h[4]) * id; g[3] = (h[5] * h[6] - h[3] * h[8]) * id;
+  g[4] = (h[0] * h[8] - h[2] * h[6]) * id; g[5] = (h[2] * h[3] - h[0] * h[5]) * id;
+  g[6] = (h[3] * h[7] - h[4] * h[6]) * id; g[7] = (h[1] * h[6] - h[0] * h[7]) * id;
+  g[8] = (h[0] * h[4] - h[1] * h[3]) * id;
   for (int q = 0; q < 9; q++) { S.hinv[9 * s + q] = g[q]; S.hinvf[9 * s + q] = (float)g[q]; }
   double V = fabs(d), w[3];
   double ext = 0;
@@ -246,30 +250,37 @@ __global__ void k_geometry(int32_t B, SysArrays S, const double* __restrict__ ce
     S.nb[3 * s + a] = nb[a];
     S.reach[3 * s + a] = m[a];
   }
+  // the image tables are rebuilt for the codes the current lists hold and the
+  // codes a list built for this geometry can hold
+  S.tbound[s] = max(S.lbound[s], image_bound(S, s));
   // positions wrapped into the cell plus the skin must stay inside the hi/lo range
   if (ext + 2.0 * rl > 0.5 * kMaxCoord) { atomicOr(err, kErrUnsupported); bad = true; }
   S.geom[s] = bad ? 2 : 3;   // an error is raised again by every call until the cell changes
 }
 
-// Image shift table S = n h for every image code, stored hi/lo (mixed) and FP64.
+// Image shift table S = n h for every image code within the system's table
+// bound (S.tbound), stored hi/lo (mixed), FP64 and fixed point.  One warp per
+// system; a system whose cell did not change keeps its tables.
 __global__ void k_shift_table(int32_t B, SysArrays S) {
-  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= (int64_t)B * kNCodes) return;
-  int s = (int)(t / kNCodes), code = (int)(t % kNCodes);
-  if (!(S.geom[s] & 2)) return;   // cell unchanged: the tables stand
-  int nx = code % kImgSide - kMaxReach, ny = (code / kImgSide) % kImgSide - kMaxReach,
-      nz = code / (kImgSide * kImgSide) - kMaxReach;
+  const int s = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (s >= B || !(S.geom[s] & 2)) return;   // cell unchanged: the tables stand
+  const int tb = S.tbound[s], side = 2 * tb + 1;
   const double* h = S.h + 9 * s;
-  double v[3];
-  for (int c = 0; c < 3; c++) v[c] = nx * h[c] + ny * h[3 + c] + nz * h[6 + c];
-  float4 hi, lo;
-  split_pos(v[0], hi.x, lo.x); split_pos(v[1], hi.y, lo.y); split_pos(v[2], hi.z, lo.z);
-  hi.w = 0.f; lo.w = 0.f;
-  S.shift[2 * t] = hi; S.shift[2 * t + 1] = lo;
-  for (int c = 0; c < 3; c++) S.shiftd[3 * t + c] = v[c];
-  S.shiftq[t] = make_uint4((uint32_t)(unsigned long long)llrint(v[0] * (double)kFix),
-                           (uint32_t)(unsigned long long)llrint(v[1] * (double)kFix),
-                           (uint32_t)(unsigned long long)llrint(v[2] * (double)kFix), 0u);
+  for (int i = lane; i < side * side * side; i += 32) {
+    const int nx = i % side - tb, ny = (i / side) % side - tb, nz = i / (side * side) - tb;
+    const int64_t t = (int64_t)s * kNCodes + img_code(nx, ny, nz);
+    double v[3];
+    for (int c = 0; c < 3; c++) v[c] = nx * h[c] + ny * h[3 + c] + nz * h[6 + c];
+    float4 hi, lo;
+    split_pos(v[0], hi.x, lo.x); split_pos(v[1], hi.y, lo.y); split_pos(v[2], hi.z, lo.z);
+    hi.w = 0.f; lo.w = 0.f;
+    S.shift[2 * t] = hi; S.shift[2 * t + 1] = lo;
+    for (int c = 0; c < 3; c++) S.shiftd[3 * t + c] = v[c];
+    S.shiftq[t] = make_uint4((uint32_t)(unsigned long long)llrint(v[0] * (double)kFix),
+                             (uint32_t)(unsigned long long)llrint(v[1] * (double)kFix),
+                             (uint32_t)(unsigned long long)llrint(v[2] * (double)kFix), 0u);
+  }
 }
 
 // Wrap a double-float position into its cell by a whole lattice vector (along
@@ -278,7 +289,8 @@ __global__ void k_shift_table(int32_t B, SysArrays S) {
 // far inside any skin); the shift itself is the system's double-float image
 // shift, added exactly to hi and with one FP32 rounding to lo, so an atom that
 // stays inside its cell is left bit-identical.  No FP64 arithmetic (slow on
-// this part).  Returns false when the atom lies more than kMaxReach cells away
+// this part).  Returns false when the atom lies more cells away than the image
+// table currently covers (S.tbound, at least 1)
 // (the caller then takes the FP64 route).
 __device__ __forceinline__ bool wrap_bin_mixed(const SysArrays& S, int s, float4& hi, float4& lo, int kb[3]) {
   const float* g = S.hinvf + 9 * s;
@@ -292,7 +304,7 @@ __device__ __forceinline__ bool wrap_bin_mixed(const SysArrays& S, int s, float4
     float fl = 0.f;
     if (pm >> a & 1) {   // periodic: whole lattice vectors back into the cell
       fl = floorf(v);
-      if (!(fabsf(fl) <= (float)kMaxReach)) return false;
+      if (!(fabsf(fl) <= (float)S.tbound[s])) return false;   // beyond the current table entries
     } else if (!(fabsf(v) <= 4096.f)) {
       return false;
     }
@@ -499,6 +511,7 @@ __global__ void k_after_relist(int32_t B, SysArrays S, int64_t* counters, int md
       S.prune[s] = 1;
     }
     if (re) {
+      S.lbound[s] = image_bound(S, s);   // the lists just built hold codes up to this bound
       S.dirty[s] = 1;
       S.relist[s] = 0;
       S.soon[s] = 0;

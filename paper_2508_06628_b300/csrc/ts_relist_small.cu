@@ -148,7 +148,7 @@ k_relist_small(int32_t B, SysArrays S, SlotArrays A, int64_t stride, int move_fi
       }
     }
     if (!done) {
-      // FP64 route: FP64 positions, or an atom more than kMaxReach cells away
+      // FP64 route: FP64 positions, or an atom further out than the image table covers
       double x[3];
       if constexpr (F64) {
         for (int c = 0; c < 3; c++) x[c] = A.xd[3 * k + c];
