@@ -34,7 +34,7 @@ BYTES_PER_ATOM = 32         # read own position, write own force, per atom-step
 # DRAM bytes (read + write) of one forces-only k_pair_small launch (inner lists) on ragged-mix-512, from one ncu
 # capture (profiles/k_pair_small_ragged_mix_512.md); reported only while the kernel's sources
 # (ts_pair.cu, then ts_internal.cuh) hash to the value recorded with the capture
-PAIR_TRAFFIC = {"bytes": 49_635_328 + 164_864, "source_sha1": "82d2c4a7ca834a3b1f070cff17c93d4982c96088"}
+PAIR_TRAFFIC = {"bytes": 49_636_352 + 126_464, "source_sha1": "ab71ef60858f2256349fefc5c6e4b3e2e3f1c2ea"}
 
 
 def pair_traffic():
