@@ -79,3 +79,42 @@ def test_fire_stream_batch_converges_like_oracle(orc):
     n = np.diff(hb.offsets)
     assert np.allclose(E / n, Er / n, atol=1e-5)
     assert np.all(fm <= 1e-3) and np.all(sm <= 1e-4)
+
+
+def tiny_cells():
+    """Cells narrower than the list radius along some axes, so that lists hold
+    images up to |n| = 2..4 and the image bound moves as the cells relax: a
+    compressed 1-atom primitive FCC cell, a rattled 4-atom cubic cell and a
+    stretched 2x1x1 supercell (one wide and two narrow axes)."""
+    rng = np.random.default_rng(21)
+    a1 = 3.61 * 0.95
+    prim = 0.5 * a1 * np.array([[0.0, 1.0, 1.0], [1.0, 0.0, 1.0], [1.0, 1.0, 0.0]])
+    systems = [dict(pos=np.zeros((1, 3)), vel=np.zeros((1, 3)), mass=np.full(1, 63.546), cell=prim, pot=0)]
+    p4, c4 = W.lattice("fcc", (1, 1, 1), 3.61 * 0.97)
+    p4 = p4 + rng.normal(0, 0.05, p4.shape)
+    systems.append(dict(pos=p4, vel=np.zeros_like(p4), mass=np.full(4, 63.546), cell=c4, pot=0))
+    p8, c8 = W.lattice("fcc", (2, 1, 1), 3.61 * 1.03)
+    p8 = p8 + rng.normal(0, 0.05, p8.shape)
+    systems.append(dict(pos=p8, vel=np.zeros_like(p8), mass=np.full(8, 63.546), cell=c8, pot=0))
+    return W.concat(systems, [W.MORSE_CU])
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_fire_tiny_cells_match_oracle(orc, precision):
+    """Variable-cell FIRE on cells whose lists reach 2-4 images out: the image
+    tables, rebuilt every step only for the codes the lists and the wrap can
+    read, give the oracle's trajectory."""
+    hb = tiny_cells()
+    x, h, conv, E, fm, sm, fv = gpu_fire(hb, precision, 15, calls=2)
+    fr = orc.FireRun(hb.offsets, hb.pos, hb.cell, hb.pbc, hb.pot_idx, hb.pots)
+    Er, fmr, smr = fr.step(30)
+    moved = np.abs(fr.cells - hb.cell).max(axis=(1, 2))
+    assert np.all(moved > 1e-3)                       # every cell took part in the relaxation
+    if precision == 1:
+        assert np.abs(h - fr.cells).max() < 1e-9
+        assert np.abs(frac_diff(x, fr.x, h, hb.offsets)).max() < 1e-8
+        assert np.allclose(E, Er, rtol=1e-9)
+    else:
+        assert np.abs(h - fr.cells).max() < 1e-5 * np.abs(fr.cells).max()
+        assert np.abs(frac_diff(x, fr.x, h, hb.offsets)).max() < 1e-5
+        assert np.allclose(E, Er, rtol=1e-5, atol=1e-5)
