@@ -296,7 +296,7 @@ FLOP_PER_PAIR_BWD = 100   # pair-force backward, per pair within rc (positions a
 
 
 def run_row_adjoint(args):
-    """the pair-force backward (gF, gE -> gradients in positions
+    """The adjoint row: the pair-force backward (gF, gE -> gradients in positions
     and potential parameters) on the MD workload after its warm-up, timed with
     CUDA events around whole backward calls (the call's gradient import,
     pair-backward kernel, export and parameter reductions)."""
@@ -345,7 +345,7 @@ def run_row_adjoint(args):
 
 
 def run_row_fire(args):
-    """variable-cell FIRE on 1024 systems of the relaxation
+    """The FIRE row: variable-cell FIRE on 1024 systems of the relaxation
     stream (Morse Cu FCC, 64-864 atoms, rattled and scaled), timed with CUDA
     events around calls of 10 FIRE steps."""
     import torch
