@@ -391,6 +391,204 @@ def run_row_fire(args):
                        "n_systems": hb.n_systems, "n_atoms": hb.n_atoms, "fire_steps_per_call": inner}}
 
 
+def _line(metric, value, unit, ms, steps, warmup, dtype, config, **extra):
+    d = {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": steps, "warmup": warmup,
+         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
+         "data": "synthetic", "config": config}
+    d.update(extra)
+    return d
+
+
+def run_row_nve256(args):
+    """One 256-atom LJ argon box (FCC 4x4x4, a = 5.26 A, 50 K), NVE velocity
+    Verlet at dt = 2 fs, 1000 steps in FP64 as calls of 100 steps; reports the
+    relative drift of E + KE beside the throughput, and the oracle on the same
+    1000 steps."""
+    import torch
+    from paper_2508_06628_b300 import ts, workloads as W
+    dev = torch.device("cuda", 0)
+    hb = W.single_lj_argon(seed=0)
+    pots = [dict(p, skin=s) for p, s in zip(hb.pots, ts.default_skins(hb.pots))]
+    b = ts.Batch(pots, hb.n_atoms, hb.n_systems, precision=ts.TS_FP64, device=0)
+    s = ts.DeviceState.from_host(hb, device=dev)
+    E = torch.zeros(1, dtype=torch.float64, device=dev)
+    KE = torch.zeros_like(E)
+    dt, n, inner = hb.meta["dt"], 1000, 100
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        b.neighbor_build(s, force=True, stream=stream)
+        b.md_step(s, 1, dt, kind=ts.TS_NVE, E=E, KE=KE, stream=stream)   # energies at the start
+        stream.synchronize()
+        H0 = float(E[0] + KE[0])
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for c in range(n // inner):
+            b.md_step(s, inner, dt, kind=ts.TS_NVE, E=E, KE=KE, stream=stream)
+        e1.record(stream)
+        stream.synchronize()
+    ms = e0.elapsed_time(e1) / n
+    H1 = float(E[0] + KE[0])
+    b.poll()
+    b.close()
+    out = _line("NVE atom-steps/s, one 256-atom LJ argon box", hb.n_atoms / (ms / 1e3), UNIT, ms, n, 1, "f64",
+                {"workload": "lj-argon-256: FCC 4x4x4, a = 5.26 A, rc 2.5 sigma shifted, MB 50 K, NVE dt 2 fs",
+                 "n_systems": 1, "n_atoms": hb.n_atoms}, row="nve256",
+                energy_drift_rel=abs(H1 - H0) / abs(H0))
+    if not args.no_cpu:
+        from oracle import oracle
+        t0 = time.time()
+        oracle.md(hb.offsets, hb.pos, hb.vel, hb.mass, hb.cell, hb.pbc, hb.pot_idx, hb.pots, dt, n, kind=0)
+        tc = time.time() - t0
+        out["cpu_baseline"] = {"value": hb.n_atoms * n / tc, "unit": UNIT, "cores": oracle.num_threads(),
+                               "kind": "oracle", "sample": "the same 1000 NVE steps, FP64 brute force"}
+    return out
+
+
+def run_row_inflight(args):
+    """Structural relaxation of a stream of 8192 Morse Cu cells (64-864 atoms,
+    0.1 A rattle, cell scaled by U[0.97, 1.03]) by variable-cell FIRE to fmax
+    1e-3 eV/A and |sigma| 1e-4 eV/A^3, at most 1024 systems in flight and an
+    atom budget of 300,000: converged systems retire and queued ones are
+    admitted between rounds of 25 FIRE steps.  Host wall time of the whole
+    relaxation, batch set-up included."""
+    import torch
+    from paper_2508_06628_b300 import runtime, ts, workloads as W
+    hb = W.fire_stream(seed=2, n_systems=8192)
+    pots = [dict(p, skin=s) for p, s in zip(hb.pots, ts.default_skins(hb.pots))]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res, log = runtime.relax_inflight(hb, pots, max_scaler=300_000, max_active=1024, n_inner=25,
+                                      precision=ts.TS_MIXED)
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    assert len(res) == hb.n_systems, "systems left unrelaxed"
+    atom_steps = sum(r["atoms"] for r in log) * 25
+    out = _line("structures relaxed per second (variable-cell FIRE, in-flight batching)", hb.n_systems / t,
+                "structures/s", 1e3 * t / len(log), len(log), 0, "f32",
+                {"workload": "fire-stream-8192: Morse Cu FCC 64-864 atoms, 0.1 A rattle, U[0.97, 1.03] scale; "
+                             "fmax 1e-3 eV/A, |sigma| 1e-4 eV/A^3; <= 1024 in flight, 300,000-atom budget",
+                 "n_systems": hb.n_systems, "n_atoms": hb.n_atoms, "fire_steps_per_round": 25},
+                row="inflight", atom_steps_per_s=atom_steps / t, rounds=len(log), wall_s=t,
+                mean_active=float(np.mean([r["active"] for r in log])))
+    if not args.no_cpu:
+        from oracle import oracle
+        sub = hb.subset(list(range(16)))
+        fr = oracle.FireRun(sub.offsets, sub.pos, sub.cell, sub.pbc, sub.pot_idx, sub.pots, use_cells=True)
+        t0 = time.time()
+        fr.step(50)
+        tc = time.time() - t0
+        out["cpu_baseline"] = {"value": sub.n_atoms * 50 / tc, "unit": UNIT, "cores": oracle.num_threads(),
+                               "kind": "oracle", "sample": "first 16 systems of the stream x 50 FIRE steps, "
+                                                           "cell-list mode (atom-steps/s)"}
+    return out
+
+
+def run_row_diff(args):
+    """The differentiable workload: 64 reduced-LJ liquid boxes of 864 atoms
+    (rho* = 0.8, T* = 1.0 after a Langevin pre-run), NVE 2000 steps at dt* =
+    0.005; loss = MSE of the trajectory-averaged 200-bin smeared RDF (to rc)
+    against a target from sigma' = 1.05; gradient in (sigma, epsilon) by the
+    adjoint with checkpoints every 100 steps.  Host wall time of one loss and
+    gradient evaluation."""
+    import torch
+    from paper_2508_06628_b300 import grad, ts, workloads as W
+    dev = torch.device("cuda", 0)
+    hb = W.lj_liquid(seed=3, n_systems=64, reps=(6, 6, 6), rho=0.8, kT=1.0)
+    pot = dict(W.LJ_REDUCED, skin=0.3)
+    b = ts.Batch([pot], hb.n_atoms, hb.n_systems, precision=ts.TS_MIXED, device=0)
+    s = ts.DeviceState.from_host(hb, device=dev)
+    b.neighbor_build(s, force=True)
+    b.md_step(s, 500, 0.005, kind=ts.TS_LANGEVIN, gamma=1.0, seed=7)       # melt at T* = 1
+    T, every, K, rmax = 2000, 100, 200, 2.5
+    grad.set_params(b, np.array([[1.05, 1.0, 0.0]]))
+    target, _ = grad.trajectory_rdf(b, s, 0.005, T, every, rmax, K)
+    grad.set_params(b, np.array([[1.0, 1.0, 0.0]]))
+    # warm-up: one 200-step evaluation (the first use of each PyTorch kernel on
+    # the device costs far more than its run); its gradient is reported too,
+    # beside the 2000-step one, to show how the adjoint of a chaotic
+    # trajectory grows with its length
+    _, _, g200 = grad.rdf_loss_and_grad(b, s, 0.005, 200, every, rmax, K, target, checkpoint=100)
+    g200 = g200.cpu().numpy()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    loss, g, gth = grad.rdf_loss_and_grad(b, s, 0.005, T, every, rmax, K, target, checkpoint=100)
+    gh = gth.cpu().numpy()
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    b.poll()
+    b.close()
+    out = _line("trajectory-gradient atom-steps/s (NVE forward + checkpointed adjoint)", hb.n_atoms * T / t, UNIT,
+                 1e3 * t / T, T, 1, "f32",
+                 {"workload": "lj-liquid-64x864: rho* 0.8, T* 1.0, NVE dt* 0.005, 2000 steps; 200-bin smeared RDF "
+                              "to rc vs sigma' = 1.05 target; d loss / d (sigma, epsilon), checkpoints every 100",
+                  "n_systems": hb.n_systems, "n_atoms": hb.n_atoms},
+                 row="diff", wall_s=t, loss=loss, dloss_dsigma=float(gh[0, 0]), dloss_deps=float(gh[0, 1]),
+                 dloss_dsigma_200_steps=float(g200[0, 0]), dloss_deps_200_steps=float(g200[0, 1]))
+    if not args.no_cpu:
+        from oracle import oracle
+        sub = hb.subset([0, 1])
+        tgt = target.cpu().numpy()
+        t0 = time.time()
+        oracle.traj_rdf_loss(sub.offsets, sub.pos, sub.vel, sub.mass, sub.cell, sub.pbc, dict(W.LJ_REDUCED), 0.005,
+                             100, 100, rmax, K, tgt, grad=True, use_cells=True)
+        tc = time.time() - t0
+        out["cpu_baseline"] = {"value": sub.n_atoms * 100 / tc, "unit": UNIT, "cores": oracle.num_threads(),
+                               "kind": "oracle", "sample": "2 of the 64 systems (lattice start) x 100 steps, "
+                                                           "loss and FP64 adjoint gradient, cell lists"}
+    return out
+
+
+def run_row_large(args):
+    """Eight reduced-LJ boxes of 2,048,000 atoms (FCC 80x80x80 at rho* = 0.85,
+    MB velocities at T* = 1.2, 0.02 sigma rattle), skin 0.3 sigma, NVE at dt* =
+    0.005 in calls of 50 steps after a Langevin pre-run; reports the energy
+    drift per atom over the timed steps."""
+    import torch
+    from paper_2508_06628_b300 import ts, workloads as W
+    dev = torch.device("cuda", 0)
+    hb = W.lj_liquid(seed=4, n_systems=8, reps=(80, 80, 80), rho=0.85, kT=1.2, rattle=0.02)
+    pots = [dict(hb.pots[0], skin=0.3)]
+    b = ts.Batch(pots, hb.n_atoms, hb.n_systems, precision=ts.TS_MIXED, device=0)
+    s = ts.DeviceState.from_host(hb, device=dev)
+    E = torch.zeros(hb.n_systems, dtype=torch.float64, device=dev)
+    KE = torch.zeros_like(E)
+    inner = 50
+    n = max(inner, (args.steps // inner) * inner) if args.steps < 5000 else 200
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        b.neighbor_build(s, force=True, stream=stream)
+        b.md_step(s, 100, 0.005, kind=ts.TS_LANGEVIN, gamma=1.0, seed=3, stream=stream)   # thermalise
+        b.md_step(s, inner, 0.005, kind=ts.TS_NVE, E=E, KE=KE, stream=stream)
+        stream.synchronize()
+        H0 = (E + KE).cpu().numpy()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(n // inner):
+            b.md_step(s, inner, 0.005, kind=ts.TS_NVE, E=E, KE=KE, stream=stream)
+        e1.record(stream)
+        stream.synchronize()
+    ms = e0.elapsed_time(e1) / n
+    H1 = (E + KE).cpu().numpy()
+    b.poll()
+    b.close()
+    out = _line("NVE atom-steps/s, 8 boxes of 2,048,000 LJ atoms", hb.n_atoms / (ms / 1e3), UNIT, ms, n, 2, "f32",
+                {"workload": "lj-large-8x2048000: FCC 80^3 at rho* 0.85, T* 1.2, rc 2.5 shifted, skin 0.3, "
+                             "NVE dt* 0.005", "n_systems": hb.n_systems, "n_atoms": hb.n_atoms},
+                row="large", energy_drift_per_atom_max=float(np.abs(H1 - H0).max() / 2048000),
+                energy_drift_steps=n)
+    if not args.no_cpu:
+        from oracle import oracle
+        sub = hb.subset([0])
+        t0 = time.time()
+        oracle.md(sub.offsets, sub.pos, sub.vel, sub.mass, sub.cell, sub.pbc, sub.pot_idx, sub.pots, 0.005, 2, kind=0,
+                  use_cells=True)
+        tc = time.time() - t0
+        out["cpu_baseline"] = {"value": sub.n_atoms * 2 / tc, "unit": UNIT, "cores": oracle.num_threads(),
+                               "kind": "oracle", "sample": "one of the 8 boxes (lattice start) x 2 NVE steps, "
+                                                           "cell lists"}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -400,11 +598,13 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-loop", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--row", default="md", choices=["md", "adjoint", "fire"],
-                    help="md: the MD step (the default line); adjoint, fire: other rows of the path, one GPU")
+    ap.add_argument("--row", default="md", choices=["md", "adjoint", "fire", "nve256", "inflight", "diff", "large"],
+                    help="md: the MD step (the default line); the others: other rows and workloads, one GPU")
     args = ap.parse_args()
     if args.row != "md":
-        print(json.dumps(run_row_adjoint(args) if args.row == "adjoint" else run_row_fire(args)))
+        rows = {"adjoint": run_row_adjoint, "fire": run_row_fire, "nve256": run_row_nve256,
+                "inflight": run_row_inflight, "diff": run_row_diff, "large": run_row_large}
+        print(json.dumps(rows[args.row](args)))
         return
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
