@@ -86,6 +86,32 @@ __global__ void k_import_pos(int64_t Npad, SysArrays S, SlotArrays A, const doub
       atomicOr(err, kErrNonFinite);
       continue;
     }
+    // Along periodic axes a position is defined modulo the lattice: take the
+    // image of the caller's position nearest the slot's listing reference, so
+    // that unwrapped coordinates (a stored trajectory, a caller's own
+    // integrator) cost no re-listing.  The lattice vector is chosen in FP32
+    // and applied in FP64, only when it is not zero.
+    if (check_skin && S.pmask[s]) {
+      double r0, r1, r2;
+      if constexpr (F64) {
+        r0 = A.xrd[3 * k]; r1 = A.xrd[3 * k + 1]; r2 = A.xrd[3 * k + 2];
+      } else {
+        const float4 rh = A.xrh[k], rl = A.xrl[k];
+        r0 = (double)rh.x + (double)rl.x; r1 = (double)rh.y + (double)rl.y; r2 = (double)rh.z + (double)rl.z;
+      }
+      const float e0 = (float)(x0 - r0), e1 = (float)(x1 - r1), e2 = (float)(x2 - r2);
+      const float* g = S.hinvf + 9 * s;
+      const int pm = S.pmask[s];
+      int n[3];
+      for (int a = 0; a < 3; a++)
+        n[a] = (pm >> a & 1) ? (int)rintf(fmaf(e0, g[a], fmaf(e1, g[3 + a], e2 * g[6 + a]))) : 0;
+      if (n[0] | n[1] | n[2]) {
+        const double* h = S.h + 9 * s;
+        x0 -= n[0] * h[0] + n[1] * h[3] + n[2] * h[6];
+        x1 -= n[0] * h[1] + n[1] * h[4] + n[2] * h[7];
+        x2 -= n[0] * h[2] + n[1] * h[5] + n[2] * h[8];
+      }
+    }
     bool changed;
     double dx, dy, dz;
     if constexpr (F64) {

@@ -76,3 +76,41 @@ def test_periodicity_and_cell_changes_between_calls(orc):
     s.cell.copy_(torch.as_tensor(hb.cell, device="cuda"))           # back to the first cell
     check(pbc, hb.cell)
     b.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_positions_shifted_by_lattice_vectors_cost_no_relisting(orc, precision):
+    """Positions handed back displaced by whole lattice vectors along the
+    periodic axes (unwrapped coordinates) are the same configuration: the
+    import takes the image nearest each atom's listing reference, so nothing
+    re-lists and the forces are those of the original positions."""
+    torch = torch_cuda()
+    from paper_2508_06628_b300 import ts
+    hb = small_mix(131, n_systems=6, lo=32, hi=300)
+    b = make_batch(hb, precision)
+    s = ts.DeviceState.from_host(hb)
+    b.neighbor_build(s, force=True)
+    F0 = torch.zeros_like(s.pos)
+    b.pair_forces(s, F0, None, None)
+    b.poll()
+    _, r0 = b.counters()
+    x = s.pos.cpu().numpy()
+    rng = np.random.default_rng(7)
+    off = hb.offsets
+    xs = x.copy()
+    for k in range(hb.n_systems):
+        n = rng.integers(-2, 3, size=(off[k + 1] - off[k], 3)) * hb.pbc[k].astype(int)
+        xs[off[k]:off[k + 1]] += n @ hb.cell[k]
+    assert np.abs(xs - x).max() > 1.0
+    s.pos.copy_(torch.as_tensor(xs, device="cuda"))
+    F1 = torch.zeros_like(s.pos)
+    b.pair_forces(s, F1, None, None)
+    b.poll()
+    _, r1 = b.counters()
+    assert r1 == r0
+    F0, F1 = F0.cpu().numpy(), F1.cpu().numpy()
+    Er, Fr, _ = orc.forces(hb.offsets, xs, hb.cell, hb.pbc, hb.pot_idx, hb.pots)
+    ok, worst, frac = force_tolerance_ok(F1, Fr, hb.offsets, precision == 1)
+    assert ok, (worst, frac)
+    assert np.abs(F1 - F0).max() <= (1e-12 if precision == 1 else 1e-5) * np.abs(F0).max()
+    b.close()
