@@ -278,7 +278,10 @@ ts_status ts_pair_forces_backward(ts_batch* b, ts_state* s, const double* gF, co
  * r_k = (k + 1/2) D, D = rmax / K, width D;
  * g_k = V/(N(N-1)) sum over ordered neighbour pairs with r < rmax + 4D of
  * exp(-(r - r_k)^2 / 2D^2) / (sqrt(2 pi) D 4 pi r_k^2).
- * g [n_systems][K] f64.  Needs rc + skin >= rmax + 4D for every potential. */
+ * g [n_systems][K] f64.  Needs rc + skin >= rmax + 4D for every potential.
+ * TS_ERR_INVALID_ARG for K outside [1, 4096] or above what four warps' rows
+ * of shared memory hold (48 KB): K <= 3072 in mixed precision, K <= 1536 in
+ * FP64 (forward), K <= 3072 for the mixed-precision backward. */
 ts_status ts_rdf(ts_batch* b, ts_state* s, double rmax, int K, double* g, void* stream);
 
 /* gPos [n_atoms][3] += d(sum_{s,k} gg[s][k] g[s][k]) / d pos. */

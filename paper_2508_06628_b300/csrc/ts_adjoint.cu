@@ -274,6 +274,8 @@ __global__ void k_rdf_norm(int32_t B, SysArrays S, double rmax, int K, double* g
 template <bool F64>
 __global__ void k_rdf_bwd(int32_t n_warps, const int32_t* __restrict__ warp_sys, SysArrays S, SlotArrays A,
                           int64_t stride, double rmax, int K, const double* __restrict__ gg) {
+  extern __shared__ __align__(8) unsigned char coef_raw[];
+  int wib = threadIdx.x >> 5;
   int w = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
   int lane = threadIdx.x & 31;
   if (w >= n_warps) return;
@@ -289,36 +291,62 @@ __global__ void k_rdf_bwd(int32_t n_warps, const int32_t* __restrict__ warp_sys,
   const double* ggs = gg + (int64_t)s * K;
   double cut2 = (rmax + 4 * D) * (rmax + 4 * D);
   double gx[3] = {0, 0, 0};
-  for (int q = 0; q < nn; q++) {
-    uint32_t ent = A.nbr[q * stride + k];
-    int64_t j = seg + (ent & kJMask);
-    int code = (int)(ent >> kJBits);
-    double d[3];
-    if constexpr (F64) {
+  if constexpr (F64) {
+    for (int q = 0; q < nn; q++) {
+      uint32_t ent = A.nbr[q * stride + k];
+      int64_t j = seg + (ent & kJMask);
+      int code = (int)(ent >> kJBits);
+      double d[3];
       const double* sh = S.shiftd + 3 * ((int64_t)s * kNCodes + code);
       for (int c = 0; c < 3; c++) d[c] = A.xd[3 * j + c] - A.xd[3 * k + c] + sh[c];
-    } else {
+      double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+      if (!(r2 < cut2)) continue;
+      double r = sqrt(r2);
+      int c = (int)(r / D);
+      double dG = 0;
+      for (int b = c - 8; b <= c + 8; b++) {
+        if (b < 0 || b >= K) continue;
+        double rk = (b + 0.5) * D, t = (r - rk) / D;
+        dG += ggs[b] * pref * exp(-0.5 * t * t) / (rk * rk) * (-t / D);
+      }
+      for (int cc = 0; cc < 3; cc++) gx[cc] -= 2.0 * dG * d[cc] / r;
+    }
+    if (valid) for (int c = 0; c < 3; c++) A.gd0[3 * k + c] = gx[c];
+  } else {
+    // FP32: the per-bin factor gg_b pref / (r_b^2 D) is staged once per warp
+    // in shared memory, so a pair's 17 bins cost one exponential each and no
+    // FP64 arithmetic (a small fraction of the FP32 rate on this part)
+    float* cf = reinterpret_cast<float*>(coef_raw) + wib * K;
+    for (int b = lane; b < K; b += 32) {
+      double rk = (b + 0.5) * D;
+      cf[b] = (float)(ggs[b] * pref / (rk * rk * D));
+    }
+    __syncwarp();
+    const float Df = (float)D, iD = (float)(1.0 / D), cut2f = (float)cut2;
+    float gxf[3] = {0.f, 0.f, 0.f};
+    for (int q = 0; q < nn; q++) {
+      uint32_t ent = __ldg(A.nbr + q * stride + k);
+      int64_t j = seg + (ent & kJMask);
+      int code = (int)(ent >> kJBits);
       int64_t t = (int64_t)s * kNCodes + code;
       float4 a = A.xh[j], b = A.xl[j], ia = A.xh[k], ib = A.xl[k], sh = S.shift[2 * t], sl = S.shift[2 * t + 1];
-      d[0] = ((a.x - ia.x) + sh.x) + ((b.x - ib.x) + sl.x);
-      d[1] = ((a.y - ia.y) + sh.y) + ((b.y - ib.y) + sl.y);
-      d[2] = ((a.z - ia.z) + sh.z) + ((b.z - ib.z) + sl.z);
+      float d0 = ((a.x - ia.x) + sh.x) + ((b.x - ib.x) + sl.x);
+      float d1 = ((a.y - ia.y) + sh.y) + ((b.y - ib.y) + sl.y);
+      float d2 = ((a.z - ia.z) + sh.z) + ((b.z - ib.z) + sl.z);
+      float r2 = d0 * d0 + d1 * d1 + d2 * d2;
+      if (!(r2 < cut2f)) continue;
+      float r = sqrtf(r2);
+      int c = (int)(r * iD);
+      float dG = 0.f;
+      for (int bb = c - 8; bb <= c + 8; bb++) {
+        if (bb < 0 || bb >= K) continue;
+        float tt = (r - (bb + 0.5f) * Df) * iD;
+        dG -= cf[bb] * expf(-0.5f * tt * tt) * tt;
+      }
+      float f = 2.0f * dG / r;
+      gxf[0] -= f * d0; gxf[1] -= f * d1; gxf[2] -= f * d2;
     }
-    double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-    if (!(r2 < cut2)) continue;
-    double r = sqrt(r2);
-    int c = (int)(r / D);
-    double dG = 0;
-    for (int b = c - 8; b <= c + 8; b++) {
-      if (b < 0 || b >= K) continue;
-      double rk = (b + 0.5) * D, t = (r - rk) / D;
-      dG += ggs[b] * pref * exp(-0.5 * t * t) / (rk * rk) * (-t / D);
-    }
-    for (int cc = 0; cc < 3; cc++) gx[cc] -= 2.0 * dG * d[cc] / r;
-  }
-  if (valid) {
-    if constexpr (F64) { for (int c = 0; c < 3; c++) A.gd0[3 * k + c] = gx[c]; }
-    else A.g0[k] = make_float4((float)gx[0], (float)gx[1], (float)gx[2], 0.f);
+    if (valid) A.g0[k] = make_float4(gxf[0], gxf[1], gxf[2], 0.f);
   }
 }
 
@@ -430,13 +458,15 @@ extern "C" ts_status ts_rdf_backward(ts_batch* b, ts_state* s, double rmax, int 
   if (r != TS_OK) return r;
   if (!gg || !gPos) return fail(b, TS_ERR_INVALID_ARG, "null pointer");
   if ((r = rdf_check(b, rmax, K)) != TS_OK) return r;
+  const size_t shm = b->f64 ? 0 : sizeof(float) * (size_t)K * 4;   // per-bin factors, one row per warp
+  if (shm > 48 * 1024) return fail(b, TS_ERR_INVALID_ARG, "K too large");
   cudaStream_t st = (cudaStream_t)stream;
   r = prologue(b, s, st, false);
   if (r != TS_OK) return r;
   relist(b, st, false);
   int blocks = (int)(((int64_t)b->nwarps * 32 + 127) / 128);
   if (b->f64) k_rdf_bwd<true><<<blocks, 128, 0, st>>>(b->nwarps, b->d_warp_sys, b->S, b->A, b->Ncap, rmax, K, gg);
-  else k_rdf_bwd<false><<<blocks, 128, 0, st>>>(b->nwarps, b->d_warp_sys, b->S, b->A, b->Ncap, rmax, K, gg);
+  else k_rdf_bwd<false><<<blocks, 128, shm, st>>>(b->nwarps, b->d_warp_sys, b->S, b->A, b->Ncap, rmax, K, gg);
   int g = egrid(b);
   if (b->f64) k_export_grad<true><<<g, 256, 0, st>>>(b->Npad, b->A, gPos, 1);
   else k_export_grad<false><<<g, 256, 0, st>>>(b->Npad, b->A, gPos, 1);
