@@ -391,6 +391,59 @@ def run_row_fire(args):
                        "n_systems": hb.n_systems, "n_atoms": hb.n_atoms, "fire_steps_per_call": inner}}
 
 
+def run_row_ensemble(args, which):
+    """The other thermostats and barostat on the MD workload (ragged-mix-512 at
+    300 K, dt 1 fs): NVT Nose-Hoover chain (tau 100 fs) or NPT Langevin with the
+    isotropic MTK piston (tau 100 fs, 1 GPa: argon above its critical
+    temperature and the purely repulsive soft spheres would expand without
+    bound at 1 bar), calls of 10 steps timed with CUDA events, L2 flushed
+    before every call as in the default line."""
+    import torch
+    from paper_2508_06628_b300 import ts, workloads as W
+    dev = torch.device("cuda", 0)
+    hb = workload(seed=1)
+    pots = [dict(p, skin=s) for p, s in zip(hb.pots, ts.default_skins(hb.pots))]
+    b = ts.Batch(pots, hb.n_atoms, hb.n_systems, precision=ts.TS_MIXED, device=0)
+    s = ts.DeviceState.from_host(hb, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    dt, gamma, tau = hb.meta["dt"], hb.meta["gamma"], 100.0 / W.T0_FS
+    kw = dict(kind=ts.TS_NVT_NHC, tau=tau, nhc=torch.zeros((hb.n_systems, 6), dtype=torch.float64, device=dev)) \
+        if which == "nhc" else \
+        dict(kind=ts.TS_NPT_LANGEVIN, gamma=gamma, tau=tau, p_ext=1.0 / 160.21766208,   # 1 GPa in eV/A^3
+             baro=torch.zeros(hb.n_systems, dtype=torch.float64, device=dev))
+    inner = 10
+    ncalls = max(1, min(args.steps, 1000) // inner)
+    stream = torch.cuda.Stream(device=dev)
+    step = 0
+    with torch.cuda.stream(stream):
+        b.neighbor_build(s, force=True, stream=stream)
+        for _ in range(max(args.warmup, 3)):
+            b.md_step(s, inner, dt, seed=5, step0=step, stream=stream, **kw)
+            step += inner
+        stream.synchronize()
+        l0, r0 = b.counters()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(ncalls)]
+        for c in range(ncalls):
+            flush.fill_(c & 0xff)
+            evs[c][0].record(stream)
+            b.md_step(s, inner, dt, seed=5, step0=step, stream=stream, **kw)
+            evs[c][1].record(stream)
+            step += inner
+        stream.synchronize()
+        l1, r1 = b.counters()
+    ms = sum(a.elapsed_time(e) for a, e in evs) / (ncalls * inner)
+    b.poll()
+    b.close()
+    name = {"nhc": "NVT Nose-Hoover chain", "npt": "NPT Langevin (isotropic MTK piston)"}[which]
+    return _line(f"batched MD atom-steps/s, {name}", hb.n_atoms / (ms / 1e3), UNIT, ms, ncalls * inner,
+                 max(args.warmup, 3), "f32",
+                 {"workload": "ragged-mix-512 (as the default line), 300 K, dt 1 fs, tau 100 fs" +
+                              (", 1 GPa" if which == "npt" else ""), "n_systems": hb.n_systems,
+                  "n_atoms": hb.n_atoms, "md_steps_per_call": inner,
+                  "l2": "flushed (256 MiB write) before every call, outside the timed events"},
+                 row=which, gpu_launches=l1 - l0, relists_in_timed_region=r1 - r0)
+
+
 def _line(metric, value, unit, ms, steps, warmup, dtype, config, **extra):
     d = {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": steps, "warmup": warmup,
          "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
@@ -598,12 +651,14 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-loop", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--row", default="md", choices=["md", "adjoint", "fire", "nve256", "inflight", "diff", "large"],
+    ap.add_argument("--row", default="md", choices=["md", "adjoint", "fire", "nve256", "inflight", "diff", "large",
+                                                    "nhc", "npt"],
                     help="md: the MD step (the default line); the others: other rows and workloads, one GPU")
     args = ap.parse_args()
     if args.row != "md":
         rows = {"adjoint": run_row_adjoint, "fire": run_row_fire, "nve256": run_row_nve256,
-                "inflight": run_row_inflight, "diff": run_row_diff, "large": run_row_large}
+                "inflight": run_row_inflight, "diff": run_row_diff, "large": run_row_large,
+                "nhc": lambda a: run_row_ensemble(a, "nhc"), "npt": lambda a: run_row_ensemble(a, "npt")}
         print(json.dumps(rows[args.row](args)))
         return
     rank = int(os.environ.get("RANK", 0))
