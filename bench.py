@@ -556,18 +556,22 @@ def run_row_diff(args):
     grad.set_params(b, np.array([[1.05, 1.0, 0.0]]))
     target, _ = grad.trajectory_rdf(b, s, 0.005, T, every, rmax, K)
     grad.set_params(b, np.array([[1.0, 1.0, 0.0]]))
-    # warm-up: one 200-step evaluation (the first use of each PyTorch kernel on
-    # the device costs far more than its run); its gradient is reported too,
-    # beside the 2000-step one, to show how the adjoint of a chaotic
-    # trajectory grows with its length
-    _, _, g200 = grad.rdf_loss_and_grad(b, s, 0.005, 200, every, rmax, K, target, checkpoint=100)
-    g200 = g200.cpu().numpy()
+    # on a stream of its own, so that the MD calls replay their CUDA graphs
+    stream = torch.cuda.Stream(device=dev)
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    loss, g, gth = grad.rdf_loss_and_grad(b, s, 0.005, T, every, rmax, K, target, checkpoint=100)
-    gh = gth.cpu().numpy()
-    torch.cuda.synchronize()
-    t = time.perf_counter() - t0
+    with torch.cuda.stream(stream):
+        # warm-up: one 200-step evaluation (the first use of each PyTorch kernel
+        # on the device costs far more than its run); its gradient is reported
+        # too, beside the 2000-step one, to show how the adjoint of a chaotic
+        # trajectory grows with its length
+        _, _, g200 = grad.rdf_loss_and_grad(b, s, 0.005, 200, every, rmax, K, target, checkpoint=100)
+        g200 = g200.cpu().numpy()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        loss, g, gth = grad.rdf_loss_and_grad(b, s, 0.005, T, every, rmax, K, target, checkpoint=100)
+        gh = gth.cpu().numpy()
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
     b.poll()
     b.close()
     out = _line("trajectory-gradient atom-steps/s (NVE forward + checkpointed adjoint)", hb.n_atoms * T / t, UNIT,
