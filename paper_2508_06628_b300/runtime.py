@@ -134,14 +134,20 @@ def relax_inflight(hb, pots, max_scaler, max_active=1024, n_inner=25, precision=
             on_round(log[-1])
         done = np.nonzero(c)[0]
         if len(done):
-            Eh, fmh, smh = E.cpu().numpy(), fm.cpu().numpy(), sm.cpu().numpy()
-            offs = np.concatenate([[0], np.cumsum([n_of[i] for i in ids_active])])
-            posh = buf.pos[:buf.n_atoms].cpu().numpy()
-            cellh = buf.cell[:buf.n_systems].cpu().numpy()
-            for k in done:
+            # gather the converged systems' rows on the device and copy only those
+            offs = np.concatenate([[0], np.cumsum(n_of[np.asarray(ids_active, dtype=np.int64)])])
+            didx = torch.as_tensor(done, device=dev)
+            sc = torch.stack([E[didx], fm[didx], sm[didx]]).cpu().numpy()
+            cellh = buf.cell[didx].cpu().numpy()
+            rows = np.concatenate([np.arange(offs[k], offs[k + 1]) for k in done])
+            posh = buf.pos[torch.as_tensor(rows, device=dev)].cpu().numpy()
+            o = 0
+            for m, k in enumerate(done):
                 i = ids_active[k]
-                results[i] = dict(E=Eh[k], fmax=fmh[k], smax=smh[k], cell=cellh[k], pos=posh[offs[k]:offs[k + 1]],
+                n = int(offs[k + 1] - offs[k])
+                results[i] = dict(E=sc[0, m], fmax=sc[1, m], smax=sc[2, m], cell=cellh[m], pos=posh[o:o + n],
                                   round=rnd)
+                o += n
             arr = (C.c_int64 * len(done))(*[ids_active[k] for k in done])
             assert L.ts_sched_retire(q, arr, len(done)) == 0
         keep[:buf.n_systems] = (~c).astype(np.uint8)
