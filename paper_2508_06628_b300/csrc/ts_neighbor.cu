@@ -65,9 +65,31 @@ __device__ __forceinline__ void import_vel_slot(SlotArrays& A, int64_t k, int p,
     h.x = (float)v0; l.x = (float)(v0 - (double)h.x);
     h.y = (float)v1; l.y = (float)(v1 - (double)h.y);
     h.z = (float)v2; l.z = (float)(v2 - (double)h.z);
-    h.w = (float)(1.0 / m); l.w = 0.f;
+    h.w = 1.0f / (float)m; l.w = 0.f;   // FP32 divide: no FP64 on the mixed import
     A.vh[k] = h; A.vl[k] = l;
   }
+}
+
+// Along periodic axes a position is defined modulo the lattice.  For an
+// imported position that lies beyond the skin of its listing reference (e its
+// displacement from it), take the image nearest the reference: unwrapped
+// coordinates (a stored trajectory, a caller's own integrator) are the same
+// configuration and cost no re-listing.  The lattice vector is chosen in FP32
+// and applied to x in FP64; returns whether x moved.
+__device__ __forceinline__ bool lattice_image(const SysArrays& S, int s, float e0, float e1, float e2, double& x0,
+                                              double& x1, double& x2) {
+  const int pm = S.pmask[s];
+  if (!pm) return false;
+  const float* g = S.hinvf + 9 * s;
+  int n[3];
+  for (int a = 0; a < 3; a++)
+    n[a] = (pm >> a & 1) ? (int)rintf(fmaf(e0, g[a], fmaf(e1, g[3 + a], e2 * g[6 + a]))) : 0;
+  if (!(n[0] | n[1] | n[2])) return false;
+  const double* h = S.h + 9 * s;
+  x0 -= n[0] * h[0] + n[1] * h[3] + n[2] * h[6];
+  x1 -= n[0] * h[1] + n[1] * h[4] + n[2] * h[7];
+  x2 -= n[0] * h[2] + n[1] * h[5] + n[2] * h[8];
+  return true;
 }
 
 // with_vel: velocities and inverse masses too (MD calls), in the same pass
@@ -86,40 +108,27 @@ __global__ void k_import_pos(int64_t Npad, SysArrays S, SlotArrays A, const doub
       atomicOr(err, kErrNonFinite);
       continue;
     }
-    // Along periodic axes a position is defined modulo the lattice: take the
-    // image of the caller's position nearest the slot's listing reference, so
-    // that unwrapped coordinates (a stored trajectory, a caller's own
-    // integrator) cost no re-listing.  The lattice vector is chosen in FP32
-    // and applied in FP64, only when it is not zero.
-    if (check_skin && S.pmask[s]) {
-      double r0, r1, r2;
-      if constexpr (F64) {
-        r0 = A.xrd[3 * k]; r1 = A.xrd[3 * k + 1]; r2 = A.xrd[3 * k + 2];
-      } else {
-        const float4 rh = A.xrh[k], rl = A.xrl[k];
-        r0 = (double)rh.x + (double)rl.x; r1 = (double)rh.y + (double)rl.y; r2 = (double)rh.z + (double)rl.z;
-      }
-      const float e0 = (float)(x0 - r0), e1 = (float)(x1 - r1), e2 = (float)(x2 - r2);
-      const float* g = S.hinvf + 9 * s;
-      const int pm = S.pmask[s];
-      int n[3];
-      for (int a = 0; a < 3; a++)
-        n[a] = (pm >> a & 1) ? (int)rintf(fmaf(e0, g[a], fmaf(e1, g[3 + a], e2 * g[6 + a]))) : 0;
-      if (n[0] | n[1] | n[2]) {
-        const double* h = S.h + 9 * s;
-        x0 -= n[0] * h[0] + n[1] * h[3] + n[2] * h[6];
-        x1 -= n[0] * h[1] + n[1] * h[4] + n[2] * h[7];
-        x2 -= n[0] * h[2] + n[1] * h[5] + n[2] * h[8];
-      }
-    }
     bool changed;
-    double dx, dy, dz;
+    const DevPot& P = pots[S.pot[s]];
     if constexpr (F64) {
       double* xd = A.xd + 3 * k;
       changed = (xd[0] != x0) || (xd[1] != x1) || (xd[2] != x2);
       if (changed) { xd[0] = x0; xd[1] = x1; xd[2] = x2; }
-      const double* xr = A.xrd + 3 * k;
-      dx = x0 - xr[0]; dy = x1 - xr[1]; dz = x2 - xr[2];
+      if (check_skin) {
+        const double* xr = A.xrd + 3 * k;
+        double dx = x0 - xr[0], dy = x1 - xr[1], dz = x2 - xr[2];
+        double sk = 0.5 * P.skin, d2 = dx * dx + dy * dy + dz * dz;
+        if (d2 > sk * sk && lattice_image(S, s, (float)dx, (float)dy, (float)dz, x0, x1, x2)) {
+          xd[0] = x0; xd[1] = x1; xd[2] = x2;
+          dx = x0 - xr[0]; dy = x1 - xr[1]; dz = x2 - xr[2];
+          d2 = dx * dx + dy * dy + dz * dz;
+        }
+        if (d2 > sk * sk) { S.relist[s] = 1; S.any[0] = 1; }
+        else if (d2 > P.soon2 * sk * sk) S.soon[s] = 1;
+        const double* xp = A.xpd + 3 * k;
+        double p0 = x0 - xp[0], p1 = x1 - xp[1], p2 = x2 - xp[2];
+        if (p0 * p0 + p1 * p1 + p2 * p2 > P.half_in2d) S.prune[s] = 1;
+      }
     } else {
       // unchanged when the caller's value is the one the slot holds (the
       // double the export wrote), whatever its hi/lo split
@@ -131,28 +140,25 @@ __global__ void k_import_pos(int64_t Npad, SysArrays S, SlotArrays A, const doub
         h.w = 0.f; l.w = 0.f;
         A.xh[k] = h; A.xl[k] = l;
       }
-      float4 rh = A.xrh[k], rl = A.xrl[k];
-      dx = (double)((h.x - rh.x) + (l.x - rl.x));
-      dy = (double)((h.y - rh.y) + (l.y - rl.y));
-      dz = (double)((h.z - rh.z) + (l.z - rl.z));
+      if (check_skin) {
+        // the skin and refresh tests in FP32, with the thresholds the kick uses
+        const float4 rh = A.xrh[k], rl = A.xrl[k];
+        float ex = (h.x - rh.x) + (l.x - rl.x), ey = (h.y - rh.y) + (l.y - rl.y), ez = (h.z - rh.z) + (l.z - rl.z);
+        float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+        if (d2 > P.half_skin2f && lattice_image(S, s, ex, ey, ez, x0, x1, x2)) {
+          split_pos(x0, h.x, l.x); split_pos(x1, h.y, l.y); split_pos(x2, h.z, l.z);
+          A.xh[k] = h; A.xl[k] = l;
+          ex = (h.x - rh.x) + (l.x - rl.x); ey = (h.y - rh.y) + (l.y - rl.y); ez = (h.z - rh.z) + (l.z - rl.z);
+          d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+        }
+        if (d2 > P.half_skin2f) { S.relist[s] = 1; S.any[0] = 1; }
+        else if (d2 > P.soon_half_skin2f) S.soon[s] = 1;
+        const float4 ph = A.xph[k], pl = A.xpl[k];
+        const float q0 = (h.x - ph.x) + (l.x - pl.x), q1 = (h.y - ph.y) + (l.y - pl.y), q2 = (h.z - ph.z) + (l.z - pl.z);
+        if (fmaf(q0, q0, fmaf(q1, q1, q2 * q2)) > P.half_in2f) S.prune[s] = 1;
+      }
     }
     if (changed) S.dirty[s] = 1;
-    if (check_skin) {
-      double sk = 0.5 * pots[S.pot[s]].skin, d2 = dx * dx + dy * dy + dz * dz;
-      if (d2 > sk * sk) { S.relist[s] = 1; S.any[0] = 1; }
-      else if (d2 > pots[S.pot[s]].soon2 * sk * sk) S.soon[s] = 1;
-      double p0, p1, p2;
-      if constexpr (F64) {
-        const double* xp = A.xpd + 3 * k;
-        p0 = x0 - xp[0]; p1 = x1 - xp[1]; p2 = x2 - xp[2];
-      } else {
-        const float4 h = A.xh[k], l = A.xl[k], ph = A.xph[k], pl = A.xpl[k];
-        p0 = (double)((h.x - ph.x) + (l.x - pl.x));
-        p1 = (double)((h.y - ph.y) + (l.y - pl.y));
-        p2 = (double)((h.z - ph.z) + (l.z - pl.z));
-      }
-      if (p0 * p0 + p1 * p1 + p2 * p2 > pots[S.pot[s]].half_in2d) S.prune[s] = 1;
-    }
   }
 }
 
