@@ -298,6 +298,20 @@ ts_status ts_rdf_backward(ts_batch* b, ts_state* s, double rmax, int K, const do
 ts_status ts_vv_adjoint_step(ts_batch* b, ts_state* s, const double* x_next, double dt, double* ax, double* av,
                              double* gParams, void* stream);
 
+/* The reverse of n NVE steps over stored frames, as n calls of
+ * ts_vv_adjoint_step issued from the library (no per-step host round trip
+ * through the caller).  frames [n+1][n_atoms][3] f64 (device, caller order)
+ * hold x_{t0}, ..., x_{t0+n}; ax, av (device, in/out) hold dL/dx, dL/dv at
+ * t0+n on entry and at t0 on return; gParams [n_pots][3] (device) accumulates.
+ * With rdf_every > 0, before the reverse step out of frame t0+m (m = n ... 1)
+ * with (t0+m) % rdf_every == 0, the gradient of sum_{s,k} gg[s][k] g_k(x_{t0+m})
+ * (ts_rdf_backward with rmax, K; gg [n_systems][K] f64, device) is added to
+ * ax.  s supplies masses, cells, pbc and the topology; s->pos and s->vel are
+ * not read.  Errors as ts_vv_adjoint_step and ts_rdf_backward; n >= 1. */
+ts_status ts_vv_adjoint_segment(ts_batch* b, ts_state* s, const double* frames, int n, int64_t t0, double dt,
+                                double* ax, double* av, double* gParams, int rdf_every, double rmax, int K,
+                                const double* gg, void* stream);
+
 /* ---- in-flight batching runtime (Sec. 3, Figs. 2-3) ---------------------- */
 
 /* Memory scaler of one system: n_atoms (model memory fixed per atom) or

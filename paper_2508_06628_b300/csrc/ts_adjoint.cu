@@ -508,3 +508,27 @@ extern "C" ts_status ts_vv_adjoint_step(ts_batch* b, ts_state* s, const double* 
   b->launches++;
   return cuda_ok(b, cudaGetLastError(), "ts_vv_adjoint_step") ? TS_OK : TS_ERR_CUDA;
 }
+
+extern "C" ts_status ts_vv_adjoint_segment(ts_batch* b, ts_state* s, const double* frames, int n, int64_t t0,
+                                           double dt, double* ax, double* av, double* gParams, int rdf_every,
+                                           double rmax, int K, const double* gg, void* stream) {
+  ts_status r = check_state(b, s, false);
+  if (r != TS_OK) return r;
+  if (!frames || n < 1 || !ax || !av || !gParams || (rdf_every > 0 && !gg))
+    return fail(b, TS_ERR_INVALID_ARG, "bad adjoint segment arguments");
+  const int64_t stride = 3 * (int64_t)s->n_atoms;
+  for (int m = n; m >= 1; m--) {
+    const double* xn = frames + (int64_t)m * stride;
+    if (rdf_every > 0 && (t0 + m) % rdf_every == 0) {
+      ts_state sn = *s;
+      sn.pos = const_cast<double*>(xn);
+      sn.vel = nullptr;
+      if ((r = ts_rdf_backward(b, &sn, rmax, K, gg, ax, stream)) != TS_OK) return r;
+    }
+    ts_state st = *s;
+    st.pos = const_cast<double*>(frames + (int64_t)(m - 1) * stride);
+    st.vel = nullptr;
+    if ((r = ts_vv_adjoint_step(b, &st, xn, dt, ax, av, gParams, stream)) != TS_OK) return r;
+  }
+  return TS_OK;
+}

@@ -114,24 +114,22 @@ def rdf_loss_and_grad(batch, state, dt, T, every, rmax, K, target, checkpoint=10
     av = torch.zeros_like(ax)
     gth = torch.zeros((len(batch.pots), 3), dtype=torch.float64, device=g.device)
     bounds = [c[0] for c in ckpts] + [T]
+    frames = None
     for seg in range(len(ckpts) - 1, -1, -1):
         t0, x0, v0 = ckpts[seg]
         t1 = bounds[seg + 1]
-        xs = [x0.clone()]
+        # the segment recomputed forward, every frame kept, then reversed step
+        # by step in the library (RDF gradients at the observed frames)
+        if frames is None or frames.shape[0] < t1 - t0 + 1:
+            frames = torch.empty((t1 - t0 + 1, N, 3), dtype=torch.float64, device=g.device)
+        fr = frames[:t1 - t0 + 1]
+        fr[0].copy_(x0)
         s = ts.DeviceState(x0.clone(), v0.clone(), state.mass, state.cell, state.pbc, state.system_idx,
                            state.pot_idx, state.uid)
         for t in range(t0, t1):
             batch.md_step(s, 1, dt, kind=ts.TS_NVE)
-            xs.append(s.pos.clone())
-        for t in range(t1 - 1, t0 - 1, -1):
-            xn = xs[t + 1 - t0]
-            if (t + 1) % every == 0:
-                sn = ts.DeviceState(xn, None, state.mass, state.cell, state.pbc, state.system_idx, state.pot_idx,
-                                    state.uid)
-                batch.rdf_backward(sn, rmax, K, gg, ax)
-            st = ts.DeviceState(xs[t - t0], None, state.mass, state.cell, state.pbc, state.system_idx,
-                                state.pot_idx, state.uid)
-            batch.vv_adjoint_step(st, xn, dt, ax, av, gth)
+            fr[t + 1 - t0].copy_(s.pos)
+        batch.vv_adjoint_segment(state, fr, t0, dt, ax, av, gth, rdf_every=every, rmax=rmax, K=K, gg=gg)
     return loss, g, gth
 
 

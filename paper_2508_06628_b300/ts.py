@@ -92,6 +92,8 @@ def lib():
         L.ts_rdf.argtypes = [P, C.POINTER(State), C.c_double, I, P, P]
         L.ts_rdf_backward.argtypes = [P, C.POINTER(State), C.c_double, I, P, P, P]
         L.ts_vv_adjoint_step.argtypes = [P, C.POINTER(State), P, C.c_double, P, P, P, P]
+        L.ts_vv_adjoint_segment.argtypes = [P, C.POINTER(State), P, I, C.c_int64, C.c_double, P, P, P, I, C.c_double,
+                                            I, P, P]
         L.ts_batch_poll.argtypes = [P, P, I]
         L.ts_autotune.argtypes = [P, C.POINTER(State), P]
         L.ts_batch_counters.argtypes = [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
@@ -269,6 +271,15 @@ class Batch:
     def vv_adjoint_step(self, s, x_next, dt, ax, av, gParams, stream=None):
         self._check(lib().ts_vv_adjoint_step(self.h, C.byref(s.c()), _ptr(x_next), float(dt), _ptr(ax), _ptr(av),
                                              _ptr(gParams), _stream(stream)), "ts_vv_adjoint_step")
+
+    def vv_adjoint_segment(self, s, frames, t0, dt, ax, av, gParams, rdf_every=0, rmax=0.0, K=0, gg=None,
+                           stream=None):
+        """Reverse of len(frames) - 1 NVE steps over frames [n+1, n_atoms, 3]
+        (f64 device tensor holding x_t0 ... x_t0+n); see ts.h."""
+        n = int(frames.shape[0]) - 1
+        self._check(lib().ts_vv_adjoint_segment(self.h, C.byref(s.c()), _ptr(frames), n, int(t0), float(dt),
+                                                _ptr(ax), _ptr(av), _ptr(gParams), int(rdf_every), float(rmax),
+                                                int(K), _ptr(gg), _stream(stream)), "ts_vv_adjoint_segment")
 
     def autotune(self, s, stream=None):
         self._check(lib().ts_autotune(self.h, C.byref(s.c()), _stream(stream)), "ts_autotune")

@@ -150,3 +150,54 @@ def test_pair_forces_autograd_function(orc):
         Es.append(E2.sum().item())
     fd = (Es[0] - Es[1]) / (2 * h * params[0, 1].item())
     assert params.grad[0, 1].item() == pytest.approx(fd, rel=1e-6)
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_adjoint_segment_equals_step_loop(precision):
+    """ts_vv_adjoint_segment over 30 stored frames with RDF gradients at every
+    10th frame gives, bit for bit, the adjoints and parameter gradient of the
+    same reverse steps issued one call at a time."""
+    torch = torch_cuda()
+    from paper_2508_06628_b300 import ts
+    hb = W.lj_liquid(seed=5, n_systems=3, reps=(2, 2, 3), rattle=0.08, kT=0.5)
+    pot = dict(W.LJ_REDUCED, skin=0.4)
+    K, rmax, dt, n, every, t0 = 50, 2.5, 0.005, 30, 10, 40
+    rng = np.random.default_rng(11)
+    gg = torch.as_tensor(rng.normal(size=(hb.n_systems, K)), device="cuda")
+    ax0 = torch.as_tensor(rng.normal(size=(hb.n_atoms, 3)), device="cuda")
+    av0 = torch.as_tensor(rng.normal(size=(hb.n_atoms, 3)), device="cuda")
+
+    def setup():
+        b = ts.Batch([pot], hb.n_atoms, hb.n_systems, precision=precision)
+        s = ts.DeviceState.from_host(hb)
+        b.neighbor_build(s, force=True)
+        frames = torch.empty((n + 1, hb.n_atoms, 3), dtype=torch.float64, device="cuda")
+        frames[0].copy_(s.pos)
+        for m in range(1, n + 1):
+            b.md_step(s, 1, dt, kind=ts.TS_NVE)
+            frames[m].copy_(s.pos)
+        return b, s, frames
+
+    b, s, frames = setup()
+    ax, av = ax0.clone(), av0.clone()
+    gth = torch.zeros((1, 3), dtype=torch.float64, device="cuda")
+    b.vv_adjoint_segment(s, frames, t0, dt, ax, av, gth, rdf_every=every, rmax=rmax, K=K, gg=gg)
+    b.poll()
+    res_seg = ax.cpu().numpy(), av.cpu().numpy(), gth.cpu().numpy()
+    b.close()
+
+    b, s, frames = setup()
+    ax, av = ax0.clone(), av0.clone()
+    gth = torch.zeros((1, 3), dtype=torch.float64, device="cuda")
+    for m in range(n, 0, -1):
+        if (t0 + m) % every == 0:
+            sn = ts.DeviceState(frames[m], None, s.mass, s.cell, s.pbc, s.system_idx, s.pot_idx, s.uid)
+            b.rdf_backward(sn, rmax, K, gg, ax)
+        st = ts.DeviceState(frames[m - 1], None, s.mass, s.cell, s.pbc, s.system_idx, s.pot_idx, s.uid)
+        b.vv_adjoint_step(st, frames[m], dt, ax, av, gth)
+    b.poll()
+    res_loop = ax.cpu().numpy(), av.cpu().numpy(), gth.cpu().numpy()
+    b.close()
+    assert np.abs(res_seg[0]).max() > 0 and np.abs(res_seg[2]).max() > 0
+    for a, c in zip(res_seg, res_loop):
+        assert np.array_equal(a, c)
