@@ -526,7 +526,10 @@ void relist_lists(ts_batch* b, cudaStream_t st, bool move_fire, int prio) {
 // end of a re-listing pass: flag bookkeeping.  md_pass: the pass's pair
 // launches ran in inner-list mode and refreshed every flagged system.
 void relist_finish(ts_batch* b, cudaStream_t st, bool md_pass) {
-  k_after_relist<<<(b->B + 127) / 128, 128, 0, st>>>(b->B, b->S, b->d_counters, md_pass ? 1 : 0);
+  // one CTA up to 1024 systems (the end-of-pass flag clear then needs no
+  // cross-CTA arrival), CTAs of 128 above
+  const int t = b->B <= 1024 ? std::max(32, (b->B + 31) / 32 * 32) : 128;
+  k_after_relist<<<(b->B + t - 1) / t, t, 0, st>>>(b->B, b->S, b->d_counters, md_pass ? 1 : 0);
   b->launches++;
 }
 

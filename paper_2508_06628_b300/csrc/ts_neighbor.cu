@@ -531,13 +531,14 @@ __global__ void k_copy_back(int64_t Npad, SysArrays S, SlotArrays A, int move_fi
 // per-system flag bookkeeping after a listing: the re-listed systems' forces are stale
 __global__ void k_after_relist(int32_t B, SysArrays S, int64_t* counters, int md_pass) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
+  bool refreshed = false, re = false;
   if (s < B) {
     // inner lists: an MD pass's pair launches refreshed every flagged or
     // re-listed system (counted in counters[1]); after any other pass a
     // re-listed system's inner list is stale until the next MD pass
-    const bool re = need_relist(S, s);
+    re = need_relist(S, s);
     if (md_pass) {
-      if (S.prune[s] || re) atomicAdd((unsigned long long*)(counters + 1), 1ull);
+      refreshed = S.prune[s] || re;
       S.prune[s] = 0;
     } else if (re) {
       S.prune[s] = 1;
@@ -548,8 +549,13 @@ __global__ void k_after_relist(int32_t B, SysArrays S, int64_t* counters, int md
       S.relist[s] = 0;
       S.soon[s] = 0;
       for (int q = 0; q < 9; q++) S.href[9 * s + q] = S.h[9 * s + q];
-      atomicAdd((unsigned long long*)counters, 1ull);
     }
+  }
+  // the counts, one atomic per warp (a mass re-listing flags most systems)
+  const unsigned nref = __popc(__ballot_sync(0xffffffffu, refreshed)), nre = __popc(__ballot_sync(0xffffffffu, re));
+  if ((threadIdx.x & 31) == 0) {
+    if (nref) atomicAdd((unsigned long long*)(counters + 1), (unsigned long long)nref);
+    if (nre) atomicAdd((unsigned long long*)counters, (unsigned long long)nre);
   }
   // end of the pass: the last block to finish clears the batch-wide flag,
   // once every block has read it (counters[3]: a wrapping block counter)
