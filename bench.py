@@ -34,7 +34,7 @@ BYTES_PER_ATOM = 32         # read own position, write own force, per atom-step
 # DRAM bytes (read + write) of one forces-only k_pair_small launch (inner lists) on ragged-mix-512, from one ncu
 # capture (profiles/k_pair_small_ragged_mix_512.md); reported only while the kernel's sources
 # (ts_pair.cu, then ts_internal.cuh) hash to the value recorded with the capture
-PAIR_TRAFFIC = {"bytes": 49_636_352 + 126_464, "source_sha1": "ab71ef60858f2256349fefc5c6e4b3e2e3f1c2ea"}
+PAIR_TRAFFIC = {"bytes": 49_635_328 + 141_568, "source_sha1": "ae957e3d43a62579a69c8983c13f37923a1164ca"}
 
 
 def pair_traffic():

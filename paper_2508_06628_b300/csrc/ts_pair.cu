@@ -218,11 +218,14 @@ __global__ void __launch_bounds__(kPairSmallThreads) k_pair_small(
       const bool img = code != kCenter;
       const uint4 sh = img ? __ldg(tab + code) : make_uint4(0, 0, 0, 0);
       const uint4 xj = hq[j];
-      // exact integer pair vector (modulo 2^32), one rounding to FP32
-      const float d0 = (float)(int)(xj.x - xi.x + sh.x) * kFixInv;
-      const float d1 = (float)(int)(xj.y - xi.y + sh.y) * kFixInv;
-      const float d2 = (float)(int)(xj.z - xi.z + sh.z) * kFixInv;
-      const float r2 = fmaf(d0, d0, fmaf(d1, d1, d2 * d2));
+      // exact integer pair vector (modulo 2^32), one rounding to FP32; kept in
+      // fixed-point units, the power-of-two scale applied once to r^2 and once
+      // to the force factor (scaling by 2^k commutes with FP32 rounding, so
+      // r^2 and the force sums are bit-identical to scaling each component)
+      const float u0 = (float)(int)(xj.x - xi.x + sh.x);
+      const float u1 = (float)(int)(xj.y - xi.y + sh.y);
+      const float u2 = (float)(int)(xj.z - xi.z + sh.z);
+      const float r2 = fmaf(u0, u0, fmaf(u1, u1, u2 * u2)) * (kFixInv * kFixInv);
       const bool in = r2 < P.rc2f;
       if (R) {   // inner list: within rc + inner skin (+ 1e-3 A), in list order
         if (r2 < P.rin2f) A.nbr_in[(int64_t)cin * stride + k] = ent;
@@ -231,8 +234,10 @@ __global__ void __launch_bounds__(kPairSmallThreads) k_pair_small(
       float phi, fr;
       PotMath<float>::eval_k<K>(P, r2, phi, fr);
       fr = in ? fr : 0.f;
-      f0 = fmaf(fr, d0, f0); f1 = fmaf(fr, d1, f1); f2 = fmaf(fr, d2, f2);
+      const float fu = fr * kFixInv;
+      f0 = fmaf(fu, u0, f0); f1 = fmaf(fu, u1, f1); f2 = fmaf(fu, u2, f2);
       if (EW) {
+        const float d0 = u0 * kFixInv, d1 = u1 * kFixInv, d2 = u2 * kFixInv;
         e += in ? 0.5f * (phi - P.phicf) : 0.f;
         float hf = 0.5f * fr;
         float h0 = hf * d0, h1 = hf * d1;
