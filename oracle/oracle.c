@@ -214,7 +214,7 @@ static void for_pairs_cells(int N, const double* x, const double* h, double rmax
   for (int c = 0; c <= nc; c++) head[c] = 0;
   for (int i = 0; i < N; i++) head[cell[i] + 1]++;
   for (int c = 0; c < nc; c++) head[c + 1] += head[c];
-  { int* fill = (int*)calloc(nc, sizeof(int));
+  { int* fill = (int*)calloc((size_t)(nc > 0 ? nc : 1), sizeof(int));
     for (int i = 0; i < N; i++) list[head[cell[i]] + fill[cell[i]]++] = i;
     free(fill); }
   for (int i = 0; i < N; i++) {
