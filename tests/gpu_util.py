@@ -34,10 +34,25 @@ def frac_diff(x, y, cell, offsets):
     return out
 
 
-def force_tolerance_ok(F, Fref, offsets, fp64):
+# Mixed precision: the smallest fraction of atoms that must also meet the
+# per-atom bound |dF_i| <= max(1e-5 |F_i|, 1e-6), by potential kind (LJ, Morse,
+# soft sphere).  The rest may miss it only where FP32 pair arithmetic cannot
+# reach it: an atom whose large pair forces cancel (one FP32 rounding of r
+# moves a Morse pair force by ~6e-7 eV/A).
+MIXED_PER_ATOM_FLOOR = {0: 0.999, 1: 0.99, 2: 0.999}
+
+
+def kinds_of(hb):
+    """Potential kind of every system of a workloads.Batch."""
+    return [int(hb.pots[p]["kind"]) for p in hb.pot_idx]
+
+
+def force_tolerance_ok(F, Fref, offsets, fp64, kinds=None):
     """FP64 mode: per atom |dF_i| <= max(1e-5 |F_i|, 1e-6).  Mixed mode (FP32
-    pair arithmetic): per system max_i |dF_i| <= max(1e-5 max_i |F_i|, 1e-6);
-    returns (ok, worst ratio, fraction of atoms passing the per-atom bound)."""
+    pair arithmetic): per system max_i |dF_i| <= max(1e-5 max_i |F_i|, 1e-6),
+    and, when the systems' potential kinds are given, at least
+    MIXED_PER_ATOM_FLOOR[kind] of each kind's atoms within the per-atom bound.
+    Returns (ok, worst ratio, fraction of atoms passing the per-atom bound)."""
     err = np.linalg.norm(F - Fref, axis=1)
     nrm = np.linalg.norm(Fref, axis=1)
     per_atom = err <= np.maximum(1e-5 * nrm, 1e-6)
@@ -49,7 +64,14 @@ def force_tolerance_ok(F, Fref, offsets, fp64):
         a, b = offsets[s], offsets[s + 1]
         tol = max(1e-5 * nrm[a:b].max(), 1e-6)
         worst = max(worst, err[a:b].max() / tol)
-    return worst <= 1.0, float(worst), float(per_atom.mean())
+    ok = worst <= 1.0
+    if kinds is not None:
+        kind_of_atom = np.repeat(np.asarray(kinds), np.diff(offsets))
+        for k, floor in MIXED_PER_ATOM_FLOOR.items():
+            sel = kind_of_atom == k
+            if sel.any() and per_atom[sel].mean() < floor:
+                ok = False
+    return ok, float(worst), float(per_atom.mean())
 
 
 def small_mix(seed, n_systems=10, lo=32, hi=400):

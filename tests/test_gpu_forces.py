@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 
 from paper_2508_06628_b300 import workloads as W
-from tests.gpu_util import force_tolerance_ok, frac_diff, make_batch, small_mix, torch_cuda
+from tests.gpu_util import force_tolerance_ok, kinds_of, frac_diff, make_batch, small_mix, torch_cuda
 
 pytestmark = pytest.mark.gpu
 
@@ -31,7 +31,7 @@ def test_pair_forces_parity(orc, precision, seed):
     # the wrapped positions are the input positions up to lattice vectors
     assert np.abs(frac_diff(pos, hb.pos, hb.cell, hb.offsets)).max() < 1e-9
     Er, Fr, Sr = orc.forces(hb.offsets, pos, hb.cell, hb.pbc, hb.pot_idx, hb.pots)
-    ok, worst, frac = force_tolerance_ok(F, Fr, hb.offsets, precision == 1)
+    ok, worst, frac = force_tolerance_ok(F, Fr, hb.offsets, precision == 1, kinds=kinds_of(hb))
     assert ok, (worst, frac)
     if precision == 1:
         assert np.allclose(E, Er, rtol=1e-9, atol=1e-12)
@@ -106,7 +106,7 @@ def test_edge_cases(orc, precision):
     hb = W.concat(systems, [W.LJ_AR, W.MORSE_CU, W.SOFT_SPHERE])
     b, s, F, E, S, pos = run_forces(hb, precision, max_neighbors=256)
     Er, Fr, Sr = orc.forces(hb.offsets, pos, hb.cell, hb.pbc, hb.pot_idx, hb.pots)
-    ok, worst, frac = force_tolerance_ok(F, Fr, hb.offsets, precision == 1)
+    ok, worst, frac = force_tolerance_ok(F, Fr, hb.offsets, precision == 1, kinds=kinds_of(hb))
     assert ok, (worst, frac)
     assert np.allclose(E, Er, rtol=1e-6 if precision == 0 else 1e-9, atol=1e-9)
 
@@ -139,7 +139,7 @@ def test_large_system_path(orc, precision):
     hb = W.concat(systems, small.pots)
     b, s, F, E, S, pos = run_forces(hb, precision)
     Er, Fr, Sr = orc.forces(hb.offsets, pos, hb.cell, hb.pbc, hb.pot_idx, hb.pots, use_cells=True)
-    ok, worst, frac = force_tolerance_ok(F, Fr, hb.offsets, precision == 1)
+    ok, worst, frac = force_tolerance_ok(F, Fr, hb.offsets, precision == 1, kinds=kinds_of(hb))
     assert ok, (worst, frac)
     assert np.all(np.abs(E - Er) <= (1e-6 if precision == 0 else 1e-9) * np.abs(Er) + 1e-9)
     # MD steps through both re-listing paths keep the state consistent
@@ -154,5 +154,5 @@ def test_large_system_path(orc, precision):
     b.poll()
     pos2 = s.pos.cpu().numpy()
     _, Fr2, _ = orc.forces(hb.offsets, pos2, hb.cell, hb.pbc, hb.pot_idx, hb.pots, use_cells=True)
-    ok, worst, frac = force_tolerance_ok(F2.cpu().numpy(), Fr2, hb.offsets, precision == 1)
+    ok, worst, frac = force_tolerance_ok(F2.cpu().numpy(), Fr2, hb.offsets, precision == 1, kinds=kinds_of(hb))
     assert ok, (worst, frac)

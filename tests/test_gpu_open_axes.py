@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 from paper_2508_06628_b300 import workloads as W
-from tests.gpu_util import force_tolerance_ok, frac_diff, make_batch, small_mix, torch_cuda
+from tests.gpu_util import force_tolerance_ok, kinds_of, frac_diff, make_batch, small_mix, torch_cuda
 
 pytestmark = pytest.mark.gpu
 
@@ -100,7 +100,7 @@ def test_open_axes_forces(orc, precision):
             if not hb.pbc[k][ax]:
                 assert np.abs(g[:, ax]).max() < 1e-12
     Er, Fr, Sr = orc.forces(hb.offsets, pos, hb.cell, hb.pbc, hb.pot_idx, hb.pots)
-    ok, worst, frac = force_tolerance_ok(F, Fr, hb.offsets, precision == 1)
+    ok, worst, frac = force_tolerance_ok(F, Fr, hb.offsets, precision == 1, kinds=kinds_of(hb))
     assert ok, (worst, frac)
     if precision == 1:
         assert np.allclose(E, Er, rtol=1e-9, atol=1e-12)

@@ -10,7 +10,7 @@
 import numpy as np
 import pytest
 
-from tests.gpu_util import force_tolerance_ok, make_batch, small_mix, torch_cuda
+from tests.gpu_util import force_tolerance_ok, kinds_of, make_batch, small_mix, torch_cuda
 
 pytestmark = pytest.mark.gpu
 
@@ -110,7 +110,7 @@ def test_positions_shifted_by_lattice_vectors_cost_no_relisting(orc, precision):
     assert r1 == r0
     F0, F1 = F0.cpu().numpy(), F1.cpu().numpy()
     Er, Fr, _ = orc.forces(hb.offsets, xs, hb.cell, hb.pbc, hb.pot_idx, hb.pots)
-    ok, worst, frac = force_tolerance_ok(F1, Fr, hb.offsets, precision == 1)
+    ok, worst, frac = force_tolerance_ok(F1, Fr, hb.offsets, precision == 1, kinds=kinds_of(hb))
     assert ok, (worst, frac)
     assert np.abs(F1 - F0).max() <= (1e-12 if precision == 1 else 1e-5) * np.abs(F0).max()
     b.close()
