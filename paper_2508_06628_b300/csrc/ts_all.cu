@@ -11,6 +11,4 @@
 #include "ts_adjoint.cu"
 #include "ts_inflight.cu"
 #include "ts_tune.cu"
-#if __has_include("ts_noalloc.cu")
 #include "ts_noalloc.cu"
-#endif
