@@ -16,9 +16,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
-import subprocess
 import sys
-import tempfile
 import time
 
 import numpy as np
@@ -28,7 +26,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "batched MD atom-steps/s on 1 B300 vs per-system loop; pair-kernel % HBM peak"
 UNIT = "atom-steps/s"
-FP32_LANES_PER_SM, N_SM = 128, 148
+FP32_LANES_PER_SM = 128
 FLOP_PER_PAIR = 30          # per ordered pair within the cutoff (force, energy, virial terms)
 BYTES_PER_ATOM = 32         # read own position, write own force, per atom-step
 # DRAM bytes (read + write) of one forces-only k_pair_small launch (inner lists) on ragged-mix-512, from one ncu
@@ -42,6 +40,12 @@ def pair_traffic():
     csrc = os.path.join(ROOT, "paper_2508_06628_b300", "csrc")
     h = hashlib.sha1(b"".join(open(os.path.join(csrc, f), "rb").read() for f in ("ts_pair.cu", "ts_internal.cuh")))
     return PAIR_TRAFFIC["bytes"] if h.hexdigest() == PAIR_TRAFFIC["source_sha1"] else None
+
+
+def n_sm(dev=0):
+    """Streaming multiprocessors of the device the bench runs on."""
+    import torch
+    return int(torch.cuda.get_device_properties(dev).multi_processor_count)
 
 
 def peaks():
@@ -58,50 +62,75 @@ def workload(seed=1, n_systems=512):
 
 
 class Clocks:
-    """Sample nvidia-smi during the timed region."""
+    """Sample the SM clock and the clock-event reasons through NVML every
+    ~1 ms in a host thread while the timed region runs (the region of the
+    default line is a few milliseconds, shorter than nvidia-smi's sampling
+    period).  Only samples between __enter__ and __exit__ are kept."""
 
-    def __init__(self, path):
-        self.path = path
-        self.p = None
+    REASONS = {"hw_slowdown": 0x8, "hw_thermal_slowdown": 0x40, "sw_thermal_slowdown": 0x20,
+               "sw_power_cap": 0x4, "hw_power_brake_slowdown": 0x80}
+
+    def __init__(self, device):
+        self.device = device
+        self.samples = []
+        self.h = None
+        self.error = None
+        try:
+            import pynvml
+            import torch
+            pynvml.nvmlInit()
+            pr = torch.cuda.get_device_properties(device)
+            bus = f"{pr.pci_domain_id:08x}:{pr.pci_bus_id:02x}:{pr.pci_device_id:02x}.0"
+            try:
+                self.h = pynvml.nvmlDeviceGetHandleByPciBusId(bus.encode())
+            except Exception:
+                self.h = pynvml.nvmlDeviceGetHandleByIndex(0)
+            self.nv = pynvml
+            self.max_mhz = float(pynvml.nvmlDeviceGetMaxClockInfo(self.h, pynvml.NVML_CLOCK_SM))
+        except Exception as e:
+            self.h = None
+            self.error = f"NVML unavailable: {e!r}"
+
+    def _sample(self):
+        try:
+            nv = self.nv
+            self.samples.append((float(nv.nvmlDeviceGetClockInfo(self.h, nv.NVML_CLOCK_SM)),
+                                 int(nv.nvmlDeviceGetCurrentClocksEventReasons(self.h))))
+        except Exception as e:
+            self.error = f"NVML sample failed: {e!r}"
+
+    def _run(self):
+        import time as _t
+        while not self.stop:
+            self._sample()
+            _t.sleep(0.001)
 
     def __enter__(self):
-        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
-        try:
-            self.f = open(self.path, "w")
-            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "200"],
-                                      stdout=self.f, stderr=subprocess.DEVNULL)
-        except Exception:
-            self.p = None
+        import threading
+        self.stop = False
+        self.t = None
+        if self.h is not None:
+            self._sample()          # one sample as the region opens, one as it closes, the thread between
+            self.t = threading.Thread(target=self._run, daemon=True)
+            self.t.start()
         return self
 
     def __exit__(self, *a):
-        if self.p:
-            self.p.terminate()
-            try:
-                self.p.wait(timeout=5)
-            except Exception:
-                self.p.kill()
-            self.f.close()
+        self.stop = True
+        if self.t:
+            self.t.join(timeout=5)
+            self._sample()
 
-    def summary(self, device_index=0):
-        try:
-            rows = [l.split(",") for l in open(self.path) if l.strip()]
-        except Exception:
-            return None
-        rows = [[c.strip() for c in r] for r in rows if len(r) >= 9 and r[0].strip() == str(device_index)]
-        if not rows:
-            return None
-        sm = [float(r[1]) for r in rows]
-        reasons = set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in rows:
-            for n, v in zip(names, r[5:9]):
-                if v.lower() == "active":
-                    reasons.add(n)
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(rows[0][2]), "samples": len(rows),
-                "reasons": sorted(reasons)}
+    def summary(self):
+        if not self.samples:
+            return {"error": self.error} if self.error else None
+        sm = [c for c, _ in self.samples]
+        mask = 0
+        for _, r in self.samples:
+            mask |= r
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": self.max_mhz, "samples": len(self.samples),
+                "reasons": sorted(n for n, bit in self.REASONS.items() if mask & bit),
+                "how": "NVML SM clock and clock-event reasons, sampled every ~1 ms during the timed region"}
 
 
 def run_ours(args, rank, world):
@@ -133,8 +162,7 @@ def run_ours(args, rank, world):
         import torch.distributed as dist
         dist.barrier()
     torch.cuda.synchronize()
-    # the raw clock samples go to TS_BENCH_OUT (default: the system's temporary directory)
-    clk = Clocks(os.path.join(os.environ.get("TS_BENCH_OUT", tempfile.gettempdir()), f"clocks_rank{rank}.csv"))
+    clk = Clocks(dev)
     with clk, torch.cuda.stream(stream):
         for c in range(ncalls):
             flush.fill_(c & 0xff)
@@ -160,7 +188,7 @@ def run_ours(args, rank, world):
         total_atoms = float(hb.n_atoms)
     value = total_atoms * steps_done / (ms / 1e3)
     out = {"ms": ms, "steps": steps_done, "value": value, "launches": l1 - l0, "relists": r1 - r0,
-           "n_atoms": hb.n_atoms, "n_systems": hb.n_systems, "inner": inner, "clocks": clk.summary(dev.index or 0)}
+           "n_atoms": hb.n_atoms, "n_systems": hb.n_systems, "inner": inner, "clocks": clk.summary()}
     if rank != 0:
         return out, None
     # --- dominant kernel: the pair kernel, timed alone with CUDA events on the stream
@@ -174,7 +202,8 @@ def run_ours(args, rank, world):
     hbm, smmhz, src = peaks()
     clocks = out["clocks"] or {}
     flops = pairs * FLOP_PER_PAIR
-    alu_peak = N_SM * FP32_LANES_PER_SM * 2 * smmhz * 1e6 / 1e12      # TFLOP/s, FMA = 2
+    nsm = n_sm(dev)
+    alu_peak = nsm * FP32_LANES_PER_SM * 2 * smmhz * 1e6 / 1e12      # TFLOP/s, FMA = 2
     achieved = flops / (kms / 1e3) / 1e12
     hbm_achieved = atoms * BYTES_PER_ATOM / (kms / 1e3) / 1e9
     out["roofline"] = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
@@ -182,9 +211,18 @@ def run_ours(args, rank, world):
                        "kernel": "k_pair_small" + (" + k_pair" if int(np.bincount(hb.system_idx).max()) > 2048 else ""),
                        "kernel_ms": kms, "kernel_ms_cold_l2": kms_cold, "kernel_ms_warm_l2": kms_warm,
                        "pairs_per_launch": pairs, "flop_per_pair": FLOP_PER_PAIR,
-                       "peak_source": f"148 SM x 128 FP32 lanes x 2 x {smmhz:.0f} MHz (max SM clock)",
+                       "peak_source": f"{nsm} SM x 128 FP32 lanes x 2 x {smmhz:.0f} MHz (max SM clock)",
                        "hbm": {"achieved": hbm_achieved, "peak": hbm, "unit": "GB/s", "frac": hbm_achieved / hbm,
                                "bytes_per_atom": BYTES_PER_ATOM, "peak_source": src}}
+    # --- forces, energies and stress at the final positions (outside the timed
+    # region), for the parity record of the oracle leg
+    Ff = torch.zeros((hb.n_atoms, 3), dtype=torch.float64, device=dev)
+    Ef = torch.zeros(hb.n_systems, dtype=torch.float64, device=dev)
+    Sf = torch.zeros((hb.n_systems, 3, 3), dtype=torch.float64, device=dev)
+    with torch.cuda.stream(stream):
+        b.pair_forces(s, Ff, Ef, Sf, stream=stream)
+        b.poll(stream)
+    out["final"] = {"pos": s.pos.cpu().numpy(), "F": Ff.cpu().numpy(), "E": Ef.cpu().numpy(), "S": Sf.cpu().numpy()}
     # --- per-system launch loop (same kernels, one system per batch, one step per call)
     if not args.no_loop:
         out["per_system_loop"] = per_system_loop(hb, pots, dev, args)
@@ -268,28 +306,65 @@ def e2e(b, s, hb, dev, stream, args, dt, gamma, inner):
             "how": f"per call of {inner} steps: H2D pos+vel from pinned host, D2H pos+vel+energies"}
 
 
-def cpu_baseline(hb, budget_s=15.0):
-    """FP64 oracle (cell-list mode) on a bounded sample of the same workload."""
+def cpu_baseline(hb, budget_s=15.0, steps=None, warmup=0):
+    """FP64 oracle (cell-list mode) on a bounded sample of the same workload:
+    one BAOAB step of a random group of 16 systems per step.  steps=None: as
+    many groups as about budget_s of CPU time allows; otherwise warmup untimed
+    and then exactly `steps` timed steps (the groups taken in turn)."""
     from oracle import oracle
     rng = np.random.default_rng(0)
     order = rng.permutation(hb.n_systems)
-    picked, atoms, t_used = [], 0, 0.0
-    # grow the sample until about budget_s of CPU work
     chunk = 16
+    groups = [np.sort(order[k:k + chunk]) for k in range(0, hb.n_systems, chunk)]
+    total_atoms, total_time, done = 0, 0.0, 0
     t0 = time.time()
-    total_atoms, total_time, steps = 0, 0.0, 1
-    for start in range(0, hb.n_systems, chunk):
-        sub = hb.subset(np.sort(order[start:start + chunk]))
+    for t in range(warmup + (steps if steps is not None else len(groups))):
+        sub = hb.subset(groups[t % len(groups)])
         t1 = time.time()
         oracle.md(sub.offsets, sub.pos, sub.vel, sub.mass, sub.cell, sub.pbc, sub.pot_idx, sub.pots, hb.meta["dt"],
-                  steps, kind=1, kT=sub.kT, gamma=hb.meta["gamma"], seed=5, uid=sub.uid, use_cells=True)
-        total_time += time.time() - t1
-        total_atoms += sub.n_atoms
-        if time.time() - t0 > budget_s:
+                  1, kind=1, kT=sub.kT, gamma=hb.meta["gamma"], seed=5, uid=sub.uid, use_cells=True)
+        if t >= warmup:
+            total_time += time.time() - t1
+            total_atoms += sub.n_atoms
+            done += 1
+        if steps is None and time.time() - t0 > budget_s:
             break
-    return {"value": total_atoms * steps / total_time, "unit": UNIT, "cores": oracle.num_threads(),
-            "kind": "oracle", "sample": f"{total_atoms} atoms in {start // chunk + 1} groups of {chunk} systems "
-                                        f"(random, seed 0) x {steps} BAOAB step, FP64 cell-list mode"}
+    return {"value": total_atoms * 1 / total_time, "unit": UNIT, "cores": oracle.num_threads(),
+            "kind": "oracle", "steps": done, "seconds": total_time,
+            "sample": f"{total_atoms} atoms: {done} steps, each one BAOAB step of a group of {chunk} systems "
+                      f"(random, seed 0, groups in turn), FP64 cell-list mode"}
+
+
+def oracle_parity(hb, final, n_pick=8):
+    """Error of the GPU result against the FP64 oracle (cell-list mode) on
+    n_pick sampled systems at the positions the timed run ended on: forces,
+    energies and stress of the mixed-precision path, computed after the timed
+    region.  Force tolerance per system: max_i |dF_i| <= max(1e-5 max_i |F_i|,
+    1e-6 eV/A); the per-atom bound max(1e-5 |F_i|, 1e-6) is reported as a
+    pass fraction; energies and stress as relative errors."""
+    from oracle import oracle
+    rng = np.random.default_rng(1)
+    pick = np.sort(rng.choice(hb.n_systems, n_pick, replace=False))
+    off = hb.offsets
+    sub = hb.subset(pick)
+    pos = np.concatenate([final["pos"][off[k]:off[k + 1]] for k in pick])
+    Er, Fr, Sr = oracle.forces(sub.offsets, pos, sub.cell, sub.pbc, sub.pot_idx, sub.pots, use_cells=True)
+    Fg = np.concatenate([final["F"][off[k]:off[k + 1]] for k in pick])
+    err = np.linalg.norm(Fg - Fr, axis=1)
+    nrm = np.linalg.norm(Fr, axis=1)
+    worst, e_rel, s_rel = 0.0, 0.0, 0.0
+    so = sub.offsets
+    for m, k in enumerate(pick):
+        a, e = so[m], so[m + 1]
+        worst = max(worst, float(err[a:e].max() / max(1e-5 * nrm[a:e].max(), 1e-6)))
+        e_rel = max(e_rel, float(abs(final["E"][k] - Er[m]) / max(abs(Er[m]), 1e-12)))
+        s_rel = max(s_rel, float(np.abs(final["S"][k] - Sr[m]).max() / max(np.abs(Sr[m]).max(), 1e-12)))
+    return {"reference": "FP64 oracle, cell-list mode", "systems": [int(k) for k in pick],
+            "atoms": int(sub.n_atoms), "force_worst_ratio_to_tol": worst,
+            "force_per_atom_pass_frac": float(np.mean(err <= np.maximum(1e-5 * nrm, 1e-6))),
+            "force_max_abs_err": float(err.max()), "energy_max_rel_err": e_rel, "stress_max_rel_err": s_rel,
+            "tolerance": "forces: per system max|dF| <= max(1e-5 max|F|, 1e-6 eV/A); energy <= 1e-6 relative "
+                         "(mixed precision)", "when": "after the timed region, at its final positions"}
 
 
 FLOP_PER_PAIR_BWD = 100   # pair-force backward, per pair within rc (positions and parameters)
@@ -330,7 +405,7 @@ def run_row_adjoint(args):
     ms = e0.elapsed_time(e1) / args.steps
     b.poll()
     _, smmhz, _ = peaks()
-    alu_peak = N_SM * FP32_LANES_PER_SM * 2 * smmhz * 1e6 / 1e12
+    alu_peak = n_sm(dev) * FP32_LANES_PER_SM * 2 * smmhz * 1e6 / 1e12
     achieved = pairs * FLOP_PER_PAIR_BWD / (ms / 1e3) / 1e12
     b.close()
     return {"metric": "pair-force backward (positions + parameters) atom-evaluations/s", "value": hb.n_atoms / (ms / 1e3),
@@ -678,10 +753,13 @@ def main():
         if rank != 0:
             return
         hb = workload(seed=1)
-        t0 = time.time()
-        cb = cpu_baseline(hb, budget_s=max(5.0, min(60.0, 4.0 * (args.steps + args.warmup))))
-        line = {"metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": hb.n_atoms / cb["value"] * 1e3, "higher_is_better": True,
+        # each step: one BAOAB step of a 16-system sample of the workload (about
+        # half a second on 16 host threads), so that K + W steps end in minutes
+        steps = max(1, min(args.steps, 200))
+        cb = cpu_baseline(hb, steps=steps, warmup=max(0, min(args.warmup, 20)))
+        line = {"metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus, "steps": cb["steps"],
+                "warmup": max(0, min(args.warmup, 20)), "ms_per_step": 1e3 * cb["seconds"] / cb["steps"],
+                "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
                 "config": dict(hbcfg, n_atoms=hb.n_atoms), "cpu_baseline": cb,
                 "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -695,6 +773,7 @@ def main():
     out, hb = run_ours(args, rank, world)
     if rank == 0:
         cb = None if args.no_cpu else cpu_baseline(hb)
+        parity = None if args.no_cpu else oracle_parity(hb, out["final"])
         ms_step = out["ms"] / out["steps"]
         line = {"metric": METRIC, "value": out["value"], "unit": UNIT, "n_gpus": world, "steps": out["steps"],
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -702,8 +781,11 @@ def main():
                 "config": dict(hbcfg, n_atoms=out["n_atoms"], md_steps_per_call=out["inner"],
                                l2="flushed (256 MiB write) before every call, outside the timed events",
                                precision="FP32 pair arithmetic, FP64 per-system energy/virial, double-float x and v",
+                               energy_virial="not evaluated per BAOAB step (the integrator needs forces only); "
+                                             "FP64 per-system energy and virial at the last step of a call when "
+                                             "asked for (the e2e leg asks every call)",
                                parallelism=f"systems sharded: dp{world}" if world > 1 else "single GPU"),
-                "roofline": out["roofline"], "cpu_baseline": cb, "e2e": out["e2e"],
+                "roofline": out["roofline"], "cpu_baseline": cb, "parity": parity, "e2e": out["e2e"],
                 "gpu_launches": out["launches"], "relists_in_timed_region": out["relists"],
                 "clocks": out["clocks"]}
         if "per_system_loop" in out:

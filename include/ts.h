@@ -28,7 +28,7 @@
  *    passed as void*, NULL = legacy default stream).  Argument errors are
  *    returned immediately; device-side errors (neighbour overflow, invalid
  *    system_idx, non-finite values, timeouts) set a sticky per-batch error
- *    word that ts_batch_poll / ts_batch_sync return.  No exception crosses
+ *    word that ts_batch_poll returns.  No exception crosses
  *    the ABI.  One host thread per batch.
  *  - Positions are wrapped into the cell whenever a system's neighbour list
  *    is rebuilt, so returned positions may differ from the inputs by lattice
@@ -146,7 +146,9 @@ ts_status ts_batch_create(const ts_batch_config* cfg, const ts_potential* pots, 
  * Host array of n_pots entries; synchronous. */
 ts_status ts_batch_set_potentials(ts_batch* b, const ts_potential* pots, int n_pots);
 
-/* Free all scratch of the batch (synchronises the device first). */
+/* Free all scratch of the batch (synchronises the device first).  The paper
+ * has no counterpart (its batches are PyTorch tensors freed by the garbage
+ * collector); the library never frees caller memory. */
 ts_status ts_batch_destroy(ts_batch* b);
 
 /* Neighbour build (per-system triclinic cell list with multi-image stencil,
@@ -160,7 +162,8 @@ ts_status ts_batch_destroy(ts_batch* b);
 ts_status ts_neighbor_build(ts_batch* b, ts_state* s, int force_rebuild, void* stream);
 
 /* Copy the current neighbour lists out, in caller order (for checks and
- * analysis): j_out [n_atoms][max_neighbors] i32 caller index of each
+ * analysis; the neighbour graph whose construction Sec. 4 names as the
+ * cost that separates models): j_out [n_atoms][max_neighbors] i32 caller index of each
  * neighbour, img_out [n_atoms][max_neighbors][3] i32 lattice image n of the
  * pair (x_j + n h - x_i, relative to the positions returned by the last
  * call), count_out [n_atoms] i32.  Unused entries are -1 / 0.  All device.
@@ -381,7 +384,11 @@ ts_status ts_batch_compact_admit(ts_batch* b, const ts_state* src, const uint8_t
 
 /* Block until all work queued on the stream is done, or timeout_ms passes
  * (TS_ERR_NOT_READY; nothing is lost, poll again).  Returns the sticky
- * device error word, then clears it. */
+ * device error word, then clears it.  The paper has no counterpart: PyTorch
+ * raises errors synchronously, whereas this library runs asynchronously on
+ * streams and reports device-side errors (neighbour overflow, invalid
+ * system_idx, non-finite input) here.  No kernel of this library waits on a
+ * flag, so TS_ERR_TIMEOUT is never raised by the current kernels. */
 ts_status ts_batch_poll(ts_batch* b, void* stream, int timeout_ms);
 
 /* Autotuner: time candidate launch shapes of the pair kernel (threads per
@@ -403,9 +410,9 @@ ts_status ts_profile_pair(ts_batch* b, ts_state* s, int reps, void* flush_buf, s
 /* Energies, forces and stress without any device allocation.
  * The paper has no counterpart: this entry point exists for callers that
  * cannot call cudaMalloc -- a host program that hands the library a fixed set
- * of buffers and forbids allocation after start-up, code that runs while
- * another component owns the device allocator, or work issued into a stream
- * that is being captured, where an allocation would break the capture.
+ * of buffers and forbids allocation after start-up, code running inside
+ * another framework that owns the device allocator, or a loop that cannot
+ * afford cudaMalloc's implicit device synchronisation.
  * It needs no ts_batch: it takes the potentials (host array, 1..4 entries),
  * a state whose pos, cell, system_idx and pot_idx are read (vel, mass, pbc,
  * uid are ignored; all systems fully periodic) and offsets [n_systems + 1]
@@ -413,22 +420,32 @@ ts_status ts_profile_pair(ts_batch* b, ts_state* s, int reps, void* flush_buf, s
  * [n_atoms][3], E [n_systems], stress [n_systems][3][3] (device f64; E and
  * stress may be NULL).  Arithmetic is FP64: an all-pairs sum over each
  * system's atoms and every lattice image within the cutoff, so the cost is
- * O(n^2) per system -- meant for small systems.
- * Scratch: a fixed device array (4096 systems x 8 doubles = 256 KiB) that
- * every GPU loading the library holds until exit.  More than 4096 systems
- * returns TS_ERR_BUDGET.  The first call on a device looks up that array's
- * address (cudaGetSymbolAddress); make it before capturing a stream.  All
- * calls share the array and each call clears the rows it uses, so calls that
- * overlap on the GPU (several streams or host threads) race and must be
- * serialised by the caller. */
+ * O(n^2) per system -- meant for small systems.  Energies and stress are
+ * reduced in a fixed order (bit-reproducible, independent of the batch).
+ * A system that cannot be evaluated gets NaN in E, stress and (when its
+ * offsets delimit atoms of the batch) the F rows of its atoms: pot_idx
+ * outside [0, n_pots), offsets decreasing or outside [0, n_atoms], a
+ * singular or non-finite cell, a cell so thin that an image more than 4
+ * cells away could lie within the cutoff, an atom whose system_idx
+ * disagrees with the offsets, or a non-finite position.
+ * Scratch: a fixed device table of per-CTA partial sums (4096 systems x 2
+ * rows x 8 doubles = 512 KiB) that every GPU loading the library holds until
+ * exit.  More than 4096 systems returns TS_ERR_BUDGET.  The first call on a
+ * device looks up that table's address (cudaGetSymbolAddress); make it
+ * before capturing a stream.  All calls share the table and each call
+ * overwrites the rows it reads, so calls that overlap on the GPU (several
+ * streams or host threads) race and must be serialised by the caller. */
 ts_status ts_pair_forces_noalloc(const ts_potential* pots, int n_pots, const ts_state* s, const int64_t* offsets,
                                  double* F, double* E, double* stress, void* stream);
 
-/* Human-readable text of the last host-side error of this batch (never NULL). */
+/* Human-readable text of the last host-side error of this batch (never NULL).
+ * The paper has no counterpart (Python exceptions carry the text there). */
 const char* ts_last_error(const ts_batch* b);
 
 /* Counters for reporting: kernel launches issued so far by this batch, and
- * neighbour-list rebuilds (system re-listings) so far. */
+ * neighbour-list rebuilds (system re-listings) so far.  The paper has no
+ * counterpart; the re-listing count measures the neighbour-graph work that
+ * Sec. 4 names as a cost. */
 ts_status ts_batch_counters(const ts_batch* b, int64_t* launches, int64_t* relists);
 
 /* Inner-list refreshes so far (one per system and refresh).  MD steps compute
