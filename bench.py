@@ -61,41 +61,72 @@ def workload(seed=1, n_systems=512):
     return W.ragged_mix(seed=seed, n_systems=n_systems)
 
 
+class _Nvml:
+    """The few read-only NVML calls the clock sampler needs, through ctypes on
+    the driver's libnvidia-ml (no Python binding required)."""
+
+    CLOCK_SM = 1
+
+    def __init__(self):
+        import ctypes as C
+        self.C = C
+        self.lib = C.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit_v2 failed")
+        self.reasons = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+
+    def handle(self, pci_bus_id, index=0):
+        C = self.C
+        h = C.c_void_p()
+        if self.lib.nvmlDeviceGetHandleByPciBusId_v2(pci_bus_id.encode(), C.byref(h)) != 0:
+            if self.lib.nvmlDeviceGetHandleByIndex_v2(C.c_uint(index), C.byref(h)) != 0:
+                raise RuntimeError("no NVML handle")
+        return h
+
+    def clock(self, h, maximum=False):
+        C = self.C
+        v = C.c_uint()
+        f = self.lib.nvmlDeviceGetMaxClockInfo if maximum else self.lib.nvmlDeviceGetClockInfo
+        if f(h, C.c_int(self.CLOCK_SM), C.byref(v)) != 0:
+            raise RuntimeError("clock query failed")
+        return float(v.value)
+
+    def event_reasons(self, h):
+        C = self.C
+        v = C.c_ulonglong()
+        if self.reasons(h, C.byref(v)) != 0:
+            raise RuntimeError("clock-event query failed")
+        return int(v.value)
+
+
 class Clocks:
     """Sample the SM clock and the clock-event reasons through NVML every
     ~1 ms in a host thread while the timed region runs (the region of the
     default line is a few milliseconds, shorter than nvidia-smi's sampling
-    period).  Only samples between __enter__ and __exit__ are kept."""
+    period), plus one sample as it opens and one as it closes."""
 
     REASONS = {"hw_slowdown": 0x8, "hw_thermal_slowdown": 0x40, "sw_thermal_slowdown": 0x20,
                "sw_power_cap": 0x4, "hw_power_brake_slowdown": 0x80}
 
     def __init__(self, device):
-        self.device = device
         self.samples = []
         self.h = None
         self.error = None
         try:
-            import pynvml
             import torch
-            pynvml.nvmlInit()
+            self.nv = _Nvml()
             pr = torch.cuda.get_device_properties(device)
             bus = f"{pr.pci_domain_id:08x}:{pr.pci_bus_id:02x}:{pr.pci_device_id:02x}.0"
-            try:
-                self.h = pynvml.nvmlDeviceGetHandleByPciBusId(bus.encode())
-            except Exception:
-                self.h = pynvml.nvmlDeviceGetHandleByIndex(0)
-            self.nv = pynvml
-            self.max_mhz = float(pynvml.nvmlDeviceGetMaxClockInfo(self.h, pynvml.NVML_CLOCK_SM))
+            self.h = self.nv.handle(bus, 0)
+            self.max_mhz = self.nv.clock(self.h, maximum=True)
         except Exception as e:
             self.h = None
             self.error = f"NVML unavailable: {e!r}"
 
     def _sample(self):
         try:
-            nv = self.nv
-            self.samples.append((float(nv.nvmlDeviceGetClockInfo(self.h, nv.NVML_CLOCK_SM)),
-                                 int(nv.nvmlDeviceGetCurrentClocksEventReasons(self.h))))
+            self.samples.append((self.nv.clock(self.h), self.nv.event_reasons(self.h)))
         except Exception as e:
             self.error = f"NVML sample failed: {e!r}"
 
@@ -110,7 +141,7 @@ class Clocks:
         self.stop = False
         self.t = None
         if self.h is not None:
-            self._sample()          # one sample as the region opens, one as it closes, the thread between
+            self._sample()
             self.t = threading.Thread(target=self._run, daemon=True)
             self.t.start()
         return self

@@ -38,9 +38,19 @@ __global__ void __launch_bounds__(128, F64 ? 4 : 8) k_pair_bwd(int32_t n_warps, 
   // test is warp-uniform and needs no host state; the inner list keeps the
   // outer list's order, so the sums are the same either way
   const bool use_in = !S.prune[s] && !need_relist(S, s);
-  const uint32_t* NB = use_in ? A.nbr_in : A.nbr;
+  const int ifmt = use_in ? S.infmt[s] : kInnerVerlet;
   int nn = valid ? (use_in ? A.nn_in : A.nn)[k] : 0;
-  int64_t seg = S.seg_start[s];
+  const int64_t seg = S.seg_start[s];
+  // entry q of the list read, and its (slot of j, image code) in either format
+  auto entry = [&](int q) -> uint32_t {
+    return use_in ? __ldg(A.nbr_in + inner_at(q, k, stride)) : __ldg(A.nbr + (int64_t)q * stride + k);
+  };
+  const TabDecode tdec(ifmt);
+  auto decode = [&](uint32_t e, int64_t& j, int& code) {
+    int jj;
+    inner_decode(e, ifmt, tdec, jj, code);
+    j = seg + jj;
+  };
   constexpr bool stress = STRESS;
   double Vinv = 0.0, Sg[9];
   if constexpr (stress) {
@@ -64,9 +74,9 @@ __global__ void __launch_bounds__(128, F64 ? 4 : 8) k_pair_bwd(int32_t n_warps, 
     const double* xi = A.xd + 3 * k;
     const double* gi = A.gd1 + 3 * k;
     for (int q = 0; q < nn; q++) {
-      uint32_t ent = NB[q * stride + k];
-      int64_t j = seg + (ent & kJMask);
-      int code = (int)(ent >> kJBits);
+      int64_t j;
+      int code;
+      decode(entry(q), j, code);
       double d[3];
       for (int c = 0; c < 3; c++) d[c] = A.xd[3 * j + c] - xi[c] + tab[3 * code + c];
       double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
@@ -101,7 +111,12 @@ __global__ void __launch_bounds__(128, F64 ? 4 : 8) k_pair_bwd(int32_t n_warps, 
   } else {
     const float4* tab = S.shift + 2 * (int64_t)s * kNCodes;
     float4 xi = A.xh[k], li = A.xl[k], gi = A.g1[k];
+    // parameter gradients: FP32 within runs of 8 pairs inside rc, FP64 across
+    // them (runs counted in pairs, not list entries, so that the sums do not
+    // depend on which list is read)
     float gxf[3] = {0.f, 0.f, 0.f}, gtf[3] = {0.f, 0.f, 0.f};
+    double gtd[3] = {0.0, 0.0, 0.0};
+    int run = 0;
     float gEf = (float)gEs, Vf = (float)Vinv;
     float Sf[9];
     for (int q = 0; q < 9; q++) Sf[q] = (float)Sg[q];
@@ -110,12 +125,13 @@ __global__ void __launch_bounds__(128, F64 ? 4 : 8) k_pair_bwd(int32_t n_warps, 
       float r, d1, d2, dd1[3];
       PotMath<float>::eval2(P, P.rc2f, r, d1, d2, dpc, dd1);
     }
-    uint32_t next = nn > 0 ? __ldg(NB + k) : 0u;
+    uint32_t next = nn > 0 ? entry(0) : 0u;
     for (int q = 0; q < nn; q++) {
-      uint32_t ent = next;
-      if (q + 1 < nn) next = __ldg(NB + (q + 1) * stride + k);
-      int64_t j = seg + (ent & kJMask);
-      int code = (int)(ent >> kJBits);
+      const uint32_t ent = next;
+      if (q + 1 < nn) next = entry(q + 1);
+      int64_t j;
+      int code;
+      decode(ent, j, code);
       float4 xj = __ldg(A.xh + j), lj = __ldg(A.xl + j);
       float4 sh = __ldg(tab + 2 * code), sl = __ldg(tab + 2 * code + 1);
       float d[3] = {((xj.x - xi.x) + sh.x) + ((lj.x - li.x) + sl.x), ((xj.y - xi.y) + sh.y) + ((lj.y - li.y) + sl.y),
@@ -131,6 +147,11 @@ __global__ void __launch_bounds__(128, F64 ? 4 : 8) k_pair_bwd(int32_t n_warps, 
       float ug = u[0] * g[0] + u[1] * g[1] + u[2] * g[2];
       float ugi = u[0] * gi.x + u[1] * gi.y + u[2] * gi.z;
       for (int c = 0; c < 3; c++) gxf[c] += d2 * ug * u[c] + d1 * ri * (g[c] - ug * u[c]);
+      if (run == 8) {
+        for (int p = 0; p < 3; p++) { gtd[p] += (double)gtf[p]; gtf[p] = 0.f; }
+        run = 0;
+      }
+      run++;
       for (int p = 0; p < 3; p++) gtf[p] += dd1[p] * ugi + 0.5f * gEf * (dphi[p] - dpc[p]);
       if constexpr (stress) {
         float Aq = (d2 - d1 * ri) * ri * ri, dSd = 0.f;
@@ -148,10 +169,8 @@ __global__ void __launch_bounds__(128, F64 ? 4 : 8) k_pair_bwd(int32_t n_warps, 
       A.g0[k] = make_float4(gxf[0] - gEf * F.x, gxf[1] - gEf * F.y, gxf[2] - gEf * F.z, 0.f);
     }
     for (int p = 0; p < 3; p++) {
-      float t = gtf[p];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-      if (lane == 0) gpart[4 * (int64_t)w + p] = (double)t;
+      const double t = warp_sum(gtd[p] + (double)gtf[p]);
+      if (lane == 0) gpart[4 * (int64_t)w + p] = t;
     }
   }
 }

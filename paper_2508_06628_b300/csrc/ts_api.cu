@@ -57,9 +57,9 @@ size_t scratch_bytes(int64_t Ncap, int64_t Bcap, int64_t Ccap, int32_t max_nbrs,
                            3 * 8 * 3 /*tmp d0,d1*/ + 4 * 8 /*tmp d2*/ + 2 * 3 * 8 /*gd*/)
                         : (2 * 16 /*x*/ + 2 * 16 /*v*/ + 16 /*F*/ + 2 * 16 /*xr*/ + 2 * 16 + 2 * 16 /*tmp f*/ +
                            2 * 16 /*g*/);
-  per_slot += (f64 ? 3 * 8 : 2 * 16) /*prune reference*/ + 4 /*nn_in*/ + (size_t)max_nbrs * 4 /*inner list*/;
+  per_slot += (f64 ? 3 * 8 : 2 * 16) /*prune reference*/ + 4 /*nn_in*/ + (size_t)(max_nbrs + 3) / 4 * 16 /*inner list*/;
   per_slot += 4 * 4 /*perm sys bin nn*/ + 3 * 4 /*tmp i*/ + (size_t)max_nbrs * 4 + 8 * 8 / 32 /*partials*/ + 4 / 32 /*warp_sys*/ + 16 / 32 /*pair work items*/;
-  size_t per_sys = 8 * 4 + 9 * 8 * 3 + 9 * 4 + 6 * 4 + 4 * 4 + 8 + 12 /*list-build work table*/ + 8 /*piston*/ + 4 /*geometry state*/ + 8 /*table bounds*/ + 32 * 4 /*FIRE FP32 coefficients*/ +
+  size_t per_sys = 4 /*inner-list format*/ + 8 * 4 + 9 * 8 * 3 + 9 * 4 + 6 * 4 + 4 * 4 + 8 + 12 /*list-build work table*/ + 8 /*piston*/ + 4 /*geometry state*/ + 8 /*table bounds*/ + 32 * 4 /*FIRE FP32 coefficients*/ +
                    (size_t)kNCodes * (32 + 24 + 16);
   return per_slot * (size_t)Ncap + per_sys * (size_t)Bcap + (size_t)Ccap * 8;
 }
@@ -142,15 +142,16 @@ extern "C" ts_status ts_batch_create(const ts_batch_config* cfg, const ts_potent
   SlotArrays& A = b->A;
   int64_t N = b->Ncap, B = b->Bcap;
   ok = ok && alloc(b, b->d_pots, kMaxPots) && alloc(b, b->d_err, 4) && alloc(b, b->d_counters, 4) &&
+
        alloc(b, b->d_step, 2);
   ok = ok && alloc(b, S.seg_start, B) && alloc(b, S.n_atoms, B) && alloc(b, S.caller_off, B + 1) && alloc(b, S.pot, B) &&
        alloc(b, S.uid, B) && alloc(b, S.bin_off, B) && alloc(b, S.bin_cap, B) && alloc(b, S.warp_start, B) &&
        alloc(b, S.warp_end, B) && alloc(b, S.h, 9 * B) && alloc(b, S.hinv, 9 * B) && alloc(b, S.hinvf, 9 * B) && alloc(b, S.href, 9 * B) &&
        alloc(b, S.nb, 3 * B) && alloc(b, S.reach, 3 * B) && alloc(b, S.pmask, B) && alloc(b, S.relist, B) && alloc(b, S.prune, B) && alloc(b, S.dirty, B) &&
-       alloc(b, S.soon, B) && alloc(b, S.any, 1) && alloc(b, S.geom, B) && alloc(b, S.tbound, B) && alloc(b, S.lbound, B) &&
+       alloc(b, S.soon, B) && alloc(b, S.infmt, B) && alloc(b, S.any, 1) && alloc(b, S.geom, B) && alloc(b, S.tbound, B) && alloc(b, S.lbound, B) &&
        alloc(b, S.kT, B) && alloc(b, S.shift, 2 * B * kNCodes) && alloc(b, S.shiftd, 3 * B * kNCodes) && alloc(b, S.shiftq, B * kNCodes);
   ok = ok && alloc(b, A.perm, N) && alloc(b, A.sys, N) && alloc(b, A.bin, N) && alloc(b, A.nn, N) &&
-       alloc(b, A.nbr, (size_t)b->max_nbrs * N) && alloc(b, A.nbr_in, (size_t)b->max_nbrs * N) && alloc(b, A.nn_in, N) && alloc(b, A.tmp_i0, N) && alloc(b, A.tmp_i1, N) &&
+       alloc(b, A.nbr, (size_t)b->max_nbrs * N) && alloc(b, A.nbr_in, (size_t)(b->max_nbrs + 3) / 4 * 4 * N) && alloc(b, A.nn_in, N) && alloc(b, A.tmp_i0, N) && alloc(b, A.tmp_i1, N) &&
        alloc(b, A.tmp_i2, N);
   if (b->f64) {
     ok = ok && alloc(b, A.xpd, 3 * N) && alloc(b, A.xd, 3 * N) && alloc(b, A.vd, 3 * N) && alloc(b, A.Fd, 3 * N) && alloc(b, A.minvd, N) &&
@@ -174,6 +175,7 @@ extern "C" ts_status ts_batch_create(const ts_batch_config* cfg, const ts_potent
                cuda_ok(b, cudaMemset(A.sys, 0xff, sizeof(int32_t) * N), "memset") &&
                cuda_ok(b, cudaMemset(A.nn, 0, sizeof(int32_t) * N), "memset") &&
                cuda_ok(b, cudaMemset(A.nn_in, 0, sizeof(int32_t) * N), "memset") &&
+               cuda_ok(b, cudaMemset(S.infmt, 0, sizeof(int32_t) * B), "memset") &&
                cuda_ok(b, cudaMemset(b->d_partial, 0, sizeof(double) * kPartialStride * b->Wcap), "memset");
   if (ok) ok = cuda_ok(b, cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming), "event");
   if (ok) {
@@ -181,7 +183,8 @@ extern "C" ts_status ts_batch_create(const ts_batch_config* cfg, const ts_potent
     ok = cuda_ok(b, cudaDeviceGetStreamPriorityRange(&least, &greatest), "priority range") &&
          cuda_ok(b, cudaStreamCreateWithPriority(&b->side, cudaStreamNonBlocking, greatest), "side stream") &&
          cuda_ok(b, cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming), "event") &&
-         cuda_ok(b, cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming), "event");
+         cuda_ok(b, cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming), "event") &&
+         cuda_ok(b, cudaEventCreateWithFlags(&b->ev_pruned, cudaEventDisableTiming), "event");
     b->prio_hi = greatest;
     const char* e = getenv("TS_OVERLAP_RELIST");
     if (e && atoi(e) == 0) b->overlap_relist = false;
@@ -191,9 +194,9 @@ extern "C" ts_status ts_batch_create(const ts_batch_config* cfg, const ts_potent
                cuda_ok(b, cudaFuncSetAttribute(k_relist_small<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)sizeof(SmallSmem)), "smem attribute") &&
                cuda_ok(b, cudaFuncSetAttribute(k_pair_small<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)(kSmallRecord * kSmallMax)), "smem attribute") &&
+                                               (int)(kPairTabBytes + kSmallRecord * kSmallMax)), "smem attribute") &&
                cuda_ok(b, cudaFuncSetAttribute(k_pair_small<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)(kSmallRecord * kSmallMax)), "smem attribute");
+                                               (int)(kPairTabBytes + kSmallRecord * kSmallMax)), "smem attribute");
   if (!ok) { ts_batch_destroy(b); return TS_ERR_CUDA; }
   b->dp_host.assign(dp, dp + kMaxPots);
   autotune_load(b);
@@ -238,6 +241,7 @@ extern "C" ts_status ts_batch_destroy(ts_batch* b) {
   if (b->ev) cudaEventDestroy(b->ev);
   if (b->ev_fork) cudaEventDestroy(b->ev_fork);
   if (b->ev_join) cudaEventDestroy(b->ev_join);
+  if (b->ev_pruned) cudaEventDestroy(b->ev_pruned);
   if (b->side) cudaStreamDestroy(b->side);
   for (auto& g : b->graphs) if (g.exec) cudaGraphExecDestroy(g.exec);
   delete b;
@@ -374,17 +378,18 @@ ts_status derive_topology(ts_batch* b, const ts_state* s, cudaStream_t st) {
   // the system boundary)
   const int wpi = kPairSmallThreads / kWarp, cap = kSmallMax / kWarp;
   std::vector<int4> items;
-  std::vector<double> work;
+  std::vector<double> work, wmax;
   b->nst_max = 0;
   {
     int first = -1, count = 0, s0 = -1;
-    double wk = 0;
+    double wk = 0, wm = 0;
     auto flush = [&](int s_last) {
       if (count == 0) return;
       items.push_back(make_int4(ws[s0], we[s_last] - ws[s0], first, count));
       work.push_back(wk);
+      wmax.push_back(wm);
       b->nst_max = std::max(b->nst_max, (we[s_last] - ws[s0]) * kWarp);
-      count = 0; wk = 0;
+      count = 0; wk = 0; wm = 0;
     };
     int s_prev = -1;
     for (int k : lay) {   // systems in slot order
@@ -396,6 +401,7 @@ ts_status derive_topology(ts_batch* b, const ts_state* s, cudaStream_t st) {
         if (count == 0) { first = w; s0 = k; }
         count++;
         wk += c * std::min(kWarp, n[k] - (w - ws[k]) * kWarp);
+        wm = std::max(wm, c);
         s_prev = k;
       }
     }
@@ -403,10 +409,14 @@ ts_status derive_topology(ts_batch* b, const ts_state* s, cudaStream_t st) {
   }
   b->n_items = (int32_t)items.size();
   if (b->n_items > b->Wcap) return fail(b, TS_ERR_BUDGET, "pair work table exceeds capacity");
-  {   // most work first (atoms, soft spheres weighted by half for their shorter lists), so the launch ends on small items
+  {   // The warps of an item run side by side, so a CTA lasts as long as its
+      // costliest warp: items with the longest per-atom lists first (any
+      // size), then by total work (atoms, soft spheres weighted by half for
+      // their shorter lists), so that the launch ends on cheap items
     std::vector<int32_t> order(b->n_items);
     for (int c = 0; c < b->n_items; c++) order[c] = c;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return work[a] > work[c]; });
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int c) { return wmax[a] != wmax[c] ? wmax[a] > wmax[c] : work[a] > work[c]; });
     std::vector<int4> sorted(b->n_items);
     for (int c = 0; c < b->n_items; c++) sorted[c] = items[order[c]];
     items.swap(sorted);
@@ -548,6 +558,13 @@ void relist(ts_batch* b, cudaStream_t st, bool move_fire) {
 // a step that re-lists nothing the side stream's launches find no work, and
 // they overlap the pair forces.  Returns false (nothing issued) when the
 // overlap is off or `st` is the legacy default stream.
+// In MD steps (inner lists) the systems that keep their lists split once
+// more: those that re-filter their inner list in this step run the longer
+// Verlet-list loop, so they are launched first and the steady systems'
+// launch follows with programmatic serialization: its CTAs are dispatched
+// once every CTA of the first launch is resident, so the long warps start in
+// the first wave instead of ending the step.  The bookkeeping waits for both
+// through an event recorded after the first.
 bool relist_pair_overlapped(ts_batch* b, cudaStream_t st, bool move_fire, bool ew, bool inner) {
   if (!b->overlap_relist || !b->side || st == nullptr) return false;
   if (!cuda_ok(b, cudaEventRecord(b->ev_fork, st), "event record") ||
@@ -557,7 +574,14 @@ bool relist_pair_overlapped(ts_batch* b, cudaStream_t st, bool move_fire, bool e
   relist_build(b, b->side, b->prio_hi);
   pair(b, b->side, ew, kPairRelisted, b->prio_hi, inner);
   cuda_ok(b, cudaEventRecord(b->ev_join, b->side), "event record");
-  pair(b, st, ew, kPairKept, 0, inner);
+  if (inner && b->ev_pruned) {
+    pair(b, st, ew, kPairPruned, 0, inner);
+    cuda_ok(b, cudaEventRecord(b->ev_pruned, st), "event record");
+    pair(b, st, ew, kPairSteady, 0, inner, true);
+    cuda_ok(b, cudaStreamWaitEvent(st, b->ev_pruned, 0), "stream wait");
+  } else {
+    pair(b, st, ew, kPairKept, 0, inner);
+  }
   cuda_ok(b, cudaStreamWaitEvent(st, b->ev_join, 0), "stream wait");
   relist_finish(b, st, inner);
   return true;
@@ -586,31 +610,46 @@ void relist_large_sort(ts_batch* b, cudaStream_t st, bool move_fire) {
   b->launches += 9;
 }
 
-void pair(ts_batch* b, cudaStream_t st, bool ew, int filter, int prio, bool inner) {
+void pair(ts_batch* b, cudaStream_t st, bool ew, int filter, int prio, bool inner, bool overlap) {
   const int in = inner ? 1 : 0;
   int threads = b->pair_threads;
   int blocks = (int)(((int64_t)b->nwarps * 32 + threads - 1) / threads);
   const DevPot* pots = b->d_pots;
   const int32_t* ws = b->d_warp_sys;
   if (b->f64) {
-    if (ew) launch_k(st, prio, blocks, threads, 0, k_pair<true, true>, b->nwarps, ws, b->S, b->A, pots, b->Ncap, filter, b->d_partial, 0, in);
-    else launch_k(st, prio, blocks, threads, 0, k_pair<true, false>, b->nwarps, ws, b->S, b->A, pots, b->Ncap, filter, b->d_partial, 0, in);
+    if (overlap) {
+      if (ew) launch_k_overlap(st, blocks, threads, 0, k_pair<true, true>, b->nwarps, ws, b->S, b->A, pots, b->Ncap, filter, b->d_partial, 0, in);
+      else launch_k_overlap(st, blocks, threads, 0, k_pair<true, false>, b->nwarps, ws, b->S, b->A, pots, b->Ncap, filter, b->d_partial, 0, in);
+    } else {
+      if (ew) launch_k(st, prio, blocks, threads, 0, k_pair<true, true>, b->nwarps, ws, b->S, b->A, pots, b->Ncap, filter, b->d_partial, 0, in);
+      else launch_k(st, prio, blocks, threads, 0, k_pair<true, false>, b->nwarps, ws, b->S, b->A, pots, b->Ncap, filter, b->d_partial, 0, in);
+    }
     b->launches++;
     return;
   }
   // mixed precision: systems up to kSmallMax atoms from shared memory, larger ones gathered through L1
   bool small = b->use_small_pair && b->n_items > 0;
   if (small) {
-    size_t shm = (size_t)kSmallRecord * b->nst_max;
+    size_t shm = kPairTabBytes + (size_t)kSmallRecord * b->nst_max;
     const int4* it = b->d_items;
-    if (ew) launch_k(st, prio, b->n_items, kPairSmallThreads, shm, k_pair_small<true>, b->n_items, it, ws, b->S, b->A, pots, b->Ncap, filter, b->d_partial, in);
-    else launch_k(st, prio, b->n_items, kPairSmallThreads, shm, k_pair_small<false>, b->n_items, it, ws, b->S, b->A, pots, b->Ncap, filter, b->d_partial, in);
+    if (overlap) {
+      if (ew) launch_k_overlap(st, b->n_items, kPairSmallThreads, shm, k_pair_small<true>, b->n_items, it, ws, b->S, b->A, pots, b->Ncap, filter, b->d_partial, in);
+      else launch_k_overlap(st, b->n_items, kPairSmallThreads, shm, k_pair_small<false>, b->n_items, it, ws, b->S, b->A, pots, b->Ncap, filter, b->d_partial, in);
+    } else {
+      if (ew) launch_k(st, prio, b->n_items, kPairSmallThreads, shm, k_pair_small<true>, b->n_items, it, ws, b->S, b->A, pots, b->Ncap, filter, b->d_partial, in);
+      else launch_k(st, prio, b->n_items, kPairSmallThreads, shm, k_pair_small<false>, b->n_items, it, ws, b->S, b->A, pots, b->Ncap, filter, b->d_partial, in);
+    }
     b->launches++;
   }
   if (!small || b->n_large > 0) {
     int sk = small ? 1 : 0;
-    if (ew) launch_k(st, prio, blocks, threads, 0, k_pair<false, true>, b->nwarps, ws, b->S, b->A, pots, b->Ncap, filter, b->d_partial, sk, in);
-    else launch_k(st, prio, blocks, threads, 0, k_pair<false, false>, b->nwarps, ws, b->S, b->A, pots, b->Ncap, filter, b->d_partial, sk, in);
+    if (overlap && !small) {
+      if (ew) launch_k_overlap(st, blocks, threads, 0, k_pair<false, true>, b->nwarps, ws, b->S, b->A, pots, b->Ncap, filter, b->d_partial, sk, in);
+      else launch_k_overlap(st, blocks, threads, 0, k_pair<false, false>, b->nwarps, ws, b->S, b->A, pots, b->Ncap, filter, b->d_partial, sk, in);
+    } else {
+      if (ew) launch_k(st, prio, blocks, threads, 0, k_pair<false, true>, b->nwarps, ws, b->S, b->A, pots, b->Ncap, filter, b->d_partial, sk, in);
+      else launch_k(st, prio, blocks, threads, 0, k_pair<false, false>, b->nwarps, ws, b->S, b->A, pots, b->Ncap, filter, b->d_partial, sk, in);
+    }
     b->launches++;
   }
 }

@@ -72,6 +72,7 @@ struct ts_batch {
   // runs beside the pair forces of the systems that keep their lists
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_pruned = nullptr;   // after the MD step's re-filtering pair launch
   bool overlap_relist = true;
   int prio_hi = 0;                // numerically greatest-priority value of the device
   // launch shapes (autotuned)
@@ -109,6 +110,24 @@ inline void launch_k(cudaStream_t st, int prio, dim3 grid, dim3 block, size_t sh
   cfg.numAttrs = prio != 0 ? 1 : 0;
   cudaLaunchKernelEx(&cfg, kern, args...);
 }
+// a launch with programmatic stream serialization: it may start once every
+// CTA of the preceding kernel on the stream has issued
+// griddepcontrol.launch_dependents (it must not read that kernel's results)
+template <typename... KArgs, typename... Args>
+inline void launch_k_overlap(cudaStream_t st, dim3 grid, dim3 block, size_t shm, void (*kern)(KArgs...),
+                             Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = shm;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kern, args...);
+}
 void relist(ts_batch* b, cudaStream_t st, bool move_fire);
 void relist_lists(ts_batch* b, cudaStream_t st, bool move_fire, int prio = 0);
 void relist_sort(ts_batch* b, cudaStream_t st, bool move_fire, int prio);
@@ -116,7 +135,7 @@ void relist_build(ts_batch* b, cudaStream_t st, int prio);
 void relist_finish(ts_batch* b, cudaStream_t st, bool md_pass);
 bool relist_pair_overlapped(ts_batch* b, cudaStream_t st, bool move_fire, bool ew, bool inner);
 void relist_large_sort(ts_batch* b, cudaStream_t st, bool move_fire);
-void pair(ts_batch* b, cudaStream_t st, bool ew, int filter, int prio = 0, bool inner = false);
+void pair(ts_batch* b, cudaStream_t st, bool ew, int filter, int prio = 0, bool inner = false, bool overlap = false);
 void reduce_sys(ts_batch* b, cudaStream_t st, double* E, double* stress, double* KE);
 void clear_dirty(ts_batch* b, cudaStream_t st);
 void export_state(ts_batch* b, cudaStream_t st, double* pos, double* vel);

@@ -64,6 +64,68 @@ __host__ __device__ inline int img_code(int nx, int ny, int nz) {
   return (nx + kMaxReach) + kImgSide * (ny + kMaxReach) + kImgSide * kImgSide * (nz + kMaxReach);
 }
 
+// ---------------------------------------------------------------------------
+// Inner (pruned) lists.  Layout: groups of four entries per slot,
+// [q / 4][slot][4], so that a thread loads four entries with one 16-byte load.
+// Entry format, per system: the format word SysArrays::infmt, written by the
+// launch that filters the list (kind in bits 0-3, and for kInnerTab the image
+// bounds b_x, b_y, b_z of the staged shift table in bits 4-6, 7-9, 10-12):
+//   kInnerVerlet  the Verlet-list format, j | code << kJBits (FP64 mode and
+//                 systems above kSmallMax atoms);
+//   kInnerTab     low 16 bits j * 16, the byte offset of neighbour j's staged
+//                 record in the shared-memory pair kernel; high 16 bits 16 x
+//                 the image's index in the staged shift table, which holds
+//                 the (2 b_x + 1)(2 b_y + 1)(2 b_z + 1) <= kTabCodes images
+//                 with |n_a| <= b_a, x fastest; kTabFar marks padding
+//                 entries (lists padded to a multiple of four);
+//   kInnerRaw     low 16 bits j * 16; high 16 bits the image code, or 0xffff
+//                 for padding entries (lists reaching more images than the
+//                 staged table holds).
+enum InnerFmt : int32_t { kInnerVerlet = 0, kInnerTab = 1, kInnerRaw = 2 };
+constexpr int kTabCodes = 125;                              // images of one staged table
+constexpr int kTabFar = kTabCodes;                          // shift entry of padding entries
+constexpr int kTabEntries = kTabCodes + 1;
+__host__ __device__ inline int64_t inner_at(int q, int64_t k, int64_t stride) {
+  return (((int64_t)(q >> 2) * stride + k) << 2) | (int64_t)(q & 3);
+}
+__host__ __device__ inline int fmt_kind(int f) { return f & 15; }
+__host__ __device__ inline int fmt_bound(int f, int a) { return (f >> (4 + 3 * a)) & 7; }
+__host__ __device__ inline int fmt_tab(int bx, int by, int bz) {
+  return kInnerTab | bx << 4 | by << 7 | bz << 10;
+}
+// Image code of staged-table index c (c < kTabEntries) under format word f:
+// table digits by multiply-shift division (m = floor(2^16 / side) + 1 is exact
+// for numerators below 2^16 / side^2 > 126), constants set once per warp.
+struct TabDecode {
+  int bx, by, bz, sx, sy, mx, my;
+  __host__ __device__ explicit TabDecode(int f)
+      : bx(fmt_bound(f, 0)), by(fmt_bound(f, 1)), bz(fmt_bound(f, 2)), sx(2 * bx + 1), sy(2 * by + 1),
+        mx(65536 / sx + 1), my(65536 / sy + 1) {}
+  __host__ __device__ int code(int c) const {
+    const int q1 = (c * mx) >> 16, q2 = (q1 * my) >> 16;
+    return img_code(c - sx * q1 - bx, q1 - sy * q2 - by, q2 - bz);
+  }
+};
+__host__ __device__ inline int tab_to_code(int c, int f) { return TabDecode(f).code(c); }
+// staged-table index of image code `code` (base-9 digits by multiply-shift
+// division, exact for code < 729); clamped into the table, which holds every
+// image the lists of a system with this format word can reference
+__host__ __device__ inline int code_to_tab(int code, int f) {
+  const int q1 = (code * 7282) >> 16, q2 = (q1 * 7282) >> 16;
+  const int nx = code - 9 * q1 - kMaxReach, ny = q1 - 9 * q2 - kMaxReach, nz = q2 - kMaxReach;
+  const int bx = fmt_bound(f, 0), by = fmt_bound(f, 1), bz = fmt_bound(f, 2);
+  const int c = (nx + bx) + (2 * bx + 1) * ((ny + by) + (2 * by + 1) * (nz + bz));
+  return c < 0 ? 0 : (c >= kTabCodes ? kTabCodes - 1 : c);
+}
+// (j, image code) of an inner-list entry under format word f (not a padding
+// entry); D = TabDecode(f)
+__host__ __device__ inline void inner_decode(uint32_t e, int f, const TabDecode& D, int& j, int& code) {
+  const int kind = fmt_kind(f);
+  if (kind == kInnerVerlet) { j = (int)(e & kJMask); code = (int)(e >> kJBits); return; }
+  j = (int)((e & 0xffffu) >> 4);
+  code = kind == kInnerTab ? D.code((int)(e >> 20)) : (int)(e >> 16);
+}
+
 struct DevPot {
   int kind, shift;
   float pf[3];
@@ -111,6 +173,7 @@ struct SysArrays {
   int32_t* tbound;        // image codes with every |n_a| <= tbound are current in the shift tables
   int32_t* lbound;        // largest |n_a| the system's Verlet list can hold (set when it is listed)
   int32_t* dirty;         // forces stale for this system
+  int32_t* infmt;         // entry format of the system's inner list (InnerFmt)
   double* kT;             // per-system kT (MD)
 };
 
@@ -128,19 +191,38 @@ __device__ __forceinline__ int image_bound(const SysArrays& S, int s) {
   return min(r, kMaxReach);
 }
 
+// Largest |n_a| along axis a of an image code in a list built for the
+// current geometry (0 along an open axis); the format word of a staged shift
+// table that covers them, or kInnerRaw when they are more than the table holds.
+__device__ __forceinline__ int axis_bound(const SysArrays& S, int s, int a) {
+  if (!(S.pmask[s] >> a & 1)) return 0;
+  const int nb = S.nb[3 * s + a], m = S.reach[3 * s + a];
+  return min((m + nb - 1) / nb, kMaxReach);
+}
+__device__ __forceinline__ int tab_format(const SysArrays& S, int s) {
+  const int bx = axis_bound(S, s, 0), by = axis_bound(S, s, 1), bz = axis_bound(S, s, 2);
+  return (2 * bx + 1) * (2 * by + 1) * (2 * bz + 1) <= kTabCodes ? fmt_tab(bx, by, bz) : (int)kInnerRaw;
+}
+
 __device__ __forceinline__ bool need_relist(const SysArrays& S, int s) {
   return S.relist[s] || (S.soon[s] && S.any[0]);
 }
 
 // Which systems a pair launch covers: all, those flagged dirty, or (while a
 // re-listing pass runs beside it) those keeping their lists or those being
-// re-listed.  The re-list flags stay fixed until the pass's bookkeeping
-// kernel runs after both halves.
-enum PairFilter : int { kPairAll = 0, kPairDirty = 1, kPairKept = 2, kPairRelisted = 3 };
+// re-listed; in MD steps the systems keeping their lists split further into
+// those whose inner list stands (kPairSteady) and those that re-filter it
+// from the Verlet list in this step (kPairPruned).  The flags stay fixed
+// until the pass's bookkeeping kernel runs after every part.
+enum PairFilter : int { kPairAll = 0, kPairDirty = 1, kPairKept = 2, kPairRelisted = 3, kPairSteady = 4,
+                        kPairPruned = 5 };
 __device__ __forceinline__ bool pair_skip(const SysArrays& S, int s, int filter) {
   if (filter == kPairAll) return false;
   if (filter == kPairDirty) return !S.dirty[s];
-  return need_relist(S, s) == (filter == kPairKept);
+  const bool re = need_relist(S, s);
+  if (filter == kPairRelisted) return !re;
+  if (filter == kPairKept) return re;
+  return re || ((S.prune[s] != 0) == (filter == kPairSteady));
 }
 
 struct SlotArrays {
@@ -161,7 +243,7 @@ struct SlotArrays {
   // inner list (dynamic pruning): the entries of nbr within rc + inner skin at
   // the last refresh, in the same order; positions at that refresh
   int32_t* nn_in;
-  uint32_t* nbr_in;           // [max_nbrs][Ncap]
+  uint32_t* nbr_in;           // [max_nbrs rounded up to 4 / 4][Ncap][4], see inner_at
   float4* xph; float4* xpl;   // mixed
   double* xpd;                // fp64 [3]
   // reorder scratch

@@ -19,6 +19,7 @@ template <bool F64, bool EW>
 __global__ void __launch_bounds__(256) k_pair(int32_t n_warps, const int32_t* __restrict__ warp_sys, SysArrays S,
                                               SlotArrays A, const DevPot* __restrict__ pots, int64_t stride,
                                               int filter, double* __restrict__ partial, int skip_small, int inner) {
+  asm volatile("griddepcontrol.launch_dependents;");   // as in k_pair_small
   int w = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
   int lane = threadIdx.x & 31;
   if (w >= n_warps) return;
@@ -28,26 +29,31 @@ __global__ void __launch_bounds__(256) k_pair(int32_t n_warps, const int32_t* __
   // inner-list mode (MD steps): a system flagged for pruning, or re-listed in
   // this pass, runs its full list and writes the inner list on the way
   const bool refresh = inner && (S.prune[s] || need_relist(S, s));   // warp-uniform
-  const uint32_t* NB = inner && !refresh ? A.nbr_in : A.nbr;
+  const bool use_in = inner && !refresh;
   int64_t k = (int64_t)w * kWarp + lane;
   const DevPot P = pots[S.pot[s]];
   bool valid = A.perm[k] >= 0;
-  int nn = valid ? (inner && !refresh ? A.nn_in : A.nn)[k] : 0;
+  int nn = valid ? (use_in ? A.nn_in : A.nn)[k] : 0;
   int cin = 0;
-  uint32_t* out_in = A.nbr_in + k;
+  // entry q of the list read (the inner list in its grouped layout, Verlet-list format here)
+  auto entry = [&](int q) -> uint32_t {
+    return use_in ? __ldcs(A.nbr_in + inner_at(q, k, stride)) : __ldcs(A.nbr + (int64_t)q * stride + k);
+  };
+  auto keep = [&](uint32_t ent) { A.nbr_in[inner_at(cin++, k, stride)] = ent; };
+  if (refresh && lane == 0) S.infmt[s] = kInnerVerlet;
   int64_t seg = S.seg_start[s];
   if constexpr (F64) {
     const double* tab = S.shiftd + 3 * (int64_t)s * kNCodes;
     double xi0 = A.xd[3 * k], xi1 = A.xd[3 * k + 1], xi2 = A.xd[3 * k + 2];
     double f0 = 0, f1 = 0, f2 = 0, e = 0, w0 = 0, w1 = 0, w2 = 0, w3 = 0, w4 = 0, w5 = 0;
     for (int q = 0; q < nn; q++) {
-      uint32_t ent = __ldg(NB + q * stride + k);
+      uint32_t ent = entry(q);
       int64_t j = seg + (ent & kJMask);
       int code = (int)(ent >> kJBits);
       double d0 = A.xd[3 * j] - xi0, d1 = A.xd[3 * j + 1] - xi1, d2 = A.xd[3 * j + 2] - xi2;
       if (code != kCenter) { d0 += tab[3 * code]; d1 += tab[3 * code + 1]; d2 += tab[3 * code + 2]; }
       double r2 = d0 * d0 + d1 * d1 + d2 * d2;
-      if (refresh && r2 < P.rin2d) out_in[(int64_t)(cin++) * stride] = ent;
+      if (refresh && r2 < P.rin2d) keep(ent);
       if (r2 < P.rc2d) {
         double phi, fr;
         PotMath<double>::eval(P, r2, phi, fr);
@@ -89,7 +95,7 @@ __global__ void __launch_bounds__(256) k_pair(int32_t n_warps, const int32_t* __
       }
       float d0 = a0 + b0, d1 = a1 + b1, d2 = a2 + b2;
       float r2 = fmaf(d0, d0, fmaf(d1, d1, d2 * d2));
-      if (refresh && r2 < P.rin2f) out_in[(int64_t)(cin++) * stride] = ent;
+      if (refresh && r2 < P.rin2f) keep(ent);
       if (r2 < P.rc2f) {
         float phi, fr;
         PotMath<float>::eval(P, r2, phi, fr);
@@ -110,18 +116,12 @@ __global__ void __launch_bounds__(256) k_pair(int32_t n_warps, const int32_t* __
     // loop, so results do not depend on the unrolling.
     const float4* ph = A.xh + seg;
     const float4* pl = A.xl + seg;
-    const uint32_t* lp = NB + k;
     int q = 0;
     uint32_t n0 = 0, n1 = 0, n2 = 0, n3 = 0;
-    if (nn >= 4) {
-      n0 = __ldcs(lp); n1 = __ldcs(lp + stride); n2 = __ldcs(lp + 2 * stride); n3 = __ldcs(lp + 3 * stride);
-    }
+    if (nn >= 4) { n0 = entry(0); n1 = entry(1); n2 = entry(2); n3 = entry(3); }
     for (; q + 4 <= nn; q += 4) {
       uint32_t e0 = n0, e1 = n1, e2 = n2, e3 = n3;
-      if (q + 8 <= nn) {
-        const uint32_t* np = lp + (int64_t)(q + 4) * stride;
-        n0 = __ldcs(np); n1 = __ldcs(np + stride); n2 = __ldcs(np + 2 * stride); n3 = __ldcs(np + 3 * stride);
-      }
+      if (q + 8 <= nn) { n0 = entry(q + 4); n1 = entry(q + 5); n2 = entry(q + 6); n3 = entry(q + 7); }
       float4 x0 = __ldg(ph + (e0 & kJMask)), l0 = __ldg(pl + (e0 & kJMask));
       float4 x1 = __ldg(ph + (e1 & kJMask)), l1 = __ldg(pl + (e1 & kJMask));
       float4 x2 = __ldg(ph + (e2 & kJMask)), l2 = __ldg(pl + (e2 & kJMask));
@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(256) k_pair(int32_t n_warps, const int32_t* __
       one(e0, x0, l0); one(e1, x1, l1); one(e2, x2, l2); one(e3, x3, l3);
     }
     for (; q < nn; q++) {
-      uint32_t ent = __ldg(NB + q * stride + k);
+      uint32_t ent = entry(q);
       int64_t j = seg + (ent & kJMask);
       one(ent, __ldg(A.xh + j), __ldg(A.xl + j));
     }
@@ -153,30 +153,140 @@ __global__ void __launch_bounds__(256) k_pair(int32_t n_warps, const int32_t* __
 // An item is a run of consecutive warps that may straddle systems; its staged
 // range holds every system those warps belong to (at most kSmallMax slots),
 // so every neighbour gather is a shared-memory read.  Staged record per atom:
-// 16 B, the fixed-point coordinates (units of 2^-26 A, modulo 2^32), so that
-// a gather is one 16-byte read and a 2048-atom system takes 32 KB; a pair
+// 16 B, the fixed-point coordinates (units of 2^-26 A, modulo 2^32); a pair
 // vector is the exact integer difference plus the fixed-point image shift,
-// converted once to FP32.  List entries stream from global memory
-// (coalesced, evict-first, prefetched two blocks of four ahead).  The potential
-// arithmetic and summation order are those of k_pair; the pair vectors carry
-// the same single FP32 rounding but a different quantisation of the
-// coordinates, so the two kernels agree within the mixed-precision tolerance,
-// not bit for bit.
+// converted once to FP32 (one rounding, the same as the double-float form).
+//
+// Three list modes per warp (a warp belongs to one system):
+//  * inner list, kInnerTab (MD steps, the common case): the system's image
+//    shifts that its lists reference (|n_a| <= b_a per axis, at most 125
+//    images) are staged in shared memory (one table per warp),
+//    and an entry holds the byte offsets of the neighbour's record and of its
+//    shift, so an entry costs a 16-byte share of a vector load, two shared
+//    loads, the integer pair vector and the potential;
+//  * inner list, kInnerRaw (lists reaching more images than a table holds):
+//    the same loop, the entries holding the image code and the shift read
+//    through L1;
+//  * Verlet list (non-MD calls, and MD steps in which the system is re-listed
+//    or an atom moved half the inner skin since the last filtering): the full
+//    list with global image shifts; in MD steps the launch writes the inner
+//    list on the way (entries within rc + inner skin, in list order, padded
+//    to a multiple of four with entries whose shift is 32 A).
+// Every mode evaluates a pair with the same function (pair_fixed) from the
+// same bits and sums the entries of the inner list in list order; pairs
+// beyond rc add exactly zero, so forces do not depend on which list was read.
 constexpr int kPairSmallThreads = 256;
-constexpr int kSmallRecord = 16;   // staged bytes per atom
+constexpr int kItemWarps = kPairSmallThreads / kWarp;
+constexpr int kSmallRecord = 16;                                    // staged bytes per atom
+constexpr size_t kPairTabBytes = (size_t)kItemWarps * kTabEntries * 16;   // image tables, one per warp
+constexpr float kFix2 = 4503599627370496.0f;                       // 2^52: r^2 in fixed-point units
+constexpr uint32_t kFarShift = 0x7fffffffu;                        // 32 A: beyond every cutoff this kernel takes
+constexpr uint32_t kRawFar = 0xffffu;                              // kInnerRaw padding entry
+
+// Per-warp constants of the potential in fixed-point units (u = 2^26 d):
+// F_i += fu u with fu = phi'(r) / (r 2^26), r2u = u.u = 2^52 r^2.
+struct PairFix {
+  float rc2u;      // rc^2 2^52
+  float a, b, c;   // LJ: sigma^2 2^52, -24 eps 2^26, 4 eps;  Morse: alpha, r0, 2 alpha D;  SS: 1/(sigma 2^26), -eps/sigma, eps/alpha
+  float d, e;      // Morse: D, 2^-26;  SS: alpha
+};
+
+template <int K>
+__device__ __forceinline__ PairFix pair_fix(const DevPot& P) {
+  PairFix C;
+  C.rc2u = P.rc2f * kFix2;
+  if constexpr (K == TS_LJ) {
+    C.a = (P.pf[0] * P.pf[0]) * kFix2; C.b = -24.0f * P.pf[1] * kFix; C.c = 4.0f * P.pf[1]; C.d = 0.f; C.e = 0.f;
+  } else if constexpr (K == TS_MORSE) {
+    C.a = P.pf[1]; C.b = P.pf[2]; C.c = 2.0f * P.pf[1] * P.pf[0]; C.d = P.pf[0]; C.e = kFixInv;
+  } else {
+    C.a = P.sinvf * kFixInv; C.b = -P.pf[1] * P.sinvf; C.c = P.pf[1] / P.pf[2]; C.d = P.pf[2]; C.e = 0.f;
+  }
+  return C;
+}
+
+// fu and (EW) the unshifted pair energy phi of a pair with r2u = u.u > 0;
+// fu is zero beyond the cutoff (selected, so that out-of-range entries add
+// exactly zero and a round of entries has no branch)
+template <int K, bool EW>
+__device__ __forceinline__ float pair_fixed(const PairFix& C, float r2u, float& phi) {
+  float fu;
+  if constexpr (K == TS_LJ) {
+    float ri2;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(ri2) : "f"(r2u));   // ~1 ulp; the LJ terms are well conditioned
+    const float s2 = C.a * ri2, s6 = s2 * s2 * s2;
+    fu = fmaf(s6, 2.0f * C.b, -C.b) * (s6 * ri2);      // -24 eps s6 (2 s6 - 1) / r^2 / 2^26
+    if (EW) phi = C.c * fmaf(s6, s6, -s6);
+  } else if constexpr (K == TS_MORSE) {
+    // r correctly rounded: it sets the exponent's argument, where the stiff
+    // Morse force amplifies any error; 1/r only scales the result
+    const float r = sqrtf(r2u) * C.e;
+    const float e = __expf(C.a * (C.b - r));
+    fu = C.c * e * (1.0f - e) * rsqrtf(r2u);
+    if (EW) phi = C.d * (e * e - 2.0f * e);
+  } else {
+    const float ri = rsqrtf(r2u);
+    const float t = fmaf(-r2u * ri, C.a, 1.0f);        // 1 - r/sigma in one fused operation
+    const float ta1 = (C.d == 2.0f) ? t : __powf(t, C.d - 1.0f);
+    fu = C.b * ta1 * ri;
+    if (EW) phi = C.c * ta1 * t;
+  }
+  return r2u < C.rc2u ? fu : 0.f;
+}
 
 template <bool EW>
-__global__ void __launch_bounds__(kPairSmallThreads) k_pair_small(
+struct PairSums {
+  float f0 = 0.f, f1 = 0.f, f2 = 0.f, e = 0.f, w0 = 0.f, w1 = 0.f, w2 = 0.f, w3 = 0.f, w4 = 0.f, w5 = 0.f;
+};
+
+// one entry: staged record xj, image shift sh (fixed point) against atom xi
+template <int K, bool EW>
+__device__ __forceinline__ float pair_add(const PairFix& C, float phic, const uint4& xi, const uint4& xj,
+                                          const uint4& sh, PairSums<EW>& A) {
+  const float u0 = (float)(int)(xj.x - xi.x + sh.x);
+  const float u1 = (float)(int)(xj.y - xi.y + sh.y);
+  const float u2 = (float)(int)(xj.z - xi.z + sh.z);
+  const float r2u = fmaf(u0, u0, fmaf(u1, u1, u2 * u2));
+  float phi = 0.f;
+  const float fu = pair_fixed<K, EW>(C, r2u, phi);
+  A.f0 = fmaf(fu, u0, A.f0); A.f1 = fmaf(fu, u1, A.f1); A.f2 = fmaf(fu, u2, A.f2);
+  if (EW) {
+    A.e += r2u < C.rc2u ? 0.5f * (phi - phic) : 0.f;
+    const float hf = fu * (0.5f * kFixInv);            // W += 1/2 (phi'/r) d d = 1/2 fu 2^-26 u u
+    const float h0 = hf * u0, h1 = hf * u1;
+    A.w0 = fmaf(h0, u0, A.w0); A.w1 = fmaf(h1, u1, A.w1); A.w2 = fmaf(hf * u2, u2, A.w2);
+    A.w3 = fmaf(h0, u1, A.w3); A.w4 = fmaf(h0, u2, A.w4); A.w5 = fmaf(h1, u2, A.w5);
+  }
+  return r2u;
+}
+
+template <bool EW>
+__global__ void __launch_bounds__(kPairSmallThreads, EW ? 3 : 4) k_pair_small(
     int32_t n_items, const int4* __restrict__ items, const int32_t* __restrict__ warp_sys, SysArrays S,
     SlotArrays A, const DevPot* __restrict__ pots, int64_t stride, int filter, double* __restrict__ partial,
     int inner) {
-  extern __shared__ __align__(16) uint4 sq[];   // [staged] fixed-point (x, y, z, -)
+  // a launch that follows this one with programmatic serialization (the MD
+  // step's steady systems after the re-filtering ones) may be dispatched as
+  // soon as every CTA of this grid is resident: it reads nothing this grid writes
+  asm volatile("griddepcontrol.launch_dependents;");
+  extern __shared__ __align__(16) uint4 smem[];
+  uint4* tabs = smem;                                   // [kItemWarps][kTabEntries] image shifts
+  uint4* sq = smem + kItemWarps * kTabEntries;          // [staged] fixed-point (x, y, z, -)
   if ((int)blockIdx.x >= n_items) return;
   const int4 W = items[blockIdx.x];
   const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int wg = W.z + wl;
+  const int s = wl < W.w ? warp_sys[wg] : 0;
+  // list mode of this warp: inner lists in MD steps unless the system is
+  // re-listed in this pass or flagged for filtering
+  const bool sel = wl < W.w && !pair_skip(S, s, filter);
+  const bool refresh = sel && inner && (S.prune[s] || need_relist(S, s));
   // leave before staging when no warp of the item is selected
-  const bool mine = wl < W.w && !pair_skip(S, warp_sys[W.z + wl], filter);
+  const bool mine = sel;
   if (!__syncthreads_or(mine)) return;
+  const int fmt = mine && inner && !refresh ? S.infmt[s] : kInnerVerlet;
+  const bool use_in = mine && inner && !refresh;
+  const bool staged_tab = use_in && fmt_kind(fmt) == kInnerTab;   // warp-uniform
   const int64_t st0 = (int64_t)W.x * kWarp;
   const int nst = W.y * kWarp;
 #pragma unroll 4
@@ -184,10 +294,23 @@ __global__ void __launch_bounds__(kPairSmallThreads) k_pair_small(
     float4 h = __ldg(A.xh + st0 + t), l = __ldg(A.xl + st0 + t);
     sq[t] = make_uint4(fix_coord(h.x, l.x), fix_coord(h.y, l.y), fix_coord(h.z, l.z), 0u);
   }
+  uint4* tab = tabs + wl * kTabEntries;
+  if (staged_tab) {   // this warp's image shifts, |n_a| <= b_a as the format word says
+    const uint4* gt = S.shiftq + (int64_t)s * kNCodes;
+    const int ntab = (2 * fmt_bound(fmt, 0) + 1) * (2 * fmt_bound(fmt, 1) + 1) * (2 * fmt_bound(fmt, 2) + 1);
+    const TabDecode td(fmt);
+    for (int c = lane; c < ntab; c += kWarp) tab[c] = __ldg(gt + td.code(c));
+    if (lane == 0) tab[kTabFar] = make_uint4(kFarShift, 0u, 0u, 0u);
+  }
+  // a warp that filters its inner list (into the table format) reads no
+  // staged table: its region holds the image code -> table index lookup
+  const int ofmt = refresh ? tab_format(S, s) : kInnerVerlet;
+  if (refresh && fmt_kind(ofmt) == kInnerTab) {
+    uint8_t* lut = reinterpret_cast<uint8_t*>(tab);
+    for (int c = lane; c < kNCodes; c += kWarp) lut[c] = (uint8_t)code_to_tab(c, ofmt);
+  }
   __syncthreads();
   if (!mine) return;
-  const int wg = W.z + wl;
-  const int s = warp_sys[wg];
   const int64_t seg = S.seg_start[s];
   const int64_t k = (int64_t)wg * kWarp + lane;
   const int i = (int)(k - seg);
@@ -195,92 +318,113 @@ __global__ void __launch_bounds__(kPairSmallThreads) k_pair_small(
   const bool valid = i < n;
   const uint4* hq = sq + (seg - st0);
   const DevPot P = pots[S.pot[s]];
-  const uint4* tab = S.shiftq + (int64_t)s * kNCodes;
-  // inner-list mode (MD steps): a system flagged for pruning, or re-listed in
-  // this pass, runs its full list and writes the inner list on the way
-  const bool refresh = inner && (S.prune[s] || need_relist(S, s));   // warp-uniform
-  const bool use_in = inner && !refresh;
-  const int nn = valid ? (use_in ? A.nn_in : A.nn)[k] : 0;
+  const uint4* gtab = S.shiftq + (int64_t)s * kNCodes;
   const uint4 xi = valid ? hq[i] : make_uint4(0, 0, 0, 0);
-  int cin = 0;
-  float f0 = 0.f, f1 = 0.f, f2 = 0.f, e = 0.f, w0 = 0.f, w1 = 0.f, w2 = 0.f, w3 = 0.f, w4 = 0.f, w5 = 0.f;
-  // The potential kind is uniform over a warp (one system): one loop per kind,
-  // with no branch inside an entry.  Every entry evaluates the potential and
-  // selects a zero force factor beyond rc (fmaf(0, d, f) == f, so the sums are
-  // those of the branching form), which lets the four entries of a round
-  // overlap.
-  auto run = [&](auto kind, auto refresh_c) {
+  PairSums<EW> acc;
+  // one loop per potential kind (uniform over the warp) and list mode
+  auto run = [&](auto kind) {
     constexpr int K = decltype(kind)::value;
-    constexpr bool R = decltype(refresh_c)::value;
-    auto one = [&](uint32_t ent) {
-      const int code = (int)(ent >> kJBits);
-      const int j = (int)(ent & kJMask);
-      const bool img = code != kCenter;
-      const uint4 sh = img ? __ldg(tab + code) : make_uint4(0, 0, 0, 0);
-      const uint4 xj = hq[j];
-      // exact integer pair vector (modulo 2^32), one rounding to FP32; kept in
-      // fixed-point units, the power-of-two scale applied once to r^2 and once
-      // to the force factor (scaling by 2^k commutes with FP32 rounding, so
-      // r^2 and the force sums are bit-identical to scaling each component)
-      const float u0 = (float)(int)(xj.x - xi.x + sh.x);
-      const float u1 = (float)(int)(xj.y - xi.y + sh.y);
-      const float u2 = (float)(int)(xj.z - xi.z + sh.z);
-      const float r2 = fmaf(u0, u0, fmaf(u1, u1, u2 * u2)) * (kFixInv * kFixInv);
-      const bool in = r2 < P.rc2f;
-      if (R) {   // inner list: within rc + inner skin (+ 1e-3 A), in list order
-        if (r2 < P.rin2f) A.nbr_in[(int64_t)cin * stride + k] = ent;
-        cin += r2 < P.rin2f;
+    const PairFix C = pair_fix<K>(P);
+    if (use_in) {
+      // four entries per 16-byte load, the next group in flight ahead of use
+      const char* hb = reinterpret_cast<const char*>(hq);
+      const char* tb = reinterpret_cast<const char*>(tab);
+      const uint4* lp = reinterpret_cast<const uint4*>(A.nbr_in) + k;
+      const int ng = valid ? (A.nn_in[k] + 3) >> 2 : 0;
+      auto one = [&](uint32_t ent) {
+        const uint4 xj = *reinterpret_cast<const uint4*>(hb + (ent & 0xffffu));
+        uint4 sh;
+        if (staged_tab) {
+          sh = *reinterpret_cast<const uint4*>(tb + (ent >> 16));
+        } else {   // kInnerRaw: the image code, or kRawFar for padding
+          const uint32_t code = ent >> 16;
+          sh = code == kRawFar ? make_uint4(kFarShift, 0u, 0u, 0u)
+                               : (code != (uint32_t)kCenter ? __ldg(gtab + code) : make_uint4(0u, 0u, 0u, 0u));
+        }
+        pair_add<K, EW>(C, P.phicf, xi, xj, sh, acc);
+      };
+#if TS_PAIR_PREFETCH2
+      uint4 n0 = make_uint4(0, 0, 0, 0), n1 = n0;
+      if (ng > 0) n0 = __ldcs(lp);
+      if (ng > 1) n1 = __ldcs(lp + stride);
+      for (int g = 0; g < ng; g++) {
+        const uint4 e = n0;
+        n0 = n1;
+        if (g + 2 < ng) n1 = __ldcs(lp + (int64_t)(g + 2) * stride);
+        one(e.x); one(e.y); one(e.z); one(e.w);
       }
-      float phi, fr;
-      PotMath<float>::eval_k<K>(P, r2, phi, fr);
-      fr = in ? fr : 0.f;
-      const float fu = fr * kFixInv;
-      f0 = fmaf(fu, u0, f0); f1 = fmaf(fu, u1, f1); f2 = fmaf(fu, u2, f2);
-      if (EW) {
-        const float d0 = u0 * kFixInv, d1 = u1 * kFixInv, d2 = u2 * kFixInv;
-        e += in ? 0.5f * (phi - P.phicf) : 0.f;
-        float hf = 0.5f * fr;
-        float h0 = hf * d0, h1 = hf * d1;
-        w0 = fmaf(h0, d0, w0); w1 = fmaf(h1, d1, w1); w2 = fmaf(hf * d2, d2, w2);
-        w3 = fmaf(h0, d1, w3); w4 = fmaf(h0, d2, w4); w5 = fmaf(h1, d2, w5);
+#else
+      // one group of four in flight ahead of use
+      uint4 n0 = make_uint4(0, 0, 0, 0);
+      if (ng > 0) n0 = __ldcs(lp);
+      for (int g = 0; g < ng; g++) {
+        const uint4 e = n0;
+        if (g + 1 < ng) n0 = __ldcs(lp + (int64_t)(g + 1) * stride);
+        one(e.x); one(e.y); one(e.z); one(e.w);
       }
-    };
-    const uint32_t* lp = (use_in ? A.nbr_in : A.nbr) + k;
-    int q = 0;
-    // list entries stream two blocks of four ahead of use (n: the next
-    // block, m: the one after)
-    uint32_t n0 = 0, n1 = 0, n2 = 0, n3 = 0, m0 = 0, m1 = 0, m2 = 0, m3 = 0;
-    if (nn >= 4) { n0 = __ldcs(lp); n1 = __ldcs(lp + stride); n2 = __ldcs(lp + 2 * stride); n3 = __ldcs(lp + 3 * stride); }
-    if (nn >= 8) {
-      const uint32_t* np = lp + 4 * stride;
-      m0 = __ldcs(np); m1 = __ldcs(np + stride); m2 = __ldcs(np + 2 * stride); m3 = __ldcs(np + 3 * stride);
+#endif
+    } else {   // Verlet list; in MD steps, filter it into the inner list
+      const int nn = valid ? A.nn[k] : 0;
+      const uint32_t* lp = A.nbr + k;
+      // the images the Verlet list can hold: those of the geometry it was
+      // built for, which is the current one (in MD steps a system whose cell
+      // changed since its listing is re-listed first)
+      const bool otab = fmt_kind(ofmt) == kInnerTab;
+      const uint8_t* lut = reinterpret_cast<const uint8_t*>(tab);
+      const float rin2u = P.rin2f * kFix2;
+      int cin = 0;
+      // inner entries collected four at a time and written as one 16-byte group
+      uint32_t g0 = 0, g1 = 0, g2 = 0, g3 = 0;
+      uint4* gout = reinterpret_cast<uint4*>(A.nbr_in) + k;
+      auto keep = [&](uint32_t e) {
+        const int r = cin & 3;
+        g0 = r == 0 ? e : g0; g1 = r == 1 ? e : g1; g2 = r == 2 ? e : g2; g3 = r == 3 ? e : g3;
+        if (r == 3) gout[(int64_t)(cin >> 2) * stride] = make_uint4(g0, g1, g2, g3);
+        cin++;
+      };
+      auto one = [&](uint32_t ent) {
+        const int code = (int)(ent >> kJBits);
+        const int j = (int)(ent & kJMask);
+        const uint4 sh = code != kCenter ? __ldg(gtab + code) : make_uint4(0, 0, 0, 0);
+        const float r2u = pair_add<K, EW>(C, P.phicf, xi, hq[j], sh, acc);
+        if (refresh && r2u < rin2u) {
+          const uint32_t hi = otab ? (uint32_t)lut[code] << 4 : (uint32_t)code;
+          keep((hi << 16) | ((uint32_t)j << 4));
+        }
+      };
+      // list entries stream one block of four ahead of use
+      int q = 0;
+      uint32_t n0 = 0, n1 = 0, n2 = 0, n3 = 0;
+      if (nn >= 4) { n0 = __ldcs(lp); n1 = __ldcs(lp + stride); n2 = __ldcs(lp + 2 * stride); n3 = __ldcs(lp + 3 * stride); }
+      for (; q + 4 <= nn; q += 4) {
+        uint32_t e0 = n0, e1 = n1, e2 = n2, e3 = n3;
+        if (q + 8 <= nn) {
+          const uint32_t* np = lp + (int64_t)(q + 4) * stride;
+          n0 = __ldcs(np); n1 = __ldcs(np + stride); n2 = __ldcs(np + 2 * stride); n3 = __ldcs(np + 3 * stride);
+        }
+        one(e0); one(e1); one(e2); one(e3);
+      }
+      for (; q < nn; q++) one(__ldcs(lp + (int64_t)q * stride));
+      if (refresh) {
+        if (valid) {
+          // pad the last group with entries whose shift is beyond every cutoff
+          const int n_in = cin;
+          const uint32_t far = otab ? (uint32_t)kTabFar << 20 : kRawFar << 16;
+          while (cin & 3) keep(far | ((uint32_t)i << 4));
+          A.nn_in[k] = n_in;
+          A.xph[k] = __ldg(A.xh + k); A.xpl[k] = __ldg(A.xl + k);
+        }
+        if (lane == 0) S.infmt[s] = ofmt;   // every warp of the system writes the same value
+      }
     }
-    for (; q + 4 <= nn; q += 4) {
-      uint32_t e0 = n0, e1 = n1, e2 = n2, e3 = n3;
-      n0 = m0; n1 = m1; n2 = m2; n3 = m3;
-      if (q + 12 <= nn) {
-        const uint32_t* np = lp + (int64_t)(q + 8) * stride;
-        m0 = __ldcs(np); m1 = __ldcs(np + stride); m2 = __ldcs(np + 2 * stride); m3 = __ldcs(np + 3 * stride);
-      }
-      one(e0); one(e1); one(e2); one(e3);
-    }
-    for (; q < nn; q++) one(__ldcs(lp + (int64_t)q * stride));
   };
-  using Off = std::false_type;
-  using On = std::true_type;
-  if (!refresh) {
-    if (P.kind == TS_LJ) run(std::integral_constant<int, TS_LJ>{}, Off{});
-    else if (P.kind == TS_MORSE) run(std::integral_constant<int, TS_MORSE>{}, Off{});
-    else run(std::integral_constant<int, TS_SOFT_SPHERE>{}, Off{});
-  } else {
-    if (P.kind == TS_LJ) run(std::integral_constant<int, TS_LJ>{}, On{});
-    else if (P.kind == TS_MORSE) run(std::integral_constant<int, TS_MORSE>{}, On{});
-    else run(std::integral_constant<int, TS_SOFT_SPHERE>{}, On{});
-    if (valid) { A.nn_in[k] = cin; A.xph[k] = __ldg(A.xh + k); A.xpl[k] = __ldg(A.xl + k); }
-  }
-  if (valid) A.F[k] = make_float4(f0, f1, f2, e);
+  if (P.kind == TS_LJ) run(std::integral_constant<int, TS_LJ>{});
+  else if (P.kind == TS_MORSE) run(std::integral_constant<int, TS_MORSE>{});
+  else run(std::integral_constant<int, TS_SOFT_SPHERE>{});
+  if (valid) A.F[k] = make_float4(acc.f0, acc.f1, acc.f2, acc.e);
   if (EW) {   // one FP64 partial per warp (every computed warp lies inside its system's padded segment)
-    double v[7] = {(double)e, (double)w0, (double)w1, (double)w2, (double)w3, (double)w4, (double)w5};
+    double v[7] = {(double)acc.e, (double)acc.w0, (double)acc.w1, (double)acc.w2, (double)acc.w3, (double)acc.w4,
+                   (double)acc.w5};
 #pragma unroll
     for (int cc = 0; cc < 7; cc++) {
       double t = warp_sum(v[cc]);

@@ -114,3 +114,58 @@ def test_pruned_md_large_system_mixed(monkeypatch):
     xb, vb, rb, _ = run(hb, 0, steps=100)
     assert pa > 0 and ra == rb
     assert np.array_equal(xa, xb) and np.array_equal(va, vb)
+
+
+def _thin_cells_batch():
+    """Thin cells whose lists reach images beyond |n_a| = 2 (a BCC argon and a
+    BCC copper slab one cubic cell thick: widths below r_list / 2) beside
+    ordinary cells, so that every inner-list format of the shared-memory pair
+    kernel is exercised in one batch."""
+    from paper_2508_06628_b300 import workloads as W
+    rng = np.random.default_rng(17)
+    systems = []
+    for kind, reps, a, pot, sp in [("bcc", (1, 4, 4), 4.175, 0, "Ar"), ("bcc", (1, 3, 5), 2.865, 1, "Cu"),
+                                   ("fcc", (3, 3, 3), 5.26, 0, "Ar"), ("fcc", (2, 3, 4), 3.61, 1, "Cu"),
+                                   ("fcc", (4, 4, 2), 1.27, 2, "SS")]:
+        pos, cell = W.lattice(kind, reps, a)
+        pos = pos + rng.normal(0.0, 0.04, pos.shape)
+        mass = np.full(len(pos), W.MASS[sp])
+        systems.append(dict(pos=pos, vel=W.maxwell_boltzmann(rng, mass, W.KB_EV * 300.0), mass=mass, cell=cell,
+                            pot=pot, kT=W.KB_EV * 300.0, uid=len(systems)))
+    hb = W.concat(systems, [W.LJ_AR, W.MORSE_CU, W.SOFT_SPHERE])
+    hb.meta = dict(dt=1.0 / W.T0_FS, gamma=0.01 * W.T0_FS)
+    return hb
+
+
+def test_pruned_md_all_inner_formats(monkeypatch, orc):
+    """Systems whose inner lists hold staged-table entries and systems whose
+    lists reach images beyond the staged table (global image shifts): MD is
+    bit-identical with pruning on and off, and the forces after the run match
+    the oracle."""
+    torch = torch_cuda()
+    from paper_2508_06628_b300 import ts
+    from tests.gpu_util import force_tolerance_ok, kinds_of
+    hb = _thin_cells_batch()
+    xa, va, ra, pa = run(hb, 0, steps=100)
+    monkeypatch.setenv("TS_INNER", "1")
+    xb, vb, rb, _ = run(hb, 0, steps=100)
+    assert pa > 0 and ra == rb
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb)
+    monkeypatch.delenv("TS_INNER")
+    b = make_batch(hb, 0)
+    s = ts.DeviceState.from_host(hb)
+    s.pos.copy_(torch.as_tensor(xa, device="cuda"))
+    s.vel.copy_(torch.as_tensor(va, device="cuda"))
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        b.neighbor_build(s, force=True, stream=stream)
+        b.md_step(s, 10, hb.meta["dt"], kind=1, gamma=hb.meta["gamma"], seed=4, step0=100, stream=stream)
+        b.profile_pair(s, reps=1, stream=stream)   # a forces-only launch from the inner lists
+        b.poll(stream)
+    F = torch.zeros_like(s.pos)
+    b.pair_forces(s, F)
+    b.poll()
+    Er, Fr, _ = orc.forces(hb.offsets, s.pos.cpu().numpy(), hb.cell, hb.pbc, hb.pot_idx, hb.pots)
+    ok, worst, frac = force_tolerance_ok(F.cpu().numpy(), Fr, hb.offsets, False, kinds=kinds_of(hb))
+    assert ok, (worst, frac)
+    b.close()
