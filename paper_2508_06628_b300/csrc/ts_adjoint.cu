@@ -45,11 +45,23 @@ __global__ void __launch_bounds__(128, F64 ? 4 : 8) k_pair_bwd(int32_t n_warps, 
   auto entry = [&](int q) -> uint32_t {
     return use_in ? __ldg(A.nbr_in + inner_at(q, k, stride)) : __ldg(A.nbr + (int64_t)q * stride + k);
   };
-  const TabDecode tdec(ifmt);
+  // staged-table index -> image code of this warp's inner-list format, looked up in shared memory
+  __shared__ uint16_t tab_code[4][kTabEntries + 2];
+  const int wib = threadIdx.x >> 5;
+  if (fmt_kind(ifmt) == kInnerTab) {
+    const TabDecode tdec(ifmt);
+    for (int c = lane; c < kTabCodes; c += kWarp) tab_code[wib][c] = (uint16_t)tdec.code(c);
+  }
+  __syncwarp();
   auto decode = [&](uint32_t e, int64_t& j, int& code) {
-    int jj;
-    inner_decode(e, ifmt, tdec, jj, code);
-    j = seg + jj;
+    const int kind = fmt_kind(ifmt);
+    if (kind == kInnerVerlet) {
+      j = seg + (e & kJMask);
+      code = (int)(e >> kJBits);
+    } else {
+      j = seg + ((e & 0xffffu) >> 4);
+      code = kind == kInnerTab ? (int)tab_code[wib][e >> 20] : (int)(e >> 16);
+    }
   };
   constexpr bool stress = STRESS;
   double Vinv = 0.0, Sg[9];
@@ -111,12 +123,10 @@ __global__ void __launch_bounds__(128, F64 ? 4 : 8) k_pair_bwd(int32_t n_warps, 
   } else {
     const float4* tab = S.shift + 2 * (int64_t)s * kNCodes;
     float4 xi = A.xh[k], li = A.xl[k], gi = A.g1[k];
-    // parameter gradients: FP32 within runs of 8 pairs inside rc, FP64 across
-    // them (runs counted in pairs, not list entries, so that the sums do not
-    // depend on which list is read)
-    float gxf[3] = {0.f, 0.f, 0.f}, gtf[3] = {0.f, 0.f, 0.f};
-    double gtd[3] = {0.0, 0.0, 0.0};
-    int run = 0;
+    // parameter gradients: compensated (Kahan) FP32 sums per thread -- the
+    // FP64 pipe of this part runs at a small fraction of the FP32 rate --
+    // then FP64 sums over the warp, the system and the batch
+    float gxf[3] = {0.f, 0.f, 0.f}, gtf[3] = {0.f, 0.f, 0.f}, gtc[3] = {0.f, 0.f, 0.f};
     float gEf = (float)gEs, Vf = (float)Vinv;
     float Sf[9];
     for (int q = 0; q < 9; q++) Sf[q] = (float)Sg[q];
@@ -125,10 +135,22 @@ __global__ void __launch_bounds__(128, F64 ? 4 : 8) k_pair_bwd(int32_t n_warps, 
       float r, d1, d2, dd1[3];
       PotMath<float>::eval2(P, P.rc2f, r, d1, d2, dpc, dd1);
     }
-    uint32_t next = nn > 0 ? entry(0) : 0u;
+    // entries four at a time, the next four in flight: one 16-byte group of
+    // the inner list, or four loads of the Verlet list
+    auto group = [&](int g) -> uint4 {
+      if (use_in) return __ldg(reinterpret_cast<const uint4*>(A.nbr_in) + (int64_t)g * stride + k);
+      const int q = 4 * g;
+      return make_uint4(q < nn ? entry(q) : 0u, q + 1 < nn ? entry(q + 1) : 0u, q + 2 < nn ? entry(q + 2) : 0u,
+                        q + 3 < nn ? entry(q + 3) : 0u);
+    };
+    uint4 cur = nn > 0 ? group(0) : make_uint4(0u, 0u, 0u, 0u), nxt = make_uint4(0u, 0u, 0u, 0u);
     for (int q = 0; q < nn; q++) {
-      const uint32_t ent = next;
-      if (q + 1 < nn) next = entry(q + 1);
+      const int c = q & 3;
+      if (c == 0) {
+        if (q > 0) cur = nxt;
+        if (q + 4 < nn) nxt = group((q >> 2) + 1);
+      }
+      const uint32_t ent = c == 0 ? cur.x : (c == 1 ? cur.y : (c == 2 ? cur.z : cur.w));
       int64_t j;
       int code;
       decode(ent, j, code);
@@ -147,12 +169,12 @@ __global__ void __launch_bounds__(128, F64 ? 4 : 8) k_pair_bwd(int32_t n_warps, 
       float ug = u[0] * g[0] + u[1] * g[1] + u[2] * g[2];
       float ugi = u[0] * gi.x + u[1] * gi.y + u[2] * gi.z;
       for (int c = 0; c < 3; c++) gxf[c] += d2 * ug * u[c] + d1 * ri * (g[c] - ug * u[c]);
-      if (run == 8) {
-        for (int p = 0; p < 3; p++) { gtd[p] += (double)gtf[p]; gtf[p] = 0.f; }
-        run = 0;
+      for (int p = 0; p < 3; p++) {
+        const float y = (dd1[p] * ugi + 0.5f * gEf * (dphi[p] - dpc[p])) - gtc[p];
+        const float t = gtf[p] + y;
+        gtc[p] = (t - gtf[p]) - y;
+        gtf[p] = t;
       }
-      run++;
-      for (int p = 0; p < 3; p++) gtf[p] += dd1[p] * ugi + 0.5f * gEf * (dphi[p] - dpc[p]);
       if constexpr (stress) {
         float Aq = (d2 - d1 * ri) * ri * ri, dSd = 0.f;
         for (int a = 0; a < 3; a++) for (int b = 0; b < 3; b++) dSd += d[a] * Sf[3 * a + b] * d[b];
@@ -169,7 +191,7 @@ __global__ void __launch_bounds__(128, F64 ? 4 : 8) k_pair_bwd(int32_t n_warps, 
       A.g0[k] = make_float4(gxf[0] - gEf * F.x, gxf[1] - gEf * F.y, gxf[2] - gEf * F.z, 0.f);
     }
     for (int p = 0; p < 3; p++) {
-      const double t = warp_sum(gtd[p] + (double)gtf[p]);
+      const double t = warp_sum((double)gtf[p] - (double)gtc[p]);
       if (lane == 0) gpart[4 * (int64_t)w + p] = t;
     }
   }
