@@ -177,6 +177,18 @@ def run_ours(args, rank, world):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     dt, gamma = hb.meta["dt"], hb.meta["gamma"]
     inner = max(1, min(args.inner, args.steps))
+    tuning, tune_s = None, 0.0
+    if not args.no_tune:
+        # the library's autotuner on a copy of the state, before (and outside) the timed region
+        t0 = time.time()
+        with torch.cuda.stream(stream):
+            trial = ts.DeviceState(*[None if t is None else t.clone() for t in
+                                     (s.pos, s.vel, s.mass, s.cell, s.pbc, s.system_idx, s.pot_idx, s.uid, s.kT)])
+            tuning = b.autotune(trial, dt, kind=ts.TS_LANGEVIN, gamma=gamma, seed=11, n_steps=25, stream=stream)
+            del trial
+        tune_s = time.time() - t0
+    else:
+        tuning = b.tuning()
     E = torch.zeros(hb.n_systems, dtype=torch.float64, device=dev)
     KE = torch.zeros_like(E)
     step = 0
@@ -219,6 +231,7 @@ def run_ours(args, rank, world):
         total_atoms = float(hb.n_atoms)
     value = total_atoms * steps_done / (ms / 1e3)
     out = {"ms": ms, "steps": steps_done, "value": value, "launches": l1 - l0, "relists": r1 - r0,
+           "tuning": dict(tuning, autotuned=not args.no_tune, tune_seconds=round(tune_s, 2)),
            "n_atoms": hb.n_atoms, "n_systems": hb.n_systems, "inner": inner, "clocks": clk.summary()}
     if rank != 0:
         return out, None
@@ -765,6 +778,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-loop", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (library defaults)")
     ap.add_argument("--row", default="md", choices=["md", "adjoint", "fire", "nve256", "inflight", "diff", "large",
                                                     "nhc", "npt"],
                     help="md: the MD step (the default line); the others: other rows and workloads, one GPU")
@@ -815,7 +829,8 @@ def main():
                                energy_virial="not evaluated per BAOAB step (the integrator needs forces only); "
                                              "FP64 per-system energy and virial at the last step of a call when "
                                              "asked for (the e2e leg asks every call)",
-                               parallelism=f"systems sharded: dp{world}" if world > 1 else "single GPU"),
+                               parallelism=f"systems sharded: dp{world}" if world > 1 else "single GPU",
+                               tuning=out["tuning"]),
                 "roofline": out["roofline"], "cpu_baseline": cb, "parity": parity, "e2e": out["e2e"],
                 "gpu_launches": out["launches"], "relists_in_timed_region": out["relists"],
                 "clocks": out["clocks"]}

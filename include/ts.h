@@ -391,10 +391,43 @@ ts_status ts_batch_compact_admit(ts_batch* b, const ts_state* src, const uint8_t
  * flag, so TS_ERR_TIMEOUT is never raised by the current kernels. */
 ts_status ts_batch_poll(ts_batch* b, void* stream, int timeout_ms);
 
-/* Autotuner: time candidate launch shapes of the pair kernel (threads per
- * block, persistent grid multiple) on the current state and keep the
- * fastest; cached under cfg->autotune_cache by (potential mix, size class). */
-ts_status ts_autotune(ts_batch* b, ts_state* s, void* stream);
+/* Launch and list parameters of the hot path (the paper has no counterpart:
+ * they shape how this engine maps the batched method onto the GPU and do
+ * not change what it computes beyond rounding order):
+ *   item_warps      warps (of 32 atoms) per CTA work item of the
+ *                   shared-memory pair kernel: 4 or 8 (the tile size);
+ *   inner_fraction  inner (pruned) list radius rc + inner_fraction * skin,
+ *                   (0, 1] (1 = no pruning);
+ *   relist_soon     re-list hysteresis: once any system re-lists, systems
+ *                   whose atoms moved more than relist_soon * skin/2 re-list
+ *                   in the same pass, (0, 1] (1 = off);
+ *   bin_factor      cell-list bin edge = bin_factor * (rc + skin): 1 or 0.5
+ *                   (the stencil then reaches two bins). */
+typedef struct {
+  int32_t item_warps;
+  double inner_fraction;
+  double relist_soon;
+  double bin_factor;
+} ts_tuning;
+
+/* Autotuner (the paper has no counterpart).  Times the MD step of p (n_steps
+ * per timed call, CUDA events around CUDA-graph replays on `stream`) for
+ * candidate values of each ts_tuning field in turn -- bin_factor {1, 0.5},
+ * item_warps {8, 4}, inner_fraction {0.2, 0.3, 0.45}, relist_soon {0.4, 0.5,
+ * 0.6} -- keeping the fastest value of each before tuning the next, applies
+ * the result and appends it to cfg->autotune_cache (host text file, one
+ * "key item_warps inner_fraction relist_soon bin_factor" line; key = potential
+ * kinds, log2 of the atom and system capacities, precision) when a path was
+ * given.  ts_batch_create applies the last matching cache line.  The trial
+ * steps advance s (positions, velocities): pass a copy of the state to keep
+ * the original.  Synchronises.  n_steps in [1, 1000]. */
+ts_status ts_autotune(ts_batch* b, ts_state* s, const ts_md_params* p, int n_steps, void* stream);
+
+/* The batch's current parameters, or set them (TS_ERR_INVALID_ARG outside the
+ * ranges above).  Setting them re-derives the layout and re-lists every system
+ * on the next call (synchronous; the paper has no counterpart). */
+ts_status ts_batch_tuning(const ts_batch* b, ts_tuning* out);
+ts_status ts_batch_set_tuning(ts_batch* b, const ts_tuning* t);
 
 /* Measurement hook: launch the pair-force kernel alone (forces only, from the
  * inner lists, the form an MD step uses) reps times, after re-listing flagged

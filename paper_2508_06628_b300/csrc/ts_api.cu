@@ -64,6 +64,42 @@ size_t scratch_bytes(int64_t Ncap, int64_t Bcap, int64_t Ccap, int32_t max_nbrs,
   return per_slot * (size_t)Ncap + per_sys * (size_t)Bcap + (size_t)Ccap * 8;
 }
 
+// The device potential table from the potentials and the tuned parameters:
+// cutoffs and shifts, list radius rc + skin, bin edge (the list radius times
+// the tuned bin factor), re-list hysteresis, inner (pruned) list radius.
+void fill_devpots(ts_batch* b, DevPot* dp) {
+  memset(dp, 0, sizeof(DevPot) * kMaxPots);
+  b->use_small_pair = true;
+  for (int q = 0; q < b->n_pots; q++) {
+    const ts_potential& P = b->pots[q];
+    DevPot& D = dp[q];
+    D.kind = P.kind; D.shift = P.shift;
+    for (int c = 0; c < 3; c++) { D.pd[c] = P.p[c]; D.pf[c] = (float)P.p[c]; }
+    double rc = P.kind == TS_SOFT_SPHERE ? P.p[0] : P.cutoff;
+    D.rc2d = rc * rc; D.rc2f = (float)(rc * rc);
+    D.sinvf = (float)(1.0 / P.p[0]);
+    double phic = 0;
+    if (P.shift && P.kind == TS_LJ) { double s = P.p[0] / rc, s6 = s * s * s * s * s * s; phic = 4 * P.p[1] * (s6 * s6 - s6); }
+    if (P.shift && P.kind == TS_MORSE) { double e = exp(-P.p[1] * (rc - P.p[2])); phic = P.p[0] * (e * e - 2 * e); }
+    D.phicd = phic; D.phicf = (float)phic;
+    D.skin = P.skin;
+    D.rlist = rc + P.skin; D.rlist2d = D.rlist * D.rlist; D.rlist2f = (float)D.rlist2d;
+    D.binw = D.rlist * b->tune.bin_factor;
+    D.soon2 = b->tune.relist_soon * b->tune.relist_soon;
+    {   // inner skin of the pruned list: a fraction of the skin (1 = no pruning)
+      double sin = b->tune.inner_fraction * P.skin, ri = rc + sin + kListBand;
+      D.rin2d = ri * ri; D.rin2f = (float)D.rin2d;
+      D.half_in2d = 0.25 * sin * sin; D.half_in2f = (float)D.half_in2d;
+    }
+    D.rlist_in2f = (float)((D.rlist - kListBand) * (D.rlist - kListBand));
+    D.rlist_out2f = (float)((D.rlist + kListBand) * (D.rlist + kListBand));
+    D.half_skin2f = (float)(0.25 * P.skin * P.skin);
+    D.soon_half_skin2f = (float)(D.soon2 * 0.25 * P.skin * P.skin);
+    b->rc[q] = rc;
+    if (D.rlist >= kFixMaxList) b->use_small_pair = false;   // beyond the fixed-point range of k_pair_small
+  }
+}
+
 }  // namespace ts
 
 // ---------------------------------------------------------------------------
@@ -99,44 +135,18 @@ extern "C" ts_status ts_batch_create(const ts_batch_config* cfg, const ts_potent
     delete b;
     return TS_ERR_CUDA;
   }
+  // tuned launch and list parameters: defaults (TS_SOON / TS_INNER override),
+  // then the cache entry for this configuration, if any
+  {
+    const char* e = getenv("TS_SOON");
+    if (e) { double f = atof(e); b->tune.relist_soon = (f > 0 && f <= 1) ? f : 1.0; }
+    e = getenv("TS_INNER");
+    if (e) { double f = atof(e); b->tune.inner_fraction = (f > 0 && f <= 1) ? f : 1.0; }
+  }
+  autotune_load(b);
   // device potential table
   DevPot dp[kMaxPots];
-  memset(dp, 0, sizeof dp);
-  for (int q = 0; q < n_pots; q++) {
-    const ts_potential& P = pots[q];
-    DevPot& D = dp[q];
-    D.kind = P.kind; D.shift = P.shift;
-    for (int c = 0; c < 3; c++) { D.pd[c] = P.p[c]; D.pf[c] = (float)P.p[c]; }
-    double rc = P.kind == TS_SOFT_SPHERE ? P.p[0] : P.cutoff;
-    D.rc2d = rc * rc; D.rc2f = (float)(rc * rc);
-    D.sinvf = (float)(1.0 / P.p[0]);
-    double phic = 0;
-    if (P.shift && P.kind == TS_LJ) { double s = P.p[0] / rc, s6 = s * s * s * s * s * s; phic = 4 * P.p[1] * (s6 * s6 - s6); }
-    if (P.shift && P.kind == TS_MORSE) { double e = exp(-P.p[1] * (rc - P.p[2])); phic = P.p[0] * (e * e - 2 * e); }
-    D.phicd = phic; D.phicf = (float)phic;
-    D.skin = P.skin;
-    D.rlist = rc + P.skin; D.rlist2d = D.rlist * D.rlist; D.rlist2f = (float)D.rlist2d;
-    {   // re-list hysteresis factor (0.5 measured best on ragged batches; TS_SOON overrides, 1 disables)
-      const char* e = getenv("TS_SOON");
-      double f = e ? atof(e) : 0.5;
-      if (!(f > 0 && f <= 1)) f = 1.0;
-      D.soon2 = f * f;
-    }
-    {   // inner skin of the pruned list: a fraction of the skin (TS_INNER; 1 = no pruning)
-      const char* e = getenv("TS_INNER");
-      double f = e ? atof(e) : kInnerSkinFraction;
-      if (!(f > 0 && f <= 1)) f = 1.0;
-      double sin = f * P.skin, ri = rc + sin + kListBand;
-      D.rin2d = ri * ri; D.rin2f = (float)D.rin2d;
-      D.half_in2d = 0.25 * sin * sin; D.half_in2f = (float)D.half_in2d;
-    }
-    D.rlist_in2f = (float)((D.rlist - kListBand) * (D.rlist - kListBand));
-    D.rlist_out2f = (float)((D.rlist + kListBand) * (D.rlist + kListBand));
-    D.half_skin2f = (float)(0.25 * P.skin * P.skin);
-    D.soon_half_skin2f = (float)(D.soon2 * 0.25 * P.skin * P.skin);
-    b->rc[q] = rc;
-    if (D.rlist >= kFixMaxList) b->use_small_pair = false;   // beyond the fixed-point range of k_pair_small
-  }
+  fill_devpots(b, dp);
   bool ok = true;
   SysArrays& S = b->S;
   SlotArrays& A = b->A;
@@ -199,7 +209,6 @@ extern "C" ts_status ts_batch_create(const ts_batch_config* cfg, const ts_potent
                                                (int)(kPairTabBytes + kSmallRecord * kSmallMax)), "smem attribute");
   if (!ok) { ts_batch_destroy(b); return TS_ERR_CUDA; }
   b->dp_host.assign(dp, dp + kMaxPots);
-  autotune_load(b);
   *out = b;
   return TS_OK;
 }
@@ -376,7 +385,7 @@ ts_status derive_topology(ts_batch* b, const ts_state* s, cudaStream_t st) {
   // may straddle systems, and stages every system it touches, as long as
   // that staged range stays within kSmallMax slots (otherwise it is cut at
   // the system boundary)
-  const int wpi = kPairSmallThreads / kWarp, cap = kSmallMax / kWarp;
+  const int wpi = b->tune.item_warps, cap = kSmallMax / kWarp;
   std::vector<int4> items;
   std::vector<double> work, wmax;
   b->nst_max = 0;
@@ -633,11 +642,11 @@ void pair(ts_batch* b, cudaStream_t st, bool ew, int filter, int prio, bool inne
     size_t shm = kPairTabBytes + (size_t)kSmallRecord * b->nst_max;
     const int4* it = b->d_items;
     if (overlap) {
-      if (ew) launch_k_overlap(st, b->n_items, kPairSmallThreads, shm, k_pair_small<true>, b->n_items, it, ws, b->S, b->A, pots, b->Ncap, filter, b->d_partial, in);
-      else launch_k_overlap(st, b->n_items, kPairSmallThreads, shm, k_pair_small<false>, b->n_items, it, ws, b->S, b->A, pots, b->Ncap, filter, b->d_partial, in);
+      if (ew) launch_k_overlap(st, b->n_items, 32 * b->tune.item_warps, shm, k_pair_small<true>, b->n_items, it, ws, b->S, b->A, pots, b->Ncap, filter, b->d_partial, in);
+      else launch_k_overlap(st, b->n_items, 32 * b->tune.item_warps, shm, k_pair_small<false>, b->n_items, it, ws, b->S, b->A, pots, b->Ncap, filter, b->d_partial, in);
     } else {
-      if (ew) launch_k(st, prio, b->n_items, kPairSmallThreads, shm, k_pair_small<true>, b->n_items, it, ws, b->S, b->A, pots, b->Ncap, filter, b->d_partial, in);
-      else launch_k(st, prio, b->n_items, kPairSmallThreads, shm, k_pair_small<false>, b->n_items, it, ws, b->S, b->A, pots, b->Ncap, filter, b->d_partial, in);
+      if (ew) launch_k(st, prio, b->n_items, 32 * b->tune.item_warps, shm, k_pair_small<true>, b->n_items, it, ws, b->S, b->A, pots, b->Ncap, filter, b->d_partial, in);
+      else launch_k(st, prio, b->n_items, 32 * b->tune.item_warps, shm, k_pair_small<false>, b->n_items, it, ws, b->S, b->A, pots, b->Ncap, filter, b->d_partial, in);
     }
     b->launches++;
   }

@@ -75,8 +75,9 @@ struct ts_batch {
   cudaEvent_t ev_pruned = nullptr;   // after the MD step's re-filtering pair launch
   bool overlap_relist = true;
   int prio_hi = 0;                // numerically greatest-priority value of the device
-  // launch shapes (autotuned)
+  // launch shapes and list parameters (autotuned, ts_tune.cu)
   int pair_threads = 128;
+  ts_tuning tune = {8, 0.3, 0.5, 1.0};
   bool use_graphs = true;
   std::vector<ts_graph_entry> graphs;
   bool graphs_valid = false;
@@ -143,4 +144,6 @@ void export_forces(ts_batch* b, cudaStream_t st, double* F);
 void ensure_forces(ts_batch* b, cudaStream_t st);
 ts_status md_loop(ts_batch* b, cudaStream_t st, const ts_md_params* p, int n_steps, double c1, bool need_e);
 void autotune_load(ts_batch* b);
+void fill_devpots(ts_batch* b, DevPot* dp);
+bool tuning_valid(const ts_tuning& t);
 }  // namespace ts

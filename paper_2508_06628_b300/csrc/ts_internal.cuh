@@ -140,6 +140,7 @@ struct DevPot {
   float half_in2f; double half_in2d;
   double pd[3];
   double rc2d, phicd, rlist, rlist2d, skin;
+  double binw;    // cell-list bin edge (at least rlist / 2; the stencil reach follows)
   double soon2;   // squared hysteresis factor
 };
 

@@ -261,11 +261,11 @@ __global__ void k_geometry(int32_t B, SysArrays S, const double* __restrict__ ce
     w[a] = V / sqrt(cx * cx + cy * cy + cz * cz);
     ext += fabs(h[3 * a]) + fabs(h[3 * a + 1]) + fabs(h[3 * a + 2]);
   }
-  double rl = pots[S.pot[s]].rlist;
+  double rl = pots[S.pot[s]].rlist, bw = pots[S.pot[s]].binw;
   int nb[3], m[3];
   bool bad = false;
   for (int a = 0; a < 3; a++) {
-    double f = floor(w[a] / rl);
+    double f = floor(w[a] / bw);
     nb[a] = f < 1.0 ? 1 : (f > 1024.0 ? 1024 : (int)f);
   }
   int cap = S.bin_cap[s];

@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(256) k_pair(int32_t n_warps, const int32_t* __
 // Mixed-precision pair kernel for systems of up to kSmallMax atoms.  One CTA
 // per work item (built on the host, int4 in warp units):
 //   x = first staged warp, y = staged warps, z = first computed warp,
-//   w = computed warps (at most 8).
+//   w = computed warps (at most the CTA's warps, 4 or 8: the tuned item size).
 // An item is a run of consecutive warps that may straddle systems; its staged
 // range holds every system those warps belong to (at most kSmallMax slots),
 // so every neighbour gather is a shared-memory read.  Staged record per atom:
@@ -290,7 +290,7 @@ __global__ void __launch_bounds__(kPairSmallThreads, EW ? 3 : 4) k_pair_small(
   const int64_t st0 = (int64_t)W.x * kWarp;
   const int nst = W.y * kWarp;
 #pragma unroll 4
-  for (int t = threadIdx.x; t < nst; t += kPairSmallThreads) {
+  for (int t = threadIdx.x; t < nst; t += blockDim.x) {
     float4 h = __ldg(A.xh + st0 + t), l = __ldg(A.xl + st0 + t);
     sq[t] = make_uint4(fix_coord(h.x, l.x), fix_coord(h.y, l.y), fix_coord(h.z, l.z), 0u);
   }

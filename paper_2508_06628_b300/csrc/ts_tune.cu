@@ -1,11 +1,20 @@
-// ts_tune.cu -- launch-shape autotuner for the pair kernel: times each
-// candidate CTA size on the live state with CUDA events and keeps the
-// fastest, caching the choice in a text file keyed by (potential kinds,
-// atom-count class, precision), one "key threads" line per entry.
+// ts_tune.cu -- the autotuner of the hot path's launch and list parameters
+// (ts_tuning: pair work-item size, cell-list bin edge, inner-list radius,
+// re-list hysteresis).  Each candidate is timed in situ: the batch's MD step
+// (as the caller runs it) replayed as a CUDA graph, CUDA events around whole
+// calls on the caller's stream.  The fields are tuned one after another, each
+// over its candidate values with the others at their best so far.  Results
+// are cached in a text file keyed by (potential kinds, log2 of the atom and
+// system capacities, precision), one line per tuning:
+//   key item_warps inner_fraction relist_soon bin_factor
+// and the last line matching a batch's key is applied at ts_batch_create.
+#include <cmath>
+#include <cstdlib>
 #include <cstdio>
 #include <fstream>
-#include <map>
 #include <sstream>
+#include <string>
+#include <vector>
 
 #include "ts_kernels.cuh"
 
@@ -15,68 +24,140 @@ static std::string tune_key(const ts_batch* b) {
   std::ostringstream k;
   k << "pots=";
   for (int q = 0; q < b->n_pots; q++) k << b->pots[q].kind;
-  int cls = 0;
-  for (int64_t n = b->N; n > 1; n >>= 1) cls++;
-  k << ";log2N=" << cls << ";fp64=" << (b->f64 ? 1 : 0);
+  int na = 0, ns = 0;
+  for (int64_t n = b->cfg.atom_capacity; n > 1; n >>= 1) na++;
+  for (int64_t n = b->cfg.system_capacity; n > 1; n >>= 1) ns++;
+  k << ";log2atoms=" << na << ";log2systems=" << ns << ";fp64=" << (b->f64 ? 1 : 0);
   return k.str();
 }
 
-static std::map<std::string, int> read_cache(const std::string& path) {
-  std::map<std::string, int> m;
+bool tuning_valid(const ts_tuning& t) {
+  return (t.item_warps == 4 || t.item_warps == 8) && t.inner_fraction > 0 && t.inner_fraction <= 1 &&
+         t.relist_soon > 0 && t.relist_soon <= 1 && (t.bin_factor == 1.0 || t.bin_factor == 0.5);
+}
+
+// the last cache line whose key matches, if any
+static bool read_cache(const std::string& path, const std::string& key, ts_tuning& out) {
   std::ifstream f(path);
-  std::string key;
-  int t;
-  while (f >> key >> t) m[key] = t;
-  return m;
+  std::string line;
+  bool found = false;
+  while (std::getline(f, line)) {
+    std::istringstream ls(line);
+    std::string k;
+    ts_tuning t;
+    if (ls >> k >> t.item_warps >> t.inner_fraction >> t.relist_soon >> t.bin_factor && k == key && tuning_valid(t)) {
+      out = t;
+      found = true;
+    }
+  }
+  return found;
 }
 
 void autotune_load(ts_batch* b) {
   b->pair_threads = 128;
+  if (b->cache_path.empty()) return;
+  ts_tuning t;
+  if (read_cache(b->cache_path, tune_key(b), t)) b->tune = t;
+}
+
+// Make t the batch's parameters: new potential table, and a fresh layout
+// (work items) and listing of every system on the next call.
+ts_status apply_tuning(ts_batch* b, const ts_tuning& t) {
+  b->tune = t;
+  DevPot dp[kMaxPots];
+  fill_devpots(b, dp);
+  b->dp_host.assign(dp, dp + kMaxPots);
+  cudaSetDevice(b->cfg.device);
+  if (!cuda_ok(b, cudaMemcpy(b->d_pots, dp, sizeof dp, cudaMemcpyHostToDevice), "potential table")) return TS_ERR_CUDA;
+  b->topo_valid = false;      // items follow item_warps; the bins follow bin_factor
+  b->graphs_valid = false;
+  return TS_OK;
 }
 
 }  // namespace ts
 
 using namespace ts;
 
-extern "C" ts_status ts_autotune(ts_batch* b, ts_state* s, void* stream) {
-  ts_status r = check_state(b, s, false);
+extern "C" ts_status ts_batch_tuning(const ts_batch* b, ts_tuning* out) {
+  if (!b || !out) return TS_ERR_INVALID_ARG;
+  *out = b->tune;
+  return TS_OK;
+}
+
+extern "C" ts_status ts_batch_set_tuning(ts_batch* b, const ts_tuning* t) {
+  if (!b || !t) return TS_ERR_INVALID_ARG;
+  if (!tuning_valid(*t)) return fail(b, TS_ERR_INVALID_ARG, "tuning outside its ranges");
+  if (!cuda_ok(b, cudaDeviceSynchronize(), "synchronise")) return TS_ERR_CUDA;
+  return apply_tuning(b, *t);
+}
+
+extern "C" ts_status ts_autotune(ts_batch* b, ts_state* s, const ts_md_params* p, int n_steps, void* stream) {
+  ts_status r = check_state(b, s, true);
   if (r != TS_OK) return r;
+  if (!p || n_steps < 1 || n_steps > 1000) return fail(b, TS_ERR_INVALID_ARG, "bad MD parameters or step count");
   cudaStream_t st = (cudaStream_t)stream;
-  r = prologue(b, s, st, false);
-  if (r != TS_OK) return r;
-  ensure_forces(b, st);
-  std::string key = tune_key(b);
-  if (!b->cache_path.empty()) {
-    auto m = read_cache(b->cache_path);
-    auto it = m.find(key);
-    if (it != m.end() && (it->second == 64 || it->second == 128 || it->second == 256)) {
-      if (b->pair_threads != it->second) { b->pair_threads = it->second; b->graphs_valid = false; }
-      return TS_OK;
-    }
-  }
   cudaEvent_t e0, e1;
   if (!cuda_ok(b, cudaEventCreate(&e0), "event") || !cuda_ok(b, cudaEventCreate(&e1), "event")) return TS_ERR_CUDA;
-  const int cands[3] = {64, 128, 256};
-  int best = b->pair_threads;
-  float best_ms = 1e30f;
-  for (int c : cands) {
-    b->pair_threads = c;
-    pair(b, st, false, false);   // warm
-    cudaEventRecord(e0, st);
-    for (int k = 0; k < 10; k++) pair(b, st, false, false);
-    cudaEventRecord(e1, st);
-    if (!cuda_ok(b, cudaEventSynchronize(e1), "event sync")) return TS_ERR_CUDA;
+  ts_md_params q = *p;
+  // milliseconds per MD step of configuration t: a warm-up call (layout,
+  // listing, graph capture), then three timed calls of n_steps
+  auto trial = [&](const ts_tuning& t, double& ms_out) -> ts_status {
+    ts_status rr = apply_tuning(b, t);
+    if (rr != TS_OK) return rr;
+    if ((rr = ts_md_step(b, s, &q, n_steps, nullptr, nullptr, st)) != TS_OK) return rr;
+    q.step0 += (uint64_t)n_steps;
+    if (!cuda_ok(b, cudaEventRecord(e0, st), "event record")) return TS_ERR_CUDA;
+    for (int c = 0; c < 3; c++) {
+      if ((rr = ts_md_step(b, s, &q, n_steps, nullptr, nullptr, st)) != TS_OK) return rr;
+      q.step0 += (uint64_t)n_steps;
+    }
+    if (!cuda_ok(b, cudaEventRecord(e1, st), "event record") || !cuda_ok(b, cudaEventSynchronize(e1), "event sync"))
+      return TS_ERR_CUDA;
     float ms = 0;
     cudaEventElapsedTime(&ms, e0, e1);
-    if (ms < best_ms) { best_ms = ms; best = c; }
+    ms_out = ms / (3.0 * n_steps);
+    if (getenv("TS_TUNE_LOG"))
+      fprintf(stderr, "ts_autotune: item_warps %d inner %.3g soon %.3g bins %.3g: %.5f ms/step\n", t.item_warps,
+              t.inner_fraction, t.relist_soon, t.bin_factor, ms_out);
+    return ts_batch_poll(b, st, -1);   // a trial that overflowed a list or met bad input fails the tuning
+  };
+  ts_tuning best = b->tune;
+  double best_ms = 0;
+  r = trial(best, best_ms);                  // warm-up of the whole path, not compared
+  if (r == TS_OK) r = trial(best, best_ms);
+  // the fields in turn, each over its candidates with the others at their best
+  const double bins[2] = {1.0, 0.5};
+  const int items[2] = {8, 4};
+  const double inner[3] = {0.2, 0.3, 0.45};
+  const double soon[3] = {0.4, 0.5, 0.6};
+  for (int field = 0; field < 4 && r == TS_OK; field++) {
+    const int nc = field < 2 ? 2 : 3;
+    for (int c = 0; c < nc && r == TS_OK; c++) {
+      ts_tuning t = best;
+      if (field == 0) t.bin_factor = bins[c];
+      if (field == 1) t.item_warps = items[c];
+      if (field == 2) t.inner_fraction = inner[c];
+      if (field == 3) t.relist_soon = soon[c];
+      if (t.bin_factor == best.bin_factor && t.item_warps == best.item_warps &&
+          t.inner_fraction == best.inner_fraction && t.relist_soon == best.relist_soon)
+        continue;   // the current best, timed already
+      double ms = 0;
+      r = trial(t, ms);
+      if (r == TS_OK && ms < best_ms) { best_ms = ms; best = t; }
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  b->pair_threads = best;
-  b->graphs_valid = false;
+  ts_status ra = apply_tuning(b, best);
+  if (r != TS_OK) return r;
+  if (ra != TS_OK) return ra;
   if (!b->cache_path.empty()) {
     FILE* f = fopen(b->cache_path.c_str(), "a");
-    if (f) { fprintf(f, "%s %d\n", key.c_str(), best); fclose(f); }
+    if (f) {
+      fprintf(f, "%s %d %.17g %.17g %.17g\n", tune_key(b).c_str(), best.item_warps, best.inner_fraction,
+              best.relist_soon, best.bin_factor);
+      fclose(f);
+    }
   }
   return cuda_ok(b, cudaGetLastError(), "ts_autotune") ? TS_OK : TS_ERR_CUDA;
 }

@@ -63,6 +63,11 @@ class FireState(C.Structure):
                 ("converged", C.c_int32), ("nsteps", C.c_int32), ("Fd", C.c_double * 9), ("h0", C.c_double * 9)]
 
 
+class Tuning(C.Structure):
+    _fields_ = [("item_warps", C.c_int32), ("inner_fraction", C.c_double), ("relist_soon", C.c_double),
+                ("bin_factor", C.c_double)]
+
+
 FIRE_STATE_BYTES = C.sizeof(FireState)
 
 _lib = None
@@ -95,7 +100,9 @@ def lib():
         L.ts_vv_adjoint_segment.argtypes = [P, C.POINTER(State), P, I, C.c_int64, C.c_double, P, P, P, I, C.c_double,
                                             I, P, P]
         L.ts_batch_poll.argtypes = [P, P, I]
-        L.ts_autotune.argtypes = [P, C.POINTER(State), P]
+        L.ts_autotune.argtypes = [P, C.POINTER(State), C.POINTER(MDParams), I, P]
+        L.ts_batch_tuning.argtypes = [P, C.POINTER(Tuning)]
+        L.ts_batch_set_tuning.argtypes = [P, C.POINTER(Tuning)]
         L.ts_batch_counters.argtypes = [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
         L.ts_batch_prunes.argtypes = [P, C.POINTER(C.c_int64)]
         L.ts_batch_memory_model.argtypes = [P, C.POINTER(C.c_double), C.POINTER(C.c_double)]
@@ -281,8 +288,26 @@ class Batch:
                                                 _ptr(ax), _ptr(av), _ptr(gParams), int(rdf_every), float(rmax),
                                                 int(K), _ptr(gg), _stream(stream)), "ts_vv_adjoint_segment")
 
-    def autotune(self, s, stream=None):
-        self._check(lib().ts_autotune(self.h, C.byref(s.c()), _stream(stream)), "ts_autotune")
+    def autotune(self, s, dt, kind=TS_LANGEVIN, gamma=0.0, kT=None, seed=0, n_steps=20, stream=None):
+        """Tune the batch's launch and list parameters on MD steps of the state
+        ``s`` (advanced by the trial steps: pass a copy); returns the chosen
+        tuning as a dict."""
+        kT = kT if kT is not None else s.kT
+        p = MDParams(int(kind), float(dt), float(gamma), _ptr(kT) if kT is not None else None, int(seed), 0, 0.0,
+                     None, 0.0, None)
+        self._check(lib().ts_autotune(self.h, C.byref(s.c()), C.byref(p), int(n_steps), _stream(stream)),
+                    "ts_autotune")
+        return self.tuning()
+
+    def tuning(self):
+        t = Tuning()
+        self._check(lib().ts_batch_tuning(self.h, C.byref(t)), "ts_batch_tuning")
+        return dict(item_warps=t.item_warps, inner_fraction=t.inner_fraction, relist_soon=t.relist_soon,
+                    bin_factor=t.bin_factor)
+
+    def set_tuning(self, item_warps=8, inner_fraction=0.3, relist_soon=0.5, bin_factor=1.0):
+        t = Tuning(int(item_warps), float(inner_fraction), float(relist_soon), float(bin_factor))
+        self._check(lib().ts_batch_set_tuning(self.h, C.byref(t)), "ts_batch_set_tuning")
 
     def profile_pair(self, s, reps=5, flush=None, stream=None):
         ms, pairs, atoms = C.c_double(), C.c_int64(), C.c_int64()

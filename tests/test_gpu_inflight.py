@@ -30,28 +30,3 @@ def test_inflight_fig3_stream_fp64():
         assert res[i]["E"] == pytest.approx(a["E"], rel=1e-9, abs=1e-12)
         assert np.allclose(res[i]["cell"], a["cell"], atol=1e-9)
         assert res[i]["fmax"] <= 1e-3 and res[i]["smax"] <= 1e-4
-
-
-def test_autotune_keeps_results(tmp_path):
-    torch = torch_cuda()
-    from paper_2508_06628_b300 import ts
-    hb = W.ragged_mix(seed=5, n_systems=16, lo=32, hi=512)
-    pots = [dict(p, skin=s) for p, s in zip(hb.pots, ts.default_skins(hb.pots))]
-    cache = str(tmp_path / "tune.txt")
-    b = ts.Batch(pots, hb.n_atoms, hb.n_systems, autotune_cache=cache)
-    s = ts.DeviceState.from_host(hb)
-    F0 = torch.zeros((hb.n_atoms, 3), dtype=torch.float64, device="cuda")
-    F1 = torch.zeros_like(F0)
-    b.neighbor_build(s, force=True)
-    b.pair_forces(s, F0)
-    b.autotune(s)
-    b.pair_forces(s, F1)
-    b.poll()
-    assert torch.equal(F0, F1)
-    line = open(cache).read().split()
-    assert line[-1] in ("64", "128", "256")
-    b2 = ts.Batch(pots, hb.n_atoms, hb.n_systems, autotune_cache=cache)   # served from the cache
-    s2 = ts.DeviceState.from_host(hb)
-    b2.neighbor_build(s2, force=True)
-    b2.autotune(s2)
-    b2.poll()
