@@ -57,12 +57,60 @@ class _Buffers:
                               self.pot[:B], self.uid[:B])
 
 
-def relax_inflight(hb, pots, max_scaler, max_active=1024, n_inner=25, precision=ts.TS_MIXED, max_rounds=10000,
-                   device=0, on_round=None, **fire_kw):
+def memory_model(pots, precision=ts.TS_MIXED, max_neighbors=0, device=0):
+    """(bytes per atom, bytes per system) of the engine's device scratch for
+    these potentials and precision (ts_batch_memory_model of a minimal batch)."""
+    b = ts.Batch(pots, 32, 1, precision=precision, max_neighbors=max_neighbors, device=device)
+    a, s = C.c_double(), C.c_double()
+    b._check(ts.lib().ts_batch_memory_model(b.h, C.byref(a), C.byref(s)), "ts_batch_memory_model")
+    b.close()
+    return a.value, s.value
+
+
+def max_scaler_from_budget(probe_atoms, probe_scaler, bytes_per_atom, bytes_per_system, budget_bytes,
+                           max_systems=1_000_000):
+    """The memory probe of Fig. 2 (ts_estimate_max_scaler) with the engine's
+    byte model as its out-of-memory test: copies of probe system k fit while
+    bytes_per_atom * atoms + bytes_per_system * systems <= budget_bytes, and
+    the largest memory scaler is min_k (copies_k * scaler_k).  Host only.
+    Returns (max_scaler, copies per probe system)."""
+    n = len(probe_atoms)
+    FITS = C.CFUNCTYPE(C.c_int, C.c_double, C.c_int, C.c_void_p)
+    L = ts.lib()
+    L.ts_estimate_max_scaler.argtypes = [C.c_void_p, C.c_int, FITS, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]
+    copies, best = [], float("inf")
+    for k in range(n):   # one probe system at a time: the test knows its atom count
+        atoms = float(probe_atoms[k])
+
+        @FITS
+        def fits(total, nsys, ctx, atoms=atoms):
+            return int(bytes_per_atom * atoms * nsys + bytes_per_system * nsys <= budget_bytes)
+
+        sc = (C.c_double * 1)(float(probe_scaler[k]))
+        nfit = (C.c_int * 1)()
+        out = C.c_double()
+        st = L.ts_estimate_max_scaler(sc, 1, fits, None, int(max_systems), nfit, C.byref(out))
+        if st != ts.TS_OK:
+            raise ts.TSError(st, f"probe system {k} ({atoms:.0f} atoms) does not fit the budget once")
+        copies.append(nfit[0])
+        best = min(best, out.value)
+    return best, copies
+
+
+def relax_inflight(hb, pots, max_scaler=None, max_active=1024, n_inner=25, precision=ts.TS_MIXED, max_rounds=10000,
+                   device=0, on_round=None, memory_budget_bytes=None, memory_scales_with="n_atoms", **fire_kw):
     """Relax every system of the host batch ``hb`` (workloads.Batch) with
-    variable-cell FIRE under an atom budget of ``max_scaler`` (memory scales
-    with n_atoms).  Returns a dict per system id with E, fmax, smax, cell and
-    positions at convergence, and the round log."""
+    variable-cell FIRE, admitting systems from the stream while their memory
+    fits (Sec. 3, Figs. 2-3).  Memory is either an atom budget ``max_scaler``
+    (memory scaling with n_atoms), or a device budget ``memory_budget_bytes``
+    turned into a limit on the memory scaler ``memory_scales_with``
+    (``n_atoms`` or ``n_atoms_x_density``) by the Fig. 2 probe over the
+    largest and the densest systems of the stream, with the engine's byte
+    model as the probe's fit test; the batch's atom capacity is what the
+    budget leaves after max_active systems' overhead, and admission keeps
+    both the scaler and the atoms within their limits.  Returns a dict per
+    system id with E, fmax, smax, cell and positions at convergence, and the
+    round log (each round's admitted, active, atoms and active scaler)."""
     torch = ts._torch()
     dev = torch.device("cuda", device)
     L = ts.lib()
@@ -75,14 +123,35 @@ def relax_inflight(hb, pots, max_scaler, max_active=1024, n_inner=25, precision=
     L.ts_batch_compact_admit.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                          C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
     prm = fire_params(**fire_kw)
-    atoms_cap = int(max_scaler)
-    b = ts.Batch(pots, atoms_cap, max_active, precision=precision, device=device)
-    q = C.c_void_p()
-    assert L.ts_sched_create(float(max_scaler), int(max_active), C.byref(q)) == 0
     off = hb.offsets
     n_of = np.diff(off)
+    scaler = memory_sizes(hb, memory_scales_with)
+    if memory_budget_bytes is None:
+        if max_scaler is None:
+            raise ValueError("give max_scaler or memory_budget_bytes")
+        if memory_scales_with != "n_atoms":
+            raise ValueError("an atom budget (max_scaler) admits by n_atoms; give memory_budget_bytes otherwise")
+        atoms_cap, limit = int(max_scaler), float(max_scaler)
+        share = scaler              # in atoms, against the atom budget
+    else:
+        per_atom, per_sys = memory_model(pots, precision, device=device)
+        # what the budget leaves after the systems' overhead, less the layout's
+        # rounding of the slot count up to a whole warp
+        atoms_cap = int((memory_budget_bytes - per_sys * max_active) / per_atom) - 32
+        if atoms_cap < int(n_of.max()):
+            raise ts.TSError(ts.TS_ERR_BUDGET, "the budget does not hold the largest system beside the others' overhead")
+        probes = sorted({int(np.argmax(n_of)), int(np.argmax(scaler))})
+        limit, _ = max_scaler_from_budget(n_of[probes], scaler[probes], per_atom, per_sys, memory_budget_bytes)
+        # the scheduler sees one share per system: the larger of its part of
+        # the scaler limit and its part of the atom capacity (a sum of these
+        # within 1 keeps both sums within their limits)
+        share = np.maximum(scaler / limit, n_of / atoms_cap)
+    b = ts.Batch(pots, atoms_cap, max_active, precision=precision, device=device,
+                 memory_budget_bytes=int(memory_budget_bytes or 0))
+    q = C.c_void_p()
+    assert L.ts_sched_create(limit if memory_budget_bytes is None else 1.0, int(max_active), C.byref(q)) == 0
     for i in range(hb.n_systems):
-        st = L.ts_sched_push(q, i, float(n_of[i]))
+        st = L.ts_sched_push(q, i, float(share[i]))
         if st != 0:
             raise ts.TSError(st, f"system {i} ({n_of[i]} atoms) exceeds the budget")
     bufs = [_Buffers(torch, dev, atoms_cap, max_active), _Buffers(torch, dev, atoms_cap, max_active)]
@@ -129,7 +198,8 @@ def relax_inflight(hb, pots, max_scaler, max_active=1024, n_inner=25, precision=
         s = buf.device_state()
         b.fire_step(s, buf.fs, buf.fvel, prm, n_inner, conv, E, fm, sm)
         c = conv[:buf.n_systems].cpu().numpy().astype(bool)
-        log.append(dict(round=rnd, active=len(ids_active), atoms=buf.n_atoms, admitted=len(new), converged=int(c.sum())))
+        log.append(dict(round=rnd, active=len(ids_active), atoms=buf.n_atoms, admitted=len(new), converged=int(c.sum()),
+                        scaler=float(scaler[np.asarray(ids_active, dtype=np.int64)].sum()) if ids_active else 0.0))
         if on_round:
             on_round(log[-1])
         done = np.nonzero(c)[0]

@@ -118,3 +118,19 @@ def test_binding_fails_loudly_without_gpu():
     from paper_2508_06628_b300 import ts
     with pytest.raises(RuntimeError):
         ts._torch()
+
+
+def test_byte_budget_drives_the_fig2_probe():
+    """The runtime's byte-budget admission runs the Fig. 2 probe with the
+    engine's byte model as its fit test: with 1 byte per atom, 15 bytes per
+    system and a 900-byte budget (the worked example's ~900-atom model),
+    probes of 400 and 80 atoms fit 2 and 9 copies and the limit is 720; with
+    the density scaler the limit is in scaler units (copies x n^2/V)."""
+    from paper_2508_06628_b300 import runtime
+    limit, copies = runtime.max_scaler_from_budget([400, 80], [400, 80], 1.0, 15.0, 900.0)
+    assert copies == [2, 9] and limit == 720.0
+    dens = [400 * 400 / 4000.0, 80 * 80 / 1000.0]           # n_atoms x density of two probe systems
+    limit_d, copies_d = runtime.max_scaler_from_budget([400, 80], dens, 1.0, 15.0, 900.0)
+    assert copies_d == [2, 9] and limit_d == min(2 * dens[0], 9 * dens[1])
+    with pytest.raises(Exception):
+        runtime.max_scaler_from_budget([1000], [1000], 1.0, 15.0, 900.0)   # not even one copy fits
