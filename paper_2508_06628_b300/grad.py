@@ -11,7 +11,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import ts
+from . import parallel, ts
 
 
 def _torch():
@@ -72,11 +72,25 @@ def set_params(batch, params):
     batch.pots = pots
 
 
-def trajectory_rdf(batch, state, dt, T, every, rmax, K, checkpoint=None, store=False):
+def rdf_mse_upstream(g, target, n_total, n_frames):
+    """The loss (1/K) sum_k (g_k - target_k)^2 of the system- and frame-averaged
+    RDF g, and its derivative with respect to each system's RDF at each
+    observed frame, 2 (g - target) / (K n_total n_frames) (the same row for
+    every system).  numpy or torch arrays."""
+    K = g.shape[-1]
+    d = g - target
+    return float((d * d).sum() / K), 2.0 * d / (K * n_total * n_frames)
+
+
+def trajectory_rdf(batch, state, dt, T, every, rmax, K, checkpoint=None, store=False, group=None):
     """NVE velocity Verlet for T steps from ``state`` (not modified); smeared
     RDF averaged over systems and the frames t = every, 2 every, ..., T.
-    Returns (g [K] tensor, checkpoints list of (t, x, v))."""
+    With several ranks (torch.distributed, ``group``) ``state`` holds this
+    rank's systems and the average runs over every rank's systems: one
+    all-reduce of the K bin sums.  Returns (g [K] tensor, checkpoints list of
+    (t, x, v))."""
     torch = _torch()
+    n_total = int(parallel.allreduce_sum([state.n_systems], group)[0])
     checkpoint = checkpoint or every
     x = state.pos.clone()
     v = state.vel.clone()
@@ -92,23 +106,30 @@ def trajectory_rdf(batch, state, dt, T, every, rmax, K, checkpoint=None, store=F
         t = nxt
         if t % every == 0:
             batch.rdf(s, rmax, K, gs)
-            g += gs.sum(0) / (state.n_systems * nfr)
+            g += gs.sum(0) / (n_total * nfr)
         if store and t % checkpoint == 0 and t < T:
             ckpts.append((t, s.pos.clone(), s.vel.clone()))
+    if parallel.rank_world(group)[1] > 1:
+        g = torch.as_tensor(parallel.allreduce_sum(g.cpu().numpy(), group), device=x.device)
     return g, ckpts
 
 
-def rdf_loss_and_grad(batch, state, dt, T, every, rmax, K, target, checkpoint=100):
+def rdf_loss_and_grad(batch, state, dt, T, every, rmax, K, target, checkpoint=100, group=None):
     """Loss = (1/K) sum_k (g_k - target_k)^2 of the trajectory-averaged smeared
     RDF, and d loss / d params [n_pots,3] by the discrete adjoint of velocity
     Verlet with checkpoints every ``checkpoint`` steps (segments recomputed
-    forward, then reversed step by step)."""
+    forward, then reversed step by step).  With several ranks (``group``),
+    ``state`` holds this rank's systems: the averaged RDF takes one all-reduce
+    of K sums, and the parameter gradient one all-reduce of n_pots x 3 sums
+    (for one LJ potential, dL/dsigma and dL/depsilon); every rank returns the
+    global loss and gradient."""
     torch = _torch()
-    g, ckpts = trajectory_rdf(batch, state, dt, T, every, rmax, K, checkpoint, store=True)
+    g, ckpts = trajectory_rdf(batch, state, dt, T, every, rmax, K, checkpoint, store=True, group=group)
     target = torch.as_tensor(target, dtype=torch.float64, device=g.device)
-    loss = float(((g - target) ** 2).mean())
     nfr = T // every
-    gg = (2.0 * (g - target) / K / (state.n_systems * nfr)).expand(state.n_systems, K).contiguous()
+    n_total = int(parallel.allreduce_sum([state.n_systems], group)[0])
+    loss, up = rdf_mse_upstream(g, target, n_total, nfr)
+    gg = up.expand(state.n_systems, K).contiguous()
     N = state.n_atoms
     ax = torch.zeros((N, 3), dtype=torch.float64, device=g.device)
     av = torch.zeros_like(ax)
@@ -130,6 +151,8 @@ def rdf_loss_and_grad(batch, state, dt, T, every, rmax, K, target, checkpoint=10
             batch.md_step(s, 1, dt, kind=ts.TS_NVE)
             fr[t + 1 - t0].copy_(s.pos)
         batch.vv_adjoint_segment(state, fr, t0, dt, ax, av, gth, rdf_every=every, rmax=rmax, K=K, gg=gg)
+    if parallel.rank_world(group)[1] > 1:
+        gth = torch.as_tensor(parallel.allreduce_sum(gth.cpu().numpy(), group), device=g.device)
     return loss, g, gth
 
 

@@ -17,7 +17,7 @@ import ctypes as C
 
 import numpy as np
 
-from . import ts
+from . import parallel, ts
 
 FIRE_DEFAULTS = dict(dt0=0.1, dt_max=1.0, finc=1.1, fdec=0.5, alpha0=0.1, falpha=0.99, maxstep=0.2, fmax=1e-3,
                      smax=1e-4, p_ext=0.0, nmin=5, variable_cell=1)
@@ -275,3 +275,24 @@ def run_binned(hb, pots, max_scaler, n_steps, dt, kind=ts.TS_LANGEVIN, gamma=0.0
             results[int(i)] = dict(pos=pos[off[j]:off[j + 1]], vel=vel[off[j]:off[j + 1]], E=Eh[j], KE=KEh[j], bin=k)
     b.close()
     return results, bins
+
+
+def relax_inflight_sharded(hb, pots, group=None, device=None, **kw):
+    """relax_inflight over several GPUs, one process per GPU: this rank relaxes
+    its shard of the stream (systems balanced by atom count) on its own GPU
+    and the results, keyed by the index in ``hb``, are gathered on every rank
+    (one all-gather after the work; no collective during it).  ``device``:
+    this rank's CUDA device (default: the current one)."""
+    torch = ts._torch()
+    dev = torch.cuda.current_device() if device is None else device
+    return parallel.run_sharded(hb, lambda sub: relax_inflight(sub, pots, device=dev, **kw)[0], group)
+
+
+def run_binned_sharded(hb, pots, max_scaler, n_steps, dt, group=None, device=None, **kw):
+    """run_binned over several GPUs, one process per GPU: this rank bins and
+    evolves its shard (systems balanced by atom count); results keyed by the
+    index in ``hb`` are gathered on every rank."""
+    torch = ts._torch()
+    dev = torch.cuda.current_device() if device is None else device
+    return parallel.run_sharded(hb, lambda sub: run_binned(sub, pots, max_scaler, n_steps, dt, device=dev, **kw)[0],
+                                group)
