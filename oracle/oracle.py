@@ -291,3 +291,44 @@ def traj_rdf_loss(offsets, x0, v0, mass, cells, pbc, pot, dt, T, obs_every, rmax
                                   C.cast(P, C.c_void_p), int(use_cells), float(dt), int(T), int(obs_every),
                                   float(rmax), int(K), _p(_f64(target)), _p(g), _p(gth))
     return loss, g, gth
+
+
+# Voigt order of stress and strain components: xx, yy, zz, yz, xz, xy
+VOIGT = [(0, 0), (1, 1), (2, 2), (1, 2), (0, 2), (0, 1)]
+
+
+def voigt_strain(j, delta):
+    """Symmetric strain tensor of Voigt component j with magnitude delta
+    (engineering shear: the tensor's off-diagonal entries are delta / 2)."""
+    e = np.zeros((3, 3))
+    a, b = VOIGT[j]
+    if a == b:
+        e[a, a] = delta
+    else:
+        e[a, b] = e[b, a] = 0.5 * delta
+    return e
+
+
+def elastic_constants(offsets, x, cells, pbc, pot_of_sys, pots, delta=1e-5, use_cells=False):
+    """Stress-strain coefficients C_ij = d sigma_i / d eps_j [B,6,6] (Voigt,
+    eV/A^3) of each system at its configuration, by central differences of
+    the stress (forces() sign: sigma = (1/V) dE/d eps) under homogeneous
+    strains x -> x (I + eps), h -> h (I + eps) with no internal relaxation (the
+    paper names elastic constants among the properties to come, Sec. 5)."""
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    B = len(offsets) - 1
+    x = _f64(x); cells = _f64(cells).reshape(B, 3, 3)
+    C6 = np.zeros((B, 6, 6))
+    for j in range(6):
+        sig = []
+        for sgn in (1.0, -1.0):
+            M = np.eye(3) + voigt_strain(j, sgn * delta)
+            xs = x.copy()
+            for s in range(B):
+                xs[offsets[s]:offsets[s + 1]] = x[offsets[s]:offsets[s + 1]] @ M
+            _, _, S = forces(offsets, xs, cells @ M, pbc, pot_of_sys, pots, use_cells=use_cells)
+            sig.append(S)
+        dS = (sig[0] - sig[1]) / (2.0 * delta)
+        for i, (a, b) in enumerate(VOIGT):
+            C6[:, i, j] = dS[:, a, b]
+    return C6

@@ -237,3 +237,52 @@ def gamma_frequencies(block, mass):
     d = 0.5 * (block + block.T) * w[:, None] * w[None, :]
     lam = np.linalg.eigvalsh(d)
     return np.sign(lam) * np.sqrt(np.abs(lam))
+
+
+# Voigt order of stress and strain components: xx, yy, zz, yz, xz, xy
+VOIGT = ((0, 0), (1, 1), (2, 2), (1, 2), (0, 2), (0, 1))
+
+
+def elastic_constants(pots, state, delta=1e-5, precision=ts.TS_FP64, device=None):
+    """Stress-strain coefficients C_ij = d sigma_i / d eps_j [B,6,6] (Voigt
+    xx, yy, zz, yz, xz, xy; eV/A^3; engineering shear strains) of every
+    system of ``state`` at its configuration, by central differences of the
+    stress under the homogeneous strains x -> x (I + eps), h -> h (I + eps),
+    eps = +-delta along each Voigt component, without internal relaxation
+    (elastic constants are among the second-order properties the paper lists
+    as next, Sec. 5).  All 12 strained copies of every system are evaluated
+    in one batched ts_pair_forces call in a batch of their own; at zero
+    stress C is the elastic-constant matrix.  ``state`` is not modified."""
+    torch = _torch()
+    pos, cell = state.pos, state.cell
+    dev = pos.device if device is None else device
+    B, N = state.n_systems, state.n_atoms
+    M = torch.zeros((12, 3, 3), dtype=torch.float64, device=dev)
+    for j, (a, b) in enumerate(VOIGT):
+        for c, sgn in enumerate((1.0, -1.0)):
+            e = torch.zeros((3, 3), dtype=torch.float64)
+            if a == b:
+                e[a, a] = sgn * delta
+            else:
+                e[a, b] = e[b, a] = 0.5 * sgn * delta
+            M[2 * j + c] = (torch.eye(3, dtype=torch.float64) + e).to(dev)
+    copies = torch.arange(12, device=dev, dtype=torch.int32)
+    big = ts.DeviceState(
+        torch.einsum("na,cab->cnb", pos.to(dev), M).reshape(12 * N, 3).contiguous(),
+        None, state.mass.to(dev).repeat(12).contiguous(),
+        torch.einsum("sab,cbd->csad", cell.to(dev), M).reshape(12 * B, 3, 3).contiguous(),
+        state.pbc.to(dev).repeat(12, 1).contiguous(),
+        (state.system_idx.to(dev)[None, :] + B * copies[:, None]).reshape(-1).contiguous(),
+        state.pot_idx.to(dev).repeat(12).contiguous(), None)
+    b = ts.Batch(pots, 12 * N, 12 * B, precision=precision, device=dev.index if dev.index is not None else 0)
+    S = torch.zeros((12 * B, 3, 3), dtype=torch.float64, device=dev)
+    b.pair_forces(big, None, None, S)
+    b.poll()
+    b.close()
+    S = S.view(12, B, 3, 3)
+    C = torch.zeros((B, 6, 6), dtype=torch.float64, device=dev)
+    for j in range(6):
+        dS = (S[2 * j] - S[2 * j + 1]) / (2.0 * delta)
+        for i, (a, b_) in enumerate(VOIGT):
+            C[:, i, j] = dS[:, a, b_]
+    return C
