@@ -232,6 +232,22 @@ typedef struct {
 ts_status ts_md_step(ts_batch* b, ts_state* s, const ts_md_params* p, int n_steps, double* E, double* KE,
                      void* stream);
 
+/* ts_md_step that also records the trajectory's positions, for the adjoint's
+ * recomputed segments (Sec. 2: differentiable simulation; the reverse needs
+ * every frame of a checkpointed segment).  frames [n_steps+1][n_atoms][3]
+ * f64 (device, caller order; caller-owned): row 0 receives the positions at
+ * the start of the call (as the library holds them: each atom in the lattice
+ * image nearest its listing reference, so a row may differ from s->pos by
+ * lattice vectors), row k those after k steps.  The last row equals s->pos on
+ * return.  Row k equals the positions after a ts_md_step call of k steps from
+ * the same state and lists.  Kinds TS_NVE, TS_LANGEVIN and TS_NVT_NHC;
+ * TS_ERR_INVALID_ARG for TS_NPT_LANGEVIN (the cell changes every step and is
+ * not recorded), a NULL frames pointer or n_steps < 1; otherwise errors as
+ * ts_md_step.  On a stream other than the legacy default stream the loop is a
+ * CUDA graph cached per (n_steps, parameters, stream, frames pointer). */
+ts_status ts_md_record(ts_batch* b, ts_state* s, const ts_md_params* p, int n_steps, double* frames,
+                       void* stream);
+
 /* FIRE parameters (Bitzek et al. 2006), with the stopping test of the
  * relaxation: max_i |F_i| <= fmax and (variable cell) max_ab |sigma_ab| <= smax. */
 typedef struct {
@@ -301,16 +317,23 @@ ts_status ts_rdf_backward(ts_batch* b, ts_state* s, double rmax, int K, const do
 ts_status ts_vv_adjoint_step(ts_batch* b, ts_state* s, const double* x_next, double dt, double* ax, double* av,
                              double* gParams, void* stream);
 
-/* The reverse of n NVE steps over stored frames, as n calls of
- * ts_vv_adjoint_step issued from the library (no per-step host round trip
- * through the caller).  frames [n+1][n_atoms][3] f64 (device, caller order)
- * hold x_{t0}, ..., x_{t0+n}; ax, av (device, in/out) hold dL/dx, dL/dv at
- * t0+n on entry and at t0 on return; gParams [n_pots][3] (device) accumulates.
- * With rdf_every > 0, before the reverse step out of frame t0+m (m = n ... 1)
- * with (t0+m) % rdf_every == 0, the gradient of sum_{s,k} gg[s][k] g_k(x_{t0+m})
- * (ts_rdf_backward with rmax, K; gg [n_systems][K] f64, device) is added to
- * ax.  s supplies masses, cells, pbc and the topology; s->pos and s->vel are
- * not read.  Errors as ts_vv_adjoint_step and ts_rdf_backward; n >= 1. */
+/* The reverse of n NVE steps over stored frames: the result of n calls of
+ * ts_vv_adjoint_step (up to rounding), issued from the library with the half
+ * kicks of adjacent reverse steps merged as the forward loop merges them:
+ * the two products (dt/2) J(x_m)^T av that the reverse steps out of and into
+ * an interior frame m take with the same av become one product with weight
+ * dt, so each frame costs one pair backward pass instead of two.
+ * frames [n+1][n_atoms][3] f64 (device, caller order) hold x_{t0}, ...,
+ * x_{t0+n}; ax, av (device, in/out) hold dL/dx, dL/dv at t0+n on entry and at
+ * t0 on return; gParams [n_pots][3] (device) accumulates.  With rdf_every > 0,
+ * at every frame t0+m (m = n ... 1) with (t0+m) % rdf_every == 0 the gradient
+ * of sum_{s,k} gg[s][k] g_k(x_{t0+m}) (ts_rdf_backward with rmax, K; gg
+ * [n_systems][K] f64, device) is added to ax before that frame's product.
+ * s supplies masses, cells, pbc and the topology; s->pos and s->vel are not
+ * read.  On a stream other than the legacy default stream, once the batch's
+ * layout is settled, the sweep is a CUDA graph cached per (n, frames, ax, av,
+ * gParams, gg, cell and pbc pointers, dt, rdf_every, t0 mod rdf_every, rmax,
+ * K, stream).  Errors as ts_vv_adjoint_step and ts_rdf_backward; n >= 1. */
 ts_status ts_vv_adjoint_segment(ts_batch* b, ts_state* s, const double* frames, int n, int64_t t0, double dt,
                                 double* ax, double* av, double* gParams, int rdf_every, double rmax, int K,
                                 const double* gg, void* stream);

@@ -550,26 +550,121 @@ extern "C" ts_status ts_vv_adjoint_step(ts_batch* b, ts_state* s, const double* 
   return cuda_ok(b, cudaGetLastError(), "ts_vv_adjoint_step") ? TS_OK : TS_ERR_CUDA;
 }
 
+namespace ts {
+
+// The reverse sweep of ts_vv_adjoint_segment.  With ax, av the adjoints of
+// (x, v) at frame t0+n, the n reverse velocity-Verlet steps issued one at a
+// time take at every interior frame m two products c J(x_m)^T av with the same
+// av (the closing half of the reverse of step m+1 and the opening half of the
+// reverse of step m, c = dt/2).  The sweep takes that product once, with weight
+// dt, as the forward loop merges the half kicks of adjacent steps:
+//   frame n:          ax += (dt/2) J(x_n)^T av;  av += dt ax
+//   frames n-1 .. 1:  ax += dt J(x_m)^T av;      av += dt ax
+//   frame 0:          ax += (dt/2) J(x_0)^T av
+// (J^T av of the pair backward, with its parameter part added to gParams;
+// the RDF gradient at an observed frame m >= 1 is added to ax first).
+static ts_status adjoint_sweep(ts_batch* b, const ts_state* s, const double* frames, int n, int64_t t0, double dt,
+                               double* ax, double* av, double* gParams, int rdf_every, double rmax, int K,
+                               const double* gg, cudaStream_t st) {
+  const int64_t stride = 3 * (int64_t)s->n_atoms;
+  const int g = egrid(b);
+  const int blocks = (int)(((int64_t)b->nwarps * 32 + 127) / 128);
+  const size_t rshm = b->f64 ? 0 : sizeof(float) * (size_t)K * 4;
+  for (int m = n; m >= 0; m--) {
+    ts_state sm = *s;
+    sm.pos = const_cast<double*>(frames + (int64_t)m * stride);
+    sm.vel = nullptr;
+    ts_status r = prologue(b, &sm, st, false);
+    if (r != TS_OK) return r;
+    relist(b, st, false);
+    if (rdf_every > 0 && m >= 1 && (t0 + m) % rdf_every == 0) {
+      if (b->f64) k_rdf_bwd<true><<<blocks, 128, 0, st>>>(b->nwarps, b->d_warp_sys, b->S, b->A, b->Ncap, rmax, K, gg);
+      else k_rdf_bwd<false><<<blocks, 128, rshm, st>>>(b->nwarps, b->d_warp_sys, b->S, b->A, b->Ncap, rmax, K, gg);
+      if (b->f64) k_export_grad<true><<<g, 256, 0, st>>>(b->Npad, b->A, ax, 1);
+      else k_export_grad<false><<<g, 256, 0, st>>>(b->Npad, b->A, ax, 1);
+      b->launches += 2;
+    }
+    const double c = (m == n || m == 0) ? 0.5 * dt : dt;
+    if (b->f64) k_import_grad<true><<<g, 256, 0, st>>>(b->Npad, b->A, av, c);
+    else k_import_grad<false><<<g, 256, 0, st>>>(b->Npad, b->A, av, c);
+    b->launches++;
+    backward_core(b, st, nullptr, nullptr, gParams, 1);
+    const int stage = m > 0 ? 1 : 2;
+    if (b->f64) k_vv_adj<true><<<g, 256, 0, st>>>(b->Npad, b->A, ax, av, dt, stage);
+    else k_vv_adj<false><<<g, 256, 0, st>>>(b->Npad, b->A, ax, av, dt, stage);
+    b->launches++;
+  }
+  return cuda_ok(b, cudaGetLastError(), "adjoint sweep") ? TS_OK : TS_ERR_CUDA;
+}
+
+}  // namespace ts
+
 extern "C" ts_status ts_vv_adjoint_segment(ts_batch* b, ts_state* s, const double* frames, int n, int64_t t0,
                                            double dt, double* ax, double* av, double* gParams, int rdf_every,
                                            double rmax, int K, const double* gg, void* stream) {
   ts_status r = check_state(b, s, false);
   if (r != TS_OK) return r;
-  if (!frames || n < 1 || !ax || !av || !gParams || (rdf_every > 0 && !gg))
+  if (!frames || n < 1 || !ax || !av || !gParams || !(dt > 0) || (rdf_every > 0 && !gg))
     return fail(b, TS_ERR_INVALID_ARG, "bad adjoint segment arguments");
-  const int64_t stride = 3 * (int64_t)s->n_atoms;
-  for (int m = n; m >= 1; m--) {
-    const double* xn = frames + (int64_t)m * stride;
-    if (rdf_every > 0 && (t0 + m) % rdf_every == 0) {
-      ts_state sn = *s;
-      sn.pos = const_cast<double*>(xn);
-      sn.vel = nullptr;
-      if ((r = ts_rdf_backward(b, &sn, rmax, K, gg, ax, stream)) != TS_OK) return r;
-    }
-    ts_state st = *s;
-    st.pos = const_cast<double*>(frames + (int64_t)(m - 1) * stride);
-    st.vel = nullptr;
-    if ((r = ts_vv_adjoint_step(b, &st, xn, dt, ax, av, gParams, stream)) != TS_OK) return r;
+  if (rdf_every > 0) {
+    if ((r = rdf_check(b, rmax, K)) != TS_OK) return r;
+    if (!b->f64 && sizeof(float) * (size_t)K * 4 > 48 * 1024) return fail(b, TS_ERR_INVALID_ARG, "K too large");
   }
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaSetDevice(b->cfg.device);
+  // replayed as a CUDA graph once the layout is settled: the sweep's launches
+  // depend only on the arguments in the key (and on which frames are observed)
+  const bool settled = b->topo_valid && !b->first_import && s->n_systems == b->B && s->n_atoms == b->N;
+  if (!(b->use_graphs && st != nullptr && settled))
+    return adjoint_sweep(b, s, frames, n, t0, dt, ax, av, gParams, rdf_every, rmax, K, gg, st);
+  graph_cache_check(b);
+  ts_graph_entry key;
+  key.kind = 1;
+  key.n_steps = n;
+  key.stream = st;
+  const void* ptrs[8] = {frames, ax, av, gParams, gg, s->cell, s->pbc, nullptr};
+  for (int q = 0; q < 8; q++) key.ptr[q] = ptrs[q];
+  key.ival[0] = rdf_every;
+  key.ival[1] = rdf_every > 0 ? ((t0 % rdf_every) + rdf_every) % rdf_every : 0;
+  key.dval[0] = dt;
+  key.dval[1] = rdf_every > 0 ? rmax : 0.0;
+  key.md_kind = rdf_every > 0 ? K : 0;
+  auto same = [&](const ts_graph_entry& e) {
+    if (e.kind != 1 || e.n_steps != n || e.stream != st || e.md_kind != key.md_kind) return false;
+    for (int q = 0; q < 8; q++) if (e.ptr[q] != key.ptr[q]) return false;
+    return e.ival[0] == key.ival[0] && e.ival[1] == key.ival[1] && e.dval[0] == key.dval[0] && e.dval[1] == key.dval[1];
+  };
+  for (auto& e : b->graphs)
+    if (same(e)) {
+      if (!cuda_ok(b, cudaGraphLaunch(e.exec, st), "cudaGraphLaunch")) return TS_ERR_CUDA;
+      b->launches += e.kernels;
+      return TS_OK;
+    }
+  if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return adjoint_sweep(b, s, frames, n, t0, dt, ax, av, gParams, rdf_every, rmax, K, gg, st);
+  }
+  const int64_t l0 = b->launches;
+  r = adjoint_sweep(b, s, frames, n, t0, dt, ax, av, gParams, rdf_every, rmax, K, gg, st);
+  const int64_t nk = b->launches - l0;
+  b->launches = l0;
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(st, &graph);
+  if (r != TS_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return r;
+  }
+  cudaGraphExec_t exec = nullptr;
+  if (e != cudaSuccess || cudaGraphInstantiate(&exec, graph, cudaGraphInstantiateFlagUseNodePriority) != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return adjoint_sweep(b, s, frames, n, t0, dt, ax, av, gParams, rdf_every, rmax, K, gg, st);
+  }
+  cudaGraphDestroy(graph);
+  key.exec = exec;
+  key.kernels = nk;
+  graph_store(b, key);
+  if (!cuda_ok(b, cudaGraphLaunch(exec, st), "cudaGraphLaunch")) return TS_ERR_CUDA;
+  b->launches += nk;
   return TS_OK;
 }

@@ -724,8 +724,11 @@ extern "C" ts_status ts_pair_forces(ts_batch* b, ts_state* s, double* F, double*
   return cuda_ok(b, cudaGetLastError(), "ts_pair_forces") ? TS_OK : TS_ERR_CUDA;
 }
 
-extern "C" ts_status ts_md_step(ts_batch* b, ts_state* s, const ts_md_params* p, int n_steps, double* E, double* KE,
-                                void* stream) {
+namespace ts {
+
+// ts_md_step, and ts_md_record with frames != nullptr
+static ts_status md_call(ts_batch* b, ts_state* s, const ts_md_params* p, int n_steps, double* E, double* KE,
+                         double* frames, void* stream) {
   ts_status r = check_state(b, s, true);
   if (r != TS_OK) return r;
   if (!p || n_steps < 0 || !(p->dt > 0) ||
@@ -754,7 +757,7 @@ extern "C" ts_status ts_md_step(ts_batch* b, ts_state* s, const ts_md_params* p,
     b->launches++;
   }
   double c1 = exp(-p->gamma * p->dt);
-  r = md_loop(b, st, p, n_steps, c1, E != nullptr || KE != nullptr);
+  r = md_loop(b, st, p, n_steps, c1, E != nullptr || KE != nullptr, frames);
   if (r != TS_OK) return r;
   if (p->kind == TS_NVT_NHC &&
       !cuda_ok(b, cudaMemcpyAsync(p->nhc, b->d_nhc, 48 * b->B, cudaMemcpyDeviceToDevice, st), "nhc"))
@@ -764,7 +767,22 @@ extern "C" ts_status ts_md_step(ts_batch* b, ts_state* s, const ts_md_params* p,
     return TS_ERR_CUDA;
   reduce_sys(b, st, E, nullptr, KE);
   export_state(b, st, s->pos, s->vel);
-  return cuda_ok(b, cudaGetLastError(), "ts_md_step") ? TS_OK : TS_ERR_CUDA;
+  return cuda_ok(b, cudaGetLastError(), frames ? "ts_md_record" : "ts_md_step") ? TS_OK : TS_ERR_CUDA;
+}
+
+}  // namespace ts
+
+extern "C" ts_status ts_md_step(ts_batch* b, ts_state* s, const ts_md_params* p, int n_steps, double* E, double* KE,
+                                void* stream) {
+  return md_call(b, s, p, n_steps, E, KE, nullptr, stream);
+}
+
+extern "C" ts_status ts_md_record(ts_batch* b, ts_state* s, const ts_md_params* p, int n_steps, double* frames,
+                                  void* stream) {
+  if (!b) return TS_ERR_INVALID_ARG;
+  if (!frames || n_steps < 1) return fail(b, TS_ERR_INVALID_ARG, "null frames or no steps");
+  if (p && p->kind == TS_NPT_LANGEVIN) return fail(b, TS_ERR_INVALID_ARG, "NPT changes the cell: not recorded");
+  return md_call(b, s, p, n_steps, nullptr, nullptr, frames, stream);
 }
 
 extern "C" ts_status ts_neighbor_export(ts_batch* b, int32_t* j_out, int32_t* img_out, int32_t* count_out, void* stream) {

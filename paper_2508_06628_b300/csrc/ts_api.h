@@ -8,8 +8,11 @@
 #include "ts_kernels.cuh"
 
 struct ts_graph_entry {
-  int kind = -1;            // 0 = MD loop
+  int kind = -1;            // 0 = MD loop, 1 = adjoint segment
   int n_steps = 0;
+  const void* ptr[8] = {};  // further key: the caller's pointers the graph's nodes hold
+  int64_t ival[2] = {};     //   ... and integer / real arguments
+  double dval[2] = {};
   int md_kind = 0;
   bool need_e = false;
   double dt = 0, c1 = 0;
@@ -142,7 +145,10 @@ void clear_dirty(ts_batch* b, cudaStream_t st);
 void export_state(ts_batch* b, cudaStream_t st, double* pos, double* vel);
 void export_forces(ts_batch* b, cudaStream_t st, double* F);
 void ensure_forces(ts_batch* b, cudaStream_t st);
-ts_status md_loop(ts_batch* b, cudaStream_t st, const ts_md_params* p, int n_steps, double c1, bool need_e);
+ts_status md_loop(ts_batch* b, cudaStream_t st, const ts_md_params* p, int n_steps, double c1, bool need_e,
+                  double* rec = nullptr);
+void graph_cache_check(ts_batch* b);
+bool graph_store(ts_batch* b, const ts_graph_entry& ge);
 void autotune_load(ts_batch* b);
 void fill_devpots(ts_batch* b, DevPot* dp);
 bool tuning_valid(const ts_tuning& t);

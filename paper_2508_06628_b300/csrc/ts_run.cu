@@ -10,10 +10,13 @@
 
 namespace ts {
 
-static void md_body(ts_batch* b, cudaStream_t st, const ts_md_params* p, int n_steps, double c1, bool need_e) {
+static void md_body(ts_batch* b, cudaStream_t st, const ts_md_params* p, int n_steps, double c1, bool need_e,
+                    double* rec) {
   // forces current for every system (re-listing what the import flagged),
   // inside the step graph so that an unchanged state costs a few empty launches
   ensure_forces(b, st);
+  const int64_t rstride = 3 * (int64_t)b->N;   // recorded frames: row k = positions after k steps
+  if (rec) export_state(b, st, rec, nullptr);
   if (p->kind == TS_NPT_LANGEVIN) pair(b, st, true, kPairAll);   // the virial of every system for the first piston kick
   int g = 0;
   {
@@ -93,25 +96,40 @@ static void md_body(ts_batch* b, cudaStream_t st, const ts_md_params* p, int n_s
       final_ke(0.0, nullptr, vscale);
       piston(kNptClose | (k < n_steps - 1 ? kNptOpen : 0), k + 1);
     }
+    if (rec) export_state(b, st, rec + (int64_t)(k + 1) * rstride, nullptr);
   }
   if (nhc) final_ke(0.0, n_steps > 0 ? vscale : nullptr, nullptr);   // the last chain scaling, kinetic energy
   else if (!npt || n_steps == 0) final_ke(n_steps > 0 ? 0.5 * p->dt : 0.0, nullptr, nullptr);
   clear_dirty(b, st);
 }
 
-ts_status md_loop(ts_batch* b, cudaStream_t st, const ts_md_params* p, int n_steps, double c1, bool need_e) {
-  k_set_u64<<<1, 1, 0, st>>>(b->d_step, p->step0);
-  b->launches++;
+// Drop every cached graph once the layout they were captured for is gone.
+void graph_cache_check(ts_batch* b) {
   if (!b->graphs_valid) {
     for (auto& g : b->graphs) if (g.exec) cudaGraphExecDestroy(g.exec);
     b->graphs.clear();
     b->graphs_valid = true;
   }
+}
+
+// Keep an instantiated graph (the oldest of more than 16 is dropped).
+bool graph_store(ts_batch* b, const ts_graph_entry& ge) {
+  if (b->graphs.size() > 16) { cudaGraphExecDestroy(b->graphs.front().exec); b->graphs.erase(b->graphs.begin()); }
+  b->graphs.push_back(ge);
+  return true;
+}
+
+ts_status md_loop(ts_batch* b, cudaStream_t st, const ts_md_params* p, int n_steps, double c1, bool need_e,
+                  double* rec) {
+  k_set_u64<<<1, 1, 0, st>>>(b->d_step, p->step0);
+  b->launches++;
+  graph_cache_check(b);
   bool capturable = b->use_graphs && st != nullptr && n_steps > 0;
   if (capturable) {
     for (auto& g : b->graphs) {
       if (g.kind == 0 && g.n_steps == n_steps && g.md_kind == p->kind && g.need_e == need_e && g.dt == p->dt &&
-          g.c1 == c1 && g.seed == p->seed && g.tau == p->tau && g.p_ext == p->p_ext && g.stream == st) {
+          g.c1 == c1 && g.seed == p->seed && g.tau == p->tau && g.p_ext == p->p_ext && g.stream == st &&
+          g.ptr[0] == rec) {
         if (!cuda_ok(b, cudaGraphLaunch(g.exec, st), "cudaGraphLaunch")) return TS_ERR_CUDA;
         b->launches += g.kernels;
         return TS_OK;
@@ -120,7 +138,7 @@ ts_status md_loop(ts_batch* b, cudaStream_t st, const ts_md_params* p, int n_ste
     cudaGraph_t graph = nullptr;
     if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
       int64_t l0 = b->launches;
-      md_body(b, st, p, n_steps, c1, need_e);
+      md_body(b, st, p, n_steps, c1, need_e, rec);
       int64_t nk = b->launches - l0;
       b->launches = l0;
       cudaError_t e = cudaStreamEndCapture(st, &graph);
@@ -130,8 +148,8 @@ ts_status md_loop(ts_batch* b, cudaStream_t st, const ts_md_params* p, int n_ste
         ts_graph_entry ge;
         ge.kind = 0; ge.n_steps = n_steps; ge.md_kind = p->kind; ge.need_e = need_e; ge.dt = p->dt; ge.c1 = c1;
         ge.seed = p->seed; ge.tau = p->tau; ge.p_ext = p->p_ext; ge.stream = st; ge.exec = exec; ge.kernels = nk;
-        if (b->graphs.size() > 16) { cudaGraphExecDestroy(b->graphs.front().exec); b->graphs.erase(b->graphs.begin()); }
-        b->graphs.push_back(ge);
+        ge.ptr[0] = rec;
+        graph_store(b, ge);
         if (!cuda_ok(b, cudaGraphLaunch(exec, st), "cudaGraphLaunch")) return TS_ERR_CUDA;
         b->launches += nk;
         return TS_OK;
@@ -142,7 +160,7 @@ ts_status md_loop(ts_batch* b, cudaStream_t st, const ts_md_params* p, int n_ste
       cudaGetLastError();
     }
   }
-  md_body(b, st, p, n_steps, c1, need_e);
+  md_body(b, st, p, n_steps, c1, need_e, rec);
   return cuda_ok(b, cudaGetLastError(), "md loop") ? TS_OK : TS_ERR_CUDA;
 }
 

@@ -139,17 +139,15 @@ def rdf_loss_and_grad(batch, state, dt, T, every, rmax, K, target, checkpoint=10
     for seg in range(len(ckpts) - 1, -1, -1):
         t0, x0, v0 = ckpts[seg]
         t1 = bounds[seg + 1]
-        # the segment recomputed forward, every frame kept, then reversed step
-        # by step in the library (RDF gradients at the observed frames)
+        # the segment recomputed forward with every frame recorded (one
+        # library call), then reversed in one library call (RDF gradients at
+        # the observed frames)
         if frames is None or frames.shape[0] < t1 - t0 + 1:
             frames = torch.empty((t1 - t0 + 1, N, 3), dtype=torch.float64, device=g.device)
         fr = frames[:t1 - t0 + 1]
-        fr[0].copy_(x0)
         s = ts.DeviceState(x0.clone(), v0.clone(), state.mass, state.cell, state.pbc, state.system_idx,
                            state.pot_idx, state.uid)
-        for t in range(t0, t1):
-            batch.md_step(s, 1, dt, kind=ts.TS_NVE)
-            fr[t + 1 - t0].copy_(s.pos)
+        batch.md_record(s, fr, dt, kind=ts.TS_NVE)
         batch.vv_adjoint_segment(state, fr, t0, dt, ax, av, gth, rdf_every=every, rmax=rmax, K=K, gg=gg)
     if parallel.rank_world(group)[1] > 1:
         gth = torch.as_tensor(parallel.allreduce_sum(gth.cpu().numpy(), group), device=g.device)

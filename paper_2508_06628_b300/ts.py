@@ -91,6 +91,7 @@ def lib():
         L.ts_batch_max_neighbors.argtypes = [P]
         L.ts_pair_forces.argtypes = [P, C.POINTER(State), P, P, P, P]
         L.ts_md_step.argtypes = [P, C.POINTER(State), C.POINTER(MDParams), I, P, P, P]
+        L.ts_md_record.argtypes = [P, C.POINTER(State), C.POINTER(MDParams), I, P, P]
         L.ts_fire_init.argtypes = [P, C.POINTER(State), C.POINTER(FireParams), P, P, P]
         L.ts_fire_step.argtypes = [P, C.POINTER(State), P, P, C.POINTER(FireParams), I, P, P, P, P, P]
         L.ts_pair_forces_backward.argtypes = [P, C.POINTER(State), P, P, P, P, P, I, P]
@@ -253,6 +254,18 @@ class Batch:
                      float(tau), _ptr(nhc), float(p_ext), _ptr(baro))
         self._check(lib().ts_md_step(self.h, C.byref(s.c()), C.byref(p), int(n_steps), _ptr(E), _ptr(KE),
                                      _stream(stream)), "ts_md_step")
+
+    def md_record(self, s: DeviceState, frames, dt, kind=TS_NVE, gamma=0.0, kT=None, seed=0, step0=0, stream=None,
+                  tau=0.0, nhc=None):
+        """len(frames) - 1 MD steps recording the positions: ``frames``
+        [n_steps + 1, n_atoms, 3] f64 device tensor, row k the positions after
+        k steps (TS_NVE, TS_LANGEVIN or TS_NVT_NHC)."""
+        kT = kT if kT is not None else s.kT
+        p = MDParams(int(kind), float(dt), float(gamma), _ptr(kT) if kT is not None else None, int(seed), int(step0),
+                     float(tau), _ptr(nhc), 0.0, None)
+        n = int(frames.shape[0]) - 1
+        self._check(lib().ts_md_record(self.h, C.byref(s.c()), C.byref(p), n, _ptr(frames), _stream(stream)),
+                    "ts_md_record")
 
     def fire_init(self, s, params, fs, fvel, stream=None):
         self._check(lib().ts_fire_init(self.h, C.byref(s.c()), C.byref(params), _ptr(fs), _ptr(fvel), _stream(stream)),

@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 
 from paper_2508_06628_b300 import workloads as W
-from tests.gpu_util import make_batch, small_mix, torch_cuda
+from tests.gpu_util import frac_diff, make_batch, small_mix, torch_cuda
 
 pytestmark = pytest.mark.gpu
 
@@ -155,8 +155,13 @@ def test_pair_forces_autograd_function(orc):
 @pytest.mark.parametrize("precision", [1, 0])
 def test_adjoint_segment_equals_step_loop(precision):
     """ts_vv_adjoint_segment over 30 stored frames with RDF gradients at every
-    10th frame gives, bit for bit, the adjoints and parameter gradient of the
-    same reverse steps issued one call at a time."""
+    10th frame gives the adjoints and parameter gradient of the same reverse
+    steps issued one call at a time: the segment merges the half kicks of
+    adjacent reverse steps (one backward pass per frame with weight dt instead
+    of two with dt/2), which changes only the order of the additions, so the
+    results agree to rounding.  The graph-replayed sweep (side stream, first
+    call captured, second replayed) equals the directly issued one bit for
+    bit, call for call (a second call starts from the lists the first left)."""
     torch = torch_cuda()
     from paper_2508_06628_b300 import ts
     hb = W.lj_liquid(seed=5, n_systems=3, reps=(2, 2, 3), rattle=0.08, kT=0.5)
@@ -178,13 +183,27 @@ def test_adjoint_segment_equals_step_loop(precision):
             frames[m].copy_(s.pos)
         return b, s, frames
 
+    def segment(b, s, frames, stream=None):
+        ax, av = ax0.clone(), av0.clone()
+        gth = torch.zeros((1, 3), dtype=torch.float64, device="cuda")
+        b.vv_adjoint_segment(s, frames, t0, dt, ax, av, gth, rdf_every=every, rmax=rmax, K=K, gg=gg, stream=stream)
+        b.poll(stream)
+        return ax.cpu().numpy(), av.cpu().numpy(), gth.cpu().numpy()
+
     b, s, frames = setup()
-    ax, av = ax0.clone(), av0.clone()
-    gth = torch.zeros((1, 3), dtype=torch.float64, device="cuda")
-    b.vv_adjoint_segment(s, frames, t0, dt, ax, av, gth, rdf_every=every, rmax=rmax, K=K, gg=gg)
-    b.poll()
-    res_seg = ax.cpu().numpy(), av.cpu().numpy(), gth.cpu().numpy()
+    res_seg = segment(b, s, frames)      # legacy default stream: issued directly
+    res_seg2 = segment(b, s, frames)
     b.close()
+
+    b, s, frames = setup()
+    stream = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        res_cap = segment(b, s, frames, stream)
+        res_rep = segment(b, s, frames, stream)
+    b.close()
+    for a, a2, c, d in zip(res_seg, res_seg2, res_cap, res_rep):
+        assert np.array_equal(a, c) and np.array_equal(a2, d)
 
     b, s, frames = setup()
     ax, av = ax0.clone(), av0.clone()
@@ -200,4 +219,54 @@ def test_adjoint_segment_equals_step_loop(precision):
     b.close()
     assert np.abs(res_seg[0]).max() > 0 and np.abs(res_seg[2]).max() > 0
     for a, c in zip(res_seg, res_loop):
-        assert np.array_equal(a, c)
+        assert np.abs(a - c).max() <= 1e-11 * np.abs(c).max()
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+@pytest.mark.parametrize("kind", [0, 1])
+def test_md_record_rows_equal_shorter_calls(orc, precision, kind):
+    """ts_md_record: row k of the frames equals the positions after a
+    ts_md_step call of k steps from the same state (bit for bit), its last row
+    equals the returned positions, and in FP64 mode the rows follow the
+    oracle's trajectory."""
+    torch = torch_cuda()
+    from paper_2508_06628_b300 import ts
+    hb = small_mix(83, n_systems=5, lo=32, hi=400)
+    dt, n = hb.meta["dt"], 12
+    md = dict(kind=kind, gamma=hb.meta["gamma"] if kind == 1 else 0.0, seed=4)
+
+    def fresh():
+        b = make_batch(hb, precision)
+        s = ts.DeviceState.from_host(hb)
+        b.neighbor_build(s, force=True)
+        return b, s
+
+    b, s = fresh()
+    frames = torch.full((n + 1, hb.n_atoms, 3), float("nan"), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        b.md_record(s, frames, dt, stream=stream, **md)
+        b.poll(stream)
+    torch.cuda.synchronize()
+    fr = frames.cpu().numpy()
+    assert np.isfinite(fr).all()
+    assert np.array_equal(fr[n], s.pos.cpu().numpy())
+    b.close()
+    for k in (1, 5, n):
+        b, s = fresh()
+        b.md_step(s, k, dt, **md)
+        b.poll()
+        assert np.array_equal(fr[k], s.pos.cpu().numpy()), k
+        b.close()
+    if precision == 1:
+        for k in (1, n):
+            xr, _, _, _ = orc.md(hb.offsets, hb.pos, hb.vel, hb.mass, hb.cell, hb.pbc, hb.pot_idx, hb.pots, dt, k,
+                                 kind=kind, kT=hb.kT, gamma=md["gamma"], seed=4, uid=hb.uid)
+            assert np.abs(frac_diff(fr[k], xr, hb.cell, hb.offsets)).max() < 1e-9
+    # NPT is not recorded
+    b, s = fresh()
+    with pytest.raises(ts.TSError) as ei:
+        b.md_record(s, frames, dt, kind=ts.TS_NPT_LANGEVIN)
+    assert ei.value.status == ts.TS_ERR_INVALID_ARG
+    b.close()
