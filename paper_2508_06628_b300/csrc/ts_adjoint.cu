@@ -24,11 +24,12 @@ template <bool F64, bool STRESS>
 __global__ void __launch_bounds__(128, F64 ? 4 : 8) k_pair_bwd(int32_t n_warps, const int32_t* __restrict__ warp_sys, SysArrays S,
                                                   SlotArrays A, const DevPot* __restrict__ pots, int64_t stride,
                                                   const double* __restrict__ gE, const double* __restrict__ gS,
-                                                  double* gpart) {
+                                                  double* gpart, int accum_part, int skip_small) {
   int w = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
   int lane = threadIdx.x & 31;
   if (w >= n_warps) return;
   int s = warp_sys[w];
+  if (skip_small && S.n_atoms[s] <= kSmallMax) return;   // k_pair_bwd_small takes it
   int64_t k = (int64_t)w * kWarp + lane;
   const DevPot P = pots[S.pot[s]];
   bool valid = A.perm[k] >= 0;
@@ -118,7 +119,7 @@ __global__ void __launch_bounds__(128, F64 ? 4 : 8) k_pair_bwd(int32_t n_warps, 
     }
     for (int p = 0; p < 3; p++) {
       double t = warp_sum(gth[p]);
-      if (lane == 0) gpart[4 * (int64_t)w + p] = t;
+      if (lane == 0) gpart[4 * (int64_t)w + p] = accum_part ? gpart[4 * (int64_t)w + p] + t : t;
     }
   } else {
     const float4* tab = S.shift + 2 * (int64_t)s * kNCodes;
@@ -192,8 +193,187 @@ __global__ void __launch_bounds__(128, F64 ? 4 : 8) k_pair_bwd(int32_t n_warps, 
     }
     for (int p = 0; p < 3; p++) {
       const double t = warp_sum((double)gtf[p] - (double)gtc[p]);
-      if (lane == 0) gpart[4 * (int64_t)w + p] = t;
+      if (lane == 0) gpart[4 * (int64_t)w + p] = accum_part ? gpart[4 * (int64_t)w + p] + t : t;
     }
+  }
+}
+
+// Mixed-precision pair backward for the systems of up to kSmallMax atoms
+// (no stress upstream): one CTA per pair work item of the forward kernel,
+// the item's systems staged in shared memory as the same fixed-point records
+// (and, for inner lists in the table format, the same per-warp image tables),
+// so that a pair vector is the exact integer difference converted once to
+// FP32, as in the forward pass; the upstream gF is staged beside them.  Same sums as
+// k_pair_bwd: list order per atom, compensated FP32 parameter sums per thread,
+// FP64 over the warp.
+constexpr int kBwdRecord = 32;   // staged bytes per atom: fixed-point position, upstream gF
+__global__ void __launch_bounds__(kPairSmallThreads, 2) k_pair_bwd_small(
+    int32_t n_items, const int4* __restrict__ items, const int32_t* __restrict__ warp_sys, SysArrays S,
+    SlotArrays A, const DevPot* __restrict__ pots, int64_t stride, const double* __restrict__ gE, double* gpart,
+    int accum_part) {
+  extern __shared__ __align__(16) uint4 smem[];
+  uint4* tabs = smem;                                   // [kItemWarps][kTabEntries] image shifts
+  uint4* sq = smem + kItemWarps * kTabEntries;          // [staged] fixed-point (x, y, z, -)
+  if ((int)blockIdx.x >= n_items) return;
+  const int4 W = items[blockIdx.x];
+  float4* sg = reinterpret_cast<float4*>(sq + W.y * kWarp);   // [staged] upstream gF
+  const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int wg = W.z + wl;
+  const bool mine = wl < W.w;
+  const int s = mine ? warp_sys[wg] : 0;
+  // the inner list holds every pair within rc unless the system was flagged or re-listed since its filtering
+  const bool use_in = mine && !S.prune[s] && !need_relist(S, s);
+  const int fmt = use_in ? S.infmt[s] : kInnerVerlet;
+  const bool staged_tab = use_in && fmt_kind(fmt) == kInnerTab;
+  const int64_t st0 = (int64_t)W.x * kWarp;
+  const int nst = W.y * kWarp;
+#pragma unroll 4
+  for (int t = threadIdx.x; t < nst; t += blockDim.x) {
+    float4 h = __ldg(A.xh + st0 + t), l = __ldg(A.xl + st0 + t);
+    sq[t] = make_uint4(fix_coord(h.x, l.x), fix_coord(h.y, l.y), fix_coord(h.z, l.z), 0u);
+    sg[t] = __ldg(A.g1 + st0 + t);
+  }
+  uint4* tab = tabs + wl * kTabEntries;
+  if (staged_tab) {
+    const uint4* gt = S.shiftq + (int64_t)s * kNCodes;
+    const int ntab = (2 * fmt_bound(fmt, 0) + 1) * (2 * fmt_bound(fmt, 1) + 1) * (2 * fmt_bound(fmt, 2) + 1);
+    const TabDecode td(fmt);
+    for (int c = lane; c < ntab; c += kWarp) tab[c] = __ldg(gt + td.code(c));
+    if (lane == 0) tab[kTabFar] = make_uint4(kFarShift, 0u, 0u, 0u);
+  }
+  __syncthreads();
+  if (!mine) return;
+  const int64_t seg = S.seg_start[s];
+  const int64_t k = (int64_t)wg * kWarp + lane;
+  const int i = (int)(k - seg);
+  const bool valid = i < S.n_atoms[s];
+  const uint4* hq = sq + (seg - st0);
+  const DevPot P = pots[S.pot[s]];
+  const uint4* gtab = S.shiftq + (int64_t)s * kNCodes;
+  const float4* g1s = sg + (seg - st0);
+  const uint4 xi = valid ? hq[i] : make_uint4(0, 0, 0, 0);
+  const float4 gi = valid ? A.g1[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+  const double gEs = gE ? gE[s] : 0.0;
+  const float gEf = (float)gEs;
+  float dpc[3] = {0.f, 0.f, 0.f};
+  if (P.shift && P.kind != TS_SOFT_SPHERE && gEs != 0.0) {
+    float r, d1, d2, dd1[3];
+    PotMath<float>::eval2(P, P.rc2f, r, d1, d2, dpc, dd1);
+  }
+  float gxf[3] = {0.f, 0.f, 0.f}, gtf[3] = {0.f, 0.f, 0.f}, gtc[3] = {0.f, 0.f, 0.f};
+  auto kahan = [&](int p, float v) {
+    const float y = v - gtc[p];
+    const float t = gtf[p] + y;
+    gtc[p] = (t - gtf[p]) - y;
+    gtf[p] = t;
+  };
+  // LJ constants: with s = sigma / r, A = phi'/r = -24 eps (2 s^12 - s^6) / r^2 and
+  // Bc = (phi'' - phi'/r) / r^2 = 24 eps (28 s^12 - 8 s^6) / r^4 need no square root
+  const float sig2 = P.pf[0] * P.pf[0], eps24 = 24.0f * P.pf[1], isig = 1.0f / P.pf[0];
+  const float hgE = 0.5f * gEf;
+  // one entry: neighbour record xj (slot j of the system), image shift sh;
+  // gx_i += (phi'/r) g + (phi'' - phi'/r) (d.g) d / r^2 with g = gF_j - gF_i,
+  // gtheta += (dphi'/dtheta) (d.gF_i) / r + gE/2 (dphi/dtheta - dphi(rc)/dtheta)
+  auto one = [&](auto kind, const uint4& xj, const uint4& sh, int j) {
+    constexpr int K = decltype(kind)::value;
+    const float d0 = (float)(int)(xj.x - xi.x + sh.x) * kFixInv;
+    const float d1v = (float)(int)(xj.y - xi.y + sh.y) * kFixInv;
+    const float d2v = (float)(int)(xj.z - xi.z + sh.z) * kFixInv;
+    const float r2 = fmaf(d0, d0, fmaf(d1v, d1v, d2v * d2v));
+    if (!(r2 < P.rc2f)) return;
+    const float4 gj = g1s[j];
+    const float g0 = gj.x - gi.x, g1v = gj.y - gi.y, g2v = gj.z - gi.z;
+    const float dg = fmaf(d0, g0, fmaf(d1v, g1v, d2v * g2v));
+    const float dgi = fmaf(d0, gi.x, fmaf(d1v, gi.y, d2v * gi.z));
+    if constexpr (K == TS_LJ) {
+      const float ri2 = __frcp_rn(r2);
+      const float s2 = sig2 * ri2, s6 = s2 * s2 * s2, s12 = s6 * s6;
+      const float A = -eps24 * fmaf(2.0f, s12, -s6) * ri2;
+      const float Bc = eps24 * fmaf(28.0f, s12, -8.0f * s6) * ri2 * ri2;
+      const float Bd = Bc * dg;
+      gxf[0] = fmaf(A, g0, fmaf(Bd, d0, gxf[0]));
+      gxf[1] = fmaf(A, g1v, fmaf(Bd, d1v, gxf[1]));
+      gxf[2] = fmaf(A, g2v, fmaf(Bd, d2v, gxf[2]));
+      // dphi'/dsigma = -144 eps (4 s^12 - s^6) / (r sigma), dphi'/deps = phi'/eps;
+      // dphi/dsigma = 24 eps (2 s^12 - s^6) / sigma, dphi/deps = 4 (s^12 - s^6)
+      const float w = dgi * ri2;
+      kahan(0, fmaf(-6.0f * eps24 * isig * fmaf(4.0f, s12, -s6), w,
+                    hgE * (eps24 * isig * fmaf(2.0f, s12, -s6) - dpc[0])));
+      kahan(1, fmaf(-24.0f * fmaf(2.0f, s12, -s6), w, hgE * (4.0f * (s12 - s6) - dpc[1])));
+    } else {
+      float r, p1, p2, dphi[3], dd1[3];
+      PotMath<float>::eval2(P, r2, r, p1, p2, dphi, dd1);
+      const float ri = 1.0f / r;
+      const float A = p1 * ri;
+      const float Bd = (p2 - A) * ri * ri * dg;
+      gxf[0] = fmaf(A, g0, fmaf(Bd, d0, gxf[0]));
+      gxf[1] = fmaf(A, g1v, fmaf(Bd, d1v, gxf[1]));
+      gxf[2] = fmaf(A, g2v, fmaf(Bd, d2v, gxf[2]));
+      const float ugi = dgi * ri;
+      for (int p = 0; p < 3; p++) kahan(p, fmaf(dd1[p], ugi, hgE * (dphi[p] - dpc[p])));
+    }
+  };
+  auto run = [&](auto kind) {
+  if (use_in) {
+    // four entries per 16-byte load, the next group in flight ahead of use
+    const char* hb = reinterpret_cast<const char*>(hq);
+    const char* tb = reinterpret_cast<const char*>(tab);
+    const uint4* lp = reinterpret_cast<const uint4*>(A.nbr_in) + k;
+    const int ng = valid ? (A.nn_in[k] + 3) >> 2 : 0;
+    auto ent1 = [&](uint32_t ent) {
+      const uint32_t off = ent & 0xffffu;
+      const uint4 xj = *reinterpret_cast<const uint4*>(hb + off);
+      uint4 sh;
+      if (staged_tab) {
+        sh = *reinterpret_cast<const uint4*>(tb + (ent >> 16));
+      } else {
+        const uint32_t code = ent >> 16;
+        sh = code == kRawFar ? make_uint4(kFarShift, 0u, 0u, 0u)
+                             : (code != (uint32_t)kCenter ? __ldg(gtab + code) : make_uint4(0u, 0u, 0u, 0u));
+      }
+      one(kind, xj, sh, (int)(off >> 4));
+    };
+    uint4 n0 = make_uint4(0, 0, 0, 0);
+    if (ng > 0) n0 = __ldcs(lp);
+    for (int gq = 0; gq < ng; gq++) {
+      const uint4 e = n0;
+      if (gq + 1 < ng) n0 = __ldcs(lp + (int64_t)(gq + 1) * stride);
+      ent1(e.x); ent1(e.y); ent1(e.z); ent1(e.w);
+    }
+  } else {
+    const int nn = valid ? A.nn[k] : 0;
+    const uint32_t* lp = A.nbr + k;
+    auto ent1 = [&](uint32_t ent) {
+      const int code = (int)(ent >> kJBits);
+      const int j = (int)(ent & kJMask);
+      const uint4 sh = code != kCenter ? __ldg(gtab + code) : make_uint4(0, 0, 0, 0);
+      one(kind, hq[j], sh, j);
+    };
+    int q = 0;
+    uint32_t n0 = 0, n1 = 0, n2 = 0, n3 = 0;
+    if (nn >= 4) { n0 = __ldcs(lp); n1 = __ldcs(lp + stride); n2 = __ldcs(lp + 2 * stride); n3 = __ldcs(lp + 3 * stride); }
+    for (; q + 4 <= nn; q += 4) {
+      uint32_t e0 = n0, e1 = n1, e2 = n2, e3 = n3;
+      if (q + 8 <= nn) {
+        const uint32_t* np = lp + (int64_t)(q + 4) * stride;
+        n0 = __ldcs(np); n1 = __ldcs(np + stride); n2 = __ldcs(np + 2 * stride); n3 = __ldcs(np + 3 * stride);
+      }
+      ent1(e0); ent1(e1); ent1(e2); ent1(e3);
+    }
+    for (; q < nn; q++) ent1(__ldcs(lp + (int64_t)q * stride));
+  }
+  };
+  // one loop per potential kind (uniform over the warp)
+  if (P.kind == TS_LJ) run(std::integral_constant<int, TS_LJ>{});
+  else if (P.kind == TS_MORSE) run(std::integral_constant<int, TS_MORSE>{});
+  else run(std::integral_constant<int, TS_SOFT_SPHERE>{});
+  if (valid) {
+    const float4 F = A.F[k];
+    A.g0[k] = make_float4(gxf[0] - gEf * F.x, gxf[1] - gEf * F.y, gxf[2] - gEf * F.z, 0.f);
+  }
+  for (int p = 0; p < 3; p++) {
+    const double t = warp_sum((double)gtf[p] - (double)gtc[p]);
+    if (lane == 0) gpart[4 * (int64_t)wg + p] = accum_part ? gpart[4 * (int64_t)wg + p] + t : t;
   }
 }
 
@@ -422,19 +602,39 @@ static int egrid(ts_batch* b) {
   return (int)(g < 1 ? 1 : (g > 148 * 16 ? 148 * 16 : g));
 }
 
-// gx of the current gF (in g1 / gd1) into slots g0 / gd0; parameter gradients into gParams
+bool bwd_attributes(ts_batch* b) {
+  return cuda_ok(b, cudaFuncSetAttribute(k_pair_bwd_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(kPairTabBytes + kBwdRecord * kSmallMax)), "smem attribute");
+}
+
+// parameter gradients of the per-warp partials into gParams
+static void gparam_reduce(ts_batch* b, cudaStream_t st, double* gParams, int accumulate_params) {
+  k_gparam_sys<<<(b->B * 32 + 127) / 128, 128, 0, st>>>(b->B, b->S, b->d_gparam_part, b->d_scal);
+  k_gparam_pot<<<1, 32 * b->n_pots, 0, st>>>(b->B, b->n_pots, b->S, b->d_scal, gParams, accumulate_params);
+  b->launches += 2;
+}
+
+// gx of the current gF (in g1 / gd1) into slots g0 / gd0; per-warp parameter
+// partials written (accum_part = 0) or added to (1); with gParams, reduced into it
 static void backward_core(ts_batch* b, cudaStream_t st, const double* gE, const double* gS, double* gParams,
-                          int accumulate_params) {
+                          int accumulate_params, int accum_part = 0) {
   int blocks = (int)(((int64_t)b->nwarps * 32 + 127) / 128);
-  auto kern = b->f64 ? (gS ? k_pair_bwd<true, true> : k_pair_bwd<true, false>)
-                     : (gS ? k_pair_bwd<false, true> : k_pair_bwd<false, false>);
-  kern<<<blocks, 128, 0, st>>>(b->nwarps, b->d_warp_sys, b->S, b->A, b->d_pots, b->Ncap, gE, gS, b->d_gparam_part);
-  b->launches++;
-  if (gParams) {
-    k_gparam_sys<<<(b->B * 32 + 127) / 128, 128, 0, st>>>(b->B, b->S, b->d_gparam_part, b->d_scal);
-    k_gparam_pot<<<1, 32 * b->n_pots, 0, st>>>(b->B, b->n_pots, b->S, b->d_scal, gParams, accumulate_params);
-    b->launches += 2;
+  // mixed precision without a stress upstream: systems up to kSmallMax atoms from shared memory
+  const size_t shm = kPairTabBytes + (size_t)kBwdRecord * b->nst_max;
+  const bool small = !b->f64 && !gS && b->use_small_pair && b->bwd_small && b->n_items > 0;
+  if (small) {
+    k_pair_bwd_small<<<b->n_items, 32 * b->tune.item_warps, shm, st>>>(
+        b->n_items, b->d_items, b->d_warp_sys, b->S, b->A, b->d_pots, b->Ncap, gE, b->d_gparam_part, accum_part);
+    b->launches++;
   }
+  if (!small || b->n_large > 0) {
+    auto kern = b->f64 ? (gS ? k_pair_bwd<true, true> : k_pair_bwd<true, false>)
+                       : (gS ? k_pair_bwd<false, true> : k_pair_bwd<false, false>);
+    kern<<<blocks, 128, 0, st>>>(b->nwarps, b->d_warp_sys, b->S, b->A, b->d_pots, b->Ncap, gE, gS,
+                                 b->d_gparam_part, accum_part, small ? 1 : 0);
+    b->launches++;
+  }
+  if (gParams) gparam_reduce(b, st, gParams, accumulate_params);
 }
 
 static ts_status rdf_check(ts_batch* b, double rmax, int K) {
@@ -561,8 +761,10 @@ namespace ts {
 //   frame n:          ax += (dt/2) J(x_n)^T av;  av += dt ax
 //   frames n-1 .. 1:  ax += dt J(x_m)^T av;      av += dt ax
 //   frame 0:          ax += (dt/2) J(x_0)^T av
-// (J^T av of the pair backward, with its parameter part added to gParams;
-// the RDF gradient at an observed frame m >= 1 is added to ax first).
+// (J^T av of the pair backward; its parameter part is summed per warp over
+// the frames and reduced into gParams once; the RDF gradient at an observed
+// frame m >= 1 is added to ax first).  The cell is the same at every frame,
+// so only the first import computes the geometry and image shifts.
 static ts_status adjoint_sweep(ts_batch* b, const ts_state* s, const double* frames, int n, int64_t t0, double dt,
                                double* ax, double* av, double* gParams, int rdf_every, double rmax, int K,
                                const double* gg, cudaStream_t st) {
@@ -574,7 +776,7 @@ static ts_status adjoint_sweep(ts_batch* b, const ts_state* s, const double* fra
     ts_state sm = *s;
     sm.pos = const_cast<double*>(frames + (int64_t)m * stride);
     sm.vel = nullptr;
-    ts_status r = prologue(b, &sm, st, false);
+    ts_status r = prologue(b, &sm, st, false, false, m == n);
     if (r != TS_OK) return r;
     relist(b, st, false);
     if (rdf_every > 0 && m >= 1 && (t0 + m) % rdf_every == 0) {
@@ -588,12 +790,13 @@ static ts_status adjoint_sweep(ts_batch* b, const ts_state* s, const double* fra
     if (b->f64) k_import_grad<true><<<g, 256, 0, st>>>(b->Npad, b->A, av, c);
     else k_import_grad<false><<<g, 256, 0, st>>>(b->Npad, b->A, av, c);
     b->launches++;
-    backward_core(b, st, nullptr, nullptr, gParams, 1);
+    backward_core(b, st, nullptr, nullptr, nullptr, 1, m < n ? 1 : 0);
     const int stage = m > 0 ? 1 : 2;
     if (b->f64) k_vv_adj<true><<<g, 256, 0, st>>>(b->Npad, b->A, ax, av, dt, stage);
     else k_vv_adj<false><<<g, 256, 0, st>>>(b->Npad, b->A, ax, av, dt, stage);
     b->launches++;
   }
+  gparam_reduce(b, st, gParams, 1);
   return cuda_ok(b, cudaGetLastError(), "adjoint sweep") ? TS_OK : TS_ERR_CUDA;
 }
 

@@ -198,6 +198,8 @@ extern "C" ts_status ts_batch_create(const ts_batch_config* cfg, const ts_potent
     b->prio_hi = greatest;
     const char* e = getenv("TS_OVERLAP_RELIST");
     if (e && atoi(e) == 0) b->overlap_relist = false;
+    e = getenv("TS_BWD_SMALL");
+    if (e && atoi(e) == 0) b->bwd_small = false;
   }
   if (ok) ok = cuda_ok(b, cudaFuncSetAttribute(k_relist_small<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)sizeof(SmallSmem)), "smem attribute") &&
@@ -206,7 +208,8 @@ extern "C" ts_status ts_batch_create(const ts_batch_config* cfg, const ts_potent
                cuda_ok(b, cudaFuncSetAttribute(k_pair_small<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)(kPairTabBytes + kSmallRecord * kSmallMax)), "smem attribute") &&
                cuda_ok(b, cudaFuncSetAttribute(k_pair_small<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)(kPairTabBytes + kSmallRecord * kSmallMax)), "smem attribute");
+                                               (int)(kPairTabBytes + kSmallRecord * kSmallMax)), "smem attribute") &&
+               bwd_attributes(b);
   if (!ok) { ts_batch_destroy(b); return TS_ERR_CUDA; }
   b->dp_host.assign(dp, dp + kMaxPots);
   *out = b;
@@ -481,7 +484,7 @@ ts_status check_state(ts_batch* b, const ts_state* s, bool need_vel) {
 
 // Per-call prologue: topology (if needed), cell geometry, image shifts,
 // position import with dirty / skin flags.
-ts_status prologue(ts_batch* b, ts_state* s, cudaStream_t st, bool import_vel, bool fire) {
+ts_status prologue(ts_batch* b, ts_state* s, cudaStream_t st, bool import_vel, bool fire, bool geometry) {
   cudaSetDevice(b->cfg.device);
   if (!b->topo_valid || s->n_systems != b->B || s->n_atoms != b->N) {
     ts_status r = derive_topology(b, s, st);
@@ -492,14 +495,19 @@ ts_status prologue(ts_batch* b, ts_state* s, cudaStream_t st, bool import_vel, b
   // checks against the listing cell (its skin test has no room for a cell
   // change); FIRE, whose own test budgets the cell change since the listing,
   // checks only for a change made by the caller since the last call.
+  // (geometry = false: the caller knows the cell is the one of its previous
+  // import, so the geometry and the image shifts stand)
   const int cell_check = b->first_import ? 0 : (fire ? 1 : 2);
-  k_geometry<<<(B + 31) / 32, 32, 0, st>>>(B, b->S, s->cell, s->pbc, b->d_pots, b->d_err, cell_check);
-  k_shift_table<<<(int)(((int64_t)B * 32 + 127) / 128), 128, 0, st>>>(B, b->S);
+  if (geometry || b->first_import) {
+    k_geometry<<<(B + 31) / 32, 32, 0, st>>>(B, b->S, s->cell, s->pbc, b->d_pots, b->d_err, cell_check);
+    k_shift_table<<<(int)(((int64_t)B * 32 + 127) / 128), 128, 0, st>>>(B, b->S);
+    b->launches += 2;
+  }
   int g = grid_for(b->Npad, 256);
   const int wv = import_vel ? 1 : 0;   // velocities in the same pass
   if (b->f64) k_import_pos<true><<<g, 256, 0, st>>>(b->Npad, b->S, b->A, s->pos, b->d_pots, !b->first_import, b->d_err, wv, s->vel, s->mass);
   else k_import_pos<false><<<g, 256, 0, st>>>(b->Npad, b->S, b->A, s->pos, b->d_pots, !b->first_import, b->d_err, wv, s->vel, s->mass);
-  b->launches += 3;
+  b->launches++;
   b->first_import = false;
   return cuda_ok(b, cudaGetLastError(), "prologue launch") ? TS_OK : TS_ERR_CUDA;
 }

@@ -77,6 +77,7 @@ struct ts_batch {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaEvent_t ev_pruned = nullptr;   // after the MD step's re-filtering pair launch
   bool overlap_relist = true;
+  bool bwd_small = true;          // pair backward of small systems from shared memory (mixed precision)
   int prio_hi = 0;                // numerically greatest-priority value of the device
   // launch shapes and list parameters (autotuned, ts_tune.cu)
   int pair_threads = 128;
@@ -96,7 +97,8 @@ ts_status fail(ts_batch* b, ts_status st, const std::string& msg);
 size_t scratch_bytes(int64_t Ncap, int64_t Bcap, int64_t Ccap, int32_t max_nbrs, bool f64);
 ts_status derive_topology(ts_batch* b, const ts_state* s, cudaStream_t st);
 ts_status check_state(ts_batch* b, const ts_state* s, bool need_vel);
-ts_status prologue(ts_batch* b, ts_state* s, cudaStream_t st, bool import_vel, bool fire = false);
+ts_status prologue(ts_batch* b, ts_state* s, cudaStream_t st, bool import_vel, bool fire = false,
+                   bool geometry = true);
 // Kernel launch with a scheduling priority (0: the stream's own).  Stream
 // capture keeps the launch attribute as the kernel node's priority.
 template <typename... KArgs, typename... Args>
@@ -148,6 +150,7 @@ void ensure_forces(ts_batch* b, cudaStream_t st);
 ts_status md_loop(ts_batch* b, cudaStream_t st, const ts_md_params* p, int n_steps, double c1, bool need_e,
                   double* rec = nullptr);
 void graph_cache_check(ts_batch* b);
+bool bwd_attributes(ts_batch* b);
 bool graph_store(ts_batch* b, const ts_graph_entry& ge);
 void autotune_load(ts_batch* b);
 void fill_devpots(ts_batch* b, DevPot* dp);

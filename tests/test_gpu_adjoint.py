@@ -35,6 +35,44 @@ def test_pair_backward_matches_oracle(orc, precision):
     assert np.all(np.abs(gp - gpr) <= rel * np.abs(gpr) + rel * 1e-2 * np.abs(gpr).max())
 
 
+@pytest.mark.parametrize("with_stress", [False, True])
+def test_pair_backward_small_and_large_systems(orc, with_stress):
+    """Mixed precision: without a stress upstream the systems of up to 2048
+    atoms take the shared-memory backward and a 2304-atom system the gather
+    kernel in the same call; with one, every system takes the gather kernel.
+    Both against the oracle."""
+    torch = torch_cuda()
+    from paper_2508_06628_b300 import ts
+    rng = np.random.default_rng(9)
+    p, c = W.lattice("fcc", (8, 8, 9), 5.26)
+    c2 = c @ (np.eye(3) + np.array([[0, 0.03, 0], [0.01, 0, 0], [0, 0.02, 0]]))
+    p = p @ np.linalg.solve(c, c2) + rng.normal(0, 0.05, p.shape)
+    big = dict(pos=p, vel=np.zeros_like(p), mass=np.full(len(p), 39.948), cell=c2, pot=0)
+    small = small_mix(19, n_systems=5, lo=32, hi=600)
+    systems = [dict(pos=small.pos[small.offsets[k]:small.offsets[k + 1]],
+                    vel=np.zeros((small.offsets[k + 1] - small.offsets[k], 3)),
+                    mass=small.mass[small.offsets[k]:small.offsets[k + 1]], cell=small.cell[k],
+                    pot=int(small.pot_idx[k])) for k in range(5)]
+    hb = W.concat(systems[:2] + [big] + systems[2:], small.pots)
+    b = make_batch(hb, 0)
+    s = ts.DeviceState.from_host(hb)
+    b.neighbor_build(s, force=True)
+    gF = rng.normal(size=(hb.n_atoms, 3))
+    gE = rng.normal(size=hb.n_systems)
+    gS = rng.normal(size=(hb.n_systems, 3, 3)) if with_stress else None
+    t = lambda a: torch.as_tensor(a, dtype=torch.float64, device="cuda").contiguous()
+    gx = torch.zeros((hb.n_atoms, 3), dtype=torch.float64, device="cuda")
+    gp = torch.zeros((len(hb.pots), 3), dtype=torch.float64, device="cuda")
+    b.pair_forces_backward(s, t(gF), t(gE), t(gS) if with_stress else None, gx, gp)
+    b.poll()
+    gxr, gpr = orc.forces_backward(hb.offsets, s.pos.cpu().numpy(), hb.cell, hb.pbc, hb.pot_idx, hb.pots, gF, gE,
+                                   gS if with_stress else np.zeros((hb.n_systems, 3, 3)), use_cells=True)
+    gx, gp = gx.cpu().numpy(), gp.cpu().numpy()
+    assert np.abs(gx - gxr).max() <= 1e-4 * np.abs(gxr).max()
+    assert np.all(np.abs(gp - gpr) <= 1e-4 * np.abs(gpr) + 1e-6 * np.abs(gpr).max())
+    b.close()
+
+
 def backward_after_md(hb, precision, with_stress):
     torch = torch_cuda()
     from paper_2508_06628_b300 import ts
