@@ -244,7 +244,8 @@ ts_status ts_md_step(ts_batch* b, ts_state* s, const ts_md_params* p, int n_step
  * TS_ERR_INVALID_ARG for TS_NPT_LANGEVIN (the cell changes every step and is
  * not recorded), a NULL frames pointer or n_steps < 1; otherwise errors as
  * ts_md_step.  On a stream other than the legacy default stream the loop is a
- * CUDA graph cached per (n_steps, parameters, stream, frames pointer). */
+ * CUDA graph cached per (n_steps, parameters, stream) as in ts_md_step; the
+ * frames address is read on the device, so one graph serves every buffer. */
 ts_status ts_md_record(ts_batch* b, ts_state* s, const ts_md_params* p, int n_steps, double* frames,
                        void* stream);
 
@@ -331,9 +332,12 @@ ts_status ts_vv_adjoint_step(ts_batch* b, ts_state* s, const double* x_next, dou
  * [n_systems][K] f64, device) is added to ax before that frame's product.
  * s supplies masses, cells, pbc and the topology; s->pos and s->vel are not
  * read.  On a stream other than the legacy default stream, once the batch's
- * layout is settled, the sweep is a CUDA graph cached per (n, frames, ax, av,
- * gParams, gg, cell and pbc pointers, dt, rdf_every, t0 mod rdf_every, rmax,
- * K, stream).  Errors as ts_vv_adjoint_step and ts_rdf_backward; n >= 1. */
+ * layout is settled, a call whose arguments (n, frames, ax, av, gParams, gg,
+ * cell and pbc pointers, dt, rdf_every, t0 mod rdf_every, rmax, K, stream)
+ * repeat those of an earlier call is captured as a CUDA graph and replayed by
+ * later such calls; a first call is issued directly (a one-off sweep over a
+ * long stored trajectory is queued far ahead of the device anyway).  Errors
+ * as ts_vv_adjoint_step and ts_rdf_backward; n >= 1. */
 ts_status ts_vv_adjoint_segment(ts_batch* b, ts_state* s, const double* frames, int n, int64_t t0, double dt,
                                 double* ax, double* av, double* gParams, int rdf_every, double rmax, int K,
                                 const double* gg, void* stream);
@@ -436,7 +440,7 @@ typedef struct {
 /* Autotuner (the paper has no counterpart).  Times the MD step of p (n_steps
  * per timed call, CUDA events around CUDA-graph replays on `stream`) for
  * candidate values of each ts_tuning field in turn -- bin_factor {1, 0.5},
- * item_warps {8, 4}, inner_fraction {0.2, 0.3, 0.45}, relist_soon {0.4, 0.5,
+ * item_warps {8, 4}, inner_fraction {0.2, 0.3, 0.45, 1}, relist_soon {0.4, 0.5,
  * 0.6} -- keeping the fastest value of each before tuning the next, applies
  * the result and appends it to cfg->autotune_cache (host text file, one
  * "key item_warps inner_fraction relist_soon bin_factor" line; key = potential

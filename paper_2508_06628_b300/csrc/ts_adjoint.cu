@@ -837,12 +837,22 @@ extern "C" ts_status ts_vv_adjoint_segment(ts_batch* b, ts_state* s, const doubl
     for (int q = 0; q < 8; q++) if (e.ptr[q] != key.ptr[q]) return false;
     return e.ival[0] == key.ival[0] && e.ival[1] == key.ival[1] && e.dval[0] == key.dval[0] && e.dval[1] == key.dval[1];
   };
-  for (auto& e : b->graphs)
-    if (same(e)) {
-      if (!cuda_ok(b, cudaGraphLaunch(e.exec, st), "cudaGraphLaunch")) return TS_ERR_CUDA;
-      b->launches += e.kernels;
-      return TS_OK;
-    }
+  // a key seen for the first time is only remembered (a one-off sweep, such
+  // as one over a whole stored trajectory, is issued directly: its launches
+  // are queued far ahead of the device); its second call is captured
+  int seen = -1;
+  for (size_t q = 0; q < b->graphs.size(); q++) {
+    ts_graph_entry& e = b->graphs[q];
+    if (!same(e)) continue;
+    if (!e.exec) { seen = (int)q; break; }
+    if (!cuda_ok(b, cudaGraphLaunch(e.exec, st), "cudaGraphLaunch")) return TS_ERR_CUDA;
+    b->launches += e.kernels;
+    return TS_OK;
+  }
+  if (seen < 0) {
+    graph_store(b, key);
+    return adjoint_sweep(b, s, frames, n, t0, dt, ax, av, gParams, rdf_every, rmax, K, gg, st);
+  }
   if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
     cudaGetLastError();
     return adjoint_sweep(b, s, frames, n, t0, dt, ax, av, gParams, rdf_every, rmax, K, gg, st);
@@ -864,9 +874,8 @@ extern "C" ts_status ts_vv_adjoint_segment(ts_batch* b, ts_state* s, const doubl
     return adjoint_sweep(b, s, frames, n, t0, dt, ax, av, gParams, rdf_every, rmax, K, gg, st);
   }
   cudaGraphDestroy(graph);
-  key.exec = exec;
-  key.kernels = nk;
-  graph_store(b, key);
+  b->graphs[seen].exec = exec;
+  b->graphs[seen].kernels = nk;
   if (!cuda_ok(b, cudaGraphLaunch(exec, st), "cudaGraphLaunch")) return TS_ERR_CUDA;
   b->launches += nk;
   return TS_OK;

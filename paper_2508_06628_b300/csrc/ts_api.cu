@@ -153,7 +153,7 @@ extern "C" ts_status ts_batch_create(const ts_batch_config* cfg, const ts_potent
   int64_t N = b->Ncap, B = b->Bcap;
   ok = ok && alloc(b, b->d_pots, kMaxPots) && alloc(b, b->d_err, 4) && alloc(b, b->d_counters, 4) &&
 
-       alloc(b, b->d_step, 2);
+       alloc(b, b->d_step, 2) && alloc(b, b->d_rec, 1);
   ok = ok && alloc(b, S.seg_start, B) && alloc(b, S.n_atoms, B) && alloc(b, S.caller_off, B + 1) && alloc(b, S.pot, B) &&
        alloc(b, S.uid, B) && alloc(b, S.bin_off, B) && alloc(b, S.bin_cap, B) && alloc(b, S.warp_start, B) &&
        alloc(b, S.warp_end, B) && alloc(b, S.h, 9 * B) && alloc(b, S.hinv, 9 * B) && alloc(b, S.hinvf, 9 * B) && alloc(b, S.href, 9 * B) &&

@@ -54,6 +54,7 @@ struct ts_batch {
   int32_t* d_err = nullptr;
   int64_t* d_counters = nullptr;
   uint64_t* d_step = nullptr;
+  uint64_t* d_rec = nullptr;      // base address of the frames ts_md_record writes (read by the step graph)
   double* d_partial = nullptr;
   int32_t* d_warp_sys = nullptr;
   int32_t* d_count = nullptr;

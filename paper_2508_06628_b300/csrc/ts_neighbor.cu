@@ -188,6 +188,27 @@ __global__ void k_export_state(int64_t Npad, SlotArrays A, double* pos, double* 
   }
 }
 
+// positions into row `row` of the frames whose base address is *base
+// (caller order, rows of 3 * n_atoms doubles): the base is read on the device,
+// so that a captured step loop writes wherever the latest call points it
+template <bool F64>
+__global__ void k_export_frame(int64_t Npad, SlotArrays A, const uint64_t* __restrict__ base, int64_t row,
+                               int64_t n_atoms) {
+  double* pos = reinterpret_cast<double*>(*base) + row * 3 * n_atoms;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < Npad; k += (int64_t)gridDim.x * blockDim.x) {
+    int p = A.perm[k];
+    if (p < 0) continue;
+    if constexpr (F64) {
+      for (int c = 0; c < 3; c++) pos[3 * (int64_t)p + c] = A.xd[3 * k + c];
+    } else {
+      float4 h = A.xh[k], l = A.xl[k];
+      pos[3 * (int64_t)p] = (double)h.x + (double)l.x;
+      pos[3 * (int64_t)p + 1] = (double)h.y + (double)l.y;
+      pos[3 * (int64_t)p + 2] = (double)h.z + (double)l.z;
+    }
+  }
+}
+
 template <bool F64>
 __global__ void k_export_forces(int64_t Npad, SlotArrays A, double* F) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < Npad; k += (int64_t)gridDim.x * blockDim.x) {

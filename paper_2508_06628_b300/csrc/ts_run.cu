@@ -11,12 +11,19 @@
 namespace ts {
 
 static void md_body(ts_batch* b, cudaStream_t st, const ts_md_params* p, int n_steps, double c1, bool need_e,
-                    double* rec) {
+                    bool rec) {
   // forces current for every system (re-listing what the import flagged),
   // inside the step graph so that an unchanged state costs a few empty launches
   ensure_forces(b, st);
-  const int64_t rstride = 3 * (int64_t)b->N;   // recorded frames: row k = positions after k steps
-  if (rec) export_state(b, st, rec, nullptr);
+  // recorded frames (base address in b->d_rec): row k = positions after k steps
+  auto record = [&](int64_t row) {
+    const int64_t blk = (b->Npad + 255) / 256;
+    const int gr = (int)(blk < 1 ? 1 : (blk > 148 * 16 ? 148 * 16 : blk));
+    if (b->f64) k_export_frame<true><<<gr, 256, 0, st>>>(b->Npad, b->A, b->d_rec, row, b->N);
+    else k_export_frame<false><<<gr, 256, 0, st>>>(b->Npad, b->A, b->d_rec, row, b->N);
+    b->launches++;
+  };
+  if (rec) record(0);
   if (p->kind == TS_NPT_LANGEVIN) pair(b, st, true, kPairAll);   // the virial of every system for the first piston kick
   int g = 0;
   {
@@ -96,7 +103,7 @@ static void md_body(ts_batch* b, cudaStream_t st, const ts_md_params* p, int n_s
       final_ke(0.0, nullptr, vscale);
       piston(kNptClose | (k < n_steps - 1 ? kNptOpen : 0), k + 1);
     }
-    if (rec) export_state(b, st, rec + (int64_t)(k + 1) * rstride, nullptr);
+    if (rec) record(k + 1);
   }
   if (nhc) final_ke(0.0, n_steps > 0 ? vscale : nullptr, nullptr);   // the last chain scaling, kinetic energy
   else if (!npt || n_steps == 0) final_ke(n_steps > 0 ? 0.5 * p->dt : 0.0, nullptr, nullptr);
@@ -112,9 +119,13 @@ void graph_cache_check(ts_batch* b) {
   }
 }
 
-// Keep an instantiated graph (the oldest of more than 16 is dropped).
+// Keep a graph entry (an instantiated graph, or the marker of a key seen
+// once); the oldest of more than 16 is dropped.
 bool graph_store(ts_batch* b, const ts_graph_entry& ge) {
-  if (b->graphs.size() > 16) { cudaGraphExecDestroy(b->graphs.front().exec); b->graphs.erase(b->graphs.begin()); }
+  if (b->graphs.size() > 16) {
+    if (b->graphs.front().exec) cudaGraphExecDestroy(b->graphs.front().exec);
+    b->graphs.erase(b->graphs.begin());
+  }
   b->graphs.push_back(ge);
   return true;
 }
@@ -123,13 +134,18 @@ ts_status md_loop(ts_batch* b, cudaStream_t st, const ts_md_params* p, int n_ste
                   double* rec) {
   k_set_u64<<<1, 1, 0, st>>>(b->d_step, p->step0);
   b->launches++;
+  if (rec) {
+    k_set_u64<<<1, 1, 0, st>>>(b->d_rec, (uint64_t)(uintptr_t)rec);
+    b->launches++;
+  }
   graph_cache_check(b);
+  const void* rkey = rec ? b->d_rec : nullptr;   // recording graphs serve every frames address
   bool capturable = b->use_graphs && st != nullptr && n_steps > 0;
   if (capturable) {
     for (auto& g : b->graphs) {
       if (g.kind == 0 && g.n_steps == n_steps && g.md_kind == p->kind && g.need_e == need_e && g.dt == p->dt &&
           g.c1 == c1 && g.seed == p->seed && g.tau == p->tau && g.p_ext == p->p_ext && g.stream == st &&
-          g.ptr[0] == rec) {
+          g.ptr[0] == rkey && g.exec) {
         if (!cuda_ok(b, cudaGraphLaunch(g.exec, st), "cudaGraphLaunch")) return TS_ERR_CUDA;
         b->launches += g.kernels;
         return TS_OK;
@@ -138,7 +154,7 @@ ts_status md_loop(ts_batch* b, cudaStream_t st, const ts_md_params* p, int n_ste
     cudaGraph_t graph = nullptr;
     if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
       int64_t l0 = b->launches;
-      md_body(b, st, p, n_steps, c1, need_e, rec);
+      md_body(b, st, p, n_steps, c1, need_e, rec != nullptr);
       int64_t nk = b->launches - l0;
       b->launches = l0;
       cudaError_t e = cudaStreamEndCapture(st, &graph);
@@ -148,7 +164,7 @@ ts_status md_loop(ts_batch* b, cudaStream_t st, const ts_md_params* p, int n_ste
         ts_graph_entry ge;
         ge.kind = 0; ge.n_steps = n_steps; ge.md_kind = p->kind; ge.need_e = need_e; ge.dt = p->dt; ge.c1 = c1;
         ge.seed = p->seed; ge.tau = p->tau; ge.p_ext = p->p_ext; ge.stream = st; ge.exec = exec; ge.kernels = nk;
-        ge.ptr[0] = rec;
+        ge.ptr[0] = rkey;
         graph_store(b, ge);
         if (!cuda_ok(b, cudaGraphLaunch(exec, st), "cudaGraphLaunch")) return TS_ERR_CUDA;
         b->launches += nk;
@@ -160,7 +176,7 @@ ts_status md_loop(ts_batch* b, cudaStream_t st, const ts_md_params* p, int n_ste
       cudaGetLastError();
     }
   }
-  md_body(b, st, p, n_steps, c1, need_e, rec);
+  md_body(b, st, p, n_steps, c1, need_e, rec != nullptr);
   return cuda_ok(b, cudaGetLastError(), "md loop") ? TS_OK : TS_ERR_CUDA;
 }
 

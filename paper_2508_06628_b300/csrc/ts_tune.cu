@@ -128,10 +128,10 @@ extern "C" ts_status ts_autotune(ts_batch* b, ts_state* s, const ts_md_params* p
   // the fields in turn, each over its candidates with the others at their best
   const double bins[2] = {1.0, 0.5};
   const int items[2] = {8, 4};
-  const double inner[3] = {0.2, 0.3, 0.45};
+  const double inner[4] = {0.2, 0.3, 0.45, 1.0};   // 1: the inner list is the Verlet list
   const double soon[3] = {0.4, 0.5, 0.6};
   for (int field = 0; field < 4 && r == TS_OK; field++) {
-    const int nc = field < 2 ? 2 : 3;
+    const int nc = field < 2 ? 2 : (field == 2 ? 4 : 3);
     for (int c = 0; c < nc && r == TS_OK; c++) {
       ts_tuning t = best;
       if (field == 0) t.bin_factor = bins[c];

@@ -82,13 +82,14 @@ def rdf_mse_upstream(g, target, n_total, n_frames):
     return float((d * d).sum() / K), 2.0 * d / (K * n_total * n_frames)
 
 
-def trajectory_rdf(batch, state, dt, T, every, rmax, K, checkpoint=None, store=False, group=None):
+def trajectory_rdf(batch, state, dt, T, every, rmax, K, checkpoint=None, store=False, group=None, frames=None):
     """NVE velocity Verlet for T steps from ``state`` (not modified); smeared
     RDF averaged over systems and the frames t = every, 2 every, ..., T.
     With several ranks (torch.distributed, ``group``) ``state`` holds this
     rank's systems and the average runs over every rank's systems: one
-    all-reduce of the K bin sums.  Returns (g [K] tensor, checkpoints list of
-    (t, x, v))."""
+    all-reduce of the K bin sums.  ``frames`` (optional f64 device tensor
+    [T + 1, n_atoms, 3]) receives every frame of the trajectory.  Returns
+    (g [K] tensor, checkpoints list of (t, x, v))."""
     torch = _torch()
     n_total = int(parallel.allreduce_sum([state.n_systems], group)[0])
     checkpoint = checkpoint or every
@@ -102,7 +103,10 @@ def trajectory_rdf(batch, state, dt, T, every, rmax, K, checkpoint=None, store=F
     t = 0
     while t < T:
         nxt = min(T, (t // every + 1) * every, (t // checkpoint + 1) * checkpoint)
-        batch.md_step(s, nxt - t, dt, kind=ts.TS_NVE)
+        if frames is not None:
+            batch.md_record(s, frames[t:nxt + 1], dt, kind=ts.TS_NVE)
+        else:
+            batch.md_step(s, nxt - t, dt, kind=ts.TS_NVE)
         t = nxt
         if t % every == 0:
             batch.rdf(s, rmax, K, gs)
@@ -114,27 +118,49 @@ def trajectory_rdf(batch, state, dt, T, every, rmax, K, checkpoint=None, store=F
     return g, ckpts
 
 
-def rdf_loss_and_grad(batch, state, dt, T, every, rmax, K, target, checkpoint=100, group=None):
+def rdf_loss_and_grad(batch, state, dt, T, every, rmax, K, target, checkpoint=None, group=None,
+                      store_budget_bytes=None):
     """Loss = (1/K) sum_k (g_k - target_k)^2 of the trajectory-averaged smeared
     RDF, and d loss / d params [n_pots,3] by the discrete adjoint of velocity
-    Verlet with checkpoints every ``checkpoint`` steps (segments recomputed
-    forward, then reversed step by step).  With several ranks (``group``),
-    ``state`` holds this rank's systems: the averaged RDF takes one all-reduce
-    of K sums, and the parameter gradient one all-reduce of n_pots x 3 sums
-    (for one LJ potential, dL/dsigma and dL/depsilon); every rank returns the
-    global loss and gradient."""
+    Verlet.  With ``checkpoint=None`` the whole trajectory (T + 1 frames of
+    24 bytes per atom) stays on the device when it fits in
+    ``store_budget_bytes`` (default: half the free device memory), and one
+    reverse sweep runs over it; otherwise, or with an explicit interval, the
+    forward pass keeps checkpoints every ``checkpoint`` steps (100 by default)
+    and the reverse recomputes each segment forward before reversing it.
+    With several ranks (``group``), ``state`` holds this rank's systems: the
+    averaged RDF takes one all-reduce of K sums, and the parameter gradient
+    one all-reduce of n_pots x 3 sums (for one LJ potential, dL/dsigma and
+    dL/depsilon); every rank returns the global loss and gradient."""
     torch = _torch()
-    g, ckpts = trajectory_rdf(batch, state, dt, T, every, rmax, K, checkpoint, store=True, group=group)
+    N = state.n_atoms
+    stored = None
+    if checkpoint is None:
+        need = (T + 1) * N * 3 * 8
+        budget = store_budget_bytes
+        if budget is None:
+            budget = torch.cuda.mem_get_info(state.pos.device)[0] // 2
+        if need <= budget:
+            stored = torch.empty((T + 1, N, 3), dtype=torch.float64, device=state.pos.device)
+        else:
+            checkpoint = 100
+    if stored is not None:
+        g, _ = trajectory_rdf(batch, state, dt, T, every, rmax, K, group=group, frames=stored)
+        ckpts = [(0, None, None)]
+    else:
+        g, ckpts = trajectory_rdf(batch, state, dt, T, every, rmax, K, checkpoint, store=True, group=group)
     target = torch.as_tensor(target, dtype=torch.float64, device=g.device)
     nfr = T // every
     n_total = int(parallel.allreduce_sum([state.n_systems], group)[0])
     loss, up = rdf_mse_upstream(g, target, n_total, nfr)
     gg = up.expand(state.n_systems, K).contiguous()
-    N = state.n_atoms
     ax = torch.zeros((N, 3), dtype=torch.float64, device=g.device)
     av = torch.zeros_like(ax)
     gth = torch.zeros((len(batch.pots), 3), dtype=torch.float64, device=g.device)
     bounds = [c[0] for c in ckpts] + [T]
+    if stored is not None:   # one sweep over the stored trajectory, nothing recomputed
+        batch.vv_adjoint_segment(state, stored, 0, dt, ax, av, gth, rdf_every=every, rmax=rmax, K=K, gg=gg)
+        ckpts = []
     frames = None
     for seg in range(len(ckpts) - 1, -1, -1):
         t0, x0, v0 = ckpts[seg]

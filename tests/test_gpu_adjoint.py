@@ -136,11 +136,12 @@ def test_rdf_and_its_gradient(orc, precision):
     assert np.abs(gx.cpu().numpy() - gxr).max() <= (1e-4 if precision == 0 else 1e-8) * np.abs(gxr).max()
 
 
-@pytest.mark.parametrize("precision", [1, 0])
-def test_trajectory_gradient_matches_oracle(orc, precision):
-    """d loss / d (sigma, eps) through 60 NVE steps with frames and
-    checkpoints every 20 steps: GPU adjoint (checkpointed, recomputed) vs the
-    oracle's stored-trajectory adjoint."""
+@pytest.mark.parametrize("precision,checkpoint", [(1, 20), (0, 20), (1, None), (0, None)])
+def test_trajectory_gradient_matches_oracle(orc, precision, checkpoint):
+    """d loss / d (sigma, eps) through 60 NVE steps with RDF frames every 20
+    steps: the GPU adjoint with checkpoints every 20 steps (segments
+    recomputed) or over the whole trajectory kept on the device (one sweep)
+    vs the oracle's stored-trajectory adjoint."""
     torch = torch_cuda()
     from paper_2508_06628_b300 import grad, ts
     hb = W.lj_liquid(seed=3, n_systems=2, reps=(2, 2, 3), rattle=0.08, kT=0.5)
@@ -153,7 +154,7 @@ def test_trajectory_gradient_matches_oracle(orc, precision):
     b = ts.Batch([dict(pot, skin=0.4)], hb.n_atoms, hb.n_systems, precision=precision)
     s = ts.DeviceState.from_host(hb)
     b.neighbor_build(s, force=True)
-    loss, g, gth = grad.rdf_loss_and_grad(b, s, dt, T, every, rmax, K, target, checkpoint=20)
+    loss, g, gth = grad.rdf_loss_and_grad(b, s, dt, T, every, rmax, K, target, checkpoint=checkpoint)
     b.poll()
     gth = gth.cpu().numpy()[0]
     rel = 1e-7 if precision == 1 else 1e-4
@@ -197,9 +198,10 @@ def test_adjoint_segment_equals_step_loop(precision):
     steps issued one call at a time: the segment merges the half kicks of
     adjacent reverse steps (one backward pass per frame with weight dt instead
     of two with dt/2), which changes only the order of the additions, so the
-    results agree to rounding.  The graph-replayed sweep (side stream, first
-    call captured, second replayed) equals the directly issued one bit for
-    bit, call for call (a second call starts from the lists the first left)."""
+    results agree to rounding.  On a side stream the first call is issued
+    directly, the second captured as a CUDA graph and launched, the third
+    replayed: each equals the directly issued call bit for bit, call for call
+    (a later call starts from the lists the previous one left)."""
     torch = torch_cuda()
     from paper_2508_06628_b300 import ts
     hb = W.lj_liquid(seed=5, n_systems=3, reps=(2, 2, 3), rattle=0.08, kT=0.5)
@@ -231,17 +233,19 @@ def test_adjoint_segment_equals_step_loop(precision):
     b, s, frames = setup()
     res_seg = segment(b, s, frames)      # legacy default stream: issued directly
     res_seg2 = segment(b, s, frames)
+    res_seg3 = segment(b, s, frames)
     b.close()
 
     b, s, frames = setup()
     stream = torch.cuda.Stream()
     torch.cuda.synchronize()
     with torch.cuda.stream(stream):
+        res_dir = segment(b, s, frames, stream)
         res_cap = segment(b, s, frames, stream)
         res_rep = segment(b, s, frames, stream)
     b.close()
-    for a, a2, c, d in zip(res_seg, res_seg2, res_cap, res_rep):
-        assert np.array_equal(a, c) and np.array_equal(a2, d)
+    for a, a2, a3, c, d, e in zip(res_seg, res_seg2, res_seg3, res_dir, res_cap, res_rep):
+        assert np.array_equal(a, c) and np.array_equal(a2, d) and np.array_equal(a3, e)
 
     b, s, frames = setup()
     ax, av = ax0.clone(), av0.clone()
@@ -290,6 +294,15 @@ def test_md_record_rows_equal_shorter_calls(orc, precision, kind):
     fr = frames.cpu().numpy()
     assert np.isfinite(fr).all()
     assert np.array_equal(fr[n], s.pos.cpu().numpy())
+    # the replayed graph writes into another buffer: the frames base is read on the device
+    frames2 = torch.full_like(frames, float("nan"))
+    with torch.cuda.stream(stream):
+        b.md_record(s, frames2, dt, stream=stream, step0=n, **md)
+        b.poll(stream)
+    torch.cuda.synchronize()
+    fr2 = frames2.cpu().numpy()
+    assert np.isfinite(fr2).all() and np.array_equal(fr2[0], fr[n]) and np.array_equal(fr2[n], s.pos.cpu().numpy())
+    assert np.array_equal(frames.cpu().numpy(), fr)
     b.close()
     for k in (1, 5, n):
         b, s = fresh()

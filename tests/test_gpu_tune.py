@@ -30,7 +30,7 @@ def test_autotune_picks_caches_and_reloads(tmp_path, orc):
     trial = _copy_state(s)   # the trial steps advance the state they are given
     best = b.autotune(trial, hb.meta["dt"], kind=ts.TS_LANGEVIN, gamma=hb.meta["gamma"], seed=3, n_steps=10)
     assert best["item_warps"] in (4, 8) and best["bin_factor"] in (1.0, 0.5)
-    assert best["inner_fraction"] in (0.2, 0.3, 0.45) and best["relist_soon"] in (0.4, 0.5, 0.6)
+    assert best["inner_fraction"] in (0.2, 0.3, 0.45, 1.0) and best["relist_soon"] in (0.4, 0.5, 0.6)
     key, iw, inner, soon, binf = open(cache).read().split("\n")[-2].split()
     assert "pots=012" in key and "fp64=0" in key
     assert (int(iw), float(inner), float(soon), float(binf)) == (best["item_warps"], best["inner_fraction"],
