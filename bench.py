@@ -29,10 +29,10 @@ UNIT = "atom-steps/s"
 FP32_LANES_PER_SM = 128
 FLOP_PER_PAIR = 30          # per ordered pair within the cutoff (force, energy, virial terms)
 BYTES_PER_ATOM = 32         # read own position, write own force, per atom-step
-# DRAM bytes (read + write) of one forces-only k_pair_small launch (inner lists) on ragged-mix-512, from one ncu
-# capture (profiles/k_pair_small_ragged_mix_512.md); reported only while the kernel's sources
+# DRAM bytes (read + write) of one forces-only k_pair_small launch (inner lists, rc + 0.45 skin) on
+# ragged-mix-512, from one ncu capture (profiles/k_pair_small_ragged_mix_512.md); reported only while the kernel's sources
 # (ts_pair.cu, then ts_internal.cuh) hash to the value recorded with the capture
-PAIR_TRAFFIC = {"bytes": 49_635_328 + 141_568, "source_sha1": "ae957e3d43a62579a69c8983c13f37923a1164ca"}
+PAIR_TRAFFIC = {"bytes": 52_658_944 + 565_248, "source_sha1": "9a94fe18fcbe37127c2663d6ffb937dedb6b7c1c"}
 
 
 def pair_traffic():
@@ -175,7 +175,11 @@ def run_ours(args, rank, world):
     hb_all = workload(seed=1, n_systems=512 * world)
     hb = hb_all if world == 1 else hb_all.subset(parallel.shard_systems(np.diff(hb_all.offsets), world)[rank])
     pots = [dict(p, skin=s) for p, s in zip(hb.pots, ts.default_skins(hb.pots))]
-    b = ts.Batch(pots, hb.n_atoms, hb.n_systems, precision=ts.TS_MIXED, device=dev.index)
+    # --tune-cache: the autotuner appends its result there, and a batch created
+    # with the file applies its last matching line (with --no-tune: a run with
+    # the tuning an earlier run chose)
+    b = ts.Batch(pots, hb.n_atoms, hb.n_systems, precision=ts.TS_MIXED, device=dev.index,
+                 autotune_cache=args.tune_cache)
     s = ts.DeviceState.from_host(hb, device=dev)
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -245,8 +249,10 @@ def run_ours(args, rank, world):
     # pair launch in `inner` starts cold and the rest find the positions in L2:
     # time both ways and weight them the same.
     with torch.cuda.stream(stream):
+        torch.cuda.nvtx.range_push("pair_kernel_timing")   # the launches a profiler capture selects
         kms_cold, pairs, atoms = b.profile_pair(s, reps=10, flush=flush, stream=stream)
         kms_warm, _, _ = b.profile_pair(s, reps=20, flush=None, stream=stream)
+        torch.cuda.nvtx.range_pop()
     kms = (kms_cold + (inner - 1) * kms_warm) / inner
     hbm, smmhz, src = peaks()
     clocks = out["clocks"] or {}
@@ -445,11 +451,13 @@ def run_row_adjoint(args):
             b.pair_forces_backward(s, gF, gE, None, gPos, gPar, stream=stream)
         stream.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push("backward_calls")   # the launches a profiler capture selects
         e0.record(stream)
         for _ in range(args.steps):
             b.pair_forces_backward(s, gF, gE, None, gPos, gPar, stream=stream)
         e1.record(stream)
         stream.synchronize()
+        torch.cuda.nvtx.range_pop()
         _, pairs, _ = b.profile_pair(s, reps=1, flush=None, stream=stream)
     ms = e0.elapsed_time(e1) / args.steps
     b.poll()
@@ -799,6 +807,7 @@ def main():
     ap.add_argument("--no-loop", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (library defaults)")
+    ap.add_argument("--tune-cache", default=None, help="autotuner cache file (written by tuning, read at create)")
     ap.add_argument("--row", default="md", choices=["md", "adjoint", "fire", "nve256", "inflight", "diff", "large",
                                                     "nhc", "npt"],
                     help="md: the MD step (the default line); the others: other rows and workloads, one GPU")
