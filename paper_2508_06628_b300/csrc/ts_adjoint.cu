@@ -203,11 +203,12 @@ __global__ void __launch_bounds__(128, F64 ? 4 : 8) k_pair_bwd(int32_t n_warps, 
 // the item's systems staged in shared memory as the same fixed-point records
 // (and, for inner lists in the table format, the same per-warp image tables),
 // so that a pair vector is the exact integer difference converted once to
-// FP32, as in the forward pass; the upstream gF is staged beside them.  Same sums as
+// FP32, as in the forward pass; the upstream gF is staged with them (24 bytes per atom, 3 CTAs per SM).  Same sums as
 // k_pair_bwd: list order per atom, compensated FP32 parameter sums per thread,
 // FP64 over the warp.
-constexpr int kBwdRecord = 32;   // staged bytes per atom: fixed-point position, upstream gF
-__global__ void __launch_bounds__(kPairSmallThreads, 2) k_pair_bwd_small(
+// staged bytes per atom: the fixed-point position with gF_x in its fourth word (16 B), gF_y and gF_z (8 B)
+constexpr int kBwdRecord = 24;
+__global__ void __launch_bounds__(kPairSmallThreads, 3) k_pair_bwd_small(
     int32_t n_items, const int4* __restrict__ items, const int32_t* __restrict__ warp_sys, SysArrays S,
     SlotArrays A, const DevPot* __restrict__ pots, int64_t stride, const double* __restrict__ gE, double* gpart,
     int accum_part) {
@@ -216,7 +217,7 @@ __global__ void __launch_bounds__(kPairSmallThreads, 2) k_pair_bwd_small(
   uint4* sq = smem + kItemWarps * kTabEntries;          // [staged] fixed-point (x, y, z, -)
   if ((int)blockIdx.x >= n_items) return;
   const int4 W = items[blockIdx.x];
-  float4* sg = reinterpret_cast<float4*>(sq + W.y * kWarp);   // [staged] upstream gF
+  float2* sg = reinterpret_cast<float2*>(sq + W.y * kWarp);   // [staged] upstream gF_y, gF_z
   const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int wg = W.z + wl;
   const bool mine = wl < W.w;
@@ -230,8 +231,9 @@ __global__ void __launch_bounds__(kPairSmallThreads, 2) k_pair_bwd_small(
 #pragma unroll 4
   for (int t = threadIdx.x; t < nst; t += blockDim.x) {
     float4 h = __ldg(A.xh + st0 + t), l = __ldg(A.xl + st0 + t);
-    sq[t] = make_uint4(fix_coord(h.x, l.x), fix_coord(h.y, l.y), fix_coord(h.z, l.z), 0u);
-    sg[t] = __ldg(A.g1 + st0 + t);
+    const float4 g = __ldg(A.g1 + st0 + t);
+    sq[t] = make_uint4(fix_coord(h.x, l.x), fix_coord(h.y, l.y), fix_coord(h.z, l.z), __float_as_uint(g.x));
+    sg[t] = make_float2(g.y, g.z);
   }
   uint4* tab = tabs + wl * kTabEntries;
   if (staged_tab) {
@@ -250,9 +252,10 @@ __global__ void __launch_bounds__(kPairSmallThreads, 2) k_pair_bwd_small(
   const uint4* hq = sq + (seg - st0);
   const DevPot P = pots[S.pot[s]];
   const uint4* gtab = S.shiftq + (int64_t)s * kNCodes;
-  const float4* g1s = sg + (seg - st0);
+  const float2* g1s = sg + (seg - st0);
   const uint4 xi = valid ? hq[i] : make_uint4(0, 0, 0, 0);
-  const float4 gi = valid ? A.g1[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float2 gyz = valid ? g1s[i] : make_float2(0.f, 0.f);
+  const float4 gi = make_float4(__uint_as_float(xi.w), gyz.x, gyz.y, 0.f);
   const double gEs = gE ? gE[s] : 0.0;
   const float gEf = (float)gEs;
   float dpc[3] = {0.f, 0.f, 0.f};
@@ -281,7 +284,8 @@ __global__ void __launch_bounds__(kPairSmallThreads, 2) k_pair_bwd_small(
     const float d2v = (float)(int)(xj.z - xi.z + sh.z) * kFixInv;
     const float r2 = fmaf(d0, d0, fmaf(d1v, d1v, d2v * d2v));
     if (!(r2 < P.rc2f)) return;
-    const float4 gj = g1s[j];
+    const float2 gjyz = g1s[j];
+    const float4 gj = make_float4(__uint_as_float(xj.w), gjyz.x, gjyz.y, 0.f);
     const float g0 = gj.x - gi.x, g1v = gj.y - gi.y, g2v = gj.z - gi.z;
     const float dg = fmaf(d0, g0, fmaf(d1v, g1v, d2v * g2v));
     const float dgi = fmaf(d0, gi.x, fmaf(d1v, gi.y, d2v * gi.z));
