@@ -761,7 +761,7 @@ def run_row_large(args):
     E = torch.zeros(hb.n_systems, dtype=torch.float64, device=dev)
     KE = torch.zeros_like(E)
     inner = 50
-    n = max(inner, (args.steps // inner) * inner) if args.steps < 5000 else 200
+    n = max(inner, (args.large_steps // inner) * inner)
     stream = torch.cuda.Stream(device=dev)
     with torch.cuda.stream(stream):
         b.neighbor_build(s, force=True, stream=stream)
@@ -808,6 +808,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (library defaults)")
     ap.add_argument("--tune-cache", default=None, help="autotuner cache file (written by tuning, read at create)")
+    ap.add_argument("--large-steps", type=int, default=200, help="NVE steps of the large row (the paper's drift "
+                                                                  "protocol runs 10,000)")
     ap.add_argument("--row", default="md", choices=["md", "adjoint", "fire", "nve256", "inflight", "diff", "large",
                                                     "nhc", "npt"],
                     help="md: the MD step (the default line); the others: other rows and workloads, one GPU")
