@@ -373,13 +373,10 @@ __global__ void __launch_bounds__(kPairSmallThreads, EW ? 3 : 4) k_pair_small(
       const uint8_t* lut = reinterpret_cast<const uint8_t*>(tab);
       const float rin2u = P.rin2f * kFix2;
       int cin = 0;
-      // inner entries collected four at a time and written as one 16-byte group
-      uint32_t g0 = 0, g1 = 0, g2 = 0, g3 = 0;
-      uint4* gout = reinterpret_cast<uint4*>(A.nbr_in) + k;
+      // inner entries stored one by one into their groups of four (one
+      // 4-byte store per kept entry beats collecting a group in registers)
       auto keep = [&](uint32_t e) {
-        const int r = cin & 3;
-        g0 = r == 0 ? e : g0; g1 = r == 1 ? e : g1; g2 = r == 2 ? e : g2; g3 = r == 3 ? e : g3;
-        if (r == 3) gout[(int64_t)(cin >> 2) * stride] = make_uint4(g0, g1, g2, g3);
+        A.nbr_in[inner_at(cin, k, stride)] = e;
         cin++;
       };
       auto one = [&](uint32_t ent) {
@@ -392,15 +389,22 @@ __global__ void __launch_bounds__(kPairSmallThreads, EW ? 3 : 4) k_pair_small(
           keep((hi << 16) | ((uint32_t)j << 4));
         }
       };
-      // list entries stream one block of four ahead of use
+      // list entries stream two blocks of four ahead of use (n: the next
+      // block, m: the one after): one 4-byte load per entry, so the loop
+      // needs more loads in flight than the inner-list loop
       int q = 0;
-      uint32_t n0 = 0, n1 = 0, n2 = 0, n3 = 0;
+      uint32_t n0 = 0, n1 = 0, n2 = 0, n3 = 0, m0 = 0, m1 = 0, m2 = 0, m3 = 0;
       if (nn >= 4) { n0 = __ldcs(lp); n1 = __ldcs(lp + stride); n2 = __ldcs(lp + 2 * stride); n3 = __ldcs(lp + 3 * stride); }
+      if (nn >= 8) {
+        const uint32_t* np = lp + 4 * stride;
+        m0 = __ldcs(np); m1 = __ldcs(np + stride); m2 = __ldcs(np + 2 * stride); m3 = __ldcs(np + 3 * stride);
+      }
       for (; q + 4 <= nn; q += 4) {
         uint32_t e0 = n0, e1 = n1, e2 = n2, e3 = n3;
-        if (q + 8 <= nn) {
-          const uint32_t* np = lp + (int64_t)(q + 4) * stride;
-          n0 = __ldcs(np); n1 = __ldcs(np + stride); n2 = __ldcs(np + 2 * stride); n3 = __ldcs(np + 3 * stride);
+        n0 = m0; n1 = m1; n2 = m2; n3 = m3;
+        if (q + 12 <= nn) {
+          const uint32_t* np = lp + (int64_t)(q + 8) * stride;
+          m0 = __ldcs(np); m1 = __ldcs(np + stride); m2 = __ldcs(np + 2 * stride); m3 = __ldcs(np + 3 * stride);
         }
         one(e0); one(e1); one(e2); one(e3);
       }
