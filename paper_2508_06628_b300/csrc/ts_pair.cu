@@ -305,9 +305,11 @@ __global__ void __launch_bounds__(kPairSmallThreads, EW ? 3 : 4) k_pair_small(
   // a warp that filters its inner list (into the table format) reads no
   // staged table: its region holds the image code -> table index lookup
   const int ofmt = refresh ? tab_format(S, s) : kInnerVerlet;
-  if (refresh && fmt_kind(ofmt) == kInnerTab) {
+  if (refresh && fmt_kind(ofmt) == kInnerTab) {   // only the codes of the format's images occur
     uint8_t* lut = reinterpret_cast<uint8_t*>(tab);
-    for (int c = lane; c < kNCodes; c += kWarp) lut[c] = (uint8_t)code_to_tab(c, ofmt);
+    const int ntab = (2 * fmt_bound(ofmt, 0) + 1) * (2 * fmt_bound(ofmt, 1) + 1) * (2 * fmt_bound(ofmt, 2) + 1);
+    const TabDecode td(ofmt);
+    for (int c = lane; c < ntab; c += kWarp) lut[td.code(c)] = (uint8_t)c;
   }
   __syncthreads();
   if (!mine) return;
