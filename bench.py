@@ -192,7 +192,7 @@ def run_ours(args, rank, world):
         with torch.cuda.stream(stream):
             trial = ts.DeviceState(*[None if t is None else t.clone() for t in
                                      (s.pos, s.vel, s.mass, s.cell, s.pbc, s.system_idx, s.pot_idx, s.uid, s.kT)])
-            tuning = b.autotune(trial, dt, kind=ts.TS_LANGEVIN, gamma=gamma, seed=11, n_steps=25, stream=stream)
+            tuning = b.autotune(trial, dt, kind=ts.TS_LANGEVIN, gamma=gamma, seed=11, n_steps=100, stream=stream)
             del trial
         tune_s = time.time() - t0
     else:
@@ -484,7 +484,7 @@ def run_row_fire(args):
     from paper_2508_06628_b300 import ts, workloads as W
     dev = torch.device("cuda", 0)
     hb = W.fire_stream(seed=2, n_systems=8192).subset(list(range(1024)))
-    pots = [dict(p, skin=s) for p, s in zip(hb.pots, ts.default_skins(hb.pots))]
+    pots = [dict(p, skin=s) for p, s in zip(hb.pots, ts.default_skins(hb.pots, relax=True))]
     b = ts.Batch(pots, hb.n_atoms, hb.n_systems, precision=ts.TS_MIXED, device=0)
     s = ts.DeviceState.from_host(hb, device=dev)
     stream = torch.cuda.Stream(device=dev)
@@ -639,7 +639,7 @@ def run_row_inflight(args):
     import torch
     from paper_2508_06628_b300 import runtime, ts, workloads as W
     hb = W.fire_stream(seed=2, n_systems=8192)
-    pots = [dict(p, skin=s) for p, s in zip(hb.pots, ts.default_skins(hb.pots))]
+    pots = [dict(p, skin=s) for p, s in zip(hb.pots, ts.default_skins(hb.pots, relax=True))]
     # warm-up on 64 systems of the stream: the first use of each PyTorch
     # kernel of the admission and retirement path costs far more than its run
     budget = 600 << 20    # device bytes of batch scratch

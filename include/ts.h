@@ -445,9 +445,14 @@ typedef struct {
  * the result and appends it to cfg->autotune_cache (host text file, one
  * "key item_warps inner_fraction relist_soon bin_factor" line; key = potential
  * kinds, log2 of the atom and system capacities, precision) when a path was
- * given.  ts_batch_create applies the last matching cache line.  The trial
- * steps advance s (positions, velocities): pass a copy of the state to keep
- * the original.  Synchronises.  n_steps in [1, 1000]. */
+ * given.  ts_batch_create applies the last matching cache line.  The state
+ * is first advanced by 4 n_steps (so that trials time the dynamics that
+ * follow, not the start-up transient), then saved in a temporary device copy
+ * (positions, velocities; the cell and piston velocities under NPT, the chain
+ * state under NHC) that is restored, with the same noise counter, before each
+ * trial.  s is left at the end of the last trial: pass a copy of the state to
+ * keep the original.  Allocates that copy, synchronises.  n_steps in
+ * [1, 1000]. */
 ts_status ts_autotune(ts_batch* b, ts_state* s, const ts_md_params* p, int n_steps, void* stream);
 
 /* The batch's current parameters, or set them (TS_ERR_INVALID_ARG outside the

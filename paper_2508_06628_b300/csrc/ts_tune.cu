@@ -99,9 +99,37 @@ extern "C" ts_status ts_autotune(ts_batch* b, ts_state* s, const ts_md_params* p
   cudaEvent_t e0, e1;
   if (!cuda_ok(b, cudaEventCreate(&e0), "event") || !cuda_ok(b, cudaEventCreate(&e1), "event")) return TS_ERR_CUDA;
   ts_md_params q = *p;
+  // Every trial starts from the same state: the caller's, advanced by an
+  // equilibrating run of 4 n_steps (trials then time the dynamics that
+  // follow, not the start-up transient of a freshly built state), saved on
+  // the device and restored, with the same noise counter, before each trial.
+  const bool npt = p->kind == TS_NPT_LANGEVIN, nhc = p->kind == TS_NVT_NHC;
+  const size_t nx = 3 * (size_t)s->n_atoms, nb = (size_t)s->n_systems;
+  const size_t nsave = 2 * nx + (npt ? 10 * nb : 0) + (nhc ? 6 * nb : 0);
+  double* save = nullptr;
+  if (!cuda_ok(b, cudaMalloc(&save, 8 * nsave), "tuning state copy")) return TS_ERR_CUDA;
+  auto copy_state = [&](bool restore) -> bool {
+    struct { double* a; size_t n; } parts[5] = {{s->pos, nx}, {s->vel, nx}, {npt ? s->cell : nullptr, 9 * nb},
+                                                {npt ? p->baro : nullptr, nb}, {nhc ? p->nhc : nullptr, 6 * nb}};
+    size_t off = 0;
+    for (auto& pt : parts) {
+      if (!pt.a) continue;
+      cudaError_t e = restore ? cudaMemcpyAsync(pt.a, save + off, 8 * pt.n, cudaMemcpyDeviceToDevice, st)
+                              : cudaMemcpyAsync(save + off, pt.a, 8 * pt.n, cudaMemcpyDeviceToDevice, st);
+      if (!cuda_ok(b, e, "tuning state copy")) return false;
+      off += pt.n;
+    }
+    return true;
+  };
+  r = ts_md_step(b, s, &q, 4 * n_steps, nullptr, nullptr, st);
+  q.step0 += 4 * (uint64_t)n_steps;
+  if (r == TS_OK && !copy_state(false)) r = TS_ERR_CUDA;
+  const uint64_t step_start = q.step0;
   // milliseconds per MD step of configuration t: a warm-up call (layout,
   // listing, graph capture), then three timed calls of n_steps
   auto trial = [&](const ts_tuning& t, double& ms_out) -> ts_status {
+    if (!copy_state(true)) return TS_ERR_CUDA;
+    q.step0 = step_start;
     ts_status rr = apply_tuning(b, t);
     if (rr != TS_OK) return rr;
     if ((rr = ts_md_step(b, s, &q, n_steps, nullptr, nullptr, st)) != TS_OK) return rr;
@@ -123,8 +151,13 @@ extern "C" ts_status ts_autotune(ts_batch* b, ts_state* s, const ts_md_params* p
   };
   ts_tuning best = b->tune;
   double best_ms = 0;
-  r = trial(best, best_ms);                  // warm-up of the whole path, not compared
   if (r == TS_OK) r = trial(best, best_ms);
+  if (r != TS_OK) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(save);
+    return r;
+  }
   // the fields in turn, each over its candidates with the others at their best
   const double bins[2] = {1.0, 0.5};
   const int items[2] = {8, 4};
@@ -148,6 +181,8 @@ extern "C" ts_status ts_autotune(ts_batch* b, ts_state* s, const ts_md_params* p
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  cudaStreamSynchronize(st);
+  cudaFree(save);
   ts_status ra = apply_tuning(b, best);
   if (r != TS_OK) return r;
   if (ra != TS_OK) return ra;

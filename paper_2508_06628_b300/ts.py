@@ -355,16 +355,18 @@ def bin_pack(sizes, capacity):
     return out, nb.value
 
 
-def default_skins(pots):
-    """Skin per potential, from a step-time sweep on the 512-system ragged batch at 300 K: 1.1 A for LJ
-    argon, 0.55 A for Morse Cu, 1.0 sigma for soft spheres (light, stiff particles whose thermal
-    excursions would otherwise force a re-listing every few steps), 0.3 sigma for reduced-unit LJ."""
+def default_skins(pots, relax=False):
+    """Skin per potential.  For MD (``relax=False``), from step-time sweeps on the 512-system ragged batch
+    at 300 K: 1.1 A for LJ argon, 0.88 A for Morse Cu, 1.2 sigma for soft spheres (light, stiff
+    particles whose thermal excursions would otherwise force a re-listing every few steps), 0.3 sigma
+    for reduced-unit LJ.  Relaxations (``relax=True``) move atoms little and re-list rarely, so shorter
+    lists pay there: 0.55 A for Morse Cu and 1.0 sigma for soft spheres (sweep on the FIRE stream)."""
     out = []
     for d in pots:
         if d["kind"] == 2:
-            out.append(1.0 * d["p"][0])
+            out.append((1.0 if relax else 1.2) * d["p"][0])
         elif d["kind"] == 0:
             out.append(0.3 * d["p"][0] if d["p"][0] < 2 else 1.1)
         else:
-            out.append(0.55)
+            out.append(0.55 if relax else 0.88)
     return out
