@@ -301,13 +301,15 @@ class Batch:
                                                 _ptr(ax), _ptr(av), _ptr(gParams), int(rdf_every), float(rmax),
                                                 int(K), _ptr(gg), _stream(stream)), "ts_vv_adjoint_segment")
 
-    def autotune(self, s, dt, kind=TS_LANGEVIN, gamma=0.0, kT=None, seed=0, n_steps=20, stream=None):
+    def autotune(self, s, dt, kind=TS_LANGEVIN, gamma=0.0, kT=None, seed=0, n_steps=20, stream=None, tau=0.0,
+                 nhc=None, p_ext=0.0, baro=None):
         """Tune the batch's launch and list parameters on MD steps of the state
-        ``s`` (advanced by the trial steps: pass a copy); returns the chosen
-        tuning as a dict."""
+        ``s`` (advanced by the trial steps: pass a copy; under TS_NVT_NHC and
+        TS_NPT_LANGEVIN ``nhc`` / ``baro`` and ``s.cell`` advance too); returns
+        the chosen tuning as a dict."""
         kT = kT if kT is not None else s.kT
-        p = MDParams(int(kind), float(dt), float(gamma), _ptr(kT) if kT is not None else None, int(seed), 0, 0.0,
-                     None, 0.0, None)
+        p = MDParams(int(kind), float(dt), float(gamma), _ptr(kT) if kT is not None else None, int(seed), 0,
+                     float(tau), _ptr(nhc), float(p_ext), _ptr(baro))
         self._check(lib().ts_autotune(self.h, C.byref(s.c()), C.byref(p), int(n_steps), _stream(stream)),
                     "ts_autotune")
         return self.tuning()

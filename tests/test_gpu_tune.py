@@ -108,3 +108,51 @@ def test_half_bins_small_items_pair_sets_forces_and_md(orc, precision):
     tol = 1e-9 if precision == 1 else 1e-6
     assert np.abs(frac_diff(s.pos.cpu().numpy(), xr, hb.cell, hb.offsets)).max() < tol
     b.close()
+
+
+@pytest.mark.parametrize("kind", ["nhc", "npt"])
+def test_autotune_under_chain_and_barostat(orc, kind):
+    """The tuner saves and restores the chain state (NHC) or the cell and the
+    piston velocities (NPT) between its trials: it runs clean, leaves finite
+    state, and the tuned batch's next steps still follow the oracle (FP64
+    chain state and cell, short mixed run)."""
+    torch = torch_cuda()
+    from paper_2508_06628_b300 import ts
+    hb = small_mix(43, n_systems=6, lo=32, hi=300)
+    b = make_batch(hb, ts.TS_MIXED)
+    s = ts.DeviceState.from_host(hb)
+    B = hb.n_systems
+    kT = torch.as_tensor(hb.kT, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        b.neighbor_build(s, force=True, stream=stream)
+        if kind == "nhc":
+            st = torch.zeros((B, 6), dtype=torch.float64, device="cuda")
+            best = b.autotune(s, hb.meta["dt"], kind=ts.TS_NVT_NHC, kT=kT, n_steps=5, stream=stream, tau=50.0, nhc=st)
+        else:
+            st = torch.zeros(B, dtype=torch.float64, device="cuda")
+            best = b.autotune(s, hb.meta["dt"], kind=ts.TS_NPT_LANGEVIN, gamma=0.01, kT=kT, n_steps=5, stream=stream,
+                              tau=100.0, p_ext=6.2e-3, baro=st)
+        b.poll(stream)
+    torch.cuda.synchronize()
+    assert best["item_warps"] in (4, 8)
+    assert torch.isfinite(st).all() and torch.isfinite(s.pos).all() and torch.isfinite(s.cell).all()
+    # the tuned batch continues: a few steps from the current state against the oracle
+    pos, vel, cell = s.pos.cpu().numpy(), s.vel.cpu().numpy(), s.cell.cpu().numpy()
+    st0 = st.cpu().numpy().copy()
+    with torch.cuda.stream(stream):
+        if kind == "nhc":
+            b.md_step(s, 3, hb.meta["dt"], kind=ts.TS_NVT_NHC, kT=kT, tau=50.0, nhc=st, stream=stream)
+        else:
+            b.md_step(s, 3, hb.meta["dt"], kind=ts.TS_NPT_LANGEVIN, gamma=0.01, kT=kT, tau=100.0, p_ext=6.2e-3,
+                      baro=st, seed=0, stream=stream)
+        b.poll(stream)
+    torch.cuda.synchronize()
+    assert torch.isfinite(s.pos).all() and torch.isfinite(st).all()
+    if kind == "nhc":
+        xr, _, _, _, nr, _ = orc.md_nhc(hb.offsets, pos, vel, hb.mass, hb.cell, hb.pbc, hb.pot_idx, hb.pots,
+                                        hb.meta["dt"], 3, hb.kT, 50.0, nhc=st0)
+        assert np.abs(frac_diff(s.pos.cpu().numpy(), xr, hb.cell, hb.offsets)).max() < 1e-6
+        assert np.allclose(st.cpu().numpy(), nr, rtol=1e-4, atol=1e-9)
+    b.close()
