@@ -552,11 +552,16 @@ void relist_lists(ts_batch* b, cudaStream_t st, bool move_fire, int prio) {
 
 // end of a re-listing pass: flag bookkeeping.  md_pass: the pass's pair
 // launches ran in inner-list mode and refreshed every flagged system.
-void relist_finish(ts_batch* b, cudaStream_t st, bool md_pass) {
+void relist_finish(ts_batch* b, cudaStream_t st, bool md_pass, bool overlap) {
   // one CTA up to 1024 systems (the end-of-pass flag clear then needs no
-  // cross-CTA arrival), CTAs of 128 above
+  // cross-CTA arrival), CTAs of 128 above; after a programmatically
+  // serialized pair launch, launched the same way: resident early, it waits
+  // in griddepcontrol.wait for that launch to complete
   const int t = b->B <= 1024 ? std::max(32, (b->B + 31) / 32 * 32) : 128;
-  k_after_relist<<<(b->B + t - 1) / t, t, 0, st>>>(b->B, b->S, b->d_counters, md_pass ? 1 : 0);
+  if (overlap)
+    launch_k_overlap(st, (b->B + t - 1) / t, t, 0, k_after_relist, b->B, b->S, b->d_counters, md_pass ? 1 : 0);
+  else
+    k_after_relist<<<(b->B + t - 1) / t, t, 0, st>>>(b->B, b->S, b->d_counters, md_pass ? 1 : 0);
   b->launches++;
 }
 
@@ -600,7 +605,7 @@ bool relist_pair_overlapped(ts_batch* b, cudaStream_t st, bool move_fire, bool e
     pair(b, st, ew, kPairKept, 0, inner);
   }
   cuda_ok(b, cudaStreamWaitEvent(st, b->ev_join, 0), "stream wait");
-  relist_finish(b, st, inner);
+  relist_finish(b, st, inner, inner && b->ev_pruned);
   return true;
 }
 

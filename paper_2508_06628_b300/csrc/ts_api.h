@@ -139,7 +139,7 @@ void relist(ts_batch* b, cudaStream_t st, bool move_fire);
 void relist_lists(ts_batch* b, cudaStream_t st, bool move_fire, int prio = 0);
 void relist_sort(ts_batch* b, cudaStream_t st, bool move_fire, int prio);
 void relist_build(ts_batch* b, cudaStream_t st, int prio);
-void relist_finish(ts_batch* b, cudaStream_t st, bool md_pass);
+void relist_finish(ts_batch* b, cudaStream_t st, bool md_pass, bool overlap = false);
 bool relist_pair_overlapped(ts_batch* b, cudaStream_t st, bool move_fire, bool ew, bool inner);
 void relist_large_sort(ts_batch* b, cudaStream_t st, bool move_fire);
 void pair(ts_batch* b, cudaStream_t st, bool ew, int filter, int prio = 0, bool inner = false, bool overlap = false);

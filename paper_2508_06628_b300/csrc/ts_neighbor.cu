@@ -551,6 +551,9 @@ __global__ void k_copy_back(int64_t Npad, SysArrays S, SlotArrays A, int move_fi
 
 // per-system flag bookkeeping after a listing: the re-listed systems' forces are stale
 __global__ void k_after_relist(int32_t B, SysArrays S, int64_t* counters, int md_pass) {
+  // launched with programmatic serialization after a pair launch: nothing
+  // before that launch has completed (no-op otherwise)
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   bool refreshed = false, re = false;
   if (s < B) {
