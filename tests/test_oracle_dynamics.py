@@ -246,12 +246,12 @@ def _fcc_energy_per_atom_numpy(pot, a):
     return 0.5 * np.sum(f(r) - f(rc))
 
 
-@pytest.mark.parametrize("pot,a0,astar_survey", [(MO, 3.61, 3.661615), (LJR, 1.55, 1.549603)])
-def test_fire_reaches_fcc_lattice_constant(orc, pot, a0, astar_survey):
+@pytest.mark.parametrize("pot,a0,astar_lattice_sum", [(MO, 3.61, 3.661615), (LJR, 1.55, 1.549603)])
+def test_fire_reaches_fcc_lattice_constant(orc, pot, a0, astar_lattice_sum):
     """Variable-cell FIRE relaxes a rattled, scaled FCC supercell to the lattice
     constant that minimises the independent lattice-vector sum."""
     astar = _golden_section(lambda a: _fcc_energy_per_atom_numpy(pot, a), 0.9 * a0, 1.1 * a0)
-    assert astar == pytest.approx(astar_survey, abs=2e-6)
+    assert astar == pytest.approx(astar_lattice_sum, abs=2e-6)
     rng = np.random.default_rng(5)
     pos, cell = W.lattice("fcc", (2, 2, 2), a0 * 0.98)
     pos = pos + rng.normal(0, 0.02 * a0, pos.shape)
