@@ -265,17 +265,23 @@ def test_adjoint_segment_equals_step_loop(precision):
 
 
 @pytest.mark.parametrize("precision", [1, 0])
-@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("kind", [0, 1, 2])
 def test_md_record_rows_equal_shorter_calls(orc, precision, kind):
-    """ts_md_record: row k of the frames equals the positions after a
-    ts_md_step call of k steps from the same state (bit for bit), its last row
-    equals the returned positions, and in FP64 mode the rows follow the
-    oracle's trajectory."""
+    """ts_md_record (velocity Verlet, BAOAB, Nose-Hoover chain): row k of the
+    frames equals the positions after a ts_md_step call of k steps from the
+    same state (bit for bit), its last row equals the returned positions, and
+    in FP64 mode the rows follow the oracle's trajectory."""
     torch = torch_cuda()
     from paper_2508_06628_b300 import ts
     hb = small_mix(83, n_systems=5, lo=32, hi=400)
-    dt, n = hb.meta["dt"], 12
-    md = dict(kind=kind, gamma=hb.meta["gamma"] if kind == 1 else 0.0, seed=4)
+    dt, n, tau = hb.meta["dt"], 12, 50.0
+    kT = torch.as_tensor(hb.kT, dtype=torch.float64, device="cuda")
+
+    def md_kw():   # the chain state starts at zero for every run
+        kw = dict(kind=kind, gamma=hb.meta["gamma"] if kind == 1 else 0.0, seed=4, kT=kT)
+        if kind == 2:
+            kw.update(tau=tau, nhc=torch.zeros((hb.n_systems, 6), dtype=torch.float64, device="cuda"))
+        return kw
 
     def fresh():
         b = make_batch(hb, precision)
@@ -287,6 +293,7 @@ def test_md_record_rows_equal_shorter_calls(orc, precision, kind):
     frames = torch.full((n + 1, hb.n_atoms, 3), float("nan"), dtype=torch.float64, device="cuda")
     stream = torch.cuda.Stream()
     torch.cuda.synchronize()
+    md = md_kw()
     with torch.cuda.stream(stream):
         b.md_record(s, frames, dt, stream=stream, **md)
         b.poll(stream)
@@ -306,14 +313,19 @@ def test_md_record_rows_equal_shorter_calls(orc, precision, kind):
     b.close()
     for k in (1, 5, n):
         b, s = fresh()
-        b.md_step(s, k, dt, **md)
+        b.md_step(s, k, dt, **md_kw())
         b.poll()
         assert np.array_equal(fr[k], s.pos.cpu().numpy()), k
         b.close()
     if precision == 1:
         for k in (1, n):
-            xr, _, _, _ = orc.md(hb.offsets, hb.pos, hb.vel, hb.mass, hb.cell, hb.pbc, hb.pot_idx, hb.pots, dt, k,
-                                 kind=kind, kT=hb.kT, gamma=md["gamma"], seed=4, uid=hb.uid)
+            if kind == 2:
+                xr = orc.md_nhc(hb.offsets, hb.pos, hb.vel, hb.mass, hb.cell, hb.pbc, hb.pot_idx, hb.pots, dt, k,
+                                hb.kT, tau)[0]
+            else:
+                xr = orc.md(hb.offsets, hb.pos, hb.vel, hb.mass, hb.cell, hb.pbc, hb.pot_idx, hb.pots, dt, k,
+                            kind=kind, kT=hb.kT, gamma=hb.meta["gamma"] if kind == 1 else 0.0, seed=4,
+                            uid=hb.uid)[0]
             assert np.abs(frac_diff(fr[k], xr, hb.cell, hb.offsets)).max() < 1e-9
     # NPT is not recorded
     b, s = fresh()
