@@ -58,7 +58,7 @@ size_t scratch_bytes(int64_t Ncap, int64_t Bcap, int64_t Ccap, int32_t max_nbrs,
                         : (2 * 16 /*x*/ + 2 * 16 /*v*/ + 16 /*F*/ + 2 * 16 /*xr*/ + 2 * 16 + 2 * 16 /*tmp f*/ +
                            2 * 16 /*g*/);
   per_slot += (f64 ? 3 * 8 : 2 * 16) /*prune reference*/ + 4 /*nn_in*/ + (size_t)(max_nbrs + 3) / 4 * 16 /*inner list*/;
-  per_slot += 4 * 4 /*perm sys bin nn*/ + 3 * 4 /*tmp i*/ + (size_t)max_nbrs * 4 + 8 * 8 / 32 /*partials*/ + 4 / 32 /*warp_sys*/ + 16 / 32 /*pair work items*/;
+  per_slot += 4 * 4 /*perm sys bin nn*/ + 3 * 4 /*tmp i*/ + (size_t)max_nbrs * 4 + 8 * 8 / 32 /*partials*/ + (4 /*warp_sys*/ + 16 /*pair work items*/ + 4 * kItemWarps /*their warps' systems*/ + 31) / 32;
   size_t per_sys = 4 /*inner-list format*/ + 8 * 4 + 9 * 8 * 3 + 9 * 4 + 6 * 4 + 4 * 4 + 8 + 12 /*list-build work table*/ + 8 /*piston*/ + 4 /*geometry state*/ + 8 /*table bounds*/ + 32 * 4 /*FIRE FP32 coefficients*/ +
                    (size_t)kNCodes * (32 + 24 + 16);
   return per_slot * (size_t)Ncap + per_sys * (size_t)Bcap + (size_t)Ccap * 8;
@@ -177,7 +177,7 @@ extern "C" ts_status ts_batch_create(const ts_batch_config* cfg, const ts_potent
        alloc(b, b->d_bsum, (b->Ccap + 1023) / 1024 + 1) && alloc(b, b->d_starts, B + 1) &&
        alloc(b, b->d_Eint, B) && alloc(b, b->d_Wint, 9 * B) && alloc(b, b->d_scal, 32 * B) && alloc(b, b->d_fcoef, 32 * B) && alloc(b, b->d_nhc, 6 * B) && alloc(b, b->d_baro, B) &&
        alloc(b, b->d_gparam_part, 4 * b->Wcap) && alloc(b, b->d_gacc, 3 * kMaxPots) &&
-       alloc(b, b->d_items, b->Wcap) && alloc(b, b->d_tab_sys, B) && alloc(b, b->d_tab_base, B + 1) && alloc(b, b->d_tab_base_a, B + 1) &&
+       alloc(b, b->d_items, b->Wcap) && alloc(b, b->d_item_sys, (size_t)kItemWarps * b->Wcap) && alloc(b, b->d_tab_sys, B) && alloc(b, b->d_tab_base, B + 1) && alloc(b, b->d_tab_base_a, B + 1) &&
        alloc(b, b->d_tab_n, 3);
   if (ok) ok = cuda_ok(b, cudaMemcpy(b->d_pots, dp, sizeof dp, cudaMemcpyHostToDevice), "copy pots");
   if (ok) ok = cuda_ok(b, cudaMemset(b->d_err, 0, 16), "memset") && cuda_ok(b, cudaMemset(b->d_counters, 0, 32), "memset");
@@ -433,6 +433,11 @@ ts_status derive_topology(ts_batch* b, const ts_state* s, cudaStream_t st) {
     for (int c = 0; c < b->n_items; c++) sorted[c] = items[order[c]];
     items.swap(sorted);
   }
+  // each item's warps' systems, read by a CTA beside its item (not through
+  // the item's first warp, which would add a dependent load to the prologue)
+  std::vector<int32_t> item_sys((size_t)kItemWarps * b->n_items, 0);
+  for (int c = 0; c < b->n_items; c++)
+    for (int w = 0; w < items[c].w; w++) item_sys[(size_t)kItemWarps * c + w] = warp_sys[items[c].z + w];
   b->h_caller_off = caller_off; b->h_n = n; b->h_pot = pot; b->h_seg = seg;
   SysArrays& S = b->S;
   bool ok = cuda_ok(b, cudaMemcpyAsync(S.seg_start, seg.data(), 8 * B, cudaMemcpyHostToDevice, st), "h2d") &&
@@ -445,7 +450,8 @@ ts_status derive_topology(ts_batch* b, const ts_state* s, cudaStream_t st) {
             cuda_ok(b, cudaMemcpyAsync(S.warp_end, we.data(), 4 * B, cudaMemcpyHostToDevice, st), "h2d") &&
             cuda_ok(b, cudaMemcpyAsync(b->d_warp_sys, warp_sys.data(), 4 * warp_sys.size(), cudaMemcpyHostToDevice, st), "h2d");
   if (ok && b->n_items > 0)
-    ok = cuda_ok(b, cudaMemcpyAsync(b->d_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice, st), "h2d");
+    ok = cuda_ok(b, cudaMemcpyAsync(b->d_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice, st), "h2d") &&
+         cuda_ok(b, cudaMemcpyAsync(b->d_item_sys, item_sys.data(), 4 * item_sys.size(), cudaMemcpyHostToDevice, st), "h2d");
   if (s->uid) {
     ok = ok && cuda_ok(b, cudaMemcpyAsync(S.uid, s->uid, 4 * B, cudaMemcpyDeviceToDevice, st), "d2d");
   } else {
@@ -655,11 +661,11 @@ void pair(ts_batch* b, cudaStream_t st, bool ew, int filter, int prio, bool inne
     size_t shm = kPairTabBytes + (size_t)kSmallRecord * b->nst_max;
     const int4* it = b->d_items;
     if (overlap) {
-      if (ew) launch_k_overlap(st, b->n_items, 32 * b->tune.item_warps, shm, k_pair_small<true>, b->n_items, it, ws, b->S, b->A, pots, b->Ncap, filter, b->d_partial, in);
-      else launch_k_overlap(st, b->n_items, 32 * b->tune.item_warps, shm, k_pair_small<false>, b->n_items, it, ws, b->S, b->A, pots, b->Ncap, filter, b->d_partial, in);
+      if (ew) launch_k_overlap(st, b->n_items, 32 * b->tune.item_warps, shm, k_pair_small<true>, b->n_items, it, b->d_item_sys, b->S, b->A, pots, b->Ncap, filter, b->d_partial, in);
+      else launch_k_overlap(st, b->n_items, 32 * b->tune.item_warps, shm, k_pair_small<false>, b->n_items, it, b->d_item_sys, b->S, b->A, pots, b->Ncap, filter, b->d_partial, in);
     } else {
-      if (ew) launch_k(st, prio, b->n_items, 32 * b->tune.item_warps, shm, k_pair_small<true>, b->n_items, it, ws, b->S, b->A, pots, b->Ncap, filter, b->d_partial, in);
-      else launch_k(st, prio, b->n_items, 32 * b->tune.item_warps, shm, k_pair_small<false>, b->n_items, it, ws, b->S, b->A, pots, b->Ncap, filter, b->d_partial, in);
+      if (ew) launch_k(st, prio, b->n_items, 32 * b->tune.item_warps, shm, k_pair_small<true>, b->n_items, it, b->d_item_sys, b->S, b->A, pots, b->Ncap, filter, b->d_partial, in);
+      else launch_k(st, prio, b->n_items, 32 * b->tune.item_warps, shm, k_pair_small<false>, b->n_items, it, b->d_item_sys, b->S, b->A, pots, b->Ncap, filter, b->d_partial, in);
     }
     b->launches++;
   }

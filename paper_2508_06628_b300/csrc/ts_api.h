@@ -39,6 +39,7 @@ struct ts_batch {
   int32_t B = 0, nwarps = 0, n_large = 0, n_items = 0, nst_max = 0;
   bool use_small_pair = true;
   int4* d_items = nullptr;        // work items of k_pair_small
+  int32_t* d_item_sys = nullptr;  // system of each warp of each work item [Wcap][kItemWarps]
   int32_t* d_tab_sys = nullptr;   // list-build work table (k_relist_small writes it)
   int32_t* d_tab_base = nullptr;
   int32_t* d_tab_base_a = nullptr;

@@ -207,7 +207,10 @@ __device__ __forceinline__ PairFix pair_fix(const DevPot& P) {
 
 // fu and (EW) the unshifted pair energy phi of a pair with r2u = u.u > 0;
 // fu is zero beyond the cutoff (selected, so that out-of-range entries add
-// exactly zero and a round of entries has no branch)
+// exactly zero and a round of entries has no branch).  Every rounding is
+// spelled out (fmaf, __fmul_rn), so that the two-entry form below, whose
+// lanes repeat these operations in packed f32x2 instructions, gives the same
+// bits as this one whatever the compiler contracts.
 template <int K, bool EW>
 __device__ __forceinline__ float pair_fixed(const PairFix& C, float r2u, float& phi) {
   float fu;
@@ -220,13 +223,13 @@ __device__ __forceinline__ float pair_fixed(const PairFix& C, float r2u, float& 
   } else if constexpr (K == TS_MORSE) {
     // r correctly rounded: it sets the exponent's argument, where the stiff
     // Morse force amplifies any error; 1/r only scales the result
-    const float r = sqrtf(r2u) * C.e;
-    const float e = __expf(C.a * (C.b - r));
-    fu = C.c * e * (1.0f - e) * rsqrtf(r2u);
-    if (EW) phi = C.d * (e * e - 2.0f * e);
+    const float r = __fmul_rn(sqrtf(r2u), C.e);
+    const float e = __expf(C.a * fmaf(r, -1.0f, C.b));
+    fu = C.c * e * fmaf(e, -1.0f, 1.0f) * rsqrtf(r2u);
+    if (EW) phi = C.d * fmaf(e, e, -2.0f * e);
   } else {
     const float ri = rsqrtf(r2u);
-    const float t = fmaf(-r2u * ri, C.a, 1.0f);        // 1 - r/sigma in one fused operation
+    const float t = fmaf(r2u * ri, -C.a, 1.0f);         // 1 - r/sigma in one fused operation
     const float ta1 = (C.d == 2.0f) ? t : __powf(t, C.d - 1.0f);
     fu = C.b * ta1 * ri;
     if (EW) phi = C.c * ta1 * t;
@@ -234,21 +237,67 @@ __device__ __forceinline__ float pair_fixed(const PairFix& C, float r2u, float& 
   return r2u < C.rc2u ? fu : 0.f;
 }
 
+// Two entries at once: each lane of a packed f32x2 instruction rounds as the
+// scalar operation does, so (fa, fb) are pair_fixed(ra) and pair_fixed(rb)
+// bit for bit; the FP32 arithmetic takes about half the issue slots.
+template <int K, bool EW>
+__device__ __forceinline__ void pair_fixed2(const PairFix& C, float ra, float rb, float& fa, float& fb, float& pa,
+                                            float& pb) {
+  const unsigned long long R2 = f2_pack(ra, rb);
+  unsigned long long FU, PHI = 0;
+  if constexpr (K == TS_LJ) {
+    float ia, ib;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(ia) : "f"(ra));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(ib) : "f"(rb));
+    const unsigned long long RI = f2_pack(ia, ib);
+    const unsigned long long S2 = f2_mul(f2_splat(C.a), RI);
+    const unsigned long long S6 = f2_mul(f2_mul(S2, S2), S2);
+    FU = f2_mul(f2_fma(S6, f2_splat(2.0f * C.b), f2_splat(-C.b)), f2_mul(S6, RI));
+    if (EW) PHI = f2_mul(f2_splat(C.c), f2_fma(S6, S6, f2_mul(S6, f2_splat(-1.0f))));
+  } else if constexpr (K == TS_MORSE) {
+    const unsigned long long R = f2_mul(f2_pack(sqrtf(ra), sqrtf(rb)), f2_splat(C.e));
+    const unsigned long long X = f2_mul(f2_splat(C.a), f2_fma(R, f2_splat(-1.0f), f2_splat(C.b)));
+    float xa, xb;
+    f2_unpack(X, xa, xb);
+    const unsigned long long E = f2_pack(__expf(xa), __expf(xb));
+    FU = f2_mul(f2_mul(f2_mul(f2_splat(C.c), E), f2_fma(E, f2_splat(-1.0f), f2_splat(1.0f))),
+                f2_pack(rsqrtf(ra), rsqrtf(rb)));
+    if (EW) PHI = f2_mul(f2_splat(C.d), f2_fma(E, E, f2_mul(E, f2_splat(-2.0f))));
+  } else {
+    const unsigned long long RI = f2_pack(rsqrtf(ra), rsqrtf(rb));
+    const unsigned long long T = f2_fma(f2_mul(R2, RI), f2_splat(-C.a), f2_splat(1.0f));
+    unsigned long long TA1 = T;
+    if (C.d != 2.0f) {
+      float ta, tb;
+      f2_unpack(T, ta, tb);
+      TA1 = f2_pack(__powf(ta, C.d - 1.0f), __powf(tb, C.d - 1.0f));
+    }
+    FU = f2_mul(f2_mul(f2_splat(C.b), TA1), RI);
+    if (EW) PHI = f2_mul(f2_mul(f2_splat(C.c), TA1), T);
+  }
+  f2_unpack(FU, fa, fb);
+  if (EW) f2_unpack(PHI, pa, pb);
+  fa = ra < C.rc2u ? fa : 0.f;
+  fb = rb < C.rc2u ? fb : 0.f;
+}
+
 template <bool EW>
 struct PairSums {
   float f0 = 0.f, f1 = 0.f, f2 = 0.f, e = 0.f, w0 = 0.f, w1 = 0.f, w2 = 0.f, w3 = 0.f, w4 = 0.f, w5 = 0.f;
 };
 
-// one entry: staged record xj, image shift sh (fixed point) against atom xi
-template <int K, bool EW>
-__device__ __forceinline__ float pair_add(const PairFix& C, float phic, const uint4& xi, const uint4& xj,
-                                          const uint4& sh, PairSums<EW>& A) {
-  const float u0 = (float)(int)(xj.x - xi.x + sh.x);
-  const float u1 = (float)(int)(xj.y - xi.y + sh.y);
-  const float u2 = (float)(int)(xj.z - xi.z + sh.z);
-  const float r2u = fmaf(u0, u0, fmaf(u1, u1, u2 * u2));
-  float phi = 0.f;
-  const float fu = pair_fixed<K, EW>(C, r2u, phi);
+// integer pair vector of staged record xj, image shift sh (fixed point), against atom xi
+__device__ __forceinline__ void pair_vec(const uint4& xi, const uint4& xj, const uint4& sh, float& u0, float& u1,
+                                         float& u2) {
+  u0 = (float)(int)(xj.x - xi.x + sh.x);
+  u1 = (float)(int)(xj.y - xi.y + sh.y);
+  u2 = (float)(int)(xj.z - xi.z + sh.z);
+}
+
+// one entry's contribution, summed in list order
+template <bool EW>
+__device__ __forceinline__ void pair_acc(const PairFix& C, float phic, float u0, float u1, float u2, float r2u,
+                                         float fu, float phi, PairSums<EW>& A) {
   A.f0 = fmaf(fu, u0, A.f0); A.f1 = fmaf(fu, u1, A.f1); A.f2 = fmaf(fu, u2, A.f2);
   if (EW) {
     A.e += r2u < C.rc2u ? 0.5f * (phi - phic) : 0.f;
@@ -257,12 +306,40 @@ __device__ __forceinline__ float pair_add(const PairFix& C, float phic, const ui
     A.w0 = fmaf(h0, u0, A.w0); A.w1 = fmaf(h1, u1, A.w1); A.w2 = fmaf(hf * u2, u2, A.w2);
     A.w3 = fmaf(h0, u1, A.w3); A.w4 = fmaf(h0, u2, A.w4); A.w5 = fmaf(h1, u2, A.w5);
   }
+}
+
+// one entry: staged record xj, image shift sh (fixed point) against atom xi
+template <int K, bool EW>
+__device__ __forceinline__ float pair_add(const PairFix& C, float phic, const uint4& xi, const uint4& xj,
+                                          const uint4& sh, PairSums<EW>& A) {
+  float u0, u1, u2;
+  pair_vec(xi, xj, sh, u0, u1, u2);
+  const float r2u = fmaf(u0, u0, fmaf(u1, u1, u2 * u2));
+  float phi = 0.f;
+  const float fu = pair_fixed<K, EW>(C, r2u, phi);
+  pair_acc<EW>(C, phic, u0, u1, u2, r2u, fu, phi, A);
   return r2u;
+}
+
+// two entries (a, then b): the same bits as two pair_add calls in that order
+template <int K, bool EW>
+__device__ __forceinline__ void pair_add2(const PairFix& C, float phic, const uint4& xi, const uint4& xa,
+                                          const uint4& sa, const uint4& xb, const uint4& sb, PairSums<EW>& A,
+                                          float& r2a, float& r2b) {
+  float a0, a1, a2, b0, b1, b2;
+  pair_vec(xi, xa, sa, a0, a1, a2);
+  pair_vec(xi, xb, sb, b0, b1, b2);
+  const unsigned long long U0 = f2_pack(a0, b0), U1 = f2_pack(a1, b1), U2 = f2_pack(a2, b2);
+  f2_unpack(f2_fma(U0, U0, f2_fma(U1, U1, f2_mul(U2, U2))), r2a, r2b);
+  float fa, fb, pa = 0.f, pb = 0.f;
+  pair_fixed2<K, EW>(C, r2a, r2b, fa, fb, pa, pb);
+  pair_acc<EW>(C, phic, a0, a1, a2, r2a, fa, pa, A);
+  pair_acc<EW>(C, phic, b0, b1, b2, r2b, fb, pb, A);
 }
 
 template <bool EW>
 __global__ void __launch_bounds__(kPairSmallThreads, EW ? 3 : 4) k_pair_small(
-    int32_t n_items, const int4* __restrict__ items, const int32_t* __restrict__ warp_sys, SysArrays S,
+    int32_t n_items, const int4* __restrict__ items, const int32_t* __restrict__ item_sys, SysArrays S,
     SlotArrays A, const DevPot* __restrict__ pots, int64_t stride, int filter, double* __restrict__ partial,
     int inner) {
   // a launch that follows this one with programmatic serialization (the MD
@@ -273,33 +350,66 @@ __global__ void __launch_bounds__(kPairSmallThreads, EW ? 3 : 4) k_pair_small(
   uint4* tabs = smem;                                   // [kItemWarps][kTabEntries] image shifts
   uint4* sq = smem + kItemWarps * kTabEntries;          // [staged] fixed-point (x, y, z, -)
   if ((int)blockIdx.x >= n_items) return;
+  // The prologue is a chain of dependent loads (item -> system words ->
+  // list words and image shifts -> staged positions): each level's loads go
+  // out together, and every load that needs no shared memory leaves before
+  // the staging loop, so that its latency overlaps it.
   const int4 W = items[blockIdx.x];
   const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int s = item_sys[(int64_t)blockIdx.x * kItemWarps + wl];   // 0 past the item's warps
+  const bool inw = wl < W.w;
   const int wg = W.z + wl;
-  const int s = wl < W.w ? warp_sys[wg] : 0;
+  const int64_t k = (int64_t)wg * kWarp + lane;
+  const uint4* lp = reinterpret_cast<const uint4*>(A.nbr_in) + k;
+  // the system's words and the slot's inner-list count and first group (the
+  // group exists for every slot; both are used only with a standing inner list)
+  const int fmt_s = S.infmt[s];
+  const int64_t seg = S.seg_start[s];
+  const int n_s = S.n_atoms[s];
+  const int pot_s = S.pot[s];
+  int nn_first = 0;
+  uint4 g_first = make_uint4(0u, 0u, 0u, 0u);
+  if (inw && inner) { nn_first = A.nn_in[k]; g_first = __ldcs(lp); }
   // list mode of this warp: inner lists in MD steps unless the system is
   // re-listed in this pass or flagged for filtering
-  const bool sel = wl < W.w && !pair_skip(S, s, filter);
+  const bool sel = inw && !pair_skip(S, s, filter);
   const bool refresh = sel && inner && (S.prune[s] || need_relist(S, s));
   // leave before staging when no warp of the item is selected
   const bool mine = sel;
   if (!__syncthreads_or(mine)) return;
-  const int fmt = mine && inner && !refresh ? S.infmt[s] : kInnerVerlet;
+  const int fmt = mine && inner && !refresh ? fmt_s : kInnerVerlet;
   const bool use_in = mine && inner && !refresh;
   const bool staged_tab = use_in && fmt_kind(fmt) == kInnerTab;   // warp-uniform
   const int64_t st0 = (int64_t)W.x * kWarp;
   const int nst = W.y * kWarp;
+  const int i = (int)(k - seg);
+  const bool valid = mine && i < n_s;
+  if (!(use_in && valid)) nn_first = 0;
+  // the warp's image shifts (|n_a| <= b_a as the format word says; at most
+  // 125, four per lane), held in registers across the staging loop
+  uint4* tab = tabs + wl * kTabEntries;
+  const uint4* gt = S.shiftq + (int64_t)s * kNCodes;
+  const int ntab = staged_tab ? (2 * fmt_bound(fmt, 0) + 1) * (2 * fmt_bound(fmt, 1) + 1) * (2 * fmt_bound(fmt, 2) + 1) : 0;
+  uint4 tv[4];
+  {
+    const TabDecode td(fmt);
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const int c = lane + q * kWarp;
+      if (c < ntab) tv[q] = __ldg(gt + td.code(c));
+    }
+  }
 #pragma unroll 4
   for (int t = threadIdx.x; t < nst; t += blockDim.x) {
     float4 h = __ldg(A.xh + st0 + t), l = __ldg(A.xl + st0 + t);
     sq[t] = make_uint4(fix_coord(h.x, l.x), fix_coord(h.y, l.y), fix_coord(h.z, l.z), 0u);
   }
-  uint4* tab = tabs + wl * kTabEntries;
-  if (staged_tab) {   // this warp's image shifts, |n_a| <= b_a as the format word says
-    const uint4* gt = S.shiftq + (int64_t)s * kNCodes;
-    const int ntab = (2 * fmt_bound(fmt, 0) + 1) * (2 * fmt_bound(fmt, 1) + 1) * (2 * fmt_bound(fmt, 2) + 1);
-    const TabDecode td(fmt);
-    for (int c = lane; c < ntab; c += kWarp) tab[c] = __ldg(gt + td.code(c));
+  if (staged_tab) {
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const int c = lane + q * kWarp;
+      if (c < ntab) tab[c] = tv[q];
+    }
     if (lane == 0) tab[kTabFar] = make_uint4(kFarShift, 0u, 0u, 0u);
   }
   // a warp that filters its inner list (into the table format) reads no
@@ -313,13 +423,8 @@ __global__ void __launch_bounds__(kPairSmallThreads, EW ? 3 : 4) k_pair_small(
   }
   __syncthreads();
   if (!mine) return;
-  const int64_t seg = S.seg_start[s];
-  const int64_t k = (int64_t)wg * kWarp + lane;
-  const int i = (int)(k - seg);
-  const int n = S.n_atoms[s];
-  const bool valid = i < n;
   const uint4* hq = sq + (seg - st0);
-  const DevPot P = pots[S.pot[s]];
+  const DevPot P = pots[pot_s];
   const uint4* gtab = S.shiftq + (int64_t)s * kNCodes;
   const uint4 xi = valid ? hq[i] : make_uint4(0, 0, 0, 0);
   PairSums<EW> acc;
@@ -331,40 +436,27 @@ __global__ void __launch_bounds__(kPairSmallThreads, EW ? 3 : 4) k_pair_small(
       // four entries per 16-byte load, the next group in flight ahead of use
       const char* hb = reinterpret_cast<const char*>(hq);
       const char* tb = reinterpret_cast<const char*>(tab);
-      const uint4* lp = reinterpret_cast<const uint4*>(A.nbr_in) + k;
-      const int ng = valid ? (A.nn_in[k] + 3) >> 2 : 0;
-      auto one = [&](uint32_t ent) {
-        const uint4 xj = *reinterpret_cast<const uint4*>(hb + (ent & 0xffffu));
-        uint4 sh;
-        if (staged_tab) {
-          sh = *reinterpret_cast<const uint4*>(tb + (ent >> 16));
-        } else {   // kInnerRaw: the image code, or kRawFar for padding
-          const uint32_t code = ent >> 16;
-          sh = code == kRawFar ? make_uint4(kFarShift, 0u, 0u, 0u)
+      const int ng = (nn_first + 3) >> 2;
+      auto shift = [&](uint32_t ent) {
+        if (staged_tab) return *reinterpret_cast<const uint4*>(tb + (ent >> 16));
+        // kInnerRaw: the image code, or kRawFar for padding
+        const uint32_t code = ent >> 16;
+        return code == kRawFar ? make_uint4(kFarShift, 0u, 0u, 0u)
                                : (code != (uint32_t)kCenter ? __ldg(gtab + code) : make_uint4(0u, 0u, 0u, 0u));
-        }
-        pair_add<K, EW>(C, P.phicf, xi, xj, sh, acc);
       };
-#if TS_PAIR_PREFETCH2
-      uint4 n0 = make_uint4(0, 0, 0, 0), n1 = n0;
-      if (ng > 0) n0 = __ldcs(lp);
-      if (ng > 1) n1 = __ldcs(lp + stride);
-      for (int g = 0; g < ng; g++) {
-        const uint4 e = n0;
-        n0 = n1;
-        if (g + 2 < ng) n1 = __ldcs(lp + (int64_t)(g + 2) * stride);
-        one(e.x); one(e.y); one(e.z); one(e.w);
-      }
-#else
+      auto two = [&](uint32_t ea, uint32_t eb) {
+        const uint4 xa = *reinterpret_cast<const uint4*>(hb + (ea & 0xffffu));
+        const uint4 xb = *reinterpret_cast<const uint4*>(hb + (eb & 0xffffu));
+        float ra, rb;
+        pair_add2<K, EW>(C, P.phicf, xi, xa, shift(ea), xb, shift(eb), acc, ra, rb);
+      };
       // one group of four in flight ahead of use
-      uint4 n0 = make_uint4(0, 0, 0, 0);
-      if (ng > 0) n0 = __ldcs(lp);
+      uint4 n0 = g_first;
       for (int g = 0; g < ng; g++) {
         const uint4 e = n0;
         if (g + 1 < ng) n0 = __ldcs(lp + (int64_t)(g + 1) * stride);
-        one(e.x); one(e.y); one(e.z); one(e.w);
+        two(e.x, e.y); two(e.z, e.w);
       }
-#endif
     } else {   // Verlet list; in MD steps, filter it into the inner list
       const int nn = valid ? A.nn[k] : 0;
       const uint32_t* lp = A.nbr + k;
