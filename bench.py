@@ -32,7 +32,7 @@ BYTES_PER_ATOM = 32         # read own position, write own force, per atom-step
 # DRAM bytes (read + write) of one forces-only k_pair_small launch (inner lists, rc + 0.45 skin) on
 # ragged-mix-512, from one ncu capture of the steady launch; reported only while the kernel's sources
 # (ts_pair.cu, then ts_internal.cuh) hash to the value recorded with the capture
-PAIR_TRAFFIC = {"bytes": 55_853_312 + 755_456, "source_sha1": "b22d031fda518c1b61d16ac0a89aece9667da6b3"}
+PAIR_TRAFFIC = {"bytes": 55_926_784 + 718_848, "source_sha1": "87b3ccc3a3fe858a74ee7694332db1d6d2d1bd4e"}
 
 
 def pair_traffic():

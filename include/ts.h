@@ -465,7 +465,9 @@ ts_status ts_batch_set_tuning(ts_batch* b, const ts_tuning* t);
  * inner lists, the form an MD step uses) reps times, after re-listing flagged
  * systems and re-filtering every inner list, each launch preceded by
  * a write of flush_bytes to flush_buf (device scratch, may be NULL) to evict
- * L2, timing each launch with CUDA events on the stream.  Synchronises.
+ * L2, timing each launch with its own pair of CUDA events on the stream (all
+ * launches are enqueued before the first is waited for, so that no event pair
+ * includes the host's launch latency).  Synchronises.
  * ms_out (host): mean launch duration in ms; pairs_out (host, may be NULL):
  * ordered pairs within the cutoff (the algorithmic work of one launch);
  * atoms_out (host, may be NULL): atoms per launch. */

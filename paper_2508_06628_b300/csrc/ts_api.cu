@@ -830,21 +830,29 @@ extern "C" ts_status ts_profile_pair(ts_batch* b, ts_state* s, int reps, void* f
   if (!cuda_ok(b, cudaMemsetAsync(b->S.prune, 1, 4 * (size_t)b->B, st), "memset")) return TS_ERR_CUDA;
   pair(b, st, false, kPairAll, 0, true);
   if (!cuda_ok(b, cudaMemsetAsync(b->S.prune, 0, 4 * (size_t)b->B, st), "memset")) return TS_ERR_CUDA;
-  cudaEvent_t e0, e1;
-  if (!cuda_ok(b, cudaEventCreate(&e0), "event") || !cuda_ok(b, cudaEventCreate(&e1), "event")) return TS_ERR_CUDA;
-  double total = 0;
-  for (int k = 0; k < reps; k++) {
+  // every launch between its own pair of events, all enqueued before the
+  // first is waited for: the stream is busy (the refreshing launch above, the
+  // previous launch or the flush) while the host submits the next, so no
+  // event pair includes the host's launch latency
+  std::vector<cudaEvent_t> ev(2 * (size_t)reps, nullptr);
+  bool ok = true;
+  for (auto& e : ev) ok = ok && cuda_ok(b, cudaEventCreate(&e), "event");
+  for (int k = 0; ok && k < reps; k++) {
     if (flush_buf && flush_bytes) cudaMemsetAsync(flush_buf, k & 0xff, flush_bytes, st);
-    cudaEventRecord(e0, st);
+    cudaEventRecord(ev[2 * k], st);
     pair(b, st, false, kPairAll, 0, true);
-    cudaEventRecord(e1, st);
-    if (!cuda_ok(b, cudaEventSynchronize(e1), "event sync")) return TS_ERR_CUDA;
+    cudaEventRecord(ev[2 * k + 1], st);
+  }
+  double total = 0;
+  if (ok) ok = cuda_ok(b, cudaEventSynchronize(ev[2 * (size_t)reps - 1]), "event sync");
+  for (int k = 0; ok && k < reps; k++) {
     float ms = 0;
-    cudaEventElapsedTime(&ms, e0, e1);
+    ok = cuda_ok(b, cudaEventElapsedTime(&ms, ev[2 * k], ev[2 * k + 1]), "event time");
     total += ms;
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  for (auto& e : ev)
+    if (e) cudaEventDestroy(e);
+  if (!ok) return TS_ERR_CUDA;
   *ms_out = total / reps;
   if (pairs_out) {
     unsigned long long* d = (unsigned long long*)b->d_counters + 2;
