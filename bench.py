@@ -322,43 +322,35 @@ def per_system_loop(hb, pots, dev, args, n_sample=32, steps=3):
 
 def e2e(b, s, hb, dev, stream, args, dt, gamma, inner):
     """Same metric through the public API with the state held on the host in
-    pinned buffers: every call copies positions and velocities in (H2D), runs
-    its steps and copies the new positions, velocities and per-system energies
-    back (D2H), so the trajectory continues from call to call."""
+    pinned buffers (runtime.HostMD): every call copies positions and
+    velocities in (H2D), runs its steps and copies the new positions,
+    velocities and per-system energies back (D2H), so the trajectory continues
+    from call to call.  HostMD splits the systems into two atom-balanced
+    groups on two streams, so that one group's copies overlap the other's
+    steps; both groups take the main batch's tuning."""
     import torch
-    from paper_2508_06628_b300 import ts
-    pos_h = torch.from_numpy(np.ascontiguousarray(hb.pos)).pin_memory()
-    vel_h = torch.from_numpy(np.ascontiguousarray(hb.vel)).pin_memory()
-    E = torch.zeros(hb.n_systems, dtype=torch.float64, device=dev)
-    KE = torch.zeros_like(E)
-    E_h = torch.zeros(hb.n_systems, dtype=torch.float64).pin_memory()
-    KE_h = torch.zeros_like(E_h).pin_memory()
+    from paper_2508_06628_b300 import runtime, ts
+    if hb.uid is None:
+        hb.uid = np.arange(hb.n_systems, dtype=np.uint32)
+    hm = runtime.HostMD(hb, [dict(p) for p in b.pots], parts=2, device=dev.index, tuning=b.tuning())
     ncalls = max(1, (args.steps + inner - 1) // inner)
-    with torch.cuda.stream(stream):
-        s.pos.copy_(pos_h, non_blocking=True)
-        s.vel.copy_(vel_h, non_blocking=True)
-        b.md_step(s, inner, dt, kind=ts.TS_LANGEVIN, gamma=gamma, seed=9, stream=stream)   # warm (re-list)
-        pos_h.copy_(s.pos, non_blocking=True)
-        vel_h.copy_(s.vel, non_blocking=True)
-        stream.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for c in range(ncalls):
-            s.pos.copy_(pos_h, non_blocking=True)
-            s.vel.copy_(vel_h, non_blocking=True)
-            b.md_step(s, inner, dt, kind=ts.TS_LANGEVIN, gamma=gamma, seed=9, step0=(c + 1) * inner, E=E, KE=KE,
-                      stream=stream)
-            pos_h.copy_(s.pos, non_blocking=True)
-            vel_h.copy_(s.vel, non_blocking=True)
-            E_h.copy_(E, non_blocking=True)
-            KE_h.copy_(KE, non_blocking=True)
-        e1.record(stream)
-        stream.synchronize()
+    hm.step(inner, dt, kind=ts.TS_LANGEVIN, gamma=gamma, seed=9)   # warm (lists built)
+    hm.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for c in range(ncalls):
+        hm.step(inner, dt, kind=ts.TS_LANGEVIN, gamma=gamma, seed=9, step0=(c + 1) * inner, after=e0 if c == 0 else None)
+    hm.join(stream)
+    e1.record(stream)
+    stream.synchronize()
+    hm.synchronize()
     ms = e0.elapsed_time(e1)
+    hm.close()
     return {"value": hb.n_atoms * ncalls * inner / (ms / 1e3), "unit": UNIT,
-            "h2d_bytes_per_step": int(2 * hb.n_atoms * 24 / inner),
-            "d2h_bytes_per_step": int((2 * hb.n_atoms * 24 + 2 * hb.n_systems * 8) / inner),
-            "how": f"per call of {inner} steps: H2D pos+vel from pinned host, D2H pos+vel+energies"}
+            "h2d_bytes_per_step": int(hm.h2d_bytes() / inner), "d2h_bytes_per_step": int(hm.d2h_bytes() / inner),
+            "how": f"per call of {inner} steps: H2D pos+vel from pinned host, D2H pos+vel+energies; the systems in "
+                   f"two atom-balanced groups on two streams (runtime.HostMD), one group's copies beside the "
+                   f"other's steps"}
 
 
 def cpu_baseline(hb, budget_s=15.0, steps=None, warmup=0):

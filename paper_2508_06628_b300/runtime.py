@@ -9,6 +9,9 @@
 * Binned fixed-length MD: pack the systems into as few bins of the maximum
   memory as ts_bin_pack finds and evolve the bins one after another.
 
+Also HostMD: MD of a batch whose state is held in host memory, its systems
+split over streams so that one group's copies overlap another's steps.
+
 Orchestration only: every step of the simulations runs in the library.
 """
 from __future__ import annotations
@@ -296,3 +299,102 @@ def run_binned_sharded(hb, pots, max_scaler, n_steps, dt, group=None, device=Non
     dev = torch.cuda.current_device() if device is None else device
     return parallel.run_sharded(hb, lambda sub: run_binned(sub, pots, max_scaler, n_steps, dt, device=dev, **kw)[0],
                                 group)
+
+
+class HostMD:
+    """MD of a batch whose state is held in host memory.
+
+    Each call copies positions and velocities to the device, runs n steps
+    there and copies them back, with the per-system energies, so the
+    trajectory lives on the host between calls (a caller that reads or edits
+    it between calls, or whose data does not fit the device).  The systems are
+    split into ``parts`` atom-balanced groups (parallel.shard_systems), each
+    its own device batch and CUDA stream with its own pinned host buffers, so
+    that one group's copies overlap another group's steps.  Every system keeps
+    its index in ``hb`` as its noise id, so its trajectory is the one a single
+    batch of all systems gives, up to the summation order of re-listed
+    neighbour lists (each group gathers its own re-listings).
+
+    ``tuning``: ts_batch_set_tuning fields for every group (default: the
+    library's).  Orchestration only: every step runs in the library."""
+
+    def __init__(self, hb, pots, parts=2, precision=ts.TS_MIXED, device=0, tuning=None):
+        torch = ts._torch()
+        self._torch = torch
+        self.dev = torch.device("cuda", device)
+        self.n_systems, self.n_atoms = hb.n_systems, hb.n_atoms
+        self.offsets = np.asarray(hb.offsets)
+        uid = np.asarray(hb.uid if hb.uid is not None else np.arange(hb.n_systems), np.uint32)
+        parts = max(1, min(int(parts), hb.n_systems))
+        self.groups = []
+        for ids in parallel.shard_systems(np.diff(self.offsets), parts):
+            if len(ids) == 0:
+                continue
+            sub = hb.subset(ids)
+            sub.uid = uid[ids]
+            b = ts.Batch(pots, sub.n_atoms, sub.n_systems, precision=precision, device=device)
+            if tuning:
+                b.set_tuning(**tuning)
+            pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+            E = torch.zeros(sub.n_systems, dtype=torch.float64, device=self.dev)
+            self.groups.append(dict(ids=np.asarray(ids), off=sub.offsets, b=b, s=ts.DeviceState.from_host(sub, self.dev),
+                                    stream=torch.cuda.Stream(device=self.dev), pos=pin(sub.pos), vel=pin(sub.vel),
+                                    E=E, KE=torch.zeros_like(E), E_h=pin(np.zeros(sub.n_systems)),
+                                    KE_h=pin(np.zeros(sub.n_systems))))
+
+    def h2d_bytes(self):
+        """Bytes copied to the device per call (positions and velocities)."""
+        return 2 * 24 * self.n_atoms
+
+    def d2h_bytes(self):
+        """Bytes copied back per call (positions, velocities, E and KE)."""
+        return 2 * 24 * self.n_atoms + 2 * 8 * self.n_systems
+
+    def step(self, n_steps, dt, kind=ts.TS_LANGEVIN, gamma=0.0, seed=0, step0=0, after=None):
+        """Enqueue one call on every group's stream (returns before it ends):
+        copy in, ``n_steps`` steps of ts_md_step, copy out.  ``after``: a CUDA
+        event every group waits for first (optional)."""
+        for g in self.groups:
+            st = g["stream"]
+            if after is not None:
+                st.wait_event(after)
+            with self._torch.cuda.stream(st):
+                g["s"].pos.copy_(g["pos"], non_blocking=True)
+                g["s"].vel.copy_(g["vel"], non_blocking=True)
+                g["b"].md_step(g["s"], n_steps, dt, kind=kind, gamma=gamma, seed=seed, step0=step0, E=g["E"],
+                               KE=g["KE"], stream=st)
+                g["pos"].copy_(g["s"].pos, non_blocking=True)
+                g["vel"].copy_(g["s"].vel, non_blocking=True)
+                g["E_h"].copy_(g["E"], non_blocking=True)
+                g["KE_h"].copy_(g["KE"], non_blocking=True)
+
+    def join(self, stream):
+        """Make ``stream`` wait for every call enqueued so far."""
+        for g in self.groups:
+            ev = self._torch.cuda.Event()
+            ev.record(g["stream"])
+            stream.wait_event(ev)
+
+    def synchronize(self):
+        for g in self.groups:
+            g["stream"].synchronize()
+            g["b"].poll(g["stream"])
+
+    def state(self):
+        """(pos, vel, E, KE) in the order of ``hb``, as numpy arrays, after
+        the calls enqueued so far."""
+        self.synchronize()
+        pos = np.empty((self.n_atoms, 3)); vel = np.empty((self.n_atoms, 3))
+        E = np.empty(self.n_systems); KE = np.empty(self.n_systems)
+        for g in self.groups:
+            gp, gv = g["pos"].numpy(), g["vel"].numpy()
+            for j, i in enumerate(g["ids"]):
+                a, e, ga = self.offsets[i], self.offsets[i + 1], g["off"][j]
+                pos[a:e] = gp[ga:ga + e - a]; vel[a:e] = gv[ga:ga + e - a]
+            E[g["ids"]] = g["E_h"].numpy(); KE[g["ids"]] = g["KE_h"].numpy()
+        return pos, vel, E, KE
+
+    def close(self):
+        for g in self.groups:
+            g["b"].close()
+        self.groups = []
