@@ -209,25 +209,43 @@ __global__ void __launch_bounds__(128, F64 ? 4 : 8) k_pair_bwd(int32_t n_warps, 
 // staged bytes per atom: the fixed-point position with gF_x in its fourth word (16 B), gF_y and gF_z (8 B)
 constexpr int kBwdRecord = 24;
 __global__ void __launch_bounds__(kPairSmallThreads, 3) k_pair_bwd_small(
-    int32_t n_items, const int4* __restrict__ items, const int32_t* __restrict__ warp_sys, SysArrays S,
+    int32_t n_items, const int4* __restrict__ items, const int32_t* __restrict__ item_sys, SysArrays S,
     SlotArrays A, const DevPot* __restrict__ pots, int64_t stride, const double* __restrict__ gE, double* gpart,
     int accum_part) {
   extern __shared__ __align__(16) uint4 smem[];
   uint4* tabs = smem;                                   // [kItemWarps][kTabEntries] image shifts
   uint4* sq = smem + kItemWarps * kTabEntries;          // [staged] fixed-point (x, y, z, -)
   if ((int)blockIdx.x >= n_items) return;
+  // the prologue's dependent loads as in k_pair_small: item and its warps'
+  // systems, then the system and slot words (and the first inner-list group)
+  // together, ahead of the staging loop
   const int4 W = items[blockIdx.x];
   float2* sg = reinterpret_cast<float2*>(sq + W.y * kWarp);   // [staged] upstream gF_y, gF_z
   const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int s = item_sys[(int64_t)blockIdx.x * kItemWarps + wl];   // 0 past the item's warps
   const int wg = W.z + wl;
   const bool mine = wl < W.w;
-  const int s = mine ? warp_sys[wg] : 0;
+  const int64_t k = (int64_t)wg * kWarp + lane;
+  const uint4* lp = reinterpret_cast<const uint4*>(A.nbr_in) + k;
+  const int fmt_s = S.infmt[s];
+  const int64_t seg = S.seg_start[s];
+  const int n_s = S.n_atoms[s];
+  const int pot_s = S.pot[s];
+  const double gEs = gE ? gE[s] : 0.0;
+  int nn_first = 0;
+  uint4 g_first = make_uint4(0u, 0u, 0u, 0u);
+  if (mine) { nn_first = A.nn_in[k]; g_first = __ldcs(lp); }   // group 0 exists for every slot
   // the inner list holds every pair within rc unless the system was flagged or re-listed since its filtering
   const bool use_in = mine && !S.prune[s] && !need_relist(S, s);
-  const int fmt = use_in ? S.infmt[s] : kInnerVerlet;
+  const int fmt = use_in ? fmt_s : kInnerVerlet;
   const bool staged_tab = use_in && fmt_kind(fmt) == kInnerTab;
   const int64_t st0 = (int64_t)W.x * kWarp;
   const int nst = W.y * kWarp;
+  const int i = (int)(k - seg);
+  const bool valid = mine && i < n_s;
+  if (!(use_in && valid)) nn_first = 0;
+  uint4* tab = tabs + wl * kTabEntries;
+  const uint4* gtab = S.shiftq + (int64_t)s * kNCodes;
 #pragma unroll 4
   for (int t = threadIdx.x; t < nst; t += blockDim.x) {
     float4 h = __ldg(A.xh + st0 + t), l = __ldg(A.xl + st0 + t);
@@ -235,28 +253,20 @@ __global__ void __launch_bounds__(kPairSmallThreads, 3) k_pair_bwd_small(
     sq[t] = make_uint4(fix_coord(h.x, l.x), fix_coord(h.y, l.y), fix_coord(h.z, l.z), __float_as_uint(g.x));
     sg[t] = make_float2(g.y, g.z);
   }
-  uint4* tab = tabs + wl * kTabEntries;
   if (staged_tab) {
-    const uint4* gt = S.shiftq + (int64_t)s * kNCodes;
     const int ntab = (2 * fmt_bound(fmt, 0) + 1) * (2 * fmt_bound(fmt, 1) + 1) * (2 * fmt_bound(fmt, 2) + 1);
     const TabDecode td(fmt);
-    for (int c = lane; c < ntab; c += kWarp) tab[c] = __ldg(gt + td.code(c));
+    for (int c = lane; c < ntab; c += kWarp) tab[c] = __ldg(gtab + td.code(c));
     if (lane == 0) tab[kTabFar] = make_uint4(kFarShift, 0u, 0u, 0u);
   }
   __syncthreads();
   if (!mine) return;
-  const int64_t seg = S.seg_start[s];
-  const int64_t k = (int64_t)wg * kWarp + lane;
-  const int i = (int)(k - seg);
-  const bool valid = i < S.n_atoms[s];
   const uint4* hq = sq + (seg - st0);
-  const DevPot P = pots[S.pot[s]];
-  const uint4* gtab = S.shiftq + (int64_t)s * kNCodes;
+  const DevPot P = pots[pot_s];
   const float2* g1s = sg + (seg - st0);
   const uint4 xi = valid ? hq[i] : make_uint4(0, 0, 0, 0);
   const float2 gyz = valid ? g1s[i] : make_float2(0.f, 0.f);
   const float4 gi = make_float4(__uint_as_float(xi.w), gyz.x, gyz.y, 0.f);
-  const double gEs = gE ? gE[s] : 0.0;
   const float gEf = (float)gEs;
   float dpc[3] = {0.f, 0.f, 0.f};
   if (P.shift && P.kind != TS_SOFT_SPHERE && gEs != 0.0) {
@@ -322,8 +332,7 @@ __global__ void __launch_bounds__(kPairSmallThreads, 3) k_pair_bwd_small(
     // four entries per 16-byte load, the next group in flight ahead of use
     const char* hb = reinterpret_cast<const char*>(hq);
     const char* tb = reinterpret_cast<const char*>(tab);
-    const uint4* lp = reinterpret_cast<const uint4*>(A.nbr_in) + k;
-    const int ng = valid ? (A.nn_in[k] + 3) >> 2 : 0;
+    const int ng = (nn_first + 3) >> 2;
     auto ent1 = [&](uint32_t ent) {
       const uint32_t off = ent & 0xffffu;
       const uint4 xj = *reinterpret_cast<const uint4*>(hb + off);
@@ -337,8 +346,7 @@ __global__ void __launch_bounds__(kPairSmallThreads, 3) k_pair_bwd_small(
       }
       one(kind, xj, sh, (int)(off >> 4));
     };
-    uint4 n0 = make_uint4(0, 0, 0, 0);
-    if (ng > 0) n0 = __ldcs(lp);
+    uint4 n0 = g_first;
     for (int gq = 0; gq < ng; gq++) {
       const uint4 e = n0;
       if (gq + 1 < ng) n0 = __ldcs(lp + (int64_t)(gq + 1) * stride);
@@ -628,7 +636,7 @@ static void backward_core(ts_batch* b, cudaStream_t st, const double* gE, const 
   const bool small = !b->f64 && !gS && b->use_small_pair && b->bwd_small && b->n_items > 0;
   if (small) {
     k_pair_bwd_small<<<b->n_items, 32 * b->tune.item_warps, shm, st>>>(
-        b->n_items, b->d_items, b->d_warp_sys, b->S, b->A, b->d_pots, b->Ncap, gE, b->d_gparam_part, accum_part);
+        b->n_items, b->d_items, b->d_item_sys, b->S, b->A, b->d_pots, b->Ncap, gE, b->d_gparam_part, accum_part);
     b->launches++;
   }
   if (!small || b->n_large > 0) {
