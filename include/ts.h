@@ -429,23 +429,31 @@ ts_status ts_batch_poll(ts_batch* b, void* stream, int timeout_ms);
  *                   whose atoms moved more than relist_soon * skin/2 re-list
  *                   in the same pass, (0, 1] (1 = off);
  *   bin_factor      cell-list bin edge = bin_factor * (rc + skin): 1 or 0.5
- *                   (the stencil then reaches two bins). */
+ *                   (the stencil then reaches two bins);
+ *   skin_scale      every potential's skin is used times skin_scale, (0, 1]
+ *                   (shorter Verlet lists and more frequent re-listing; the
+ *                   lists never outgrow the capacity sized for the skins
+ *                   given at create; ts_rdf refuses an rmax + 4D beyond
+ *                   rc + skin * skin_scale). */
 typedef struct {
   int32_t item_warps;
   double inner_fraction;
   double relist_soon;
   double bin_factor;
+  double skin_scale;
 } ts_tuning;
 
 /* Autotuner (the paper has no counterpart).  Times the MD step of p (n_steps
  * per timed call, CUDA events around CUDA-graph replays on `stream`) for
  * candidate values of each ts_tuning field in turn -- bin_factor {1, 0.5},
- * item_warps {8, 4}, inner_fraction {0.2, 0.3, 0.45, 1}, relist_soon {0.4, 0.5,
- * 0.6} -- keeping the fastest value of each before tuning the next, applies
- * the result and appends it to cfg->autotune_cache (host text file, one
- * "key item_warps inner_fraction relist_soon bin_factor" line; key = potential
- * kinds, log2 of the atom and system capacities, precision) when a path was
- * given.  ts_batch_create applies the last matching cache line.  The state
+ * item_warps {8, 4}, skin_scale {1, 0.9, 0.8}, inner_fraction {0.2, 0.3, 0.45,
+ * 0.5, 1}, relist_soon {0.4, 0.5, 0.6} -- keeping the fastest value of each
+ * before tuning the next, applies the result and appends it to
+ * cfg->autotune_cache (host text file, one "key item_warps inner_fraction
+ * relist_soon bin_factor skin_scale" line; key = potential kinds, log2 of the
+ * atom and system capacities, precision; a line without skin_scale reads as
+ * 1) when a path was given.  ts_batch_create applies the last matching cache
+ * line.  The state
  * is first advanced by 4 n_steps (so that trials time the dynamics that
  * follow, not the start-up transient), then saved in a temporary device copy
  * (positions, velocities; the cell and piston velocities under NPT, the chain

@@ -666,7 +666,7 @@ static void backward_core(ts_batch* b, cudaStream_t st, const double* gE, const 
 static ts_status rdf_check(ts_batch* b, double rmax, int K) {
   if (!(rmax > 0) || K < 1 || K > 4096) return fail(b, TS_ERR_INVALID_ARG, "bad rmax or K");
   for (int q = 0; q < b->n_pots; q++)
-    if (b->rc[q] + b->pots[q].skin < rmax + 4.0 * rmax / K)
+    if (b->rc[q] + b->pots[q].skin * b->tune.skin_scale < rmax + 4.0 * rmax / K)
       return fail(b, TS_ERR_INVALID_ARG, "neighbour lists shorter than rmax + 4 D: raise the skin");
   return TS_OK;
 }

@@ -65,8 +65,9 @@ size_t scratch_bytes(int64_t Ncap, int64_t Bcap, int64_t Ccap, int32_t max_nbrs,
 }
 
 // The device potential table from the potentials and the tuned parameters:
-// cutoffs and shifts, list radius rc + skin, bin edge (the list radius times
-// the tuned bin factor), re-list hysteresis, inner (pruned) list radius.
+// cutoffs and shifts, list radius rc + skin (the potential's skin times the
+// tuned scale), bin edge (the list radius times the tuned bin factor), re-list
+// hysteresis, inner (pruned) list radius.
 void fill_devpots(ts_batch* b, DevPot* dp) {
   memset(dp, 0, sizeof(DevPot) * kMaxPots);
   b->use_small_pair = true;
@@ -82,19 +83,20 @@ void fill_devpots(ts_batch* b, DevPot* dp) {
     if (P.shift && P.kind == TS_LJ) { double s = P.p[0] / rc, s6 = s * s * s * s * s * s; phic = 4 * P.p[1] * (s6 * s6 - s6); }
     if (P.shift && P.kind == TS_MORSE) { double e = exp(-P.p[1] * (rc - P.p[2])); phic = P.p[0] * (e * e - 2 * e); }
     D.phicd = phic; D.phicf = (float)phic;
-    D.skin = P.skin;
-    D.rlist = rc + P.skin; D.rlist2d = D.rlist * D.rlist; D.rlist2f = (float)D.rlist2d;
+    const double skin = P.skin * b->tune.skin_scale;   // the tuned skin
+    D.skin = skin;
+    D.rlist = rc + skin; D.rlist2d = D.rlist * D.rlist; D.rlist2f = (float)D.rlist2d;
     D.binw = D.rlist * b->tune.bin_factor;
     D.soon2 = b->tune.relist_soon * b->tune.relist_soon;
     {   // inner skin of the pruned list: a fraction of the skin (1 = no pruning)
-      double sin = b->tune.inner_fraction * P.skin, ri = rc + sin + kListBand;
+      double sin = b->tune.inner_fraction * skin, ri = rc + sin + kListBand;
       D.rin2d = ri * ri; D.rin2f = (float)D.rin2d;
       D.half_in2d = 0.25 * sin * sin; D.half_in2f = (float)D.half_in2d;
     }
     D.rlist_in2f = (float)((D.rlist - kListBand) * (D.rlist - kListBand));
     D.rlist_out2f = (float)((D.rlist + kListBand) * (D.rlist + kListBand));
-    D.half_skin2f = (float)(0.25 * P.skin * P.skin);
-    D.soon_half_skin2f = (float)(D.soon2 * 0.25 * P.skin * P.skin);
+    D.half_skin2f = (float)(0.25 * skin * skin);
+    D.soon_half_skin2f = (float)(D.soon2 * 0.25 * skin * skin);
     b->rc[q] = rc;
     if (D.rlist >= kFixMaxList) b->use_small_pair = false;   // beyond the fixed-point range of k_pair_small
   }

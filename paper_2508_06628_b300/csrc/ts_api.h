@@ -83,7 +83,7 @@ struct ts_batch {
   int prio_hi = 0;                // numerically greatest-priority value of the device
   // launch shapes and list parameters (autotuned, ts_tune.cu)
   int pair_threads = 128;
-  ts_tuning tune = {8, 0.3, 0.5, 1.0};
+  ts_tuning tune = {8, 0.3, 0.5, 1.0, 1.0};
   bool use_graphs = true;
   std::vector<ts_graph_entry> graphs;
   bool graphs_valid = false;

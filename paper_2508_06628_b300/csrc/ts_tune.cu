@@ -1,13 +1,14 @@
 // ts_tune.cu -- the autotuner of the hot path's launch and list parameters
-// (ts_tuning: pair work-item size, cell-list bin edge, inner-list radius,
-// re-list hysteresis).  Each candidate is timed in situ: the batch's MD step
+// (ts_tuning: pair work-item size, cell-list bin edge, skin scale,
+// inner-list radius, re-list hysteresis).  Each candidate is timed in situ: the batch's MD step
 // (as the caller runs it) replayed as a CUDA graph, CUDA events around whole
 // calls on the caller's stream.  The fields are tuned one after another, each
 // over its candidate values with the others at their best so far.  Results
 // are cached in a text file keyed by (potential kinds, log2 of the atom and
 // system capacities, precision), one line per tuning:
-//   key item_warps inner_fraction relist_soon bin_factor
-// and the last line matching a batch's key is applied at ts_batch_create.
+//   key item_warps inner_fraction relist_soon bin_factor skin_scale
+// (a line without skin_scale reads as 1), and the last line matching a
+// batch's key is applied at ts_batch_create.
 #include <cmath>
 #include <cstdlib>
 #include <cstdio>
@@ -33,7 +34,8 @@ static std::string tune_key(const ts_batch* b) {
 
 bool tuning_valid(const ts_tuning& t) {
   return (t.item_warps == 4 || t.item_warps == 8) && t.inner_fraction > 0 && t.inner_fraction <= 1 &&
-         t.relist_soon > 0 && t.relist_soon <= 1 && (t.bin_factor == 1.0 || t.bin_factor == 0.5);
+         t.relist_soon > 0 && t.relist_soon <= 1 && (t.bin_factor == 1.0 || t.bin_factor == 0.5) &&
+         t.skin_scale > 0 && t.skin_scale <= 1;
 }
 
 // the last cache line whose key matches, if any
@@ -45,7 +47,11 @@ static bool read_cache(const std::string& path, const std::string& key, ts_tunin
     std::istringstream ls(line);
     std::string k;
     ts_tuning t;
-    if (ls >> k >> t.item_warps >> t.inner_fraction >> t.relist_soon >> t.bin_factor && k == key && tuning_valid(t)) {
+    t.skin_scale = 1.0;
+    if (!(ls >> k >> t.item_warps >> t.inner_fraction >> t.relist_soon >> t.bin_factor)) continue;
+    double sc;
+    if (ls >> sc) t.skin_scale = sc;
+    if (k == key && tuning_valid(t)) {
       out = t;
       found = true;
     }
@@ -145,8 +151,8 @@ extern "C" ts_status ts_autotune(ts_batch* b, ts_state* s, const ts_md_params* p
     cudaEventElapsedTime(&ms, e0, e1);
     ms_out = ms / (3.0 * n_steps);
     if (getenv("TS_TUNE_LOG"))
-      fprintf(stderr, "ts_autotune: item_warps %d inner %.3g soon %.3g bins %.3g: %.5f ms/step\n", t.item_warps,
-              t.inner_fraction, t.relist_soon, t.bin_factor, ms_out);
+      fprintf(stderr, "ts_autotune: item_warps %d inner %.3g soon %.3g bins %.3g skin %.3g: %.5f ms/step\n",
+              t.item_warps, t.inner_fraction, t.relist_soon, t.bin_factor, t.skin_scale, ms_out);
     return ts_batch_poll(b, st, -1);   // a trial that overflowed a list or met bad input fails the tuning
   };
   ts_tuning best = b->tune;
@@ -161,17 +167,19 @@ extern "C" ts_status ts_autotune(ts_batch* b, ts_state* s, const ts_md_params* p
   // the fields in turn, each over its candidates with the others at their best
   const double bins[2] = {1.0, 0.5};
   const int items[2] = {8, 4};
-  const double inner[4] = {0.2, 0.3, 0.45, 1.0};   // 1: the inner list is the Verlet list
+  const double skins[3] = {1.0, 0.9, 0.8};
+  const double inner[5] = {0.2, 0.3, 0.45, 0.5, 1.0};   // 1: the inner list is the Verlet list
   const double soon[3] = {0.4, 0.5, 0.6};
-  for (int field = 0; field < 4 && r == TS_OK; field++) {
-    const int nc = field < 2 ? 2 : (field == 2 ? 4 : 3);
-    for (int c = 0; c < nc && r == TS_OK; c++) {
+  const int ncand[5] = {2, 2, 3, 5, 3};
+  for (int field = 0; field < 5 && r == TS_OK; field++) {
+    for (int c = 0; c < ncand[field] && r == TS_OK; c++) {
       ts_tuning t = best;
       if (field == 0) t.bin_factor = bins[c];
       if (field == 1) t.item_warps = items[c];
-      if (field == 2) t.inner_fraction = inner[c];
-      if (field == 3) t.relist_soon = soon[c];
-      if (t.bin_factor == best.bin_factor && t.item_warps == best.item_warps &&
+      if (field == 2) t.skin_scale = skins[c];
+      if (field == 3) t.inner_fraction = inner[c];
+      if (field == 4) t.relist_soon = soon[c];
+      if (t.bin_factor == best.bin_factor && t.item_warps == best.item_warps && t.skin_scale == best.skin_scale &&
           t.inner_fraction == best.inner_fraction && t.relist_soon == best.relist_soon)
         continue;   // the current best, timed already
       double ms = 0;
@@ -189,8 +197,8 @@ extern "C" ts_status ts_autotune(ts_batch* b, ts_state* s, const ts_md_params* p
   if (!b->cache_path.empty()) {
     FILE* f = fopen(b->cache_path.c_str(), "a");
     if (f) {
-      fprintf(f, "%s %d %.17g %.17g %.17g\n", tune_key(b).c_str(), best.item_warps, best.inner_fraction,
-              best.relist_soon, best.bin_factor);
+      fprintf(f, "%s %d %.17g %.17g %.17g %.17g\n", tune_key(b).c_str(), best.item_warps, best.inner_fraction,
+              best.relist_soon, best.bin_factor, best.skin_scale);
       fclose(f);
     }
   }

@@ -65,7 +65,7 @@ class FireState(C.Structure):
 
 class Tuning(C.Structure):
     _fields_ = [("item_warps", C.c_int32), ("inner_fraction", C.c_double), ("relist_soon", C.c_double),
-                ("bin_factor", C.c_double)]
+                ("bin_factor", C.c_double), ("skin_scale", C.c_double)]
 
 
 FIRE_STATE_BYTES = C.sizeof(FireState)
@@ -318,10 +318,10 @@ class Batch:
         t = Tuning()
         self._check(lib().ts_batch_tuning(self.h, C.byref(t)), "ts_batch_tuning")
         return dict(item_warps=t.item_warps, inner_fraction=t.inner_fraction, relist_soon=t.relist_soon,
-                    bin_factor=t.bin_factor)
+                    bin_factor=t.bin_factor, skin_scale=t.skin_scale)
 
-    def set_tuning(self, item_warps=8, inner_fraction=0.3, relist_soon=0.5, bin_factor=1.0):
-        t = Tuning(int(item_warps), float(inner_fraction), float(relist_soon), float(bin_factor))
+    def set_tuning(self, item_warps=8, inner_fraction=0.3, relist_soon=0.5, bin_factor=1.0, skin_scale=1.0):
+        t = Tuning(int(item_warps), float(inner_fraction), float(relist_soon), float(bin_factor), float(skin_scale))
         self._check(lib().ts_batch_set_tuning(self.h, C.byref(t)), "ts_batch_set_tuning")
 
     def profile_pair(self, s, reps=5, flush=None, stream=None):

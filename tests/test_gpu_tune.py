@@ -1,8 +1,8 @@
 """The autotuner of the hot path's launch and list parameters (pair work-item
-size, cell-list bin edge, inner-list radius, re-list hysteresis): it picks a
-valid configuration by timing MD steps, caches it, a new batch applies the
-cache at create, and every configuration it can pick gives the oracle's pair
-sets and forces."""
+size, cell-list bin edge, skin scale, inner-list radius, re-list hysteresis):
+it picks a valid configuration by timing MD steps, caches it, a new batch
+applies the cache at create, and every configuration it can pick gives the
+oracle's pair sets and forces."""
 import numpy as np
 import pytest
 
@@ -30,11 +30,12 @@ def test_autotune_picks_caches_and_reloads(tmp_path, orc):
     trial = _copy_state(s)   # the trial steps advance the state they are given
     best = b.autotune(trial, hb.meta["dt"], kind=ts.TS_LANGEVIN, gamma=hb.meta["gamma"], seed=3, n_steps=10)
     assert best["item_warps"] in (4, 8) and best["bin_factor"] in (1.0, 0.5)
-    assert best["inner_fraction"] in (0.2, 0.3, 0.45, 1.0) and best["relist_soon"] in (0.4, 0.5, 0.6)
-    key, iw, inner, soon, binf = open(cache).read().split("\n")[-2].split()
+    assert best["inner_fraction"] in (0.2, 0.3, 0.45, 0.5, 1.0) and best["relist_soon"] in (0.4, 0.5, 0.6)
+    assert best["skin_scale"] in (1.0, 0.9, 0.8)
+    key, iw, inner, soon, binf, scale = open(cache).read().split("\n")[-2].split()
     assert "pots=012" in key and "fp64=0" in key
-    assert (int(iw), float(inner), float(soon), float(binf)) == (best["item_warps"], best["inner_fraction"],
-                                                                 best["relist_soon"], best["bin_factor"])
+    assert (int(iw), float(inner), float(soon), float(binf), float(scale)) == (
+        best["item_warps"], best["inner_fraction"], best["relist_soon"], best["bin_factor"], best["skin_scale"])
     b.close()
     # a new batch of the same configuration starts from the cached tuning
     b2 = ts.Batch(pots, hb.n_atoms, hb.n_systems, autotune_cache=cache)
@@ -57,23 +58,44 @@ def test_tuning_rejects_values_outside_its_ranges():
     from paper_2508_06628_b300 import ts
     hb = small_mix(31, n_systems=3, lo=32, hi=128)
     b = make_batch(hb, ts.TS_MIXED)
-    for bad in (dict(item_warps=6), dict(bin_factor=0.7), dict(inner_fraction=0.0), dict(relist_soon=1.5)):
+    for bad in (dict(item_warps=6), dict(bin_factor=0.7), dict(inner_fraction=0.0), dict(relist_soon=1.5),
+                dict(skin_scale=0.0), dict(skin_scale=1.2)):
         with pytest.raises(ts.TSError) as ei:
             b.set_tuning(**bad)
         assert ei.value.status == ts.TS_ERR_INVALID_ARG
     b.close()
 
 
+def test_cache_line_without_skin_scale_reads_as_one(tmp_path):
+    """A cache line of the earlier five-field format (no skin_scale) applies
+    with the skins unscaled."""
+    torch_cuda()
+    from paper_2508_06628_b300 import ts
+    hb = small_mix(37, n_systems=3, lo=32, hi=128)
+    pots = [dict(p, skin=s) for p, s in zip(hb.pots, ts.default_skins(hb.pots))]
+    probe = ts.Batch(pots, hb.n_atoms, hb.n_systems, autotune_cache=str(tmp_path / "none.txt"))
+    probe.close()
+    cache = tmp_path / "tune.txt"
+    # the key a batch of this configuration looks up (kinds, log2 capacities, precision)
+    na, ns = int(hb.n_atoms).bit_length() - 1, int(hb.n_systems).bit_length() - 1
+    kinds = "".join(str(p["kind"]) for p in pots)
+    cache.write_text(f"pots={kinds};log2atoms={na};log2systems={ns};fp64=0 4 0.2 0.6 0.5\n")
+    b = ts.Batch(pots, hb.n_atoms, hb.n_systems, autotune_cache=str(cache))
+    assert b.tuning() == dict(item_warps=4, inner_fraction=0.2, relist_soon=0.6, bin_factor=0.5, skin_scale=1.0)
+    b.close()
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_half_bins_small_items_pair_sets_forces_and_md(orc, precision):
-    """Bins of half the list radius (two-bin stencils), four-warp items, a
-    tight inner list and a late hysteresis: pair sets equal the oracle's brute
-    force, forces match the oracle, and BAOAB steps follow the oracle."""
+    """Bins of half the list radius (two-bin stencils), four-warp items, the
+    skins scaled by 0.8, a tight inner list and a late hysteresis: pair sets
+    equal the oracle's brute force at the scaled list radius, forces match the
+    oracle, and BAOAB steps follow the oracle."""
     torch = torch_cuda()
     from paper_2508_06628_b300 import ts
     hb = small_mix(41, n_systems=8, lo=32, hi=600)
     b = make_batch(hb, precision)
-    b.set_tuning(item_warps=4, inner_fraction=0.2, relist_soon=0.6, bin_factor=0.5)
+    b.set_tuning(item_warps=4, inner_fraction=0.2, relist_soon=0.6, bin_factor=0.5, skin_scale=0.8)
     s = ts.DeviceState.from_host(hb)
     b.neighbor_build(s, force=True)
     j, img, cnt = b.neighbor_export(s)
@@ -86,7 +108,7 @@ def test_half_bins_small_items_pair_sets_forces_and_md(orc, precision):
     for k in range(hb.n_systems):
         a, e = off[k], off[k + 1]
         pot = hb.pots[hb.pot_idx[k]]
-        rl = (pot["rc"] if pot["kind"] != 2 else pot["p"][0]) + ts.default_skins([pot])[0]
+        rl = (pot["rc"] if pot["kind"] != 2 else pot["p"][0]) + 0.8 * ts.default_skins([pot])[0]
         ref = orc.neighbors(pos[a:e], hb.cell[k], [1, 1, 1], rl)
         h = hb.cell[k]
         near = lambda i, jj, n: abs(np.linalg.norm(pos[a + jj] - pos[a + i] + np.asarray(n) @ h) - rl) < 1e-6
