@@ -32,7 +32,7 @@ BYTES_PER_ATOM = 32         # read own position, write own force, per atom-step
 # DRAM bytes (read + write) of one forces-only k_pair_small launch (inner lists, rc + 0.45 skin) on
 # ragged-mix-512, from one ncu capture of the steady launch; reported only while the kernel's sources
 # (ts_pair.cu, then ts_internal.cuh) hash to the value recorded with the capture
-PAIR_TRAFFIC = {"bytes": 55_926_784 + 718_848, "source_sha1": "87b3ccc3a3fe858a74ee7694332db1d6d2d1bd4e"}
+PAIR_TRAFFIC = {"bytes": 54_294_272 + 569_344, "source_sha1": "87b3ccc3a3fe858a74ee7694332db1d6d2d1bd4e"}
 
 
 def pair_traffic():
