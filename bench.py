@@ -681,7 +681,9 @@ def run_row_diff(args):
     0.005; loss = MSE of the trajectory-averaged 200-bin smeared RDF (to rc)
     against a target from sigma' = 1.05; gradient in (sigma, epsilon) by the
     adjoint over the whole trajectory kept on the device (2001 frames, 2.7 GB:
-    no recomputation).  Host wall time of one loss and gradient evaluation."""
+    no recomputation).  Host wall time of one loss and gradient evaluation;
+    the same evaluation with the workload's checkpoints every 100 steps is
+    timed beside it (wall_s_checkpoint_100)."""
     import torch
     from paper_2508_06628_b300 import grad, ts, workloads as W
     dev = torch.device("cuda", 0)
@@ -723,6 +725,13 @@ def run_row_diff(args):
         gh = gth.cpu().numpy()
         torch.cuda.synchronize()
         t = time.perf_counter() - t0
+        # the workload's own protocol: checkpoints every 100 steps, each segment
+        # recomputed forward and reversed (same loss and gradient up to rounding)
+        t0 = time.perf_counter()
+        loss_c, _, gth_c = grad.rdf_loss_and_grad(b, s, 0.005, T, every, rmax, K, target, checkpoint=100)
+        gh_c = gth_c.cpu().numpy()
+        torch.cuda.synchronize()
+        t_c = time.perf_counter() - t0
     b.poll()
     b.close()
     out = _line("trajectory-gradient atom-steps/s (NVE forward + adjoint)", hb.n_atoms * T / t, UNIT,
@@ -731,7 +740,10 @@ def run_row_diff(args):
                               "to rc vs sigma' = 1.05 target; d loss / d (sigma, epsilon), trajectory kept on the device",
                   "n_systems": hb.n_systems, "n_atoms": hb.n_atoms,
                   "tuning": dict(tuning, autotuned=not args.no_tune, tune_seconds=round(tune_s, 2))},
-                 row="diff", wall_s=t, loss=loss, dloss_dsigma=float(gh[0, 0]), dloss_deps=float(gh[0, 1]),
+                 row="diff", wall_s=t, wall_s_checkpoint_100=t_c,
+                 checkpointed_vs_resident_max_rel_diff=float(np.max(np.abs(gh_c[0, :2] - gh[0, :2]) /
+                                                                    np.maximum(np.abs(gh[0, :2]), 1e-300))),
+                 loss=loss, dloss_dsigma=float(gh[0, 0]), dloss_deps=float(gh[0, 1]),
                  dloss_dsigma_200_steps=float(g200[0, 0]), dloss_deps_200_steps=float(g200[0, 1]))
     if not args.no_cpu:
         from oracle import oracle
