@@ -582,11 +582,16 @@ __global__ void k_after_relist(int32_t B, SysArrays S, int64_t* counters, int md
     if (nre) atomicAdd((unsigned long long*)counters, (unsigned long long)nre);
   }
   // end of the pass: the last block to finish clears the batch-wide flag,
-  // once every block has read it (counters[3]: a wrapping block counter)
+  // once every block has read it (counters[3]: a wrapping block counter); a
+  // single block (batches up to 1024 systems) has read it at the barrier
   __syncthreads();
   if (threadIdx.x == 0) {
-    __threadfence();
-    if (atomicInc((unsigned*)(counters + 3), gridDim.x - 1) == gridDim.x - 1) S.any[0] = 0;
+    if (gridDim.x == 1) {
+      S.any[0] = 0;
+    } else {
+      __threadfence();
+      if (atomicInc((unsigned*)(counters + 3), gridDim.x - 1) == gridDim.x - 1) S.any[0] = 0;
+    }
   }
 }
 
