@@ -241,7 +241,11 @@ __global__ void k_md_final(int32_t n_warps, SysArrays S, SlotArrays A, double ki
       }
       A.vh[k] = vh; A.vl[k] = vl;
       double v0 = (double)vh.x + vl.x, v1 = (double)vh.y + vl.y, v2 = (double)vh.z + vl.z;
-      ke = 0.5 / (double)vh.w * (v0 * v0 + v1 * v1 + v2 * v2);
+      // the mass as the correctly rounded FP32 reciprocal of the stored FP32
+      // inverse mass (half an FP32 ulp, the size of the error the stored
+      // inverse already carries): no FP64 division per atom, which is slow on
+      // this part and runs every step under the chain and the barostat
+      ke = 0.5 * (double)__frcp_rn(vh.w) * (v0 * v0 + v1 * v1 + v2 * v2);
     }
   }
   ke = warp_sum(ke);
