@@ -264,24 +264,33 @@ __global__ void k_set_u64(uint64_t* p, uint64_t v) { *p = v; }
 // h/2 and damped again; the thermostat positions advance by h w; the atoms'
 // velocities scale by exp(-h w1); the same sweep runs bottom up with the new
 // K.  Returns the velocity scale.
-__device__ double nhc_half_step(double h, double K, double nf, double kT, double tau, double* xi, double* w) {
+// The state lives in registers (xi, w by reference to the caller's locals) and
+// the masses' reciprocals are taken once, so that the serial chain of FP64
+// operations (slow on this part) holds no division and no memory round trip.
+struct NhcConst {
+  double nf, kT, q1, qk, iq1, iqk;   // Nf, kT, Q1 = Nf kT tau^2, Qk = kT tau^2, 1/Q1, 1/Qk
+};
+__device__ __forceinline__ double nhc_half_step(double h, double K, const NhcConst& c, double (&xi)[3],
+                                                double (&w)[3]) {
   constexpr int M = 3;
-  const double q1 = nf * kT * tau * tau, qk = kT * tau * tau;
   auto force = [&](int k, double Kin) {   // G_k
-    return k == 0 ? (2.0 * Kin - nf * kT) / q1 : ((k == 1 ? q1 : qk) * w[k - 1] * w[k - 1] - kT) / qk;
+    return k == 0 ? (2.0 * Kin - c.nf * c.kT) * c.iq1 : ((k == 1 ? c.q1 : c.qk) * w[k - 1] * w[k - 1] - c.kT) * c.iqk;
   };
   w[M - 1] += 0.5 * h * force(M - 1, K);
+#pragma unroll
   for (int k = M - 2; k >= 0; k--) {
     const double d = exp(-0.25 * h * w[k + 1]);
     w[k] = (w[k] * d + 0.5 * h * force(k, K)) * d;
   }
+#pragma unroll
   for (int k = 0; k < M; k++) xi[k] += h * w[k];
   const double sc = exp(-h * w[0]);
   K *= sc * sc;
-  for (int k = 0; k < M - 1; k++) {
-    const double d = exp(-0.25 * h * w[k + 1]);
-    w[k] = (w[k] * d + 0.5 * h * force(k, K)) * d;
-  }
+  // the closing sweep's factors use w_2, w_3 as they stand now (the sweep
+  // updates w_1 and w_2 only afterwards): both exponentials go out together
+  const double d0 = exp(-0.25 * h * w[1]), d1 = exp(-0.25 * h * w[2]);
+  w[0] = (w[0] * d0 + 0.5 * h * force(0, K)) * d0;
+  w[1] = (w[1] * d1 + 0.5 * h * force(1, K)) * d1;
   w[M - 1] += 0.5 * h * force(M - 1, K);
   return sc;
 }
@@ -299,14 +308,22 @@ __global__ void k_nhc_update(int32_t B, SysArrays S, const double* __restrict__ 
   for (int w = S.warp_start[s] + lane; w < S.warp_end[s]; w += 32) K += partial[(int64_t)w * kPartialStride + 7];
   K = warp_sum(K);
   if (lane != 0) return;
-  const double nf = fmax(3.0 * S.n_atoms[s] - 3.0, 1.0);
+  NhcConst c;
+  c.nf = fmax(3.0 * S.n_atoms[s] - 3.0, 1.0);
+  c.kT = S.kT[s];
+  c.qk = c.kT * tau * tau;
+  c.q1 = c.nf * c.qk;
+  c.iq1 = 1.0 / c.q1;
+  c.iqk = 1.0 / c.qk;
   double* st = nhc + 6 * (int64_t)s;
+  double xi[3] = {st[0], st[1], st[2]}, w[3] = {st[3], st[4], st[5]};
   double sc = 1.0;
   for (int q = 0; q < halves; q++) {
-    const double c = nhc_half_step(0.5 * dt, K, nf, S.kT[s], tau, st, st + 3);
-    K *= c * c;
-    sc *= c;
+    const double f = nhc_half_step(0.5 * dt, K, c, xi, w);
+    K *= f * f;
+    sc *= f;
   }
+  for (int q = 0; q < 3; q++) { st[q] = xi[q]; st[3 + q] = w[q]; }
   vscale[s] = sc;
 }
 
