@@ -508,7 +508,7 @@ ts_status prologue(ts_batch* b, ts_state* s, cudaStream_t st, bool import_vel, b
   const int cell_check = b->first_import ? 0 : (fire ? 1 : 2);
   if (geometry || b->first_import) {
     k_geometry<<<(B + 31) / 32, 32, 0, st>>>(B, b->S, s->cell, s->pbc, b->d_pots, b->d_err, cell_check);
-    k_shift_table<<<(int)(((int64_t)B * 32 + 127) / 128), 128, 0, st>>>(B, b->S);
+    k_shift_table<<<B, 128, 0, st>>>(B, b->S);
     b->launches += 2;
   }
   int g = grid_for(b->Npad, 256);

@@ -353,7 +353,7 @@ extern "C" ts_status ts_fire_step(ts_batch* b, ts_state* s, ts_fire_state* fs, d
     if (b->f64) k_fire_update<true><<<g, 256, 0, st>>>(b->Npad, b->S, b->A, b->d_scal, b->d_fcoef, b->d_pots);
     else k_fire_update<false><<<g, 256, 0, st>>>(b->Npad, b->S, b->A, b->d_scal, b->d_fcoef, b->d_pots);
     k_geometry<<<(b->B + 31) / 32, 32, 0, st>>>(b->B, b->S, s->cell, s->pbc, b->d_pots, b->d_err, 0);
-    k_shift_table<<<(int)(((int64_t)b->B * 32 + 127) / 128), 128, 0, st>>>(b->B, b->S);
+    k_shift_table<<<b->B, 128, 0, st>>>(b->B, b->S);
     b->launches += 3;
     relist(b, st, true);
     pair(b, st, true, false);

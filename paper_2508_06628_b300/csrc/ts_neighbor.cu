@@ -312,15 +312,16 @@ __global__ void k_geometry(int32_t B, SysArrays S, const double* __restrict__ ce
 }
 
 // Image shift table S = n h for every image code within the system's table
-// bound (S.tbound), stored hi/lo (mixed), FP64 and fixed point.  One warp per
-// system; a system whose cell did not change keeps its tables.
+// bound (S.tbound), stored hi/lo (mixed), FP64 and fixed point.  One CTA per
+// system, its threads over the codes (up to 729 for a small cell, whose FP64
+// work per code would otherwise set the launch's length); a system whose cell
+// did not change keeps its tables.
 __global__ void k_shift_table(int32_t B, SysArrays S) {
-  const int s = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
-  const int lane = threadIdx.x & 31;
+  const int s = blockIdx.x;
   if (s >= B || !(S.geom[s] & 2)) return;   // cell unchanged: the tables stand
   const int tb = S.tbound[s], side = 2 * tb + 1;
   const double* h = S.h + 9 * s;
-  for (int i = lane; i < side * side * side; i += 32) {
+  for (int i = threadIdx.x; i < side * side * side; i += blockDim.x) {
     const int nx = i % side - tb, ny = (i / side) % side - tb, nz = i / (side * side) - tb;
     const int64_t t = (int64_t)s * kNCodes + img_code(nx, ny, nz);
     double v[3];

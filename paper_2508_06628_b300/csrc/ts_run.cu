@@ -84,7 +84,7 @@ static void md_body(ts_batch* b, cudaStream_t st, const ts_md_params* p, int n_s
     b->launches++;
     if (npt) {   // geometry and image shifts of the new cell (k_npt_sys scaled it)
       k_geometry<<<(b->B + 31) / 32, 32, 0, st>>>(b->B, b->S, b->S.h, nullptr, b->d_pots, b->d_err, 0, 1, 1);
-      k_shift_table<<<(int)(((int64_t)b->B * 32 + 127) / 128), 128, 0, st>>>(b->B, b->S);
+      k_shift_table<<<b->B, 128, 0, st>>>(b->B, b->S);
       b->launches += 2;
     }
     bool ew = npt || (need_e && k == n_steps - 1);   // NPT: the virial drives the piston
