@@ -273,20 +273,25 @@ __global__ void k_geometry(int32_t B, SysArrays S, const double* __restrict__ ce
   g[6] = (h[3] * h[7] - h[4] * h[6]) * id; g[7] = (h[1] * h[6] - h[0] * h[7]) * id;
   g[8] = (h[0] * h[4] - h[1] * h[3]) * id;
   for (int q = 0; q < 9; q++) { S.hinv[9 * s + q] = g[q]; S.hinvf[9 * s + q] = (float)g[q]; }
-  double V = fabs(d), w[3];
+  // widths w_a = V / |b x c| between opposite faces, and their reciprocals
+  // |b x c| / V from the reciprocal already taken: one divide per axis
+  double V = fabs(d), w[3], iw[3];
   double ext = 0;
   for (int a = 0; a < 3; a++) {
     const double* b = h + 3 * ((a + 1) % 3);
     const double* c = h + 3 * ((a + 2) % 3);
     double cx = b[1] * c[2] - b[2] * c[1], cy = b[2] * c[0] - b[0] * c[2], cz = b[0] * c[1] - b[1] * c[0];
-    w[a] = V / sqrt(cx * cx + cy * cy + cz * cz);
+    const double nc = sqrt(cx * cx + cy * cy + cz * cz);
+    w[a] = V / nc;
+    iw[a] = nc * fabs(id);
     ext += fabs(h[3 * a]) + fabs(h[3 * a + 1]) + fabs(h[3 * a + 2]);
   }
   double rl = pots[S.pot[s]].rlist, bw = pots[S.pot[s]].binw;
+  const double ibw = 1.0 / bw;
   int nb[3], m[3];
   bool bad = false;
   for (int a = 0; a < 3; a++) {
-    double f = floor(w[a] / bw);
+    double f = floor(w[a] * ibw);
     nb[a] = f < 1.0 ? 1 : (f > 1024.0 ? 1024 : (int)f);
   }
   int cap = S.bin_cap[s];
@@ -296,7 +301,7 @@ __global__ void k_geometry(int32_t B, SysArrays S, const double* __restrict__ ce
     if (nb[0] == 1 && nb[1] == 1 && nb[2] == 1) break;
   }
   for (int a = 0; a < 3; a++) {
-    m[a] = (int)ceil(rl * nb[a] / w[a]);
+    m[a] = (int)ceil(rl * nb[a] * iw[a]);
     if (m[a] < 1) m[a] = 1;
     if (!(pm >> a & 1)) m[a] = m[a] < nb[a] ? m[a] : nb[a];   // open axis: no images, the stencil stops at the edges
     else if (m[a] > kMaxReach) { m[a] = kMaxReach; atomicOr(err, kErrUnsupported); bad = true; }
