@@ -118,3 +118,59 @@ def test_noalloc_rejects_too_many_systems():
     st = L.ts_pair_forces_noalloc(pots, 1, C.byref(st_c), C.c_void_p(dummy.data_ptr()), C.c_void_p(dummy.data_ptr()),
                                   None, None, None)
     assert st == ts.TS_ERR_BUDGET
+
+
+def _wrapped(hb, pos):
+    """Positions moved into their cells (fractional coordinates in [0, 1))."""
+    out = np.empty_like(pos)
+    off = hb.offsets
+    for k in range(hb.n_systems):
+        f = pos[off[k]:off[k + 1]] @ np.linalg.inv(hb.cell[k])
+        out[off[k]:off[k + 1]] = (f - np.floor(f)) @ hb.cell[k]
+    return out
+
+
+def test_noalloc_replays_inside_a_captured_graph(orc):
+    """After one warm call the entry point can be captured into a CUDA graph in
+    global capture mode (in which a cudaMalloc from any thread breaks the
+    capture).  Each replay, on positions changed in place, gives the oracle's
+    results and the bits of an eager call on the same positions."""
+    torch = torch_cuda()
+    ts, L = _lib()
+    hb = small_mix(94, n_systems=6, lo=32, hi=250)
+    rng = np.random.default_rng(94)
+    dev = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
+    pos = dev(_wrapped(hb, hb.pos), torch.float64)
+    cell, sidx, pot = dev(hb.cell, torch.float64), dev(hb.system_idx, torch.int32), dev(hb.pot_idx, torch.int32)
+    off = dev(hb.offsets, torch.int64)
+    F = torch.empty((hb.n_atoms, 3), dtype=torch.float64, device="cuda")
+    E = torch.empty(hb.n_systems, dtype=torch.float64, device="cuda")
+    S = torch.empty((hb.n_systems, 3, 3), dtype=torch.float64, device="cuda")
+    state = ts.State(hb.n_systems, hb.n_atoms, C.c_void_p(pos.data_ptr()), None, None, C.c_void_p(cell.data_ptr()),
+                     None, C.c_void_p(sidx.data_ptr()), C.c_void_p(pot.data_ptr()), None)
+    pots = ts.potentials(hb.pots)
+
+    def call():
+        return L.ts_pair_forces_noalloc(pots, len(hb.pots), C.byref(state), C.c_void_p(off.data_ptr()),
+                                        C.c_void_p(F.data_ptr()), C.c_void_p(E.data_ptr()),
+                                        C.c_void_p(S.data_ptr()), C.c_void_p(torch.cuda.current_stream().cuda_stream))
+
+    assert call() == ts.TS_OK            # the warm call looks up the table's address
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        st = call()
+    assert st == ts.TS_OK
+    for rep in range(2):
+        p = _wrapped(hb, hb.pos + rng.normal(0.0, 0.02, hb.pos.shape))
+        pos.copy_(torch.as_tensor(p))
+        F.fill_(np.nan); E.fill_(np.nan); S.fill_(np.nan)
+        g.replay()
+        torch.cuda.synchronize()
+        Fg, Eg, Sg = F.cpu().numpy(), E.cpu().numpy(), S.cpu().numpy()
+        Er, Fr, Sr = orc.forces(hb.offsets, p, hb.cell, hb.pbc, hb.pot_idx, hb.pots)
+        assert _fp64_ok(Fg, Eg, Sg, Fr, Er, Sr), f"replay {rep}: vs the oracle"
+        assert call() == ts.TS_OK
+        torch.cuda.synchronize()
+        assert (np.array_equal(F.cpu().numpy(), Fg) and np.array_equal(E.cpu().numpy(), Eg) and
+                np.array_equal(S.cpu().numpy(), Sg)), f"replay {rep}: vs an eager call"
