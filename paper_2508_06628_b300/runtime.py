@@ -394,6 +394,24 @@ class HostMD:
             E[g["ids"]] = g["E_h"].numpy(); KE[g["ids"]] = g["KE_h"].numpy()
         return pos, vel, E, KE
 
+    def set_state(self, pos=None, vel=None):
+        """Replace positions and/or velocities ([n_atoms, 3] in the order of
+        ``hb``) in the host buffers; the next call starts from them.  Waits
+        for the calls enqueued so far first, since their copies back write
+        these buffers."""
+        self.synchronize()
+        for name, a in (("pos", pos), ("vel", vel)):
+            if a is None:
+                continue
+            a = np.asarray(a, dtype=np.float64)
+            if a.shape != (self.n_atoms, 3):
+                raise ValueError(f"{name}: shape {a.shape}, expected ({self.n_atoms}, 3)")
+            for g in self.groups:
+                buf = g[name].numpy()
+                for j, i in enumerate(g["ids"]):
+                    a0, e, ga = self.offsets[i], self.offsets[i + 1], g["off"][j]
+                    buf[ga:ga + e - a0] = a[a0:e]
+
     def close(self):
         for g in self.groups:
             g["b"].close()

@@ -56,11 +56,16 @@ def test_host_md_state_edits_between_calls(monkeypatch):
     pots = [dict(p, skin=s) for p, s in zip(hb.pots, skins_for(hb.pots))]
     hm = runtime.HostMD(hb, pots, parts=2)
     hm.step(5, hb.meta["dt"], kind=ts.TS_NVE)
-    _, vel0, _, _ = hm.state()
-    for g in hm.groups:
-        g["vel"].zero_()
+    pos0, vel0, _, _ = hm.state()
+    # set_state scatters caller-ordered arrays into the groups' buffers
+    moved = pos0 + np.arange(hb.n_atoms)[:, None] * 1e-7
+    hm.set_state(pos=moved)
+    assert np.array_equal(hm.state()[0], moved)
+    hm.set_state(pos=pos0, vel=np.zeros_like(vel0))
     hm.step(1, hb.meta["dt"], kind=ts.TS_NVE, step0=5)
     _, vel1, _, KE1 = hm.state()
+    with pytest.raises(ValueError):
+        hm.set_state(vel=np.zeros((hb.n_atoms + 1, 3)))
     hm.close()
     # from rest, one velocity-Verlet step leaves v = dt F / m: nonzero, and far
     # below the thermal velocities the systems had before (the call did not
